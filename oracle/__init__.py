@@ -1,0 +1,227 @@
+"""ctypes binding of the FP64 CPU oracle (``dp_oracle.cpp``).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py``; never by the library. It takes the plain numpy arrays of a
+workload description (any object with the attributes of ``workloads.Model``) and never
+touches the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "dp_oracle.cpp")
+LIB = os.path.join(HERE, "_build", "liboracle.so")
+
+
+def build(force=False):
+    """Compile the oracle with the host C++ compiler (plain IEEE FP64, no fast-math)."""
+    os.makedirs(os.path.dirname(LIB), exist_ok=True)
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
+        return LIB
+    tmp = LIB + ".tmp%d" % os.getpid()
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, SRC])
+    os.replace(tmp, LIB)
+    return LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        _lib.orc_bf16.restype = C.c_double
+        _lib.orc_bf16.argtypes = [C.c_double]
+    return _lib
+
+
+PI = C.POINTER(C.c_int32)
+PD = C.POINTER(C.c_double)
+
+
+class Topo(C.Structure):
+    _fields_ = [("nb", C.c_int32), ("nj", C.c_int32), ("ns", C.c_int32), ("np", C.c_int32),
+                ("joint_type", PI), ("joint_body", PI), ("joint_flags", PI), ("sphere_body", PI),
+                ("pair_sphere", PI), ("n_layers", C.c_int32), ("widths", PI), ("skip", C.c_int32),
+                ("features", C.c_int32), ("imu_body", C.c_int32), ("clock_hz", C.c_double),
+                ("gravity", C.c_double * 3), ("dt", C.c_double), ("ground_z", C.c_double),
+                ("beta", C.c_double), ("gamma", C.c_double), ("slop", C.c_double), ("iters", C.c_int32),
+                ("loss_kind", C.c_int32), ("loss_mode", C.c_int32), ("loss_body", C.c_int32),
+                ("exact_mlp", C.c_int32)]
+
+
+INST_FIELDS = ("mass", "inertia", "anchor", "axis", "ref", "limit", "motor", "sph_off", "sph_rad", "sph_mu",
+               "sph_e", "loss_point", "loss_target", "state0")
+
+
+class Inst(C.Structure):
+    _fields_ = [(k, PD) for k in INST_FIELDS]
+
+
+class Grad(C.Structure):
+    _fields_ = [(k, PD) for k in INST_FIELDS + ("W",)]
+
+
+def _ip(a):
+    return a.ctypes.data_as(PI)
+
+
+def _dp(a):
+    return a.ctypes.data_as(PD)
+
+
+class _Keep:
+    """Holds the numpy buffers referenced by a ctypes structure."""
+
+    def __init__(self):
+        self.refs = []
+
+    def i32(self, a):
+        a = np.ascontiguousarray(np.asarray(a, dtype=np.int32).reshape(-1))
+        if a.size == 0:
+            a = np.zeros(1, np.int32)
+        self.refs.append(a)
+        return _ip(a)
+
+    def f64(self, a):
+        a = np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
+        if a.size == 0:
+            a = np.zeros(1, np.float64)
+        self.refs.append(a)
+        return _dp(a)
+
+
+def topo(m, keep, iters=None):
+    t = Topo()
+    t.nb, t.nj, t.ns, t.np = m.nb, m.nj, m.ns, m.np_
+    t.joint_type = keep.i32(m.joint_type)
+    t.joint_body = keep.i32(m.joint_body)
+    t.joint_flags = keep.i32(m.joint_flags)
+    t.sphere_body = keep.i32(m.sphere_body)
+    t.pair_sphere = keep.i32(m.pair_sphere)
+    t.n_layers = max(len(m.widths) - 1, 0)
+    t.widths = keep.i32(m.widths if m.widths else [0])
+    t.skip = m.skip
+    t.features = m.features
+    t.imu_body = m.imu_body
+    t.clock_hz = m.clock_hz
+    for k in range(3):
+        t.gravity[k] = m.gravity[k]
+    t.dt, t.ground_z, t.beta, t.gamma, t.slop = m.dt, m.ground_z, m.beta, m.gamma, m.slop
+    t.iters = m.iters if iters is None else iters
+    t.loss_kind, t.loss_mode, t.loss_body = m.loss_kind, m.loss_mode, m.loss_body
+    t.exact_mlp = int(getattr(m, "exact_mlp", 0))
+    return t
+
+
+def inst(m, i, keep, state0=None, overrides=None):
+    s = Inst()
+    for k in INST_FIELDS:
+        a = getattr(m, k)[i]
+        if k == "state0" and state0 is not None:
+            a = state0
+        if overrides and k in overrides:
+            a = overrides[k]
+        setattr(s, k, keep.f64(a))
+    return s
+
+
+def weights(m, keep, W=None):
+    W = m.W if W is None else W
+    if W is None or len(W) == 0:
+        return keep.f64(np.zeros(1))
+    return keep.f64(np.asarray(W, dtype=np.float64))
+
+
+def n_slots(m):
+    keep = _Keep()
+    return lib().orc_num_slots(C.byref(topo(m, keep)))
+
+
+def schedule(m):
+    """Static row schedule: dict of per-slot kind, idx, sub, body_a, body_b, colour and the
+    sweep order."""
+    keep = _Keep()
+    t = topo(m, keep)
+    n = lib().orc_num_slots(C.byref(t))
+    out = {k: np.zeros(max(n, 1), np.int32) for k in ("kind", "idx", "sub", "body_a", "body_b", "colour", "order")}
+    r = lib().orc_schedule(C.byref(t), *[_ip(out[k]) for k in ("kind", "idx", "sub", "body_a", "body_b", "colour", "order")])
+    assert r == n
+    return {k: v[:n] for k, v in out.items()}
+
+
+def rollout(m, i, horizon=None, W=None, log=False, iters=None, overrides=None):
+    """Roll instance ``i`` forward. Returns (states [T+1, nb, 18], loss, active, gap)."""
+    T = m.horizon if horizon is None else horizon
+    keep = _Keep()
+    t = topo(m, keep, iters)
+    s = inst(m, i, keep, overrides=overrides)
+    ns = lib().orc_num_slots(C.byref(t))
+    states = np.zeros((T + 1, m.nb, 18))
+    loss = C.c_double(0.0)
+    active = np.zeros((T, max(ns, 1)), np.int8) if log else None
+    gap = np.zeros((T, max(ns, 1))) if log else None
+    r = lib().orc_rollout(C.byref(t), C.byref(s), weights(m, keep, W), T, _dp(states), C.byref(loss),
+                          active.ctypes.data_as(C.POINTER(C.c_int8)) if log else None,
+                          _dp(gap) if log else None)
+    if r != 0:
+        raise ValueError("oracle rejected the model")
+    if log:
+        return states, loss.value, active[:, :ns], gap[:, :ns]
+    return states, loss.value, None, None
+
+
+def step(m, i, x, t=0, W=None, iters=None):
+    """One step from state ``x`` [nb, 18] at step index ``t``; returns (x_next, active, gap, lambda)."""
+    keep = _Keep()
+    tp = topo(m, keep, iters)
+    s = inst(m, i, keep)
+    ns = lib().orc_num_slots(C.byref(tp))
+    x = np.ascontiguousarray(np.asarray(x, np.float64).reshape(-1))
+    xn = np.zeros_like(x)
+    active = np.zeros(max(ns, 1), np.int8)
+    gap = np.zeros(max(ns, 1))
+    lam = np.zeros(max(ns, 1))
+    r = lib().orc_step(C.byref(tp), C.byref(s), weights(m, keep, W), t, _dp(x), _dp(xn),
+                       active.ctypes.data_as(C.POINTER(C.c_int8)), _dp(gap), _dp(lam))
+    if r != 0:
+        raise ValueError("oracle rejected the model")
+    return xn.reshape(m.nb, 18), active[:ns], gap[:ns], lam[:ns]
+
+
+def rollout_grad(m, i, horizon=None, W=None, iters=None, overrides=None):
+    """Loss and gradient dict (same keys/shapes as the per-instance fields, plus ``W``)."""
+    T = m.horizon if horizon is None else horizon
+    keep = _Keep()
+    t = topo(m, keep, iters)
+    s = inst(m, i, keep, overrides=overrides)
+    g = Grad()
+    out = {}
+    for k in INST_FIELDS:
+        out[k] = np.zeros(getattr(m, k)[i].shape)
+        setattr(g, k, keep.f64(out[k]) if out[k].size else None)
+        out[k] = keep.refs[-1].reshape(out[k].shape) if out[k].size else out[k]
+    nW = 0 if m.W is None else len(m.W)
+    out["W"] = np.zeros(max(nW, 1))
+    g.W = _dp(out["W"])
+    loss = C.c_double(0.0)
+    r = lib().orc_rollout_grad(C.byref(t), C.byref(s), weights(m, keep, W), T, C.byref(loss), C.byref(g))
+    if r != 0:
+        raise ValueError("oracle rejected the model")
+    out["W"] = out["W"][:nW]
+    return loss.value, out
+
+
+def param_count(widths, skip=0):
+    w = np.asarray(widths, np.int32)
+    return lib().orc_param_count(len(widths) - 1, _ip(w), skip)
+
+
+def bf16(x):
+    return lib().orc_bf16(float(x))

@@ -1,0 +1,401 @@
+"""Seeded synthetic workloads: robot descriptions and initial states.
+
+This module only *builds inputs*: body geometry, masses, inertias, joint frames, sphere
+placements, initial poses and controller weights. It holds none of the stepping arithmetic
+and is the one module that both the CUDA path and the FP64 oracle tests consume.
+
+Every floating-point value is rounded to float32 before it is handed out (stored as float64
+here), so the oracle and the GPU library read bit-identical inputs.
+
+Workloads (the paper's experiments give their shapes; section numbers refer to the paper):
+  * ``ball``       - one sphere thrown onto the ground (section 2.1.1 "Throwing a Ball").
+  * ``pendulum3``  - contact-free 3-link hinge chains (shaped like the arm of section 3.2).
+  * ``quadruped``  - box torso, 4 legs x 2 links on hinges with limits and servo motors,
+                     sphere feet and 4 spheres inside the torso (section 3.1 and Fig. 3B),
+                     driven by a dense controller (Eq. g).
+  * ``two_spheres``- two free spheres colliding (sphere-sphere contact check).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# Joint types, flags, feature bits and loss kinds (the same values are part of the C ABI).
+BALL, HINGE = 0, 1
+FLAG_LIMIT, FLAG_MOTOR = 1, 2
+F_ANGLES, F_RATES, F_CLOCK, F_IMU, F_TARGET = 1, 2, 4, 8, 16
+L_SQDIST, L_DIST, L_LINEAR, L_DISP = 0, 1, 2, 3
+M_FINAL, M_MEAN = 0, 1
+
+
+def f32(x):
+    """Round to float32 and return float64 holding the same value."""
+    return np.asarray(x, dtype=np.float64).astype(np.float32).astype(np.float64)
+
+
+@dataclass
+class Model:
+    """A batch of robots that share one topology (one bin)."""
+
+    name: str
+    B: int
+    # topology
+    joint_type: np.ndarray
+    joint_body: np.ndarray
+    joint_flags: np.ndarray
+    sphere_body: np.ndarray
+    pair_sphere: np.ndarray
+    nb: int
+    # per-instance parameters, leading dimension B
+    mass: np.ndarray
+    inertia: np.ndarray
+    anchor: np.ndarray
+    axis: np.ndarray
+    ref: np.ndarray
+    limit: np.ndarray
+    motor: np.ndarray
+    sph_off: np.ndarray
+    sph_rad: np.ndarray
+    sph_mu: np.ndarray
+    sph_e: np.ndarray
+    loss_point: np.ndarray
+    loss_target: np.ndarray
+    state0: np.ndarray
+    # controller
+    widths: list = field(default_factory=list)
+    skip: int = 0
+    features: int = 0
+    imu_body: int = 0
+    clock_hz: float = 0.0
+    W: np.ndarray | None = None
+    # constants
+    gravity: tuple = (0.0, 0.0, -9.81)
+    dt: float = 0.01
+    ground_z: float = 0.0
+    beta: float = 0.2
+    gamma: float = 0.0
+    slop: float = 0.005
+    iters: int = 20
+    horizon: int = 100
+    ckpt_every: int = 0
+    loss_kind: int = L_SQDIST
+    loss_mode: int = M_FINAL
+    loss_body: int = 0
+
+    @property
+    def nj(self):
+        return int(len(self.joint_type))
+
+    @property
+    def ns(self):
+        return int(len(self.sphere_body))
+
+    @property
+    def np_(self):
+        return int(len(self.pair_sphere))
+
+    def subset(self, idx):
+        """Instances ``idx`` of the batch as a new Model (shared topology/controller)."""
+        idx = np.atleast_1d(np.asarray(idx))
+        names = [f.name for f in dataclasses.fields(self)]
+        kw = {k: getattr(self, k) for k in names}
+        for k in PER_INSTANCE:
+            kw[k] = getattr(self, k)[idx].copy()
+        kw["B"] = int(len(idx))
+        out = Model(**kw)
+        for k, v in self.__dict__.items():
+            if k not in names and isinstance(v, np.ndarray) and len(v) == self.B:
+                setattr(out, k, v[idx].copy())
+        return out
+
+
+PER_INSTANCE = ("mass", "inertia", "anchor", "axis", "ref", "limit", "motor", "sph_off", "sph_rad",
+                "sph_mu", "sph_e", "loss_point", "loss_target", "state0")
+
+
+def param_count(widths, skip=0):
+    """Number of controller parameters: per dense layer W [out][in] and a bias [out];
+    with ``skip`` the output layer also has a second biased dense layer from the input."""
+    if not widths:
+        return 0
+    n = sum(widths[i] * widths[i + 1] + widths[i + 1] for i in range(len(widths) - 1))
+    if skip:
+        n += widths[0] * widths[-1] + widths[-1]
+    return n
+
+
+def xavier_weights(widths, skip, rng, zero_output=False):
+    """Flat float32 controller parameters: Xavier-uniform weights, zero biases."""
+    parts = []
+    L = len(widths) - 1
+    for l in range(L):
+        ni, no = widths[l], widths[l + 1]
+        a = math.sqrt(6.0 / (ni + no))
+        w = rng.uniform(-a, a, size=(no, ni))
+        if zero_output and l == L - 1:
+            w[:] = 0.0
+        parts += [w.ravel(), np.zeros(no)]
+    if skip:
+        ni, no = widths[0], widths[-1]
+        a = math.sqrt(6.0 / (ni + no))
+        w = rng.uniform(-a, a, size=(no, ni))
+        if zero_output:
+            w[:] = 0.0
+        parts += [w.ravel(), np.zeros(no)]
+    return np.concatenate(parts).astype(np.float32) if parts else np.zeros(0, np.float32)
+
+
+def _rot_z(psi):
+    c, s = math.cos(psi), math.sin(psi)
+    return np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
+
+
+def _rot_y(phi):
+    c, s = math.cos(phi), math.sin(phi)
+    return np.array([[c, 0.0, s], [0.0, 1.0, 0.0], [-s, 0.0, c]])
+
+
+def _state(p, R, v, w):
+    return np.concatenate([p, R.reshape(9), v, w])
+
+
+def _empty(B, nb, nj, ns):
+    return dict(
+        mass=np.zeros((B, nb)), inertia=np.zeros((B, nb, 3)), anchor=np.zeros((B, nj, 2, 3)),
+        axis=np.zeros((B, nj, 2, 3)), ref=np.zeros((B, nj, 2, 3)), limit=np.zeros((B, nj, 2)),
+        motor=np.zeros((B, nj, 3)), sph_off=np.zeros((B, ns, 3)), sph_rad=np.zeros((B, ns)),
+        sph_mu=np.zeros((B, ns)), sph_e=np.zeros((B, ns)), loss_point=np.zeros((B, 3)),
+        loss_target=np.zeros((B, 3)), state0=np.zeros((B, nb, 18)))
+
+
+def _finish(d):
+    for k in PER_INSTANCE:
+        d[k] = f32(d[k])
+    return d
+
+
+def ball(B=1, seed=1000, horizon=300, iters=20, dt=0.01):
+    """Sphere r=0.1 m, m=1 kg, launched from the ground with speed U[2,8] m/s, elevation
+    U[20,70] deg, azimuth U[0,2pi); ground friction 0.5, restitution 0. Loss: squared distance
+    of the final centre to a seeded target point."""
+    rng = np.random.default_rng(seed)
+    d = _empty(B, 1, 0, 1)
+    r, m = 0.1, 1.0
+    d["mass"][:] = m
+    d["inertia"][:] = 0.4 * m * r * r
+    d["sph_rad"][:] = r
+    d["sph_mu"][:] = 0.5
+    d["sph_e"][:] = 0.0
+    for i in range(B):
+        sp = rng.uniform(2.0, 8.0)
+        el = math.radians(rng.uniform(20.0, 70.0))
+        az = rng.uniform(0.0, 2.0 * math.pi)
+        v = sp * np.array([math.cos(el) * math.cos(az), math.cos(el) * math.sin(az), math.sin(el)])
+        d["state0"][i, 0] = _state(np.array([0.0, 0.0, r]), np.eye(3), v, np.zeros(3))
+        d["loss_target"][i] = [rng.uniform(-5, 5), rng.uniform(-5, 5), r]
+    _finish(d)
+    return Model(name="ball", B=B, joint_type=np.zeros(0, np.int32), joint_body=np.zeros((0, 2), np.int32),
+                 joint_flags=np.zeros(0, np.int32), sphere_body=np.zeros(1, np.int32),
+                 pair_sphere=np.zeros((0, 2), np.int32), nb=1, dt=dt, iters=iters, horizon=horizon,
+                 loss_kind=L_SQDIST, loss_mode=M_FINAL, loss_body=0, **d)
+
+
+def pendulum3(B=1024, seed=1001, horizon=1000, iters=10, dt=0.001, ckpt_every=32, rod_radius=0.02):
+    """3-link pendulum chains, first hinge pinned to the world at the origin, horizontal (y)
+    hinge axes. Links are uniform rods (thin cylinders of radius ``rod_radius``) of length
+    U[0.3,1.0] m and mass U[0.5,2.0] kg; relative initial angles U[-pi/2, pi/2]. Loss: height
+    of the far end of the last link at the final step."""
+    rng = np.random.default_rng(seed)
+    nb = nj = 3
+    d = _empty(B, nb, nj, 0)
+    Ls = np.zeros((B, nb))
+    for i in range(B):
+        L = rng.uniform(0.3, 1.0, size=nb)
+        m = rng.uniform(0.5, 2.0, size=nb)
+        th = rng.uniform(-math.pi / 2, math.pi / 2, size=nb)
+        Ls[i] = L
+        phi = 0.0
+        pivot = np.zeros(3)
+        for k in range(nb):
+            phi += th[k]
+            R = _rot_y(phi)
+            c = pivot + R @ np.array([0.0, 0.0, -L[k] / 2])
+            d["state0"][i, k] = _state(c, R, np.zeros(3), np.zeros(3))
+            pivot = pivot + R @ np.array([0.0, 0.0, -L[k]])
+            d["mass"][i, k] = m[k]
+            It = m[k] * (3 * rod_radius ** 2 + L[k] ** 2) / 12.0
+            d["inertia"][i, k] = [It, It, 0.5 * m[k] * rod_radius ** 2]
+            d["anchor"][i, k, 0] = [0.0, 0.0, 0.0] if k == 0 else [0.0, 0.0, -L[k - 1] / 2]
+            d["anchor"][i, k, 1] = [0.0, 0.0, L[k] / 2]
+            d["axis"][i, k, :] = [0.0, 1.0, 0.0]
+            d["ref"][i, k, :] = [1.0, 0.0, 0.0]
+        d["loss_point"][i] = [0.0, 0.0, -L[2] / 2]
+        d["loss_target"][i] = [0.0, 0.0, 1.0]
+    _finish(d)
+    mdl = Model(name="pendulum3", B=B, joint_type=np.full(nj, HINGE, np.int32),
+                joint_body=np.array([[-1, 0], [0, 1], [1, 2]], np.int32), joint_flags=np.zeros(nj, np.int32),
+                sphere_body=np.zeros(0, np.int32), pair_sphere=np.zeros((0, 2), np.int32), nb=nb, dt=dt,
+                iters=iters, horizon=horizon, ckpt_every=ckpt_every, loss_kind=L_LINEAR, loss_mode=M_FINAL,
+                loss_body=2, **d)
+    mdl.link_length = f32(Ls)
+    return mdl
+
+
+def _capsule_inertia(m, r, L):
+    """Principal moments of a solid capsule (cylinder of length L and radius r along z plus two
+    hemispherical caps), total mass m."""
+    vc = math.pi * r * r * L
+    vs = 4.0 / 3.0 * math.pi * r ** 3
+    mc, ms = m * vc / (vc + vs), m * vs / (vc + vs)
+    Iz = mc * r * r / 2 + ms * 2 * r * r / 5
+    Ix = mc * (L * L / 12 + r * r / 4) + ms * (2 * r * r / 5 + L * L / 4 + 3 * L * r / 8)
+    return [Ix, Ix, Iz]
+
+
+QUADRUPED_WIDTHS = [24, 128, 128, 8]
+
+
+def quadruped(B=4096, seed=1002, horizon=1000, iters=20, dt=0.01, widths=None, skip=0, yaw=0.3, vel=0.1,
+              w_seed=None):
+    """Quadruped: box torso 0.6x0.3x0.1 m, 8 kg; 4 legs x 2 capsule links (0.2 m, radius 0.025,
+    0.5 kg) on hinges about the body y axis with limits +-60 deg and servo motors (gain 30 1/s,
+    4 N m, 45 deg/s); sphere feet r=0.03 and four r=0.05 spheres inside the torso, all touching
+    the ground with mu=0.8, e=0. Hips at the torso corners. Dense controller
+    24->128->128->8 (Xavier-uniform, seeded) fed by 8 joint angles, 8 joint rates, a
+    1.5 Hz sin/cos clock and the torso's gravity direction and angular rate (body frame).
+    Loss: negative forward (x) displacement of the torso. Per instance a seeded yaw in
+    [-yaw, yaw] and a common horizontal velocity in [-vel, vel]^2."""
+    rng = np.random.default_rng(seed)
+    widths = list(widths or QUADRUPED_WIDTHS)
+    nb, nj, ns = 9, 8, 8
+    d = _empty(B, nb, nj, ns)
+    hips = [(0.3, 0.15), (0.3, -0.15), (-0.3, 0.15), (-0.3, -0.15)]
+    link, crad, cm = 0.2, 0.025, 0.5
+    foot_r, torso_r = 0.03, 0.05
+    z0 = 2 * link + foot_r - 0.001  # feet start 1 mm inside the ground (inside the slop)
+    jt = np.full(nj, HINGE, np.int32)
+    jb = np.zeros((nj, 2), np.int32)
+    jf = np.full(nj, FLAG_LIMIT | FLAG_MOTOR, np.int32)
+    sb = np.zeros(ns, np.int32)
+    # local body poses at yaw 0 (body frame axes aligned with the world)
+    local = [np.array([0.0, 0.0, z0])]
+    for l, (hx, hy) in enumerate(hips):
+        local.append(np.array([hx, hy, z0 - link / 2]))
+        local.append(np.array([hx, hy, z0 - 1.5 * link]))
+        jb[2 * l] = [0, 1 + 2 * l]
+        jb[2 * l + 1] = [1 + 2 * l, 2 + 2 * l]
+        sb[l] = 2 + 2 * l
+        sb[4 + l] = 0
+    I_torso = [8.0 / 12 * (0.3 ** 2 + 0.1 ** 2), 8.0 / 12 * (0.6 ** 2 + 0.1 ** 2), 8.0 / 12 * (0.6 ** 2 + 0.3 ** 2)]
+    I_link = _capsule_inertia(cm, crad, link)
+    for i in range(B):
+        psi = rng.uniform(-yaw, yaw)
+        vxy = rng.uniform(-vel, vel, size=2)
+        Rz = _rot_z(psi)
+        c0 = local[0]
+        for b in range(nb):
+            p = c0 + Rz @ (local[b] - c0)
+            d["state0"][i, b] = _state(p, Rz, np.array([vxy[0], vxy[1], 0.0]), np.zeros(3))
+        d["mass"][i, 0] = 8.0
+        d["inertia"][i, 0] = I_torso
+        d["mass"][i, 1:] = cm
+        d["inertia"][i, 1:] = I_link
+        for l, (hx, hy) in enumerate(hips):
+            d["anchor"][i, 2 * l, 0] = [hx, hy, 0.0]
+            d["anchor"][i, 2 * l, 1] = [0.0, 0.0, link / 2]
+            d["anchor"][i, 2 * l + 1, 0] = [0.0, 0.0, -link / 2]
+            d["anchor"][i, 2 * l + 1, 1] = [0.0, 0.0, link / 2]
+            d["sph_off"][i, l] = [0.0, 0.0, -link / 2]
+            d["sph_rad"][i, l] = foot_r
+            d["sph_off"][i, 4 + l] = [0.25 * np.sign(hx), 0.1 * np.sign(hy), 0.0]
+            d["sph_rad"][i, 4 + l] = torso_r
+        d["axis"][i, :, :] = [0.0, 1.0, 0.0]
+        d["ref"][i, :, :] = [1.0, 0.0, 0.0]
+        d["limit"][i, :] = [-math.pi / 3, math.pi / 3]
+        d["motor"][i, :] = [30.0, 4.0, math.pi / 4]
+        d["sph_mu"][i] = 0.8
+        d["sph_e"][i] = 0.0
+        d["loss_point"][i] = [0.0, 0.0, 0.0]
+        d["loss_target"][i] = [-1.0, 0.0, 0.0]
+    _finish(d)
+    wr = np.random.default_rng(seed + 7 if w_seed is None else w_seed)
+    W = xavier_weights(widths, skip, wr)
+    return Model(name="quadruped", B=B, joint_type=jt, joint_body=jb, joint_flags=jf, sphere_body=sb,
+                 pair_sphere=np.zeros((0, 2), np.int32), nb=nb, widths=widths, skip=skip,
+                 features=F_ANGLES | F_RATES | F_CLOCK | F_IMU, imu_body=0, clock_hz=1.5, W=W, dt=dt,
+                 iters=iters, horizon=horizon, loss_kind=L_DISP, loss_mode=M_FINAL, loss_body=0, **d)
+
+
+def two_spheres(B=4, seed=1003, horizon=60, iters=20, dt=0.01, e=0.0, mu=0.3, gravity=(0.0, 0.0, 0.0)):
+    """Two free spheres (r=0.1 and 0.15 m, masses 1 and 2 kg) flying at each other above the
+    ground (zero gravity by default), one sphere-sphere candidate pair. Loss: squared distance
+    of sphere 0's centre to a target."""
+    rng = np.random.default_rng(seed)
+    nb, ns = 2, 2
+    d = _empty(B, nb, 0, ns)
+    for i in range(B):
+        r = np.array([0.1, 0.15])
+        m = np.array([1.0, 2.0])
+        d["mass"][i] = m
+        d["inertia"][i, 0] = 0.4 * m[0] * r[0] ** 2
+        d["inertia"][i, 1] = 0.4 * m[1] * r[1] ** 2
+        d["sph_rad"][i] = r
+        d["sph_mu"][i] = mu
+        d["sph_e"][i] = e
+        off = rng.uniform(-0.08, 0.08, size=2)
+        p0 = np.array([-0.6, off[0], 1.0])
+        p1 = np.array([0.6, off[1], 1.0])
+        v0 = np.array([rng.uniform(2.0, 4.0), 0.0, 0.0])
+        v1 = np.array([-rng.uniform(1.0, 3.0), 0.0, 0.0])
+        w0 = rng.uniform(-2, 2, size=3)
+        w1 = rng.uniform(-2, 2, size=3)
+        d["state0"][i, 0] = _state(p0, np.eye(3), v0, w0)
+        d["state0"][i, 1] = _state(p1, np.eye(3), v1, w1)
+        d["loss_target"][i] = [0.0, 0.0, 1.0]
+    _finish(d)
+    return Model(name="two_spheres", B=B, joint_type=np.zeros(0, np.int32), joint_body=np.zeros((0, 2), np.int32),
+                 joint_flags=np.zeros(0, np.int32), sphere_body=np.array([0, 1], np.int32),
+                 pair_sphere=np.array([[0, 1]], np.int32), nb=nb, gravity=tuple(gravity), dt=dt, iters=iters,
+                 horizon=horizon, ground_z=-10.0, loss_kind=L_SQDIST, loss_mode=M_FINAL, loss_body=0, **d)
+
+
+def free_body(B=2, seed=1004, horizon=200, dt=0.001, iters=1):
+    """One asymmetric free box without gravity or contacts, spinning about a seeded axis."""
+    rng = np.random.default_rng(seed)
+    d = _empty(B, 1, 0, 0)
+    for i in range(B):
+        d["mass"][i] = 2.0
+        d["inertia"][i, 0] = [0.1, 0.2, 0.3]
+        d["state0"][i, 0] = _state(rng.uniform(-1, 1, 3), np.eye(3), rng.uniform(-1, 1, 3), rng.uniform(-3, 3, 3))
+        d["loss_target"][i] = [1.0, 2.0, 3.0]
+    _finish(d)
+    return Model(name="free_body", B=B, joint_type=np.zeros(0, np.int32), joint_body=np.zeros((0, 2), np.int32),
+                 joint_flags=np.zeros(0, np.int32), sphere_body=np.zeros(0, np.int32),
+                 pair_sphere=np.zeros((0, 2), np.int32), nb=1, gravity=(0.0, 0.0, 0.0), dt=dt, iters=iters,
+                 horizon=horizon, loss_kind=L_SQDIST, loss_mode=M_FINAL, loss_body=0, **d)
+
+
+def pendulum1(B=1, L=0.5, m=1.0, amp_deg=1.0, horizon=3000, dt=0.001, iters=20, rod_radius=0.005):
+    """Single rod on a world hinge, released from a small angle (period check)."""
+    d = _empty(B, 1, 1, 0)
+    th = math.radians(amp_deg)
+    R = _rot_y(th)
+    for i in range(B):
+        d["state0"][i, 0] = _state(R @ np.array([0.0, 0.0, -L / 2]), R, np.zeros(3), np.zeros(3))
+        d["mass"][i] = m
+        It = m * (3 * rod_radius ** 2 + L ** 2) / 12.0
+        d["inertia"][i, 0] = [It, It, 0.5 * m * rod_radius ** 2]
+        d["anchor"][i, 0, 0] = [0.0, 0.0, 0.0]
+        d["anchor"][i, 0, 1] = [0.0, 0.0, L / 2]
+        d["axis"][i, 0] = [0.0, 1.0, 0.0]
+        d["ref"][i, 0] = [1.0, 0.0, 0.0]
+        d["loss_point"][i] = [0.0, 0.0, -L / 2]
+        d["loss_target"][i] = [0.0, 0.0, 1.0]
+    _finish(d)
+    return Model(name="pendulum1", B=B, joint_type=np.array([HINGE], np.int32), joint_body=np.array([[-1, 0]], np.int32),
+                 joint_flags=np.zeros(1, np.int32), sphere_body=np.zeros(0, np.int32),
+                 pair_sphere=np.zeros((0, 2), np.int32), nb=1, dt=dt, iters=iters, horizon=horizon,
+                 loss_kind=L_LINEAR, loss_mode=M_FINAL, loss_body=0, **d)
