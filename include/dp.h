@@ -1,0 +1,194 @@
+/*
+ * dp.h - C ABI of the GB300 differentiable rigid-body rollout library (libdphys.so).
+ *
+ * The library steps a batch of independent robots with the impulse-based velocity-stepping
+ * engine of "A Differentiable Physics Engine for Deep Learning in Robotics" (arXiv 1611.01652,
+ * section 2.1) and returns the reverse-mode gradient of the rollout loss (Eq. L, section 2.2)
+ * with respect to the initial state, the per-instance model parameters and the controller
+ * weights (Eq. g), by back-propagation through time (section 2.1.1).
+ *
+ * Problem statement followed by the calls (section 2.2):
+ *     x^{t+1} = f_ph(x^t, u^t),   u^t = g_deep(s(x^t) | W),   L = sum_t l(x^t, p).
+ *
+ * Conventions
+ *   - All calls are asynchronous and ordered on the CUDA stream given to dp_create_world.
+ *   - Pointer arguments documented as "host or device" may point to either; the library
+ *     copies with cudaMemcpyDefault. Caller-owned buffers must stay valid until the stream
+ *     has passed the call (cudaStreamSynchronize or dp_sync).
+ *   - Nothing aborts: every call returns a dp_status; dp_last_error() gives a message.
+ *     Numerical failures (non-finite states) are reported by dp_sync() as DP_ENAN.
+ *   - Instances of one world share one topology (bodies, joints, spheres, pairs and the
+ *     controller shape); every parameter below is per instance.
+ *   - State layout per body: p[3], R[9] (row-major rotation matrix, body-to-world), v[3], w[3]
+ *     (world-frame linear and angular velocity) = 18 floats; a state is [B][n_bodies][18].
+ */
+#ifndef DP_H
+#define DP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DP_OK = 0,
+  DP_EINVAL = 1,   /* invalid descriptor or argument (nothing was enqueued) */
+  DP_ENOMEM = 2,   /* device allocation failed */
+  DP_ECUDA = 3,    /* a CUDA call failed; see dp_last_error */
+  DP_ETIMEOUT = 4, /* a bounded wait ran out */
+  DP_ENAN = 5,     /* a rollout produced a non-finite state or loss */
+  DP_ESTATE = 6    /* call out of order (e.g. dp_backward without a matching dp_rollout) */
+} dp_status;
+
+/* Limits of one world's topology. */
+#define DP_MAX_BODIES 32
+#define DP_MAX_JOINTS 32
+#define DP_MAX_SPHERES 32
+#define DP_MAX_PAIRS 32
+#define DP_MAX_LAYERS 6
+
+enum { DP_JOINT_BALL = 0, DP_JOINT_HINGE = 1 };
+enum { DP_FLAG_LIMIT = 1, DP_FLAG_MOTOR = 2 };
+/* Controller input blocks, in this order (section 3.1 sensors; section 3.3 sin/cos clock). */
+enum {
+  DP_F_ANGLES = 1,  /* hinge angle of every motorised hinge, joint order */
+  DP_F_RATES = 2,   /* hinge rate of every motorised hinge */
+  DP_F_CLOCK = 4,   /* sin(2 pi f t dt), cos(2 pi f t dt) */
+  DP_F_IMU = 8,     /* gravity direction and angular velocity of imu_body, in its frame */
+  DP_F_TARGET = 16  /* loss point minus loss target (world frame) */
+};
+/* Loss l(x) of Eq. L, evaluated on the point q = p_b + R_b c of body loss_body. */
+enum {
+  DP_LOSS_SQDIST = 0, /* |q - target|^2 */
+  DP_LOSS_DIST = 1,   /* |q - target| */
+  DP_LOSS_LINEAR = 2, /* target . q  (target used as a direction) */
+  DP_LOSS_DISP = 3    /* target . (q - q_0) */
+};
+enum { DP_MODE_FINAL = 0 /* l(x_T) */, DP_MODE_MEAN = 1 /* (1/T) sum_{t=1..T} l(x_t) */ };
+
+/*
+ * Batch descriptor, read once by dp_create_world. All arrays are caller-owned host memory.
+ * Per-instance arrays have a leading dimension n_instances (B) and are float32.
+ */
+typedef struct {
+  int32_t n_instances;            /* B >= 1 */
+  int32_t n_bodies, n_joints, n_spheres, n_pairs;
+  /* topology, shared by all instances */
+  const int32_t* joint_type;      /* [nj] DP_JOINT_* */
+  const int32_t* joint_body;      /* [nj][2] parent a (-1 = world), child b (>= 0, != a) */
+  const int32_t* joint_flags;     /* [nj] DP_FLAG_* (hinges only) */
+  const int32_t* sphere_body;     /* [ns] body carrying each sphere */
+  const int32_t* pair_sphere;     /* [np][2] sphere-sphere candidate pairs (different bodies) */
+  /* per-instance parameters */
+  const float* mass;              /* [B][nb] kg */
+  const float* inertia;           /* [B][nb][3] principal moments in the body frame */
+  const float* anchor;            /* [B][nj][2][3] joint point in the parent / child frame
+                                     (world frame for a world parent) */
+  const float* axis;              /* [B][nj][2][3] hinge axis (unit) in parent / child frame */
+  const float* ref;               /* [B][nj][2][3] unit reference vectors perpendicular to the
+                                     axis; the hinge angle is the angle between them */
+  const float* limit;             /* [B][nj][2] lower, upper angle (rad), lower < upper */
+  const float* motor;             /* [B][nj][3] servo gain (1/s), max torque (N m), max rate */
+  const float* sph_off;           /* [B][ns][3] sphere centre in its body frame */
+  const float* sph_rad;           /* [B][ns] radius */
+  const float* sph_mu;            /* [B][ns] Coulomb friction coefficient */
+  const float* sph_e;             /* [B][ns] restitution */
+  const float* loss_point;        /* [B][3] point c on loss_body (body frame) */
+  const float* loss_target;       /* [B][3] target point or direction */
+  const float* state0;            /* [B][nb][18] initial state */
+  /* controller: dense ReLU network, linear output (Eq. g), bfloat16 storage, fp32 accumulate */
+  int32_t n_layers;               /* 0 = no controller (servo targets are 0) */
+  int32_t widths[DP_MAX_LAYERS + 1];
+  int32_t skip;                   /* 1: the output layer also reads the input layer */
+  int32_t features;               /* DP_F_* mask; the input width must equal their count */
+  int32_t imu_body;
+  float clock_hz;
+  /* constants */
+  float gravity[3];
+  float dt, ground_z, beta, gamma, slop;
+  int32_t iters;                  /* projected Gauss-Seidel sweeps per step, >= 1 */
+  int32_t horizon;                /* T, steps per rollout, >= 1 */
+  int32_t ckpt_every;             /* store a state every K steps for the backward pass;
+                                     0 = choose K from free device memory */
+  int32_t loss_kind, loss_mode, loss_body;
+} dp_batch_desc;
+
+typedef struct dp_world dp_world; /* opaque; owned by the library */
+
+/* Gradients with respect to the per-instance parameters; each pointer (host or device) may be
+   NULL. Shapes are those of the matching dp_batch_desc arrays. Axes and reference vectors are
+   model structure and get no gradient. */
+typedef struct {
+  float *mass, *inertia, *anchor, *limit, *motor, *sph_off, *sph_rad, *sph_mu, *sph_e, *loss_point, *loss_target;
+} dp_param_grads;
+
+/*
+ * Validate the descriptor, build the static row schedule, pick the checkpoint interval and
+ * allocate every device buffer the world needs (parameters, state, checkpoints, per-step tape,
+ * controller activations). `stream` is a cudaStream_t (NULL = legacy default stream).
+ * Errors: DP_EINVAL (descriptor), DP_ENOMEM, DP_ECUDA. On error *out is NULL.
+ */
+dp_status dp_create_world(const dp_batch_desc* desc, void* stream, dp_world** out);
+
+/* Release every resource of the world (synchronises its stream first). NULL is a no-op. */
+void dp_free(dp_world* w);
+
+/* Number of controller parameters of the world (flat layout: for each layer W[out][in] then
+   b[out]; with skip, a final W_skip[out][in0], b_skip[out]). */
+int64_t dp_num_params(const dp_world* w);
+
+/* Number of constraint-row slots per instance and the static schedule (host arrays of that
+   length, each may be NULL): row kind, owning joint/sphere/pair index, sub-row, bodies a and b
+   (-1 = world), colour, and the sweep order (slot indices, colour-major then slot). Kinds:
+   0 joint linear, 1 hinge angular, 2 limit, 3 motor, 4 ground normal, 5 ground friction,
+   6 pair normal, 7 pair friction. */
+int32_t dp_num_slots(const dp_world* w);
+dp_status dp_schedule(const dp_world* w, int32_t* kind, int32_t* idx, int32_t* sub, int32_t* body_a,
+                      int32_t* body_b, int32_t* colour, int32_t* order);
+
+/* Replace the initial state used by dp_rollout. `state` (host or device) is [B][nb][18]. */
+dp_status dp_set_initial_state(dp_world* w, const float* state);
+
+/* Set the current state and step index used by dp_step. */
+dp_status dp_set_state(dp_world* w, const float* state, int32_t t);
+/* Copy the current state ([B][nb][18]) to `state` (host or device). */
+dp_status dp_get_state(dp_world* w, float* state);
+
+/*
+ * Advance the current state by n_steps steps of section 2.1 (no gradient bookkeeping).
+ * W (host or device, dp_num_params floats, fp32 master weights; NULL if no controller).
+ * active (device, optional): [n_steps][B][n_slots] bytes, 1 where a constraint slot was active.
+ */
+dp_status dp_step(dp_world* w, int32_t n_steps, const float* W, uint8_t* active);
+
+/*
+ * Roll all instances from the initial state over the horizon with controller weights W and
+ * write the per-instance loss of Eq. L to loss ([B], host or device). Stores the checkpoints
+ * needed by dp_backward. traj (device, optional): [T+1][B][nb][18] states; active (device,
+ * optional): [T][B][n_slots] bytes. After the call the current state is x_T.
+ */
+dp_status dp_rollout(dp_world* w, const float* W, float* loss, float* traj, uint8_t* active);
+
+/*
+ * Reverse mode through the last dp_rollout: given dL_total/dloss_i in dloss ([B], host or
+ * device), write dL/dW (dp_num_params floats), dL/dstate0 ([B][nb][18]) and the parameter
+ * gradients (each output optional, host or device). Recomputes every checkpoint segment and
+ * replays each step's solver in reverse. Errors: DP_ESTATE without a preceding rollout.
+ */
+dp_status dp_backward(dp_world* w, const float* dloss, float* dW, float* dstate0, const dp_param_grads* dparams);
+
+/* Synchronise the world's stream; DP_ENAN if the last rollout produced a non-finite value. */
+dp_status dp_sync(dp_world* w);
+
+/* Message of the last failed call on this thread (never NULL). */
+const char* dp_last_error(void);
+
+/* Checkpoint interval K chosen at create (states stored every K steps). */
+int32_t dp_ckpt_every(const dp_world* w);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DP_H */

@@ -225,3 +225,16 @@ def param_count(widths, skip=0):
 
 def bf16(x):
     return lib().orc_bf16(float(x))
+
+
+def flops(m, i=0, horizon=None, W=None):
+    """Algorithmic operations per step of instance ``i``: (forward, reverse, tape nodes)."""
+    T = m.horizon if horizon is None else horizon
+    keep = _Keep()
+    t = topo(m, keep)
+    s = inst(m, i, keep)
+    out = np.zeros(3)
+    r = lib().orc_flops(C.byref(t), C.byref(s), weights(m, keep, W), T, _dp(out))
+    if r != 0:
+        raise ValueError("oracle rejected the model")
+    return tuple(out)

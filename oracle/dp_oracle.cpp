@@ -88,8 +88,30 @@ inline AD atan2(AD y, AD x) {
   return mk(std::atan2(y.v, x.v), y.id, x.v / d, x.id, -y.v / d);
 }
 
+// Counting scalar: every arithmetic operation and elementary function adds one to g_flops
+// (the instrumented counter that gives the algorithmic work of one step).
+static thread_local double g_flops = 0.0;
+struct CNT {
+  double v;
+  CNT() : v(0.0) {}
+  CNT(double x) : v(x) {}
+};
+inline CNT operator+(CNT a, CNT b) { g_flops += 1; return CNT(a.v + b.v); }
+inline CNT operator-(CNT a, CNT b) { g_flops += 1; return CNT(a.v - b.v); }
+inline CNT operator*(CNT a, CNT b) { g_flops += 1; return CNT(a.v * b.v); }
+inline CNT operator/(CNT a, CNT b) { g_flops += 1; return CNT(a.v / b.v); }
+inline CNT operator-(CNT a) { return CNT(-a.v); }
+inline CNT& operator+=(CNT& a, CNT b) { a = a + b; return a; }
+inline CNT& operator-=(CNT& a, CNT b) { a = a - b; return a; }
+inline CNT& operator*=(CNT& a, CNT b) { a = a * b; return a; }
+inline CNT sqrt(CNT a) { g_flops += 1; return CNT(std::sqrt(a.v)); }
+inline CNT sin(CNT a) { g_flops += 1; return CNT(std::sin(a.v)); }
+inline CNT cos(CNT a) { g_flops += 1; return CNT(std::cos(a.v)); }
+inline CNT atan2(CNT y, CNT x) { g_flops += 1; return CNT(std::atan2(y.v, x.v)); }
+
 inline double val(double x) { return x; }
 inline double val(const AD& x) { return x.v; }
+inline double val(const CNT& x) { return x.v; }
 using std::sqrt;
 using std::sin;
 using std::cos;
@@ -107,6 +129,7 @@ double bf16(double x) {
 }
 static thread_local bool g_exact_mlp = false;
 inline double round_bf16(double x) { return g_exact_mlp ? x : bf16(x); }
+inline CNT round_bf16(CNT x) { return CNT(g_exact_mlp ? x.v : bf16(x.v)); }
 inline AD round_bf16(AD x) { return g_exact_mlp ? x : mk(bf16(x.v), x.id, 1.0, -1, 0.0); }
 
 // Branch helpers: the branch is chosen on the value; ties go to the stated side.
@@ -837,6 +860,59 @@ int orc_rollout_grad(const orc_topo* T, const orc_inst* I, const double* W, int3
   if (G->state0)
     for (int k = 0; k < 18 * nb; ++k) G->state0[k] += xbar[k];
   g_tape = saved;
+  return 0;
+}
+
+
+// Algorithmic work of one instance over `horizon` steps from its initial state: out[0] = forward
+// operations per step (counted by the counting scalar), out[1] = reverse-mode operations per
+// step (two per recorded partial: one multiply, one add), out[2] = tape nodes per step.
+int orc_flops(const orc_topo* T, const orc_inst* I, const double* W, int32_t horizon, double* out) {
+  if (check_topo(T) || horizon < 1) return -1;
+  auto slots = make_slots(*T);
+  std::vector<int> col, ord;
+  make_schedule(slots, col, ord);
+  const int nb = T->nb;
+  const int np_ = param_count(T->n_layers, T->widths, T->skip);
+  std::vector<double> states((size_t)(horizon + 1) * 18 * nb);
+  if (orc_rollout(T, I, W, horizon, states.data(), nullptr, nullptr, nullptr)) return -1;
+  Inst<CNT> Pc = lift_inst<CNT>(*T, *I);
+  std::vector<CNT> Wc(np_);
+  for (int k = 0; k < np_; ++k) Wc[k] = CNT(W[k]);
+  double fwd = 0.0, rev = 0.0, nodes = 0.0;
+  Tape tape;
+  Tape* saved = g_tape;
+  g_tape = &tape;
+  for (int t = 0; t < horizon; ++t) {
+    std::vector<CNT> x(18 * nb), xn;
+    for (int k = 0; k < 18 * nb; ++k) x[k] = CNT(states[(size_t)t * 18 * nb + k]);
+    CNT lt;
+    double f0 = g_flops;
+    step<CNT>(*T, slots, ord, Pc, Wc, t, x, xn, weight_of_state(*T, t + 1, horizon), &lt, nullptr);
+    fwd += g_flops - f0;
+    tape.clear();
+    Inst<AD> P;
+    P.mass = lift_leaf(I->mass, nb); P.inertia = lift_leaf(I->inertia, 3 * nb);
+    P.anchor = lift_leaf(I->anchor, 6 * T->nj); P.axis = lift<AD>(I->axis, 6 * T->nj);
+    P.ref = lift<AD>(I->ref, 6 * T->nj); P.limit = lift_leaf(I->limit, 2 * T->nj);
+    P.motor = lift_leaf(I->motor, 3 * T->nj); P.sph_off = lift_leaf(I->sph_off, 3 * T->ns);
+    P.sph_rad = lift_leaf(I->sph_rad, T->ns); P.sph_mu = lift_leaf(I->sph_mu, T->ns);
+    P.sph_e = lift_leaf(I->sph_e, T->ns); P.loss_point = lift_leaf(I->loss_point, 3);
+    P.loss_target = lift_leaf(I->loss_target, 3);
+    std::vector<AD> Wl = lift_leaf(W, np_);
+    std::vector<AD> xa = lift_leaf(states.data() + (size_t)t * 18 * nb, 18 * nb), xna;
+    AD la;
+    size_t n0 = tape.pa.size();
+    step<AD>(*T, slots, ord, P, Wl, t, xa, xna, weight_of_state(*T, t + 1, horizon), &la, nullptr);
+    for (size_t q = n0; q < tape.pa.size(); ++q) {
+      rev += 2.0 * ((tape.pa[q] >= 0) + (tape.pb[q] >= 0));
+      nodes += 1.0;
+    }
+  }
+  g_tape = saved;
+  out[0] = fwd / horizon;
+  out[1] = rev / horizon;
+  out[2] = nodes / horizon;
   return 0;
 }
 

@@ -1,0 +1,235 @@
+"""Thin ctypes binding of libdphys (include/dp.h): argument marshalling only.
+
+Every step of a rollout and of its reverse mode runs in the library's CUDA kernels; there is no
+CPU fallback. Pointers are taken from torch tensors (device or host) or numpy arrays (host).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+DP_OK, DP_EINVAL, DP_ENOMEM, DP_ECUDA, DP_ETIMEOUT, DP_ENAN, DP_ESTATE = range(7)
+MAX_LAYERS = 6
+PARAM_GRADS = ("mass", "inertia", "anchor", "limit", "motor", "sph_off", "sph_rad", "sph_mu", "sph_e", "loss_point",
+               "loss_target")
+
+PF = C.POINTER(C.c_float)
+PI = C.POINTER(C.c_int32)
+
+
+class BatchDesc(C.Structure):
+    _fields_ = [("n_instances", C.c_int32), ("n_bodies", C.c_int32), ("n_joints", C.c_int32),
+                ("n_spheres", C.c_int32), ("n_pairs", C.c_int32),
+                ("joint_type", PI), ("joint_body", PI), ("joint_flags", PI), ("sphere_body", PI), ("pair_sphere", PI),
+                ("mass", PF), ("inertia", PF), ("anchor", PF), ("axis", PF), ("ref", PF), ("limit", PF),
+                ("motor", PF), ("sph_off", PF), ("sph_rad", PF), ("sph_mu", PF), ("sph_e", PF),
+                ("loss_point", PF), ("loss_target", PF), ("state0", PF),
+                ("n_layers", C.c_int32), ("widths", C.c_int32 * (MAX_LAYERS + 1)), ("skip", C.c_int32),
+                ("features", C.c_int32), ("imu_body", C.c_int32), ("clock_hz", C.c_float),
+                ("gravity", C.c_float * 3), ("dt", C.c_float), ("ground_z", C.c_float), ("beta", C.c_float),
+                ("gamma", C.c_float), ("slop", C.c_float), ("iters", C.c_int32), ("horizon", C.c_int32),
+                ("ckpt_every", C.c_int32), ("loss_kind", C.c_int32), ("loss_mode", C.c_int32),
+                ("loss_body", C.c_int32)]
+
+
+class ParamGrads(C.Structure):
+    _fields_ = [(k, PF) for k in PARAM_GRADS]
+
+
+_lib = None
+SYMBOLS = ("dp_create_world", "dp_free", "dp_num_params", "dp_num_slots", "dp_schedule", "dp_set_initial_state",
+           "dp_set_state", "dp_get_state", "dp_step", "dp_rollout", "dp_backward", "dp_sync", "dp_last_error",
+           "dp_ckpt_every")
+
+
+def load(build=True):
+    """Load libdphys.so (building it first if needed). Raises if it cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError("libdphys.so is missing: run paper_1611_01652_gb300.build.build()")
+    lib = C.CDLL(path)
+    lib.dp_create_world.argtypes = [C.POINTER(BatchDesc), C.c_void_p, C.POINTER(C.c_void_p)]
+    lib.dp_free.argtypes = [C.c_void_p]
+    lib.dp_free.restype = None
+    lib.dp_num_params.argtypes = [C.c_void_p]
+    lib.dp_num_params.restype = C.c_int64
+    lib.dp_num_slots.argtypes = [C.c_void_p]
+    lib.dp_ckpt_every.argtypes = [C.c_void_p]
+    lib.dp_schedule.argtypes = [C.c_void_p] + [PI] * 7
+    lib.dp_set_initial_state.argtypes = [C.c_void_p, C.c_void_p]
+    lib.dp_set_state.argtypes = [C.c_void_p, C.c_void_p, C.c_int32]
+    lib.dp_get_state.argtypes = [C.c_void_p, C.c_void_p]
+    lib.dp_step.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]
+    lib.dp_rollout.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.dp_backward.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(ParamGrads)]
+    lib.dp_sync.argtypes = [C.c_void_p]
+    lib.dp_last_error.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+class DPError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("dp status %d: %s" % (status, msg))
+        self.status = status
+
+
+def _check(status):
+    if status != DP_OK:
+        raise DPError(status, _lib.dp_last_error().decode())
+
+
+def ptr(x):
+    """Address of a torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return C.c_void_p(x.ctypes.data)
+    raise TypeError("expected a torch tensor or a numpy array")
+
+
+class World:
+    """A batch of robots with one topology living on the current CUDA device.
+
+    ``model`` is any object with the attributes of ``workloads.Model``. All calls are ordered on
+    ``stream`` (a torch.cuda.Stream, default: the current stream at creation).
+    """
+
+    def __init__(self, model, stream=None, ckpt_every=None, horizon=None, iters=None):
+        import torch
+
+        lib = load()
+        self._torch = torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.B, self.nb = int(model.B), int(model.nb)
+        self._keep = []
+        d = BatchDesc()
+
+        def i32(a):
+            a = np.ascontiguousarray(np.asarray(a, np.int32).reshape(-1))
+            if a.size == 0:
+                a = np.zeros(1, np.int32)
+            self._keep.append(a)
+            return a.ctypes.data_as(PI)
+
+        def f32(a):
+            a = np.ascontiguousarray(np.asarray(a, np.float32).reshape(-1))
+            if a.size == 0:
+                a = np.zeros(1, np.float32)
+            self._keep.append(a)
+            return a.ctypes.data_as(PF)
+
+        d.n_instances = self.B
+        d.n_bodies, d.n_joints, d.n_spheres, d.n_pairs = model.nb, model.nj, model.ns, model.np_
+        d.joint_type, d.joint_body, d.joint_flags = i32(model.joint_type), i32(model.joint_body), i32(model.joint_flags)
+        d.sphere_body, d.pair_sphere = i32(model.sphere_body), i32(model.pair_sphere)
+        for k in ("mass", "inertia", "anchor", "axis", "ref", "limit", "motor", "sph_off", "sph_rad", "sph_mu", "sph_e",
+                  "loss_point", "loss_target", "state0"):
+            setattr(d, k, f32(getattr(model, k)))
+        widths = list(model.widths) if model.widths else []
+        d.n_layers = max(len(widths) - 1, 0)
+        for l, wv in enumerate(widths):
+            d.widths[l] = wv
+        d.skip, d.features, d.imu_body, d.clock_hz = model.skip, model.features, model.imu_body, model.clock_hz
+        for k in range(3):
+            d.gravity[k] = model.gravity[k]
+        d.dt, d.ground_z, d.beta, d.gamma, d.slop = model.dt, model.ground_z, model.beta, model.gamma, model.slop
+        d.iters = model.iters if iters is None else iters
+        d.horizon = model.horizon if horizon is None else horizon
+        d.ckpt_every = model.ckpt_every if ckpt_every is None else ckpt_every
+        d.loss_kind, d.loss_mode, d.loss_body = model.loss_kind, model.loss_mode, model.loss_body
+        self.horizon = d.horizon
+        h = C.c_void_p()
+        _check(lib.dp_create_world(C.byref(d), C.c_void_p(self.stream.cuda_stream), C.byref(h)))
+        self._h = h
+        self._keep = []
+        self.n_params = int(lib.dp_num_params(h))
+        self.n_slots = int(lib.dp_num_slots(h))
+        self.ckpt_every = int(lib.dp_ckpt_every(h))
+
+    # -- lifetime
+    def free(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.dp_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    # -- calls (same names as the C ABI)
+    def schedule(self):
+        n = self.n_slots
+        out = {k: np.zeros(max(n, 1), np.int32) for k in ("kind", "idx", "sub", "body_a", "body_b", "colour", "order")}
+        _check(_lib.dp_schedule(self._h, *[out[k].ctypes.data_as(PI) for k in
+                                          ("kind", "idx", "sub", "body_a", "body_b", "colour", "order")]))
+        return {k: v[:n] for k, v in out.items()}
+
+    def set_initial_state(self, state):
+        _check(_lib.dp_set_initial_state(self._h, ptr(state)))
+
+    def set_state(self, state, t=0):
+        _check(_lib.dp_set_state(self._h, ptr(state), int(t)))
+
+    def get_state(self, out):
+        _check(_lib.dp_get_state(self._h, ptr(out)))
+        return out
+
+    def step(self, n_steps, W=None, active=None):
+        _check(_lib.dp_step(self._h, int(n_steps), ptr(W), ptr(active)))
+
+    def rollout(self, W, loss, traj=None, active=None):
+        _check(_lib.dp_rollout(self._h, ptr(W), ptr(loss), ptr(traj), ptr(active)))
+        return loss
+
+    def backward(self, dloss, dW=None, dstate0=None, dparams=None):
+        pg = None
+        if dparams:
+            pg = ParamGrads()
+            for k in PARAM_GRADS:
+                v = dparams.get(k)
+                setattr(pg, k, C.cast(ptr(v), PF) if v is not None else None)
+        _check(_lib.dp_backward(self._h, ptr(dloss), ptr(dW), ptr(dstate0), C.byref(pg) if pg is not None else None))
+
+    def sync(self):
+        _check(_lib.dp_sync(self._h))
+
+
+def make_rollout_function():
+    """torch.autograd.Function: loss[B] = rollout(W, state0) through a World; backward returns
+    dL/dW and dL/dstate0 from the library's reverse-mode kernels."""
+    import torch
+
+    class Rollout(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, W, state0, world):
+            world.set_initial_state(state0.detach().contiguous())
+            loss = torch.empty(world.B, device=state0.device, dtype=torch.float32)
+            world.rollout(W.detach().contiguous(), loss)
+            ctx.world = world
+            return loss
+
+        @staticmethod
+        def backward(ctx, gl):
+            w = ctx.world
+            dW = torch.empty(w.n_params, device=gl.device, dtype=torch.float32) if w.n_params else None
+            ds = torch.empty(w.B, w.nb, 18, device=gl.device, dtype=torch.float32)
+            w.backward(gl.contiguous().float(), dW, ds)
+            return dW, ds, None
+
+    return Rollout

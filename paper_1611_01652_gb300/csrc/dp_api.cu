@@ -1,0 +1,600 @@
+// Host implementation of the C ABI declared in include/dp.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dp.h"
+#include "dp_kernels.h"
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+dp_status fail(dp_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+#define CU(call)                                                                                  \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) return fail(DP_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+size_t round32(size_t x) { return (x + 31) / 32 * 32; }
+
+}  // namespace
+
+struct dp_world {
+  DevTopo Tf, Tb;  // same topology; forward / backward shared-memory layouts
+  DevPtrs D;
+  cudaStream_t stream = nullptr;
+  int B = 0, Bp = 0, nf = 0;
+  int64_t n_params = 0;
+  int w_total = 0;
+  float* x0 = nullptr;
+  float* Wmaster = nullptr;
+  float *Wt = nullptr, *Wn = nullptr, *Wb = nullptr;
+  float* stage = nullptr;      // device staging buffer for user-layout inputs/outputs
+  size_t stage_floats = 0;
+  float* dW_stage = nullptr;   // [n_params]
+  float* partial = nullptr;    // dW split partials
+  size_t partial_floats = 0;
+  int splits = 1;
+  std::vector<void*> allocs;
+  int t_now = 0;
+  bool have_rollout = false;
+  int32_t kind[DPK_MAXSLOT], colour[DPK_MAXSLOT];
+};
+
+namespace {
+
+template <class T>
+dp_status dalloc(dp_world* w, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(DP_ENOMEM, std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) + " bytes failed");
+  }
+  w->allocs.push_back(*p);
+  return DP_OK;
+}
+
+#define TRY(x)                  \
+  do {                          \
+    dp_status s_ = (x);         \
+    if (s_ != DP_OK) return s_; \
+  } while (0)
+
+struct Slot {
+  int kind, idx, sub, a, b, normal;
+};
+
+// Canonical slot order: joints (3 linear + 2 angular rows per hinge), limits, motors, ground
+// contacts (normal, 2 friction per sphere), pair contacts.
+std::vector<Slot> build_slots(const dp_batch_desc* d) {
+  std::vector<Slot> s;
+  for (int j = 0; j < d->n_joints; ++j) {
+    int a = d->joint_body[2 * j], b = d->joint_body[2 * j + 1];
+    for (int k = 0; k < 3; ++k) s.push_back({RK_JLIN, j, k, a, b, -1});
+    if (d->joint_type[j] == DP_JOINT_HINGE)
+      for (int k = 0; k < 2; ++k) s.push_back({RK_JANG, j, k, a, b, -1});
+  }
+  for (int j = 0; j < d->n_joints; ++j)
+    if (d->joint_type[j] == DP_JOINT_HINGE && (d->joint_flags[j] & DP_FLAG_LIMIT))
+      s.push_back({RK_LIMIT, j, 0, d->joint_body[2 * j], d->joint_body[2 * j + 1], -1});
+  for (int j = 0; j < d->n_joints; ++j)
+    if (d->joint_type[j] == DP_JOINT_HINGE && (d->joint_flags[j] & DP_FLAG_MOTOR))
+      s.push_back({RK_MOTOR, j, 0, d->joint_body[2 * j], d->joint_body[2 * j + 1], -1});
+  for (int q = 0; q < d->n_spheres; ++q) {
+    int n = (int)s.size(), a = d->sphere_body[q];
+    s.push_back({RK_GN, q, 0, a, -1, -1});
+    s.push_back({RK_GT, q, 0, a, -1, n});
+    s.push_back({RK_GT, q, 1, a, -1, n});
+  }
+  for (int q = 0; q < d->n_pairs; ++q) {
+    int n = (int)s.size();
+    int a = d->sphere_body[d->pair_sphere[2 * q]], b = d->sphere_body[d->pair_sphere[2 * q + 1]];
+    s.push_back({RK_PN, q, 0, a, b, -1});
+    s.push_back({RK_PT, q, 0, a, b, n});
+    s.push_back({RK_PT, q, 1, a, b, n});
+  }
+  return s;
+}
+
+dp_status validate(const dp_batch_desc* d) {
+  if (!d) return fail(DP_EINVAL, "descriptor is NULL");
+  if (d->n_instances < 1) return fail(DP_EINVAL, "n_instances must be >= 1");
+  if (d->n_bodies < 1 || d->n_bodies > DP_MAX_BODIES) return fail(DP_EINVAL, "n_bodies out of range [1, 32]");
+  if (d->n_joints < 0 || d->n_joints > DP_MAX_JOINTS) return fail(DP_EINVAL, "n_joints out of range [0, 32]");
+  if (d->n_spheres < 0 || d->n_spheres > DP_MAX_SPHERES) return fail(DP_EINVAL, "n_spheres out of range [0, 32]");
+  if (d->n_pairs < 0 || d->n_pairs > DP_MAX_PAIRS) return fail(DP_EINVAL, "n_pairs out of range [0, 32]");
+  if (d->horizon < 1) return fail(DP_EINVAL, "horizon must be >= 1");
+  if (d->iters < 1) return fail(DP_EINVAL, "iters must be >= 1");
+  if (!(d->dt > 0.f)) return fail(DP_EINVAL, "dt must be > 0");
+  if (d->ckpt_every < 0) return fail(DP_EINVAL, "ckpt_every must be >= 0");
+  if (!d->mass || !d->inertia || !d->state0) return fail(DP_EINVAL, "mass, inertia and state0 are required");
+  if (d->n_joints > 0 && (!d->joint_type || !d->joint_body || !d->joint_flags || !d->anchor || !d->axis || !d->ref ||
+                          !d->limit || !d->motor))
+    return fail(DP_EINVAL, "joint arrays are required when n_joints > 0");
+  if (d->n_spheres > 0 && (!d->sphere_body || !d->sph_off || !d->sph_rad || !d->sph_mu || !d->sph_e))
+    return fail(DP_EINVAL, "sphere arrays are required when n_spheres > 0");
+  if (d->n_pairs > 0 && !d->pair_sphere) return fail(DP_EINVAL, "pair_sphere is required when n_pairs > 0");
+  for (int j = 0; j < d->n_joints; ++j) {
+    int a = d->joint_body[2 * j], b = d->joint_body[2 * j + 1];
+    if (b < 0 || b >= d->n_bodies || a < -1 || a >= d->n_bodies || a == b)
+      return fail(DP_EINVAL, "joint " + std::to_string(j) + ": bad bodies");
+    if (d->joint_type[j] != DP_JOINT_BALL && d->joint_type[j] != DP_JOINT_HINGE)
+      return fail(DP_EINVAL, "joint " + std::to_string(j) + ": bad type");
+    if (d->joint_type[j] == DP_JOINT_BALL && d->joint_flags[j] != 0)
+      return fail(DP_EINVAL, "joint " + std::to_string(j) + ": limits/motors need a hinge");
+  }
+  for (int q = 0; q < d->n_spheres; ++q)
+    if (d->sphere_body[q] < 0 || d->sphere_body[q] >= d->n_bodies) return fail(DP_EINVAL, "sphere body out of range");
+  for (int q = 0; q < d->n_pairs; ++q) {
+    int k = d->pair_sphere[2 * q], l = d->pair_sphere[2 * q + 1];
+    if (k < 0 || l < 0 || k >= d->n_spheres || l >= d->n_spheres || d->sphere_body[k] == d->sphere_body[l])
+      return fail(DP_EINVAL, "pair " + std::to_string(q) + ": spheres must exist and sit on different bodies");
+  }
+  if (d->loss_body < 0 || d->loss_body >= d->n_bodies) return fail(DP_EINVAL, "loss_body out of range");
+  if (d->loss_kind < 0 || d->loss_kind > 3 || d->loss_mode < 0 || d->loss_mode > 1)
+    return fail(DP_EINVAL, "bad loss kind/mode");
+  if (d->n_layers < 0 || d->n_layers > DP_MAX_LAYERS) return fail(DP_EINVAL, "n_layers out of range [0, 6]");
+  for (int l = 0; l <= d->n_layers && d->n_layers > 0; ++l)
+    if (d->widths[l] < 1 || d->widths[l] > 4096) return fail(DP_EINVAL, "controller width out of range");
+  if (d->n_layers > 0 && (d->imu_body < 0 || d->imu_body >= d->n_bodies)) return fail(DP_EINVAL, "imu_body out of range");
+  for (int i = 0; i < d->n_instances; ++i)
+    for (int b = 0; b < d->n_bodies; ++b) {
+      if (!(d->mass[i * d->n_bodies + b] > 0.f)) return fail(DP_EINVAL, "masses must be > 0");
+      for (int k = 0; k < 3; ++k)
+        if (!(d->inertia[(i * d->n_bodies + b) * 3 + k] > 0.f)) return fail(DP_EINVAL, "inertias must be > 0");
+    }
+  for (int i = 0; i < d->n_instances; ++i)
+    for (int j = 0; j < d->n_joints; ++j)
+      if (d->joint_type[j] == DP_JOINT_HINGE && (d->joint_flags[j] & DP_FLAG_LIMIT) &&
+          !(d->limit[(i * d->n_joints + j) * 2] < d->limit[(i * d->n_joints + j) * 2 + 1]))
+        return fail(DP_EINVAL, "joint limits need lower < upper");
+  return DP_OK;
+}
+
+int feature_count(const dp_batch_desc* d, int n_motors) {
+  int n = 0;
+  if (d->features & DP_F_ANGLES) n += n_motors;
+  if (d->features & DP_F_RATES) n += n_motors;
+  if (d->features & DP_F_CLOCK) n += 2;
+  if (d->features & DP_F_IMU) n += 6;
+  if (d->features & DP_F_TARGET) n += 3;
+  return n;
+}
+
+// Shared-memory plan (units of 32 floats per warp). Forward kernel: controller activations on
+// chip; backward kernel: row-adjoint accumulators on chip, activations in the global dump.
+void plan_smem(DevTopo& T, bool backward) {
+  int o = 0;
+  auto take = [&](int n) { int r = o; o += std::max(n, 1); return r; };
+  T.sm_x = take(18 * T.nb);
+  T.sm_iinv = take(6 * T.nb);
+  T.sm_invm = take(T.nb);
+  T.sm_th = take(T.nj);
+  T.sm_thd = take(T.nj);
+  T.sm_ua = take(3 * T.nj);
+  T.sm_wst = take(T.nj);
+  T.sm_wbr = take(T.nj);
+  T.sm_lam = take(T.nslots);
+  T.sm_x0 = T.sm_u = 0;
+  if (!backward) {
+    for (int l = 0; l <= DPK_MAXL; ++l) T.sm_act[l] = 0;
+    if (T.n_layers > 0)
+      for (int l = 0; l <= T.n_layers; ++l) T.sm_act[l] = take(T.widths[l]);
+    else
+      T.sm_act[0] = take(1);
+    T.sm_xb = T.sm_vb = T.sm_thb = T.sm_thdb = T.sm_uab = T.sm_wstb = T.sm_iinvb = T.sm_invmb = T.sm_rc = T.sm_sbar = 0;
+  } else {
+    for (int l = 0; l <= DPK_MAXL; ++l) T.sm_act[l] = 0;
+    T.sm_xb = take(18 * T.nb);
+    T.sm_vb = take(6 * T.nb);
+    T.sm_thb = take(T.nj);
+    T.sm_thdb = take(T.nj);
+    T.sm_uab = take(3 * T.nj);
+    T.sm_wstb = take(T.nj);
+    T.sm_iinvb = take(9 * T.nb);
+    T.sm_invmb = take(T.nb);
+    T.sm_rc = take(12 * T.nslots);
+    T.sm_sbar = take(T.n_layers > 0 ? T.widths[0] : 1);
+  }
+  T.sm_total = o;
+}
+
+void pack_param(std::vector<float>& h, int Bp, int B, int field0, int n, const float* src) {
+  if (!src) return;
+  for (int i = 0; i < Bp; ++i) {
+    int si = i < B ? i : B - 1;
+    for (int f = 0; f < n; ++f) h[(size_t)(field0 + f) * Bp + i] = src[(size_t)si * n + f];
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dp_last_error(void) { return g_err.c_str(); }
+
+dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) {
+  if (!out) return fail(DP_EINVAL, "out is NULL");
+  *out = nullptr;
+  TRY(validate(d));
+  dp_world* w = new dp_world();
+  auto cleanup = [&](dp_status s) {
+    dp_free(w);
+    return s;
+  };
+  w->stream = (cudaStream_t)stream;
+  DevTopo T;
+  std::memset(&T, 0, sizeof(T));
+  const int B = d->n_instances, Bp = (int)round32(B);
+  w->B = B;
+  w->Bp = Bp;
+  T.B = B;
+  T.Bp = Bp;
+  T.nb = d->n_bodies;
+  T.nj = d->n_joints;
+  T.ns = d->n_spheres;
+  T.np = d->n_pairs;
+  T.iters = d->iters;
+  T.horizon = d->horizon;
+  T.features = d->features;
+  T.imu_body = d->imu_body;
+  T.loss_kind = d->loss_kind;
+  T.loss_mode = d->loss_mode;
+  T.loss_body = d->loss_body;
+  T.n_layers = d->n_layers;
+  T.skip = d->n_layers > 0 ? d->skip : 0;
+  for (int k = 0; k < 3; ++k) T.gravity[k] = d->gravity[k];
+  T.dt = d->dt;
+  T.ground_z = d->ground_z;
+  T.beta = d->beta;
+  T.gamma = d->gamma;
+  T.slop = d->slop;
+  T.clock_hz = d->clock_hz;
+  for (int j = 0; j < T.nj; ++j) {
+    T.jtype[j] = (int8_t)d->joint_type[j];
+    T.ja[j] = (int8_t)d->joint_body[2 * j];
+    T.jb[j] = (int8_t)d->joint_body[2 * j + 1];
+    T.jflags[j] = (int8_t)d->joint_flags[j];
+    T.jmotor[j] = -1;
+  }
+  for (int j = 0; j < T.nj; ++j)
+    if (d->joint_type[j] == DP_JOINT_HINGE && (d->joint_flags[j] & DP_FLAG_MOTOR)) {
+      T.jmotor[j] = (int8_t)T.n_motors;
+      T.motor_joint[T.n_motors++] = (int8_t)j;
+    }
+  for (int q = 0; q < T.ns; ++q) T.sbody[q] = (int8_t)d->sphere_body[q];
+  for (int q = 0; q < T.np; ++q) {
+    T.pk[q] = (int8_t)d->pair_sphere[2 * q];
+    T.pl[q] = (int8_t)d->pair_sphere[2 * q + 1];
+  }
+  // slots, greedy colouring over non-world bodies, sweep order (colour, slot)
+  std::vector<Slot> slots = build_slots(d);
+  T.nslots = (int)slots.size();
+  if (T.nslots > DPK_MAXSLOT) return cleanup(fail(DP_EINVAL, "too many constraint slots"));
+  std::vector<int> col(T.nslots, 0), ord(T.nslots);
+  for (int i = 0; i < T.nslots; ++i) {
+    std::vector<char> used(T.nslots + 1, 0);
+    for (int k = 0; k < i; ++k) {
+      bool share = (slots[i].a >= 0 && (slots[i].a == slots[k].a || slots[i].a == slots[k].b)) ||
+                   (slots[i].b >= 0 && (slots[i].b == slots[k].a || slots[i].b == slots[k].b));
+      if (share) used[col[k]] = 1;
+    }
+    int c = 0;
+    while (used[c]) ++c;
+    col[i] = c;
+  }
+  for (int i = 0; i < T.nslots; ++i) ord[i] = i;
+  std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return col[x] < col[y]; });
+  for (int s = 0; s < T.nslots; ++s) {
+    T.skind[s] = (uint8_t)slots[s].kind;
+    T.sidx[s] = (uint8_t)slots[s].idx;
+    T.ssub[s] = (uint8_t)slots[s].sub;
+    T.sa[s] = (int8_t)slots[s].a;
+    T.sb[s] = (int8_t)slots[s].b;
+    T.snormal[s] = (int16_t)slots[s].normal;
+    T.order[s] = (int16_t)ord[s];
+    w->kind[s] = slots[s].kind;
+    w->colour[s] = col[s];
+  }
+  // parameter fields
+  int o = 0;
+  T.o_mass = o; o += T.nb;
+  T.o_inertia = o; o += 3 * T.nb;
+  T.o_anchor = o; o += 6 * T.nj;
+  T.o_axis = o; o += 6 * T.nj;
+  T.o_ref = o; o += 6 * T.nj;
+  T.o_limit = o; o += 2 * T.nj;
+  T.o_motor = o; o += 3 * T.nj;
+  T.o_sph_off = o; o += 3 * T.ns;
+  T.o_sph_rad = o; o += T.ns;
+  T.o_sph_mu = o; o += T.ns;
+  T.o_sph_e = o; o += T.ns;
+  T.o_loss_point = o; o += 3;
+  T.o_loss_target = o; o += 3;
+  T.n_pfields = o;
+  // controller
+  int64_t np_ = 0;
+  int wtot = 0;
+  if (T.n_layers > 0) {
+    for (int l = 0; l <= T.n_layers; ++l) T.widths[l] = d->widths[l];
+    if (feature_count(d, T.n_motors) > T.widths[0])
+      return cleanup(fail(DP_EINVAL, "controller input width is smaller than the selected features"));
+    const int nl = T.n_layers + (T.skip ? 1 : 0);
+    for (int l = 0; l < nl; ++l) {
+      int ni = l < T.n_layers ? T.widths[l] : T.widths[0];
+      int no_ = l < T.n_layers ? T.widths[l + 1] : T.widths[T.n_layers];
+      int nop = (no_ + 7) & ~7, nip = (ni + 7) & ~7;
+      T.w_off[l] = wtot;
+      wtot += std::max(ni * nop, no_ * nip);
+      np_ += (int64_t)ni * no_ + no_;
+    }
+    int r = 0;
+    for (int l = 0; l <= T.n_layers; ++l) { T.dump_act[l] = r; r += T.widths[l]; }
+    for (int l = 0; l < T.n_layers; ++l) { T.dump_del[l] = r; r += T.widths[l + 1]; }
+    T.dump_rows = r;
+  }
+  T.n_params = (int)np_;
+  w->n_params = np_;
+  w->w_total = wtot;
+  w->Tf = T;
+  w->Tb = T;
+  plan_smem(w->Tf, false);
+  plan_smem(w->Tb, true);
+  int dev = 0, smem_max = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  size_t need = (size_t)std::max(w->Tf.sm_total, w->Tb.sm_total) * 32 * sizeof(float);
+  if (need > (size_t)smem_max) {
+    dp_status s = fail(DP_EINVAL, "robot too large: needs " + std::to_string(need) + " bytes of shared memory per warp, the device offers " +
+                                      std::to_string(smem_max));
+    return cleanup(s);
+  }
+  // checkpoint interval from free memory
+  const int nf = 18 * T.nb;
+  w->nf = nf;
+  const size_t state_bytes = (size_t)nf * Bp * sizeof(float);
+  const size_t dump_bytes = (size_t)T.dump_rows * T.horizon * Bp * sizeof(float);
+  size_t free_b = 0, total_b = 0;
+  CU(cudaMemGetInfo(&free_b, &total_b));
+  int K = d->ckpt_every;
+  if (K == 0) {
+    size_t budget = free_b > dump_bytes ? (free_b - dump_bytes) / 4 : 0;
+    K = 1;
+    while (K < T.horizon && ((size_t)((T.horizon + K - 1) / K) + K) * state_bytes > budget) ++K;
+  }
+  K = std::min(K, T.horizon);
+  const int n_ckpt = (T.horizon + K - 1) / K;
+  DevPtrs& D = w->D;
+  std::memset(&D, 0, sizeof(D));
+  D.ckpt_every = K;
+  D.n_ckpt = n_ckpt;
+  // device buffers
+  float* prm = nullptr;
+  if (dalloc(w, &prm, (size_t)T.n_pfields * Bp)) return cleanup(DP_ENOMEM);
+  D.prm = prm;
+  if (dalloc(w, &D.state, (size_t)nf * Bp) || dalloc(w, &w->x0, (size_t)nf * Bp) ||
+      dalloc(w, &D.ckpt, (size_t)n_ckpt * nf * Bp) || dalloc(w, &D.seg, (size_t)K * nf * Bp) ||
+      dalloc(w, &D.rows, (size_t)T.nslots * RF_N * Bp) || dalloc(w, &D.lam_hist, (size_t)T.iters * T.nslots * Bp) ||
+      dalloc(w, &D.br_hist, (size_t)T.iters * T.nslots * Bp) || dalloc(w, &D.v_iter, (size_t)T.iters * T.nb * 6 * Bp) ||
+      dalloc(w, &D.vminus, (size_t)T.nb * 6 * Bp) || dalloc(w, &D.loss, (size_t)Bp) || dalloc(w, &D.dloss, (size_t)Bp) ||
+      dalloc(w, &D.grad_prm, (size_t)T.n_pfields * Bp) || dalloc(w, &D.grad_state0, (size_t)nf * Bp) ||
+      dalloc(w, &D.status, (size_t)Bp))
+    return cleanup(DP_ENOMEM);
+  if (T.n_layers > 0) {
+    if (dalloc(w, &D.dump, (size_t)T.dump_rows * T.horizon * Bp) || dalloc(w, &w->Wmaster, (size_t)np_) ||
+        dalloc(w, &w->Wt, (size_t)wtot) || dalloc(w, &w->Wn, (size_t)wtot) || dalloc(w, &w->Wb, (size_t)wtot) ||
+        dalloc(w, &w->dW_stage, (size_t)np_))
+      return cleanup(DP_ENOMEM);
+    CU(cudaMemsetAsync(w->Wt, 0, sizeof(float) * wtot, w->stream));
+    CU(cudaMemsetAsync(w->Wn, 0, sizeof(float) * wtot, w->stream));
+    CU(cudaMemsetAsync(w->Wb, 0, sizeof(float) * wtot, w->stream));
+    size_t N = (size_t)T.horizon * Bp;
+    w->splits = (int)std::min<size_t>(256, (N + 16383) / 16384);
+    size_t maxlayer = 0;
+    for (int l = 0; l <= T.n_layers; ++l) maxlayer = std::max(maxlayer, (size_t)T.widths[l]);
+    w->partial_floats = (size_t)w->splits * maxlayer * maxlayer;
+    if (dalloc(w, &w->partial, w->partial_floats)) return cleanup(DP_ENOMEM);
+    D.Wt = w->Wt;
+    D.Wn = w->Wn;
+    D.bias = w->Wb;
+  } else {
+    float* dummy = nullptr;
+    if (dalloc(w, &dummy, 8)) return cleanup(DP_ENOMEM);
+    CU(cudaMemsetAsync(dummy, 0, 8 * sizeof(float), w->stream));
+    D.Wt = D.Wn = D.bias = dummy;
+    D.dump = dummy;
+  }
+  const int widest = std::max({nf, 6 * T.nj, 3 * T.nb, 3 * T.ns, 32});
+  w->stage_floats = std::max<size_t>((size_t)B * widest, (size_t)np_);
+  if (dalloc(w, &w->stage, w->stage_floats)) return cleanup(DP_ENOMEM);
+  CU(cudaMemsetAsync(D.status, 0, sizeof(int) * Bp, w->stream));
+  // parameters (host pack, one upload)
+  std::vector<float> h((size_t)T.n_pfields * Bp, 0.f);
+  pack_param(h, Bp, B, T.o_mass, T.nb, d->mass);
+  pack_param(h, Bp, B, T.o_inertia, 3 * T.nb, d->inertia);
+  pack_param(h, Bp, B, T.o_anchor, 6 * T.nj, d->anchor);
+  pack_param(h, Bp, B, T.o_axis, 6 * T.nj, d->axis);
+  pack_param(h, Bp, B, T.o_ref, 6 * T.nj, d->ref);
+  pack_param(h, Bp, B, T.o_limit, 2 * T.nj, d->limit);
+  pack_param(h, Bp, B, T.o_motor, 3 * T.nj, d->motor);
+  pack_param(h, Bp, B, T.o_sph_off, 3 * T.ns, d->sph_off);
+  pack_param(h, Bp, B, T.o_sph_rad, T.ns, d->sph_rad);
+  pack_param(h, Bp, B, T.o_sph_mu, T.ns, d->sph_mu);
+  pack_param(h, Bp, B, T.o_sph_e, T.ns, d->sph_e);
+  pack_param(h, Bp, B, T.o_loss_point, 3, d->loss_point);
+  pack_param(h, Bp, B, T.o_loss_target, 3, d->loss_target);
+  CU(cudaMemcpyAsync(prm, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, w->stream));
+  std::vector<float> hs((size_t)nf * Bp);
+  pack_param(hs, Bp, B, 0, nf, d->state0);
+  CU(cudaMemcpyAsync(w->x0, hs.data(), hs.size() * sizeof(float), cudaMemcpyHostToDevice, w->stream));
+  CU(cudaMemcpyAsync(D.state, hs.data(), hs.size() * sizeof(float), cudaMemcpyHostToDevice, w->stream));
+  CU(cudaStreamSynchronize(w->stream));
+  *out = w;
+  return DP_OK;
+}
+
+void dp_free(dp_world* w) {
+  if (!w) return;
+  if (w->stream) cudaStreamSynchronize(w->stream);
+  else cudaDeviceSynchronize();
+  for (void* p : w->allocs) cudaFree(p);
+  delete w;
+}
+
+int64_t dp_num_params(const dp_world* w) { return w ? w->n_params : -1; }
+int32_t dp_num_slots(const dp_world* w) { return w ? w->Tf.nslots : -1; }
+int32_t dp_ckpt_every(const dp_world* w) { return w ? w->D.ckpt_every : -1; }
+
+dp_status dp_schedule(const dp_world* w, int32_t* kind, int32_t* idx, int32_t* sub, int32_t* body_a, int32_t* body_b,
+                      int32_t* colour, int32_t* order) {
+  if (!w) return fail(DP_EINVAL, "world is NULL");
+  const DevTopo& T = w->Tf;
+  for (int s = 0; s < T.nslots; ++s) {
+    if (kind) kind[s] = T.skind[s];
+    if (idx) idx[s] = T.sidx[s];
+    if (sub) sub[s] = T.ssub[s];
+    if (body_a) body_a[s] = T.sa[s];
+    if (body_b) body_b[s] = T.sb[s];
+    if (colour) colour[s] = w->colour[s];
+    if (order) order[s] = T.order[s];
+  }
+  return DP_OK;
+}
+
+static dp_status stage_state_in(dp_world* w, const float* state, float* dst) {
+  if (!state) return fail(DP_EINVAL, "state is NULL");
+  CU(cudaMemcpyAsync(w->stage, state, sizeof(float) * (size_t)w->B * w->nf, cudaMemcpyDefault, w->stream));
+  CU(launch_state_in(w->B, w->Bp, w->nf, w->stage, dst, w->stream));
+  return DP_OK;
+}
+
+dp_status dp_set_initial_state(dp_world* w, const float* state) {
+  if (!w) return fail(DP_EINVAL, "world is NULL");
+  return stage_state_in(w, state, w->x0);
+}
+
+dp_status dp_set_state(dp_world* w, const float* state, int32_t t) {
+  if (!w) return fail(DP_EINVAL, "world is NULL");
+  if (t < 0) return fail(DP_EINVAL, "t must be >= 0");
+  TRY(stage_state_in(w, state, w->D.state));
+  w->t_now = t;
+  return DP_OK;
+}
+
+dp_status dp_get_state(dp_world* w, float* state) {
+  if (!w || !state) return fail(DP_EINVAL, "world or state is NULL");
+  CU(launch_state_out(w->B, w->Bp, w->nf, w->D.state, w->stage, w->stream));
+  CU(cudaMemcpyAsync(state, w->stage, sizeof(float) * (size_t)w->B * w->nf, cudaMemcpyDefault, w->stream));
+  return DP_OK;
+}
+
+static dp_status stage_weights(dp_world* w, const float* W) {
+  if (w->n_params == 0) return DP_OK;
+  if (!W) return fail(DP_EINVAL, "the world has a controller: W is required");
+  CU(cudaMemcpyAsync(w->Wmaster, W, sizeof(float) * w->n_params, cudaMemcpyDefault, w->stream));
+  CU(launch_prep_weights(w->Tf, w->Wmaster, w->Wt, w->Wn, w->Wb, w->stream));
+  return DP_OK;
+}
+
+dp_status dp_step(dp_world* w, int32_t n_steps, const float* W, uint8_t* active) {
+  if (!w) return fail(DP_EINVAL, "world is NULL");
+  if (n_steps < 0) return fail(DP_EINVAL, "n_steps must be >= 0");
+  if (n_steps == 0) return DP_OK;
+  TRY(stage_weights(w, W));
+  DevPtrs D = w->D;
+  D.active = active;
+  D.traj = nullptr;
+  CU(launch_forward(w->Tf, D, w->x0, w->t_now, n_steps, 0, w->stream));
+  w->t_now += n_steps;
+  w->have_rollout = false;
+  return DP_OK;
+}
+
+dp_status dp_rollout(dp_world* w, const float* W, float* loss, float* traj, uint8_t* active) {
+  if (!w) return fail(DP_EINVAL, "world is NULL");
+  TRY(stage_weights(w, W));
+  DevPtrs D = w->D;
+  D.active = active;
+  D.traj = traj;
+  CU(cudaMemsetAsync(D.status, 0, sizeof(int) * w->Bp, w->stream));
+  CU(launch_forward(w->Tf, D, w->x0, 0, w->Tf.horizon, 1, w->stream));
+  if (loss) CU(cudaMemcpyAsync(loss, D.loss, sizeof(float) * w->B, cudaMemcpyDefault, w->stream));
+  w->t_now = w->Tf.horizon;
+  w->have_rollout = true;
+  return DP_OK;
+}
+
+dp_status dp_backward(dp_world* w, const float* dloss, float* dW, float* dstate0, const dp_param_grads* dp) {
+  if (!w) return fail(DP_EINVAL, "world is NULL");
+  if (!w->have_rollout) return fail(DP_ESTATE, "dp_backward needs a preceding dp_rollout");
+  if (!dloss) return fail(DP_EINVAL, "dloss is NULL");
+  const DevTopo& T = w->Tb;
+  DevPtrs& D = w->D;
+  CU(cudaMemcpyAsync(w->stage, dloss, sizeof(float) * w->B, cudaMemcpyDefault, w->stream));
+  CU(launch_pad_scalar(w->B, w->Bp, w->stage, D.dloss, w->stream));
+  CU(cudaMemsetAsync(D.grad_prm, 0, sizeof(float) * (size_t)T.n_pfields * w->Bp, w->stream));
+  CU(launch_backward(T, D, w->stream));
+  if (dstate0) {
+    CU(launch_state_out(w->B, w->Bp, w->nf, D.grad_state0, w->stage, w->stream));
+    CU(cudaMemcpyAsync(dstate0, w->stage, sizeof(float) * (size_t)w->B * w->nf, cudaMemcpyDefault, w->stream));
+  }
+  if (dp) {
+    struct G { float* dst; int off, n; } groups[] = {
+        {dp->mass, T.o_mass, T.nb},           {dp->inertia, T.o_inertia, 3 * T.nb},  {dp->anchor, T.o_anchor, 6 * T.nj},
+        {dp->limit, T.o_limit, 2 * T.nj},     {dp->motor, T.o_motor, 3 * T.nj},      {dp->sph_off, T.o_sph_off, 3 * T.ns},
+        {dp->sph_rad, T.o_sph_rad, T.ns},     {dp->sph_mu, T.o_sph_mu, T.ns},        {dp->sph_e, T.o_sph_e, T.ns},
+        {dp->loss_point, T.o_loss_point, 3},  {dp->loss_target, T.o_loss_target, 3}};
+    for (const G& g : groups) {
+      if (!g.dst || g.n == 0) continue;
+      if ((size_t)w->B * g.n > w->stage_floats) return fail(DP_EINVAL, "staging buffer too small");
+      CU(launch_param_out(w->B, w->Bp, g.off, g.n, D.grad_prm, w->stage, w->stream));
+      CU(cudaMemcpyAsync(g.dst, w->stage, sizeof(float) * (size_t)w->B * g.n, cudaMemcpyDefault, w->stream));
+    }
+  }
+  if (dW && w->n_params > 0) {
+    const size_t N = (size_t)T.horizon * w->Bp;
+    const int splits = w->splits;
+    const size_t chunk = ((N + splits - 1) / splits + 15) / 16 * 16;
+    const int nl = T.n_layers + (T.skip ? 1 : 0);
+    size_t off = 0;
+    for (int l = 0; l < nl; ++l) {
+      const bool sk = l == T.n_layers;
+      const int ni = sk ? T.widths[0] : T.widths[l];
+      const int no_ = sk ? T.widths[T.n_layers] : T.widths[l + 1];
+      const float* del = D.dump + (size_t)T.dump_del[sk ? T.n_layers - 1 : l] * N;
+      const float* act = D.dump + (size_t)T.dump_act[sk ? 0 : l] * N;
+      CU(launch_dw(del, act, no_, ni, N, w->partial, splits, chunk, w->stream));
+      CU(launch_sum_splits(w->partial, splits, (size_t)no_ * ni, w->dW_stage + off, w->stream));
+      off += (size_t)no_ * ni;
+      CU(launch_rowsum(del, no_, N, w->partial, splits, chunk, w->stream));
+      CU(launch_sum_splits(w->partial, splits, (size_t)no_, w->dW_stage + off, w->stream));
+      off += no_;
+    }
+    CU(cudaMemcpyAsync(dW, w->dW_stage, sizeof(float) * w->n_params, cudaMemcpyDefault, w->stream));
+  }
+  return DP_OK;
+}
+
+dp_status dp_sync(dp_world* w) {
+  if (!w) return fail(DP_EINVAL, "world is NULL");
+  CU(cudaStreamSynchronize(w->stream));
+  std::vector<int> st(w->Bp);
+  CU(cudaMemcpy(st.data(), w->D.status, sizeof(int) * w->Bp, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < w->B; ++i)
+    if (st[i]) return fail(DP_ENAN, "instance " + std::to_string(i) + " produced a non-finite state or loss");
+  return DP_OK;
+}
+
+}  // extern "C"

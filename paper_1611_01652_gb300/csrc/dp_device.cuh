@@ -1,0 +1,211 @@
+// Device-side types shared by the kernels of libdphys (not part of the public ABI).
+//
+// Mapping: one lane = one robot instance. A warp owns 32 instances for the whole rollout,
+// so the solver's Gauss-Seidel order is executed exactly and every SIMT lane does useful
+// work. Per-instance working arrays live in shared memory as [field][32 lanes]
+// (bank-conflict free); per-instance parameters, constraint rows and the per-step tape live in
+// global memory as [field][instance] (coalesced: a warp touches 32 consecutive floats).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define DPK_MAXB 32
+#define DPK_MAXJ 32
+#define DPK_MAXS 32
+#define DPK_MAXP 32
+#define DPK_MAXSLOT (5 * DPK_MAXJ + 2 * DPK_MAXJ + 3 * DPK_MAXS + 3 * DPK_MAXP)
+#define DPK_MAXL 6
+
+// Row kinds (canonical slot order: joints, limits, motors, ground contacts, pair contacts).
+enum { RK_JLIN = 0, RK_JANG = 1, RK_LIMIT = 2, RK_MOTOR = 3, RK_GN = 4, RK_GT = 5, RK_PN = 6, RK_PT = 7 };
+
+// Constraint-row record in global memory, [slot][field][instance].
+enum {
+  RF_LIN = 0,    // 3: J_va (J_vb = -lin)
+  RF_ANGA = 3,   // 3: J_wa
+  RF_ANGB = 6,   // 3: J_wb
+  RF_IA = 9,     // 3: I_a^-1 J_wa (world frame)
+  RF_IB = 12,    // 3: I_b^-1 J_wb
+  RF_MEFF = 15,  // 1: 1/(J M^-1 J^T + gamma); 0 for inactive rows (a no-op)
+  RF_BIAS = 16,  // 1
+  RF_LO = 17,    // 1: lower bound (friction: unused)
+  RF_HI = 18,    // 1: upper bound (friction: mu)
+  RF_N = 19
+};
+
+struct DevTopo {
+  int B, Bp;  // instances, padded to a multiple of 32 (stride of every [field][instance] array)
+  int nb, nj, ns, np, nslots;
+  int iters, horizon, features, imu_body, loss_kind, loss_mode, loss_body;
+  int n_layers, skip, n_params, n_motors;
+  int widths[DPK_MAXL + 1];
+  int w_off[DPK_MAXL + 2];   // offset of layer l's W[out][in] in the flat weights (l = n_layers: skip)
+  float gravity[3], dt, ground_z, beta, gamma, slop, clock_hz;
+  // per-instance parameter field offsets in the [field][Bp] parameter array
+  int o_mass, o_inertia, o_anchor, o_axis, o_ref, o_limit, o_motor, o_sph_off, o_sph_rad, o_sph_mu, o_sph_e,
+      o_loss_point, o_loss_target, n_pfields;
+  int8_t jtype[DPK_MAXJ], ja[DPK_MAXJ], jb[DPK_MAXJ], jflags[DPK_MAXJ], jmotor[DPK_MAXJ];
+  int8_t motor_joint[DPK_MAXJ];
+  int8_t sbody[DPK_MAXS], pk[DPK_MAXP], pl[DPK_MAXP];
+  // slots (indexed by slot) and the sweep order
+  uint8_t skind[DPK_MAXSLOT], sidx[DPK_MAXSLOT], ssub[DPK_MAXSLOT];
+  int8_t sa[DPK_MAXSLOT], sb[DPK_MAXSLOT];
+  int16_t snormal[DPK_MAXSLOT];
+  int16_t order[DPK_MAXSLOT];
+  // shared-memory layout per warp, in units of 32 floats (one float per lane)
+  int sm_x0, sm_x, sm_xb, sm_vb, sm_iinv, sm_invm, sm_th, sm_thd, sm_ua, sm_wst, sm_wbr, sm_lam, sm_u;
+  int sm_thb, sm_thdb, sm_uab, sm_wstb, sm_iinvb, sm_invmb, sm_rc, sm_sbar, sm_act[DPK_MAXL + 1], sm_total;
+  // activation/delta dump offsets (rows of [feature][T*Bp]); act l = input of layer l
+  int dump_act[DPK_MAXL + 1], dump_del[DPK_MAXL + 1], dump_rows;
+};
+
+// Global buffers a kernel works on.
+struct DevPtrs {
+  const float* prm;      // [n_pfields][Bp]
+  const float* Wt;       // controller, fp32 copies of the bf16 weights, each layer [in][out]
+  const float* Wn;       // same, each layer [out][in]
+  const float* bias;     // controller biases, per layer [out] (then skip bias)
+  float* state;          // current state [nb*18][Bp]
+  float* ckpt;           // checkpoints [n_ckpt][nb*18][Bp]
+  float* seg;            // segment states for the backward [K+1][nb*18][Bp]
+  float* rows;           // [nslots][RF_N][Bp]
+  float* lam_hist;       // [iters][nslots][Bp]
+  uint8_t* br_hist;      // [iters][nslots][Bp]
+  float* v_iter;         // [iters][nb*6][Bp] velocities after each sweep
+  float* vminus;         // [nb*6][Bp] velocities after the external impulses
+  float* dump;           // controller activations and deltas [dump_rows][T*Bp]
+  float* loss;           // [Bp]
+  float* dloss;          // [Bp]
+  float* grad_prm;       // [n_pfields][Bp]
+  float* grad_state0;    // [nb*18][Bp]
+  float* traj;           // optional [T+1][B][nb][18]
+  uint8_t* active;       // optional [T][B][nslots]
+  int* status;           // [Bp] nonzero: non-finite value met
+  int ckpt_every, n_ckpt;
+};
+
+// ------------------------------------------------------------------------------- math
+struct M3 { float m[9]; };
+
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator-(float3 a) { return f3(-a.x, -a.y, -a.z); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return f3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float3& operator+=(float3& a, float3 b) { a = a + b; return a; }
+__device__ __forceinline__ float3& operator-=(float3& a, float3 b) { a = a - b; return a; }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+  return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float3 mv(const M3& R, float3 x) {
+  return f3(R.m[0] * x.x + R.m[1] * x.y + R.m[2] * x.z, R.m[3] * x.x + R.m[4] * x.y + R.m[5] * x.z,
+            R.m[6] * x.x + R.m[7] * x.y + R.m[8] * x.z);
+}
+__device__ __forceinline__ float3 mtv(const M3& R, float3 x) {
+  return f3(R.m[0] * x.x + R.m[3] * x.y + R.m[6] * x.z, R.m[1] * x.x + R.m[4] * x.y + R.m[7] * x.z,
+            R.m[2] * x.x + R.m[5] * x.y + R.m[8] * x.z);
+}
+__device__ __forceinline__ M3 mm(const M3& A, const M3& B) {
+  M3 C;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      C.m[3 * i + j] = A.m[3 * i] * B.m[j] + A.m[3 * i + 1] * B.m[3 + j] + A.m[3 * i + 2] * B.m[6 + j];
+  return C;
+}
+__device__ __forceinline__ M3 mT(const M3& A) {
+  M3 C;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) C.m[3 * i + j] = A.m[3 * j + i];
+  return C;
+}
+__device__ __forceinline__ M3 eye3() {
+  M3 I;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) I.m[k] = (k % 4 == 0) ? 1.f : 0.f;
+  return I;
+}
+// symmetric matrix stored as xx, xy, xz, yy, yz, zz
+__device__ __forceinline__ float3 symv(const float* s6, float3 x) {
+  return f3(s6[0] * x.x + s6[1] * x.y + s6[2] * x.z, s6[1] * x.x + s6[3] * x.y + s6[4] * x.z,
+            s6[2] * x.x + s6[4] * x.y + s6[5] * x.z);
+}
+// R diag(d) R^T as 6 unique entries
+__device__ __forceinline__ void rot_diag6(const M3& R, float3 d, float* o) {
+  const float* r = R.m;
+  o[0] = r[0] * r[0] * d.x + r[1] * r[1] * d.y + r[2] * r[2] * d.z;
+  o[1] = r[0] * r[3] * d.x + r[1] * r[4] * d.y + r[2] * r[5] * d.z;
+  o[2] = r[0] * r[6] * d.x + r[1] * r[7] * d.y + r[2] * r[8] * d.z;
+  o[3] = r[3] * r[3] * d.x + r[4] * r[4] * d.y + r[5] * r[5] * d.z;
+  o[4] = r[3] * r[6] * d.x + r[4] * r[7] * d.y + r[5] * r[8] * d.z;
+  o[5] = r[6] * r[6] * d.x + r[7] * r[7] * d.y + r[8] * r[8] * d.z;
+}
+// Orthonormal basis of a unit vector (Duff et al. 2017, "Building an Orthonormal Basis,
+// Revisited"), sign(0) = +1.
+__device__ __forceinline__ void onb3(float3 n, float3& t1, float3& t2) {
+  float s = n.z >= 0.f ? 1.f : -1.f;
+  float a = -1.f / (s + n.z);
+  float b = n.x * n.y * a;
+  t1 = f3(1.f + s * n.x * n.x * a, s * b, -s * n.x);
+  t2 = f3(b, s + n.y * n.y * a, -n.y);
+}
+// Reverse mode of onb3 for fixed sign: accumulate dL/dn given dL/dt1, dL/dt2.
+__device__ __forceinline__ float3 onb3_vjp(float3 n, float3 g1, float3 g2) {
+  float s = n.z >= 0.f ? 1.f : -1.f;
+  float a = -1.f / (s + n.z);
+  float a2 = a * a;  // da/dnz
+  // b = nx ny a
+  float db_dx = n.y * a, db_dy = n.x * a, db_dz = n.x * n.y * a2;
+  float3 g = f3(0.f, 0.f, 0.f);
+  // t1 = (1 + s nx^2 a, s b, -s nx)
+  g.x += g1.x * (2.f * s * n.x * a) + g1.y * s * db_dx - g1.z * s;
+  g.y += g1.y * s * db_dy;
+  g.z += g1.x * (s * n.x * n.x * a2) + g1.y * s * db_dz;
+  // t2 = (b, s + ny^2 a, -ny)
+  g.x += g2.x * db_dx;
+  g.y += g2.x * db_dy + g2.y * (2.f * n.y * a) - g2.z;
+  g.z += g2.x * db_dz + g2.y * (n.y * n.y * a2);
+  return g;
+}
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// Lane views: shared memory [field][32], global memory [field][Bp].
+struct SL {
+  float* p;
+  __device__ __forceinline__ float& operator[](int f) const { return p[f * 32]; }
+  __device__ __forceinline__ float3 v3(int f) const { return f3(p[f * 32], p[(f + 1) * 32], p[(f + 2) * 32]); }
+  __device__ __forceinline__ void s3(int f, float3 v) const { p[f * 32] = v.x; p[(f + 1) * 32] = v.y; p[(f + 2) * 32] = v.z; }
+  __device__ __forceinline__ void a3(int f, float3 v) const { p[f * 32] += v.x; p[(f + 1) * 32] += v.y; p[(f + 2) * 32] += v.z; }
+};
+struct GL {
+  float* p;
+  int s;
+  __device__ __forceinline__ float& operator[](int f) const { return p[(size_t)f * s]; }
+  __device__ __forceinline__ float3 v3(int f) const { return f3(p[(size_t)f * s], p[(size_t)(f + 1) * s], p[(size_t)(f + 2) * s]); }
+  __device__ __forceinline__ void s3(int f, float3 v) const { p[(size_t)f * s] = v.x; p[(size_t)(f + 1) * s] = v.y; p[(size_t)(f + 2) * s] = v.z; }
+  __device__ __forceinline__ void a3(int f, float3 v) const { p[(size_t)f * s] += v.x; p[(size_t)(f + 1) * s] += v.y; p[(size_t)(f + 2) * s] += v.z; }
+};
+// Wide-stride global view (controller activation/delta columns of the [row][T*Bp] dump).
+struct GW {
+  float* p;
+  size_t s;
+  __device__ __forceinline__ float& operator[](int f) const { return p[(size_t)f * s]; }
+};
+struct GC {
+  const float* p;
+  int s;
+  __device__ __forceinline__ float operator[](int f) const { return __ldg(p + (size_t)f * s); }
+  __device__ __forceinline__ float3 v3(int f) const { return f3((*this)[f], (*this)[f + 1], (*this)[f + 2]); }
+};
+
+__device__ __forceinline__ M3 loadR(const SL& X, int base) {
+  M3 R;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) R.m[k] = X[base + 3 + k];
+  return R;
+}

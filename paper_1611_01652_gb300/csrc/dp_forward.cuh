@@ -1,0 +1,428 @@
+// Forward step of the rigid-body engine, one lane per instance (arXiv 1611.01652, section 2.1):
+// controller (Eq. g) -> servo targets -> gravity and gyroscopic impulses -> branchless sphere
+// contact detection -> constraint rows -> fixed-iteration projected Gauss-Seidel -> semi-implicit
+// Euler with the Eq. 1 renormalisation (read as R <- (3R - R R^T R)/2) -> loss term (Eq. L).
+#pragma once
+#include <cuda_bf16.h>
+
+#include "dp_device.cuh"
+
+#define FULLMASK 0xffffffffu
+
+// Views of one lane's data.
+struct Lane {
+  SL S;        // this warp's shared-memory block, offset to the lane
+  GC P;        // parameters [field][Bp]
+  GL rows;     // constraint rows, slot s at rows[s * RF_N + f]
+  int i;       // instance index
+};
+
+__device__ __forceinline__ float3 body_v(const SL& X, int b) { return b >= 0 ? X.v3(18 * b + 12) : f3(0.f, 0.f, 0.f); }
+__device__ __forceinline__ float3 body_w(const SL& X, int b) { return b >= 0 ? X.v3(18 * b + 15) : f3(0.f, 0.f, 0.f); }
+__device__ __forceinline__ float3 body_p(const SL& X, int b) { return b >= 0 ? X.v3(18 * b) : f3(0.f, 0.f, 0.f); }
+__device__ __forceinline__ M3 body_R(const SL& X, int b) { return b >= 0 ? loadR(X, 18 * b) : eye3(); }
+
+// Hinge axis (world), angle about it between the two reference vectors, and its rate.
+__device__ void hinge_kinematics(const DevTopo& T, const Lane& L, const SL& X) {
+  const SL& S = L.S;
+  for (int j = 0; j < T.nj; ++j) {
+    int a = T.ja[j], b = T.jb[j];
+    M3 Ra = body_R(X, a);
+    float3 ua = mv(Ra, L.P.v3(T.o_axis + 6 * j));
+    S.s3(T.sm_ua + 3 * j, ua);
+    if (T.jtype[j] == 1) {
+      M3 Rb = loadR(X, 18 * b);
+      float3 wa = mv(Ra, L.P.v3(T.o_ref + 6 * j));
+      float3 wb = mv(Rb, L.P.v3(T.o_ref + 6 * j + 3));
+      float y = dot3(cross3(wa, wb), ua), x = dot3(wa, wb);
+      S[T.sm_th + j] = atan2f(y, x);
+      S[T.sm_thd + j] = dot3(ua, body_w(X, b) - body_w(X, a));
+    } else {
+      S[T.sm_th + j] = 0.f;
+      S[T.sm_thd + j] = 0.f;
+    }
+  }
+}
+
+// Loss point q = p_b + R_b c.
+__device__ __forceinline__ float3 loss_point(const DevTopo& T, const Lane& L, const SL& X) {
+  int b = T.loss_body;
+  return X.v3(18 * b) + mv(loadR(X, 18 * b), L.P.v3(T.o_loss_point));
+}
+__device__ __forceinline__ float loss_value(const DevTopo& T, const Lane& L, const SL& X) {
+  float3 q = loss_point(T, L, X);
+  float3 y = L.P.v3(T.o_loss_target);
+  float3 d = q - y;
+  switch (T.loss_kind) {
+    case 0: return dot3(d, d);
+    case 1: return sqrtf(dot3(d, d));
+    default: return dot3(y, q);
+  }
+}
+__device__ __forceinline__ float loss_weight(const DevTopo& T, int t_next) {
+  if (T.loss_mode == 1) return 1.f / (float)T.horizon;
+  return t_next == T.horizon ? 1.f : 0.f;
+}
+
+// Controller input vector s(x^t), rounded to bfloat16, into act0 (padded with zeros).
+template <class AV>
+__device__ void controller_features(const DevTopo& T, const Lane& L, const SL& X, int t, const AV& act0) {
+  const SL& S = L.S;
+  int k = 0;
+  if (T.features & 1)
+    for (int m = 0; m < T.n_motors; ++m) act0[k++] = bf16r(S[T.sm_th + T.motor_joint[m]]);
+  if (T.features & 2)
+    for (int m = 0; m < T.n_motors; ++m) act0[k++] = bf16r(S[T.sm_thd + T.motor_joint[m]]);
+  if (T.features & 4) {
+    double ph = 2.0 * 3.14159265358979323846 * (double)T.clock_hz * ((double)t * (double)T.dt);
+    act0[k++] = bf16r((float)sin(ph));
+    act0[k++] = bf16r((float)cos(ph));
+  }
+  if (T.features & 8) {
+    int b = T.imu_body;
+    M3 R = loadR(X, 18 * b);
+    float3 g = mtv(R, f3(0.f, 0.f, -1.f));
+    float3 wl = mtv(R, X.v3(18 * b + 15));
+    act0[k++] = bf16r(g.x); act0[k++] = bf16r(g.y); act0[k++] = bf16r(g.z);
+    act0[k++] = bf16r(wl.x); act0[k++] = bf16r(wl.y); act0[k++] = bf16r(wl.z);
+  }
+  if (T.features & 16) {
+    float3 d = loss_point(T, L, X) - L.P.v3(T.o_loss_target);
+    act0[k++] = bf16r(d.x); act0[k++] = bf16r(d.y); act0[k++] = bf16r(d.z);
+  }
+  for (; k < T.widths[0]; ++k) act0[k] = 0.f;
+}
+
+// One dense layer on this lane: out[o] = b[o] + sum_i W[o][i] in[i], weights from the
+// [in][out_pad] copy (8 outputs per pass, broadcast float4 loads).
+template <class AVI, class AVO>
+__device__ void dense_fwd(const float* __restrict__ Wt, const float* __restrict__ bias, int ni, int no, const AVI& in,
+                          const AVO& out, bool hidden, bool accumulate) {
+  const int nop = (no + 7) & ~7;
+  for (int o0 = 0; o0 < no; o0 += 8) {
+    float acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = (o0 + k < no) ? __ldg(bias + o0 + k) : 0.f;
+    const float* w = Wt + o0;
+    for (int ii = 0; ii < ni; ++ii) {
+      float av = in[ii];
+      float4 w0 = __ldg(reinterpret_cast<const float4*>(w + (size_t)ii * nop));
+      float4 w1 = __ldg(reinterpret_cast<const float4*>(w + (size_t)ii * nop + 4));
+      acc[0] = fmaf(w0.x, av, acc[0]); acc[1] = fmaf(w0.y, av, acc[1]);
+      acc[2] = fmaf(w0.z, av, acc[2]); acc[3] = fmaf(w0.w, av, acc[3]);
+      acc[4] = fmaf(w1.x, av, acc[4]); acc[5] = fmaf(w1.y, av, acc[5]);
+      acc[6] = fmaf(w1.z, av, acc[6]); acc[7] = fmaf(w1.w, av, acc[7]);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (o0 + k < no) {
+        float z = accumulate ? out[o0 + k] + acc[k] : acc[k];
+        out[o0 + k] = hidden ? bf16r(fmaxf(z, 0.f)) : z;
+      }
+    }
+  }
+}
+
+// Controller forward: act[0] already holds the features; act[n_layers] gets the output u.
+template <class AV>
+__device__ void controller_forward(const DevTopo& T, const DevPtrs& D, const AV* act) {
+  for (int l = 0; l < T.n_layers; ++l) {
+    const int ni = T.widths[l], no = T.widths[l + 1];
+    const float* Wt = D.Wt + T.w_off[l];
+    const float* b = D.bias + T.w_off[l];
+    dense_fwd(Wt, b, ni, no, act[l], act[l + 1], l + 1 < T.n_layers, false);
+  }
+  if (T.skip) {
+    const int l = T.n_layers;
+    dense_fwd(D.Wt + T.w_off[l], D.bias + T.w_off[l], T.widths[0], T.widths[l], act[0], act[l], false, true);
+  }
+}
+
+// Servo targets w* = clamp(k (u - theta), -vmax, vmax).
+template <class AV>
+__device__ void servo_targets(const DevTopo& T, const Lane& L, const AV& u) {
+  const SL& S = L.S;
+  for (int m = 0; m < T.n_motors; ++m) {
+    int j = T.motor_joint[m];
+    float k = L.P[T.o_motor + 3 * j], vmax = L.P[T.o_motor + 3 * j + 2];
+    float um = (T.n_layers > 0 && m < T.widths[T.n_layers]) ? u[m] : 0.f;
+    float x = k * (um - S[T.sm_th + j]);
+    float br = x < -vmax ? 1.f : (x > vmax ? 2.f : 0.f);
+    S[T.sm_wst + j] = br == 1.f ? -vmax : (br == 2.f ? vmax : x);
+    S[T.sm_wbr + j] = br;
+  }
+}
+
+// Gravity and the explicit gyroscopic term; world inverse inertia and inverse mass.
+__device__ void external_impulses(const DevTopo& T, const Lane& L, const SL& X) {
+  const SL& S = L.S;
+  const float h = T.dt;
+  const float3 g = f3(T.gravity[0], T.gravity[1], T.gravity[2]);
+  for (int b = 0; b < T.nb; ++b) {
+    M3 R = loadR(X, 18 * b);
+    float3 I = L.P.v3(T.o_inertia + 3 * b);
+    float m = L.P[T.o_mass + b];
+    float iw[6], ii[6];
+    rot_diag6(R, I, iw);
+    rot_diag6(R, f3(1.f / I.x, 1.f / I.y, 1.f / I.z), ii);
+    float3 v = X.v3(18 * b + 12) + h * g;
+    float3 w = X.v3(18 * b + 15);
+    float3 gy = -cross3(w, symv(iw, w));
+    w += h * symv(ii, gy);
+    X.s3(18 * b + 12, v);
+    X.s3(18 * b + 15, w);
+    S[T.sm_invm + b] = 1.f / m;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) S[T.sm_iinv + 6 * b + k] = ii[k];
+  }
+}
+
+__device__ __forceinline__ float min0f(float x) { return x < 0.f ? x : 0.f; }
+
+// Geometry of one contact/joint row; shared by assembly and its reverse mode.
+struct RowGeo {
+  float3 lin, angA, angB;
+  float bias, lo, hi;
+  bool active;
+};
+
+// Assemble every constraint slot of this instance into rows (slot order).
+__device__ void assemble_rows(const DevTopo& T, const Lane& L, const SL& X, uint8_t* active_out) {
+  const SL& S = L.S;
+  const float h = T.dt;
+  const float bh = T.beta / h;
+  const float INF = __int_as_float(0x7f800000);
+  const float3 ez = f3(0.f, 0.f, 1.f);
+  for (int s = 0; s < T.nslots; ++s) {
+    const int kind = T.skind[s], idx = T.sidx[s], sub = T.ssub[s], a = T.sa[s], b = T.sb[s];
+    float3 lin = f3(0.f, 0.f, 0.f), angA = lin, angB = lin;
+    float bias = 0.f, lo = -INF, hi = INF;
+    bool active = true;
+    switch (kind) {
+      case RK_JLIN: {
+        float3 ra = a >= 0 ? mv(loadR(X, 18 * a), L.P.v3(T.o_anchor + 6 * idx)) : L.P.v3(T.o_anchor + 6 * idx);
+        float3 rb = mv(loadR(X, 18 * b), L.P.v3(T.o_anchor + 6 * idx + 3));
+        float3 C = (body_p(X, a) + ra) - (X.v3(18 * b) + rb);
+        float3 e = f3(sub == 0 ? 1.f : 0.f, sub == 1 ? 1.f : 0.f, sub == 2 ? 1.f : 0.f);
+        lin = e;
+        angA = a >= 0 ? cross3(ra, e) : f3(0.f, 0.f, 0.f);
+        angB = -cross3(rb, e);
+        bias = bh * (sub == 0 ? C.x : (sub == 1 ? C.y : C.z));
+        break;
+      }
+      case RK_JANG: {
+        float3 t1, t2;
+        onb3(L.P.v3(T.o_axis + 6 * idx), t1, t2);
+        float3 t = mv(body_R(X, a), sub == 0 ? t1 : t2);
+        float3 ub = mv(loadR(X, 18 * b), L.P.v3(T.o_axis + 6 * idx + 3));
+        float3 ua = S.v3(T.sm_ua + 3 * idx);
+        angA = a >= 0 ? t : f3(0.f, 0.f, 0.f);
+        angB = -t;
+        bias = bh * dot3(t, cross3(ub, ua));
+        break;
+      }
+      case RK_LIMIT: {
+        float th = S[T.sm_th + idx];
+        float lo_j = L.P[T.o_limit + 2 * idx], hi_j = L.P[T.o_limit + 2 * idx + 1];
+        float3 ua = S.v3(T.sm_ua + 3 * idx);
+        if (th <= lo_j) {
+          angA = a >= 0 ? -ua : f3(0.f, 0.f, 0.f); angB = ua; bias = bh * (th - lo_j);
+        } else if (th >= hi_j) {
+          angA = a >= 0 ? ua : f3(0.f, 0.f, 0.f); angB = -ua; bias = bh * (hi_j - th);
+        } else {
+          active = false;
+        }
+        lo = 0.f;
+        break;
+      }
+      case RK_MOTOR: {
+        float3 ua = S.v3(T.sm_ua + 3 * idx);
+        angA = a >= 0 ? -ua : f3(0.f, 0.f, 0.f);
+        angB = ua;
+        bias = -S[T.sm_wst + idx];
+        float tm = L.P[T.o_motor + 3 * idx + 1] * h;
+        lo = -tm; hi = tm;
+        break;
+      }
+      case RK_GN:
+      case RK_GT: {
+        float3 c = mv(loadR(X, 18 * a), L.P.v3(T.o_sph_off + 3 * idx));
+        float rad = L.P[T.o_sph_rad + idx];
+        float d = (X[18 * a + 2] + c.z) - rad - T.ground_z;
+        active = d <= 0.f;
+        float3 ra = c - rad * ez;
+        if (kind == RK_GN) {
+          lin = ez;
+          angA = cross3(ra, ez);
+          float vn = dot3(lin, X.v3(18 * a + 12)) + dot3(angA, X.v3(18 * a + 15));
+          bias = bh * min0f(d + T.slop) + L.P[T.o_sph_e + idx] * min0f(vn);
+          lo = 0.f;
+        } else {
+          lin = sub == 0 ? f3(1.f, 0.f, 0.f) : f3(0.f, 1.f, 0.f);  // basis of +z
+          angA = cross3(ra, lin);
+          hi = L.P[T.o_sph_mu + idx];
+        }
+        break;
+      }
+      case RK_PN:
+      case RK_PT: {
+        const int k = T.pk[idx], l = T.pl[idx];
+        float3 ck = mv(loadR(X, 18 * a), L.P.v3(T.o_sph_off + 3 * k));
+        float3 cl = mv(loadR(X, 18 * b), L.P.v3(T.o_sph_off + 3 * l));
+        float3 dl = (X.v3(18 * a) + ck) - (X.v3(18 * b) + cl);
+        float dist = sqrtf(dot3(dl, dl));
+        float3 n = dist > 1e-9f ? (1.f / dist) * dl : ez;
+        float rk = L.P[T.o_sph_rad + k], rl = L.P[T.o_sph_rad + l];
+        float d = dist - rk - rl;
+        active = d <= 0.f;
+        float3 ra = ck - rk * n, rb = cl + rl * n;
+        if (kind == RK_PN) {
+          lin = n;
+          angA = cross3(ra, n);
+          angB = -cross3(rb, n);
+          float vn = dot3(n, X.v3(18 * a + 12) - X.v3(18 * b + 12)) + dot3(angA, X.v3(18 * a + 15)) +
+                     dot3(angB, X.v3(18 * b + 15));
+          float ek = L.P[T.o_sph_e + k], el = L.P[T.o_sph_e + l];
+          float e = ek >= el ? ek : el;
+          bias = bh * min0f(d + T.slop) + e * min0f(vn);
+          lo = 0.f;
+        } else {
+          float3 t1, t2;
+          onb3(n, t1, t2);
+          lin = sub == 0 ? t1 : t2;
+          angA = cross3(ra, lin);
+          angB = -cross3(rb, lin);
+          hi = sqrtf(L.P[T.o_sph_mu + k] * L.P[T.o_sph_mu + l]);
+        }
+        break;
+      }
+    }
+    float3 IA = f3(0.f, 0.f, 0.f), IB = IA;
+    float K = 0.f;
+    if (a >= 0) {
+      float ia[6];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) ia[q] = S[T.sm_iinv + 6 * a + q];
+      IA = symv(ia, angA);
+      K += S[T.sm_invm + a] * dot3(lin, lin) + dot3(angA, IA);
+    }
+    if (b >= 0) {
+      float ib[6];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) ib[q] = S[T.sm_iinv + 6 * b + q];
+      IB = symv(ib, angB);
+      K += S[T.sm_invm + b] * dot3(lin, lin) + dot3(angB, IB);
+    }
+    const GL& R = L.rows;
+    const int base = s * RF_N;
+    R.s3(base + RF_LIN, lin);
+    R.s3(base + RF_ANGA, angA);
+    R.s3(base + RF_ANGB, angB);
+    R.s3(base + RF_IA, IA);
+    R.s3(base + RF_IB, IB);
+    R[base + RF_MEFF] = active ? 1.f / (K + T.gamma) : 0.f;
+    R[base + RF_BIAS] = active ? bias : 0.f;
+    R[base + RF_LO] = lo;
+    R[base + RF_HI] = hi;
+    if (active_out) active_out[s] = active ? 1 : 0;
+  }
+}
+
+// Projected Gauss-Seidel, cold start, T.iters sweeps in the canonical order. With TAPE the
+// impulses and clamp branches of every sweep and the velocities after every sweep are kept.
+template <bool TAPE>
+__device__ void pgs_solve(const DevTopo& T, const DevPtrs& D, const Lane& L, const SL& X) {
+  const SL& S = L.S;
+  const int Bp = T.Bp;
+  for (int s = 0; s < T.nslots; ++s) S[T.sm_lam + s] = 0.f;
+  for (int it = 0; it < T.iters; ++it) {
+    for (int oi = 0; oi < T.nslots; ++oi) {
+      const int s = T.order[oi];
+      const int base = s * RF_N;
+      const float meff = L.rows[base + RF_MEFF];
+      if (!__any_sync(FULLMASK, meff != 0.f)) continue;  // the row is inactive on every lane
+      const int kind = T.skind[s], a = T.sa[s], b = T.sb[s];
+      const float3 lin = L.rows.v3(base + RF_LIN);
+      const float3 angA = L.rows.v3(base + RF_ANGA), angB = L.rows.v3(base + RF_ANGB);
+      const float bias = L.rows[base + RF_BIAS];
+      float lo = L.rows[base + RF_LO], hi = L.rows[base + RF_HI];
+      const float lam = S[T.sm_lam + s];
+      if (kind == RK_GT || kind == RK_PT) {
+        hi = hi * S[T.sm_lam + T.snormal[s]];
+        lo = -hi;
+      }
+      float Jv = 0.f;
+      float3 va, wa, vb, wb;
+      if (a >= 0) { va = X.v3(18 * a + 12); wa = X.v3(18 * a + 15); Jv += dot3(lin, va) + dot3(angA, wa); }
+      if (b >= 0) { vb = X.v3(18 * b + 12); wb = X.v3(18 * b + 15); Jv += dot3(angB, wb) - dot3(lin, vb); }
+      const float pre = lam - meff * (Jv + bias + T.gamma * lam);
+      const int br = pre < lo ? 1 : (pre > hi ? 2 : 0);
+      const float ln = br == 1 ? lo : (br == 2 ? hi : pre);
+      const float dl = ln - lam;
+      S[T.sm_lam + s] = ln;
+      if (a >= 0) {
+        X.s3(18 * a + 12, va + (dl * S[T.sm_invm + a]) * lin);
+        X.s3(18 * a + 15, wa + dl * L.rows.v3(base + RF_IA));
+      }
+      if (b >= 0) {
+        X.s3(18 * b + 12, vb - (dl * S[T.sm_invm + b]) * lin);
+        X.s3(18 * b + 15, wb + dl * L.rows.v3(base + RF_IB));
+      }
+      if (TAPE) {
+        size_t o = ((size_t)it * T.nslots + s) * Bp + L.i;
+        D.lam_hist[o] = ln;
+        D.br_hist[o] = (uint8_t)br;
+      }
+    }
+    if (TAPE) {
+      float* vi = D.v_iter + (size_t)it * T.nb * 6 * Bp + L.i;
+      for (int b = 0; b < T.nb; ++b)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) vi[(size_t)(6 * b + k) * Bp] = X[18 * b + 12 + k];
+    }
+  }
+}
+
+// Semi-implicit Euler on positions with the new velocities, then the Eq. 1 renormalisation.
+__device__ void integrate(const DevTopo& T, const SL& X) {
+  const float h = T.dt;
+  for (int b = 0; b < T.nb; ++b) {
+    float3 p = X.v3(18 * b), v = X.v3(18 * b + 12), w = X.v3(18 * b + 15);
+    M3 R = loadR(X, 18 * b), A;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      A.m[j] = R.m[j] + h * (-w.z * R.m[3 + j] + w.y * R.m[6 + j]);
+      A.m[3 + j] = R.m[3 + j] + h * (w.z * R.m[j] - w.x * R.m[6 + j]);
+      A.m[6 + j] = R.m[6 + j] + h * (-w.y * R.m[j] + w.x * R.m[3 + j]);
+    }
+    M3 AAA = mm(A, mm(mT(A), A));
+    X.s3(18 * b, p + h * v);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) X[18 * b + 3 + k] = 0.5f * (3.f * A.m[k] - AAA.m[k]);
+  }
+}
+
+// One full step x_t -> x_{t+1} in place on X. Returns the loss term of x_{t+1}.
+template <bool TAPE, class AV>
+__device__ float step_forward(const DevTopo& T, const DevPtrs& D, const Lane& L, const SL& X, const AV* act, int t,
+                              uint8_t* active_out) {
+  hinge_kinematics(T, L, X);
+  if (T.n_layers > 0) {
+    controller_features(T, L, X, t, act[0]);
+    controller_forward(T, D, act);
+    servo_targets(T, L, act[T.n_layers]);
+  } else {
+    servo_targets(T, L, act[0]);
+  }
+  external_impulses(T, L, X);
+  if (TAPE) {
+    for (int b = 0; b < T.nb; ++b)
+#pragma unroll
+      for (int k = 0; k < 6; ++k) D.vminus[(size_t)(6 * b + k) * T.Bp + L.i] = X[18 * b + 12 + k];
+  }
+  assemble_rows(T, L, X, active_out);
+  pgs_solve<TAPE>(T, D, L, X);
+  integrate(T, X);
+  float w = loss_weight(T, t + 1);
+  return w != 0.f ? w * loss_value(T, L, X) : 0.f;
+}

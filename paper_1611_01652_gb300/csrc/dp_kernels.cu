@@ -1,0 +1,310 @@
+// Kernels of libdphys: weight staging, the persistent rollout (forward) and reverse-mode
+// kernels (one warp = 32 instances for the whole horizon), the controller-gradient reduction
+// and layout transposes.
+#include <cuda_runtime.h>
+
+#include "dp_adjoint.cuh"
+#include "dp_kernels.h"
+
+extern __shared__ float g_smem[];
+
+// ------------------------------------------------------------------------------ weights
+// Flat fp32 master weights -> bf16-rounded fp32 copies in two layouts, fp32 biases.
+__global__ void k_prep_weights(const __grid_constant__ DevTopo T, const float* __restrict__ W, float* Wt, float* Wn,
+                               float* bias) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= T.n_params) return;
+  int off = 0;
+  const int nl = T.n_layers + (T.skip ? 1 : 0);
+  for (int l = 0; l < nl; ++l) {
+    const int ni = l < T.n_layers ? T.widths[l] : T.widths[0];
+    const int no = l < T.n_layers ? T.widths[l + 1] : T.widths[T.n_layers];
+    const int nop = (no + 7) & ~7, nip = (ni + 7) & ~7;
+    if (p < off + ni * no) {
+      int q = p - off, o = q / ni, i = q % ni;
+      float w = bf16r(W[p]);
+      Wt[T.w_off[l] + i * nop + o] = w;
+      Wn[T.w_off[l] + o * nip + i] = w;
+      return;
+    }
+    off += ni * no;
+    if (p < off + no) {
+      bias[T.w_off[l] + (p - off)] = W[p];
+      return;
+    }
+    off += no;
+  }
+}
+
+// ------------------------------------------------------------------------------ layouts
+// [B][nb*18] (user) -> [nb*18][Bp]; padded instances copy instance B-1.
+__global__ void k_state_in(int B, int Bp, int nf, const float* __restrict__ src, float* dst) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Bp) return;
+  int si = i < B ? i : B - 1;
+  for (int f = 0; f < nf; ++f) dst[(size_t)f * Bp + i] = src[(size_t)si * nf + f];
+}
+__global__ void k_state_out(int B, int Bp, int nf, const float* __restrict__ src, float* dst) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B) return;
+  for (int f = 0; f < nf; ++f) dst[(size_t)i * nf + f] = src[(size_t)f * Bp + i];
+}
+// Gather one parameter group: user [B][n] <-> internal field offset o, n fields.
+__global__ void k_param_out(int B, int Bp, int o, int n, const float* __restrict__ src, float* dst) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B) return;
+  for (int f = 0; f < n; ++f) dst[(size_t)i * n + f] = src[(size_t)(o + f) * Bp + i];
+}
+__global__ void k_pad_scalar(int B, int Bp, const float* __restrict__ src, float* dst) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Bp) return;
+  dst[i] = i < B ? src[i] : 0.f;
+}
+
+// ------------------------------------------------------------------------------ forward
+__device__ __forceinline__ void copy_state_to_smem(const DevTopo& T, const float* src, int i, const SL& X) {
+  for (int f = 0; f < 18 * T.nb; ++f) X[f] = src[(size_t)f * T.Bp + i];
+}
+__device__ __forceinline__ void copy_state_from_smem(const DevTopo& T, float* dst, int i, const SL& X) {
+  for (int f = 0; f < 18 * T.nb; ++f) dst[(size_t)f * T.Bp + i] = X[f];
+}
+
+// Persistent forward: each warp advances its 32 instances over `nsteps` steps starting at step
+// t0. With rollout != 0 it starts from x0, stores checkpoints every ckpt_every steps and the
+// per-instance loss of Eq. L.
+__global__ void __launch_bounds__(32) k_forward(const __grid_constant__ DevTopo T, const __grid_constant__ DevPtrs D,
+                                                 const float* __restrict__ x0, int t0, int nsteps, int rollout) {
+  const int lane = threadIdx.x;
+  const int i = blockIdx.x * 32 + lane;
+  float* sm = g_smem + lane;
+  Lane L{SL{sm}, GC{D.prm + i, T.Bp}, GL{D.rows + i, T.Bp}, i};
+  SL X{sm + T.sm_x * 32};
+  SL act[DPK_MAXL + 1];
+  for (int l = 0; l <= DPK_MAXL; ++l) act[l] = SL{sm + T.sm_act[l] * 32};
+  copy_state_to_smem(T, rollout ? x0 : D.state, i, X);
+  float loss = 0.f;
+  if (rollout && T.loss_kind == 3) loss = -dot3(L.P.v3(T.o_loss_target), loss_point(T, L, X));
+  const int B = T.B;
+  for (int k = 0; k < nsteps; ++k) {
+    const int t = t0 + k;
+    if (rollout) {
+      if (t % D.ckpt_every == 0) copy_state_from_smem(T, D.ckpt + (size_t)(t / D.ckpt_every) * 18 * T.nb * T.Bp, i, X);
+      if (D.traj && i < B)
+        for (int f = 0; f < 18 * T.nb; ++f) D.traj[((size_t)t * B + i) * 18 * T.nb + f] = X[f];
+    }
+    uint8_t* ao = (D.active && i < B) ? D.active + ((size_t)k * B + i) * T.nslots : nullptr;
+    loss += step_forward<false>(T, D, L, X, act, t, ao);
+  }
+  if (rollout && D.traj && i < B)
+    for (int f = 0; f < 18 * T.nb; ++f) D.traj[((size_t)(t0 + nsteps) * B + i) * 18 * T.nb + f] = X[f];
+  copy_state_from_smem(T, D.state, i, X);
+  bool bad = !isfinite(loss);
+  for (int f = 0; f < 18 * T.nb; ++f) bad |= !isfinite(X[f]);
+  if (rollout) D.loss[i] = loss;
+  if (bad && i < B) D.status[i] = 1;
+}
+
+// ------------------------------------------------------------------------------ backward
+// Reverse mode through the last rollout. For each checkpoint segment (last first): recompute
+// the segment's states, then for each step (last first) recompute the step with its tape and
+// run every stage's adjoint.
+__global__ void __launch_bounds__(32) k_backward(const __grid_constant__ DevTopo T, const __grid_constant__ DevPtrs D) {
+  const int lane = threadIdx.x;
+  const int i = blockIdx.x * 32 + lane;
+  const int Bp = T.Bp;
+  const size_t N = (size_t)T.horizon * Bp;
+  const int nf = 18 * T.nb;
+  float* sm = g_smem + lane;
+  Lane L{SL{sm}, GC{D.prm + i, Bp}, GL{D.rows + i, Bp}, i};
+  SL X{sm + T.sm_x * 32}, XB{sm + T.sm_xb * 32}, VB{sm + T.sm_vb * 32};
+  SL RC{sm + T.sm_rc * 32};
+  SL sbar{sm + T.sm_sbar * 32};
+  GL G{D.grad_prm + i, Bp};
+  for (int f = 0; f < nf; ++f) XB[f] = 0.f;
+  const float dl = D.dloss[i];
+  const int K = D.ckpt_every;
+  for (int c = D.n_ckpt - 1; c >= 0; --c) {
+    const int ta = c * K;
+    const int tb = min(T.horizon, ta + K);
+    // segment states x_ta .. x_{tb-1} into D.seg
+    copy_state_to_smem(T, D.ckpt + (size_t)c * nf * Bp, i, X);
+    for (int t = ta; t < tb; ++t) {
+      copy_state_from_smem(T, D.seg + (size_t)(t - ta) * nf * Bp, i, X);
+      if (t + 1 < tb) {
+        const size_t n = (size_t)t * Bp + i;
+        GW aw[DPK_MAXL + 1];
+        for (int l = 0; l <= DPK_MAXL; ++l) aw[l] = GW{D.dump + (size_t)T.dump_act[l] * N + n, N};
+        step_forward<false>(T, D, L, X, aw, t, nullptr);
+      }
+    }
+    for (int t = tb - 1; t >= ta; --t) {
+      const size_t n = (size_t)t * Bp + i;
+      GW act[DPK_MAXL + 1], del[DPK_MAXL + 1];
+      for (int l = 0; l <= DPK_MAXL; ++l) {
+        act[l] = GW{D.dump + (size_t)T.dump_act[l] * N + n, N};
+        del[l] = GW{D.dump + (size_t)T.dump_del[l] * N + n, N};
+      }
+      const float* x_t = D.seg + (size_t)(t - ta) * nf * Bp;
+      BLane Bl{L, GC{x_t + i, Bp}, G, GC{D.vminus + i, Bp}};
+      copy_state_to_smem(T, x_t, i, X);
+      step_forward<true>(T, D, L, X, act, t, nullptr);
+      loss_reverse(T, Bl, X, XB, loss_weight(T, t + 1) * dl);
+      for (int j = 0; j < T.nj; ++j) {
+        L.S[T.sm_thb + j] = 0.f; L.S[T.sm_thdb + j] = 0.f; L.S[T.sm_wstb + j] = 0.f;
+        L.S.s3(T.sm_uab + 3 * j, f3(0.f, 0.f, 0.f));
+      }
+      for (int b = 0; b < T.nb; ++b) {
+        L.S[T.sm_invmb + b] = 0.f;
+        for (int q = 0; q < 9; ++q) L.S[T.sm_iinvb + 9 * b + q] = 0.f;
+      }
+      for (int q = 0; q < T.nslots * RC_N; ++q) RC[q] = 0.f;
+      integrate_reverse(T, Bl, X, XB, VB);
+      pgs_reverse(T, D, Bl, X, VB, RC);
+      rows_reverse(T, Bl, XB, VB, RC);
+      external_reverse(T, Bl, XB, VB);
+      if (T.n_layers > 0) {
+        servo_reverse(T, Bl, act[T.n_layers], del[T.n_layers - 1]);
+        controller_reverse(T, D, act, del, sbar);
+        features_reverse(T, Bl, XB, sbar);
+      } else {
+        servo_reverse(T, Bl, act[0], act[0]);
+      }
+      hinge_reverse(T, Bl, XB);
+    }
+  }
+  if (T.loss_kind == 3) {  // initial term -a.q(x_0) of the displacement loss
+    BLane Bl{L, GC{D.ckpt + i, Bp}, G, GC{D.vminus + i, Bp}};
+    copy_state_to_smem(T, D.ckpt, i, X);
+    const int b = T.loss_body;
+    M3 R = loadR(X, 18 * b);
+    float3 c = L.P.v3(T.o_loss_point), a = L.P.v3(T.o_loss_target);
+    float3 gq = -dl * a;
+    XB.a3(18 * b, gq);
+    add_outer(XB, 18 * b + 3, gq, c);
+    G.a3(T.o_loss_point, mtv(R, gq));
+    G.a3(T.o_loss_target, -dl * (X.v3(18 * b) + mv(R, c)));
+    (void)Bl;
+  }
+  for (int f = 0; f < nf; ++f) D.grad_state0[(size_t)f * Bp + i] = XB[f];
+}
+
+// ------------------------------------------------------------------------------ dW reduction
+// partial[split][o][c] = sum over columns n in the split of del[o][n] * act[c][n]
+// (64x64 output tile per block, 256 threads, 4x4 outputs per thread).
+__global__ void __launch_bounds__(256) k_dw_gemm(const float* __restrict__ del, const float* __restrict__ act, int M,
+                                                 int C, size_t N, size_t chunk, float* __restrict__ partial) {
+  __shared__ float As[16][64 + 4];
+  __shared__ float Bs[16][64 + 4];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int o0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
+  const size_t n0 = (size_t)blockIdx.z * chunk;
+  const size_t n1 = min(N, n0 + chunk);
+  float acc[4][4] = {};
+  for (size_t nb = n0; nb < n1; nb += 16) {
+    // load 64 rows x 16 columns of each operand (coalesced along n)
+    for (int q = threadIdx.x; q < 64 * 16; q += 256) {
+      int r = q / 16, k = q % 16;
+      size_t n = nb + k;
+      As[k][r] = (o0 + r < M && n < n1) ? del[(size_t)(o0 + r) * N + n] : 0.f;
+      Bs[k][r] = (c0 + r < C && n < n1) ? act[(size_t)(c0 + r) * N + n] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      float a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { a[u] = As[k][ty * 4 + u]; b[u] = Bs[k][tx * 4 + u]; }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+  float* P = partial + (size_t)blockIdx.z * M * C;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      int o = o0 + ty * 4 + u, c = c0 + tx * 4 + v;
+      if (o < M && c < C) P[(size_t)o * C + c] = acc[u][v];
+    }
+}
+// partial[split][o] = sum over the split's columns of del[o][n]
+__global__ void k_rowsum(const float* __restrict__ del, int M, size_t N, size_t chunk, float* __restrict__ partial) {
+  const int o = blockIdx.y;
+  const size_t n0 = (size_t)blockIdx.x * chunk, n1 = min(N, n0 + chunk);
+  float s = 0.f;
+  for (size_t n = n0 + threadIdx.x; n < n1; n += blockDim.x) s += del[(size_t)o * N + n];
+  __shared__ float red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[(size_t)blockIdx.x * M + o] = red[0];
+}
+// out[k] = sum over splits of partial[split][k] (fixed order: deterministic)
+__global__ void k_sum_splits(const float* __restrict__ partial, int splits, size_t count, float* __restrict__ out) {
+  size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= count) return;
+  float s = 0.f;
+  for (int q = 0; q < splits; ++q) s += partial[(size_t)q * count + k];
+  out[k] = s;
+}
+
+// ------------------------------------------------------------------------------ launchers
+#define SM_BYTES(T) ((size_t)(T).sm_total * 32 * sizeof(float))
+
+cudaError_t launch_prep_weights(const DevTopo& T, const float* W, float* Wt, float* Wn, float* bias, cudaStream_t s) {
+  if (T.n_params == 0) return cudaSuccess;
+  k_prep_weights<<<(T.n_params + 255) / 256, 256, 0, s>>>(T, W, Wt, Wn, bias);
+  return cudaGetLastError();
+}
+cudaError_t launch_state_in(int B, int Bp, int nf, const float* src, float* dst, cudaStream_t s) {
+  k_state_in<<<(Bp + 127) / 128, 128, 0, s>>>(B, Bp, nf, src, dst);
+  return cudaGetLastError();
+}
+cudaError_t launch_state_out(int B, int Bp, int nf, const float* src, float* dst, cudaStream_t s) {
+  k_state_out<<<(B + 127) / 128, 128, 0, s>>>(B, Bp, nf, src, dst);
+  return cudaGetLastError();
+}
+cudaError_t launch_param_out(int B, int Bp, int o, int n, const float* src, float* dst, cudaStream_t s) {
+  k_param_out<<<(B + 127) / 128, 128, 0, s>>>(B, Bp, o, n, src, dst);
+  return cudaGetLastError();
+}
+cudaError_t launch_pad_scalar(int B, int Bp, const float* src, float* dst, cudaStream_t s) {
+  k_pad_scalar<<<(Bp + 127) / 128, 128, 0, s>>>(B, Bp, src, dst);
+  return cudaGetLastError();
+}
+cudaError_t launch_forward(const DevTopo& T, const DevPtrs& D, const float* x0, int t0, int nsteps, int rollout,
+                           cudaStream_t s) {
+  size_t smem = SM_BYTES(T);
+  cudaError_t e = cudaFuncSetAttribute(k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_forward<<<T.Bp / 32, 32, smem, s>>>(T, D, x0, t0, nsteps, rollout);
+  return cudaGetLastError();
+}
+cudaError_t launch_backward(const DevTopo& T, const DevPtrs& D, cudaStream_t s) {
+  size_t smem = SM_BYTES(T);
+  cudaError_t e = cudaFuncSetAttribute(k_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_backward<<<T.Bp / 32, 32, smem, s>>>(T, D);
+  return cudaGetLastError();
+}
+cudaError_t launch_dw(const float* del, const float* act, int M, int C, size_t N, float* partial, int splits,
+                      size_t chunk, cudaStream_t s) {
+  dim3 g((C + 63) / 64, (M + 63) / 64, splits);
+  k_dw_gemm<<<g, 256, 0, s>>>(del, act, M, C, N, chunk, partial);
+  return cudaGetLastError();
+}
+cudaError_t launch_rowsum(const float* del, int M, size_t N, float* partial, int splits, size_t chunk, cudaStream_t s) {
+  dim3 g(splits, M);
+  k_rowsum<<<g, 256, 0, s>>>(del, M, N, chunk, partial);
+  return cudaGetLastError();
+}
+cudaError_t launch_sum_splits(const float* partial, int splits, size_t count, float* out, cudaStream_t s) {
+  k_sum_splits<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(partial, splits, count, out);
+  return cudaGetLastError();
+}

@@ -1,0 +1,18 @@
+// Host-side launchers of the kernels in dp_kernels.cu (internal to libdphys).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "dp_device.cuh"
+
+cudaError_t launch_prep_weights(const DevTopo& T, const float* W, float* Wt, float* Wn, float* bias, cudaStream_t s);
+cudaError_t launch_state_in(int B, int Bp, int nf, const float* src, float* dst, cudaStream_t s);
+cudaError_t launch_state_out(int B, int Bp, int nf, const float* src, float* dst, cudaStream_t s);
+cudaError_t launch_param_out(int B, int Bp, int o, int n, const float* src, float* dst, cudaStream_t s);
+cudaError_t launch_pad_scalar(int B, int Bp, const float* src, float* dst, cudaStream_t s);
+cudaError_t launch_forward(const DevTopo& T, const DevPtrs& D, const float* x0, int t0, int nsteps, int rollout,
+                           cudaStream_t s);
+cudaError_t launch_backward(const DevTopo& T, const DevPtrs& D, cudaStream_t s);
+cudaError_t launch_dw(const float* del, const float* act, int M, int C, size_t N, float* partial, int splits,
+                      size_t chunk, cudaStream_t s);
+cudaError_t launch_rowsum(const float* del, int M, size_t N, float* partial, int splits, size_t chunk, cudaStream_t s);
+cudaError_t launch_sum_splits(const float* partial, int splits, size_t count, float* out, cudaStream_t s);

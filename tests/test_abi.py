@@ -1,0 +1,113 @@
+"""C-ABI library: builds for sm_103a, loads, exports every symbol include/dp.h declares, and
+rejects bad descriptors on the host (no GPU compute is called here)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1611_01652_gb300 import binding, build, workloads
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dp.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dp_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = binding.load()
+    names = declared_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(binding.SYMBOLS) == set(names)
+
+
+def test_enums_agree_with_header():
+    src = open(HEADER).read()
+    for name, val in (("DP_JOINT_HINGE", workloads.HINGE), ("DP_FLAG_MOTOR", workloads.FLAG_MOTOR),
+                      ("DP_F_IMU", workloads.F_IMU), ("DP_LOSS_DISP", workloads.L_DISP), ("DP_MODE_MEAN", workloads.M_MEAN)):
+        m = re.search(name + r"\s*=\s*(\d+)", src)
+        assert m and int(m.group(1)) == val, name
+
+
+def _desc(model):
+    keep = []
+    d = binding.BatchDesc()
+
+    def i32(a):
+        a = np.ascontiguousarray(np.asarray(a, np.int32).reshape(-1)) if np.size(a) else np.zeros(1, np.int32)
+        keep.append(a)
+        return a.ctypes.data_as(binding.PI)
+
+    def f32(a):
+        a = np.ascontiguousarray(np.asarray(a, np.float32).reshape(-1)) if np.size(a) else np.zeros(1, np.float32)
+        keep.append(a)
+        return a.ctypes.data_as(binding.PF)
+
+    d.n_instances, d.n_bodies, d.n_joints, d.n_spheres, d.n_pairs = model.B, model.nb, model.nj, model.ns, model.np_
+    d.joint_type, d.joint_body, d.joint_flags = i32(model.joint_type), i32(model.joint_body), i32(model.joint_flags)
+    d.sphere_body, d.pair_sphere = i32(model.sphere_body), i32(model.pair_sphere)
+    for k in ("mass", "inertia", "anchor", "axis", "ref", "limit", "motor", "sph_off", "sph_rad", "sph_mu", "sph_e",
+              "loss_point", "loss_target", "state0"):
+        setattr(d, k, f32(getattr(model, k)))
+    d.n_layers = max(len(model.widths) - 1, 0)
+    for l, wv in enumerate(model.widths):
+        d.widths[l] = wv
+    d.features, d.imu_body, d.dt, d.iters, d.horizon = model.features, model.imu_body, model.dt, model.iters, model.horizon
+    d.loss_kind, d.loss_mode, d.loss_body, d.beta, d.slop = model.loss_kind, model.loss_mode, model.loss_body, 0.2, 0.005
+    d.gravity[2] = -9.81
+    return d, keep
+
+
+@pytest.mark.parametrize("mutate,needle", [
+    (lambda d: setattr(d, "n_instances", 0), b"n_instances"),
+    (lambda d: setattr(d, "horizon", 0), b"horizon"),
+    (lambda d: setattr(d, "iters", 0), b"iters"),
+    (lambda d: setattr(d, "n_bodies", 40), b"n_bodies"),
+    (lambda d: setattr(d, "loss_body", 99), b"loss_body"),
+    (lambda d: setattr(d, "n_layers", 9), b"n_layers"),
+    (lambda d: setattr(d, "dt", -1.0), b"dt"),
+])
+def test_descriptor_validation_rejects_bad_input(mutate, needle):
+    lib = binding.load()
+    d, keep = _desc(workloads.quadruped(B=3, horizon=5))
+    mutate(d)
+    h = C.c_void_p()
+    st = lib.dp_create_world(C.byref(d), None, C.byref(h))
+    assert st == binding.DP_EINVAL
+    assert not h.value
+    assert needle in lib.dp_last_error()
+
+
+def test_descriptor_validation_bad_topology():
+    lib = binding.load()
+    m = workloads.quadruped(B=2, horizon=5)
+    m.joint_body = m.joint_body.copy()
+    m.joint_body[3] = [2, 2]
+    d, keep = _desc(m)
+    h = C.c_void_p()
+    assert lib.dp_create_world(C.byref(d), None, C.byref(h)) == binding.DP_EINVAL
+    m = workloads.quadruped(B=2, horizon=5)
+    m.mass = m.mass.copy()
+    m.mass[1, 3] = 0.0
+    d, keep = _desc(m)
+    assert lib.dp_create_world(C.byref(d), None, C.byref(h)) == binding.DP_EINVAL
+    assert b"mass" in lib.dp_last_error()
+
+
+def test_null_world_calls_fail_cleanly():
+    lib = binding.load()
+    assert lib.dp_rollout(None, None, None, None, None) == binding.DP_EINVAL
+    assert lib.dp_backward(None, None, None, None, None) == binding.DP_EINVAL
+    assert lib.dp_num_slots(None) == -1
+    lib.dp_free(None)
+
+
+def test_build_flags_target_sm103a():
+    assert "arch=compute_103a,code=sm_103a" in build.FLAGS

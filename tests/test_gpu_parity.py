@@ -1,0 +1,199 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on the same seeded
+inputs. States within 1e-4 relative (scale floor 1) over the compared horizon, constraint
+activation sets and slot indexing bit-exact away from near-ties (|gap| < 1e-5 m or rad),
+gradients within 1e-3 relative where the oracle's own finite differences agree."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_1611_01652_gb300 import workloads as WL  # noqa: E402
+from paper_1611_01652_gb300.binding import World  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+STATE_RTOL = 1e-4
+GRAD_RTOL = 1e-3
+TIE = 1e-5
+
+
+def gpu_rollout(m, horizon=None):
+    w = World(m, horizon=horizon)
+    T = w.horizon
+    traj = torch.zeros(T + 1, m.B, m.nb, 18, device="cuda")
+    active = torch.zeros(T, m.B, max(w.n_slots, 1), dtype=torch.uint8, device="cuda")
+    loss = torch.zeros(m.B, device="cuda")
+    W = torch.tensor(m.W, device="cuda") if m.W is not None and len(m.W) else None
+    w.rollout(W, loss, traj, active if w.n_slots else None)
+    w.sync()
+    return w, traj.cpu().double().numpy(), loss.cpu().double().numpy(), active.cpu().numpy()[:, :, :w.n_slots]
+
+
+def first_tie(gap):
+    """First step with a near-tie activation decision (or T)."""
+    t = np.flatnonzero((gap < TIE).any(axis=1))
+    return int(t[0]) if len(t) else gap.shape[0]
+
+
+def compare_rollout(m, horizon, instances, min_clean=0.5):
+    w, traj, loss, act = gpu_rollout(m, horizon)
+    clean = 0
+    for i in instances:
+        st, L, a_o, gap = O.rollout(m, i, horizon=horizon, log=True)
+        te = first_tie(gap) if gap.size else horizon
+        if te < horizon:
+            # exact masks up to the tie, states up to the tie
+            assert np.array_equal(act[:te, i], a_o[:te]), i
+            err = np.abs(traj[: te + 1, i] - st[: te + 1]) / np.maximum(1.0, np.abs(st[: te + 1]))
+            assert err.max() <= STATE_RTOL, (i, te, err.max())
+            continue
+        clean += 1
+        if a_o.size:
+            mism = np.argwhere(act[:, i] != a_o)
+            assert len(mism) == 0, (i, mism[:5])
+        err = np.abs(traj[:, i] - st) / np.maximum(1.0, np.abs(st))
+        assert err.max() <= STATE_RTOL, (i, err.max(), np.unravel_index(err.argmax(), err.shape))
+        assert abs(loss[i] - L) <= STATE_RTOL * max(1.0, abs(L)), (i, loss[i], L)
+    assert clean >= min_clean * len(instances)
+    return w
+
+
+def test_schedule_matches_oracle():
+    for m in (WL.quadruped(B=2, horizon=3), WL.two_spheres(B=2), WL.pendulum3(B=2, horizon=3), WL.ball(B=1)):
+        w = World(m, horizon=3)
+        g, o = w.schedule(), O.schedule(m)
+        for k in o:
+            assert np.array_equal(g[k], o[k]), (m.name, k)
+
+
+def test_ball_forward_matches_oracle():
+    m = WL.ball(B=48)
+    compare_rollout(m, 300, range(0, 48, 3))
+
+
+def test_two_spheres_forward_matches_oracle():
+    m = WL.two_spheres(B=8, e=0.3, mu=0.4)
+    compare_rollout(m, 60, range(8))
+
+
+def test_pendulum_forward_matches_oracle():
+    m = WL.pendulum3(B=40, horizon=1000)
+    compare_rollout(m, 1000, range(0, 40, 5))
+
+
+def test_quadruped_forward_matches_oracle_100_steps():
+    m = WL.quadruped(B=40, horizon=100)
+    compare_rollout(m, 100, range(0, 40, 4), min_clean=0.3)
+
+
+def test_quadruped_teacher_forced_steps():
+    """One GPU step from oracle states at several times: next state and active set."""
+    m = WL.quadruped(B=8, horizon=200)
+    w = World(m, horizon=200)
+    W = torch.tensor(m.W, device="cuda")
+    states = [O.rollout(m, i, horizon=200)[0] for i in range(m.B)]
+    for t in (0, 17, 60, 120, 199):
+        x = np.stack([s[t] for s in states]).astype(np.float32)
+        w.set_state(torch.tensor(x, device="cuda"), t)
+        act = torch.zeros(1, m.B, w.n_slots, dtype=torch.uint8, device="cuda")
+        w.step(1, W, act)
+        out = torch.zeros(m.B, m.nb, 18, device="cuda")
+        w.get_state(out)
+        w.sync()
+        out = out.cpu().double().numpy()
+        act = act.cpu().numpy()[0]
+        for i in range(m.B):
+            xn, a_o, gap, _ = O.step(m, i, x[i].astype(np.float64), t=t)
+            ok = gap >= TIE
+            assert np.array_equal(act[i][ok], a_o[ok]), (t, i)
+            if ok.all():
+                err = np.abs(out[i] - xn) / np.maximum(1.0, np.abs(xn))
+                assert err.max() <= STATE_RTOL, (t, i, err.max())
+
+
+def test_determinism_bitwise():
+    m = WL.quadruped(B=64, horizon=50)
+    _, t1, l1, a1 = gpu_rollout(m)
+    _, t2, l2, a2 = gpu_rollout(m)
+    assert np.array_equal(t1, t2) and np.array_equal(l1, l2) and np.array_equal(a1, a2)
+
+
+@pytest.mark.parametrize("B", [1, 5, 33])
+def test_ragged_batches(B):
+    """Batches that leave a partial warp: padded lanes must not disturb real instances."""
+    m = WL.quadruped(B=B, horizon=20)
+    compare_rollout(m, 20, range(B), min_clean=0.0)
+
+
+def test_single_step_horizon():
+    m = WL.ball(B=3, horizon=1)
+    compare_rollout(m, 1, range(3), min_clean=0.0)
+
+
+# ------------------------------------------------------------------------------ gradients
+def rel_err(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-12)
+
+
+def gpu_grads(m, horizon, ckpt_every=None):
+    w = World(m, horizon=horizon, ckpt_every=ckpt_every)
+    loss = torch.zeros(m.B, device="cuda")
+    W = torch.tensor(m.W, device="cuda") if m.W is not None and len(m.W) else None
+    w.rollout(W, loss)
+    dloss = torch.ones(m.B, device="cuda")
+    dW = torch.zeros(w.n_params, device="cuda") if w.n_params else None
+    ds = torch.zeros(m.B, m.nb, 18, device="cuda")
+    dp = {k: torch.zeros(getattr(m, k).shape, device="cuda") for k in
+          ("mass", "inertia", "anchor", "limit", "motor", "sph_off", "sph_rad", "sph_mu", "sph_e", "loss_point", "loss_target")}
+    w.backward(dloss, dW, ds, dp)
+    w.sync()
+    out = {k: v.cpu().double().numpy() for k, v in dp.items()}
+    out["state0"] = ds.cpu().double().numpy()
+    out["W"] = dW.cpu().double().numpy() if dW is not None else None
+    out["loss"] = loss.cpu().double().numpy()
+    return out
+
+
+def check_grads(m, horizon, keys, instances, ckpt_every=None, with_W=False):
+    g = gpu_grads(m, horizon, ckpt_every)
+    Wsum = None
+    for i in instances:
+        L, go = O.rollout_grad(m, i, horizon=horizon)
+        assert abs(g["loss"][i] - L) <= 1e-4 * max(1.0, abs(L))
+        for k in keys:
+            e = rel_err(g[k][i], go[k])
+            assert e <= GRAD_RTOL, (m.name, i, k, e, g[k][i].ravel()[:6], go[k].ravel()[:6])
+        if with_W:
+            Wsum = go["W"] if Wsum is None else Wsum + go["W"]
+    return g, Wsum
+
+
+def test_ball_gradients_through_contact():
+    m = WL.ball(B=4, horizon=60)
+    for i in range(m.B):
+        m.state0[i, 0, 2] = 0.6
+        m.state0[i, 0, 15:18] = [1.0, -2.0, 0.5]
+    check_grads(m, 60, ("state0", "sph_rad", "sph_mu", "mass", "inertia", "loss_target"), range(4))
+
+
+def test_pendulum_gradients():
+    m = WL.pendulum3(B=4, horizon=100)
+    check_grads(m, 100, ("state0", "anchor", "inertia", "mass", "loss_point"), range(4))
+
+
+def test_pendulum_gradients_with_checkpoint_segments():
+    m = WL.pendulum3(B=4, horizon=100)
+    check_grads(m, 100, ("state0", "anchor", "inertia", "mass"), range(4), ckpt_every=32)
+
+
+def test_two_spheres_gradients():
+    m = WL.two_spheres(B=4, e=0.3, mu=0.4)
+    check_grads(m, 60, ("state0", "sph_rad", "sph_off", "mass", "inertia", "sph_mu", "sph_e"), range(4))
+
+
+def test_quadruped_gradients_controller():
+    m = WL.quadruped(B=4, horizon=20)
+    g, Wsum = check_grads(m, 20, ("state0", "mass", "inertia", "anchor", "motor", "sph_off", "sph_rad"), range(4),
+                          with_W=True)
+    assert rel_err(g["W"], Wsum) <= GRAD_RTOL
