@@ -113,6 +113,8 @@ typedef struct {
   int32_t ckpt_every;             /* store a state every K steps for the backward pass;
                                      0 = choose K from free device memory */
   int32_t loss_kind, loss_mode, loss_body;
+  int32_t ctrl_fp32;              /* 0: bfloat16 storage points (default); 1: the controller keeps its
+                                     input, weights and hidden activations in fp32 (no rounding) */
 } dp_batch_desc;
 
 typedef struct dp_world dp_world; /* opaque; owned by the library */

@@ -116,7 +116,7 @@ def topo(m, keep, iters=None):
     t.dt, t.ground_z, t.beta, t.gamma, t.slop = m.dt, m.ground_z, m.beta, m.gamma, m.slop
     t.iters = m.iters if iters is None else iters
     t.loss_kind, t.loss_mode, t.loss_body = m.loss_kind, m.loss_mode, m.loss_body
-    t.exact_mlp = int(getattr(m, "exact_mlp", 0))
+    t.exact_mlp = int(getattr(m, "exact_mlp", 0) or getattr(m, "ctrl_fp32", 0))
     return t
 
 
@@ -156,8 +156,9 @@ def schedule(m):
     return {k: v[:n] for k, v in out.items()}
 
 
-def rollout(m, i, horizon=None, W=None, log=False, iters=None, overrides=None):
-    """Roll instance ``i`` forward. Returns (states [T+1, nb, 18], loss, active, gap)."""
+def rollout(m, i, horizon=None, W=None, log=False, iters=None, overrides=None, margins=False):
+    """Roll instance ``i`` forward. Returns (states [T+1, nb, 18], loss, active, gap); with
+    ``margins`` also the per-step bfloat16 tie margins [T]."""
     T = m.horizon if horizon is None else horizon
     keep = _Keep()
     t = topo(m, keep, iters)
@@ -167,18 +168,19 @@ def rollout(m, i, horizon=None, W=None, log=False, iters=None, overrides=None):
     loss = C.c_double(0.0)
     active = np.zeros((T, max(ns, 1)), np.int8) if log else None
     gap = np.zeros((T, max(ns, 1))) if log else None
+    marg = np.zeros(max(T, 1)) if margins else None
     r = lib().orc_rollout(C.byref(t), C.byref(s), weights(m, keep, W), T, _dp(states), C.byref(loss),
                           active.ctypes.data_as(C.POINTER(C.c_int8)) if log else None,
-                          _dp(gap) if log else None)
+                          _dp(gap) if log else None, _dp(marg) if margins else None)
     if r != 0:
         raise ValueError("oracle rejected the model")
-    if log:
-        return states, loss.value, active[:, :ns], gap[:, :ns]
-    return states, loss.value, None, None
+    out = (states, loss.value, active[:, :ns] if log else None, gap[:, :ns] if log else None)
+    return out + (marg[:T],) if margins else out
 
 
-def step(m, i, x, t=0, W=None, iters=None):
-    """One step from state ``x`` [nb, 18] at step index ``t``; returns (x_next, active, gap, lambda)."""
+def step(m, i, x, t=0, W=None, iters=None, margins=False):
+    """One step from state ``x`` [nb, 18] at step index ``t``; returns (x_next, active, gap, lambda)
+    and, with ``margins``, the step's bfloat16 tie margin."""
     keep = _Keep()
     tp = topo(m, keep, iters)
     s = inst(m, i, keep)
@@ -188,11 +190,13 @@ def step(m, i, x, t=0, W=None, iters=None):
     active = np.zeros(max(ns, 1), np.int8)
     gap = np.zeros(max(ns, 1))
     lam = np.zeros(max(ns, 1))
+    marg = np.zeros(1)
     r = lib().orc_step(C.byref(tp), C.byref(s), weights(m, keep, W), t, _dp(x), _dp(xn),
-                       active.ctypes.data_as(C.POINTER(C.c_int8)), _dp(gap), _dp(lam))
+                       active.ctypes.data_as(C.POINTER(C.c_int8)), _dp(gap), _dp(lam), _dp(marg))
     if r != 0:
         raise ValueError("oracle rejected the model")
-    return xn.reshape(m.nb, 18), active[:ns], gap[:ns], lam[:ns]
+    out = (xn.reshape(m.nb, 18), active[:ns], gap[:ns], lam[:ns])
+    return out + (float(marg[0]),) if margins else out
 
 
 def rollout_grad(m, i, horizon=None, W=None, iters=None, overrides=None):

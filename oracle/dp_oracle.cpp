@@ -128,7 +128,22 @@ double bf16(double x) {
   return std::ldexp(r, e - 8);
 }
 static thread_local bool g_exact_mlp = false;
-inline double round_bf16(double x) { return g_exact_mlp ? x : bf16(x); }
+// Smallest relative distance, over the roundings of one step, of a pre-rounding value to a
+// bfloat16 rounding midpoint (how close a quantisation decision came to flipping).
+static thread_local double g_bf16_margin = INFINITY;
+inline double bf16_tie_distance(double x) {
+  if (x == 0.0 || !std::isfinite(x)) return INFINITY;
+  int e;
+  double m = std::frexp(x, &e);
+  double s = std::ldexp(std::fabs(m), 8);  // [128, 256)
+  double frac = s - std::floor(s);
+  return std::fabs(frac - 0.5) / s;
+}
+inline double round_bf16(double x) {
+  if (g_exact_mlp) return x;
+  g_bf16_margin = std::min(g_bf16_margin, bf16_tie_distance(x));
+  return bf16(x);
+}
 inline CNT round_bf16(CNT x) { return CNT(g_exact_mlp ? x.v : bf16(x.v)); }
 inline AD round_bf16(AD x) { return g_exact_mlp ? x : mk(bf16(x.v), x.id, 1.0, -1, 0.0); }
 
@@ -346,7 +361,8 @@ int feature_count(const orc_topo& T, int n_motors) {
 struct StepLog {
   int8_t* active;
   double* gap;
-  double* lambda;  // final impulses per slot
+  double* lambda;       // final impulses per slot
+  double* bf16_margin;  // see g_bf16_margin
 };
 
 // The loss point q = p_b + R_b c of the body named by loss_body.
@@ -382,6 +398,7 @@ static void step(const orc_topo& T, const std::vector<Slot>& slots, const std::v
   const double h = T.dt;
   const int nb = T.nb, nj = T.nj;
   g_exact_mlp = T.exact_mlp != 0;
+  g_bf16_margin = INFINITY;
   std::vector<V3<S>> p(nb), v(nb), w(nb);
   std::vector<M3<S>> R(nb);
   for (int b = 0; b < nb; ++b) {
@@ -611,7 +628,7 @@ static void step(const orc_topo& T, const std::vector<Slot>& slots, const std::v
           r.angB = vneg(cross(rb, r.lin));
           r.friction = true;
           r.mu = sqrt(P.sph_mu[k] * P.sph_mu[l]);
-          gap = std::min(gap, std::fabs(val(n[2])));  // basis sign decision
+          if (r.active) gap = std::min(gap, std::fabs(val(n[2])));  // basis sign decision
         }
         break;
       }
@@ -659,6 +676,7 @@ static void step(const orc_topo& T, const std::vector<Slot>& slots, const std::v
   }
   if (log && log->lambda)
     for (int si = 0; si < ns_; ++si) log->lambda[si] = val(lam[si]);
+  if (log && log->bf16_margin) *log->bf16_margin = g_bf16_margin;
 
   // Semi-implicit Euler with the new velocities, then the Eq. 1 renormalisation.
   xn.resize(x.size());
@@ -749,7 +767,7 @@ int orc_schedule(const orc_topo* T, int32_t* kind, int32_t* idx, int32_t* sub, i
 
 // One step from a given state (used for teacher-forced comparisons).
 int orc_step(const orc_topo* T, const orc_inst* I, const double* W, int32_t t, const double* x, double* xn,
-             int8_t* active, double* gap, double* lambda) {
+             int8_t* active, double* gap, double* lambda, double* bf16_margin) {
   if (check_topo(T)) return -1;
   auto slots = make_slots(*T);
   std::vector<int> col, ord;
@@ -758,7 +776,7 @@ int orc_step(const orc_topo* T, const orc_inst* I, const double* W, int32_t t, c
   int np_ = param_count(T->n_layers, T->widths, T->skip);
   std::vector<double> Wv(W, W + np_);
   std::vector<double> xs(x, x + 18 * T->nb), xo;
-  StepLog lg{active, gap, lambda};
+  StepLog lg{active, gap, lambda, bf16_margin};
   step<double>(*T, slots, ord, P, Wv, t, xs, xo, 0.0, nullptr, (active && gap) ? &lg : nullptr);
   std::memcpy(xn, xo.data(), sizeof(double) * xo.size());
   return 0;
@@ -767,7 +785,7 @@ int orc_step(const orc_topo* T, const orc_inst* I, const double* W, int32_t t, c
 // Full rollout of `horizon` steps; writes all states [horizon+1][nb][18] (optional), the loss,
 // and per step the slot activity / decision distances [horizon][n_slots] (optional).
 int orc_rollout(const orc_topo* T, const orc_inst* I, const double* W, int32_t horizon, double* states,
-                double* loss, int8_t* active, double* gap) {
+                double* loss, int8_t* active, double* gap, double* bf16_margin) {
   if (check_topo(T) || horizon < 0) return -1;
   auto slots = make_slots(*T);
   std::vector<int> col, ord;
@@ -781,7 +799,8 @@ int orc_rollout(const orc_topo* T, const orc_inst* I, const double* W, int32_t h
   if (states) std::memcpy(states, x.data(), sizeof(double) * x.size());
   for (int t = 0; t < horizon; ++t) {
     double lt = 0.0;
-    StepLog lg{active ? active + (size_t)t * nsl : nullptr, gap ? gap + (size_t)t * nsl : nullptr, nullptr};
+    StepLog lg{active ? active + (size_t)t * nsl : nullptr, gap ? gap + (size_t)t * nsl : nullptr, nullptr,
+               bf16_margin ? bf16_margin + t : nullptr};
     step<double>(*T, slots, ord, P, Wv, t, x, xn, weight_of_state(*T, t + 1, horizon), &lt,
                  (active && gap) ? &lg : nullptr);
     L += lt;
@@ -805,7 +824,7 @@ int orc_rollout_grad(const orc_topo* T, const orc_inst* I, const double* W, int3
   const int nb = T->nb;
   const int np_ = param_count(T->n_layers, T->widths, T->skip);
   std::vector<double> states((size_t)(horizon + 1) * 18 * nb);
-  if (orc_rollout(T, I, W, horizon, states.data(), loss, nullptr, nullptr)) return -1;
+  if (orc_rollout(T, I, W, horizon, states.data(), loss, nullptr, nullptr, nullptr)) return -1;
 
   Tape tape;
   Tape* saved = g_tape;
@@ -875,7 +894,7 @@ int orc_flops(const orc_topo* T, const orc_inst* I, const double* W, int32_t hor
   const int nb = T->nb;
   const int np_ = param_count(T->n_layers, T->widths, T->skip);
   std::vector<double> states((size_t)(horizon + 1) * 18 * nb);
-  if (orc_rollout(T, I, W, horizon, states.data(), nullptr, nullptr, nullptr)) return -1;
+  if (orc_rollout(T, I, W, horizon, states.data(), nullptr, nullptr, nullptr, nullptr)) return -1;
   Inst<CNT> Pc = lift_inst<CNT>(*T, *I);
   std::vector<CNT> Wc(np_);
   for (int k = 0; k < np_; ++k) Wc[k] = CNT(W[k]);

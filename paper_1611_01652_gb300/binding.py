@@ -33,7 +33,7 @@ class BatchDesc(C.Structure):
                 ("gravity", C.c_float * 3), ("dt", C.c_float), ("ground_z", C.c_float), ("beta", C.c_float),
                 ("gamma", C.c_float), ("slop", C.c_float), ("iters", C.c_int32), ("horizon", C.c_int32),
                 ("ckpt_every", C.c_int32), ("loss_kind", C.c_int32), ("loss_mode", C.c_int32),
-                ("loss_body", C.c_int32)]
+                ("loss_body", C.c_int32), ("ctrl_fp32", C.c_int32)]
 
 
 class ParamGrads(C.Structure):
@@ -151,6 +151,7 @@ class World:
         d.horizon = model.horizon if horizon is None else horizon
         d.ckpt_every = model.ckpt_every if ckpt_every is None else ckpt_every
         d.loss_kind, d.loss_mode, d.loss_body = model.loss_kind, model.loss_mode, model.loss_body
+        d.ctrl_fp32 = int(getattr(model, "ctrl_fp32", 0))
         self.horizon = d.horizon
         h = C.c_void_p()
         _check(lib.dp_create_world(C.byref(d), C.c_void_p(self.stream.cuda_stream), C.byref(h)))

@@ -255,6 +255,7 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
   T.loss_body = d->loss_body;
   T.n_layers = d->n_layers;
   T.skip = d->n_layers > 0 ? d->skip : 0;
+  T.ctrl_round = d->ctrl_fp32 ? 0 : 1;
   for (int k = 0; k < 3; ++k) T.gravity[k] = d->gravity[k];
   T.dt = d->dt;
   T.ground_z = d->ground_z;

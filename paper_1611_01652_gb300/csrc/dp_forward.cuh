@@ -64,31 +64,34 @@ __device__ __forceinline__ float loss_weight(const DevTopo& T, int t_next) {
   return t_next == T.horizon ? 1.f : 0.f;
 }
 
-// Controller input vector s(x^t), rounded to bfloat16, into act0 (padded with zeros).
+__device__ __forceinline__ float qz(const DevTopo& T, float x) { return T.ctrl_round ? bf16r(x) : x; }
+
+// Controller input vector s(x^t), rounded to bfloat16 (unless the fp32 controller mode is
+// selected), into act0 (padded with zeros).
 template <class AV>
 __device__ void controller_features(const DevTopo& T, const Lane& L, const SL& X, int t, const AV& act0) {
   const SL& S = L.S;
   int k = 0;
   if (T.features & 1)
-    for (int m = 0; m < T.n_motors; ++m) act0[k++] = bf16r(S[T.sm_th + T.motor_joint[m]]);
+    for (int m = 0; m < T.n_motors; ++m) act0[k++] = qz(T, S[T.sm_th + T.motor_joint[m]]);
   if (T.features & 2)
-    for (int m = 0; m < T.n_motors; ++m) act0[k++] = bf16r(S[T.sm_thd + T.motor_joint[m]]);
+    for (int m = 0; m < T.n_motors; ++m) act0[k++] = qz(T, S[T.sm_thd + T.motor_joint[m]]);
   if (T.features & 4) {
     double ph = 2.0 * 3.14159265358979323846 * (double)T.clock_hz * ((double)t * (double)T.dt);
-    act0[k++] = bf16r((float)sin(ph));
-    act0[k++] = bf16r((float)cos(ph));
+    act0[k++] = qz(T, (float)sin(ph));
+    act0[k++] = qz(T, (float)cos(ph));
   }
   if (T.features & 8) {
     int b = T.imu_body;
     M3 R = loadR(X, 18 * b);
     float3 g = mtv(R, f3(0.f, 0.f, -1.f));
     float3 wl = mtv(R, X.v3(18 * b + 15));
-    act0[k++] = bf16r(g.x); act0[k++] = bf16r(g.y); act0[k++] = bf16r(g.z);
-    act0[k++] = bf16r(wl.x); act0[k++] = bf16r(wl.y); act0[k++] = bf16r(wl.z);
+    act0[k++] = qz(T, g.x); act0[k++] = qz(T, g.y); act0[k++] = qz(T, g.z);
+    act0[k++] = qz(T, wl.x); act0[k++] = qz(T, wl.y); act0[k++] = qz(T, wl.z);
   }
   if (T.features & 16) {
     float3 d = loss_point(T, L, X) - L.P.v3(T.o_loss_target);
-    act0[k++] = bf16r(d.x); act0[k++] = bf16r(d.y); act0[k++] = bf16r(d.z);
+    act0[k++] = qz(T, d.x); act0[k++] = qz(T, d.y); act0[k++] = qz(T, d.z);
   }
   for (; k < T.widths[0]; ++k) act0[k] = 0.f;
 }
@@ -97,7 +100,7 @@ __device__ void controller_features(const DevTopo& T, const Lane& L, const SL& X
 // [in][out_pad] copy (8 outputs per pass, broadcast float4 loads).
 template <class AVI, class AVO>
 __device__ void dense_fwd(const float* __restrict__ Wt, const float* __restrict__ bias, int ni, int no, const AVI& in,
-                          const AVO& out, bool hidden, bool accumulate) {
+                          const AVO& out, bool hidden, bool accumulate, bool round) {
   const int nop = (no + 7) & ~7;
   for (int o0 = 0; o0 < no; o0 += 8) {
     float acc[8];
@@ -117,7 +120,7 @@ __device__ void dense_fwd(const float* __restrict__ Wt, const float* __restrict_
     for (int k = 0; k < 8; ++k) {
       if (o0 + k < no) {
         float z = accumulate ? out[o0 + k] + acc[k] : acc[k];
-        out[o0 + k] = hidden ? bf16r(fmaxf(z, 0.f)) : z;
+        out[o0 + k] = hidden ? (round ? bf16r(fmaxf(z, 0.f)) : fmaxf(z, 0.f)) : z;
       }
     }
   }
@@ -130,11 +133,11 @@ __device__ void controller_forward(const DevTopo& T, const DevPtrs& D, const AV*
     const int ni = T.widths[l], no = T.widths[l + 1];
     const float* Wt = D.Wt + T.w_off[l];
     const float* b = D.bias + T.w_off[l];
-    dense_fwd(Wt, b, ni, no, act[l], act[l + 1], l + 1 < T.n_layers, false);
+    dense_fwd(Wt, b, ni, no, act[l], act[l + 1], l + 1 < T.n_layers, false, T.ctrl_round != 0);
   }
   if (T.skip) {
     const int l = T.n_layers;
-    dense_fwd(D.Wt + T.w_off[l], D.bias + T.w_off[l], T.widths[0], T.widths[l], act[0], act[l], false, true);
+    dense_fwd(D.Wt + T.w_off[l], D.bias + T.w_off[l], T.widths[0], T.widths[l], act[0], act[l], false, true, false);
   }
 }
 

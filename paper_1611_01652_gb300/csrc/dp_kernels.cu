@@ -22,7 +22,7 @@ __global__ void k_prep_weights(const __grid_constant__ DevTopo T, const float* _
     const int nop = (no + 7) & ~7, nip = (ni + 7) & ~7;
     if (p < off + ni * no) {
       int q = p - off, o = q / ni, i = q % ni;
-      float w = bf16r(W[p]);
+      float w = T.ctrl_round ? bf16r(W[p]) : W[p];
       Wt[T.w_off[l] + i * nop + o] = w;
       Wn[T.w_off[l] + o * nip + i] = w;
       return;

