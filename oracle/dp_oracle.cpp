@@ -145,7 +145,11 @@ inline double round_bf16(double x) {
   return bf16(x);
 }
 inline CNT round_bf16(CNT x) { return CNT(g_exact_mlp ? x.v : bf16(x.v)); }
+inline CNT round_bf16_w(CNT x) { return round_bf16(x); }
 inline AD round_bf16(AD x) { return g_exact_mlp ? x : mk(bf16(x.v), x.id, 1.0, -1, 0.0); }
+// Weights are exact float32 inputs on every side, so their rounding is not a tie risk.
+inline double round_bf16_w(double x) { return g_exact_mlp ? x : bf16(x); }
+inline AD round_bf16_w(AD x) { return round_bf16(x); }
 
 // Branch helpers: the branch is chosen on the value; ties go to the stated side.
 template <class S> inline S clamp_sel(S x, S lo, S hi, int* branch) {
@@ -460,7 +464,7 @@ static void step(const orc_topo& T, const std::vector<Slot>& slots, const std::v
       std::vector<S> z(no);
       for (int o = 0; o < no; ++o) {
         S acc = W[off + (size_t)ni * no + o];  // bias (kept in fp32)
-        for (int i = 0; i < ni; ++i) acc += round_bf16(W[off + (size_t)o * ni + i]) * a[i];
+        for (int i = 0; i < ni; ++i) acc += round_bf16_w(W[off + (size_t)o * ni + i]) * a[i];
         z[o] = acc;
       }
       off += (size_t)ni * no + no;
@@ -469,7 +473,7 @@ static void step(const orc_topo& T, const std::vector<Slot>& slots, const std::v
       } else if (T.skip) {
         for (int o = 0; o < no; ++o) {
           S acc = W[off + (size_t)T.widths[0] * no + o];  // skip-layer bias
-          for (int i = 0; i < T.widths[0]; ++i) acc += round_bf16(W[off + (size_t)o * T.widths[0] + i]) * s[i];
+          for (int i = 0; i < T.widths[0]; ++i) acc += round_bf16_w(W[off + (size_t)o * T.widths[0] + i]) * s[i];
           z[o] += acc;
         }
       }
