@@ -9,8 +9,9 @@
 // Row-adjoint accumulators kept in shared memory per slot (the solver's inner quantities).
 enum { RC_LIN = 0, RC_ANGA = 3, RC_ANGB = 6, RC_MEFF = 9, RC_BIAS = 10, RC_BND = 11, RC_N = 12 };
 
-struct BLane {
-  Lane L;
+template <class RV>
+struct BLaneT {
+  LaneT<RV> L;
   GC X0;        // x_t (global, [field][Bp])
   GL G;         // parameter gradients [field][Bp]
   GC vminus;    // velocities after the external impulses [nb*6][Bp]
@@ -33,7 +34,8 @@ __device__ __forceinline__ float3 body_pg(const GC& X, int b) { return b >= 0 ? 
 
 // ---------------------------------------------------------------- loss (Eq. L) reverse
 // Adds wgt * dl(x)/dx at state X (on-chip) into XB, and the loss point / target gradients.
-__device__ void loss_reverse(const DevTopo& T, const BLane& B, const SL& X, const SL& XB, float wgt) {
+template <class RV>
+__device__ void loss_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& X, const SL& XB, float wgt) {
   if (wgt == 0.f) return;
   const int b = T.loss_body;
   M3 R = loadR(X, 18 * b);
@@ -55,7 +57,8 @@ __device__ void loss_reverse(const DevTopo& T, const BLane& B, const SL& X, cons
 // ---------------------------------------------------------------- integrate + Eq. 1 reverse
 // XB holds the adjoint of x_{t+1}; on return its p/R fields hold the adjoint of x_t's p/R,
 // its v/w fields are zero, and VB holds the adjoint of the solver's output velocities.
-__device__ void integrate_reverse(const DevTopo& T, const BLane& B, const SL& X, const SL& XB, const SL& VB) {
+template <class RV>
+__device__ void integrate_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& X, const SL& XB, const SL& VB) {
   const float h = T.dt;
   for (int b = 0; b < T.nb; ++b) {
     M3 R = loadRg(B.X0, 18 * b);
@@ -95,9 +98,10 @@ __device__ void integrate_reverse(const DevTopo& T, const BLane& B, const SL& X,
 // ---------------------------------------------------------------- PGS reverse
 // Replays every sweep backwards. Working velocities are reset to the stored post-sweep values at
 // each sweep boundary and un-applied row by row. S[sm_lam] holds the impulse adjoints.
-__device__ void pgs_reverse(const DevTopo& T, const DevPtrs& D, const BLane& B, const SL& X, const SL& VB,
+template <class RV>
+__device__ void pgs_reverse(const DevTopo& T, const DevPtrs& D, const BLaneT<RV>& B, const SL& X, const SL& VB,
                             const SL& RC) {
-  const Lane& L = B.L;
+  const LaneT<RV>& L = B.L;
   const SL& S = L.S;
   const int Bp = T.Bp;
   for (int s = 0; s < T.nslots; ++s) S[T.sm_lam + s] = 0.f;
@@ -110,13 +114,13 @@ __device__ void pgs_reverse(const DevTopo& T, const DevPtrs& D, const BLane& B, 
     }
     for (int oi = T.nslots - 1; oi >= 0; --oi) {
       const int s = T.order[oi];
-      const int base = s * RF_N;
-      const float meff = L.rows[base + RF_MEFF];
+      const RV R = L.rows.at(s * RF_N);
+      const float meff = R[RF_MEFF];
       if (!__any_sync(FULLMASK, meff != 0.f)) continue;
       const int kind = T.skind[s], a = T.sa[s], b = T.sb[s];
-      const float3 lin = L.rows.v3(base + RF_LIN);
-      const float3 angA = L.rows.v3(base + RF_ANGA), angB = L.rows.v3(base + RF_ANGB);
-      const float bias = L.rows[base + RF_BIAS];
+      const float3 lin = R.v3(RF_LIN);
+      const float3 angA = R.v3(RF_ANGA), angB = R.v3(RF_ANGB);
+      const float bias = R[RF_BIAS];
       const size_t o = ((size_t)it * T.nslots + s) * Bp + L.i;
       const float la = D.lam_hist[o];
       const float lb = it > 0 ? D.lam_hist[o - (size_t)T.nslots * Bp] : 0.f;
@@ -128,7 +132,7 @@ __device__ void pgs_reverse(const DevTopo& T, const DevPtrs& D, const BLane& B, 
       float dbar = 0.f;
       if (a >= 0) {
         ima = S[T.sm_invm + a];
-        IA = L.rows.v3(base + RF_IA);
+        IA = R.v3(RF_IA);
         va = X.v3(18 * a + 12) - (dl * ima) * lin;
         wa = X.v3(18 * a + 15) - dl * IA;
         X.s3(18 * a + 12, va);
@@ -139,7 +143,7 @@ __device__ void pgs_reverse(const DevTopo& T, const DevPtrs& D, const BLane& B, 
       }
       if (b >= 0) {
         imb = S[T.sm_invm + b];
-        IB = L.rows.v3(base + RF_IB);
+        IB = R.v3(RF_IB);
         vb = X.v3(18 * b + 12) + (dl * imb) * lin;
         wb = X.v3(18 * b + 15) - dl * IB;
         X.s3(18 * b + 12, vb);
@@ -184,7 +188,7 @@ __device__ void pgs_reverse(const DevTopo& T, const DevPtrs& D, const BLane& B, 
         // bound = +-mu * lambda_n (current value of the contact's normal impulse)
         const int ns_ = T.snormal[s];
         const float lnrm = D.lam_hist[((size_t)it * T.nslots + ns_) * Bp + L.i];
-        const float mu = L.rows[base + RF_HI];
+        const float mu = R[RF_BND];
         const float sg = br == 2 ? 1.f : -1.f;
         RC[rc + RC_BND] += sg * lnrm * lbar_a;
         S[T.sm_lam + ns_] += sg * mu * lbar_a;
@@ -225,20 +229,21 @@ __device__ __forceinline__ void addR_outer(const SL& XB, int b, float3 g, float3
 
 // Pushes the row adjoints (and the effective-mass adjoint) back to positions, rotations, the
 // solver's input velocities (restitution), hinge axes/angles, servo targets and parameters.
-__device__ void rows_reverse(const DevTopo& T, const BLane& B, const SL& XB, const SL& VB, const SL& RC) {
-  const Lane& L = B.L;
+template <class RV>
+__device__ void rows_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& XB, const SL& VB, const SL& RC) {
+  const LaneT<RV>& L = B.L;
   const SL& S = L.S;
   const float h = T.dt;
   const float bh = T.beta / h;
   const float3 ez = f3(0.f, 0.f, 1.f);
   for (int s = 0; s < T.nslots; ++s) {
-    const int base = s * RF_N;
-    const float meff = L.rows[base + RF_MEFF];
+    const RV R = L.rows.at(s * RF_N);
+    const float meff = R[RF_MEFF];
     if (meff == 0.f) continue;  // inactive on this lane: constant row
     const int kind = T.skind[s], idx = T.sidx[s], sub = T.ssub[s], a = T.sa[s], b = T.sb[s];
     const int rc = s * RC_N;
-    const float3 lin = L.rows.v3(base + RF_LIN);
-    const float3 angA = L.rows.v3(base + RF_ANGA), angB = L.rows.v3(base + RF_ANGB);
+    const float3 lin = R.v3(RF_LIN);
+    const float3 angA = R.v3(RF_ANGA), angB = R.v3(RF_ANGB);
     float3 linb = RC.v3(rc + RC_LIN), angAb = RC.v3(rc + RC_ANGA), angBb = RC.v3(rc + RC_ANGB);
     const float biasb = RC[rc + RC_BIAS];
     // effective mass 1/(K + gamma)
@@ -246,7 +251,7 @@ __device__ void rows_reverse(const DevTopo& T, const BLane& B, const SL& XB, con
     if (a >= 0) {
       const float ima = S[T.sm_invm + a];
       linb += (2.f * Kb * ima) * lin;
-      angAb += (2.f * Kb) * L.rows.v3(base + RF_IA);
+      angAb += (2.f * Kb) * R.v3(RF_IA);
       const int ib9 = T.sm_iinvb + 9 * a;
       S[ib9 + 0] += Kb * angA.x * angA.x; S[ib9 + 1] += Kb * angA.x * angA.y; S[ib9 + 2] += Kb * angA.x * angA.z;
       S[ib9 + 3] += Kb * angA.y * angA.x; S[ib9 + 4] += Kb * angA.y * angA.y; S[ib9 + 5] += Kb * angA.y * angA.z;
@@ -256,7 +261,7 @@ __device__ void rows_reverse(const DevTopo& T, const BLane& B, const SL& XB, con
     if (b >= 0) {
       const float imb = S[T.sm_invm + b];
       linb += (2.f * Kb * imb) * lin;
-      angBb += (2.f * Kb) * L.rows.v3(base + RF_IB);
+      angBb += (2.f * Kb) * R.v3(RF_IB);
       const int ib9 = T.sm_iinvb + 9 * b;
       S[ib9 + 0] += Kb * angB.x * angB.x; S[ib9 + 1] += Kb * angB.x * angB.y; S[ib9 + 2] += Kb * angB.x * angB.z;
       S[ib9 + 3] += Kb * angB.y * angB.x; S[ib9 + 4] += Kb * angB.y * angB.y; S[ib9 + 5] += Kb * angB.y * angB.z;
@@ -448,7 +453,8 @@ __device__ void rows_reverse(const DevTopo& T, const BLane& B, const SL& XB, con
 // VB holds the adjoint of the velocities after gravity/gyroscopic impulses; adds into XB
 // (x_t's v, w, R) and the mass/inertia gradients. IINVB/INVMB hold the world inverse-inertia
 // and inverse-mass adjoints gathered from the solver and the rows.
-__device__ void external_reverse(const DevTopo& T, const BLane& B, const SL& XB, const SL& VB) {
+template <class RV>
+__device__ void external_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& XB, const SL& VB) {
   const SL& S = B.L.S;
   const float h = T.dt;
   for (int b = 0; b < T.nb; ++b) {
@@ -516,8 +522,8 @@ __device__ void external_reverse(const DevTopo& T, const BLane& B, const SL& XB,
 }
 
 // ---------------------------------------------------------------- servo reverse
-template <class AV>
-__device__ void servo_reverse(const DevTopo& T, const BLane& B, const AV& u, const AV& ub) {
+template <class RV, class AV>
+__device__ void servo_reverse(const DevTopo& T, const BLaneT<RV>& B, const AV& u, const AV& ub) {
   const SL& S = B.L.S;
   const int nout = T.n_layers > 0 ? T.widths[T.n_layers] : 0;
   for (int o = 0; o < nout; ++o) ub[o] = 0.f;
@@ -582,8 +588,8 @@ __device__ void controller_reverse(const DevTopo& T, const DevPtrs& D, const AV*
 }
 
 // Features reverse: sbar -> hinge angle/rate adjoints, IMU body state, loss point/target.
-template <class AV>
-__device__ void features_reverse(const DevTopo& T, const BLane& B, const SL& XB, const AV& sbar) {
+template <class RV, class AV>
+__device__ void features_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& XB, const AV& sbar) {
   const SL& S = B.L.S;
   int k = 0;
   if (T.features & 1)
@@ -617,7 +623,8 @@ __device__ void features_reverse(const DevTopo& T, const BLane& B, const SL& XB,
 }
 
 // Hinge kinematics reverse (x_t): axis, angle and rate adjoints to R and w.
-__device__ void hinge_reverse(const DevTopo& T, const BLane& B, const SL& XB) {
+template <class RV>
+__device__ void hinge_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& XB) {
   const SL& S = B.L.S;
   for (int j = 0; j < T.nj; ++j) {
     int a = T.ja[j], b = T.jb[j];

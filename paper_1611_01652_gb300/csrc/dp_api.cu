@@ -175,7 +175,7 @@ int feature_count(const dp_batch_desc* d, int n_motors) {
 
 // Shared-memory plan (units of 32 floats per warp). Forward kernel: controller activations on
 // chip; backward kernel: row-adjoint accumulators on chip, activations in the global dump.
-void plan_smem(DevTopo& T, bool backward) {
+void plan_smem(DevTopo& T, bool backward, int smem_floats_max) {
   int o = 0;
   auto take = [&](int n) { int r = o; o += std::max(n, 1); return r; };
   T.sm_x = take(18 * T.nb);
@@ -188,12 +188,24 @@ void plan_smem(DevTopo& T, bool backward) {
   T.sm_wbr = take(T.nj);
   T.sm_lam = take(T.nslots);
   T.sm_x0 = T.sm_u = 0;
+  T.sm_rows = -1;
   if (!backward) {
+    // controller activations and constraint rows share one region: the rows are assembled after
+    // the servo targets have consumed the controller output
     for (int l = 0; l <= DPK_MAXL; ++l) T.sm_act[l] = 0;
+    const int region = o;
+    int acts = 0;
     if (T.n_layers > 0)
-      for (int l = 0; l <= T.n_layers; ++l) T.sm_act[l] = take(T.widths[l]);
+      for (int l = 0; l <= T.n_layers; ++l) { T.sm_act[l] = region + acts; acts += T.widths[l]; }
     else
-      T.sm_act[0] = take(1);
+      acts = 1;
+    const int rows = T.nslots * RF_N;
+    if ((region + std::max(acts, rows)) * 32 <= smem_floats_max) {
+      T.sm_rows = region;
+      o = region + std::max(acts, rows);
+    } else {
+      o = region + acts;
+    }
     T.sm_xb = T.sm_vb = T.sm_thb = T.sm_thdb = T.sm_uab = T.sm_wstb = T.sm_iinvb = T.sm_invmb = T.sm_rc = T.sm_sbar = 0;
   } else {
     for (int l = 0; l <= DPK_MAXL; ++l) T.sm_act[l] = 0;
@@ -351,11 +363,11 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
   w->w_total = wtot;
   w->Tf = T;
   w->Tb = T;
-  plan_smem(w->Tf, false);
-  plan_smem(w->Tb, true);
   int dev = 0, smem_max = 0;
   CU(cudaGetDevice(&dev));
   CU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  plan_smem(w->Tf, false, smem_max / (int)sizeof(float));
+  plan_smem(w->Tb, true, smem_max / (int)sizeof(float));
   size_t need = (size_t)std::max(w->Tf.sm_total, w->Tb.sm_total) * 32 * sizeof(float);
   if (need > (size_t)smem_max) {
     dp_status s = fail(DP_EINVAL, "robot too large: needs " + std::to_string(need) + " bytes of shared memory per warp, the device offers " +

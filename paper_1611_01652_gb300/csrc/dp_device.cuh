@@ -29,9 +29,9 @@ enum {
   RF_IB = 12,    // 3: I_b^-1 J_wb
   RF_MEFF = 15,  // 1: 1/(J M^-1 J^T + gamma); 0 for inactive rows (a no-op)
   RF_BIAS = 16,  // 1
-  RF_LO = 17,    // 1: lower bound (friction: unused)
-  RF_HI = 18,    // 1: upper bound (friction: mu)
-  RF_N = 19
+  RF_BND = 17,   // 1: servo impulse bound tau_max*h (motor rows), mu (friction rows); the other
+                 //    kinds have fixed bounds: joints (-inf, inf), limits and normals [0, inf)
+  RF_N = 18
 };
 
 struct DevTopo {
@@ -55,7 +55,7 @@ struct DevTopo {
   int16_t order[DPK_MAXSLOT];
   // shared-memory layout per warp, in units of 32 floats (one float per lane)
   int sm_x0, sm_x, sm_xb, sm_vb, sm_iinv, sm_invm, sm_th, sm_thd, sm_ua, sm_wst, sm_wbr, sm_lam, sm_u;
-  int sm_thb, sm_thdb, sm_uab, sm_wstb, sm_iinvb, sm_invmb, sm_rc, sm_sbar, sm_act[DPK_MAXL + 1], sm_total;
+  int sm_thb, sm_thdb, sm_uab, sm_wstb, sm_iinvb, sm_invmb, sm_rc, sm_sbar, sm_act[DPK_MAXL + 1], sm_rows, sm_total;
   // activation/delta dump offsets (rows of [feature][T*Bp]); act l = input of layer l
   int dump_act[DPK_MAXL + 1], dump_del[DPK_MAXL + 1], dump_rows;
 };
@@ -177,18 +177,21 @@ __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__floa
 // Lane views: shared memory [field][32], global memory [field][Bp].
 struct SL {
   float* p;
+  __device__ __forceinline__ SL at(int f) const { return SL{p + f * 32}; }
   __device__ __forceinline__ float& operator[](int f) const { return p[f * 32]; }
   __device__ __forceinline__ float3 v3(int f) const { return f3(p[f * 32], p[(f + 1) * 32], p[(f + 2) * 32]); }
   __device__ __forceinline__ void s3(int f, float3 v) const { p[f * 32] = v.x; p[(f + 1) * 32] = v.y; p[(f + 2) * 32] = v.z; }
   __device__ __forceinline__ void a3(int f, float3 v) const { p[f * 32] += v.x; p[(f + 1) * 32] += v.y; p[(f + 2) * 32] += v.z; }
 };
+// Global view with a run-time stride (f * s stays below 2^31 for every buffer indexed this way).
 struct GL {
   float* p;
   int s;
-  __device__ __forceinline__ float& operator[](int f) const { return p[(size_t)f * s]; }
-  __device__ __forceinline__ float3 v3(int f) const { return f3(p[(size_t)f * s], p[(size_t)(f + 1) * s], p[(size_t)(f + 2) * s]); }
-  __device__ __forceinline__ void s3(int f, float3 v) const { p[(size_t)f * s] = v.x; p[(size_t)(f + 1) * s] = v.y; p[(size_t)(f + 2) * s] = v.z; }
-  __device__ __forceinline__ void a3(int f, float3 v) const { p[(size_t)f * s] += v.x; p[(size_t)(f + 1) * s] += v.y; p[(size_t)(f + 2) * s] += v.z; }
+  __device__ __forceinline__ float& operator[](int f) const { return p[f * s]; }
+  __device__ __forceinline__ float3 v3(int f) const { return f3(p[f * s], p[(f + 1) * s], p[(f + 2) * s]); }
+  __device__ __forceinline__ void s3(int f, float3 v) const { p[f * s] = v.x; p[(f + 1) * s] = v.y; p[(f + 2) * s] = v.z; }
+  __device__ __forceinline__ void a3(int f, float3 v) const { p[f * s] += v.x; p[(f + 1) * s] += v.y; p[(f + 2) * s] += v.z; }
+  __device__ __forceinline__ GL at(int f) const { return GL{p + f * s, s}; }
 };
 // Wide-stride global view (controller activation/delta columns of the [row][T*Bp] dump).
 struct GW {
@@ -199,7 +202,7 @@ struct GW {
 struct GC {
   const float* p;
   int s;
-  __device__ __forceinline__ float operator[](int f) const { return __ldg(p + (size_t)f * s); }
+  __device__ __forceinline__ float operator[](int f) const { return __ldg(p + f * s); }
   __device__ __forceinline__ float3 v3(int f) const { return f3((*this)[f], (*this)[f + 1], (*this)[f + 2]); }
 };
 

@@ -9,11 +9,13 @@
 
 #define FULLMASK 0xffffffffu
 
-// Views of one lane's data.
-struct Lane {
+// Views of one lane's data. RV is the constraint-row view: shared memory (SL) when the rows of
+// 32 instances fit next to the rest of the warp's working set, else global memory (GL).
+template <class RV>
+struct LaneT {
   SL S;        // this warp's shared-memory block, offset to the lane
   GC P;        // parameters [field][Bp]
-  GL rows;     // constraint rows, slot s at rows[s * RF_N + f]
+  RV rows;     // constraint rows, slot s at rows[s * RF_N + f]
   int i;       // instance index
 };
 
@@ -23,7 +25,8 @@ __device__ __forceinline__ float3 body_p(const SL& X, int b) { return b >= 0 ? X
 __device__ __forceinline__ M3 body_R(const SL& X, int b) { return b >= 0 ? loadR(X, 18 * b) : eye3(); }
 
 // Hinge axis (world), angle about it between the two reference vectors, and its rate.
-__device__ void hinge_kinematics(const DevTopo& T, const Lane& L, const SL& X) {
+template <class RV>
+__device__ void hinge_kinematics(const DevTopo& T, const LaneT<RV>& L, const SL& X) {
   const SL& S = L.S;
   for (int j = 0; j < T.nj; ++j) {
     int a = T.ja[j], b = T.jb[j];
@@ -45,11 +48,13 @@ __device__ void hinge_kinematics(const DevTopo& T, const Lane& L, const SL& X) {
 }
 
 // Loss point q = p_b + R_b c.
-__device__ __forceinline__ float3 loss_point(const DevTopo& T, const Lane& L, const SL& X) {
+template <class RV>
+__device__ __forceinline__ float3 loss_point(const DevTopo& T, const LaneT<RV>& L, const SL& X) {
   int b = T.loss_body;
   return X.v3(18 * b) + mv(loadR(X, 18 * b), L.P.v3(T.o_loss_point));
 }
-__device__ __forceinline__ float loss_value(const DevTopo& T, const Lane& L, const SL& X) {
+template <class RV>
+__device__ __forceinline__ float loss_value(const DevTopo& T, const LaneT<RV>& L, const SL& X) {
   float3 q = loss_point(T, L, X);
   float3 y = L.P.v3(T.o_loss_target);
   float3 d = q - y;
@@ -68,8 +73,8 @@ __device__ __forceinline__ float qz(const DevTopo& T, float x) { return T.ctrl_r
 
 // Controller input vector s(x^t), rounded to bfloat16 (unless the fp32 controller mode is
 // selected), into act0 (padded with zeros).
-template <class AV>
-__device__ void controller_features(const DevTopo& T, const Lane& L, const SL& X, int t, const AV& act0) {
+template <class RV, class AV>
+__device__ void controller_features(const DevTopo& T, const LaneT<RV>& L, const SL& X, int t, const AV& act0) {
   const SL& S = L.S;
   int k = 0;
   if (T.features & 1)
@@ -142,8 +147,8 @@ __device__ void controller_forward(const DevTopo& T, const DevPtrs& D, const AV*
 }
 
 // Servo targets w* = clamp(k (u - theta), -vmax, vmax).
-template <class AV>
-__device__ void servo_targets(const DevTopo& T, const Lane& L, const AV& u) {
+template <class RV, class AV>
+__device__ void servo_targets(const DevTopo& T, const LaneT<RV>& L, const AV& u) {
   const SL& S = L.S;
   for (int m = 0; m < T.n_motors; ++m) {
     int j = T.motor_joint[m];
@@ -157,7 +162,8 @@ __device__ void servo_targets(const DevTopo& T, const Lane& L, const AV& u) {
 }
 
 // Gravity and the explicit gyroscopic term; world inverse inertia and inverse mass.
-__device__ void external_impulses(const DevTopo& T, const Lane& L, const SL& X) {
+template <class RV>
+__device__ void external_impulses(const DevTopo& T, const LaneT<RV>& L, const SL& X) {
   const SL& S = L.S;
   const float h = T.dt;
   const float3 g = f3(T.gravity[0], T.gravity[1], T.gravity[2]);
@@ -190,7 +196,8 @@ struct RowGeo {
 };
 
 // Assemble every constraint slot of this instance into rows (slot order).
-__device__ void assemble_rows(const DevTopo& T, const Lane& L, const SL& X, uint8_t* active_out) {
+template <class RV>
+__device__ void assemble_rows(const DevTopo& T, const LaneT<RV>& L, const SL& X, uint8_t* active_out) {
   const SL& S = L.S;
   const float h = T.dt;
   const float bh = T.beta / h;
@@ -199,7 +206,7 @@ __device__ void assemble_rows(const DevTopo& T, const Lane& L, const SL& X, uint
   for (int s = 0; s < T.nslots; ++s) {
     const int kind = T.skind[s], idx = T.sidx[s], sub = T.ssub[s], a = T.sa[s], b = T.sb[s];
     float3 lin = f3(0.f, 0.f, 0.f), angA = lin, angB = lin;
-    float bias = 0.f, lo = -INF, hi = INF;
+    float bias = 0.f, bnd = 0.f;
     bool active = true;
     switch (kind) {
       case RK_JLIN: {
@@ -235,7 +242,6 @@ __device__ void assemble_rows(const DevTopo& T, const Lane& L, const SL& X, uint
         } else {
           active = false;
         }
-        lo = 0.f;
         break;
       }
       case RK_MOTOR: {
@@ -243,8 +249,7 @@ __device__ void assemble_rows(const DevTopo& T, const Lane& L, const SL& X, uint
         angA = a >= 0 ? -ua : f3(0.f, 0.f, 0.f);
         angB = ua;
         bias = -S[T.sm_wst + idx];
-        float tm = L.P[T.o_motor + 3 * idx + 1] * h;
-        lo = -tm; hi = tm;
+        bnd = L.P[T.o_motor + 3 * idx + 1] * h;
         break;
       }
       case RK_GN:
@@ -259,11 +264,10 @@ __device__ void assemble_rows(const DevTopo& T, const Lane& L, const SL& X, uint
           angA = cross3(ra, ez);
           float vn = dot3(lin, X.v3(18 * a + 12)) + dot3(angA, X.v3(18 * a + 15));
           bias = bh * min0f(d + T.slop) + L.P[T.o_sph_e + idx] * min0f(vn);
-          lo = 0.f;
         } else {
           lin = sub == 0 ? f3(1.f, 0.f, 0.f) : f3(0.f, 1.f, 0.f);  // basis of +z
           angA = cross3(ra, lin);
-          hi = L.P[T.o_sph_mu + idx];
+          bnd = L.P[T.o_sph_mu + idx];
         }
         break;
       }
@@ -288,14 +292,13 @@ __device__ void assemble_rows(const DevTopo& T, const Lane& L, const SL& X, uint
           float ek = L.P[T.o_sph_e + k], el = L.P[T.o_sph_e + l];
           float e = ek >= el ? ek : el;
           bias = bh * min0f(d + T.slop) + e * min0f(vn);
-          lo = 0.f;
         } else {
           float3 t1, t2;
           onb3(n, t1, t2);
           lin = sub == 0 ? t1 : t2;
           angA = cross3(ra, lin);
           angB = -cross3(rb, lin);
-          hi = sqrtf(L.P[T.o_sph_mu + k] * L.P[T.o_sph_mu + l]);
+          bnd = sqrtf(L.P[T.o_sph_mu + k] * L.P[T.o_sph_mu + l]);
         }
         break;
       }
@@ -316,60 +319,68 @@ __device__ void assemble_rows(const DevTopo& T, const Lane& L, const SL& X, uint
       IB = symv(ib, angB);
       K += S[T.sm_invm + b] * dot3(lin, lin) + dot3(angB, IB);
     }
-    const GL& R = L.rows;
-    const int base = s * RF_N;
-    R.s3(base + RF_LIN, lin);
-    R.s3(base + RF_ANGA, angA);
-    R.s3(base + RF_ANGB, angB);
-    R.s3(base + RF_IA, IA);
-    R.s3(base + RF_IB, IB);
-    R[base + RF_MEFF] = active ? 1.f / (K + T.gamma) : 0.f;
-    R[base + RF_BIAS] = active ? bias : 0.f;
-    R[base + RF_LO] = lo;
-    R[base + RF_HI] = hi;
+    const RV R = L.rows.at(s * RF_N);
+    R.s3(RF_LIN, lin);
+    R.s3(RF_ANGA, angA);
+    R.s3(RF_ANGB, angB);
+    R.s3(RF_IA, IA);
+    R.s3(RF_IB, IB);
+    R[RF_MEFF] = active ? 1.f / (K + T.gamma) : 0.f;
+    R[RF_BIAS] = active ? bias : 0.f;
+    R[RF_BND] = bnd;
     if (active_out) active_out[s] = active ? 1 : 0;
   }
 }
 
 // Projected Gauss-Seidel, cold start, T.iters sweeps in the canonical order. With TAPE the
 // impulses and clamp branches of every sweep and the velocities after every sweep are kept.
-template <bool TAPE>
-__device__ void pgs_solve(const DevTopo& T, const DevPtrs& D, const Lane& L, const SL& X) {
+template <bool TAPE, class RV>
+__device__ void pgs_solve(const DevTopo& T, const DevPtrs& D, const LaneT<RV>& L, const SL& X) {
   const SL& S = L.S;
   const int Bp = T.Bp;
   for (int s = 0; s < T.nslots; ++s) S[T.sm_lam + s] = 0.f;
   for (int it = 0; it < T.iters; ++it) {
     for (int oi = 0; oi < T.nslots; ++oi) {
       const int s = T.order[oi];
-      const int base = s * RF_N;
-      const float meff = L.rows[base + RF_MEFF];
+      const RV R = L.rows.at(s * RF_N);
+      const float meff = R[RF_MEFF];
       if (!__any_sync(FULLMASK, meff != 0.f)) continue;  // the row is inactive on every lane
       const int kind = T.skind[s], a = T.sa[s], b = T.sb[s];
-      const float3 lin = L.rows.v3(base + RF_LIN);
-      const float3 angA = L.rows.v3(base + RF_ANGA), angB = L.rows.v3(base + RF_ANGB);
-      const float bias = L.rows[base + RF_BIAS];
-      float lo = L.rows[base + RF_LO], hi = L.rows[base + RF_HI];
+      const float3 lin = R.v3(RF_LIN);
+      const float3 angA = R.v3(RF_ANGA), angB = R.v3(RF_ANGB);
+      const float bias = R[RF_BIAS];
       const float lam = S[T.sm_lam + s];
+      float lo, hi;
       if (kind == RK_GT || kind == RK_PT) {
-        hi = hi * S[T.sm_lam + T.snormal[s]];
+        hi = R[RF_BND] * S[T.sm_lam + T.snormal[s]];
         lo = -hi;
+      } else if (kind == RK_MOTOR) {
+        hi = R[RF_BND];
+        lo = -hi;
+      } else if (kind == RK_JLIN || kind == RK_JANG) {
+        lo = -__int_as_float(0x7f800000);
+        hi = __int_as_float(0x7f800000);
+      } else {
+        lo = 0.f;
+        hi = __int_as_float(0x7f800000);
       }
       float Jv = 0.f;
       float3 va, wa, vb, wb;
-      if (a >= 0) { va = X.v3(18 * a + 12); wa = X.v3(18 * a + 15); Jv += dot3(lin, va) + dot3(angA, wa); }
-      if (b >= 0) { vb = X.v3(18 * b + 12); wb = X.v3(18 * b + 15); Jv += dot3(angB, wb) - dot3(lin, vb); }
+      const SL Xa = X.at(18 * a + 12), Xb = X.at(18 * b + 12);
+      if (a >= 0) { va = Xa.v3(0); wa = Xa.v3(3); Jv += dot3(lin, va) + dot3(angA, wa); }
+      if (b >= 0) { vb = Xb.v3(0); wb = Xb.v3(3); Jv += dot3(angB, wb) - dot3(lin, vb); }
       const float pre = lam - meff * (Jv + bias + T.gamma * lam);
       const int br = pre < lo ? 1 : (pre > hi ? 2 : 0);
       const float ln = br == 1 ? lo : (br == 2 ? hi : pre);
       const float dl = ln - lam;
       S[T.sm_lam + s] = ln;
       if (a >= 0) {
-        X.s3(18 * a + 12, va + (dl * S[T.sm_invm + a]) * lin);
-        X.s3(18 * a + 15, wa + dl * L.rows.v3(base + RF_IA));
+        Xa.s3(0, va + (dl * S[T.sm_invm + a]) * lin);
+        Xa.s3(3, wa + dl * R.v3(RF_IA));
       }
       if (b >= 0) {
-        X.s3(18 * b + 12, vb - (dl * S[T.sm_invm + b]) * lin);
-        X.s3(18 * b + 15, wb + dl * L.rows.v3(base + RF_IB));
+        Xb.s3(0, vb - (dl * S[T.sm_invm + b]) * lin);
+        Xb.s3(3, wb + dl * R.v3(RF_IB));
       }
       if (TAPE) {
         size_t o = ((size_t)it * T.nslots + s) * Bp + L.i;
@@ -406,8 +417,8 @@ __device__ void integrate(const DevTopo& T, const SL& X) {
 }
 
 // One full step x_t -> x_{t+1} in place on X. Returns the loss term of x_{t+1}.
-template <bool TAPE, class AV>
-__device__ float step_forward(const DevTopo& T, const DevPtrs& D, const Lane& L, const SL& X, const AV* act, int t,
+template <bool TAPE, class RV, class AV>
+__device__ float step_forward(const DevTopo& T, const DevPtrs& D, const LaneT<RV>& L, const SL& X, const AV* act, int t,
                               uint8_t* active_out) {
   hinge_kinematics(T, L, X);
   if (T.n_layers > 0) {

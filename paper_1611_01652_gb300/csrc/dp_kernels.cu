@@ -72,12 +72,24 @@ __device__ __forceinline__ void copy_state_from_smem(const DevTopo& T, float* ds
 // Persistent forward: each warp advances its 32 instances over `nsteps` steps starting at step
 // t0. With rollout != 0 it starts from x0, stores checkpoints every ckpt_every steps and the
 // per-instance loss of Eq. L.
+template <class RV>
+__device__ __forceinline__ RV row_view(const DevTopo& T, const DevPtrs& D, float* sm, int i);
+template <>
+__device__ __forceinline__ SL row_view<SL>(const DevTopo& T, const DevPtrs& D, float* sm, int i) {
+  return SL{sm + T.sm_rows * 32};
+}
+template <>
+__device__ __forceinline__ GL row_view<GL>(const DevTopo& T, const DevPtrs& D, float* sm, int i) {
+  return GL{D.rows + i, T.Bp};
+}
+
+template <class RV>
 __global__ void __launch_bounds__(32) k_forward(const __grid_constant__ DevTopo T, const __grid_constant__ DevPtrs D,
                                                  const float* __restrict__ x0, int t0, int nsteps, int rollout) {
   const int lane = threadIdx.x;
   const int i = blockIdx.x * 32 + lane;
   float* sm = g_smem + lane;
-  Lane L{SL{sm}, GC{D.prm + i, T.Bp}, GL{D.rows + i, T.Bp}, i};
+  LaneT<RV> L{SL{sm}, GC{D.prm + i, T.Bp}, row_view<RV>(T, D, sm, i), i};
   SL X{sm + T.sm_x * 32};
   SL act[DPK_MAXL + 1];
   for (int l = 0; l <= DPK_MAXL; ++l) act[l] = SL{sm + T.sm_act[l] * 32};
@@ -115,7 +127,7 @@ __global__ void __launch_bounds__(32) k_backward(const __grid_constant__ DevTopo
   const size_t N = (size_t)T.horizon * Bp;
   const int nf = 18 * T.nb;
   float* sm = g_smem + lane;
-  Lane L{SL{sm}, GC{D.prm + i, Bp}, GL{D.rows + i, Bp}, i};
+  LaneT<GL> L{SL{sm}, GC{D.prm + i, Bp}, GL{D.rows + i, Bp}, i};
   SL X{sm + T.sm_x * 32}, XB{sm + T.sm_xb * 32}, VB{sm + T.sm_vb * 32};
   SL RC{sm + T.sm_rc * 32};
   SL sbar{sm + T.sm_sbar * 32};
@@ -145,7 +157,7 @@ __global__ void __launch_bounds__(32) k_backward(const __grid_constant__ DevTopo
         del[l] = GW{D.dump + (size_t)T.dump_del[l] * N + n, N};
       }
       const float* x_t = D.seg + (size_t)(t - ta) * nf * Bp;
-      BLane Bl{L, GC{x_t + i, Bp}, G, GC{D.vminus + i, Bp}};
+      BLaneT<GL> Bl{L, GC{x_t + i, Bp}, G, GC{D.vminus + i, Bp}};
       copy_state_to_smem(T, x_t, i, X);
       step_forward<true>(T, D, L, X, act, t, nullptr);
       loss_reverse(T, Bl, X, XB, loss_weight(T, t + 1) * dl);
@@ -173,7 +185,7 @@ __global__ void __launch_bounds__(32) k_backward(const __grid_constant__ DevTopo
     }
   }
   if (T.loss_kind == 3) {  // initial term -a.q(x_0) of the displacement loss
-    BLane Bl{L, GC{D.ckpt + i, Bp}, G, GC{D.vminus + i, Bp}};
+    BLaneT<GL> Bl{L, GC{D.ckpt + i, Bp}, G, GC{D.vminus + i, Bp}};
     copy_state_to_smem(T, D.ckpt, i, X);
     const int b = T.loss_body;
     M3 R = loadR(X, 18 * b);
@@ -281,9 +293,15 @@ cudaError_t launch_pad_scalar(int B, int Bp, const float* src, float* dst, cudaS
 cudaError_t launch_forward(const DevTopo& T, const DevPtrs& D, const float* x0, int t0, int nsteps, int rollout,
                            cudaStream_t s) {
   size_t smem = SM_BYTES(T);
-  cudaError_t e = cudaFuncSetAttribute(k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_forward<<<T.Bp / 32, 32, smem, s>>>(T, D, x0, t0, nsteps, rollout);
+  if (T.sm_rows >= 0) {
+    cudaError_t e = cudaFuncSetAttribute(k_forward<SL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_forward<SL><<<T.Bp / 32, 32, smem, s>>>(T, D, x0, t0, nsteps, rollout);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(k_forward<GL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_forward<GL><<<T.Bp / 32, 32, smem, s>>>(T, D, x0, t0, nsteps, rollout);
+  }
   return cudaGetLastError();
 }
 cudaError_t launch_backward(const DevTopo& T, const DevPtrs& D, cudaStream_t s) {
