@@ -181,6 +181,29 @@ dp_status dp_rollout(dp_world* w, const float* W, float* loss, float* traj, uint
  */
 dp_status dp_backward(dp_world* w, const float* dloss, float* dW, float* dstate0, const dp_param_grads* dparams);
 
+/*
+ * dp_backward_noalloc: dL/dW through the last dp_rollout, for callers that must not allocate
+ * device memory once they are running, such as a training loop replayed from a captured CUDA
+ * graph or an application that fixes its device memory up front. The paper has no counterpart
+ * to this call.
+ *
+ * It computes the same controller gradient as dp_backward (the other gradients are not
+ * produced) and calls no cudaMalloc, cudaFree or other allocating routine: besides the world's
+ * own buffers it uses one static device array of DP_NOALLOC_SCRATCH_FLOATS floats (4 MiB),
+ * which every GPU that loads the library holds until the process exits, for the split partial
+ * sums of the gradient reduction.
+ *   - The first call on a device looks up that device's address of the array; make that first
+ *     call before any stream capture.
+ *   - A controller layer with more than DP_NOALLOC_SCRATCH_FLOATS weights is rejected with
+ *     DP_EINVAL before anything is enqueued.
+ *   - All calls on a device share the array. Every value a call reads from it is written
+ *     earlier by the same call, but calls that overlap on the GPU (unordered streams) race:
+ *     order them on one stream.
+ * dloss ([B]) and dW (dp_num_params floats) may be host or device pointers.
+ */
+#define DP_NOALLOC_SCRATCH_FLOATS (1 << 20)
+dp_status dp_backward_noalloc(dp_world* w, const float* dloss, float* dW);
+
 /* Synchronise the world's stream; DP_ENAN if the last rollout produced a non-finite value. */
 dp_status dp_sync(dp_world* w);
 

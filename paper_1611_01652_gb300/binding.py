@@ -43,7 +43,7 @@ class ParamGrads(C.Structure):
 _lib = None
 SYMBOLS = ("dp_create_world", "dp_free", "dp_num_params", "dp_num_slots", "dp_schedule", "dp_set_initial_state",
            "dp_set_state", "dp_get_state", "dp_step", "dp_rollout", "dp_backward", "dp_sync", "dp_last_error",
-           "dp_ckpt_every")
+           "dp_ckpt_every", "dp_backward_noalloc")
 
 
 def load(build=True):
@@ -69,6 +69,7 @@ def load(build=True):
     lib.dp_step.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]
     lib.dp_rollout.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.dp_backward.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(ParamGrads)]
+    lib.dp_backward_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
     lib.dp_sync.argtypes = [C.c_void_p]
     lib.dp_last_error.restype = C.c_char_p
     _lib = lib
@@ -206,6 +207,10 @@ class World:
                 v = dparams.get(k)
                 setattr(pg, k, C.cast(ptr(v), PF) if v is not None else None)
         _check(_lib.dp_backward(self._h, ptr(dloss), ptr(dW), ptr(dstate0), C.byref(pg) if pg is not None else None))
+
+    def backward_noalloc(self, dloss, dW):
+        """dL/dW through the last rollout without any device allocation (static scratch)."""
+        _check(_lib.dp_backward_noalloc(self._h, ptr(dloss), ptr(dW)))
 
     def sync(self):
         _check(_lib.dp_sync(self._h))

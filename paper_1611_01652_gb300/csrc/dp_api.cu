@@ -9,6 +9,7 @@
 
 #include "../../include/dp.h"
 #include "dp_kernels.h"
+#include "dp_world.h"
 
 namespace {
 
@@ -29,27 +30,6 @@ size_t round32(size_t x) { return (x + 31) / 32 * 32; }
 
 }  // namespace
 
-struct dp_world {
-  DevTopo Tf, Tb;  // same topology; forward / backward shared-memory layouts
-  DevPtrs D;
-  cudaStream_t stream = nullptr;
-  int B = 0, Bp = 0, nf = 0;
-  int64_t n_params = 0;
-  int w_total = 0;
-  float* x0 = nullptr;
-  float* Wmaster = nullptr;
-  float *Wt = nullptr, *Wn = nullptr, *Wb = nullptr;
-  float* stage = nullptr;      // device staging buffer for user-layout inputs/outputs
-  size_t stage_floats = 0;
-  float* dW_stage = nullptr;   // [n_params]
-  float* partial = nullptr;    // dW split partials
-  size_t partial_floats = 0;
-  int splits = 1;
-  std::vector<void*> allocs;
-  int t_now = 0;
-  bool have_rollout = false;
-  int32_t kind[DPK_MAXSLOT], colour[DPK_MAXSLOT];
-};
 
 namespace {
 
@@ -232,6 +212,9 @@ void pack_param(std::vector<float>& h, int Bp, int B, int field0, int n, const f
 }
 
 }  // namespace
+
+// Error reporting for the other C-ABI translation units of the library.
+dp_status dp_internal_fail(dp_status s, const char* msg) { return fail(s, msg); }
 
 extern "C" {
 

@@ -1,0 +1,34 @@
+// Internal layout of a dp_world (shared by the C-ABI translation units of libdphys).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/dp.h"
+#include "dp_device.cuh"
+
+struct dp_world {
+  DevTopo Tf, Tb;  // same topology; forward / backward shared-memory layouts
+  DevPtrs D;
+  cudaStream_t stream = nullptr;
+  int B = 0, Bp = 0, nf = 0;
+  int64_t n_params = 0;
+  int w_total = 0;
+  float* x0 = nullptr;
+  float* Wmaster = nullptr;
+  float *Wt = nullptr, *Wn = nullptr, *Wb = nullptr;
+  float* stage = nullptr;      // device staging buffer for user-layout inputs/outputs
+  size_t stage_floats = 0;
+  float* dW_stage = nullptr;   // [n_params]
+  float* partial = nullptr;    // dW split partials
+  size_t partial_floats = 0;
+  int splits = 1;
+  std::vector<void*> allocs;
+  int t_now = 0;
+  bool have_rollout = false;
+  int32_t kind[DPK_MAXSLOT], colour[DPK_MAXSLOT];
+};
+
+// Records `msg` as the thread's last error and returns `s`.
+dp_status dp_internal_fail(dp_status s, const char* msg);
