@@ -99,15 +99,15 @@ __device__ void integrate_reverse(const DevTopo& T, const BLaneT<RV>& B, const S
 // Replays every sweep backwards. Working velocities are reset to the stored post-sweep values at
 // each sweep boundary and un-applied row by row. S[sm_lam] holds the impulse adjoints.
 template <class RV>
-__device__ void pgs_reverse(const DevTopo& T, const DevPtrs& D, const BLaneT<RV>& B, const SL& X, const SL& VB,
-                            const SL& RC) {
+__device__ void pgs_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& X, const SL& VB, const SL& RC,
+                            const TapeStep& tp) {
   const LaneT<RV>& L = B.L;
   const SL& S = L.S;
   const int Bp = T.Bp;
   for (int s = 0; s < T.nslots; ++s) S[T.sm_lam + s] = 0.f;
   for (int it = T.iters - 1; it >= 0; --it) {
     {
-      const float* vi = D.v_iter + (size_t)it * T.nb * 6 * Bp + L.i;
+      const float* vi = tp.viter + (size_t)it * T.nb * 6 * Bp + L.i;
       for (int b = 0; b < T.nb; ++b)
 #pragma unroll
         for (int k = 0; k < 6; ++k) X[18 * b + 12 + k] = vi[(size_t)(6 * b + k) * Bp];
@@ -121,10 +121,10 @@ __device__ void pgs_reverse(const DevTopo& T, const DevPtrs& D, const BLaneT<RV>
       const float3 lin = R.v3(RF_LIN);
       const float3 angA = R.v3(RF_ANGA), angB = R.v3(RF_ANGB);
       const float bias = R[RF_BIAS];
-      const size_t o = ((size_t)it * T.nslots + s) * Bp + L.i;
-      const float la = D.lam_hist[o];
-      const float lb = it > 0 ? D.lam_hist[o - (size_t)T.nslots * Bp] : 0.f;
-      const int br = D.br_hist[o];
+      const int o = (it * T.nslots + s) * Bp + L.i;
+      const float la = tp.lam[o];
+      const float lb = it > 0 ? tp.lam[o - T.nslots * Bp] : 0.f;
+      const int br = tp.br[o];
       const float dl = la - lb;
       float3 va = f3(0.f, 0.f, 0.f), wa = va, vb = va, wb = va, vba = va, wba = va, vbb = va, wbb = va;
       float ima = 0.f, imb = 0.f;
@@ -187,7 +187,7 @@ __device__ void pgs_reverse(const DevTopo& T, const DevPtrs& D, const BLaneT<RV>
       } else if (kind == RK_GT || kind == RK_PT) {
         // bound = +-mu * lambda_n (current value of the contact's normal impulse)
         const int ns_ = T.snormal[s];
-        const float lnrm = D.lam_hist[((size_t)it * T.nslots + ns_) * Bp + L.i];
+        const float lnrm = tp.lam[(it * T.nslots + ns_) * Bp + L.i];
         const float mu = R[RF_BND];
         const float sg = br == 2 ? 1.f : -1.f;
         RC[rc + RC_BND] += sg * lnrm * lbar_a;

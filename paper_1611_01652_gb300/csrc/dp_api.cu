@@ -357,36 +357,63 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
                                       std::to_string(smem_max));
     return cleanup(s);
   }
-  // checkpoint interval from free memory
+  // Memory plan. With enough device memory the rollout records every step's solver tape and the
+  // backward pass only reads it (no recomputation). Otherwise states are checkpointed every K
+  // steps and the backward pass recomputes one K-step segment at a time with its tape.
   const int nf = 18 * T.nb;
   w->nf = nf;
   const size_t state_bytes = (size_t)nf * Bp * sizeof(float);
+  const size_t tape_step_bytes = ((size_t)T.nslots * RF_N * sizeof(float) + (size_t)T.iters * T.nslots * (sizeof(float) + 1) +
+                                  (size_t)T.iters * T.nb * 6 * sizeof(float) + (size_t)T.nb * 6 * sizeof(float)) *
+                                 Bp;
   const size_t dump_bytes = (size_t)T.dump_rows * T.horizon * Bp * sizeof(float);
   size_t free_b = 0, total_b = 0;
   CU(cudaMemGetInfo(&free_b, &total_b));
+  const size_t fixed = (size_t)T.nslots * RF_N * Bp * sizeof(float) + 8 * state_bytes + ((size_t)64 << 20);
+  const size_t usable = (size_t)(0.85 * (double)free_b);
+  const size_t budget = usable > dump_bytes + fixed ? usable - dump_bytes - fixed : 0;
   int K = d->ckpt_every;
+  bool full = false;
+  auto seg_bytes = [&](int k) {
+    return (size_t)((T.horizon + k - 1) / k) * state_bytes + (size_t)k * tape_step_bytes + (size_t)(k + 1) * state_bytes;
+  };
   if (K == 0) {
-    size_t budget = free_b > dump_bytes ? (free_b - dump_bytes) / 4 : 0;
-    K = 1;
-    while (K < T.horizon && ((size_t)((T.horizon + K - 1) / K) + K) * state_bytes > budget) ++K;
+    if ((size_t)T.horizon * (tape_step_bytes + state_bytes) <= budget) {
+      full = true;
+      K = 1;
+    } else {
+      int best = 1;
+      for (int k = 1; k <= T.horizon; ++k)
+        if (seg_bytes(k) < seg_bytes(best)) best = k;
+      if (seg_bytes(best) > budget)
+        return cleanup(fail(DP_ENOMEM, "not enough device memory for checkpoints and one segment's tape"));
+      K = best;
+    }
   }
   K = std::min(K, T.horizon);
   const int n_ckpt = (T.horizon + K - 1) / K;
+  const int tape_steps = full ? T.horizon : K;
   DevPtrs& D = w->D;
   std::memset(&D, 0, sizeof(D));
   D.ckpt_every = K;
   D.n_ckpt = n_ckpt;
+  D.tape_steps = tape_steps;
+  D.tape_full = full ? 1 : 0;
   // device buffers
   float* prm = nullptr;
   if (dalloc(w, &prm, (size_t)T.n_pfields * Bp)) return cleanup(DP_ENOMEM);
   D.prm = prm;
-  if (dalloc(w, &D.state, (size_t)nf * Bp) || dalloc(w, &w->x0, (size_t)nf * Bp) ||
-      dalloc(w, &D.ckpt, (size_t)n_ckpt * nf * Bp) || dalloc(w, &D.seg, (size_t)K * nf * Bp) ||
-      dalloc(w, &D.rows, (size_t)T.nslots * RF_N * Bp) || dalloc(w, &D.lam_hist, (size_t)T.iters * T.nslots * Bp) ||
-      dalloc(w, &D.br_hist, (size_t)T.iters * T.nslots * Bp) || dalloc(w, &D.v_iter, (size_t)T.iters * T.nb * 6 * Bp) ||
-      dalloc(w, &D.vminus, (size_t)T.nb * 6 * Bp) || dalloc(w, &D.loss, (size_t)Bp) || dalloc(w, &D.dloss, (size_t)Bp) ||
-      dalloc(w, &D.grad_prm, (size_t)T.n_pfields * Bp) || dalloc(w, &D.grad_state0, (size_t)nf * Bp) ||
-      dalloc(w, &D.status, (size_t)Bp))
+  const size_t Bz = (size_t)Bp;
+  if (dalloc(w, &D.state, (size_t)nf * Bz) || dalloc(w, &w->x0, (size_t)nf * Bz) ||
+      dalloc(w, &D.ckpt, (size_t)n_ckpt * nf * Bz) || dalloc(w, &D.seg, full ? (size_t)1 : (size_t)(K + 1) * nf * Bz) ||
+      dalloc(w, &D.rows, (size_t)T.nslots * RF_N * Bz) ||
+      dalloc(w, &D.t_rows, (size_t)tape_steps * T.nslots * RF_N * Bz) ||
+      dalloc(w, &D.t_lam, (size_t)tape_steps * T.iters * T.nslots * Bz) ||
+      dalloc(w, &D.t_br, (size_t)tape_steps * T.iters * T.nslots * Bz) ||
+      dalloc(w, &D.t_viter, (size_t)tape_steps * T.iters * T.nb * 6 * Bz) ||
+      dalloc(w, &D.t_vminus, (size_t)tape_steps * T.nb * 6 * Bz) || dalloc(w, &D.loss, Bz) || dalloc(w, &D.dloss, Bz) ||
+      dalloc(w, &D.grad_prm, (size_t)T.n_pfields * Bz) || dalloc(w, &D.grad_state0, (size_t)nf * Bz) ||
+      dalloc(w, &D.status, Bz))
     return cleanup(DP_ENOMEM);
   if (T.n_layers > 0) {
     if (dalloc(w, &D.dump, (size_t)T.dump_rows * T.horizon * Bp) || dalloc(w, &w->Wmaster, (size_t)np_) ||
@@ -486,6 +513,7 @@ dp_status dp_set_state(dp_world* w, const float* state, int32_t t) {
   if (t < 0) return fail(DP_EINVAL, "t must be >= 0");
   TRY(stage_state_in(w, state, w->D.state));
   w->t_now = t;
+  w->have_rollout = false;
   return DP_OK;
 }
 
@@ -512,7 +540,7 @@ dp_status dp_step(dp_world* w, int32_t n_steps, const float* W, uint8_t* active)
   DevPtrs D = w->D;
   D.active = active;
   D.traj = nullptr;
-  CU(launch_forward(w->Tf, D, w->x0, w->t_now, n_steps, 0, w->stream));
+  CU(launch_forward(w->Tf, D, w->x0, w->t_now, n_steps, 0, 0, w->stream));
   w->t_now += n_steps;
   w->have_rollout = false;
   return DP_OK;
@@ -525,7 +553,7 @@ dp_status dp_rollout(dp_world* w, const float* W, float* loss, float* traj, uint
   D.active = active;
   D.traj = traj;
   CU(cudaMemsetAsync(D.status, 0, sizeof(int) * w->Bp, w->stream));
-  CU(launch_forward(w->Tf, D, w->x0, 0, w->Tf.horizon, 1, w->stream));
+  CU(launch_forward(w->Tf, D, w->x0, 0, w->Tf.horizon, 1, D.tape_full, w->stream));
   if (loss) CU(cudaMemcpyAsync(loss, D.loss, sizeof(float) * w->B, cudaMemcpyDefault, w->stream));
   w->t_now = w->Tf.horizon;
   w->have_rollout = true;

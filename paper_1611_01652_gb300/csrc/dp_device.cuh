@@ -69,11 +69,14 @@ struct DevPtrs {
   float* state;          // current state [nb*18][Bp]
   float* ckpt;           // checkpoints [n_ckpt][nb*18][Bp]
   float* seg;            // segment states for the backward [K+1][nb*18][Bp]
-  float* rows;           // [nslots][RF_N][Bp]
-  float* lam_hist;       // [iters][nslots][Bp]
-  uint8_t* br_hist;      // [iters][nslots][Bp]
-  float* v_iter;         // [iters][nb*6][Bp] velocities after each sweep
-  float* vminus;         // [nb*6][Bp] velocities after the external impulses
+  float* rows;           // constraint rows without a tape (rows that do not fit on chip) [nslots][RF_N][Bp]
+  // Per-step solver tape, tape_steps slots: the whole horizon when it fits in device memory
+  // (recorded by the rollout), else one checkpoint segment (recorded by the backward pass).
+  float* t_rows;         // [tape_steps][nslots][RF_N][Bp] constraint rows
+  float* t_lam;          // [tape_steps][iters][nslots][Bp] impulse after each row update
+  uint8_t* t_br;         // [tape_steps][iters][nslots][Bp] clamp branch (0 inside, 1 lower, 2 upper)
+  float* t_viter;        // [tape_steps][iters][nb*6][Bp] velocities after each sweep
+  float* t_vminus;       // [tape_steps][nb*6][Bp] velocities after the external impulses
   float* dump;           // controller activations and deltas [dump_rows][T*Bp]
   float* loss;           // [Bp]
   float* dloss;          // [Bp]
@@ -83,7 +86,27 @@ struct DevPtrs {
   uint8_t* active;       // optional [T][B][nslots]
   int* status;           // [Bp] nonzero: non-finite value met
   int ckpt_every, n_ckpt;
+  int tape_steps, tape_full;  // tape_full: the rollout records every step (no recompute)
 };
+
+// Tape slot of one step.
+struct TapeStep {
+  float* rows;
+  float* lam;
+  uint8_t* br;
+  float* viter;
+  float* vminus;
+};
+__device__ __forceinline__ TapeStep tape_step(const DevTopo& T, const DevPtrs& D, int ts) {
+  const size_t Bp = T.Bp;
+  TapeStep p;
+  p.rows = D.t_rows + (size_t)ts * T.nslots * RF_N * Bp;
+  p.lam = D.t_lam + (size_t)ts * T.iters * T.nslots * Bp;
+  p.br = D.t_br + (size_t)ts * T.iters * T.nslots * Bp;
+  p.viter = D.t_viter + (size_t)ts * T.iters * T.nb * 6 * Bp;
+  p.vminus = D.t_vminus + (size_t)ts * T.nb * 6 * Bp;
+  return p;
+}
 
 // ------------------------------------------------------------------------------- math
 struct M3 { float m[9]; };
@@ -176,6 +199,7 @@ __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__floa
 
 // Lane views: shared memory [field][32], global memory [field][Bp].
 struct SL {
+  static constexpr bool is_global = false;
   float* p;
   __device__ __forceinline__ SL at(int f) const { return SL{p + f * 32}; }
   __device__ __forceinline__ float& operator[](int f) const { return p[f * 32]; }
@@ -185,6 +209,7 @@ struct SL {
 };
 // Global view with a run-time stride (f * s stays below 2^31 for every buffer indexed this way).
 struct GL {
+  static constexpr bool is_global = true;
   float* p;
   int s;
   __device__ __forceinline__ float& operator[](int f) const { return p[f * s]; }
@@ -206,6 +231,13 @@ struct GC {
   __device__ __forceinline__ float3 v3(int f) const { return f3((*this)[f], (*this)[f + 1], (*this)[f + 2]); }
 };
 
+template <class XV>
+__device__ __forceinline__ M3 loadRv(const XV& X, int base) {
+  M3 R;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) R.m[k] = X[base + 3 + k];
+  return R;
+}
 __device__ __forceinline__ M3 loadR(const SL& X, int base) {
   M3 R;
 #pragma unroll

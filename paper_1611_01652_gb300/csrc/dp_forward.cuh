@@ -19,14 +19,18 @@ struct LaneT {
   int i;       // instance index
 };
 
-__device__ __forceinline__ float3 body_v(const SL& X, int b) { return b >= 0 ? X.v3(18 * b + 12) : f3(0.f, 0.f, 0.f); }
-__device__ __forceinline__ float3 body_w(const SL& X, int b) { return b >= 0 ? X.v3(18 * b + 15) : f3(0.f, 0.f, 0.f); }
-__device__ __forceinline__ float3 body_p(const SL& X, int b) { return b >= 0 ? X.v3(18 * b) : f3(0.f, 0.f, 0.f); }
-__device__ __forceinline__ M3 body_R(const SL& X, int b) { return b >= 0 ? loadR(X, 18 * b) : eye3(); }
+template <class XV>
+__device__ __forceinline__ float3 body_v(const XV& X, int b) { return b >= 0 ? X.v3(18 * b + 12) : f3(0.f, 0.f, 0.f); }
+template <class XV>
+__device__ __forceinline__ float3 body_w(const XV& X, int b) { return b >= 0 ? X.v3(18 * b + 15) : f3(0.f, 0.f, 0.f); }
+template <class XV>
+__device__ __forceinline__ float3 body_p(const XV& X, int b) { return b >= 0 ? X.v3(18 * b) : f3(0.f, 0.f, 0.f); }
+template <class XV>
+__device__ __forceinline__ M3 body_R(const XV& X, int b) { return b >= 0 ? loadRv(X, 18 * b) : eye3(); }
 
 // Hinge axis (world), angle about it between the two reference vectors, and its rate.
-template <class RV>
-__device__ void hinge_kinematics(const DevTopo& T, const LaneT<RV>& L, const SL& X) {
+template <class RV, class XV>
+__device__ void hinge_kinematics(const DevTopo& T, const LaneT<RV>& L, const XV& X) {
   const SL& S = L.S;
   for (int j = 0; j < T.nj; ++j) {
     int a = T.ja[j], b = T.jb[j];
@@ -34,7 +38,7 @@ __device__ void hinge_kinematics(const DevTopo& T, const LaneT<RV>& L, const SL&
     float3 ua = mv(Ra, L.P.v3(T.o_axis + 6 * j));
     S.s3(T.sm_ua + 3 * j, ua);
     if (T.jtype[j] == 1) {
-      M3 Rb = loadR(X, 18 * b);
+      M3 Rb = loadRv(X, 18 * b);
       float3 wa = mv(Ra, L.P.v3(T.o_ref + 6 * j));
       float3 wb = mv(Rb, L.P.v3(T.o_ref + 6 * j + 3));
       float y = dot3(cross3(wa, wb), ua), x = dot3(wa, wb);
@@ -181,6 +185,21 @@ __device__ void external_impulses(const DevTopo& T, const LaneT<RV>& L, const SL
     X.s3(18 * b + 12, v);
     X.s3(18 * b + 15, w);
     S[T.sm_invm + b] = 1.f / m;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) S[T.sm_iinv + 6 * b + k] = ii[k];
+  }
+}
+
+// World inverse inertia and inverse mass of every body at state X (no state change).
+template <class RV, class XV>
+__device__ void inverse_inertia(const DevTopo& T, const LaneT<RV>& L, const XV& X) {
+  const SL& S = L.S;
+  for (int b = 0; b < T.nb; ++b) {
+    M3 R = loadRv(X, 18 * b);
+    float3 I = L.P.v3(T.o_inertia + 3 * b);
+    float ii[6];
+    rot_diag6(R, f3(1.f / I.x, 1.f / I.y, 1.f / I.z), ii);
+    S[T.sm_invm + b] = 1.f / L.P[T.o_mass + b];
 #pragma unroll
     for (int k = 0; k < 6; ++k) S[T.sm_iinv + 6 * b + k] = ii[k];
   }
@@ -335,7 +354,7 @@ __device__ void assemble_rows(const DevTopo& T, const LaneT<RV>& L, const SL& X,
 // Projected Gauss-Seidel, cold start, T.iters sweeps in the canonical order. With TAPE the
 // impulses and clamp branches of every sweep and the velocities after every sweep are kept.
 template <bool TAPE, class RV>
-__device__ void pgs_solve(const DevTopo& T, const DevPtrs& D, const LaneT<RV>& L, const SL& X) {
+__device__ void pgs_solve(const DevTopo& T, const LaneT<RV>& L, const SL& X, const TapeStep& tp) {
   const SL& S = L.S;
   const int Bp = T.Bp;
   for (int s = 0; s < T.nslots; ++s) S[T.sm_lam + s] = 0.f;
@@ -383,13 +402,13 @@ __device__ void pgs_solve(const DevTopo& T, const DevPtrs& D, const LaneT<RV>& L
         Xb.s3(3, wb + dl * R.v3(RF_IB));
       }
       if (TAPE) {
-        size_t o = ((size_t)it * T.nslots + s) * Bp + L.i;
-        D.lam_hist[o] = ln;
-        D.br_hist[o] = (uint8_t)br;
+        const int o = (it * T.nslots + s) * Bp + L.i;
+        tp.lam[o] = ln;
+        tp.br[o] = (uint8_t)br;
       }
     }
     if (TAPE) {
-      float* vi = D.v_iter + (size_t)it * T.nb * 6 * Bp + L.i;
+      float* vi = tp.viter + (size_t)it * T.nb * 6 * Bp + L.i;
       for (int b = 0; b < T.nb; ++b)
 #pragma unroll
         for (int k = 0; k < 6; ++k) vi[(size_t)(6 * b + k) * Bp] = X[18 * b + 12 + k];
@@ -417,25 +436,39 @@ __device__ void integrate(const DevTopo& T, const SL& X) {
 }
 
 // One full step x_t -> x_{t+1} in place on X. Returns the loss term of x_{t+1}.
+// One full step x_t -> x_{t+1} in place on X. With TAPE the step's solver tape is written to
+// slot `ts` of the tape (rows are copied there when they are assembled on chip) and, when
+// `dump_col` is given, the controller activations are stored in the dump column.
 template <bool TAPE, class RV, class AV>
 __device__ float step_forward(const DevTopo& T, const DevPtrs& D, const LaneT<RV>& L, const SL& X, const AV* act, int t,
-                              uint8_t* active_out) {
+                              uint8_t* active_out, int ts = 0, float* dump_col = nullptr) {
   hinge_kinematics(T, L, X);
   if (T.n_layers > 0) {
     controller_features(T, L, X, t, act[0]);
     controller_forward(T, D, act);
+    if (dump_col) {
+      const size_t N = (size_t)T.horizon * T.Bp;
+      for (int l = 0; l <= T.n_layers; ++l)
+        for (int k = 0; k < T.widths[l]; ++k) dump_col[(size_t)(T.dump_act[l] + k) * N] = act[l][k];
+    }
     servo_targets(T, L, act[T.n_layers]);
   } else {
     servo_targets(T, L, act[0]);
   }
   external_impulses(T, L, X);
+  TapeStep tp;
   if (TAPE) {
+    tp = tape_step(T, D, ts);
     for (int b = 0; b < T.nb; ++b)
 #pragma unroll
-      for (int k = 0; k < 6; ++k) D.vminus[(size_t)(6 * b + k) * T.Bp + L.i] = X[18 * b + 12 + k];
+      for (int k = 0; k < 6; ++k) tp.vminus[(6 * b + k) * T.Bp + L.i] = X[18 * b + 12 + k];
   }
   assemble_rows(T, L, X, active_out);
-  pgs_solve<TAPE>(T, D, L, X);
+  if (TAPE && !RV::is_global) {
+    float* dst = tp.rows + L.i;
+    for (int f = 0; f < T.nslots * RF_N; ++f) dst[f * T.Bp] = L.rows[f];
+  }
+  pgs_solve<TAPE>(T, L, X, tp);
   integrate(T, X);
   float w = loss_weight(T, t + 1);
   return w != 0.f ? w * loss_value(T, L, X) : 0.f;

@@ -83,9 +83,13 @@ __device__ __forceinline__ GL row_view<GL>(const DevTopo& T, const DevPtrs& D, f
   return GL{D.rows + i, T.Bp};
 }
 
-template <class RV>
-__global__ void __launch_bounds__(32) k_forward(const __grid_constant__ DevTopo T, const __grid_constant__ DevPtrs D,
-                                                 const float* __restrict__ x0, int t0, int nsteps, int rollout) {
+// Persistent forward: each warp advances its 32 instances over `nsteps` steps starting at step
+// t0. With rollout != 0 it starts from x0, stores checkpoints every ckpt_every steps and the
+// per-instance loss of Eq. L; with REC it also records every step's solver tape and
+// controller activations for the reverse pass.
+template <class RV, bool REC>
+__global__ void __launch_bounds__(32, 1) k_forward(const __grid_constant__ DevTopo T, const __grid_constant__ DevPtrs D,
+                                                    const float* __restrict__ x0, int t0, int nsteps, int rollout) {
   const int lane = threadIdx.x;
   const int i = blockIdx.x * 32 + lane;
   float* sm = g_smem + lane;
@@ -105,7 +109,10 @@ __global__ void __launch_bounds__(32) k_forward(const __grid_constant__ DevTopo 
         for (int f = 0; f < 18 * T.nb; ++f) D.traj[((size_t)t * B + i) * 18 * T.nb + f] = X[f];
     }
     uint8_t* ao = (D.active && i < B) ? D.active + ((size_t)k * B + i) * T.nslots : nullptr;
-    loss += step_forward<false>(T, D, L, X, act, t, ao);
+    if (REC)
+      loss += step_forward<true>(T, D, L, X, act, t, ao, t, T.n_layers > 0 ? D.dump + (size_t)t * T.Bp + i : nullptr);
+    else
+      loss += step_forward<false>(T, D, L, X, act, t, ao);
   }
   if (rollout && D.traj && i < B)
     for (int f = 0; f < 18 * T.nb; ++f) D.traj[((size_t)(t0 + nsteps) * B + i) * 18 * T.nb + f] = X[f];
@@ -117,87 +124,105 @@ __global__ void __launch_bounds__(32) k_forward(const __grid_constant__ DevTopo 
 }
 
 // ------------------------------------------------------------------------------ backward
-// Reverse mode through the last rollout. For each checkpoint segment (last first): recompute
-// the segment's states, then for each step (last first) recompute the step with its tape and
-// run every stage's adjoint.
-__global__ void __launch_bounds__(32) k_backward(const __grid_constant__ DevTopo T, const __grid_constant__ DevPtrs D) {
+struct BwdCtx {
+  SL S, X, XB, VB, RC, sbar;
+  GC P;
+  GL G;
+  int i;
+  float dl;
+};
+
+// Reverse of step t from its tape slot ts, with x_t and x_{t+1} in global memory.
+__device__ void reverse_step(const DevTopo& T, const DevPtrs& D, const BwdCtx& C, int t, int ts, const float* x_t,
+                             const float* x_t1) {
+  const int Bp = T.Bp, i = C.i;
+  const size_t N = (size_t)T.horizon * Bp;
+  const size_t n = (size_t)t * Bp + i;
+  const TapeStep tp = tape_step(T, D, ts);
+  LaneT<GL> L{C.S, C.P, GL{tp.rows + i, Bp}, i};
+  BLaneT<GL> Bl{L, GC{x_t + i, Bp}, C.G, GC{tp.vminus + i, Bp}};
+  GW act[DPK_MAXL + 1], del[DPK_MAXL + 1];
+  for (int l = 0; l <= DPK_MAXL; ++l) {
+    act[l] = GW{D.dump + (size_t)T.dump_act[l] * N + n, N};
+    del[l] = GW{D.dump + (size_t)T.dump_del[l] * N + n, N};
+  }
+  copy_state_to_smem(T, x_t1, i, C.X);
+  // per-step forward quantities of x_t that the adjoints use (recomputed bit-identically)
+  hinge_kinematics(T, L, Bl.X0);
+  servo_targets(T, L, act[T.n_layers > 0 ? T.n_layers : 0]);
+  inverse_inertia(T, L, Bl.X0);
+  loss_reverse(T, Bl, C.X, C.XB, loss_weight(T, t + 1) * C.dl);
+  for (int j = 0; j < T.nj; ++j) {
+    C.S[T.sm_thb + j] = 0.f; C.S[T.sm_thdb + j] = 0.f; C.S[T.sm_wstb + j] = 0.f;
+    C.S.s3(T.sm_uab + 3 * j, f3(0.f, 0.f, 0.f));
+  }
+  for (int b = 0; b < T.nb; ++b) {
+    C.S[T.sm_invmb + b] = 0.f;
+    for (int q = 0; q < 9; ++q) C.S[T.sm_iinvb + 9 * b + q] = 0.f;
+  }
+  for (int q = 0; q < T.nslots * RC_N; ++q) C.RC[q] = 0.f;
+  integrate_reverse(T, Bl, C.X, C.XB, C.VB);
+  pgs_reverse(T, Bl, C.X, C.VB, C.RC, tp);
+  rows_reverse(T, Bl, C.XB, C.VB, C.RC);
+  external_reverse(T, Bl, C.XB, C.VB);
+  if (T.n_layers > 0) {
+    servo_reverse(T, Bl, act[T.n_layers], del[T.n_layers - 1]);
+    controller_reverse(T, D, act, del, C.sbar);
+    features_reverse(T, Bl, C.XB, C.sbar);
+  } else {
+    servo_reverse(T, Bl, act[0], act[0]);
+  }
+  hinge_reverse(T, Bl, C.XB);
+}
+
+// Reverse mode through the last rollout, last step first. With a full tape every step is read
+// from it; otherwise each checkpoint segment (last first) is recomputed with its tape.
+__global__ void __launch_bounds__(32, 1) k_backward(const __grid_constant__ DevTopo T, const __grid_constant__ DevPtrs D) {
   const int lane = threadIdx.x;
   const int i = blockIdx.x * 32 + lane;
   const int Bp = T.Bp;
   const size_t N = (size_t)T.horizon * Bp;
   const int nf = 18 * T.nb;
   float* sm = g_smem + lane;
-  LaneT<GL> L{SL{sm}, GC{D.prm + i, Bp}, GL{D.rows + i, Bp}, i};
-  SL X{sm + T.sm_x * 32}, XB{sm + T.sm_xb * 32}, VB{sm + T.sm_vb * 32};
-  SL RC{sm + T.sm_rc * 32};
-  SL sbar{sm + T.sm_sbar * 32};
-  GL G{D.grad_prm + i, Bp};
-  for (int f = 0; f < nf; ++f) XB[f] = 0.f;
-  const float dl = D.dloss[i];
-  const int K = D.ckpt_every;
-  for (int c = D.n_ckpt - 1; c >= 0; --c) {
-    const int ta = c * K;
-    const int tb = min(T.horizon, ta + K);
-    // segment states x_ta .. x_{tb-1} into D.seg
-    copy_state_to_smem(T, D.ckpt + (size_t)c * nf * Bp, i, X);
-    for (int t = ta; t < tb; ++t) {
-      copy_state_from_smem(T, D.seg + (size_t)(t - ta) * nf * Bp, i, X);
-      if (t + 1 < tb) {
+  BwdCtx C{SL{sm}, SL{sm + T.sm_x * 32}, SL{sm + T.sm_xb * 32}, SL{sm + T.sm_vb * 32}, SL{sm + T.sm_rc * 32},
+           SL{sm + T.sm_sbar * 32}, GC{D.prm + i, Bp}, GL{D.grad_prm + i, Bp}, i, D.dloss[i]};
+  for (int f = 0; f < nf; ++f) C.XB[f] = 0.f;
+  const size_t sbytes = (size_t)nf * Bp;
+  if (D.tape_full) {
+    for (int t = T.horizon - 1; t >= 0; --t)
+      reverse_step(T, D, C, t, t, D.ckpt + (size_t)t * sbytes, t + 1 < T.horizon ? D.ckpt + (size_t)(t + 1) * sbytes : D.state);
+  } else {
+    const int K = D.ckpt_every;
+    for (int c = D.n_ckpt - 1; c >= 0; --c) {
+      const int ta = c * K;
+      const int tb = min(T.horizon, ta + K);
+      copy_state_to_smem(T, D.ckpt + (size_t)c * sbytes, i, C.X);
+      for (int t = ta; t < tb; ++t) {
+        copy_state_from_smem(T, D.seg + (size_t)(t - ta) * sbytes, i, C.X);
+        const TapeStep tp = tape_step(T, D, t - ta);
+        LaneT<GL> L{C.S, C.P, GL{tp.rows + i, Bp}, i};
         const size_t n = (size_t)t * Bp + i;
         GW aw[DPK_MAXL + 1];
         for (int l = 0; l <= DPK_MAXL; ++l) aw[l] = GW{D.dump + (size_t)T.dump_act[l] * N + n, N};
-        step_forward<false>(T, D, L, X, aw, t, nullptr);
+        step_forward<true>(T, D, L, C.X, aw, t, nullptr, t - ta);
       }
-    }
-    for (int t = tb - 1; t >= ta; --t) {
-      const size_t n = (size_t)t * Bp + i;
-      GW act[DPK_MAXL + 1], del[DPK_MAXL + 1];
-      for (int l = 0; l <= DPK_MAXL; ++l) {
-        act[l] = GW{D.dump + (size_t)T.dump_act[l] * N + n, N};
-        del[l] = GW{D.dump + (size_t)T.dump_del[l] * N + n, N};
-      }
-      const float* x_t = D.seg + (size_t)(t - ta) * nf * Bp;
-      BLaneT<GL> Bl{L, GC{x_t + i, Bp}, G, GC{D.vminus + i, Bp}};
-      copy_state_to_smem(T, x_t, i, X);
-      step_forward<true>(T, D, L, X, act, t, nullptr);
-      loss_reverse(T, Bl, X, XB, loss_weight(T, t + 1) * dl);
-      for (int j = 0; j < T.nj; ++j) {
-        L.S[T.sm_thb + j] = 0.f; L.S[T.sm_thdb + j] = 0.f; L.S[T.sm_wstb + j] = 0.f;
-        L.S.s3(T.sm_uab + 3 * j, f3(0.f, 0.f, 0.f));
-      }
-      for (int b = 0; b < T.nb; ++b) {
-        L.S[T.sm_invmb + b] = 0.f;
-        for (int q = 0; q < 9; ++q) L.S[T.sm_iinvb + 9 * b + q] = 0.f;
-      }
-      for (int q = 0; q < T.nslots * RC_N; ++q) RC[q] = 0.f;
-      integrate_reverse(T, Bl, X, XB, VB);
-      pgs_reverse(T, D, Bl, X, VB, RC);
-      rows_reverse(T, Bl, XB, VB, RC);
-      external_reverse(T, Bl, XB, VB);
-      if (T.n_layers > 0) {
-        servo_reverse(T, Bl, act[T.n_layers], del[T.n_layers - 1]);
-        controller_reverse(T, D, act, del, sbar);
-        features_reverse(T, Bl, XB, sbar);
-      } else {
-        servo_reverse(T, Bl, act[0], act[0]);
-      }
-      hinge_reverse(T, Bl, XB);
+      copy_state_from_smem(T, D.seg + (size_t)(tb - ta) * sbytes, i, C.X);
+      for (int t = tb - 1; t >= ta; --t)
+        reverse_step(T, D, C, t, t - ta, D.seg + (size_t)(t - ta) * sbytes, D.seg + (size_t)(t - ta + 1) * sbytes);
     }
   }
   if (T.loss_kind == 3) {  // initial term -a.q(x_0) of the displacement loss
-    BLaneT<GL> Bl{L, GC{D.ckpt + i, Bp}, G, GC{D.vminus + i, Bp}};
-    copy_state_to_smem(T, D.ckpt, i, X);
+    copy_state_to_smem(T, D.ckpt, i, C.X);
     const int b = T.loss_body;
-    M3 R = loadR(X, 18 * b);
-    float3 c = L.P.v3(T.o_loss_point), a = L.P.v3(T.o_loss_target);
-    float3 gq = -dl * a;
-    XB.a3(18 * b, gq);
-    add_outer(XB, 18 * b + 3, gq, c);
-    G.a3(T.o_loss_point, mtv(R, gq));
-    G.a3(T.o_loss_target, -dl * (X.v3(18 * b) + mv(R, c)));
-    (void)Bl;
+    M3 R = loadR(C.X, 18 * b);
+    float3 c = C.P.v3(T.o_loss_point), a = C.P.v3(T.o_loss_target);
+    float3 gq = -C.dl * a;
+    C.XB.a3(18 * b, gq);
+    add_outer(C.XB, 18 * b + 3, gq, c);
+    C.G.a3(T.o_loss_point, mtv(R, gq));
+    C.G.a3(T.o_loss_target, -C.dl * (C.X.v3(18 * b) + mv(R, c)));
   }
-  for (int f = 0; f < nf; ++f) D.grad_state0[(size_t)f * Bp + i] = XB[f];
+  for (int f = 0; f < nf; ++f) D.grad_state0[(size_t)f * Bp + i] = C.XB[f];
 }
 
 // ------------------------------------------------------------------------------ dW reduction
@@ -290,19 +315,22 @@ cudaError_t launch_pad_scalar(int B, int Bp, const float* src, float* dst, cudaS
   k_pad_scalar<<<(Bp + 127) / 128, 128, 0, s>>>(B, Bp, src, dst);
   return cudaGetLastError();
 }
-cudaError_t launch_forward(const DevTopo& T, const DevPtrs& D, const float* x0, int t0, int nsteps, int rollout,
-                           cudaStream_t s) {
-  size_t smem = SM_BYTES(T);
-  if (T.sm_rows >= 0) {
-    cudaError_t e = cudaFuncSetAttribute(k_forward<SL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_forward<SL><<<T.Bp / 32, 32, smem, s>>>(T, D, x0, t0, nsteps, rollout);
-  } else {
-    cudaError_t e = cudaFuncSetAttribute(k_forward<GL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_forward<GL><<<T.Bp / 32, 32, smem, s>>>(T, D, x0, t0, nsteps, rollout);
-  }
+template <class RV, bool REC>
+static cudaError_t launch_forward_t(const DevTopo& T, const DevPtrs& D, const float* x0, int t0, int nsteps,
+                                    int rollout, cudaStream_t s) {
+  const size_t smem = SM_BYTES(T);
+  cudaError_t e = cudaFuncSetAttribute(k_forward<RV, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_forward<RV, REC><<<T.Bp / 32, 32, smem, s>>>(T, D, x0, t0, nsteps, rollout);
   return cudaGetLastError();
+}
+cudaError_t launch_forward(const DevTopo& T, const DevPtrs& D, const float* x0, int t0, int nsteps, int rollout,
+                           int record, cudaStream_t s) {
+  if (T.sm_rows >= 0)
+    return record ? launch_forward_t<SL, true>(T, D, x0, t0, nsteps, rollout, s)
+                  : launch_forward_t<SL, false>(T, D, x0, t0, nsteps, rollout, s);
+  return record ? launch_forward_t<GL, true>(T, D, x0, t0, nsteps, rollout, s)
+                : launch_forward_t<GL, false>(T, D, x0, t0, nsteps, rollout, s);
 }
 cudaError_t launch_backward(const DevTopo& T, const DevPtrs& D, cudaStream_t s) {
   size_t smem = SM_BYTES(T);

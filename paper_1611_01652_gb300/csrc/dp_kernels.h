@@ -10,7 +10,7 @@ cudaError_t launch_state_out(int B, int Bp, int nf, const float* src, float* dst
 cudaError_t launch_param_out(int B, int Bp, int o, int n, const float* src, float* dst, cudaStream_t s);
 cudaError_t launch_pad_scalar(int B, int Bp, const float* src, float* dst, cudaStream_t s);
 cudaError_t launch_forward(const DevTopo& T, const DevPtrs& D, const float* x0, int t0, int nsteps, int rollout,
-                           cudaStream_t s);
+                           int record, cudaStream_t s);
 cudaError_t launch_backward(const DevTopo& T, const DevPtrs& D, cudaStream_t s);
 cudaError_t launch_dw(const float* del, const float* act, int M, int C, size_t N, float* partial, int splits,
                       size_t chunk, cudaStream_t s);

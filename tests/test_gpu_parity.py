@@ -220,12 +220,13 @@ def test_two_spheres_gradients():
     check_grads(m, 60, ("state0", "sph_rad", "sph_off", "mass", "inertia", "sph_mu", "sph_e"), range(4))
 
 
-@pytest.mark.parametrize("fp32,T", [(1, 40), (0, 10)])
-def test_quadruped_gradients_controller(fp32, T):
+@pytest.mark.parametrize("fp32,T,ckpt", [(1, 40, None), (0, 10, None), (1, 40, 8)])
+def test_quadruped_gradients_controller(fp32, T, ckpt):
     """Gradient w.r.t. every controller weight, the initial state and the model parameters
-    (fp32 controller over 40 steps; bfloat16 controller over 10 steps, before rounding flips)."""
+    (fp32 controller over 40 steps; bfloat16 controller over 10 steps, before rounding flips);
+    full solver tape recorded by the rollout, or 8-step checkpoint segments recomputed."""
     m = WL.quadruped(B=4, horizon=T)
     m.ctrl_fp32 = fp32
     g, Wsum = check_grads(m, T, ("state0", "mass", "inertia", "anchor", "motor", "sph_off", "sph_rad"), range(4),
-                          with_W=True)
+                          ckpt_every=ckpt, with_W=True)
     assert rel_err(g["W"], Wsum) <= GRAD_RTOL
