@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -342,6 +343,9 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
     T.dump_rows = r;
   }
   T.n_params = (int)np_;
+  T.topo_id = match_compiled_topology(T, T.nb, T.nj, T.ns, T.np, d->joint_type, d->joint_body, d->joint_flags,
+                                      d->sphere_body, d->pair_sphere);
+  if (getenv("DP_FORCE_RUNTIME_TOPOLOGY")) T.topo_id = 0;
   w->n_params = np_;
   w->w_total = wtot;
   w->Tf = T;

@@ -39,6 +39,7 @@ struct DevTopo {
   int nb, nj, ns, np, nslots;
   int iters, horizon, features, imu_body, loss_kind, loss_mode, loss_body;
   int n_layers, skip, n_params, n_motors, ctrl_round;  // ctrl_round: 1 = bfloat16 storage points
+  int topo_id;  // 0: run-time topology loops; otherwise the compiled topology with this id
   int widths[DPK_MAXL + 1];
   int w_off[DPK_MAXL + 2];   // offset of layer l's W[out][in] in the flat weights (l = n_layers: skip)
   float gravity[3], dt, ground_z, beta, gamma, slop, clock_hz;

@@ -9,6 +9,11 @@
 
 #define FULLMASK 0xffffffffu
 
+// Tag of the run-time topology path (compile-time topologies are in dp_static.cuh).
+struct DynTopo {
+  static constexpr int id = 0;
+};
+
 // Views of one lane's data. RV is the constraint-row view: shared memory (SL) when the rows of
 // 32 instances fit next to the rest of the warp's working set, else global memory (GL).
 template <class RV>
@@ -436,10 +441,13 @@ __device__ void integrate(const DevTopo& T, const SL& X) {
 }
 
 // One full step x_t -> x_{t+1} in place on X. Returns the loss term of x_{t+1}.
+template <class Q, bool TAPE, class RV>
+__device__ void pgs_solve_static(const DevTopo& T, const LaneT<RV>& L, const SL& X, const TapeStep& tp);
+
 // One full step x_t -> x_{t+1} in place on X. With TAPE the step's solver tape is written to
 // slot `ts` of the tape (rows are copied there when they are assembled on chip) and, when
 // `dump_col` is given, the controller activations are stored in the dump column.
-template <bool TAPE, class RV, class AV>
+template <bool TAPE, class Q = DynTopo, class RV, class AV>
 __device__ float step_forward(const DevTopo& T, const DevPtrs& D, const LaneT<RV>& L, const SL& X, const AV* act, int t,
                               uint8_t* active_out, int ts = 0, float* dump_col = nullptr) {
   hinge_kinematics(T, L, X);
@@ -468,7 +476,10 @@ __device__ float step_forward(const DevTopo& T, const DevPtrs& D, const LaneT<RV
     float* dst = tp.rows + L.i;
     for (int f = 0; f < T.nslots * RF_N; ++f) dst[f * T.Bp] = L.rows[f];
   }
-  pgs_solve<TAPE>(T, L, X, tp);
+  if constexpr (Q::id == 0)
+    pgs_solve<TAPE>(T, L, X, tp);
+  else
+    pgs_solve_static<Q, TAPE>(T, L, X, tp);
   integrate(T, X);
   float w = loss_weight(T, t + 1);
   return w != 0.f ? w * loss_value(T, L, X) : 0.f;

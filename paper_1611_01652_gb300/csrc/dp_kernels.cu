@@ -3,7 +3,7 @@
 // and layout transposes.
 #include <cuda_runtime.h>
 
-#include "dp_adjoint.cuh"
+#include "dp_static.cuh"
 #include "dp_kernels.h"
 
 extern __shared__ float g_smem[];
@@ -87,7 +87,7 @@ __device__ __forceinline__ GL row_view<GL>(const DevTopo& T, const DevPtrs& D, f
 // t0. With rollout != 0 it starts from x0, stores checkpoints every ckpt_every steps and the
 // per-instance loss of Eq. L; with REC it also records every step's solver tape and
 // controller activations for the reverse pass.
-template <class RV, bool REC>
+template <class RV, bool REC, class Q>
 __global__ void __launch_bounds__(32, 1) k_forward(const __grid_constant__ DevTopo T, const __grid_constant__ DevPtrs D,
                                                     const float* __restrict__ x0, int t0, int nsteps, int rollout) {
   const int lane = threadIdx.x;
@@ -110,9 +110,9 @@ __global__ void __launch_bounds__(32, 1) k_forward(const __grid_constant__ DevTo
     }
     uint8_t* ao = (D.active && i < B) ? D.active + ((size_t)k * B + i) * T.nslots : nullptr;
     if (REC)
-      loss += step_forward<true>(T, D, L, X, act, t, ao, t, T.n_layers > 0 ? D.dump + (size_t)t * T.Bp + i : nullptr);
+      loss += step_forward<true, Q>(T, D, L, X, act, t, ao, t, T.n_layers > 0 ? D.dump + (size_t)t * T.Bp + i : nullptr);
     else
-      loss += step_forward<false>(T, D, L, X, act, t, ao);
+      loss += step_forward<false, Q>(T, D, L, X, act, t, ao);
   }
   if (rollout && D.traj && i < B)
     for (int f = 0; f < 18 * T.nb; ++f) D.traj[((size_t)(t0 + nsteps) * B + i) * 18 * T.nb + f] = X[f];
@@ -133,6 +133,7 @@ struct BwdCtx {
 };
 
 // Reverse of step t from its tape slot ts, with x_t and x_{t+1} in global memory.
+template <class Q>
 __device__ void reverse_step(const DevTopo& T, const DevPtrs& D, const BwdCtx& C, int t, int ts, const float* x_t,
                              const float* x_t1) {
   const int Bp = T.Bp, i = C.i;
@@ -162,7 +163,10 @@ __device__ void reverse_step(const DevTopo& T, const DevPtrs& D, const BwdCtx& C
   }
   for (int q = 0; q < T.nslots * RC_N; ++q) C.RC[q] = 0.f;
   integrate_reverse(T, Bl, C.X, C.XB, C.VB);
-  pgs_reverse(T, Bl, C.X, C.VB, C.RC, tp);
+  if constexpr (Q::id == 0)
+    pgs_reverse(T, Bl, C.X, C.VB, C.RC, tp);
+  else
+    pgs_reverse_static<Q>(T, Bl, C.X, C.VB, C.RC, tp);
   rows_reverse(T, Bl, C.XB, C.VB, C.RC);
   external_reverse(T, Bl, C.XB, C.VB);
   if (T.n_layers > 0) {
@@ -177,6 +181,7 @@ __device__ void reverse_step(const DevTopo& T, const DevPtrs& D, const BwdCtx& C
 
 // Reverse mode through the last rollout, last step first. With a full tape every step is read
 // from it; otherwise each checkpoint segment (last first) is recomputed with its tape.
+template <class Q>
 __global__ void __launch_bounds__(32, 1) k_backward(const __grid_constant__ DevTopo T, const __grid_constant__ DevPtrs D) {
   const int lane = threadIdx.x;
   const int i = blockIdx.x * 32 + lane;
@@ -190,7 +195,7 @@ __global__ void __launch_bounds__(32, 1) k_backward(const __grid_constant__ DevT
   const size_t sbytes = (size_t)nf * Bp;
   if (D.tape_full) {
     for (int t = T.horizon - 1; t >= 0; --t)
-      reverse_step(T, D, C, t, t, D.ckpt + (size_t)t * sbytes, t + 1 < T.horizon ? D.ckpt + (size_t)(t + 1) * sbytes : D.state);
+      reverse_step<Q>(T, D, C, t, t, D.ckpt + (size_t)t * sbytes, t + 1 < T.horizon ? D.ckpt + (size_t)(t + 1) * sbytes : D.state);
   } else {
     const int K = D.ckpt_every;
     for (int c = D.n_ckpt - 1; c >= 0; --c) {
@@ -204,11 +209,11 @@ __global__ void __launch_bounds__(32, 1) k_backward(const __grid_constant__ DevT
         const size_t n = (size_t)t * Bp + i;
         GW aw[DPK_MAXL + 1];
         for (int l = 0; l <= DPK_MAXL; ++l) aw[l] = GW{D.dump + (size_t)T.dump_act[l] * N + n, N};
-        step_forward<true>(T, D, L, C.X, aw, t, nullptr, t - ta);
+        step_forward<true, Q>(T, D, L, C.X, aw, t, nullptr, t - ta);
       }
       copy_state_from_smem(T, D.seg + (size_t)(tb - ta) * sbytes, i, C.X);
       for (int t = tb - 1; t >= ta; --t)
-        reverse_step(T, D, C, t, t - ta, D.seg + (size_t)(t - ta) * sbytes, D.seg + (size_t)(t - ta + 1) * sbytes);
+        reverse_step<Q>(T, D, C, t, t - ta, D.seg + (size_t)(t - ta) * sbytes, D.seg + (size_t)(t - ta + 1) * sbytes);
     }
   }
   if (T.loss_kind == 3) {  // initial term -a.q(x_0) of the displacement loss
@@ -315,29 +320,54 @@ cudaError_t launch_pad_scalar(int B, int Bp, const float* src, float* dst, cudaS
   k_pad_scalar<<<(Bp + 127) / 128, 128, 0, s>>>(B, Bp, src, dst);
   return cudaGetLastError();
 }
-template <class RV, bool REC>
+template <class RV, bool REC, class Q>
 static cudaError_t launch_forward_t(const DevTopo& T, const DevPtrs& D, const float* x0, int t0, int nsteps,
                                     int rollout, cudaStream_t s) {
   const size_t smem = SM_BYTES(T);
-  cudaError_t e = cudaFuncSetAttribute(k_forward<RV, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_forward<RV, REC, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_forward<RV, REC><<<T.Bp / 32, 32, smem, s>>>(T, D, x0, t0, nsteps, rollout);
+  k_forward<RV, REC, Q><<<T.Bp / 32, 32, smem, s>>>(T, D, x0, t0, nsteps, rollout);
   return cudaGetLastError();
 }
 cudaError_t launch_forward(const DevTopo& T, const DevPtrs& D, const float* x0, int t0, int nsteps, int rollout,
                            int record, cudaStream_t s) {
+  // the compiled-topology path keeps its rows on chip; otherwise the run-time path
+  if (T.topo_id == QuadrupedTopo::id && T.sm_rows >= 0)
+    return record ? launch_forward_t<SL, true, QuadrupedTopo>(T, D, x0, t0, nsteps, rollout, s)
+                  : launch_forward_t<SL, false, QuadrupedTopo>(T, D, x0, t0, nsteps, rollout, s);
   if (T.sm_rows >= 0)
-    return record ? launch_forward_t<SL, true>(T, D, x0, t0, nsteps, rollout, s)
-                  : launch_forward_t<SL, false>(T, D, x0, t0, nsteps, rollout, s);
-  return record ? launch_forward_t<GL, true>(T, D, x0, t0, nsteps, rollout, s)
-                : launch_forward_t<GL, false>(T, D, x0, t0, nsteps, rollout, s);
+    return record ? launch_forward_t<SL, true, DynTopo>(T, D, x0, t0, nsteps, rollout, s)
+                  : launch_forward_t<SL, false, DynTopo>(T, D, x0, t0, nsteps, rollout, s);
+  return record ? launch_forward_t<GL, true, DynTopo>(T, D, x0, t0, nsteps, rollout, s)
+                : launch_forward_t<GL, false, DynTopo>(T, D, x0, t0, nsteps, rollout, s);
+}
+template <class Q>
+static cudaError_t launch_backward_q(const DevTopo& T, const DevPtrs& D, cudaStream_t s) {
+  size_t smem = SM_BYTES(T);
+  cudaError_t e = cudaFuncSetAttribute(k_backward<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_backward<Q><<<T.Bp / 32, 32, smem, s>>>(T, D);
+  return cudaGetLastError();
 }
 cudaError_t launch_backward(const DevTopo& T, const DevPtrs& D, cudaStream_t s) {
-  size_t smem = SM_BYTES(T);
-  cudaError_t e = cudaFuncSetAttribute(k_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_backward<<<T.Bp / 32, 32, smem, s>>>(T, D);
-  return cudaGetLastError();
+  if (T.topo_id == QuadrupedTopo::id) return launch_backward_q<QuadrupedTopo>(T, D, s);
+  return launch_backward_q<DynTopo>(T, D, s);
+}
+
+// Compiled topology matching a run-time one (0: none). The compiled schedule must also equal
+// the run-time schedule slot for slot.
+int match_compiled_topology(const DevTopo& T, int nb, int nj, int ns, int np, const int* jtype, const int* jbody,
+                            const int* jflags, const int* sbody, const int* pair) {
+  if (topo_matches<QuadrupedTopo>(nb, nj, ns, np, jtype, jbody, jflags, sbody, pair)) {
+    const SlotTab& S = QuadrupedTopo::S;
+    if (S.n != T.nslots) return 0;
+    for (int q = 0; q < S.n; ++q)
+      if (S.kind[q] != T.skind[q] || S.a[q] != T.sa[q] || S.b[q] != T.sb[q] || S.order[q] != T.order[q] ||
+          S.normal[q] != T.snormal[q] || S.sub[q] != T.ssub[q] || S.idx[q] != T.sidx[q])
+        return 0;
+    return QuadrupedTopo::id;
+  }
+  return 0;
 }
 cudaError_t launch_dw(const float* del, const float* act, int M, int C, size_t N, float* partial, int splits,
                       size_t chunk, cudaStream_t s) {

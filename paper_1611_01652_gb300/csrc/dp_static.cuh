@@ -1,0 +1,376 @@
+// Compile-time specialisation of the projected Gauss-Seidel sweeps (forward and reverse) for
+// robot topologies known when the library is built. The slot schedule is computed by constexpr
+// code from the same rules as the run-time path (canonical slot order, greedy colouring,
+// colour-major sweep), so slot kinds, bodies and the sweep order are constants: the row loop is
+// fully unrolled, body velocities and impulses live in registers and every shared-memory row
+// field is read at a constant offset. A world whose topology matches one of these uses them;
+// any other topology uses the run-time loops.
+#pragma once
+#include <utility>
+
+#include "dp_adjoint.cuh"
+
+struct TopoDesc {
+  int nb, nj, ns, np;
+  int jtype[DPK_MAXJ], ja[DPK_MAXJ], jb[DPK_MAXJ], jflags[DPK_MAXJ];
+  int sbody[DPK_MAXS], pk[DPK_MAXP], pl[DPK_MAXP];
+};
+
+struct SlotTab {
+  int n;
+  int kind[DPK_MAXSLOT], idx[DPK_MAXSLOT], sub[DPK_MAXSLOT], a[DPK_MAXSLOT], b[DPK_MAXSLOT], normal[DPK_MAXSLOT],
+      colour[DPK_MAXSLOT], order[DPK_MAXSLOT];
+};
+
+constexpr void slot_push(SlotTab& S, int kind, int idx, int sub, int a, int b, int normal) {
+  S.kind[S.n] = kind; S.idx[S.n] = idx; S.sub[S.n] = sub; S.a[S.n] = a; S.b[S.n] = b; S.normal[S.n] = normal;
+  ++S.n;
+}
+
+constexpr SlotTab build_schedule(const TopoDesc& d) {
+  SlotTab S{};
+  for (int j = 0; j < d.nj; ++j) {
+    for (int k = 0; k < 3; ++k) slot_push(S, RK_JLIN, j, k, d.ja[j], d.jb[j], -1);
+    if (d.jtype[j] == 1)
+      for (int k = 0; k < 2; ++k) slot_push(S, RK_JANG, j, k, d.ja[j], d.jb[j], -1);
+  }
+  for (int j = 0; j < d.nj; ++j)
+    if (d.jtype[j] == 1 && (d.jflags[j] & 1)) slot_push(S, RK_LIMIT, j, 0, d.ja[j], d.jb[j], -1);
+  for (int j = 0; j < d.nj; ++j)
+    if (d.jtype[j] == 1 && (d.jflags[j] & 2)) slot_push(S, RK_MOTOR, j, 0, d.ja[j], d.jb[j], -1);
+  for (int q = 0; q < d.ns; ++q) {
+    const int n = S.n;
+    slot_push(S, RK_GN, q, 0, d.sbody[q], -1, -1);
+    slot_push(S, RK_GT, q, 0, d.sbody[q], -1, n);
+    slot_push(S, RK_GT, q, 1, d.sbody[q], -1, n);
+  }
+  for (int q = 0; q < d.np; ++q) {
+    const int n = S.n;
+    const int a = d.sbody[d.pk[q]], b = d.sbody[d.pl[q]];
+    slot_push(S, RK_PN, q, 0, a, b, -1);
+    slot_push(S, RK_PT, q, 0, a, b, n);
+    slot_push(S, RK_PT, q, 1, a, b, n);
+  }
+  for (int i = 0; i < S.n; ++i) {
+    bool used[DPK_MAXSLOT + 1] = {};
+    for (int k = 0; k < i; ++k) {
+      const bool share = (S.a[i] >= 0 && (S.a[i] == S.a[k] || S.a[i] == S.b[k])) ||
+                         (S.b[i] >= 0 && (S.b[i] == S.a[k] || S.b[i] == S.b[k]));
+      if (share) used[S.colour[k]] = true;
+    }
+    int c = 0;
+    while (used[c]) ++c;
+    S.colour[i] = c;
+  }
+  // stable sort of slot indices by colour (insertion sort)
+  for (int i = 0; i < S.n; ++i) S.order[i] = i;
+  for (int i = 1; i < S.n; ++i) {
+    const int x = S.order[i];
+    int j = i - 1;
+    while (j >= 0 && S.colour[S.order[j]] > S.colour[x]) {
+      S.order[j + 1] = S.order[j];
+      --j;
+    }
+    S.order[j + 1] = x;
+  }
+  return S;
+}
+
+// The quadruped of the benchmark: torso (body 0), legs l = 0..3 with an upper link 1+2l on a
+// hip hinge and a lower link 2+2l on a knee hinge, both with limit and servo; a foot sphere on
+// each lower link and four spheres inside the torso.
+struct QuadrupedTopo {
+  static constexpr TopoDesc desc = {
+      9, 8, 8, 0,
+      {1, 1, 1, 1, 1, 1, 1, 1},
+      {0, 1, 0, 3, 0, 5, 0, 7},
+      {1, 2, 3, 4, 5, 6, 7, 8},
+      {3, 3, 3, 3, 3, 3, 3, 3},
+      {2, 4, 6, 8, 0, 0, 0, 0},
+      {},
+      {}};
+  static constexpr SlotTab S = build_schedule(desc);
+  static constexpr int NB = desc.nb;
+  static constexpr int NS = S.n;
+  static constexpr int id = 1;
+};
+
+// Host-side check: does the descriptor's topology equal a compiled one? Returns its id or 0.
+template <class Q>
+inline bool topo_matches(int nb, int nj, int ns, int np, const int* jtype, const int* jbody, const int* jflags,
+                         const int* sbody, const int* pair) {
+  const TopoDesc& d = Q::desc;
+  if (nb != d.nb || nj != d.nj || ns != d.ns || np != d.np) return false;
+  for (int j = 0; j < nj; ++j)
+    if (jtype[j] != d.jtype[j] || jbody[2 * j] != d.ja[j] || jbody[2 * j + 1] != d.jb[j] || jflags[j] != d.jflags[j])
+      return false;
+  for (int q = 0; q < ns; ++q)
+    if (sbody[q] != d.sbody[q]) return false;
+  for (int q = 0; q < np; ++q)
+    if (pair[2 * q] != d.pk[q] || pair[2 * q + 1] != d.pl[q]) return false;
+  return true;
+}
+
+// ---------------------------------------------------------------------------- helpers
+template <class F, int... I>
+__device__ __forceinline__ void static_for_impl(F&& f, std::integer_sequence<int, I...>) {
+  (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+template <int KIND, int SUB>
+__device__ __forceinline__ constexpr bool lin_is_constant() {
+  return KIND == RK_JLIN || KIND == RK_GN || KIND == RK_GT;
+}
+template <int KIND, int SUB>
+__device__ __forceinline__ float3 const_lin() {
+  if (KIND == RK_JLIN) return f3(SUB == 0 ? 1.f : 0.f, SUB == 1 ? 1.f : 0.f, SUB == 2 ? 1.f : 0.f);
+  if (KIND == RK_GN) return f3(0.f, 0.f, 1.f);
+  if (KIND == RK_GT) return f3(SUB == 0 ? 1.f : 0.f, SUB == 1 ? 1.f : 0.f, 0.f);
+  return f3(0.f, 0.f, 0.f);
+}
+template <int KIND>
+__device__ __forceinline__ constexpr bool lin_is_zero() {
+  return KIND == RK_JANG || KIND == RK_LIMIT || KIND == RK_MOTOR;
+}
+template <int KIND>
+__device__ __forceinline__ constexpr bool maybe_inactive() {
+  return KIND == RK_LIMIT || KIND >= RK_GN;
+}
+
+// ---------------------------------------------------------------------------- forward sweeps
+template <class Q, bool TAPE, class RV>
+__device__ void pgs_solve_static(const DevTopo& T, const LaneT<RV>& L, const SL& X, const TapeStep& tp) {
+  constexpr int NB = Q::NB, NS = Q::NS;
+  const SL& S = L.S;
+  const int Bp = T.Bp;
+  float v[NB][6], im[NB], lam[NS];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v[b][k] = X[18 * b + 12 + k];
+    im[b] = S[T.sm_invm + b];
+  }
+#pragma unroll
+  for (int s = 0; s < NS; ++s) lam[s] = 0.f;
+  const float gamma = T.gamma;
+  for (int it = 0; it < T.iters; ++it) {
+    static_for<NS>([&](auto OI) {
+      constexpr int s = Q::S.order[decltype(OI)::value];
+      constexpr int kind = Q::S.kind[s], sub = Q::S.sub[s], a = Q::S.a[s], b = Q::S.b[s];
+      const RV R = L.rows.at(s * RF_N);
+      const float meff = R[RF_MEFF];
+      if (maybe_inactive<kind>() && !__any_sync(FULLMASK, meff != 0.f)) return;
+      float3 lin;
+      if (lin_is_constant<kind, sub>()) lin = const_lin<kind, sub>();
+      else if (lin_is_zero<kind>()) lin = f3(0.f, 0.f, 0.f);
+      else lin = R.v3(RF_LIN);
+      float Jv = 0.f;
+      float3 angA = f3(0.f, 0.f, 0.f), angB = angA;
+      if (a >= 0) {
+        angA = R.v3(RF_ANGA);
+        Jv += lin.x * v[a][0] + lin.y * v[a][1] + lin.z * v[a][2] + angA.x * v[a][3] + angA.y * v[a][4] + angA.z * v[a][5];
+      }
+      if (b >= 0) {
+        angB = R.v3(RF_ANGB);
+        Jv += angB.x * v[b][3] + angB.y * v[b][4] + angB.z * v[b][5] - (lin.x * v[b][0] + lin.y * v[b][1] + lin.z * v[b][2]);
+      }
+      const float l0 = lam[s];
+      const float pre = l0 - meff * (Jv + R[RF_BIAS] + gamma * l0);
+      float lo, hi;
+      if constexpr (kind == RK_GT || kind == RK_PT) {
+        constexpr int nrm = Q::S.normal[s];
+        hi = R[RF_BND] * lam[nrm];
+        lo = -hi;
+      } else if constexpr (kind == RK_MOTOR) {
+        hi = R[RF_BND];
+        lo = -hi;
+      } else if constexpr (kind == RK_JLIN || kind == RK_JANG) {
+        lo = -__int_as_float(0x7f800000);
+        hi = __int_as_float(0x7f800000);
+      } else {
+        lo = 0.f;
+        hi = __int_as_float(0x7f800000);
+      }
+      const int br = pre < lo ? 1 : (pre > hi ? 2 : 0);
+      const float ln = br == 1 ? lo : (br == 2 ? hi : pre);
+      const float dl = ln - l0;
+      lam[s] = ln;
+      if (a >= 0) {
+        const float c = dl * im[a];
+        const float3 IA = R.v3(RF_IA);
+        v[a][0] += c * lin.x; v[a][1] += c * lin.y; v[a][2] += c * lin.z;
+        v[a][3] += dl * IA.x; v[a][4] += dl * IA.y; v[a][5] += dl * IA.z;
+      }
+      if (b >= 0) {
+        const float c = dl * im[b];
+        const float3 IB = R.v3(RF_IB);
+        v[b][0] -= c * lin.x; v[b][1] -= c * lin.y; v[b][2] -= c * lin.z;
+        v[b][3] += dl * IB.x; v[b][4] += dl * IB.y; v[b][5] += dl * IB.z;
+      }
+      if (TAPE) {
+        const int o = (it * NS + s) * Bp + L.i;
+        tp.lam[o] = ln;
+        tp.br[o] = (uint8_t)br;
+      }
+    });
+    if (TAPE) {
+      float* vi = tp.viter + (size_t)it * NB * 6 * Bp + L.i;
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) vi[(6 * b + k) * Bp] = v[b][k];
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) X[18 * b + 12 + k] = v[b][k];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) S[T.sm_lam + s] = lam[s];
+}
+
+// ---------------------------------------------------------------------------- reverse sweeps
+// Same arithmetic as pgs_reverse with constant slots: working velocities and their adjoints in
+// registers, impulse adjoints and row-adjoint accumulators in shared memory.
+template <class Q, class RV>
+__device__ void pgs_reverse_static(const DevTopo& T, const BLaneT<RV>& B, const SL& X, const SL& VB, const SL& RC,
+                                   const TapeStep& tp) {
+  constexpr int NB = Q::NB, NS = Q::NS;
+  const LaneT<RV>& L = B.L;
+  const SL& S = L.S;
+  const int Bp = T.Bp;
+  const float gamma = T.gamma;
+  float v[NB][6], vb[NB][6], im[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) vb[b][k] = VB[6 * b + k];
+    im[b] = S[T.sm_invm + b];
+  }
+#pragma unroll
+  for (int s = 0; s < NS; ++s) S[T.sm_lam + s] = 0.f;
+  for (int it = T.iters - 1; it >= 0; --it) {
+    {
+      const float* vi = tp.viter + (size_t)it * NB * 6 * Bp + L.i;
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v[b][k] = vi[(6 * b + k) * Bp];
+    }
+    static_for<NS>([&](auto RI) {
+      constexpr int s = Q::S.order[NS - 1 - decltype(RI)::value];
+      constexpr int kind = Q::S.kind[s], sub = Q::S.sub[s], a = Q::S.a[s], b = Q::S.b[s];
+      const RV R = L.rows.at(s * RF_N);
+      const float meff = R[RF_MEFF];
+      if (maybe_inactive<kind>() && !__any_sync(FULLMASK, meff != 0.f)) return;
+      float3 lin;
+      if (lin_is_constant<kind, sub>()) lin = const_lin<kind, sub>();
+      else if (lin_is_zero<kind>()) lin = f3(0.f, 0.f, 0.f);
+      else lin = R.v3(RF_LIN);
+      const float3 angA = a >= 0 ? R.v3(RF_ANGA) : f3(0.f, 0.f, 0.f);
+      const float3 angB = b >= 0 ? R.v3(RF_ANGB) : f3(0.f, 0.f, 0.f);
+      const float bias = R[RF_BIAS];
+      const int o = (it * NS + s) * Bp + L.i;
+      const float la = tp.lam[o];
+      const float lb = it > 0 ? tp.lam[o - NS * Bp] : 0.f;
+      const int br = tp.br[o];
+      const float dl = la - lb;
+      float dbar = 0.f;
+      float3 va = f3(0.f, 0.f, 0.f), wa = va, vb3 = va, wb3 = va, vba = va, wba = va, vbb = va, wbb = va;
+      float3 IA = va, IB = va;
+      if (a >= 0) {
+        IA = R.v3(RF_IA);
+        const float c = dl * im[a];
+        v[a][0] -= c * lin.x; v[a][1] -= c * lin.y; v[a][2] -= c * lin.z;
+        v[a][3] -= dl * IA.x; v[a][4] -= dl * IA.y; v[a][5] -= dl * IA.z;
+        va = f3(v[a][0], v[a][1], v[a][2]);
+        wa = f3(v[a][3], v[a][4], v[a][5]);
+        vba = f3(vb[a][0], vb[a][1], vb[a][2]);
+        wba = f3(vb[a][3], vb[a][4], vb[a][5]);
+        dbar += im[a] * dot3(lin, vba) + dot3(IA, wba);
+      }
+      if (b >= 0) {
+        IB = R.v3(RF_IB);
+        const float c = dl * im[b];
+        v[b][0] += c * lin.x; v[b][1] += c * lin.y; v[b][2] += c * lin.z;
+        v[b][3] -= dl * IB.x; v[b][4] -= dl * IB.y; v[b][5] -= dl * IB.z;
+        vb3 = f3(v[b][0], v[b][1], v[b][2]);
+        wb3 = f3(v[b][3], v[b][4], v[b][5]);
+        vbb = f3(vb[b][0], vb[b][1], vb[b][2]);
+        wbb = f3(vb[b][3], vb[b][4], vb[b][5]);
+        dbar += -im[b] * dot3(lin, vbb) + dot3(IB, wbb);
+      }
+      float3 linb = dl * ((a >= 0 ? im[a] : 0.f) * vba - (b >= 0 ? im[b] : 0.f) * vbb);
+      float3 angAb = f3(0.f, 0.f, 0.f), angBb = angAb;
+      if (a >= 0) {
+        const float3 g = dl * wba;
+        float ia[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) ia[q] = S[T.sm_iinv + 6 * a + q];
+        angAb += symv(ia, g);
+        const int ib9 = T.sm_iinvb + 9 * a;
+        S[ib9 + 0] += g.x * angA.x; S[ib9 + 1] += g.x * angA.y; S[ib9 + 2] += g.x * angA.z;
+        S[ib9 + 3] += g.y * angA.x; S[ib9 + 4] += g.y * angA.y; S[ib9 + 5] += g.y * angA.z;
+        S[ib9 + 6] += g.z * angA.x; S[ib9 + 7] += g.z * angA.y; S[ib9 + 8] += g.z * angA.z;
+        if (!lin_is_zero<kind>()) S[T.sm_invmb + a] += dl * dot3(lin, vba);
+      }
+      if (b >= 0) {
+        const float3 g = dl * wbb;
+        float ib[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) ib[q] = S[T.sm_iinv + 6 * b + q];
+        angBb += symv(ib, g);
+        const int ib9 = T.sm_iinvb + 9 * b;
+        S[ib9 + 0] += g.x * angB.x; S[ib9 + 1] += g.x * angB.y; S[ib9 + 2] += g.x * angB.z;
+        S[ib9 + 3] += g.y * angB.x; S[ib9 + 4] += g.y * angB.y; S[ib9 + 5] += g.y * angB.z;
+        S[ib9 + 6] += g.z * angB.x; S[ib9 + 7] += g.z * angB.y; S[ib9 + 8] += g.z * angB.z;
+        if (!lin_is_zero<kind>()) S[T.sm_invmb + b] -= dl * dot3(lin, vbb);
+      }
+      const float lbar_a = S[T.sm_lam + s] + dbar;
+      float pbar = 0.f;
+      const int rc = s * RC_N;
+      if (br == 0) {
+        pbar = lbar_a;
+      } else if constexpr (kind == RK_GT || kind == RK_PT) {
+        constexpr int ns_ = Q::S.normal[s];
+        const float lnrm = tp.lam[(it * NS + ns_) * Bp + L.i];
+        const float mu = R[RF_BND];
+        const float sg = br == 2 ? 1.f : -1.f;
+        RC[rc + RC_BND] += sg * lnrm * lbar_a;
+        S[T.sm_lam + ns_] += sg * mu * lbar_a;
+      } else if (kind == RK_MOTOR) {
+        RC[rc + RC_BND] += (br == 2 ? 1.f : -1.f) * lbar_a;
+      }
+      float Jv = 0.f;
+      if (a >= 0) Jv += dot3(lin, va) + dot3(angA, wa);
+      if (b >= 0) Jv += dot3(angB, wb3) - dot3(lin, vb3);
+      RC[rc + RC_MEFF] += -pbar * (Jv + bias + gamma * lb);
+      const float jvb = -meff * pbar;
+      RC[rc + RC_BIAS] += jvb;
+      if (a >= 0) {
+        vb[a][0] += jvb * lin.x; vb[a][1] += jvb * lin.y; vb[a][2] += jvb * lin.z;
+        vb[a][3] += jvb * angA.x; vb[a][4] += jvb * angA.y; vb[a][5] += jvb * angA.z;
+        linb += jvb * va;
+        angAb += jvb * wa;
+      }
+      if (b >= 0) {
+        vb[b][0] -= jvb * lin.x; vb[b][1] -= jvb * lin.y; vb[b][2] -= jvb * lin.z;
+        vb[b][3] += jvb * angB.x; vb[b][4] += jvb * angB.y; vb[b][5] += jvb * angB.z;
+        linb -= jvb * vb3;
+        angBb += jvb * wb3;
+      }
+      if (!lin_is_constant<kind, sub>() && !lin_is_zero<kind>()) RC.a3(rc + RC_LIN, linb);
+      if (a >= 0) RC.a3(rc + RC_ANGA, angAb);
+      if (b >= 0) RC.a3(rc + RC_ANGB, angBb);
+      S[T.sm_lam + s] = -dbar + pbar * (1.f - meff * gamma);
+    });
+  }
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) VB[6 * b + k] = vb[b][k];
+}

@@ -230,3 +230,13 @@ def test_quadruped_gradients_controller(fp32, T, ckpt):
     g, Wsum = check_grads(m, T, ("state0", "mass", "inertia", "anchor", "motor", "sph_off", "sph_rad"), range(4),
                           ckpt_every=ckpt, with_W=True)
     assert rel_err(g["W"], Wsum) <= GRAD_RTOL
+
+
+def test_quadruped_runtime_topology_path(monkeypatch):
+    """The quadruped normally runs the compiled-topology sweeps; the run-time topology loops
+    must give the same answers (forced here)."""
+    monkeypatch.setenv("DP_FORCE_RUNTIME_TOPOLOGY", "1")
+    m = WL.quadruped(B=8, horizon=60)
+    m.ctrl_fp32 = 1
+    compare_rollout(m, 60, range(8), min_clean=0.5)
+    check_grads(WL.quadruped(B=2, horizon=20), 20, ("state0", "anchor", "motor"), range(2))
