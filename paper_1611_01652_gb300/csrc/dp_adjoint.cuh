@@ -12,7 +12,7 @@ enum { RC_LIN = 0, RC_ANGA = 3, RC_ANGB = 6, RC_MEFF = 9, RC_BIAS = 10, RC_BND =
 template <class RV>
 struct BLaneT {
   LaneT<RV> L;
-  GC X0;        // x_t (global, [field][Bp])
+  SL X0;        // x_t (on chip)
   GL G;         // parameter gradients [field][Bp]
   GC vminus;    // velocities after the external impulses [nb*6][Bp]
 };
@@ -23,14 +23,12 @@ __device__ __forceinline__ void add_outer(const SL& XB, int base, float3 a, floa
   XB[base + 3] += a.y * b.x; XB[base + 4] += a.y * b.y; XB[base + 5] += a.y * b.z;
   XB[base + 6] += a.z * b.x; XB[base + 7] += a.z * b.y; XB[base + 8] += a.z * b.z;
 }
-__device__ __forceinline__ M3 loadRg(const GC& X, int base) {
-  M3 R;
-#pragma unroll
-  for (int k = 0; k < 9; ++k) R.m[k] = X[base + 3 + k];
-  return R;
+template <class XV>
+__device__ __forceinline__ M3 loadRg(const XV& X, int base) {
+  return loadRv(X, base);
 }
-__device__ __forceinline__ M3 body_Rg(const GC& X, int b) { return b >= 0 ? loadRg(X, 18 * b) : eye3(); }
-__device__ __forceinline__ float3 body_pg(const GC& X, int b) { return b >= 0 ? X.v3(18 * b) : f3(0.f, 0.f, 0.f); }
+template <class XV>
+__device__ __forceinline__ M3 body_Rg(const XV& X, int b) { return b >= 0 ? loadRv(X, 18 * b) : eye3(); }
 
 // ---------------------------------------------------------------- loss (Eq. L) reverse
 // Adds wgt * dl(x)/dx at state X (on-chip) into XB, and the loss point / target gradients.
@@ -50,18 +48,17 @@ __device__ void loss_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& X,
   gq = wgt * gq;
   XB.a3(18 * b, gq);
   add_outer(XB, 18 * b + 3, gq, c);
-  B.G.a3(T.o_loss_point, mtv(R, gq));
-  B.G.a3(T.o_loss_target, wgt * gy);
+  B.G.red3(T.o_loss_point, mtv(R, gq));
+  B.G.red3(T.o_loss_target, wgt * gy);
 }
 
 // ---------------------------------------------------------------- integrate + Eq. 1 reverse
 // XB holds the adjoint of x_{t+1}; on return its p/R fields hold the adjoint of x_t's p/R,
 // its v/w fields are zero, and VB holds the adjoint of the solver's output velocities.
-template <class RV>
-__device__ void integrate_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& X, const SL& XB, const SL& VB) {
+__device__ void integrate_reverse(const DevTopo& T, const GC& Xt, const SL& X, const SL& XB, const SL& VB) {
   const float h = T.dt;
   for (int b = 0; b < T.nb; ++b) {
-    M3 R = loadRg(B.X0, 18 * b);
+    M3 R = loadRg(Xt, 18 * b);
     float3 w = X.v3(18 * b + 15);  // solver output angular velocity
     M3 A;
 #pragma unroll
@@ -99,7 +96,7 @@ __device__ void integrate_reverse(const DevTopo& T, const BLaneT<RV>& B, const S
 // Replays every sweep backwards. Working velocities are reset to the stored post-sweep values at
 // each sweep boundary and un-applied row by row. S[sm_lam] holds the impulse adjoints.
 template <class RV>
-__device__ void pgs_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& X, const SL& VB, const SL& RC,
+__device__ void pgs_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& VW, const SL& VB, const SL& RC,
                             const TapeStep& tp) {
   const LaneT<RV>& L = B.L;
   const SL& S = L.S;
@@ -110,7 +107,7 @@ __device__ void pgs_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& X, 
       const float* vi = tp.viter + (size_t)it * T.nb * 6 * Bp + L.i;
       for (int b = 0; b < T.nb; ++b)
 #pragma unroll
-        for (int k = 0; k < 6; ++k) X[18 * b + 12 + k] = vi[(size_t)(6 * b + k) * Bp];
+        for (int k = 0; k < 6; ++k) VW[6 * b + k] = vi[(size_t)(6 * b + k) * Bp];
     }
     for (int oi = T.nslots - 1; oi >= 0; --oi) {
       const int s = T.order[oi];
@@ -133,10 +130,10 @@ __device__ void pgs_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& X, 
       if (a >= 0) {
         ima = S[T.sm_invm + a];
         IA = R.v3(RF_IA);
-        va = X.v3(18 * a + 12) - (dl * ima) * lin;
-        wa = X.v3(18 * a + 15) - dl * IA;
-        X.s3(18 * a + 12, va);
-        X.s3(18 * a + 15, wa);
+        va = VW.v3(6 * a) - (dl * ima) * lin;
+        wa = VW.v3(6 * a + 3) - dl * IA;
+        VW.s3(6 * a, va);
+        VW.s3(6 * a + 3, wa);
         vba = VB.v3(6 * a);
         wba = VB.v3(6 * a + 3);
         dbar += ima * dot3(lin, vba) + dot3(IA, wba);
@@ -144,10 +141,10 @@ __device__ void pgs_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& X, 
       if (b >= 0) {
         imb = S[T.sm_invm + b];
         IB = R.v3(RF_IB);
-        vb = X.v3(18 * b + 12) + (dl * imb) * lin;
-        wb = X.v3(18 * b + 15) - dl * IB;
-        X.s3(18 * b + 12, vb);
-        X.s3(18 * b + 15, wb);
+        vb = VW.v3(6 * b) + (dl * imb) * lin;
+        wb = VW.v3(6 * b + 3) - dl * IB;
+        VW.s3(6 * b, vb);
+        VW.s3(6 * b + 3, wb);
         vbb = VB.v3(6 * b);
         wbb = VB.v3(6 * b + 3);
         dbar += -imb * dot3(lin, vbb) + dot3(IB, wbb);
@@ -280,14 +277,14 @@ __device__ void rows_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& XB
           M3 Ra = loadRg(B.X0, 18 * a);
           XB.a3(18 * a, Cb);
           add_outer(XB, 18 * a + 3, rab, anca);
-          B.G.a3(T.o_anchor + 6 * idx, mtv(Ra, rab));
+          B.G.red3(T.o_anchor + 6 * idx, mtv(Ra, rab));
         } else {
-          B.G.a3(T.o_anchor + 6 * idx, rab);
+          B.G.red3(T.o_anchor + 6 * idx, rab);
         }
         M3 Rb = loadRg(B.X0, 18 * b);
         XB.a3(18 * b, -Cb);
         add_outer(XB, 18 * b + 3, rbb, ancb);
-        B.G.a3(T.o_anchor + 6 * idx + 3, mtv(Rb, rbb));
+        B.G.red3(T.o_anchor + 6 * idx + 3, mtv(Rb, rbb));
         break;
       }
       case RK_JANG: {
@@ -317,11 +314,11 @@ __device__ void rows_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& XB
         if (th <= lo_j) {  // angA = -ua, angB = ua, bias = bh (th - lo)
           uab = angBb - (a >= 0 ? angAb : f3(0.f, 0.f, 0.f));
           S[T.sm_thb + idx] += bh * biasb;
-          B.G[T.o_limit + 2 * idx] -= bh * biasb;
+          B.G.red(T.o_limit + 2 * idx, -(bh * biasb));
         } else {           // angA = ua, angB = -ua, bias = bh (hi - th)
           uab = (a >= 0 ? angAb : f3(0.f, 0.f, 0.f)) - angBb;
           S[T.sm_thb + idx] -= bh * biasb;
-          B.G[T.o_limit + 2 * idx + 1] += bh * biasb;
+          B.G.red(T.o_limit + 2 * idx + 1, bh * biasb);
         }
         S.a3(T.sm_uab + 3 * idx, uab);
         break;
@@ -329,7 +326,7 @@ __device__ void rows_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& XB
       case RK_MOTOR: {
         S.a3(T.sm_uab + 3 * idx, angBb - (a >= 0 ? angAb : f3(0.f, 0.f, 0.f)));
         S[T.sm_wstb + idx] -= biasb;
-        B.G[T.o_motor + 3 * idx + 1] += h * RC[rc + RC_BND];
+        B.G.red(T.o_motor + 3 * idx + 1, h * RC[rc + RC_BND]);
         break;
       }
       case RK_GN:
@@ -347,22 +344,22 @@ __device__ void rows_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& XB
           if (d + T.slop < 0.f) db += bh * biasb;
           if (vn < 0.f) {
             float e = L.P[T.o_sph_e + idx];
-            B.G[T.o_sph_e + idx] += vn * biasb;
+            B.G.red(T.o_sph_e + idx, vn * biasb);
             float vnb = e * biasb;
             VB.a3(6 * a, vnb * lin);
             VB.a3(6 * a + 3, vnb * angA);
             angAb += vnb * wm;
           }
         } else {
-          B.G[T.o_sph_mu + idx] += RC[rc + RC_BND];
+          B.G.red(T.o_sph_mu + idx, RC[rc + RC_BND]);
         }
         float3 rab = cross3(lin, angAb);  // angA = ra x lin (lin constant)
         float3 cb = rab + f3(0.f, 0.f, db);
         float radb = -rab.z - db;
         XB[18 * a + 2] += db;
         add_outer(XB, 18 * a + 3, cb, off);
-        B.G.a3(T.o_sph_off + 3 * idx, mtv(Ra, cb));
-        B.G[T.o_sph_rad + idx] += radb;
+        B.G.red3(T.o_sph_off + 3 * idx, mtv(Ra, cb));
+        B.G.red(T.o_sph_rad + idx, radb);
         break;
       }
       case RK_PN:
@@ -388,7 +385,7 @@ __device__ void rows_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& XB
           if (vn < 0.f) {
             float ek = L.P[T.o_sph_e + k], el = L.P[T.o_sph_e + l];
             float e = ek >= el ? ek : el;
-            B.G[T.o_sph_e + (ek >= el ? k : l)] += vn * biasb;
+            B.G.red(T.o_sph_e + (ek >= el ? k : l), vn * biasb);
             float vnb = e * biasb;
             nb += vnb * (vma - vmb);
             VB.a3(6 * a, vnb * n);
@@ -412,10 +409,10 @@ __device__ void rows_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& XB
           XB.a3(18 * a, dlb); XB.a3(18 * b, -dlb);
           add_outer(XB, 18 * a + 3, ckb, offk);
           add_outer(XB, 18 * b + 3, clb, offl);
-          B.G.a3(T.o_sph_off + 3 * k, mtv(Ra, ckb));
-          B.G.a3(T.o_sph_off + 3 * l, mtv(Rb, clb));
-          B.G[T.o_sph_rad + k] += rkb;
-          B.G[T.o_sph_rad + l] += rlb;
+          B.G.red3(T.o_sph_off + 3 * k, mtv(Ra, ckb));
+          B.G.red3(T.o_sph_off + 3 * l, mtv(Rb, clb));
+          B.G.red(T.o_sph_rad + k, rkb);
+          B.G.red(T.o_sph_rad + l, rlb);
         } else {
           float3 t1, t2;
           onb3(n, t1, t2);
@@ -431,16 +428,16 @@ __device__ void rows_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& XB
           XB.a3(18 * a, dlb); XB.a3(18 * b, -dlb);
           add_outer(XB, 18 * a + 3, ckb, offk);
           add_outer(XB, 18 * b + 3, clb, offl);
-          B.G.a3(T.o_sph_off + 3 * k, mtv(Ra, ckb));
-          B.G.a3(T.o_sph_off + 3 * l, mtv(Rb, clb));
-          B.G[T.o_sph_rad + k] += rkb;
-          B.G[T.o_sph_rad + l] += rlb;
+          B.G.red3(T.o_sph_off + 3 * k, mtv(Ra, ckb));
+          B.G.red3(T.o_sph_off + 3 * l, mtv(Rb, clb));
+          B.G.red(T.o_sph_rad + k, rkb);
+          B.G.red(T.o_sph_rad + l, rlb);
           float muk = L.P[T.o_sph_mu + k], mul = L.P[T.o_sph_mu + l];
           float mu = sqrtf(muk * mul);
           float mub = RC[rc + RC_BND];
           if (mu > 0.f) {
-            B.G[T.o_sph_mu + k] += mub * mul / (2.f * mu);
-            B.G[T.o_sph_mu + l] += mub * muk / (2.f * mu);
+            B.G.red(T.o_sph_mu + k, mub * mul / (2.f * mu));
+            B.G.red(T.o_sph_mu + l, mub * muk / (2.f * mu));
           }
         }
         break;
@@ -516,14 +513,14 @@ __device__ void external_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL
     for (int k = 0; k < 9; ++k) XB[18 * b + 3 + k] += Rb.m[k];
     XB.a3(18 * b + 12, VB.v3(6 * b));
     XB.a3(18 * b + 15, wb);
-    B.G.a3(T.o_inertia + 3 * b, f3(Ib[0], Ib[1], Ib[2]));
-    B.G[T.o_mass + b] -= S[T.sm_invmb + b] / (m * m);
+    B.G.red3(T.o_inertia + 3 * b, f3(Ib[0], Ib[1], Ib[2]));
+    B.G.red(T.o_mass + b, -(S[T.sm_invmb + b] / (m * m)));
   }
 }
 
 // ---------------------------------------------------------------- servo reverse
 template <class RV, class AV>
-__device__ void servo_reverse(const DevTopo& T, const BLaneT<RV>& B, const AV& u, const AV& ub) {
+__device__ void servo_reverse(const DevTopo& T, const BLaneT<RV>& B, const AV& u, const AV& ubd, const SL& ub) {
   const SL& S = B.L.S;
   const int nout = T.n_layers > 0 ? T.widths[T.n_layers] : 0;
   for (int o = 0; o < nout; ++o) ub[o] = 0.f;
@@ -536,11 +533,12 @@ __device__ void servo_reverse(const DevTopo& T, const BLaneT<RV>& B, const AV& u
       float um = (m < nout) ? u[m] : 0.f;
       if (m < nout) ub[m] = k * g;
       S[T.sm_thb + j] -= k * g;
-      B.G[T.o_motor + 3 * j] += (um - S[T.sm_th + j]) * g;
+      B.G.red(T.o_motor + 3 * j, (um - S[T.sm_th + j]) * g);
     } else {
-      B.G[T.o_motor + 3 * j + 2] += (br == 2.f ? 1.f : -1.f) * g;
+      B.G.red(T.o_motor + 3 * j + 2, (br == 2.f ? 1.f : -1.f) * g);
     }
   }
+  for (int o = 0; o < nout; ++o) ubd[o] = ub[o];
 }
 
 // One dense layer reversed on this lane: in_bar[i] (+)= sum_o W[o][i] out_bar[o], using the
@@ -573,16 +571,26 @@ __device__ void dense_bwd(const float* __restrict__ Wn, int ni, int no, const AV
   }
 }
 
-// Controller reverse: del[l] = adjoint of layer l's pre-activation output (del[L-1] = u_bar
-// on entry). Leaves the input adjoint in sbar.
-template <class AV, class SV>
-__device__ void controller_reverse(const DevTopo& T, const DevPtrs& D, const AV* act, const AV* del, const SV& sbar) {
+// Controller reverse: zb0 holds u_bar (the adjoint of the linear output) on entry. The adjoint
+// of each layer's pre-activation output is formed on chip (ping-pong buffers zb0/zb1) and also
+// stored in the dump (del[l]) for the weight-gradient reduction. Leaves the input adjoint in sbar.
+template <class AV>
+__device__ void controller_reverse(const DevTopo& T, const DevPtrs& D, const AV* act, const AV* del, const SL& zb0,
+                                   const SL& zb1, const SL& sbar) {
   const int L = T.n_layers;
+  SL cur = zb0, nxt = zb1;
   for (int l = L - 1; l >= 0; --l) {
     const int ni = T.widths[l], no = T.widths[l + 1];
     const float* Wn = D.Wn + T.w_off[l];
-    if (l > 0) dense_bwd(Wn, ni, no, del[l], act[l], del[l - 1], true, false);
-    else dense_bwd(Wn, ni, no, del[0], act[0], sbar, false, false);
+    if (l > 0) {
+      dense_bwd(Wn, ni, no, cur, act[l], nxt, true, false);
+      for (int k = 0; k < ni; ++k) del[l - 1][k] = nxt[k];
+      const SL tmp = cur;
+      cur = nxt;
+      nxt = tmp;
+    } else {
+      dense_bwd(Wn, ni, no, cur, act[0], sbar, false, false);
+    }
   }
   if (T.skip) dense_bwd(D.Wn + T.w_off[L], T.widths[0], T.widths[L], del[L - 1], act[0], sbar, false, true);
 }
@@ -617,8 +625,8 @@ __device__ void features_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL
     k += 3;
     XB.a3(18 * b, qb);
     add_outer(XB, 18 * b + 3, qb, c);
-    B.G.a3(T.o_loss_point, mtv(R, qb));
-    B.G.a3(T.o_loss_target, -qb);
+    B.G.red3(T.o_loss_point, mtv(R, qb));
+    B.G.red3(T.o_loss_target, -qb);
   }
 }
 

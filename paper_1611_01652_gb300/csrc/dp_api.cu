@@ -188,6 +188,7 @@ void plan_smem(DevTopo& T, bool backward, int smem_floats_max) {
       o = region + acts;
     }
     T.sm_xb = T.sm_vb = T.sm_thb = T.sm_thdb = T.sm_uab = T.sm_wstb = T.sm_iinvb = T.sm_invmb = T.sm_rc = T.sm_sbar = 0;
+    T.sm_vw = T.sm_zb = 0;
   } else {
     for (int l = 0; l <= DPK_MAXL; ++l) T.sm_act[l] = 0;
     T.sm_xb = take(18 * T.nb);
@@ -200,6 +201,11 @@ void plan_smem(DevTopo& T, bool backward, int smem_floats_max) {
     T.sm_invmb = take(T.nb);
     T.sm_rc = take(12 * T.nslots);
     T.sm_sbar = take(T.n_layers > 0 ? T.widths[0] : 1);
+    T.sm_vw = take(6 * T.nb);
+    // controller-reverse ping-pong buffers: the row-adjoint region is free by then
+    int maxw = 1;
+    for (int l = 0; l <= T.n_layers && T.n_layers > 0; ++l) maxw = std::max(maxw, T.widths[l]);
+    T.sm_zb = 2 * maxw <= 12 * T.nslots ? T.sm_rc : take(2 * maxw);
   }
   T.sm_total = o;
 }

@@ -56,7 +56,8 @@ struct DevTopo {
   int16_t order[DPK_MAXSLOT];
   // shared-memory layout per warp, in units of 32 floats (one float per lane)
   int sm_x0, sm_x, sm_xb, sm_vb, sm_iinv, sm_invm, sm_th, sm_thd, sm_ua, sm_wst, sm_wbr, sm_lam, sm_u;
-  int sm_thb, sm_thdb, sm_uab, sm_wstb, sm_iinvb, sm_invmb, sm_rc, sm_sbar, sm_act[DPK_MAXL + 1], sm_rows, sm_total;
+  int sm_thb, sm_thdb, sm_uab, sm_wstb, sm_iinvb, sm_invmb, sm_rc, sm_sbar, sm_vw, sm_zb, sm_act[DPK_MAXL + 1], sm_rows,
+      sm_total;
   // activation/delta dump offsets (rows of [feature][T*Bp]); act l = input of layer l
   int dump_act[DPK_MAXL + 1], dump_del[DPK_MAXL + 1], dump_rows;
 };
@@ -218,6 +219,14 @@ struct GL {
   __device__ __forceinline__ void s3(int f, float3 v) const { p[f * s] = v.x; p[(f + 1) * s] = v.y; p[(f + 2) * s] = v.z; }
   __device__ __forceinline__ void a3(int f, float3 v) const { p[f * s] += v.x; p[(f + 1) * s] += v.y; p[(f + 2) * s] += v.z; }
   __device__ __forceinline__ GL at(int f) const { return GL{p + f * s, s}; }
+  // fire-and-forget accumulation (a reduction whose result is not read back): no load latency;
+  // each lane owns its addresses, and one thread's reductions to one address apply in order
+  __device__ __forceinline__ void red(int f, float v) const { atomicAdd(p + f * s, v); }
+  __device__ __forceinline__ void red3(int f, float3 v) const {
+    atomicAdd(p + f * s, v.x);
+    atomicAdd(p + (f + 1) * s, v.y);
+    atomicAdd(p + (f + 2) * s, v.z);
+  }
 };
 // Wide-stride global view (controller activation/delta columns of the [row][T*Bp] dump).
 struct GW {

@@ -141,18 +141,26 @@ __device__ void reverse_step(const DevTopo& T, const DevPtrs& D, const BwdCtx& C
   const size_t n = (size_t)t * Bp + i;
   const TapeStep tp = tape_step(T, D, ts);
   LaneT<GL> L{C.S, C.P, GL{tp.rows + i, Bp}, i};
-  BLaneT<GL> Bl{L, GC{x_t + i, Bp}, C.G, GC{tp.vminus + i, Bp}};
+  BLaneT<GL> Bl{L, C.X, C.G, GC{tp.vminus + i, Bp}};
   GW act[DPK_MAXL + 1], del[DPK_MAXL + 1];
   for (int l = 0; l <= DPK_MAXL; ++l) {
     act[l] = GW{D.dump + (size_t)T.dump_act[l] * N + n, N};
     del[l] = GW{D.dump + (size_t)T.dump_del[l] * N + n, N};
   }
+  const SL VW{C.S.p + T.sm_vw * 32}, zb0{C.S.p + T.sm_zb * 32};
+  int maxw = 1;
+  for (int l = 0; l <= T.n_layers && T.n_layers > 0; ++l) maxw = max(maxw, T.widths[l]);
+  const SL zb1{C.S.p + (T.sm_zb + maxw) * 32};
+  // loss term and integrator with x_{t+1} on chip
   copy_state_to_smem(T, x_t1, i, C.X);
-  // per-step forward quantities of x_t that the adjoints use (recomputed bit-identically)
-  hinge_kinematics(T, L, Bl.X0);
-  servo_targets(T, L, act[T.n_layers > 0 ? T.n_layers : 0]);
-  inverse_inertia(T, L, Bl.X0);
   loss_reverse(T, Bl, C.X, C.XB, loss_weight(T, t + 1) * C.dl);
+  integrate_reverse(T, GC{x_t + i, Bp}, C.X, C.XB, C.VB);
+  // x_t on chip for every later stage; its per-step forward quantities are recomputed
+  // bit-identically (hinge kinematics, servo targets, inverse inertias)
+  copy_state_to_smem(T, x_t, i, C.X);
+  hinge_kinematics(T, L, C.X);
+  servo_targets(T, L, act[T.n_layers > 0 ? T.n_layers : 0]);
+  inverse_inertia(T, L, C.X);
   for (int j = 0; j < T.nj; ++j) {
     C.S[T.sm_thb + j] = 0.f; C.S[T.sm_thdb + j] = 0.f; C.S[T.sm_wstb + j] = 0.f;
     C.S.s3(T.sm_uab + 3 * j, f3(0.f, 0.f, 0.f));
@@ -162,19 +170,18 @@ __device__ void reverse_step(const DevTopo& T, const DevPtrs& D, const BwdCtx& C
     for (int q = 0; q < 9; ++q) C.S[T.sm_iinvb + 9 * b + q] = 0.f;
   }
   for (int q = 0; q < T.nslots * RC_N; ++q) C.RC[q] = 0.f;
-  integrate_reverse(T, Bl, C.X, C.XB, C.VB);
   if constexpr (Q::id == 0)
-    pgs_reverse(T, Bl, C.X, C.VB, C.RC, tp);
+    pgs_reverse(T, Bl, VW, C.VB, C.RC, tp);
   else
     pgs_reverse_static<Q>(T, Bl, C.X, C.VB, C.RC, tp);
   rows_reverse(T, Bl, C.XB, C.VB, C.RC);
   external_reverse(T, Bl, C.XB, C.VB);
   if (T.n_layers > 0) {
-    servo_reverse(T, Bl, act[T.n_layers], del[T.n_layers - 1]);
-    controller_reverse(T, D, act, del, C.sbar);
+    servo_reverse(T, Bl, act[T.n_layers], del[T.n_layers - 1], zb0);
+    controller_reverse(T, D, act, del, zb0, zb1, C.sbar);
     features_reverse(T, Bl, C.XB, C.sbar);
   } else {
-    servo_reverse(T, Bl, act[0], act[0]);
+    servo_reverse(T, Bl, act[0], act[0], zb0);
   }
   hinge_reverse(T, Bl, C.XB);
 }
@@ -224,8 +231,8 @@ __global__ void __launch_bounds__(32, 1) k_backward(const __grid_constant__ DevT
     float3 gq = -C.dl * a;
     C.XB.a3(18 * b, gq);
     add_outer(C.XB, 18 * b + 3, gq, c);
-    C.G.a3(T.o_loss_point, mtv(R, gq));
-    C.G.a3(T.o_loss_target, -C.dl * (C.X.v3(18 * b) + mv(R, c)));
+    C.G.red3(T.o_loss_point, mtv(R, gq));
+    C.G.red3(T.o_loss_target, -C.dl * (C.X.v3(18 * b) + mv(R, c)));
   }
   for (int f = 0; f < nf; ++f) D.grad_state0[(size_t)f * Bp + i] = C.XB[f];
 }
