@@ -234,23 +234,34 @@ __device__ void pgs_solve_static(const DevTopo& T, const LaneT<RV>& L, const SL&
 }
 
 // ---------------------------------------------------------------------------- reverse sweeps
-// Same arithmetic as pgs_reverse with constant slots: working velocities and their adjoints in
-// registers, impulse adjoints and row-adjoint accumulators in shared memory.
+// Same arithmetic as pgs_reverse with constant slots: working velocities in registers; velocity
+// adjoints, impulse adjoints and row-adjoint accumulators in shared memory. Which rows are active
+// on some lane is decided once per step (a bit mask in registers), and the clamp branch enters
+// the arithmetic as a selector, so every load of a row can be issued before any of it is used.
 template <class Q, class RV>
-__device__ void pgs_reverse_static(const DevTopo& T, const BLaneT<RV>& B, const SL& X, const SL& VB, const SL& RC,
+__device__ __noinline__ void pgs_reverse_static(const DevTopo& T, const BLaneT<RV>& B, const SL& X, const SL& VB, const SL& RC,
                                    const TapeStep& tp) {
   constexpr int NB = Q::NB, NS = Q::NS;
+  constexpr int NW = (NS + 31) / 32;
   const LaneT<RV>& L = B.L;
   const SL& S = L.S;
   const int Bp = T.Bp;
   const float gamma = T.gamma;
-  float v[NB][6], vb[NB][6], im[NB];
+  float v[NB][6], im[NB];
 #pragma unroll
-  for (int b = 0; b < NB; ++b) {
+  for (int b = 0; b < NB; ++b) im[b] = S[T.sm_invm + b];
+  unsigned live[NW];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) vb[b][k] = VB[6 * b + k];
-    im[b] = S[T.sm_invm + b];
-  }
+  for (int w = 0; w < NW; ++w) live[w] = 0u;
+  static_for<NS>([&](auto SI) {
+    constexpr int s = decltype(SI)::value;
+    if constexpr (maybe_inactive<Q::S.kind[s]>()) {
+      const float meff = L.rows.at(s * RF_N)[RF_MEFF];
+      if (__any_sync(FULLMASK, meff != 0.f)) live[s >> 5] |= 1u << (s & 31);
+    } else {
+      live[s >> 5] |= 1u << (s & 31);
+    }
+  });
 #pragma unroll
   for (int s = 0; s < NS; ++s) S[T.sm_lam + s] = 0.f;
   for (int it = T.iters - 1; it >= 0; --it) {
@@ -264,44 +275,51 @@ __device__ void pgs_reverse_static(const DevTopo& T, const BLaneT<RV>& B, const 
     static_for<NS>([&](auto RI) {
       constexpr int s = Q::S.order[NS - 1 - decltype(RI)::value];
       constexpr int kind = Q::S.kind[s], sub = Q::S.sub[s], a = Q::S.a[s], b = Q::S.b[s];
+      if constexpr (maybe_inactive<kind>())
+        if (!((live[s >> 5] >> (s & 31)) & 1u)) return;
       const RV R = L.rows.at(s * RF_N);
+      // loads first
       const float meff = R[RF_MEFF];
-      if (maybe_inactive<kind>() && !__any_sync(FULLMASK, meff != 0.f)) return;
+      const float bias = R[RF_BIAS];
       float3 lin;
-      if (lin_is_constant<kind, sub>()) lin = const_lin<kind, sub>();
-      else if (lin_is_zero<kind>()) lin = f3(0.f, 0.f, 0.f);
+      if constexpr (lin_is_constant<kind, sub>()) lin = const_lin<kind, sub>();
+      else if constexpr (lin_is_zero<kind>()) lin = f3(0.f, 0.f, 0.f);
       else lin = R.v3(RF_LIN);
       const float3 angA = a >= 0 ? R.v3(RF_ANGA) : f3(0.f, 0.f, 0.f);
       const float3 angB = b >= 0 ? R.v3(RF_ANGB) : f3(0.f, 0.f, 0.f);
-      const float bias = R[RF_BIAS];
+      const float3 IA = a >= 0 ? R.v3(RF_IA) : f3(0.f, 0.f, 0.f);
+      const float3 IB = b >= 0 ? R.v3(RF_IB) : f3(0.f, 0.f, 0.f);
       const int o = (it * NS + s) * Bp + L.i;
       const float la = tp.lam[o];
       const float lb = it > 0 ? tp.lam[o - NS * Bp] : 0.f;
       const int br = tp.br[o];
+      float bnd = 0.f, lnrm = 0.f;
+      if constexpr (kind == RK_GT || kind == RK_PT) {
+        constexpr int ns_ = Q::S.normal[s];
+        bnd = R[RF_BND];
+        lnrm = tp.lam[(it * NS + ns_) * Bp + L.i];
+      }
       const float dl = la - lb;
       float dbar = 0.f;
       float3 va = f3(0.f, 0.f, 0.f), wa = va, vb3 = va, wb3 = va, vba = va, wba = va, vbb = va, wbb = va;
-      float3 IA = va, IB = va;
       if (a >= 0) {
-        IA = R.v3(RF_IA);
         const float c = dl * im[a];
         v[a][0] -= c * lin.x; v[a][1] -= c * lin.y; v[a][2] -= c * lin.z;
         v[a][3] -= dl * IA.x; v[a][4] -= dl * IA.y; v[a][5] -= dl * IA.z;
         va = f3(v[a][0], v[a][1], v[a][2]);
         wa = f3(v[a][3], v[a][4], v[a][5]);
-        vba = f3(vb[a][0], vb[a][1], vb[a][2]);
-        wba = f3(vb[a][3], vb[a][4], vb[a][5]);
+        vba = VB.v3(6 * a);
+        wba = VB.v3(6 * a + 3);
         dbar += im[a] * dot3(lin, vba) + dot3(IA, wba);
       }
       if (b >= 0) {
-        IB = R.v3(RF_IB);
         const float c = dl * im[b];
         v[b][0] += c * lin.x; v[b][1] += c * lin.y; v[b][2] += c * lin.z;
         v[b][3] -= dl * IB.x; v[b][4] -= dl * IB.y; v[b][5] -= dl * IB.z;
         vb3 = f3(v[b][0], v[b][1], v[b][2]);
         wb3 = f3(v[b][3], v[b][4], v[b][5]);
-        vbb = f3(vb[b][0], vb[b][1], vb[b][2]);
-        wbb = f3(vb[b][3], vb[b][4], vb[b][5]);
+        vbb = VB.v3(6 * b);
+        wbb = VB.v3(6 * b + 3);
         dbar += -im[b] * dot3(lin, vbb) + dot3(IB, wbb);
       }
       float3 linb = dl * ((a >= 0 ? im[a] : 0.f) * vba - (b >= 0 ? im[b] : 0.f) * vbb);
@@ -316,7 +334,7 @@ __device__ void pgs_reverse_static(const DevTopo& T, const BLaneT<RV>& B, const 
         S[ib9 + 0] += g.x * angA.x; S[ib9 + 1] += g.x * angA.y; S[ib9 + 2] += g.x * angA.z;
         S[ib9 + 3] += g.y * angA.x; S[ib9 + 4] += g.y * angA.y; S[ib9 + 5] += g.y * angA.z;
         S[ib9 + 6] += g.z * angA.x; S[ib9 + 7] += g.z * angA.y; S[ib9 + 8] += g.z * angA.z;
-        if (!lin_is_zero<kind>()) S[T.sm_invmb + a] += dl * dot3(lin, vba);
+        if constexpr (!lin_is_zero<kind>()) S[T.sm_invmb + a] += dl * dot3(lin, vba);
       }
       if (b >= 0) {
         const float3 g = dl * wbb;
@@ -328,22 +346,20 @@ __device__ void pgs_reverse_static(const DevTopo& T, const BLaneT<RV>& B, const 
         S[ib9 + 0] += g.x * angB.x; S[ib9 + 1] += g.x * angB.y; S[ib9 + 2] += g.x * angB.z;
         S[ib9 + 3] += g.y * angB.x; S[ib9 + 4] += g.y * angB.y; S[ib9 + 5] += g.y * angB.z;
         S[ib9 + 6] += g.z * angB.x; S[ib9 + 7] += g.z * angB.y; S[ib9 + 8] += g.z * angB.z;
-        if (!lin_is_zero<kind>()) S[T.sm_invmb + b] -= dl * dot3(lin, vbb);
+        if constexpr (!lin_is_zero<kind>()) S[T.sm_invmb + b] -= dl * dot3(lin, vbb);
       }
       const float lbar_a = S[T.sm_lam + s] + dbar;
-      float pbar = 0.f;
       const int rc = s * RC_N;
-      if (br == 0) {
-        pbar = lbar_a;
-      } else if constexpr (kind == RK_GT || kind == RK_PT) {
+      // clamp branch as selectors: inside -> pre gets the adjoint; at a bound -> the bound does
+      const float inside = br == 0 ? 1.f : 0.f;
+      const float sg = br == 2 ? 1.f : (br == 1 ? -1.f : 0.f);
+      const float pbar = inside * lbar_a;
+      if constexpr (kind == RK_GT || kind == RK_PT) {
         constexpr int ns_ = Q::S.normal[s];
-        const float lnrm = tp.lam[(it * NS + ns_) * Bp + L.i];
-        const float mu = R[RF_BND];
-        const float sg = br == 2 ? 1.f : -1.f;
         RC[rc + RC_BND] += sg * lnrm * lbar_a;
-        S[T.sm_lam + ns_] += sg * mu * lbar_a;
-      } else if (kind == RK_MOTOR) {
-        RC[rc + RC_BND] += (br == 2 ? 1.f : -1.f) * lbar_a;
+        S[T.sm_lam + ns_] += sg * bnd * lbar_a;
+      } else if constexpr (kind == RK_MOTOR) {
+        RC[rc + RC_BND] += sg * lbar_a;
       }
       float Jv = 0.f;
       if (a >= 0) Jv += dot3(lin, va) + dot3(angA, wa);
@@ -352,25 +368,21 @@ __device__ void pgs_reverse_static(const DevTopo& T, const BLaneT<RV>& B, const 
       const float jvb = -meff * pbar;
       RC[rc + RC_BIAS] += jvb;
       if (a >= 0) {
-        vb[a][0] += jvb * lin.x; vb[a][1] += jvb * lin.y; vb[a][2] += jvb * lin.z;
-        vb[a][3] += jvb * angA.x; vb[a][4] += jvb * angA.y; vb[a][5] += jvb * angA.z;
+        VB.s3(6 * a, vba + jvb * lin);
+        VB.s3(6 * a + 3, wba + jvb * angA);
         linb += jvb * va;
         angAb += jvb * wa;
       }
       if (b >= 0) {
-        vb[b][0] -= jvb * lin.x; vb[b][1] -= jvb * lin.y; vb[b][2] -= jvb * lin.z;
-        vb[b][3] += jvb * angB.x; vb[b][4] += jvb * angB.y; vb[b][5] += jvb * angB.z;
+        VB.s3(6 * b, vbb - jvb * lin);
+        VB.s3(6 * b + 3, wbb + jvb * angB);
         linb -= jvb * vb3;
         angBb += jvb * wb3;
       }
-      if (!lin_is_constant<kind, sub>() && !lin_is_zero<kind>()) RC.a3(rc + RC_LIN, linb);
+      if constexpr (!lin_is_constant<kind, sub>() && !lin_is_zero<kind>()) RC.a3(rc + RC_LIN, linb);
       if (a >= 0) RC.a3(rc + RC_ANGA, angAb);
       if (b >= 0) RC.a3(rc + RC_ANGB, angBb);
       S[T.sm_lam + s] = -dbar + pbar * (1.f - meff * gamma);
     });
   }
-#pragma unroll
-  for (int b = 0; b < NB; ++b)
-#pragma unroll
-    for (int k = 0; k < 6; ++k) VB[6 * b + k] = vb[b][k];
 }
