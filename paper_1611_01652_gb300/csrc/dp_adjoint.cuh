@@ -104,10 +104,10 @@ __device__ __noinline__ void pgs_reverse(const DevTopo& T, const BLaneT<RV>& B, 
   for (int s = 0; s < T.nslots; ++s) S[T.sm_lam + s] = 0.f;
   for (int it = T.iters - 1; it >= 0; --it) {
     {
-      const float* vi = tp.viter + (size_t)it * T.nb * 6 * Bp + L.i;
+      const float* vi = tp.viter + it * T.nb * 6 * 32;
       for (int b = 0; b < T.nb; ++b)
 #pragma unroll
-        for (int k = 0; k < 6; ++k) VW[6 * b + k] = vi[(size_t)(6 * b + k) * Bp];
+        for (int k = 0; k < 6; ++k) VW[6 * b + k] = vi[(6 * b + k) * 32];
     }
     for (int oi = T.nslots - 1; oi >= 0; --oi) {
       const int s = T.order[oi];
@@ -118,9 +118,9 @@ __device__ __noinline__ void pgs_reverse(const DevTopo& T, const BLaneT<RV>& B, 
       const float3 lin = R.v3(RF_LIN);
       const float3 angA = R.v3(RF_ANGA), angB = R.v3(RF_ANGB);
       const float bias = R[RF_BIAS];
-      const int o = (it * T.nslots + s) * Bp + L.i;
+      const int o = (it * T.nslots + s) * 32;
       const float la = tp.lam[o];
-      const float lb = it > 0 ? tp.lam[o - T.nslots * Bp] : 0.f;
+      const float lb = it > 0 ? tp.lam[o - T.nslots * 32] : 0.f;
       const int br = tp.br[o];
       const float dl = la - lb;
       float3 va = f3(0.f, 0.f, 0.f), wa = va, vb = va, wb = va, vba = va, wba = va, vbb = va, wbb = va;
@@ -184,7 +184,7 @@ __device__ __noinline__ void pgs_reverse(const DevTopo& T, const BLaneT<RV>& B, 
       } else if (kind == RK_GT || kind == RK_PT) {
         // bound = +-mu * lambda_n (current value of the contact's normal impulse)
         const int ns_ = T.snormal[s];
-        const float lnrm = tp.lam[(it * T.nslots + ns_) * Bp + L.i];
+        const float lnrm = tp.lam[(it * T.nslots + ns_) * 32];
         const float mu = R[RF_BND];
         const float sg = br == 2 ? 1.f : -1.f;
         RC[rc + RC_BND] += sg * lnrm * lbar_a;

@@ -373,9 +373,28 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
   const int nf = 18 * T.nb;
   w->nf = nf;
   const size_t state_bytes = (size_t)nf * Bp * sizeof(float);
-  const size_t tape_step_bytes = ((size_t)T.nslots * RF_N * sizeof(float) + (size_t)T.iters * T.nslots * (sizeof(float) + 1) +
-                                  (size_t)T.iters * T.nb * 6 * sizeof(float) + (size_t)T.nb * 6 * sizeof(float)) *
-                                 Bp;
+  // tape record of one (step, warp): rows, impulses, per-sweep velocities, post-impulse
+  // velocities, clamp branches; 32 lanes interleaved; 16-byte multiple for bulk prefetches
+  {
+    long long o = (long long)T.nslots * RF_N * 32 * 4;
+    T.rec_lam = o;
+    o += (long long)T.iters * T.nslots * 32 * 4;
+    T.rec_viter = o;
+    o += (long long)T.iters * T.nb * 6 * 32 * 4;
+    T.rec_vminus = o;
+    o += (long long)T.nb * 6 * 32 * 4;
+    T.rec_br = o;
+    o += (long long)T.iters * T.nslots * 32;
+    T.rec_bytes = (o + 255) / 256 * 256;
+    for (DevTopo* t2 : {&w->Tf, &w->Tb}) {
+      t2->rec_lam = T.rec_lam;
+      t2->rec_viter = T.rec_viter;
+      t2->rec_vminus = T.rec_vminus;
+      t2->rec_br = T.rec_br;
+      t2->rec_bytes = T.rec_bytes;
+    }
+  }
+  const size_t tape_step_bytes = (size_t)T.rec_bytes * (Bp / 32);
   const size_t dump_bytes = (size_t)T.dump_rows * T.horizon * Bp * sizeof(float);
   size_t free_b = 0, total_b = 0;
   CU(cudaMemGetInfo(&free_b, &total_b));
@@ -417,11 +436,7 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
   if (dalloc(w, &D.state, (size_t)nf * Bz) || dalloc(w, &w->x0, (size_t)nf * Bz) ||
       dalloc(w, &D.ckpt, (size_t)n_ckpt * nf * Bz) || dalloc(w, &D.seg, full ? (size_t)1 : (size_t)(K + 1) * nf * Bz) ||
       dalloc(w, &D.rows, (size_t)T.nslots * RF_N * Bz) ||
-      dalloc(w, &D.t_rows, (size_t)tape_steps * T.nslots * RF_N * Bz) ||
-      dalloc(w, &D.t_lam, (size_t)tape_steps * T.iters * T.nslots * Bz) ||
-      dalloc(w, &D.t_br, (size_t)tape_steps * T.iters * T.nslots * Bz) ||
-      dalloc(w, &D.t_viter, (size_t)tape_steps * T.iters * T.nb * 6 * Bz) ||
-      dalloc(w, &D.t_vminus, (size_t)tape_steps * T.nb * 6 * Bz) || dalloc(w, &D.loss, Bz) || dalloc(w, &D.dloss, Bz) ||
+      dalloc(w, &D.tape, (size_t)tape_steps * tape_step_bytes) || dalloc(w, &D.loss, Bz) || dalloc(w, &D.dloss, Bz) ||
       dalloc(w, &D.grad_prm, (size_t)T.n_pfields * Bz) || dalloc(w, &D.grad_state0, (size_t)nf * Bz) ||
       dalloc(w, &D.status, Bz))
     return cleanup(DP_ENOMEM);

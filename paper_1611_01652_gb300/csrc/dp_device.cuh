@@ -60,6 +60,13 @@ struct DevTopo {
       sm_total;
   // activation/delta dump offsets (rows of [feature][T*Bp]); act l = input of layer l
   int dump_act[DPK_MAXL + 1], dump_del[DPK_MAXL + 1], dump_rows;
+  // tape record of one (step, warp), lanes interleaved ([field][32]): byte offsets
+  //   rows   [nslots][RF_N]       float   constraint rows
+  //   lam    [iters][nslots]      float   impulse after each row update
+  //   viter  [iters][nb*6]        float   velocities after each sweep
+  //   vminus [nb*6]               float   velocities after the external impulses
+  //   br     [iters][nslots]      uint8   clamp branch (0 inside, 1 lower bound, 2 upper bound)
+  long long rec_lam, rec_viter, rec_vminus, rec_br, rec_bytes;
 };
 
 // Global buffers a kernel works on.
@@ -74,11 +81,9 @@ struct DevPtrs {
   float* rows;           // constraint rows without a tape (rows that do not fit on chip) [nslots][RF_N][Bp]
   // Per-step solver tape, tape_steps slots: the whole horizon when it fits in device memory
   // (recorded by the rollout), else one checkpoint segment (recorded by the backward pass).
-  float* t_rows;         // [tape_steps][nslots][RF_N][Bp] constraint rows
-  float* t_lam;          // [tape_steps][iters][nslots][Bp] impulse after each row update
-  uint8_t* t_br;         // [tape_steps][iters][nslots][Bp] clamp branch (0 inside, 1 lower, 2 upper)
-  float* t_viter;        // [tape_steps][iters][nb*6][Bp] velocities after each sweep
-  float* t_vminus;       // [tape_steps][nb*6][Bp] velocities after the external impulses
+  // One contiguous record per (step, warp) of rec_bytes (see DevTopo.rec_*), so a whole record
+  // can be prefetched into L2 with one bulk operation.
+  uint8_t* tape;
   float* dump;           // controller activations and deltas [dump_rows][T*Bp]
   float* loss;           // [Bp]
   float* dloss;          // [Bp]
@@ -91,23 +96,34 @@ struct DevPtrs {
   int tape_steps, tape_full;  // tape_full: the rollout records every step (no recompute)
 };
 
-// Tape slot of one step.
+// Tape record of one step for this lane's warp (pointers include the lane offset).
 struct TapeStep {
-  float* rows;
-  float* lam;
-  uint8_t* br;
-  float* viter;
-  float* vminus;
+  float* rows;    // field f at rows[f * 32]
+  float* lam;     // (it, s) at lam[(it * nslots + s) * 32]
+  float* viter;   // (it, j) at viter[(it * nb * 6 + j) * 32]
+  float* vminus;  // j at vminus[j * 32]
+  uint8_t* br;    // (it, s) at br[(it * nslots + s) * 32]
+  const uint8_t* rec;
 };
 __device__ __forceinline__ TapeStep tape_step(const DevTopo& T, const DevPtrs& D, int ts) {
-  const size_t Bp = T.Bp;
+  const int lane = threadIdx.x & 31, warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint8_t* rec = D.tape + ((size_t)ts * (T.Bp / 32) + warp) * (size_t)T.rec_bytes;
   TapeStep p;
-  p.rows = D.t_rows + (size_t)ts * T.nslots * RF_N * Bp;
-  p.lam = D.t_lam + (size_t)ts * T.iters * T.nslots * Bp;
-  p.br = D.t_br + (size_t)ts * T.iters * T.nslots * Bp;
-  p.viter = D.t_viter + (size_t)ts * T.iters * T.nb * 6 * Bp;
-  p.vminus = D.t_vminus + (size_t)ts * T.nb * 6 * Bp;
+  p.rec = rec;
+  p.rows = (float*)rec + lane;
+  p.lam = (float*)(rec + T.rec_lam) + lane;
+  p.viter = (float*)(rec + T.rec_viter) + lane;
+  p.vminus = (float*)(rec + T.rec_vminus) + lane;
+  p.br = (uint8_t*)(rec + T.rec_br) + lane;
   return p;
+}
+// Bulk prefetch of a tape record into L2 (issued by one lane; fire-and-forget).
+__device__ __forceinline__ void prefetch_record_l2(const DevTopo& T, const uint8_t* rec) {
+  if ((threadIdx.x & 31) != 0) return;
+  for (long long off = 0; off < T.rec_bytes; off += 32768) {
+    const unsigned n = (unsigned)min((long long)32768, T.rec_bytes - off);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(rec + off), "r"(n) : "memory");
+  }
 }
 
 // ------------------------------------------------------------------------------- math
@@ -227,6 +243,15 @@ struct GL {
     atomicAdd(p + (f + 1) * s, v.y);
     atomicAdd(p + (f + 2) * s, v.z);
   }
+};
+// Global view with the lane-interleaved layout of shared memory (stride 32): tape records.
+struct GS {
+  static constexpr bool is_global = true;
+  float* p;
+  __device__ __forceinline__ GS at(int f) const { return GS{p + f * 32}; }
+  __device__ __forceinline__ float& operator[](int f) const { return p[f * 32]; }
+  __device__ __forceinline__ float3 v3(int f) const { return f3(p[f * 32], p[(f + 1) * 32], p[(f + 2) * 32]); }
+  __device__ __forceinline__ void s3(int f, float3 v) const { p[f * 32] = v.x; p[(f + 1) * 32] = v.y; p[(f + 2) * 32] = v.z; }
 };
 // Wide-stride global view (controller activation/delta columns of the [row][T*Bp] dump).
 struct GW {

@@ -407,16 +407,16 @@ __device__ void pgs_solve(const DevTopo& T, const LaneT<RV>& L, const SL& X, con
         Xb.s3(3, wb + dl * R.v3(RF_IB));
       }
       if (TAPE) {
-        const int o = (it * T.nslots + s) * Bp + L.i;
+        const int o = (it * T.nslots + s) * 32;
         tp.lam[o] = ln;
         tp.br[o] = (uint8_t)br;
       }
     }
     if (TAPE) {
-      float* vi = tp.viter + (size_t)it * T.nb * 6 * Bp + L.i;
+      float* vi = tp.viter + it * T.nb * 6 * 32;
       for (int b = 0; b < T.nb; ++b)
 #pragma unroll
-        for (int k = 0; k < 6; ++k) vi[(size_t)(6 * b + k) * Bp] = X[18 * b + 12 + k];
+        for (int k = 0; k < 6; ++k) vi[(6 * b + k) * 32] = X[18 * b + 12 + k];
     }
   }
 }
@@ -469,12 +469,11 @@ __device__ float step_forward(const DevTopo& T, const DevPtrs& D, const LaneT<RV
     tp = tape_step(T, D, ts);
     for (int b = 0; b < T.nb; ++b)
 #pragma unroll
-      for (int k = 0; k < 6; ++k) tp.vminus[(6 * b + k) * T.Bp + L.i] = X[18 * b + 12 + k];
+      for (int k = 0; k < 6; ++k) tp.vminus[(6 * b + k) * 32] = X[18 * b + 12 + k];
   }
   assemble_rows(T, L, X, active_out);
   if (TAPE && !RV::is_global) {
-    float* dst = tp.rows + L.i;
-    for (int f = 0; f < T.nslots * RF_N; ++f) dst[f * T.Bp] = L.rows[f];
+    for (int f = 0; f < T.nslots * RF_N; ++f) tp.rows[f * 32] = L.rows[f];
   }
   if constexpr (Q::id == 0)
     pgs_solve<TAPE>(T, L, X, tp);

@@ -140,8 +140,9 @@ __device__ void reverse_step(const DevTopo& T, const DevPtrs& D, const BwdCtx& C
   const size_t N = (size_t)T.horizon * Bp;
   const size_t n = (size_t)t * Bp + i;
   const TapeStep tp = tape_step(T, D, ts);
-  LaneT<GL> L{C.S, C.P, GL{tp.rows + i, Bp}, i};
-  BLaneT<GL> Bl{L, C.X, C.G, GC{tp.vminus + i, Bp}};
+  if (ts > 0) prefetch_record_l2(T, tape_step(T, D, ts - 1).rec);  // the next step to reverse
+  LaneT<GS> L{C.S, C.P, GS{tp.rows}, i};
+  BLaneT<GS> Bl{L, C.X, C.G, GC{tp.vminus, 32}};
   GW act[DPK_MAXL + 1], del[DPK_MAXL + 1];
   for (int l = 0; l <= DPK_MAXL; ++l) {
     act[l] = GW{D.dump + (size_t)T.dump_act[l] * N + n, N};
@@ -212,7 +213,7 @@ __global__ void __launch_bounds__(32, 1) k_backward(const __grid_constant__ DevT
       for (int t = ta; t < tb; ++t) {
         copy_state_from_smem(T, D.seg + (size_t)(t - ta) * sbytes, i, C.X);
         const TapeStep tp = tape_step(T, D, t - ta);
-        LaneT<GL> L{C.S, C.P, GL{tp.rows + i, Bp}, i};
+        LaneT<GS> L{C.S, C.P, GS{tp.rows}, i};
         const size_t n = (size_t)t * Bp + i;
         GW aw[DPK_MAXL + 1];
         for (int l = 0; l <= DPK_MAXL; ++l) aw[l] = GW{D.dump + (size_t)T.dump_act[l] * N + n, N};

@@ -146,7 +146,6 @@ template <class Q, bool TAPE, class RV>
 __device__ void pgs_solve_static(const DevTopo& T, const LaneT<RV>& L, const SL& X, const TapeStep& tp) {
   constexpr int NB = Q::NB, NS = Q::NS;
   const SL& S = L.S;
-  const int Bp = T.Bp;
   float v[NB][6], im[NB], lam[NS];
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
@@ -212,17 +211,17 @@ __device__ void pgs_solve_static(const DevTopo& T, const LaneT<RV>& L, const SL&
         v[b][3] += dl * IB.x; v[b][4] += dl * IB.y; v[b][5] += dl * IB.z;
       }
       if (TAPE) {
-        const int o = (it * NS + s) * Bp + L.i;
+        const int o = (it * NS + s) * 32;
         tp.lam[o] = ln;
         tp.br[o] = (uint8_t)br;
       }
     });
     if (TAPE) {
-      float* vi = tp.viter + (size_t)it * NB * 6 * Bp + L.i;
+      float* vi = tp.viter + it * NB * 6 * 32;
 #pragma unroll
       for (int b = 0; b < NB; ++b)
 #pragma unroll
-        for (int k = 0; k < 6; ++k) vi[(6 * b + k) * Bp] = v[b][k];
+        for (int k = 0; k < 6; ++k) vi[(6 * b + k) * 32] = v[b][k];
     }
   }
 #pragma unroll
@@ -234,20 +233,22 @@ __device__ void pgs_solve_static(const DevTopo& T, const LaneT<RV>& L, const SL&
 }
 
 // ---------------------------------------------------------------------------- reverse sweeps
-// Same arithmetic as pgs_reverse with constant slots: working velocities in registers; velocity
-// adjoints, impulse adjoints and row-adjoint accumulators in shared memory. Which rows are active
-// on some lane is decided once per step (a bit mask in registers), and the clamp branch enters
-// the arithmetic as a selector, so every load of a row can be issued before any of it is used.
+// Same arithmetic as pgs_reverse with constant slots. Working velocities and the impulse of
+// every row after the sweep being reversed live in registers (one tape load per row per sweep);
+// velocity adjoints, impulse adjoints and row-adjoint accumulators in shared memory; I^-1 J^T is
+// recomputed from the on-chip world inverse inertias. Which rows are active on some lane is
+// decided once per step (a bit mask), and the clamp branch enters the arithmetic as a selector,
+// so the loads of a row are issued before any of them is used.
 template <class Q, class RV>
-__device__ __noinline__ void pgs_reverse_static(const DevTopo& T, const BLaneT<RV>& B, const SL& X, const SL& VB, const SL& RC,
-                                   const TapeStep& tp) {
+__device__ __noinline__ void pgs_reverse_static(const DevTopo& T, const BLaneT<RV>& B, const SL& X, const SL& VB,
+                                                const SL& RC, const TapeStep& tp) {
   constexpr int NB = Q::NB, NS = Q::NS;
   constexpr int NW = (NS + 31) / 32;
   const LaneT<RV>& L = B.L;
   const SL& S = L.S;
-  const int Bp = T.Bp;
   const float gamma = T.gamma;
-  float v[NB][6], im[NB];
+  const int iters = T.iters;
+  float v[NB][6], im[NB], lc[NS];
 #pragma unroll
   for (int b = 0; b < NB; ++b) im[b] = S[T.sm_invm + b];
   unsigned live[NW];
@@ -262,15 +263,19 @@ __device__ __noinline__ void pgs_reverse_static(const DevTopo& T, const BLaneT<R
       live[s >> 5] |= 1u << (s & 31);
     }
   });
+  // impulses after the last sweep
 #pragma unroll
-  for (int s = 0; s < NS; ++s) S[T.sm_lam + s] = 0.f;
-  for (int it = T.iters - 1; it >= 0; --it) {
+  for (int s = 0; s < NS; ++s) {
+    lc[s] = tp.lam[((iters - 1) * NS + s) * 32];
+    S[T.sm_lam + s] = 0.f;
+  }
+  for (int it = iters - 1; it >= 0; --it) {
     {
-      const float* vi = tp.viter + (size_t)it * NB * 6 * Bp + L.i;
+      const float* vi = tp.viter + it * NB * 6 * 32;
 #pragma unroll
       for (int b = 0; b < NB; ++b)
 #pragma unroll
-        for (int k = 0; k < 6; ++k) v[b][k] = vi[(6 * b + k) * Bp];
+        for (int k = 0; k < 6; ++k) v[b][k] = vi[(6 * b + k) * 32];
     }
     static_for<NS>([&](auto RI) {
       constexpr int s = Q::S.order[NS - 1 - decltype(RI)::value];
@@ -287,22 +292,30 @@ __device__ __noinline__ void pgs_reverse_static(const DevTopo& T, const BLaneT<R
       else lin = R.v3(RF_LIN);
       const float3 angA = a >= 0 ? R.v3(RF_ANGA) : f3(0.f, 0.f, 0.f);
       const float3 angB = b >= 0 ? R.v3(RF_ANGB) : f3(0.f, 0.f, 0.f);
-      const float3 IA = a >= 0 ? R.v3(RF_IA) : f3(0.f, 0.f, 0.f);
-      const float3 IB = b >= 0 ? R.v3(RF_IB) : f3(0.f, 0.f, 0.f);
-      const int o = (it * NS + s) * Bp + L.i;
-      const float la = tp.lam[o];
-      const float lb = it > 0 ? tp.lam[o - NS * Bp] : 0.f;
+      const int o = (it * NS + s) * 32;
+      const float la = lc[s];
+      const float lb = it > 0 ? tp.lam[o - NS * 32] : 0.f;
       const int br = tp.br[o];
       float bnd = 0.f, lnrm = 0.f;
       if constexpr (kind == RK_GT || kind == RK_PT) {
-        constexpr int ns_ = Q::S.normal[s];
+        constexpr int nrm = Q::S.normal[s];
         bnd = R[RF_BND];
-        lnrm = tp.lam[(it * NS + ns_) * Bp + L.i];
+        lnrm = lc[nrm];
+      }
+      float ia[6], ib[6];
+      if (a >= 0) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) ia[q] = S[T.sm_iinv + 6 * a + q];
+      }
+      if (b >= 0) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) ib[q] = S[T.sm_iinv + 6 * b + q];
       }
       const float dl = la - lb;
       float dbar = 0.f;
       float3 va = f3(0.f, 0.f, 0.f), wa = va, vb3 = va, wb3 = va, vba = va, wba = va, vbb = va, wbb = va;
       if (a >= 0) {
+        const float3 IA = symv(ia, angA);
         const float c = dl * im[a];
         v[a][0] -= c * lin.x; v[a][1] -= c * lin.y; v[a][2] -= c * lin.z;
         v[a][3] -= dl * IA.x; v[a][4] -= dl * IA.y; v[a][5] -= dl * IA.z;
@@ -313,6 +326,7 @@ __device__ __noinline__ void pgs_reverse_static(const DevTopo& T, const BLaneT<R
         dbar += im[a] * dot3(lin, vba) + dot3(IA, wba);
       }
       if (b >= 0) {
+        const float3 IB = symv(ib, angB);
         const float c = dl * im[b];
         v[b][0] += c * lin.x; v[b][1] += c * lin.y; v[b][2] += c * lin.z;
         v[b][3] -= dl * IB.x; v[b][4] -= dl * IB.y; v[b][5] -= dl * IB.z;
@@ -326,9 +340,6 @@ __device__ __noinline__ void pgs_reverse_static(const DevTopo& T, const BLaneT<R
       float3 angAb = f3(0.f, 0.f, 0.f), angBb = angAb;
       if (a >= 0) {
         const float3 g = dl * wba;
-        float ia[6];
-#pragma unroll
-        for (int q = 0; q < 6; ++q) ia[q] = S[T.sm_iinv + 6 * a + q];
         angAb += symv(ia, g);
         const int ib9 = T.sm_iinvb + 9 * a;
         S[ib9 + 0] += g.x * angA.x; S[ib9 + 1] += g.x * angA.y; S[ib9 + 2] += g.x * angA.z;
@@ -338,9 +349,6 @@ __device__ __noinline__ void pgs_reverse_static(const DevTopo& T, const BLaneT<R
       }
       if (b >= 0) {
         const float3 g = dl * wbb;
-        float ib[6];
-#pragma unroll
-        for (int q = 0; q < 6; ++q) ib[q] = S[T.sm_iinv + 6 * b + q];
         angBb += symv(ib, g);
         const int ib9 = T.sm_iinvb + 9 * b;
         S[ib9 + 0] += g.x * angB.x; S[ib9 + 1] += g.x * angB.y; S[ib9 + 2] += g.x * angB.z;
@@ -350,7 +358,6 @@ __device__ __noinline__ void pgs_reverse_static(const DevTopo& T, const BLaneT<R
       }
       const float lbar_a = S[T.sm_lam + s] + dbar;
       const int rc = s * RC_N;
-      // clamp branch as selectors: inside -> pre gets the adjoint; at a bound -> the bound does
       const float inside = br == 0 ? 1.f : 0.f;
       const float sg = br == 2 ? 1.f : (br == 1 ? -1.f : 0.f);
       const float pbar = inside * lbar_a;
@@ -383,6 +390,7 @@ __device__ __noinline__ void pgs_reverse_static(const DevTopo& T, const BLaneT<R
       if (a >= 0) RC.a3(rc + RC_ANGA, angAb);
       if (b >= 0) RC.a3(rc + RC_ANGB, angBb);
       S[T.sm_lam + s] = -dbar + pbar * (1.f - meff * gamma);
+      lc[s] = lb;
     });
   }
 }
