@@ -33,7 +33,7 @@ __device__ __forceinline__ M3 body_Rg(const XV& X, int b) { return b >= 0 ? load
 // ---------------------------------------------------------------- loss (Eq. L) reverse
 // Adds wgt * dl(x)/dx at state X (on-chip) into XB, and the loss point / target gradients.
 template <class RV>
-__device__ __noinline__ void loss_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& X, const SL& XB, float wgt) {
+__device__ void loss_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& X, const SL& XB, float wgt) {
   if (wgt == 0.f) return;
   const int b = T.loss_body;
   M3 R = loadR(X, 18 * b);
@@ -55,7 +55,7 @@ __device__ __noinline__ void loss_reverse(const DevTopo& T, const BLaneT<RV>& B,
 // ---------------------------------------------------------------- integrate + Eq. 1 reverse
 // XB holds the adjoint of x_{t+1}; on return its p/R fields hold the adjoint of x_t's p/R,
 // its v/w fields are zero, and VB holds the adjoint of the solver's output velocities.
-__device__ __noinline__ void integrate_reverse(const DevTopo& T, const GC& Xt, const SL& X, const SL& XB, const SL& VB) {
+__device__ void integrate_reverse(const DevTopo& T, const GC& Xt, const SL& X, const SL& XB, const SL& VB) {
   const float h = T.dt;
   for (int b = 0; b < T.nb; ++b) {
     M3 R = loadRg(Xt, 18 * b);
@@ -96,7 +96,7 @@ __device__ __noinline__ void integrate_reverse(const DevTopo& T, const GC& Xt, c
 // Replays every sweep backwards. Working velocities are reset to the stored post-sweep values at
 // each sweep boundary and un-applied row by row. S[sm_lam] holds the impulse adjoints.
 template <class RV>
-__device__ __noinline__ void pgs_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& VW, const SL& VB, const SL& RC,
+__device__ void pgs_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& VW, const SL& VB, const SL& RC,
                             const TapeStep& tp) {
   const LaneT<RV>& L = B.L;
   const SL& S = L.S;
@@ -227,7 +227,7 @@ __device__ __forceinline__ void addR_outer(const SL& XB, int b, float3 g, float3
 // Pushes the row adjoints (and the effective-mass adjoint) back to positions, rotations, the
 // solver's input velocities (restitution), hinge axes/angles, servo targets and parameters.
 template <class RV>
-__device__ __noinline__ void rows_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& XB, const SL& VB, const SL& RC) {
+__device__ void rows_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& XB, const SL& VB, const SL& RC) {
   const LaneT<RV>& L = B.L;
   const SL& S = L.S;
   const float h = T.dt;
@@ -451,7 +451,7 @@ __device__ __noinline__ void rows_reverse(const DevTopo& T, const BLaneT<RV>& B,
 // (x_t's v, w, R) and the mass/inertia gradients. IINVB/INVMB hold the world inverse-inertia
 // and inverse-mass adjoints gathered from the solver and the rows.
 template <class RV>
-__device__ __noinline__ void external_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& XB, const SL& VB) {
+__device__ void external_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& XB, const SL& VB) {
   const SL& S = B.L.S;
   const float h = T.dt;
   for (int b = 0; b < T.nb; ++b) {
@@ -520,7 +520,7 @@ __device__ __noinline__ void external_reverse(const DevTopo& T, const BLaneT<RV>
 
 // ---------------------------------------------------------------- servo reverse
 template <class RV, class AV>
-__device__ __noinline__ void servo_reverse(const DevTopo& T, const BLaneT<RV>& B, const AV& u, const AV& ubd, const SL& ub) {
+__device__ void servo_reverse(const DevTopo& T, const BLaneT<RV>& B, const AV& u, const AV& ubd, const SL& ub) {
   const SL& S = B.L.S;
   const int nout = T.n_layers > 0 ? T.widths[T.n_layers] : 0;
   for (int o = 0; o < nout; ++o) ub[o] = 0.f;
@@ -575,7 +575,7 @@ __device__ void dense_bwd(const float* __restrict__ Wn, int ni, int no, const AV
 // of each layer's pre-activation output is formed on chip (ping-pong buffers zb0/zb1) and also
 // stored in the dump (del[l]) for the weight-gradient reduction. Leaves the input adjoint in sbar.
 template <class AV>
-__device__ __noinline__ void controller_reverse(const DevTopo& T, const DevPtrs& D, const AV* act, const AV* del, const SL& zb0,
+__device__ void controller_reverse(const DevTopo& T, const DevPtrs& D, const AV* act, const AV* del, const SL& zb0,
                                    const SL& zb1, const SL& sbar) {
   const int L = T.n_layers;
   SL cur = zb0, nxt = zb1;
@@ -597,7 +597,7 @@ __device__ __noinline__ void controller_reverse(const DevTopo& T, const DevPtrs&
 
 // Features reverse: sbar -> hinge angle/rate adjoints, IMU body state, loss point/target.
 template <class RV, class AV>
-__device__ __noinline__ void features_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& XB, const AV& sbar) {
+__device__ void features_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& XB, const AV& sbar) {
   const SL& S = B.L.S;
   int k = 0;
   if (T.features & 1)
@@ -632,7 +632,7 @@ __device__ __noinline__ void features_reverse(const DevTopo& T, const BLaneT<RV>
 
 // Hinge kinematics reverse (x_t): axis, angle and rate adjoints to R and w.
 template <class RV>
-__device__ __noinline__ void hinge_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& XB) {
+__device__ void hinge_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& XB) {
   const SL& S = B.L.S;
   for (int j = 0; j < T.nj; ++j) {
     int a = T.ja[j], b = T.jb[j];

@@ -253,6 +253,14 @@ struct GS {
   __device__ __forceinline__ float3 v3(int f) const { return f3(p[f * 32], p[(f + 1) * 32], p[(f + 2) * 32]); }
   __device__ __forceinline__ void s3(int f, float3 v) const { p[f * 32] = v.x; p[(f + 1) * 32] = v.y; p[(f + 2) * 32] = v.z; }
 };
+// Read-only tape view (non-coherent loads: the record was written by an earlier kernel).
+struct GSR {
+  static constexpr bool is_global = true;
+  const float* p;
+  __device__ __forceinline__ GSR at(int f) const { return GSR{p + f * 32}; }
+  __device__ __forceinline__ float operator[](int f) const { return __ldg(p + f * 32); }
+  __device__ __forceinline__ float3 v3(int f) const { return f3(__ldg(p + f * 32), __ldg(p + (f + 1) * 32), __ldg(p + (f + 2) * 32)); }
+};
 // Wide-stride global view (controller activation/delta columns of the [row][T*Bp] dump).
 struct GW {
   float* p;

@@ -3,6 +3,8 @@
 // and layout transposes.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "dp_static.cuh"
 #include "dp_kernels.h"
 
@@ -132,8 +134,9 @@ struct BwdCtx {
   float dl;
 };
 
-// Reverse of step t from its tape slot ts, with x_t and x_{t+1} in global memory.
-template <class Q>
+// Reverse of step t from its tape slot ts, with x_t and x_{t+1} in global memory. RV is the
+// tape-row view: read-only (GSR) when the rollout recorded the whole tape, else GS.
+template <class Q, class RV>
 __device__ void reverse_step(const DevTopo& T, const DevPtrs& D, const BwdCtx& C, int t, int ts, const float* x_t,
                              const float* x_t1) {
   const int Bp = T.Bp, i = C.i;
@@ -141,8 +144,8 @@ __device__ void reverse_step(const DevTopo& T, const DevPtrs& D, const BwdCtx& C
   const size_t n = (size_t)t * Bp + i;
   const TapeStep tp = tape_step(T, D, ts);
   if (ts > 0) prefetch_record_l2(T, tape_step(T, D, ts - 1).rec);  // the next step to reverse
-  LaneT<GS> L{C.S, C.P, GS{tp.rows}, i};
-  BLaneT<GS> Bl{L, C.X, C.G, GC{tp.vminus, 32}};
+  LaneT<RV> L{C.S, C.P, RV{tp.rows}, i};
+  BLaneT<RV> Bl{L, C.X, C.G, GC{tp.vminus, 32}};
   GW act[DPK_MAXL + 1], del[DPK_MAXL + 1];
   for (int l = 0; l <= DPK_MAXL; ++l) {
     act[l] = GW{D.dump + (size_t)T.dump_act[l] * N + n, N};
@@ -171,10 +174,10 @@ __device__ void reverse_step(const DevTopo& T, const DevPtrs& D, const BwdCtx& C
     for (int q = 0; q < 9; ++q) C.S[T.sm_iinvb + 9 * b + q] = 0.f;
   }
   for (int q = 0; q < T.nslots * RC_N; ++q) C.RC[q] = 0.f;
-  if constexpr (Q::id == 0)
-    pgs_reverse(T, Bl, VW, C.VB, C.RC, tp);
+  if constexpr (Q::id != 0 && std::is_same<RV, GSR>::value)
+    pgs_reverse_static<Q>(T, L, tp);
   else
-    pgs_reverse_static<Q>(T, Bl, C.X, C.VB, C.RC, tp);
+    pgs_reverse(T, Bl, VW, C.VB, C.RC, tp);
   rows_reverse(T, Bl, C.XB, C.VB, C.RC);
   external_reverse(T, Bl, C.XB, C.VB);
   if (T.n_layers > 0) {
@@ -203,7 +206,7 @@ __global__ void __launch_bounds__(32, 1) k_backward(const __grid_constant__ DevT
   const size_t sbytes = (size_t)nf * Bp;
   if (D.tape_full) {
     for (int t = T.horizon - 1; t >= 0; --t)
-      reverse_step<Q>(T, D, C, t, t, D.ckpt + (size_t)t * sbytes, t + 1 < T.horizon ? D.ckpt + (size_t)(t + 1) * sbytes : D.state);
+      reverse_step<Q, GSR>(T, D, C, t, t, D.ckpt + (size_t)t * sbytes, t + 1 < T.horizon ? D.ckpt + (size_t)(t + 1) * sbytes : D.state);
   } else {
     const int K = D.ckpt_every;
     for (int c = D.n_ckpt - 1; c >= 0; --c) {
@@ -221,7 +224,7 @@ __global__ void __launch_bounds__(32, 1) k_backward(const __grid_constant__ DevT
       }
       copy_state_from_smem(T, D.seg + (size_t)(tb - ta) * sbytes, i, C.X);
       for (int t = tb - 1; t >= ta; --t)
-        reverse_step<Q>(T, D, C, t, t - ta, D.seg + (size_t)(t - ta) * sbytes, D.seg + (size_t)(t - ta + 1) * sbytes);
+        reverse_step<Q, GS>(T, D, C, t, t - ta, D.seg + (size_t)(t - ta) * sbytes, D.seg + (size_t)(t - ta + 1) * sbytes);
     }
   }
   if (T.loss_kind == 3) {  // initial term -a.q(x_0) of the displacement loss

@@ -10,6 +10,8 @@
 
 #include "dp_adjoint.cuh"
 
+extern __shared__ float g_smem[];
+
 struct TopoDesc {
   int nb, nj, ns, np;
   int jtype[DPK_MAXJ], ja[DPK_MAXJ], jb[DPK_MAXJ], jflags[DPK_MAXJ];
@@ -239,13 +241,16 @@ __device__ void pgs_solve_static(const DevTopo& T, const LaneT<RV>& L, const SL&
 // recomputed from the on-chip world inverse inertias. Which rows are active on some lane is
 // decided once per step (a bit mask), and the clamp branch enters the arithmetic as a selector,
 // so the loads of a row are issued before any of them is used.
-template <class Q, class RV>
-__device__ __noinline__ void pgs_reverse_static(const DevTopo& T, const BLaneT<RV>& B, const SL& X, const SL& VB,
-                                                const SL& RC, const TapeStep& tp) {
+// Called with a read-only tape view (the whole tape was recorded by the rollout kernel).
+template <class Q>
+__device__ __noinline__ void pgs_reverse_static(const DevTopo& T, const LaneT<GSR>& L, const TapeStep& tp) {
   constexpr int NB = Q::NB, NS = Q::NS;
   constexpr int NW = (NS + 31) / 32;
-  const LaneT<RV>& L = B.L;
-  const SL& S = L.S;
+  // shared-memory views re-derived from the __shared__ array so their address space is known
+  const SL S{g_smem + (threadIdx.x & 31)};
+  const SL VB = S.at(T.sm_vb), RC = S.at(T.sm_rc);
+  const float* tlam = tp.lam;
+  const uint8_t* tbr = tp.br;
   const float gamma = T.gamma;
   const int iters = T.iters;
   float v[NB][6], im[NB], lc[NS];
@@ -266,7 +271,7 @@ __device__ __noinline__ void pgs_reverse_static(const DevTopo& T, const BLaneT<R
   // impulses after the last sweep
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    lc[s] = tp.lam[((iters - 1) * NS + s) * 32];
+    lc[s] = __ldg(tlam + ((iters - 1) * NS + s) * 32);
     S[T.sm_lam + s] = 0.f;
   }
   for (int it = iters - 1; it >= 0; --it) {
@@ -275,14 +280,14 @@ __device__ __noinline__ void pgs_reverse_static(const DevTopo& T, const BLaneT<R
 #pragma unroll
       for (int b = 0; b < NB; ++b)
 #pragma unroll
-        for (int k = 0; k < 6; ++k) v[b][k] = vi[(6 * b + k) * 32];
+        for (int k = 0; k < 6; ++k) v[b][k] = __ldg(vi + (6 * b + k) * 32);
     }
     static_for<NS>([&](auto RI) {
       constexpr int s = Q::S.order[NS - 1 - decltype(RI)::value];
       constexpr int kind = Q::S.kind[s], sub = Q::S.sub[s], a = Q::S.a[s], b = Q::S.b[s];
       if constexpr (maybe_inactive<kind>())
         if (!((live[s >> 5] >> (s & 31)) & 1u)) return;
-      const RV R = L.rows.at(s * RF_N);
+      const GSR R = L.rows.at(s * RF_N);
       // loads first
       const float meff = R[RF_MEFF];
       const float bias = R[RF_BIAS];
@@ -294,8 +299,8 @@ __device__ __noinline__ void pgs_reverse_static(const DevTopo& T, const BLaneT<R
       const float3 angB = b >= 0 ? R.v3(RF_ANGB) : f3(0.f, 0.f, 0.f);
       const int o = (it * NS + s) * 32;
       const float la = lc[s];
-      const float lb = it > 0 ? tp.lam[o - NS * 32] : 0.f;
-      const int br = tp.br[o];
+      const float lb = it > 0 ? __ldg(tlam + o - NS * 32) : 0.f;
+      const int br = __ldg(tbr + o);
       float bnd = 0.f, lnrm = 0.f;
       if constexpr (kind == RK_GT || kind == RK_PT) {
         constexpr int nrm = Q::S.normal[s];
