@@ -269,7 +269,7 @@ __device__ __forceinline__ void ring_issue(const DevTopo& T, const TapeStep& tp,
 #define S3(p, f, v) do { float3 v_ = (v); (p)[(f) * 32] = v_.x; (p)[((f) + 1) * 32] = v_.y; (p)[((f) + 2) * 32] = v_.z; } while (0)
 #define A3(p, f, v) do { float3 v_ = (v); (p)[(f) * 32] += v_.x; (p)[((f) + 1) * 32] += v_.y; (p)[((f) + 2) * 32] += v_.z; } while (0)
 template <class Q>
-__device__ __forceinline__ void pgs_reverse_static_impl(const DevTopo& T, int* __restrict__ status, const float* __restrict__ trows,
+__device__ __noinline__ void pgs_reverse_static_impl(const DevTopo& T, int* __restrict__ status, const float* __restrict__ trows,
                                                      const TapeStep& tp, float* __restrict__ VBp, float* __restrict__ RCp,
                                                      float* __restrict__ IIBp, float* __restrict__ IMBp,
                                                      float* __restrict__ LBp, const float* __restrict__ IIp,
