@@ -263,35 +263,31 @@ __device__ __forceinline__ void ring_issue(const DevTopo& T, const TapeStep& tp,
   tma_load_1d(dst + rows_b + 128, tp.rec + T.rec_br + ((size_t)it * NS + s) * 32, 32u, bar);
 }
 
-// Every shared-memory region the sweep touches comes in as its own restrict-qualified pointer
-// (lane-offset, field stride 32), so loads and stores of different regions can overlap.
-#define F3(p, f) f3((p)[(f) * 32], (p)[((f) + 1) * 32], (p)[((f) + 2) * 32])
-#define S3(p, f, v) do { float3 v_ = (v); (p)[(f) * 32] = v_.x; (p)[((f) + 1) * 32] = v_.y; (p)[((f) + 2) * 32] = v_.z; } while (0)
-#define A3(p, f, v) do { float3 v_ = (v); (p)[(f) * 32] += v_.x; (p)[((f) + 1) * 32] += v_.y; (p)[((f) + 2) * 32] += v_.z; } while (0)
 template <class Q>
-__device__ __noinline__ void pgs_reverse_static_impl(const DevTopo& T, int* __restrict__ status, const float* __restrict__ trows,
-                                                     const TapeStep& tp, float* __restrict__ VBp, float* __restrict__ RCp,
-                                                     float* __restrict__ IIBp, float* __restrict__ IMBp,
-                                                     float* __restrict__ LBp, const float* __restrict__ IIp,
-                                                     const float* __restrict__ IMp, float* __restrict__ ring) {
+__device__ __noinline__ void pgs_reverse_static(const DevTopo& T, const DevPtrs& D, const LaneT<GSR>& L,
+                                                const TapeStep& tp) {
   constexpr int NB = Q::NB, NS = Q::NS;
   constexpr int NW = (NS + 31) / 32;
   constexpr int RING = ring_slots_for<NS>();
   const int lane = threadIdx.x & 31;
+  // shared-memory views re-derived from the __shared__ array so their address space is known
+  const SL S{g_smem + lane};
+  const SL VB = S.at(T.sm_vb), RC = S.at(T.sm_rc);
+  float* ring = g_smem + T.sm_ring * 32;
   const uint32_t ring_s = smem_u32(ring), bar_s = smem_u32(g_smem + T.sm_bar * 32);
   const float gamma = T.gamma;
   const int iters = T.iters;
-  if (*status == 2) return;  // an earlier bounded wait ran out: results are void already
+  if (D.status[L.i] == 2) return;  // an earlier bounded wait ran out: results are void already
   float v[NB][6], im[NB], lc[NS];
 #pragma unroll
-  for (int b = 0; b < NB; ++b) im[b] = IMp[b * 32];
+  for (int b = 0; b < NB; ++b) im[b] = S[T.sm_invm + b];
   unsigned live[NW];
 #pragma unroll
   for (int w = 0; w < NW; ++w) live[w] = 0u;
   static_for<NS>([&](auto SI) {
     constexpr int s = decltype(SI)::value;
     if constexpr (maybe_inactive<Q::S.kind[s]>()) {
-      const float meff = __ldg(trows + (s * RF_N + RF_MEFF) * 32);
+      const float meff = L.rows.at(s * RF_N)[RF_MEFF];
       if (__any_sync(FULLMASK, meff != 0.f)) live[s >> 5] |= 1u << (s & 31);
     } else {
       live[s >> 5] |= 1u << (s & 31);
@@ -300,7 +296,7 @@ __device__ __noinline__ void pgs_reverse_static_impl(const DevTopo& T, int* __re
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     lc[s] = __ldg(tp.lam + ((iters - 1) * NS + s) * 32);
-    LBp[s * 32] = 0.f;
+    S[T.sm_lam + s] = 0.f;
   }
   // ring prologue: the first RING visits of the last sweep
   if (lane == 0) {
@@ -333,34 +329,35 @@ __device__ __noinline__ void pgs_reverse_static_impl(const DevTopo& T, int* __re
         last_waited = visit - 1;
         return;
       }
-      const float* __restrict__ rs = ring + slot * (T.ring_slot_bytes / 4) + lane;
+      const float* rs = ring + slot * (T.ring_slot_bytes / 4) + lane;
       const bool active = !maybe_inactive<kind>() || ((live[s >> 5] >> (s & 31)) & 1u);
       if (active) {
-        const float meff = rs[RF_MEFF * 32];
-        const float bias = rs[RF_BIAS * 32];
+        const SL R{const_cast<float*>(rs)};
+        const float meff = R[RF_MEFF];
+        const float bias = R[RF_BIAS];
         float3 lin;
         if constexpr (lin_is_constant<kind, sub>()) lin = const_lin<kind, sub>();
         else if constexpr (lin_is_zero<kind>()) lin = f3(0.f, 0.f, 0.f);
-        else lin = F3(rs, RF_LIN);
-        const float3 angA = a >= 0 ? F3(rs, RF_ANGA) : f3(0.f, 0.f, 0.f);
-        const float3 angB = b >= 0 ? F3(rs, RF_ANGB) : f3(0.f, 0.f, 0.f);
+        else lin = R.v3(RF_LIN);
+        const float3 angA = a >= 0 ? R.v3(RF_ANGA) : f3(0.f, 0.f, 0.f);
+        const float3 angB = b >= 0 ? R.v3(RF_ANGB) : f3(0.f, 0.f, 0.f);
         const float la = lc[s];
         const float lb = it > 0 ? rs[RF_N * 32] : 0.f;
         const int br = reinterpret_cast<const uint8_t*>(ring + slot * (T.ring_slot_bytes / 4) + RF_N * 32 + 32)[lane];
         float bnd = 0.f, lnrm = 0.f;
         if constexpr (kind == RK_GT || kind == RK_PT) {
           constexpr int nrm = Q::S.normal[s];
-          bnd = rs[RF_BND * 32];
+          bnd = R[RF_BND];
           lnrm = lc[nrm];
         }
         float ia[6], ib[6];
         if (a >= 0) {
 #pragma unroll
-          for (int q = 0; q < 6; ++q) ia[q] = IIp[(6 * a + q) * 32];
+          for (int q = 0; q < 6; ++q) ia[q] = S[T.sm_iinv + 6 * a + q];
         }
         if (b >= 0) {
 #pragma unroll
-          for (int q = 0; q < 6; ++q) ib[q] = IIp[(6 * b + q) * 32];
+          for (int q = 0; q < 6; ++q) ib[q] = S[T.sm_iinv + 6 * b + q];
         }
         const float dl = la - lb;
         float dbar = 0.f;
@@ -372,8 +369,8 @@ __device__ __noinline__ void pgs_reverse_static_impl(const DevTopo& T, int* __re
           v[a][3] -= dl * IA.x; v[a][4] -= dl * IA.y; v[a][5] -= dl * IA.z;
           va = f3(v[a][0], v[a][1], v[a][2]);
           wa = f3(v[a][3], v[a][4], v[a][5]);
-          vba = F3(VBp, 6 * a);
-          wba = F3(VBp, 6 * a + 3);
+          vba = VB.v3(6 * a);
+          wba = VB.v3(6 * a + 3);
           dbar += im[a] * dot3(lin, vba) + dot3(IA, wba);
         }
         if (b >= 0) {
@@ -383,8 +380,8 @@ __device__ __noinline__ void pgs_reverse_static_impl(const DevTopo& T, int* __re
           v[b][3] -= dl * IB.x; v[b][4] -= dl * IB.y; v[b][5] -= dl * IB.z;
           vb3 = f3(v[b][0], v[b][1], v[b][2]);
           wb3 = f3(v[b][3], v[b][4], v[b][5]);
-          vbb = F3(VBp, 6 * b);
-          wbb = F3(VBp, 6 * b + 3);
+          vbb = VB.v3(6 * b);
+          wbb = VB.v3(6 * b + 3);
           dbar += -im[b] * dot3(lin, vbb) + dot3(IB, wbb);
         }
         float3 linb = dl * ((a >= 0 ? im[a] : 0.f) * vba - (b >= 0 ? im[b] : 0.f) * vbb);
@@ -392,55 +389,55 @@ __device__ __noinline__ void pgs_reverse_static_impl(const DevTopo& T, int* __re
         if (a >= 0) {
           const float3 g = dl * wba;
           angAb += symv(ia, g);
-          float* __restrict__ gi = IIBp + 9 * a * 32;
-          gi[0] += g.x * angA.x; gi[32] += g.x * angA.y; gi[64] += g.x * angA.z;
-          gi[96] += g.y * angA.x; gi[128] += g.y * angA.y; gi[160] += g.y * angA.z;
-          gi[192] += g.z * angA.x; gi[224] += g.z * angA.y; gi[256] += g.z * angA.z;
-          if constexpr (!lin_is_zero<kind>()) IMBp[a * 32] += dl * dot3(lin, vba);
+          const int ib9 = T.sm_iinvb + 9 * a;
+          S[ib9 + 0] += g.x * angA.x; S[ib9 + 1] += g.x * angA.y; S[ib9 + 2] += g.x * angA.z;
+          S[ib9 + 3] += g.y * angA.x; S[ib9 + 4] += g.y * angA.y; S[ib9 + 5] += g.y * angA.z;
+          S[ib9 + 6] += g.z * angA.x; S[ib9 + 7] += g.z * angA.y; S[ib9 + 8] += g.z * angA.z;
+          if constexpr (!lin_is_zero<kind>()) S[T.sm_invmb + a] += dl * dot3(lin, vba);
         }
         if (b >= 0) {
           const float3 g = dl * wbb;
           angBb += symv(ib, g);
-          float* __restrict__ gi = IIBp + 9 * b * 32;
-          gi[0] += g.x * angB.x; gi[32] += g.x * angB.y; gi[64] += g.x * angB.z;
-          gi[96] += g.y * angB.x; gi[128] += g.y * angB.y; gi[160] += g.y * angB.z;
-          gi[192] += g.z * angB.x; gi[224] += g.z * angB.y; gi[256] += g.z * angB.z;
-          if constexpr (!lin_is_zero<kind>()) IMBp[b * 32] -= dl * dot3(lin, vbb);
+          const int ib9 = T.sm_iinvb + 9 * b;
+          S[ib9 + 0] += g.x * angB.x; S[ib9 + 1] += g.x * angB.y; S[ib9 + 2] += g.x * angB.z;
+          S[ib9 + 3] += g.y * angB.x; S[ib9 + 4] += g.y * angB.y; S[ib9 + 5] += g.y * angB.z;
+          S[ib9 + 6] += g.z * angB.x; S[ib9 + 7] += g.z * angB.y; S[ib9 + 8] += g.z * angB.z;
+          if constexpr (!lin_is_zero<kind>()) S[T.sm_invmb + b] -= dl * dot3(lin, vbb);
         }
-        const float lbar_a = LBp[s * 32] + dbar;
-        float* __restrict__ rc = RCp + s * RC_N * 32;
+        const float lbar_a = S[T.sm_lam + s] + dbar;
+        const int rc = s * RC_N;
         const float inside = br == 0 ? 1.f : 0.f;
         const float sg = br == 2 ? 1.f : (br == 1 ? -1.f : 0.f);
         const float pbar = inside * lbar_a;
         if constexpr (kind == RK_GT || kind == RK_PT) {
           constexpr int ns_ = Q::S.normal[s];
-          rc[RC_BND * 32] += sg * lnrm * lbar_a;
-          LBp[ns_ * 32] += sg * bnd * lbar_a;
+          RC[rc + RC_BND] += sg * lnrm * lbar_a;
+          S[T.sm_lam + ns_] += sg * bnd * lbar_a;
         } else if constexpr (kind == RK_MOTOR) {
-          rc[RC_BND * 32] += sg * lbar_a;
+          RC[rc + RC_BND] += sg * lbar_a;
         }
         float Jv = 0.f;
         if (a >= 0) Jv += dot3(lin, va) + dot3(angA, wa);
         if (b >= 0) Jv += dot3(angB, wb3) - dot3(lin, vb3);
-        rc[RC_MEFF * 32] += -pbar * (Jv + bias + gamma * lb);
+        RC[rc + RC_MEFF] += -pbar * (Jv + bias + gamma * lb);
         const float jvb = -meff * pbar;
-        rc[RC_BIAS * 32] += jvb;
+        RC[rc + RC_BIAS] += jvb;
         if (a >= 0) {
-          S3(VBp, 6 * a, vba + jvb * lin);
-          S3(VBp, 6 * a + 3, wba + jvb * angA);
+          VB.s3(6 * a, vba + jvb * lin);
+          VB.s3(6 * a + 3, wba + jvb * angA);
           linb += jvb * va;
           angAb += jvb * wa;
         }
         if (b >= 0) {
-          S3(VBp, 6 * b, vbb - jvb * lin);
-          S3(VBp, 6 * b + 3, wbb + jvb * angB);
+          VB.s3(6 * b, vbb - jvb * lin);
+          VB.s3(6 * b + 3, wbb + jvb * angB);
           linb -= jvb * vb3;
           angBb += jvb * wb3;
         }
-        if constexpr (!lin_is_constant<kind, sub>() && !lin_is_zero<kind>()) A3(rc, RC_LIN, linb);
-        if (a >= 0) A3(rc, RC_ANGA, angAb);
-        if (b >= 0) A3(rc, RC_ANGB, angBb);
-        LBp[s * 32] = -dbar + pbar * (1.f - meff * gamma);
+        if constexpr (!lin_is_constant<kind, sub>() && !lin_is_zero<kind>()) RC.a3(rc + RC_LIN, linb);
+        if (a >= 0) RC.a3(rc + RC_ANGA, angAb);
+        if (b >= 0) RC.a3(rc + RC_ANGB, angBb);
+        S[T.sm_lam + s] = -dbar + pbar * (1.f - meff * gamma);
         lc[s] = lb;
       }
       // every lane has read the slot: refill it with the visit RING ahead
@@ -458,18 +455,6 @@ __device__ __noinline__ void pgs_reverse_static_impl(const DevTopo& T, int* __re
     const int total = iters * NS;
     for (int v2 = last_waited + 1; v2 < min(total, last_waited + 1 + RING); ++v2)
       mbar_wait_bounded(bar_s + 8u * (v2 % RING), (uint32_t)((v2 / RING) & 1));
-    *status = 2;
+    D.status[L.i] = 2;
   }
-}
-#undef F3
-#undef S3
-#undef A3
-
-template <class Q>
-__device__ __forceinline__ void pgs_reverse_static(const DevTopo& T, const DevPtrs& D, const LaneT<GSR>& L,
-                                                   const TapeStep& tp) {
-  float* base = g_smem + (threadIdx.x & 31);
-  pgs_reverse_static_impl<Q>(T, D.status + L.i, tp.rows, tp, base + T.sm_vb * 32, base + T.sm_rc * 32,
-                             base + T.sm_iinvb * 32, base + T.sm_invmb * 32, base + T.sm_lam * 32,
-                             base + T.sm_iinv * 32, base + T.sm_invm * 32, g_smem + T.sm_ring * 32);
 }
