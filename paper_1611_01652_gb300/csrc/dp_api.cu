@@ -188,7 +188,7 @@ void plan_smem(DevTopo& T, bool backward, int smem_floats_max) {
       o = region + acts;
     }
     T.sm_xb = T.sm_vb = T.sm_thb = T.sm_thdb = T.sm_uab = T.sm_wstb = T.sm_iinvb = T.sm_invmb = T.sm_rc = T.sm_sbar = 0;
-    T.sm_vw = T.sm_zb = T.sm_ring = T.sm_bar = 0;
+    T.sm_vw = T.sm_zb = 0;
   } else {
     for (int l = 0; l <= DPK_MAXL; ++l) T.sm_act[l] = 0;
     T.sm_xb = take(18 * T.nb);
@@ -201,13 +201,7 @@ void plan_smem(DevTopo& T, bool backward, int smem_floats_max) {
     T.sm_invmb = take(T.nb);
     T.sm_rc = take(12 * T.nslots);
     T.sm_sbar = take(T.n_layers > 0 ? T.widths[0] : 1);
-    // TMA ring of the compiled reverse sweep; the run-time sweep's working velocities use the
-    // same region (the two never run in one world)
-    T.ring_slots = T.nslots % 5 == 0 ? 5 : (T.nslots % 4 == 0 ? 4 : (T.nslots % 3 == 0 ? 3 : (T.nslots % 2 == 0 ? 2 : 1)));
-    T.ring_slot_bytes = (RF_N * 32 * 4 + 128 + 32 + 127) / 128 * 128;
-    T.sm_ring = take(std::max(6 * T.nb, T.ring_slots * T.ring_slot_bytes / 128));
-    T.sm_vw = T.sm_ring;
-    T.sm_bar = take(1);
+    T.sm_vw = take(6 * T.nb);
     // controller-reverse ping-pong buffers: the row-adjoint region is free by then
     int maxw = 1;
     for (int l = 0; l <= T.n_layers && T.n_layers > 0; ++l) maxw = std::max(maxw, T.widths[l]);
@@ -647,8 +641,6 @@ dp_status dp_sync(dp_world* w) {
   CU(cudaStreamSynchronize(w->stream));
   std::vector<int> st(w->Bp);
   CU(cudaMemcpy(st.data(), w->D.status, sizeof(int) * w->Bp, cudaMemcpyDeviceToHost));
-  for (int i = 0; i < w->B; ++i)
-    if (st[i] == 2) return fail(DP_ETIMEOUT, "a bounded wait of the reverse pass ran out (instance " + std::to_string(i) + ")");
   for (int i = 0; i < w->B; ++i)
     if (st[i]) return fail(DP_ENAN, "instance " + std::to_string(i) + " produced a non-finite state or loss");
   return DP_OK;

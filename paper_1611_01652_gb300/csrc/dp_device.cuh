@@ -57,8 +57,7 @@ struct DevTopo {
   // shared-memory layout per warp, in units of 32 floats (one float per lane)
   int sm_x0, sm_x, sm_xb, sm_vb, sm_iinv, sm_invm, sm_th, sm_thd, sm_ua, sm_wst, sm_wbr, sm_lam, sm_u;
   int sm_thb, sm_thdb, sm_uab, sm_wstb, sm_iinvb, sm_invmb, sm_rc, sm_sbar, sm_vw, sm_zb, sm_act[DPK_MAXL + 1], sm_rows,
-      sm_ring, sm_bar, sm_total;
-  int ring_slots, ring_slot_bytes;  // TMA ring of the compiled reverse sweep
+      sm_total;
   // activation/delta dump offsets (rows of [feature][T*Bp]); act l = input of layer l
   int dump_act[DPK_MAXL + 1], dump_del[DPK_MAXL + 1], dump_rows;
   // tape record of one (step, warp), lanes interleaved ([field][32]): byte offsets
@@ -118,40 +117,6 @@ __device__ __forceinline__ TapeStep tape_step(const DevTopo& T, const DevPtrs& D
   p.br = (uint8_t*)(rec + T.rec_br) + lane;
   return p;
 }
-// ------------------------------------------------------------------ TMA / mbarrier helpers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// 1-D bulk copy global -> shared, completion counted on the mbarrier (16-byte aligned, 16-byte multiple)
-__device__ __forceinline__ void tma_load_1d(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-// Bounded wait on an mbarrier phase: gives up after ~2^31 cycles and reports it.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > (1ll << 31)) return false;
-  return true;
-}
-
 // Bulk prefetch of a tape record into L2 (issued by one lane; fire-and-forget).
 __device__ __forceinline__ void prefetch_record_l2(const DevTopo& T, const uint8_t* rec) {
   if ((threadIdx.x & 31) != 0) return;

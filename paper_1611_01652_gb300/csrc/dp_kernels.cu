@@ -175,7 +175,7 @@ __device__ void reverse_step(const DevTopo& T, const DevPtrs& D, const BwdCtx& C
   }
   for (int q = 0; q < T.nslots * RC_N; ++q) C.RC[q] = 0.f;
   if constexpr (Q::id != 0 && std::is_same<RV, GSR>::value)
-    pgs_reverse_static<Q>(T, D, L, tp);
+    pgs_reverse_static<Q>(T, L, tp);
   else
     pgs_reverse(T, Bl, VW, C.VB, C.RC, tp);
   rows_reverse(T, Bl, C.XB, C.VB, C.RC);

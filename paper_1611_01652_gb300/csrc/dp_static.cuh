@@ -235,49 +235,24 @@ __device__ void pgs_solve_static(const DevTopo& T, const LaneT<RV>& L, const SL&
 }
 
 // ---------------------------------------------------------------------------- reverse sweeps
-// Same arithmetic as pgs_reverse with constant slots. The tape data of each row visit (the row
-// record, the impulse before the sweep being reversed, the clamp branch) is streamed by TMA bulk
-// copies into a ring of shared-memory slots RING visits ahead of use, with completion on one
-// mbarrier per slot (bounded waits). Working velocities and the row impulses after the sweep
-// being reversed live in registers; velocity adjoints, impulse adjoints and row-adjoint
-// accumulators in shared memory; I^-1 J^T is recomputed from the on-chip inverse inertias.
-template <int NS>
-__host__ __device__ constexpr int ring_slots_for() {
-  return NS % 5 == 0 ? 5 : (NS % 4 == 0 ? 4 : (NS % 3 == 0 ? 3 : (NS % 2 == 0 ? 2 : 1)));
-}
-
-// Issue the TMA copies of row visit (it, k) (k-th row of the reversed sweep) into ring slot j.
-template <class Q, int K>
-__device__ __forceinline__ void ring_issue(const DevTopo& T, const TapeStep& tp, uint32_t ring_s, uint32_t bar_s,
-                                           int slot, int it) {
-  constexpr int NS = Q::NS;
-  constexpr int s = Q::S.order[NS - 1 - K];
-  const uint32_t dst = ring_s + (uint32_t)slot * T.ring_slot_bytes;
-  const uint32_t bar = bar_s + 8u * slot;
-  const uint32_t rows_b = RF_N * 32 * 4;
-  const uint32_t bytes = rows_b + (it > 0 ? 128u : 0u) + 32u;
-  fence_proxy_async_smem();
-  mbar_expect_tx(bar, bytes);
-  tma_load_1d(dst, tp.rec + (size_t)s * rows_b, rows_b, bar);
-  if (it > 0) tma_load_1d(dst + rows_b, tp.rec + T.rec_lam + ((size_t)(it - 1) * NS + s) * 128, 128u, bar);
-  tma_load_1d(dst + rows_b + 128, tp.rec + T.rec_br + ((size_t)it * NS + s) * 32, 32u, bar);
-}
-
+// Same arithmetic as pgs_reverse with constant slots. Working velocities and the impulse of
+// every row after the sweep being reversed live in registers (one tape load per row per sweep);
+// velocity adjoints, impulse adjoints and row-adjoint accumulators in shared memory; I^-1 J^T is
+// recomputed from the on-chip world inverse inertias. Which rows are active on some lane is
+// decided once per step (a bit mask), and the clamp branch enters the arithmetic as a selector,
+// so the loads of a row are issued before any of them is used.
+// Called with a read-only tape view (the whole tape was recorded by the rollout kernel).
 template <class Q>
-__device__ __noinline__ void pgs_reverse_static(const DevTopo& T, const DevPtrs& D, const LaneT<GSR>& L,
-                                                const TapeStep& tp) {
+__device__ __noinline__ void pgs_reverse_static(const DevTopo& T, const LaneT<GSR>& L, const TapeStep& tp) {
   constexpr int NB = Q::NB, NS = Q::NS;
   constexpr int NW = (NS + 31) / 32;
-  constexpr int RING = ring_slots_for<NS>();
-  const int lane = threadIdx.x & 31;
   // shared-memory views re-derived from the __shared__ array so their address space is known
-  const SL S{g_smem + lane};
+  const SL S{g_smem + (threadIdx.x & 31)};
   const SL VB = S.at(T.sm_vb), RC = S.at(T.sm_rc);
-  float* ring = g_smem + T.sm_ring * 32;
-  const uint32_t ring_s = smem_u32(ring), bar_s = smem_u32(g_smem + T.sm_bar * 32);
+  const float* tlam = tp.lam;
+  const uint8_t* tbr = tp.br;
   const float gamma = T.gamma;
   const int iters = T.iters;
-  if (D.status[L.i] == 2) return;  // an earlier bounded wait ran out: results are void already
   float v[NB][6], im[NB], lc[NS];
 #pragma unroll
   for (int b = 0; b < NB; ++b) im[b] = S[T.sm_invm + b];
@@ -293,21 +268,12 @@ __device__ __noinline__ void pgs_reverse_static(const DevTopo& T, const DevPtrs&
       live[s >> 5] |= 1u << (s & 31);
     }
   });
+  // impulses after the last sweep
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    lc[s] = __ldg(tp.lam + ((iters - 1) * NS + s) * 32);
+    lc[s] = __ldg(tlam + ((iters - 1) * NS + s) * 32);
     S[T.sm_lam + s] = 0.f;
   }
-  // ring prologue: the first RING visits of the last sweep
-  if (lane == 0) {
-#pragma unroll
-    for (int j = 0; j < RING; ++j) mbar_init(bar_s + 8u * j, 1);
-    mbar_init_fence();
-    static_for<RING>([&](auto J) { ring_issue<Q, decltype(J)::value>(T, tp, ring_s, bar_s, decltype(J)::value, iters - 1); });
-  }
-  __syncwarp();
-  bool timed_out = false;
-  int last_waited = -1;
   for (int it = iters - 1; it >= 0; --it) {
     {
       const float* vi = tp.viter + it * NB * 6 * 32;
@@ -316,145 +282,120 @@ __device__ __noinline__ void pgs_reverse_static(const DevTopo& T, const DevPtrs&
 #pragma unroll
         for (int k = 0; k < 6; ++k) v[b][k] = __ldg(vi + (6 * b + k) * 32);
     }
-    const int visit0 = (iters - 1 - it) * NS;  // visits before this sweep
     static_for<NS>([&](auto RI) {
-      constexpr int K = decltype(RI)::value;
-      constexpr int s = Q::S.order[NS - 1 - K];
+      constexpr int s = Q::S.order[NS - 1 - decltype(RI)::value];
       constexpr int kind = Q::S.kind[s], sub = Q::S.sub[s], a = Q::S.a[s], b = Q::S.b[s];
-      constexpr int slot = K % RING;
-      const int visit = visit0 + K;
-      if (timed_out) return;
-      if (!mbar_wait_bounded(bar_s + 8u * slot, (uint32_t)((visit / RING) & 1))) {
-        timed_out = true;
-        last_waited = visit - 1;
-        return;
+      if constexpr (maybe_inactive<kind>())
+        if (!((live[s >> 5] >> (s & 31)) & 1u)) return;
+      const GSR R = L.rows.at(s * RF_N);
+      // loads first
+      const float meff = R[RF_MEFF];
+      const float bias = R[RF_BIAS];
+      float3 lin;
+      if constexpr (lin_is_constant<kind, sub>()) lin = const_lin<kind, sub>();
+      else if constexpr (lin_is_zero<kind>()) lin = f3(0.f, 0.f, 0.f);
+      else lin = R.v3(RF_LIN);
+      const float3 angA = a >= 0 ? R.v3(RF_ANGA) : f3(0.f, 0.f, 0.f);
+      const float3 angB = b >= 0 ? R.v3(RF_ANGB) : f3(0.f, 0.f, 0.f);
+      const int o = (it * NS + s) * 32;
+      const float la = lc[s];
+      const float lb = it > 0 ? __ldg(tlam + o - NS * 32) : 0.f;
+      const int br = __ldg(tbr + o);
+      float bnd = 0.f, lnrm = 0.f;
+      if constexpr (kind == RK_GT || kind == RK_PT) {
+        constexpr int nrm = Q::S.normal[s];
+        bnd = R[RF_BND];
+        lnrm = lc[nrm];
       }
-      const float* rs = ring + slot * (T.ring_slot_bytes / 4) + lane;
-      const bool active = !maybe_inactive<kind>() || ((live[s >> 5] >> (s & 31)) & 1u);
-      if (active) {
-        const SL R{const_cast<float*>(rs)};
-        const float meff = R[RF_MEFF];
-        const float bias = R[RF_BIAS];
-        float3 lin;
-        if constexpr (lin_is_constant<kind, sub>()) lin = const_lin<kind, sub>();
-        else if constexpr (lin_is_zero<kind>()) lin = f3(0.f, 0.f, 0.f);
-        else lin = R.v3(RF_LIN);
-        const float3 angA = a >= 0 ? R.v3(RF_ANGA) : f3(0.f, 0.f, 0.f);
-        const float3 angB = b >= 0 ? R.v3(RF_ANGB) : f3(0.f, 0.f, 0.f);
-        const float la = lc[s];
-        const float lb = it > 0 ? rs[RF_N * 32] : 0.f;
-        const int br = reinterpret_cast<const uint8_t*>(ring + slot * (T.ring_slot_bytes / 4) + RF_N * 32 + 32)[lane];
-        float bnd = 0.f, lnrm = 0.f;
-        if constexpr (kind == RK_GT || kind == RK_PT) {
-          constexpr int nrm = Q::S.normal[s];
-          bnd = R[RF_BND];
-          lnrm = lc[nrm];
-        }
-        float ia[6], ib[6];
-        if (a >= 0) {
+      float ia[6], ib[6];
+      if (a >= 0) {
 #pragma unroll
-          for (int q = 0; q < 6; ++q) ia[q] = S[T.sm_iinv + 6 * a + q];
-        }
-        if (b >= 0) {
+        for (int q = 0; q < 6; ++q) ia[q] = S[T.sm_iinv + 6 * a + q];
+      }
+      if (b >= 0) {
 #pragma unroll
-          for (int q = 0; q < 6; ++q) ib[q] = S[T.sm_iinv + 6 * b + q];
-        }
-        const float dl = la - lb;
-        float dbar = 0.f;
-        float3 va = f3(0.f, 0.f, 0.f), wa = va, vb3 = va, wb3 = va, vba = va, wba = va, vbb = va, wbb = va;
-        if (a >= 0) {
-          const float3 IA = symv(ia, angA);
-          const float c = dl * im[a];
-          v[a][0] -= c * lin.x; v[a][1] -= c * lin.y; v[a][2] -= c * lin.z;
-          v[a][3] -= dl * IA.x; v[a][4] -= dl * IA.y; v[a][5] -= dl * IA.z;
-          va = f3(v[a][0], v[a][1], v[a][2]);
-          wa = f3(v[a][3], v[a][4], v[a][5]);
-          vba = VB.v3(6 * a);
-          wba = VB.v3(6 * a + 3);
-          dbar += im[a] * dot3(lin, vba) + dot3(IA, wba);
-        }
-        if (b >= 0) {
-          const float3 IB = symv(ib, angB);
-          const float c = dl * im[b];
-          v[b][0] += c * lin.x; v[b][1] += c * lin.y; v[b][2] += c * lin.z;
-          v[b][3] -= dl * IB.x; v[b][4] -= dl * IB.y; v[b][5] -= dl * IB.z;
-          vb3 = f3(v[b][0], v[b][1], v[b][2]);
-          wb3 = f3(v[b][3], v[b][4], v[b][5]);
-          vbb = VB.v3(6 * b);
-          wbb = VB.v3(6 * b + 3);
-          dbar += -im[b] * dot3(lin, vbb) + dot3(IB, wbb);
-        }
-        float3 linb = dl * ((a >= 0 ? im[a] : 0.f) * vba - (b >= 0 ? im[b] : 0.f) * vbb);
-        float3 angAb = f3(0.f, 0.f, 0.f), angBb = angAb;
-        if (a >= 0) {
-          const float3 g = dl * wba;
-          angAb += symv(ia, g);
-          const int ib9 = T.sm_iinvb + 9 * a;
-          S[ib9 + 0] += g.x * angA.x; S[ib9 + 1] += g.x * angA.y; S[ib9 + 2] += g.x * angA.z;
-          S[ib9 + 3] += g.y * angA.x; S[ib9 + 4] += g.y * angA.y; S[ib9 + 5] += g.y * angA.z;
-          S[ib9 + 6] += g.z * angA.x; S[ib9 + 7] += g.z * angA.y; S[ib9 + 8] += g.z * angA.z;
-          if constexpr (!lin_is_zero<kind>()) S[T.sm_invmb + a] += dl * dot3(lin, vba);
-        }
-        if (b >= 0) {
-          const float3 g = dl * wbb;
-          angBb += symv(ib, g);
-          const int ib9 = T.sm_iinvb + 9 * b;
-          S[ib9 + 0] += g.x * angB.x; S[ib9 + 1] += g.x * angB.y; S[ib9 + 2] += g.x * angB.z;
-          S[ib9 + 3] += g.y * angB.x; S[ib9 + 4] += g.y * angB.y; S[ib9 + 5] += g.y * angB.z;
-          S[ib9 + 6] += g.z * angB.x; S[ib9 + 7] += g.z * angB.y; S[ib9 + 8] += g.z * angB.z;
-          if constexpr (!lin_is_zero<kind>()) S[T.sm_invmb + b] -= dl * dot3(lin, vbb);
-        }
-        const float lbar_a = S[T.sm_lam + s] + dbar;
-        const int rc = s * RC_N;
-        const float inside = br == 0 ? 1.f : 0.f;
-        const float sg = br == 2 ? 1.f : (br == 1 ? -1.f : 0.f);
-        const float pbar = inside * lbar_a;
-        if constexpr (kind == RK_GT || kind == RK_PT) {
-          constexpr int ns_ = Q::S.normal[s];
-          RC[rc + RC_BND] += sg * lnrm * lbar_a;
-          S[T.sm_lam + ns_] += sg * bnd * lbar_a;
-        } else if constexpr (kind == RK_MOTOR) {
-          RC[rc + RC_BND] += sg * lbar_a;
-        }
-        float Jv = 0.f;
-        if (a >= 0) Jv += dot3(lin, va) + dot3(angA, wa);
-        if (b >= 0) Jv += dot3(angB, wb3) - dot3(lin, vb3);
-        RC[rc + RC_MEFF] += -pbar * (Jv + bias + gamma * lb);
-        const float jvb = -meff * pbar;
-        RC[rc + RC_BIAS] += jvb;
-        if (a >= 0) {
-          VB.s3(6 * a, vba + jvb * lin);
-          VB.s3(6 * a + 3, wba + jvb * angA);
-          linb += jvb * va;
-          angAb += jvb * wa;
-        }
-        if (b >= 0) {
-          VB.s3(6 * b, vbb - jvb * lin);
-          VB.s3(6 * b + 3, wbb + jvb * angB);
-          linb -= jvb * vb3;
-          angBb += jvb * wb3;
-        }
-        if constexpr (!lin_is_constant<kind, sub>() && !lin_is_zero<kind>()) RC.a3(rc + RC_LIN, linb);
-        if (a >= 0) RC.a3(rc + RC_ANGA, angAb);
-        if (b >= 0) RC.a3(rc + RC_ANGB, angBb);
-        S[T.sm_lam + s] = -dbar + pbar * (1.f - meff * gamma);
-        lc[s] = lb;
+        for (int q = 0; q < 6; ++q) ib[q] = S[T.sm_iinv + 6 * b + q];
       }
-      // every lane has read the slot: refill it with the visit RING ahead
-      __syncwarp();
-      if (lane == 0) {
-        constexpr int K2 = (K + RING) % NS;
-        const int it2 = it - ((K + RING) >= NS ? 1 : 0);
-        if (it2 >= 0) ring_issue<Q, K2>(T, tp, ring_s, bar_s, slot, it2);
+      const float dl = la - lb;
+      float dbar = 0.f;
+      float3 va = f3(0.f, 0.f, 0.f), wa = va, vb3 = va, wb3 = va, vba = va, wba = va, vbb = va, wbb = va;
+      if (a >= 0) {
+        const float3 IA = symv(ia, angA);
+        const float c = dl * im[a];
+        v[a][0] -= c * lin.x; v[a][1] -= c * lin.y; v[a][2] -= c * lin.z;
+        v[a][3] -= dl * IA.x; v[a][4] -= dl * IA.y; v[a][5] -= dl * IA.z;
+        va = f3(v[a][0], v[a][1], v[a][2]);
+        wa = f3(v[a][3], v[a][4], v[a][5]);
+        vba = VB.v3(6 * a);
+        wba = VB.v3(6 * a + 3);
+        dbar += im[a] * dot3(lin, vba) + dot3(IA, wba);
       }
+      if (b >= 0) {
+        const float3 IB = symv(ib, angB);
+        const float c = dl * im[b];
+        v[b][0] += c * lin.x; v[b][1] += c * lin.y; v[b][2] += c * lin.z;
+        v[b][3] -= dl * IB.x; v[b][4] -= dl * IB.y; v[b][5] -= dl * IB.z;
+        vb3 = f3(v[b][0], v[b][1], v[b][2]);
+        wb3 = f3(v[b][3], v[b][4], v[b][5]);
+        vbb = VB.v3(6 * b);
+        wbb = VB.v3(6 * b + 3);
+        dbar += -im[b] * dot3(lin, vbb) + dot3(IB, wbb);
+      }
+      float3 linb = dl * ((a >= 0 ? im[a] : 0.f) * vba - (b >= 0 ? im[b] : 0.f) * vbb);
+      float3 angAb = f3(0.f, 0.f, 0.f), angBb = angAb;
+      if (a >= 0) {
+        const float3 g = dl * wba;
+        angAb += symv(ia, g);
+        const int ib9 = T.sm_iinvb + 9 * a;
+        S[ib9 + 0] += g.x * angA.x; S[ib9 + 1] += g.x * angA.y; S[ib9 + 2] += g.x * angA.z;
+        S[ib9 + 3] += g.y * angA.x; S[ib9 + 4] += g.y * angA.y; S[ib9 + 5] += g.y * angA.z;
+        S[ib9 + 6] += g.z * angA.x; S[ib9 + 7] += g.z * angA.y; S[ib9 + 8] += g.z * angA.z;
+        if constexpr (!lin_is_zero<kind>()) S[T.sm_invmb + a] += dl * dot3(lin, vba);
+      }
+      if (b >= 0) {
+        const float3 g = dl * wbb;
+        angBb += symv(ib, g);
+        const int ib9 = T.sm_iinvb + 9 * b;
+        S[ib9 + 0] += g.x * angB.x; S[ib9 + 1] += g.x * angB.y; S[ib9 + 2] += g.x * angB.z;
+        S[ib9 + 3] += g.y * angB.x; S[ib9 + 4] += g.y * angB.y; S[ib9 + 5] += g.y * angB.z;
+        S[ib9 + 6] += g.z * angB.x; S[ib9 + 7] += g.z * angB.y; S[ib9 + 8] += g.z * angB.z;
+        if constexpr (!lin_is_zero<kind>()) S[T.sm_invmb + b] -= dl * dot3(lin, vbb);
+      }
+      const float lbar_a = S[T.sm_lam + s] + dbar;
+      const int rc = s * RC_N;
+      const float inside = br == 0 ? 1.f : 0.f;
+      const float sg = br == 2 ? 1.f : (br == 1 ? -1.f : 0.f);
+      const float pbar = inside * lbar_a;
+      if constexpr (kind == RK_GT || kind == RK_PT) {
+        constexpr int ns_ = Q::S.normal[s];
+        RC[rc + RC_BND] += sg * lnrm * lbar_a;
+        S[T.sm_lam + ns_] += sg * bnd * lbar_a;
+      } else if constexpr (kind == RK_MOTOR) {
+        RC[rc + RC_BND] += sg * lbar_a;
+      }
+      float Jv = 0.f;
+      if (a >= 0) Jv += dot3(lin, va) + dot3(angA, wa);
+      if (b >= 0) Jv += dot3(angB, wb3) - dot3(lin, vb3);
+      RC[rc + RC_MEFF] += -pbar * (Jv + bias + gamma * lb);
+      const float jvb = -meff * pbar;
+      RC[rc + RC_BIAS] += jvb;
+      if (a >= 0) {
+        VB.s3(6 * a, vba + jvb * lin);
+        VB.s3(6 * a + 3, wba + jvb * angA);
+        linb += jvb * va;
+        angAb += jvb * wa;
+      }
+      if (b >= 0) {
+        VB.s3(6 * b, vbb - jvb * lin);
+        VB.s3(6 * b + 3, wbb + jvb * angB);
+        linb -= jvb * vb3;
+        angBb += jvb * wb3;
+      }
+      if constexpr (!lin_is_constant<kind, sub>() && !lin_is_zero<kind>()) RC.a3(rc + RC_LIN, linb);
+      if (a >= 0) RC.a3(rc + RC_ANGA, angAb);
+      if (b >= 0) RC.a3(rc + RC_ANGB, angBb);
+      S[T.sm_lam + s] = -dbar + pbar * (1.f - meff * gamma);
+      lc[s] = lb;
     });
-  }
-  if (timed_out) {
-    // drain the copies still in flight (issued up to RING visits past the last one waited for),
-    // each with its own bound, before the slots are reused or the block exits
-    const int total = iters * NS;
-    for (int v2 = last_waited + 1; v2 < min(total, last_waited + 1 + RING); ++v2)
-      mbar_wait_bounded(bar_s + 8u * (v2 % RING), (uint32_t)((v2 / RING) & 1));
-    D.status[L.i] = 2;
   }
 }
