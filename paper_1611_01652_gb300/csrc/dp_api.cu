@@ -10,6 +10,7 @@
 
 #include "../../include/dp.h"
 #include "dp_kernels.h"
+#include "dp_mma.cuh"
 #include "dp_world.h"
 
 namespace {
@@ -349,6 +350,8 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
     T.dump_rows = r;
   }
   T.n_params = (int)np_;
+  T.mlp_tc = T.n_layers == 3 && !T.skip && T.ctrl_round && T.widths[0] == CtrlTC::K0 && T.widths[1] == CtrlTC::H1 &&
+             T.widths[2] == CtrlTC::H2 && T.widths[3] == CtrlTC::NO && !getenv("DP_FORCE_SIMT_CONTROLLER");
   T.topo_id = match_compiled_topology(T, T.nb, T.nj, T.ns, T.np, d->joint_type, d->joint_body, d->joint_flags,
                                       d->sphere_body, d->pair_sphere);
   if (getenv("DP_FORCE_RUNTIME_TOPOLOGY")) T.topo_id = 0;
@@ -457,6 +460,13 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
     D.Wt = w->Wt;
     D.Wn = w->Wn;
     D.bias = w->Wb;
+    if (T.mlp_tc) {
+      void* p = nullptr;
+      if (cudaMalloc(&p, sizeof(__nv_bfloat16) * CtrlTC::SIZE) != cudaSuccess) return cleanup(DP_ENOMEM);
+      w->allocs.push_back(p);
+      w->Wtc = (__nv_bfloat16*)p;
+    }
+    D.Wtc = w->Wtc;
   } else {
     float* dummy = nullptr;
     if (dalloc(w, &dummy, 8)) return cleanup(DP_ENOMEM);
@@ -554,6 +564,7 @@ static dp_status stage_weights(dp_world* w, const float* W) {
   if (!W) return fail(DP_EINVAL, "the world has a controller: W is required");
   CU(cudaMemcpyAsync(w->Wmaster, W, sizeof(float) * w->n_params, cudaMemcpyDefault, w->stream));
   CU(launch_prep_weights(w->Tf, w->Wmaster, w->Wt, w->Wn, w->Wb, w->stream));
+  if (w->Tf.mlp_tc) CU(launch_prep_weights_tc(w->Tf, w->Wmaster, w->Wtc, w->stream));
   return DP_OK;
 }
 

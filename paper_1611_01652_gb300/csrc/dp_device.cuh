@@ -40,6 +40,7 @@ struct DevTopo {
   int iters, horizon, features, imu_body, loss_kind, loss_mode, loss_body;
   int n_layers, skip, n_params, n_motors, ctrl_round;  // ctrl_round: 1 = bfloat16 storage points
   int topo_id;  // 0: run-time topology loops; otherwise the compiled topology with this id
+  int mlp_tc;   // 1: the controller is the 24-128-128-8 bfloat16 network, run on the tensor cores
   int widths[DPK_MAXL + 1];
   int w_off[DPK_MAXL + 2];   // offset of layer l's W[out][in] in the flat weights (l = n_layers: skip)
   float gravity[3], dt, ground_z, beta, gamma, slop, clock_hz;
@@ -75,6 +76,7 @@ struct DevPtrs {
   const float* Wt;       // controller, fp32 copies of the bf16 weights, each layer [in][out]
   const float* Wn;       // same, each layer [out][in]
   const float* bias;     // controller biases, per layer [out] (then skip bias)
+  const __nv_bfloat16* Wtc;  // tensor-core weight layouts (CtrlTC), when DevTopo.mlp_tc
   float* state;          // current state [nb*18][Bp]
   float* ckpt;           // checkpoints [n_ckpt][nb*18][Bp]
   float* seg;            // segment states for the backward [K+1][nb*18][Bp]
@@ -221,6 +223,8 @@ struct SL {
   float* p;
   __device__ __forceinline__ SL at(int f) const { return SL{p + f * 32}; }
   __device__ __forceinline__ float& operator[](int f) const { return p[f * 32]; }
+  // field f of lane r of this warp
+  __device__ __forceinline__ float& lane_at(int f, int r) const { return p[f * 32 + r - (int)(threadIdx.x & 31)]; }
   __device__ __forceinline__ float3 v3(int f) const { return f3(p[f * 32], p[(f + 1) * 32], p[(f + 2) * 32]); }
   __device__ __forceinline__ void s3(int f, float3 v) const { p[f * 32] = v.x; p[(f + 1) * 32] = v.y; p[(f + 2) * 32] = v.z; }
   __device__ __forceinline__ void a3(int f, float3 v) const { p[f * 32] += v.x; p[(f + 1) * 32] += v.y; p[(f + 2) * 32] += v.z; }
@@ -266,6 +270,7 @@ struct GW {
   float* p;
   size_t s;
   __device__ __forceinline__ float& operator[](int f) const { return p[(size_t)f * s]; }
+  __device__ __forceinline__ float& lane_at(int f, int r) const { return p[(size_t)f * s + r - (int)(threadIdx.x & 31)]; }
 };
 struct GC {
   const float* p;

@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 
 #include "dp_device.cuh"
+#include "dp_mma.cuh"
 
 #define FULLMASK 0xffffffffu
 
@@ -153,6 +154,31 @@ __device__ void controller_forward(const DevTopo& T, const DevPtrs& D, const AV*
     const int l = T.n_layers;
     dense_fwd(D.Wt + T.w_off[l], D.bias + T.w_off[l], T.widths[0], T.widths[l], act[0], act[l], false, true, false);
   }
+}
+
+// Controller forward on the tensor cores (the bfloat16 24-128-128-8 network): the warp's 32
+// instances are the rows of each product. act[0] holds the features, act[3] receives u. Hidden
+// activations go to the dump column when one is given, to act[1], act[2] when those are dump
+// views (segment recompute), and nowhere otherwise.
+template <class AV>
+__device__ void controller_forward_tc(const DevTopo& T, const DevPtrs& D, const AV* act, float* dump_col) {
+  const __nv_bfloat16* Wc = D.Wtc;
+  const size_t N = (size_t)T.horizon * T.Bp;
+  const int lane = threadIdx.x & 31;
+  float* dbase = dump_col ? dump_col - lane : nullptr;
+  const int d1 = T.dump_act[1], d2 = T.dump_act[2];
+  const AV a0 = act[0], a1 = act[1], a2 = act[2], a3 = act[3];
+  __syncwarp();
+  mlp3_forward<CtrlTC::K0, CtrlTC::H1, CtrlTC::H2, CtrlTC::NO>(
+      [&](int f, int r) { return a0.lane_at(f, r); }, Wc + CtrlTC::W1, D.bias + T.w_off[0], Wc + CtrlTC::W2,
+      D.bias + T.w_off[1], Wc + CtrlTC::W3, D.bias + T.w_off[2], [&](int f, int r, float v) { a3.lane_at(f, r) = v; },
+      [&](int l, int f, int r, float v) {
+        if (dbase)
+          dbase[(size_t)((l == 1 ? d1 : d2) + f) * N + r] = v;
+        else if constexpr (!std::is_same<AV, SL>::value)
+          (l == 1 ? a1 : a2).lane_at(f, r) = v;
+      });
+  __syncwarp();
 }
 
 // Servo targets w* = clamp(k (u - theta), -vmax, vmax).
@@ -453,11 +479,16 @@ __device__ float step_forward(const DevTopo& T, const DevPtrs& D, const LaneT<RV
   hinge_kinematics(T, L, X);
   if (T.n_layers > 0) {
     controller_features(T, L, X, t, act[0]);
-    controller_forward(T, D, act);
+    if (T.mlp_tc)
+      controller_forward_tc(T, D, act, dump_col);
+    else
+      controller_forward(T, D, act);
     if (dump_col) {
       const size_t N = (size_t)T.horizon * T.Bp;
-      for (int l = 0; l <= T.n_layers; ++l)
+      for (int l = 0; l <= T.n_layers; ++l) {
+        if (T.mlp_tc && l > 0 && l < T.n_layers) continue;  // hidden layers went straight to the dump
         for (int k = 0; k < T.widths[l]; ++k) dump_col[(size_t)(T.dump_act[l] + k) * N] = act[l][k];
+      }
     }
     servo_targets(T, L, act[T.n_layers]);
   } else {

@@ -38,6 +38,36 @@ __global__ void k_prep_weights(const __grid_constant__ DevTopo T, const float* _
   }
 }
 
+// Tensor-core layouts of the 24-128-128-8 controller (CtrlTC), bfloat16, zero padded.
+__global__ void k_prep_weights_tc(const __grid_constant__ DevTopo T, const float* __restrict__ W, __nv_bfloat16* Wc) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= CtrlTC::SIZE) return;
+  // flat master layout: per layer W[out][in] then b[out]
+  const int m1 = CtrlTC::K0 * CtrlTC::H1 + CtrlTC::H1, m2 = m1 + CtrlTC::H1 * CtrlTC::H2 + CtrlTC::H2;
+  auto w = [&](int l, int o, int i) { return W[(l == 0 ? 0 : l == 1 ? m1 : m2) + o * T.widths[l] + i]; };
+  float v = 0.f;
+  if (p < CtrlTC::W2) {  // W1 [H1][32]
+    int o = p / 32, i = p % 32;
+    v = i < CtrlTC::K0 ? w(0, o, i) : 0.f;
+  } else if (p < CtrlTC::W3) {  // W2 [H2][H1]
+    int q = p - CtrlTC::W2, o = q / CtrlTC::H1, i = q % CtrlTC::H1;
+    v = w(1, o, i);
+  } else if (p < CtrlTC::W3T) {  // W3 [8][H2]
+    int q = p - CtrlTC::W3, o = q / CtrlTC::H2, i = q % CtrlTC::H2;
+    v = o < CtrlTC::NO ? w(2, o, i) : 0.f;
+  } else if (p < CtrlTC::W2T) {  // W3^T [H2][16]
+    int q = p - CtrlTC::W3T, i = q / 16, o = q % 16;
+    v = o < CtrlTC::NO ? w(2, o, i) : 0.f;
+  } else if (p < CtrlTC::W1T) {  // W2^T [H1][H2]
+    int q = p - CtrlTC::W2T, i = q / CtrlTC::H2, o = q % CtrlTC::H2;
+    v = w(1, o, i);
+  } else {  // W1^T [24][H1]
+    int q = p - CtrlTC::W1T, i = q / CtrlTC::H1, o = q % CtrlTC::H1;
+    v = w(0, o, i);
+  }
+  Wc[p] = __float2bfloat16_rn(v);
+}
+
 // ------------------------------------------------------------------------------ layouts
 // [B][nb*18] (user) -> [nb*18][Bp]; padded instances copy instance B-1.
 __global__ void k_state_in(int B, int Bp, int nf, const float* __restrict__ src, float* dst) {
@@ -182,7 +212,10 @@ __device__ void reverse_step(const DevTopo& T, const DevPtrs& D, const BwdCtx& C
   external_reverse(T, Bl, C.XB, C.VB);
   if (T.n_layers > 0) {
     servo_reverse(T, Bl, act[T.n_layers], del[T.n_layers - 1], zb0);
-    controller_reverse(T, D, act, del, zb0, zb1, C.sbar);
+    if (T.mlp_tc)
+      controller_reverse_tc(T, D, act, del, zb0, C.sbar);
+    else
+      controller_reverse(T, D, act, del, zb0, zb1, C.sbar);
     features_reverse(T, Bl, C.XB, C.sbar);
   } else {
     servo_reverse(T, Bl, act[0], act[0], zb0);
@@ -313,6 +346,10 @@ __global__ void k_sum_splits(const float* __restrict__ partial, int splits, size
 cudaError_t launch_prep_weights(const DevTopo& T, const float* W, float* Wt, float* Wn, float* bias, cudaStream_t s) {
   if (T.n_params == 0) return cudaSuccess;
   k_prep_weights<<<(T.n_params + 255) / 256, 256, 0, s>>>(T, W, Wt, Wn, bias);
+  return cudaGetLastError();
+}
+cudaError_t launch_prep_weights_tc(const DevTopo& T, const float* W, __nv_bfloat16* Wc, cudaStream_t s) {
+  k_prep_weights_tc<<<(CtrlTC::SIZE + 255) / 256, 256, 0, s>>>(T, W, Wc);
   return cudaGetLastError();
 }
 cudaError_t launch_state_in(int B, int Bp, int nf, const float* src, float* dst, cudaStream_t s) {

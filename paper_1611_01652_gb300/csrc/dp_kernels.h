@@ -5,6 +5,7 @@
 #include "dp_device.cuh"
 
 cudaError_t launch_prep_weights(const DevTopo& T, const float* W, float* Wt, float* Wn, float* bias, cudaStream_t s);
+cudaError_t launch_prep_weights_tc(const DevTopo& T, const float* W, __nv_bfloat16* Wc, cudaStream_t s);
 cudaError_t launch_state_in(int B, int Bp, int nf, const float* src, float* dst, cudaStream_t s);
 cudaError_t launch_state_out(int B, int Bp, int nf, const float* src, float* dst, cudaStream_t s);
 cudaError_t launch_param_out(int B, int Bp, int o, int n, const float* src, float* dst, cudaStream_t s);

@@ -18,6 +18,7 @@ struct dp_world {
   float* x0 = nullptr;
   float* Wmaster = nullptr;
   float *Wt = nullptr, *Wn = nullptr, *Wb = nullptr;
+  __nv_bfloat16* Wtc = nullptr;  // tensor-core layouts of the controller (DevTopo.mlp_tc)
   float* stage = nullptr;      // device staging buffer for user-layout inputs/outputs
   size_t stage_floats = 0;
   float* dW_stage = nullptr;   // [n_params]

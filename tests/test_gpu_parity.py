@@ -240,3 +240,21 @@ def test_quadruped_runtime_topology_path(monkeypatch):
     m.ctrl_fp32 = 1
     compare_rollout(m, 60, range(8), min_clean=0.5)
     check_grads(WL.quadruped(B=2, horizon=20), 20, ("state0", "anchor", "motor"), range(2))
+
+
+def test_tensor_core_controller_matches_simt(monkeypatch):
+    """The bfloat16 24-128-128-8 controller runs on the tensor cores; the SIMT path (forced here)
+    computes the same network with another summation order. Both must give the same step and
+    the same gradients up to fp32 rounding (and the hi/lo bfloat16 split of the deltas)."""
+    m = WL.quadruped(B=64, horizon=10)
+    out = []
+    for force in (False, True):
+        if force:
+            monkeypatch.setenv("DP_FORCE_SIMT_CONTROLLER", "1")
+        g = gpu_grads(m, 10)
+        _, traj, loss, _ = gpu_rollout(m, 10)
+        out.append((traj, g))
+    (ta, ga), (tb, gb) = out
+    assert np.abs(ta[1] - tb[1]).max() <= 1e-5
+    assert rel_err(ga["W"], gb["W"]) <= 1e-3
+    assert rel_err(ga["state0"], gb["state0"]) <= 1e-3
