@@ -53,7 +53,10 @@ class Topo(C.Structure):
                 ("gravity", C.c_double * 3), ("dt", C.c_double), ("ground_z", C.c_double),
                 ("beta", C.c_double), ("gamma", C.c_double), ("slop", C.c_double), ("iters", C.c_int32),
                 ("loss_kind", C.c_int32), ("loss_mode", C.c_int32), ("loss_body", C.c_int32),
-                ("exact_mlp", C.c_int32)]
+                ("exact_mlp", C.c_int32), ("warmstart", C.c_int32), ("ws_W", PD)]
+
+WS_IN, WS_H, WS_OUT = 16, 64, 3
+WS_PARAMS = WS_IN * WS_H + WS_H + WS_H * WS_H + WS_H + WS_H * WS_OUT + WS_OUT
 
 
 INST_FIELDS = ("mass", "inertia", "anchor", "axis", "ref", "limit", "motor", "sph_off", "sph_rad", "sph_mu",
@@ -117,6 +120,9 @@ def topo(m, keep, iters=None):
     t.iters = m.iters if iters is None else iters
     t.loss_kind, t.loss_mode, t.loss_body = m.loss_kind, m.loss_mode, m.loss_body
     t.exact_mlp = int(getattr(m, "exact_mlp", 0) or getattr(m, "ctrl_fp32", 0))
+    ws = getattr(m, "ws_W", None)
+    t.warmstart = int(bool(getattr(m, "warmstart", 0)) and ws is not None)
+    t.ws_W = keep.f64(ws) if t.warmstart else None
     return t
 
 
@@ -242,3 +248,67 @@ def flops(m, i=0, horizon=None, W=None):
     if r != 0:
         raise ValueError("oracle rejected the model")
     return tuple(out)
+
+
+def step_log(m, i, x, t=0, W=None, iters=None):
+    """One step from state ``x`` with the full step record: dict with ``xn`` [nb, 18], ``active``,
+    ``gap``, ``lam`` (final impulses), ``lam0`` (initial impulses), ``margin`` (bfloat16 tie
+    margin), ``resid`` (RMS residual of the solve) and ``feats`` [ns + np, 16] (warm-start
+    features of every contact)."""
+    keep = _Keep()
+    tp = topo(m, keep, iters)
+    s = inst(m, i, keep)
+    ns = lib().orc_num_slots(C.byref(tp))
+    nc = m.ns + m.np_
+    x = np.ascontiguousarray(np.asarray(x, np.float64).reshape(-1))
+    xn = np.zeros_like(x)
+    active = np.zeros(max(ns, 1), np.int8)
+    gap, lam, lam0 = np.zeros(max(ns, 1)), np.zeros(max(ns, 1)), np.zeros(max(ns, 1))
+    marg, resid = np.zeros(1), np.zeros(1)
+    feats = np.zeros((max(nc, 1), WS_IN))
+    r = lib().orc_step_log(C.byref(tp), C.byref(s), weights(m, keep, W), t, _dp(x), _dp(xn),
+                           active.ctypes.data_as(C.POINTER(C.c_int8)), _dp(gap), _dp(lam), _dp(marg), _dp(resid),
+                           _dp(feats), _dp(lam0))
+    if r != 0:
+        raise ValueError("oracle rejected the model")
+    return dict(xn=xn.reshape(m.nb, 18), active=active[:ns], gap=gap[:ns], lam=lam[:ns], lam0=lam0[:ns],
+                margin=float(marg[0]), resid=float(resid[0]), feats=feats[:nc])
+
+
+def rollout_resid(m, i, horizon=None, W=None, iters=None):
+    """Rollout of instance ``i`` with the residual of every step's solve: (states, loss, resid [T])."""
+    T = m.horizon if horizon is None else horizon
+    keep = _Keep()
+    t = topo(m, keep, iters)
+    s = inst(m, i, keep)
+    states = np.zeros((T + 1, m.nb, 18))
+    resid = np.zeros(max(T, 1))
+    loss = C.c_double(0.0)
+    r = lib().orc_rollout_log(C.byref(t), C.byref(s), weights(m, keep, W), T, _dp(states), C.byref(loss), None, None,
+                              None, _dp(resid))
+    if r != 0:
+        raise ValueError("oracle rejected the model")
+    return states, loss.value, resid[:T]
+
+
+def ws_loss_grad(Wws, rows, exact=False):
+    """Mean squared error of the warm-start network over harvested rows [n, 19] and its gradient
+    [WS_PARAMS] (bfloat16 storage points unless ``exact``)."""
+    Wws = np.ascontiguousarray(np.asarray(Wws, np.float64).reshape(-1))
+    rows = np.ascontiguousarray(np.asarray(rows, np.float64).reshape(-1, 19))
+    assert Wws.size == WS_PARAMS
+    loss = C.c_double(0.0)
+    dW = np.zeros(WS_PARAMS)
+    r = lib().orc_ws_loss_grad(_dp(Wws), _dp(rows), C.c_int64(rows.shape[0]), int(exact), C.byref(loss), _dp(dW))
+    if r != 0:
+        raise ValueError("oracle rejected the rows")
+    return loss.value, dW
+
+
+def ws_forward(Wws, feats, exact=False):
+    """Warm-start network outputs [n, 3] for features [n, 16]."""
+    Wws = np.ascontiguousarray(np.asarray(Wws, np.float64).reshape(-1))
+    feats = np.ascontiguousarray(np.asarray(feats, np.float64).reshape(-1, WS_IN))
+    y = np.zeros((feats.shape[0], WS_OUT))
+    lib().orc_ws_forward(_dp(Wws), _dp(feats), C.c_int64(feats.shape[0]), int(exact), _dp(y))
+    return y

@@ -242,7 +242,13 @@ typedef struct {
   int32_t iters;
   int32_t loss_kind, loss_mode, loss_body;
   int32_t exact_mlp;           // 1: skip the bfloat16 rounding (finite-difference checks only)
+  int32_t warmstart;           // 1: contact impulses start from the learned warm start (ws_W)
+  const double* ws_W;          // warm-start network parameters [ORC_WS_PARAMS]
 } orc_topo;
+
+// Learned warm start: a 16-64-64-3 network per contact (W1, b1, W2, b2, W3, b3; W[out][in]).
+enum { ORC_WS_IN = 16, ORC_WS_H = 64, ORC_WS_OUT = 3,
+       ORC_WS_PARAMS = ORC_WS_IN * ORC_WS_H + ORC_WS_H + ORC_WS_H * ORC_WS_H + ORC_WS_H + ORC_WS_H * ORC_WS_OUT + ORC_WS_OUT };
 
 typedef struct {
   const double* mass;         // [nb]
@@ -367,7 +373,40 @@ struct StepLog {
   double* gap;
   double* lambda;       // final impulses per slot
   double* bf16_margin;  // see g_bf16_margin
+  double* resid;        // RMS complementarity residual of the solve over the active rows
+  double* feats;        // [ns + np][ORC_WS_IN] warm-start features of every contact
+  double* lam0;         // [n_slots] initial impulses of the solve
 };
+
+// The warm-start network on one feature vector: inputs, weights and hidden activations stored
+// in bfloat16, fp32 biases, ReLU hidden layers, linear output.
+template <class S, class SW>
+static void ws_forward(const SW* W, const S* x, S* y) {
+  const int I = ORC_WS_IN, H = ORC_WS_H, O = ORC_WS_OUT;
+  const SW* W1 = W;
+  const SW* b1 = W1 + I * H;
+  const SW* W2 = b1 + H;
+  const SW* b2 = W2 + H * H;
+  const SW* W3 = b2 + H;
+  const SW* b3 = W3 + H * O;
+  S xi[ORC_WS_IN], h1[ORC_WS_H], h2[ORC_WS_H];
+  for (int i = 0; i < I; ++i) xi[i] = round_bf16(x[i]);
+  for (int o = 0; o < H; ++o) {
+    S acc = b1[o];
+    for (int i = 0; i < I; ++i) acc += round_bf16_w(W1[o * I + i]) * xi[i];
+    h1[o] = round_bf16(relu(acc));
+  }
+  for (int o = 0; o < H; ++o) {
+    S acc = b2[o];
+    for (int i = 0; i < H; ++i) acc += round_bf16_w(W2[o * H + i]) * h1[i];
+    h2[o] = round_bf16(relu(acc));
+  }
+  for (int o = 0; o < O; ++o) {
+    S acc = b3[o];
+    for (int i = 0; i < H; ++i) acc += round_bf16_w(W3[o * H + i]) * h2[i];
+    y[o] = acc;
+  }
+}
 
 // The loss point q = p_b + R_b c of the body named by loss_body.
 template <class S> static V3<S> loss_point_of(const orc_topo& T, const Inst<S>& P, const std::vector<S>& x) {
@@ -649,16 +688,101 @@ static void step(const orc_topo& T, const std::vector<Slot>& slots, const std::v
     }
   }
 
-  // Projected Gauss-Seidel, cold start (lambda = 0), fixed number of sweeps in the
-  // canonical order: lambda' = clamp(lambda - meff (J v + bias + gamma lambda), lo, hi),
-  // then v += M^-1 J^T (lambda' - lambda).
+  auto Jv_of = [&](const Row& r) {
+    return dot(r.lin, vsub(vof(r.a), vof(r.b))) + dot(r.angA, wvof(r.a)) + dot(r.angB, wvof(r.b));
+  };
+  auto apply = [&](const Row& r, S dl) {
+    if (r.a >= 0) {
+      v[r.a] = vadd(v[r.a], vscale(r.lin, dl * invm[r.a]));
+      w[r.a] = vadd(w[r.a], vscale(matvec(Iinv[r.a], r.angA), dl));
+    }
+    if (r.b >= 0) {
+      v[r.b] = vsub(v[r.b], vscale(r.lin, dl * invm[r.b]));
+      w[r.b] = vadd(w[r.b], vscale(matvec(Iinv[r.b], r.angB), dl));
+    }
+  };
+
+  // Initial impulses: zero (cold start), or the learned warm start on the contact rows. The
+  // warm start sees 16 features of each contact, computed from the assembled rows and the
+  // pre-solve velocities; its output (normal, t1, t2 impulses) is projected on the bounds
+  // (normal >= 0, |friction| <= mu normal) and applied in slot order before the sweeps. It is a
+  // starting guess, not part of the modelled dynamics: reverse mode treats it as a constant.
   std::vector<S> lam(ns_, S(0.0));
+  std::vector<int> cnorm;  // normal slot of every contact (ground contacts, then pairs)
+  for (int si = 0; si < ns_; ++si)
+    if (slots[si].kind == ORC_GN || slots[si].kind == ORC_PN) cnorm.push_back(si);
+  if (T.warmstart || (log && log->feats)) {
+    double mtot = 0.0, pc[3] = {0.0, 0.0, 0.0}, vcz = 0.0;
+    for (int b = 0; b < nb; ++b) {
+      double m = val(P.mass[b]);
+      mtot += m;
+      for (int k = 0; k < 3; ++k) pc[k] += m * val(p[b][k]);
+      vcz += m * val(v[b][2]);
+    }
+    for (int k = 0; k < 3; ++k) pc[k] /= mtot;
+    vcz /= mtot;
+    int nact = 0;
+    for (int n : cnorm) nact += rows[n].active ? 1 : 0;
+    const double gnorm = std::sqrt(T.gravity[0] * T.gravity[0] + T.gravity[1] * T.gravity[1] + T.gravity[2] * T.gravity[2]);
+    for (size_t c = 0; c < cnorm.size(); ++c) {
+      const int n = cnorm[c];
+      const Row &rn = rows[n], &r1 = rows[n + 1], &r2 = rows[n + 2];
+      const int a = rn.a;
+      // lever arm r_a of the contact point on body a
+      V3<S> ra;
+      if (slots[n].kind == ORC_GN) {
+        int q = slots[n].idx;
+        ra = vsub(matvec(R[a], get3(P.sph_off, 3 * q)), vscale(ez, P.sph_rad[q]));
+      } else {
+        int k = T.pair_sphere[2 * slots[n].idx];
+        ra = vsub(matvec(R[a], get3(P.sph_off, 3 * k)), vscale(rn.lin, P.sph_rad[k]));
+      }
+      double phi[ORC_WS_IN];
+      phi[0] = val(Jv_of(rn));
+      phi[1] = val(Jv_of(r1));
+      phi[2] = val(Jv_of(r2));
+      phi[3] = val(rn.bias);
+      phi[4] = val(rn.meff);
+      phi[5] = val(r1.meff);
+      phi[6] = val(r2.meff);
+      phi[7] = val(r1.mu);
+      phi[8] = (double)nact;
+      phi[9] = mtot * gnorm * h / std::max(1, nact);
+      phi[10] = vcz;
+      phi[11] = val(p[a][0]) + val(ra[0]) - pc[0];
+      phi[12] = val(p[a][1]) + val(ra[1]) - pc[1];
+      phi[13] = pc[2] - T.ground_z;
+      phi[14] = phi[4] * (-phi[0] - phi[3]);
+      phi[15] = slots[n].kind == ORC_PN ? 1.0 : 0.0;
+      if (log && log->feats)
+        for (int k = 0; k < ORC_WS_IN; ++k) log->feats[c * ORC_WS_IN + k] = phi[k];
+      if (!T.warmstart || !rn.active) continue;
+      double y[ORC_WS_OUT];
+      ws_forward<double, double>(T.ws_W, phi, y);
+      double l0[3];
+      l0[0] = y[0] > 0.0 ? y[0] : 0.0;
+      const double hi = val(r1.mu) * l0[0];
+      l0[1] = y[1] < -hi ? -hi : (y[1] > hi ? hi : y[1]);
+      l0[2] = y[2] < -hi ? -hi : (y[2] > hi ? hi : y[2]);
+      for (int k = 0; k < 3; ++k) lam[n + k] = S(l0[k]);
+    }
+    if (T.warmstart)
+      for (int n : cnorm)
+        for (int k = 0; k < 3; ++k)
+          if (rows[n + k].active) apply(rows[n + k], lam[n + k]);
+  }
+  if (log && log->lam0)
+    for (int si = 0; si < ns_; ++si) log->lam0[si] = val(lam[si]);
+
+  // Projected Gauss-Seidel, fixed number of sweeps in the canonical order:
+  // lambda' = clamp(lambda - meff (J v + bias + gamma lambda), lo, hi),
+  // then v += M^-1 J^T (lambda' - lambda).
   for (int it = 0; it < T.iters; ++it) {
     for (int oi = 0; oi < ns_; ++oi) {
       int si = order[oi];
       Row& r = rows[si];
       if (!r.active) continue;
-      S Jv = dot(r.lin, vsub(vof(r.a), vof(r.b))) + dot(r.angA, wvof(r.a)) + dot(r.angB, wvof(r.b));
+      S Jv = Jv_of(r);
       S lo = r.lo, hi = r.hi;
       if (r.friction) {
         hi = r.mu * lam[r.normal];
@@ -668,18 +792,39 @@ static void step(const orc_topo& T, const std::vector<Slot>& slots, const std::v
       S ln = clamp_sel(pre, lo, hi, (int*)nullptr);
       S dl = ln - lam[si];
       lam[si] = ln;
-      if (r.a >= 0) {
-        v[r.a] = vadd(v[r.a], vscale(r.lin, dl * invm[r.a]));
-        w[r.a] = vadd(w[r.a], vscale(matvec(Iinv[r.a], r.angA), dl));
-      }
-      if (r.b >= 0) {
-        v[r.b] = vsub(v[r.b], vscale(r.lin, dl * invm[r.b]));
-        w[r.b] = vadd(w[r.b], vscale(matvec(Iinv[r.b], r.angB), dl));
-      }
+      apply(r, dl);
     }
   }
   if (log && log->lambda)
     for (int si = 0; si < ns_; ++si) log->lambda[si] = val(lam[si]);
+  // Residual of the solve: per active row with w = J v + bias + gamma lambda,
+  // bilateral |w|; one-sided [0, inf) |min(lambda, w)|; boxed |lambda - clamp(lambda - w, lo, hi)|
+  // (motors: +-tau_max h, friction: +-mu lambda_n); RMS over the active rows.
+  if (log && log->resid) {
+    double ss = 0.0;
+    int na = 0;
+    for (int si = 0; si < ns_; ++si) {
+      const Row& r = rows[si];
+      if (!r.active) continue;
+      const double wv = val(Jv_of(r)) + val(r.bias) + T.gamma * val(lam[si]), l = val(lam[si]);
+      const int kd = slots[si].kind;
+      double e;
+      if (kd == ORC_JLIN || kd == ORC_JANG) {
+        e = wv;
+      } else if (kd == ORC_LIMIT || kd == ORC_GN || kd == ORC_PN) {
+        e = std::min(l, wv);
+      } else {
+        double lo = val(r.lo), hi = val(r.hi);
+        if (r.friction) { hi = val(r.mu) * val(lam[r.normal]); lo = -hi; }
+        double z = l - wv;
+        z = z < lo ? lo : (z > hi ? hi : z);
+        e = l - z;
+      }
+      ss += e * e;
+      ++na;
+    }
+    *log->resid = na ? std::sqrt(ss / na) : 0.0;
+  }
   if (log && log->bf16_margin) *log->bf16_margin = g_bf16_margin;
 
   // Semi-implicit Euler with the new velocities, then the Eq. 1 renormalisation.
@@ -769,6 +914,74 @@ int orc_schedule(const orc_topo* T, int32_t* kind, int32_t* idx, int32_t* sub, i
   return (int)s.size();
 }
 
+// One step from a given state (used for teacher-forced comparisons), with the solve's residual,
+// the warm-start features of every contact [ns + np][16] and the initial impulses [n_slots].
+int orc_step_log(const orc_topo* T, const orc_inst* I, const double* W, int32_t t, const double* x, double* xn,
+                 int8_t* active, double* gap, double* lambda, double* bf16_margin, double* resid, double* feats,
+                 double* lam0) {
+  if (check_topo(T)) return -1;
+  auto slots = make_slots(*T);
+  std::vector<int> col, ord;
+  make_schedule(slots, col, ord);
+  Inst<double> P = lift_inst<double>(*T, *I);
+  int np_ = param_count(T->n_layers, T->widths, T->skip);
+  std::vector<double> Wv(W ? W : nullptr, W ? W + np_ : nullptr);
+  std::vector<double> xs(x, x + 18 * T->nb), xo;
+  std::vector<int8_t> act(slots.size());
+  std::vector<double> gp(slots.size());
+  StepLog lg{active ? active : act.data(), gap ? gap : gp.data(), lambda, bf16_margin, resid, feats, lam0};
+  step<double>(*T, slots, ord, P, Wv, t, xs, xo, 0.0, nullptr, &lg);
+  std::memcpy(xn, xo.data(), sizeof(double) * xo.size());
+  return 0;
+}
+
+// Mean squared error of the warm-start network over n harvested rows [n][19] (16 features,
+// then the 3 converged impulses): loss = (1/n) sum_rows sum_k (y_k - lambda_k)^2, and its
+// gradient w.r.t. the ORC_WS_PARAMS parameters (reverse mode, straight-through roundings).
+// exact = 1 drops the bfloat16 roundings.
+int orc_ws_loss_grad(const double* Wws, const double* rows, int64_t n, int32_t exact, double* loss, double* dW) {
+  if (n <= 0) return -1;
+  Tape tape;
+  Tape* saved = g_tape;
+  g_tape = &tape;
+  g_exact_mlp = exact != 0;
+  double L = 0.0;
+  std::vector<double> g(ORC_WS_PARAMS, 0.0);
+  for (int64_t r = 0; r < n; ++r) {
+    tape.clear();
+    std::vector<AD> Wl = lift_leaf(Wws, ORC_WS_PARAMS);
+    AD x[ORC_WS_IN], y[ORC_WS_OUT];
+    for (int k = 0; k < ORC_WS_IN; ++k) x[k] = AD(rows[r * 19 + k]);
+    ws_forward<AD, AD>(Wl.data(), x, y);
+    AD e = AD(0.0);
+    for (int k = 0; k < ORC_WS_OUT; ++k) {
+      AD d = y[k] - AD(rows[r * 19 + ORC_WS_IN + k]);
+      e += d * d;
+    }
+    L += e.v;
+    tape.adj.assign(tape.pa.size(), 0.0);
+    if (e.id >= 0) tape.adj[e.id] = 1.0;
+    tape.backward();
+    for (int k = 0; k < ORC_WS_PARAMS; ++k) g[k] += tape.adj[Wl[k].id];
+  }
+  g_tape = saved;
+  g_exact_mlp = false;
+  if (loss) *loss = L / (double)n;
+  if (dW)
+    for (int k = 0; k < ORC_WS_PARAMS; ++k) dW[k] = g[k] / (double)n;
+  return 0;
+}
+
+// The warm-start network's outputs [n][3] for features [n][16].
+int orc_ws_forward(const double* Wws, const double* feats, int64_t n, int32_t exact, double* y) {
+  g_exact_mlp = exact != 0;
+  for (int64_t r = 0; r < n; ++r) ws_forward<double, double>(Wws, feats + r * ORC_WS_IN, y + r * ORC_WS_OUT);
+  g_exact_mlp = false;
+  return 0;
+}
+
+int orc_ws_param_count() { return ORC_WS_PARAMS; }
+
 // One step from a given state (used for teacher-forced comparisons).
 int orc_step(const orc_topo* T, const orc_inst* I, const double* W, int32_t t, const double* x, double* xn,
              int8_t* active, double* gap, double* lambda, double* bf16_margin) {
@@ -788,8 +1001,15 @@ int orc_step(const orc_topo* T, const orc_inst* I, const double* W, int32_t t, c
 
 // Full rollout of `horizon` steps; writes all states [horizon+1][nb][18] (optional), the loss,
 // and per step the slot activity / decision distances [horizon][n_slots] (optional).
+int orc_rollout_log(const orc_topo* T, const orc_inst* I, const double* W, int32_t horizon, double* states,
+                    double* loss, int8_t* active, double* gap, double* bf16_margin, double* resid);
 int orc_rollout(const orc_topo* T, const orc_inst* I, const double* W, int32_t horizon, double* states,
                 double* loss, int8_t* active, double* gap, double* bf16_margin) {
+  return orc_rollout_log(T, I, W, horizon, states, loss, active, gap, bf16_margin, nullptr);
+}
+// orc_rollout that also gives the residual of every step's solve [horizon].
+int orc_rollout_log(const orc_topo* T, const orc_inst* I, const double* W, int32_t horizon, double* states,
+                    double* loss, int8_t* active, double* gap, double* bf16_margin, double* resid) {
   if (check_topo(T) || horizon < 0) return -1;
   auto slots = make_slots(*T);
   std::vector<int> col, ord;
@@ -803,10 +1023,13 @@ int orc_rollout(const orc_topo* T, const orc_inst* I, const double* W, int32_t h
   if (states) std::memcpy(states, x.data(), sizeof(double) * x.size());
   for (int t = 0; t < horizon; ++t) {
     double lt = 0.0;
-    StepLog lg{active ? active + (size_t)t * nsl : nullptr, gap ? gap + (size_t)t * nsl : nullptr, nullptr,
-               bf16_margin ? bf16_margin + t : nullptr};
+    std::vector<int8_t> act_tmp;
+    std::vector<double> gap_tmp;
+    if (resid && !(active && gap)) { act_tmp.resize(nsl); gap_tmp.resize(nsl); }
+    StepLog lg{active ? active + (size_t)t * nsl : act_tmp.data(), gap ? gap + (size_t)t * nsl : gap_tmp.data(),
+               nullptr, bf16_margin ? bf16_margin + t : nullptr, resid ? resid + t : nullptr, nullptr, nullptr};
     step<double>(*T, slots, ord, P, Wv, t, x, xn, weight_of_state(*T, t + 1, horizon), &lt,
-                 (active && gap) ? &lg : nullptr);
+                 ((active && gap) || resid) ? &lg : nullptr);
     L += lt;
     x.swap(xn);
     if (states) std::memcpy(states + (size_t)(t + 1) * 18 * T->nb, x.data(), sizeof(double) * x.size());
