@@ -758,7 +758,10 @@ static void step(const orc_topo& T, const std::vector<Slot>& slots, const std::v
         for (int k = 0; k < ORC_WS_IN; ++k) log->feats[c * ORC_WS_IN + k] = phi[k];
       if (!T.warmstart || !rn.active) continue;
       double y[ORC_WS_OUT];
+      const bool exact_ctrl = g_exact_mlp;  // the warm-start network always keeps its bfloat16 storage
+      g_exact_mlp = false;
       ws_forward<double, double>(T.ws_W, phi, y);
+      g_exact_mlp = exact_ctrl;
       double l0[3];
       l0[0] = y[0] > 0.0 ? y[0] : 0.0;
       const double hi = val(r1.mu) * l0[0];
