@@ -253,13 +253,13 @@ def flops(m, i=0, horizon=None, W=None):
 def step_log(m, i, x, t=0, W=None, iters=None):
     """One step from state ``x`` with the full step record: dict with ``xn`` [nb, 18], ``active``,
     ``gap``, ``lam`` (final impulses), ``lam0`` (initial impulses), ``margin`` (bfloat16 tie
-    margin), ``resid`` (RMS residual of the solve) and ``feats`` [ns + np, 16] (warm-start
-    features of every contact)."""
+    margin), ``resid`` (RMS residual of the solve) and ``feats`` [groups, 16] (warm-start
+    features of every group, see ``ws_groups``)."""
     keep = _Keep()
     tp = topo(m, keep, iters)
     s = inst(m, i, keep)
     ns = lib().orc_num_slots(C.byref(tp))
-    nc = m.ns + m.np_
+    nc = lib().orc_ws_groups(C.byref(tp))
     x = np.ascontiguousarray(np.asarray(x, np.float64).reshape(-1))
     xn = np.zeros_like(x)
     active = np.zeros(max(ns, 1), np.int8)
@@ -312,3 +312,25 @@ def ws_forward(Wws, feats, exact=False):
     y = np.zeros((feats.shape[0], WS_OUT))
     lib().orc_ws_forward(_dp(Wws), _dp(feats), C.c_int64(feats.shape[0]), int(exact), _dp(y))
     return y
+
+
+WS_GROUND, WS_PAIR, WS_JOINT, WS_HINGE = 0, 1, 2, 3
+
+
+def ws_groups(m):
+    """Warm-start groups of a model, in the oracle's order: list of (type, (slot0, slot1, slot2)),
+    derived from the slot schedule (joint linear rows, hinge angular rows + motor, contacts)."""
+    sch = schedule(m)
+    kind, idx, sub = sch["kind"], sch["idx"], sch["sub"]
+    out = []
+    for i in range(len(kind)):
+        if kind[i] == 0 and sub[i] == 0:
+            out.append((WS_JOINT, (i, i + 1, i + 2)))
+        elif kind[i] == 1 and sub[i] == 0:
+            mot = [k for k in range(len(kind)) if kind[k] == 3 and idx[k] == idx[i]]
+            out.append((WS_HINGE, (i, i + 1, mot[-1] if mot else -1)))
+        elif kind[i] == 4:
+            out.append((WS_GROUND, (i, i + 1, i + 2)))
+        elif kind[i] == 6:
+            out.append((WS_PAIR, (i, i + 1, i + 2)))
+    return out

@@ -331,6 +331,33 @@ static void make_schedule(const std::vector<Slot>& s, std::vector<int>& colour, 
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return colour[x] < colour[y]; });
 }
 
+// Warm-start groups of three rows, in slot order of their first row: the linear rows of each
+// joint (x, y, z), the angular rows of each hinge with its motor row (slot -1 without a motor),
+// and the normal, t1, t2 rows of each contact.
+enum { WS_GROUND = 0, WS_PAIR = 1, WS_JOINT = 2, WS_HINGE = 3 };
+struct WsGroup {
+  int type, slot[3];
+};
+static std::vector<WsGroup> ws_groups(const orc_topo& T, const std::vector<Slot>& s) {
+  std::vector<WsGroup> g;
+  const int n = (int)s.size();
+  for (int i = 0; i < n; ++i) {
+    if (s[i].kind == ORC_JLIN && s[i].sub == 0) {
+      g.push_back({WS_JOINT, {i, i + 1, i + 2}});
+    } else if (s[i].kind == ORC_JANG && s[i].sub == 0) {
+      int motor = -1;
+      for (int k = 0; k < n; ++k)
+        if (s[k].kind == ORC_MOTOR && s[k].idx == s[i].idx) motor = k;
+      g.push_back({WS_HINGE, {i, i + 1, motor}});
+    } else if (s[i].kind == ORC_GN) {
+      g.push_back({WS_GROUND, {i, i + 1, i + 2}});
+    } else if (s[i].kind == ORC_PN) {
+      g.push_back({WS_PAIR, {i, i + 1, i + 2}});
+    }
+  }
+  return g;
+}
+
 template <class S> struct Inst {
   std::vector<S> mass, inertia, anchor, axis, ref, limit, motor, sph_off, sph_rad, sph_mu, sph_e, loss_point, loss_target;
 };
@@ -374,7 +401,7 @@ struct StepLog {
   double* lambda;       // final impulses per slot
   double* bf16_margin;  // see g_bf16_margin
   double* resid;        // RMS complementarity residual of the solve over the active rows
-  double* feats;        // [ns + np][ORC_WS_IN] warm-start features of every contact
+  double* feats;        // [groups][ORC_WS_IN] warm-start features of every group
   double* lam0;         // [n_slots] initial impulses of the solve
 };
 
@@ -702,77 +729,88 @@ static void step(const orc_topo& T, const std::vector<Slot>& slots, const std::v
     }
   };
 
-  // Initial impulses: zero (cold start), or the learned warm start on the contact rows. The
-  // warm start sees 16 features of each contact, computed from the assembled rows and the
-  // pre-solve velocities; its output (normal, t1, t2 impulses) is projected on the bounds
-  // (normal >= 0, |friction| <= mu normal) and applied in slot order before the sweeps. It is a
-  // starting guess, not part of the modelled dynamics: reverse mode treats it as a constant.
+  // Initial impulses: zero (cold start), or the learned warm start. The warm start works on
+  // groups of three rows: the linear rows of a joint, the angular rows of a hinge with its motor
+  // row, and the normal and friction rows of a contact. Each group gets 16 features from its
+  // assembled rows, the pre-solve velocities and the robot's mass distribution; the network's
+  // three outputs are projected on the rows' bounds and applied in slot order before the
+  // sweeps. It is a starting guess, not part of the modelled dynamics: reverse mode treats it as
+  // a constant.
   std::vector<S> lam(ns_, S(0.0));
-  std::vector<int> cnorm;  // normal slot of every contact (ground contacts, then pairs)
-  for (int si = 0; si < ns_; ++si)
-    if (slots[si].kind == ORC_GN || slots[si].kind == ORC_PN) cnorm.push_back(si);
+  const std::vector<WsGroup> groups = ws_groups(T, slots);
   if (T.warmstart || (log && log->feats)) {
-    double mtot = 0.0, pc[3] = {0.0, 0.0, 0.0}, vcz = 0.0;
+    double mtot = 0.0, pc[3] = {0.0, 0.0, 0.0};
     for (int b = 0; b < nb; ++b) {
       double m = val(P.mass[b]);
       mtot += m;
       for (int k = 0; k < 3; ++k) pc[k] += m * val(p[b][k]);
-      vcz += m * val(v[b][2]);
     }
     for (int k = 0; k < 3; ++k) pc[k] /= mtot;
-    vcz /= mtot;
     int nact = 0;
-    for (int n : cnorm) nact += rows[n].active ? 1 : 0;
+    for (int si = 0; si < ns_; ++si)
+      if ((slots[si].kind == ORC_GN || slots[si].kind == ORC_PN) && rows[si].active) ++nact;
     const double gnorm = std::sqrt(T.gravity[0] * T.gravity[0] + T.gravity[1] * T.gravity[1] + T.gravity[2] * T.gravity[2]);
-    for (size_t c = 0; c < cnorm.size(); ++c) {
-      const int n = cnorm[c];
-      const Row &rn = rows[n], &r1 = rows[n + 1], &r2 = rows[n + 2];
-      const int a = rn.a;
-      // lever arm r_a of the contact point on body a
-      V3<S> ra;
-      if (slots[n].kind == ORC_GN) {
-        int q = slots[n].idx;
-        ra = vsub(matvec(R[a], get3(P.sph_off, 3 * q)), vscale(ez, P.sph_rad[q]));
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+      const WsGroup& G = groups[gi];
+      const Slot& s0 = slots[G.slot[0]];
+      // the group's point: the contact point on body a, or the joint's anchor on its child body
+      V3<S> q;
+      if (G.type == WS_GROUND) {
+        int qi = s0.idx, a = s0.a;
+        q = vadd(p[a], vsub(matvec(R[a], get3(P.sph_off, 3 * qi)), vscale(ez, P.sph_rad[qi])));
+      } else if (G.type == WS_PAIR) {
+        int k = T.pair_sphere[2 * s0.idx], a = s0.a;
+        q = vadd(p[a], vsub(matvec(R[a], get3(P.sph_off, 3 * k)), vscale(rows[G.slot[0]].lin, P.sph_rad[k])));
       } else {
-        int k = T.pair_sphere[2 * slots[n].idx];
-        ra = vsub(matvec(R[a], get3(P.sph_off, 3 * k)), vscale(rn.lin, P.sph_rad[k]));
+        int j = s0.idx, b = s0.b;
+        q = vadd(p[b], matvec(R[b], get3(P.anchor, 6 * j + 3)));
       }
       double phi[ORC_WS_IN];
-      phi[0] = val(Jv_of(rn));
-      phi[1] = val(Jv_of(r1));
-      phi[2] = val(Jv_of(r2));
-      phi[3] = val(rn.bias);
-      phi[4] = val(rn.meff);
-      phi[5] = val(r1.meff);
-      phi[6] = val(r2.meff);
-      phi[7] = val(r1.mu);
-      phi[8] = (double)nact;
-      phi[9] = mtot * gnorm * h / std::max(1, nact);
-      phi[10] = vcz;
-      phi[11] = val(p[a][0]) + val(ra[0]) - pc[0];
-      phi[12] = val(p[a][1]) + val(ra[1]) - pc[1];
-      phi[13] = pc[2] - T.ground_z;
-      phi[14] = phi[4] * (-phi[0] - phi[3]);
-      phi[15] = slots[n].kind == ORC_PN ? 1.0 : 0.0;
+      for (int k = 0; k < 3; ++k) {
+        const int si = G.slot[k];
+        const bool on = si >= 0 && rows[si].active;  // rows of inactive slots contribute zeros
+        phi[k] = on ? val(Jv_of(rows[si])) : 0.0;
+        phi[3 + k] = on ? val(rows[si].bias) : 0.0;
+        phi[6 + k] = on ? val(rows[si].meff) : 0.0;
+      }
+      phi[9] = G.type == WS_GROUND || G.type == WS_PAIR ? val(rows[G.slot[1]].mu)
+               : (G.type == WS_HINGE && G.slot[2] >= 0 ? val(rows[G.slot[2]].hi) : 0.0);
+      phi[10] = mtot * gnorm * h / std::max(1, nact);
+      phi[11] = (double)nact;
+      phi[12] = val(q[0]) - pc[0];
+      phi[13] = val(q[1]) - pc[1];
+      phi[14] = val(q[2]) - T.ground_z;
+      phi[15] = (double)G.type;
       if (log && log->feats)
-        for (int k = 0; k < ORC_WS_IN; ++k) log->feats[c * ORC_WS_IN + k] = phi[k];
-      if (!T.warmstart || !rn.active) continue;
+        for (int k = 0; k < ORC_WS_IN; ++k) log->feats[gi * ORC_WS_IN + k] = phi[k];
+      if (!T.warmstart) continue;
       double y[ORC_WS_OUT];
       const bool exact_ctrl = g_exact_mlp;  // the warm-start network always keeps its bfloat16 storage
       g_exact_mlp = false;
       ws_forward<double, double>(T.ws_W, phi, y);
       g_exact_mlp = exact_ctrl;
-      double l0[3];
-      l0[0] = y[0] > 0.0 ? y[0] : 0.0;
-      const double hi = val(r1.mu) * l0[0];
-      l0[1] = y[1] < -hi ? -hi : (y[1] > hi ? hi : y[1]);
-      l0[2] = y[2] < -hi ? -hi : (y[2] > hi ? hi : y[2]);
-      for (int k = 0; k < 3; ++k) lam[n + k] = S(l0[k]);
+      auto clampd = [](double x, double lo, double hi) { return x < lo ? lo : (x > hi ? hi : x); };
+      double l0[3] = {0.0, 0.0, 0.0};
+      if (G.type == WS_GROUND || G.type == WS_PAIR) {
+        if (rows[G.slot[0]].active) {
+          l0[0] = y[0] > 0.0 ? y[0] : 0.0;
+          const double hi = val(rows[G.slot[1]].mu) * l0[0];
+          l0[1] = clampd(y[1], -hi, hi);
+          l0[2] = clampd(y[2], -hi, hi);
+        }
+      } else {
+        for (int k = 0; k < 3; ++k) {
+          const int si = G.slot[k];
+          if (si < 0 || !rows[si].active) continue;
+          l0[k] = slots[si].kind == ORC_MOTOR ? clampd(y[k], val(rows[si].lo), val(rows[si].hi)) : y[k];
+        }
+      }
+      for (int k = 0; k < 3; ++k)
+        if (G.slot[k] >= 0) lam[G.slot[k]] = S(l0[k]);
     }
     if (T.warmstart)
-      for (int n : cnorm)
-        for (int k = 0; k < 3; ++k)
-          if (rows[n + k].active) apply(rows[n + k], lam[n + k]);
+      for (int si = 0; si < ns_; ++si)
+        if (rows[si].active && val(lam[si]) != 0.0) apply(rows[si], lam[si]);
   }
   if (log && log->lam0)
     for (int si = 0; si < ns_; ++si) log->lam0[si] = val(lam[si]);
@@ -918,7 +956,7 @@ int orc_schedule(const orc_topo* T, int32_t* kind, int32_t* idx, int32_t* sub, i
 }
 
 // One step from a given state (used for teacher-forced comparisons), with the solve's residual,
-// the warm-start features of every contact [ns + np][16] and the initial impulses [n_slots].
+// the warm-start features of every group [orc_ws_groups][16] and the initial impulses [n_slots].
 int orc_step_log(const orc_topo* T, const orc_inst* I, const double* W, int32_t t, const double* x, double* xn,
                  int8_t* active, double* gap, double* lambda, double* bf16_margin, double* resid, double* feats,
                  double* lam0) {
@@ -984,6 +1022,12 @@ int orc_ws_forward(const double* Wws, const double* feats, int64_t n, int32_t ex
 }
 
 int orc_ws_param_count() { return ORC_WS_PARAMS; }
+
+// Number of warm-start groups of the topology (rows of the feature log of orc_step_log).
+int orc_ws_groups(const orc_topo* T) {
+  if (check_topo(T)) return -1;
+  return (int)ws_groups(*T, make_slots(*T)).size();
+}
 
 // One step from a given state (used for teacher-forced comparisons).
 int orc_step(const orc_topo* T, const orc_inst* I, const double* W, int32_t t, const double* x, double* xn,

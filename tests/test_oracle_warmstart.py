@@ -2,8 +2,9 @@
 (no GPU).
 
 What each test pins:
-* the 16 contact features, against closed forms of the quadruped's first step (robot at rest
-  vertically, feet directly below the lower-link centres, gravity impulse only);
+* the 16 features of every row group (joint, hinge + motor, contact), against closed forms of
+  the quadruped's first step (robot at rest vertically, joints closed, feet directly below the
+  lower-link centres, gravity impulse only);
 * the residual, by the facts that it vanishes at a converged solve for every row kind (a
   sliding sphere is solved exactly in one sweep; the quadruped after many sweeps) and shrinks
   with the number of sweeps;
@@ -50,8 +51,14 @@ def const_ws(b3):
 
 
 # ----------------------------------------------------------------------------- features
-def test_contact_features_closed_form_first_step():
+def test_group_features_closed_form_first_step():
+    """First step of the quadruped at rest vertically (yaw 0): every body has the same velocity
+    and no spin, the joints are closed, the feet sit 1 mm inside the ground straight below the
+    lower-link centres, and the only impulse before the solve is gravity's."""
     m = WL.quadruped(B=3, horizon=1, yaw=0.0)  # body axes along the world axes
+    groups = O.ws_groups(m)
+    types = [g[0] for g in groups]
+    assert types == [O.WS_JOINT, O.WS_HINGE] * 8 + [O.WS_GROUND] * 8
     for i in range(m.B):
         d = O.step_log(m, i, m.state0[i], t=0)
         f = d["feats"]
@@ -61,26 +68,41 @@ def test_contact_features_closed_form_first_step():
         mass = m.mass[i]
         M = mass.sum()
         pc = (mass[:, None] * x0[:, :3]).sum(0) / M
+        tau_h = m.motor[i, 0, 1] * h
+        for j in range(8):  # joints: closed, no relative motion
+            lin, hin = f[2 * j], f[2 * j + 1]
+            child = m.joint_body[j, 1]
+            q = x0[child, :3] + m.anchor[i, j, 1]
+            for g, code, bound in ((lin, O.WS_JOINT, 0.0), (hin, O.WS_HINGE, tau_h)):
+                np.testing.assert_allclose(g[0:3], 0.0, atol=1e-12)
+                np.testing.assert_allclose(g[9], bound, rtol=1e-12)
+                np.testing.assert_allclose(g[10], M * G * h / 4.0, rtol=1e-12)
+                assert g[11] == 4.0 and g[15] == code
+                np.testing.assert_allclose(g[12:14], (q - pc)[:2], atol=1e-12)
+                np.testing.assert_allclose(g[14], q[2] - m.ground_z, atol=1e-12)
+            np.testing.assert_allclose(lin[3:6], 0.0, atol=1e-6)  # closed joint (to the inputs' float32 grid)
+            np.testing.assert_allclose(hin[3:5], 0.0, atol=1e-6)  # aligned hinge axes
+            assert abs(hin[5]) <= m.motor[i, j, 2] + 1e-12  # servo rate within +-vmax
+            assert (lin[6:9] > 0).all() and (hin[6:9] > 0).all()
         for c in range(4):  # feet
+            g = f[16 + c]
             body = m.sphere_body[c]
             Ix = float(m.inertia[i, body, 0])  # capsule moment about a horizontal axis
-            # the foot centre sits straight below the lower link's centre: lever arm of the
-            # contact point, straight down
-            ell = -float(m.sph_off[i, c, 2]) + float(m.sph_rad[i, c])
+            ell = -float(m.sph_off[i, c, 2]) + float(m.sph_rad[i, c])  # contact point below the centre
             q = x0[body, :3] + np.array([0.0, 0.0, -ell])
-            np.testing.assert_allclose(f[c, 0], -G * h, rtol=1e-12)
-            np.testing.assert_allclose(f[c, 1:3], [vx, vy], atol=1e-12)
-            assert f[c, 3] == 0.0  # inside the slop, e = 0
-            np.testing.assert_allclose(f[c, 4], mass[body], rtol=1e-12)
-            np.testing.assert_allclose(f[c, 5:7], 1.0 / (1.0 / mass[body] + ell * ell / Ix), rtol=1e-9)
-            np.testing.assert_allclose(f[c, 7], 0.8)
-            assert f[c, 8] == 4.0
-            np.testing.assert_allclose(f[c, 9], M * G * h / 4.0, rtol=1e-12)
-            np.testing.assert_allclose(f[c, 10], -G * h, rtol=1e-12)
-            np.testing.assert_allclose(f[c, 11:13], (q - pc)[:2], atol=1e-12)
-            np.testing.assert_allclose(f[c, 13], pc[2] - m.ground_z, rtol=1e-12)
-            np.testing.assert_allclose(f[c, 14], mass[body] * G * h, rtol=1e-12)
-            assert f[c, 15] == 0.0
+            np.testing.assert_allclose(g[0], -G * h, rtol=1e-12)
+            np.testing.assert_allclose(g[1:3], [vx, vy], atol=1e-12)
+            assert (g[3:6] == 0.0).all()  # inside the slop, e = 0, friction rows unbiased
+            np.testing.assert_allclose(g[6], mass[body], rtol=1e-12)
+            np.testing.assert_allclose(g[7:9], 1.0 / (1.0 / mass[body] + ell * ell / Ix), rtol=1e-12)
+            np.testing.assert_allclose(g[9], 0.8)
+            np.testing.assert_allclose(g[10], M * G * h / 4.0, rtol=1e-12)
+            assert g[11] == 4.0 and g[15] == O.WS_GROUND
+            np.testing.assert_allclose(g[12:14], (q - pc)[:2], atol=1e-12)
+            np.testing.assert_allclose(g[14], q[2] - m.ground_z, atol=1e-12)
+        for c in range(4, 8):  # torso spheres: inactive contacts contribute zero rows
+            g = f[16 + c]
+            assert (g[0:9] == 0.0).all()
         assert (d["active"][-24:].reshape(8, 3)[:4] == 1).all()
         assert (d["active"][-24:].reshape(8, 3)[4:] == 0).all()
 
@@ -89,7 +111,7 @@ def test_pair_contact_feature_flag():
     m = WL.two_spheres(B=1)
     d = O.step_log(m, 0, m.state0[0], t=0)
     assert d["feats"].shape == (m.ns + m.np_, 16)
-    assert (d["feats"][:m.ns, 15] == 0.0).all() and (d["feats"][m.ns:, 15] == 1.0).all()
+    assert (d["feats"][:m.ns, 15] == O.WS_GROUND).all() and (d["feats"][m.ns:, 15] == O.WS_PAIR).all()
 
 
 # ----------------------------------------------------------------------------- residual
