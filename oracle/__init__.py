@@ -53,7 +53,7 @@ class Topo(C.Structure):
                 ("gravity", C.c_double * 3), ("dt", C.c_double), ("ground_z", C.c_double),
                 ("beta", C.c_double), ("gamma", C.c_double), ("slop", C.c_double), ("iters", C.c_int32),
                 ("loss_kind", C.c_int32), ("loss_mode", C.c_int32), ("loss_body", C.c_int32),
-                ("exact_mlp", C.c_int32), ("warmstart", C.c_int32), ("ws_W", PD)]
+                ("exact_mlp", C.c_int32), ("warmstart", C.c_int32), ("ws_W", PD), ("ws_alpha", C.c_double)]
 
 WS_IN, WS_H, WS_OUT = 16, 64, 3
 WS_PARAMS = WS_IN * WS_H + WS_H + WS_H * WS_H + WS_H + WS_H * WS_OUT + WS_OUT
@@ -123,6 +123,7 @@ def topo(m, keep, iters=None):
     ws = getattr(m, "ws_W", None)
     t.warmstart = int(bool(getattr(m, "warmstart", 0)) and ws is not None)
     t.ws_W = keep.f64(ws) if t.warmstart else None
+    t.ws_alpha = float(getattr(m, "ws_alpha", 0.7))
     return t
 
 
@@ -250,11 +251,12 @@ def flops(m, i=0, horizon=None, W=None):
     return tuple(out)
 
 
-def step_log(m, i, x, t=0, W=None, iters=None):
+def step_log(m, i, x, t=0, W=None, iters=None, lam_prev=None):
     """One step from state ``x`` with the full step record: dict with ``xn`` [nb, 18], ``active``,
     ``gap``, ``lam`` (final impulses), ``lam0`` (initial impulses), ``margin`` (bfloat16 tie
     margin), ``resid`` (RMS residual of the solve) and ``feats`` [groups, 16] (warm-start
-    features of every group, see ``ws_groups``)."""
+    features of every group, see ``ws_groups``). ``lam_prev`` [n_slots]: the impulses the
+    previous step ended with (default zeros)."""
     keep = _Keep()
     tp = topo(m, keep, iters)
     s = inst(m, i, keep)
@@ -268,7 +270,8 @@ def step_log(m, i, x, t=0, W=None, iters=None):
     feats = np.zeros((max(nc, 1), WS_IN))
     r = lib().orc_step_log(C.byref(tp), C.byref(s), weights(m, keep, W), t, _dp(x), _dp(xn),
                            active.ctypes.data_as(C.POINTER(C.c_int8)), _dp(gap), _dp(lam), _dp(marg), _dp(resid),
-                           _dp(feats), _dp(lam0))
+                           _dp(feats), _dp(lam0),
+                           keep.f64(lam_prev) if lam_prev is not None else None)
     if r != 0:
         raise ValueError("oracle rejected the model")
     return dict(xn=xn.reshape(m.nb, 18), active=active[:ns], gap=gap[:ns], lam=lam[:ns], lam0=lam0[:ns],

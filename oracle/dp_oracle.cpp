@@ -242,8 +242,9 @@ typedef struct {
   int32_t iters;
   int32_t loss_kind, loss_mode, loss_body;
   int32_t exact_mlp;           // 1: skip the bfloat16 rounding (finite-difference checks only)
-  int32_t warmstart;           // 1: contact impulses start from the learned warm start (ws_W)
+  int32_t warmstart;           // 1: the solve starts from the learned warm start (ws_W, ws_alpha)
   const double* ws_W;          // warm-start network parameters [ORC_WS_PARAMS]
+  double ws_alpha;             // weight of the previous step's impulses in the warm start
 } orc_topo;
 
 // Learned warm start: a 16-64-64-3 network per contact (W1, b1, W2, b2, W3, b3; W[out][in]).
@@ -464,7 +465,7 @@ template <class S> static S loss_initial(const orc_topo& T, const Inst<S>& P, co
 template <class S>
 static void step(const orc_topo& T, const std::vector<Slot>& slots, const std::vector<int>& order, const Inst<S>& P,
                  const std::vector<S>& W, int t, const std::vector<S>& x, std::vector<S>& xn, double w_next, S* loss,
-                 StepLog* log) {
+                 StepLog* log, const double* lam_prev = nullptr, double* lam_out = nullptr) {
   const double h = T.dt;
   const int nb = T.nb, nj = T.nj;
   g_exact_mlp = T.exact_mlp != 0;
@@ -732,20 +733,17 @@ static void step(const orc_topo& T, const std::vector<Slot>& slots, const std::v
   // Initial impulses: zero (cold start), or the learned warm start. The warm start works on
   // groups of three rows: the linear rows of a joint, the angular rows of a hinge with its motor
   // row, and the normal and friction rows of a contact. Each group gets 16 features from its
-  // assembled rows, the pre-solve velocities and the robot's mass distribution; the network's
-  // three outputs are projected on the rows' bounds and applied in slot order before the
-  // sweeps. It is a starting guess, not part of the modelled dynamics: reverse mode treats it as
-  // a constant.
+  // assembled rows, the pre-solve velocities, the impulses its rows ended the previous step with
+  // (lambda_prev) and the robot's mass distribution. The start is alpha lambda_prev plus the
+  // network's three outputs, projected on the rows' bounds and applied in slot order before the
+  // sweeps; a zero network is the damped classic warm start. It is a starting guess, not part of
+  // the modelled dynamics: reverse mode treats it as a constant.
   std::vector<S> lam(ns_, S(0.0));
   const std::vector<WsGroup> groups = ws_groups(T, slots);
+  auto lp = [&](int si) { return si >= 0 && lam_prev ? lam_prev[si] : 0.0; };
   if (T.warmstart || (log && log->feats)) {
-    double mtot = 0.0, pc[3] = {0.0, 0.0, 0.0};
-    for (int b = 0; b < nb; ++b) {
-      double m = val(P.mass[b]);
-      mtot += m;
-      for (int k = 0; k < 3; ++k) pc[k] += m * val(p[b][k]);
-    }
-    for (int k = 0; k < 3; ++k) pc[k] /= mtot;
+    double mtot = 0.0;
+    for (int b = 0; b < nb; ++b) mtot += val(P.mass[b]);
     int nact = 0;
     for (int si = 0; si < ns_; ++si)
       if ((slots[si].kind == ORC_GN || slots[si].kind == ORC_PN) && rows[si].active) ++nact;
@@ -772,13 +770,11 @@ static void step(const orc_topo& T, const std::vector<Slot>& slots, const std::v
         phi[k] = on ? val(Jv_of(rows[si])) : 0.0;
         phi[3 + k] = on ? val(rows[si].bias) : 0.0;
         phi[6 + k] = on ? val(rows[si].meff) : 0.0;
+        phi[10 + k] = lp(si);
       }
       phi[9] = G.type == WS_GROUND || G.type == WS_PAIR ? val(rows[G.slot[1]].mu)
                : (G.type == WS_HINGE && G.slot[2] >= 0 ? val(rows[G.slot[2]].hi) : 0.0);
-      phi[10] = mtot * gnorm * h / std::max(1, nact);
-      phi[11] = (double)nact;
-      phi[12] = val(q[0]) - pc[0];
-      phi[13] = val(q[1]) - pc[1];
+      phi[13] = mtot * gnorm * h / std::max(1, nact);
       phi[14] = val(q[2]) - T.ground_z;
       phi[15] = (double)G.type;
       if (log && log->feats)
@@ -790,19 +786,20 @@ static void step(const orc_topo& T, const std::vector<Slot>& slots, const std::v
       ws_forward<double, double>(T.ws_W, phi, y);
       g_exact_mlp = exact_ctrl;
       auto clampd = [](double x, double lo, double hi) { return x < lo ? lo : (x > hi ? hi : x); };
-      double l0[3] = {0.0, 0.0, 0.0};
+      double l0[3] = {0.0, 0.0, 0.0}, z[3];
+      for (int k = 0; k < 3; ++k) z[k] = T.ws_alpha * phi[10 + k] + y[k];  // corrected previous impulses
       if (G.type == WS_GROUND || G.type == WS_PAIR) {
         if (rows[G.slot[0]].active) {
-          l0[0] = y[0] > 0.0 ? y[0] : 0.0;
+          l0[0] = z[0] > 0.0 ? z[0] : 0.0;
           const double hi = val(rows[G.slot[1]].mu) * l0[0];
-          l0[1] = clampd(y[1], -hi, hi);
-          l0[2] = clampd(y[2], -hi, hi);
+          l0[1] = clampd(z[1], -hi, hi);
+          l0[2] = clampd(z[2], -hi, hi);
         }
       } else {
         for (int k = 0; k < 3; ++k) {
           const int si = G.slot[k];
           if (si < 0 || !rows[si].active) continue;
-          l0[k] = slots[si].kind == ORC_MOTOR ? clampd(y[k], val(rows[si].lo), val(rows[si].hi)) : y[k];
+          l0[k] = slots[si].kind == ORC_MOTOR ? clampd(z[k], val(rows[si].lo), val(rows[si].hi)) : z[k];
         }
       }
       for (int k = 0; k < 3; ++k)
@@ -838,6 +835,8 @@ static void step(const orc_topo& T, const std::vector<Slot>& slots, const std::v
   }
   if (log && log->lambda)
     for (int si = 0; si < ns_; ++si) log->lambda[si] = val(lam[si]);
+  if (lam_out)
+    for (int si = 0; si < ns_; ++si) lam_out[si] = val(lam[si]);
   // Residual of the solve: per active row with w = J v + bias + gamma lambda,
   // bilateral |w|; one-sided [0, inf) |min(lambda, w)|; boxed |lambda - clamp(lambda - w, lo, hi)|
   // (motors: +-tau_max h, friction: +-mu lambda_n); RMS over the active rows.
@@ -956,10 +955,11 @@ int orc_schedule(const orc_topo* T, int32_t* kind, int32_t* idx, int32_t* sub, i
 }
 
 // One step from a given state (used for teacher-forced comparisons), with the solve's residual,
-// the warm-start features of every group [orc_ws_groups][16] and the initial impulses [n_slots].
+// the warm-start features of every group [orc_ws_groups][16] and the initial impulses [n_slots];
+// lam_prev [n_slots] (or NULL: zeros) are the impulses the previous step ended with.
 int orc_step_log(const orc_topo* T, const orc_inst* I, const double* W, int32_t t, const double* x, double* xn,
                  int8_t* active, double* gap, double* lambda, double* bf16_margin, double* resid, double* feats,
-                 double* lam0) {
+                 double* lam0, const double* lam_prev) {
   if (check_topo(T)) return -1;
   auto slots = make_slots(*T);
   std::vector<int> col, ord;
@@ -971,7 +971,7 @@ int orc_step_log(const orc_topo* T, const orc_inst* I, const double* W, int32_t 
   std::vector<int8_t> act(slots.size());
   std::vector<double> gp(slots.size());
   StepLog lg{active ? active : act.data(), gap ? gap : gp.data(), lambda, bf16_margin, resid, feats, lam0};
-  step<double>(*T, slots, ord, P, Wv, t, xs, xo, 0.0, nullptr, &lg);
+  step<double>(*T, slots, ord, P, Wv, t, xs, xo, 0.0, nullptr, &lg, lam_prev);
   std::memcpy(xn, xo.data(), sizeof(double) * xo.size());
   return 0;
 }
@@ -1054,9 +1054,20 @@ int orc_rollout(const orc_topo* T, const orc_inst* I, const double* W, int32_t h
                 double* loss, int8_t* active, double* gap, double* bf16_margin) {
   return orc_rollout_log(T, I, W, horizon, states, loss, active, gap, bf16_margin, nullptr);
 }
+static int rollout_impl(const orc_topo* T, const orc_inst* I, const double* W, int32_t horizon, double* states,
+                        double* loss, int8_t* active, double* gap, double* bf16_margin, double* resid,
+                        std::vector<double>* lam_prevs);
 // orc_rollout that also gives the residual of every step's solve [horizon].
 int orc_rollout_log(const orc_topo* T, const orc_inst* I, const double* W, int32_t horizon, double* states,
                     double* loss, int8_t* active, double* gap, double* bf16_margin, double* resid) {
+  return rollout_impl(T, I, W, horizon, states, loss, active, gap, bf16_margin, resid, nullptr);
+}
+}  // extern "C"
+// The rollout; with the warm start each step starts from the impulses the previous one ended with
+// (zero before the first step), and lam_prevs (optional) receives them per step [horizon][n_slots].
+static int rollout_impl(const orc_topo* T, const orc_inst* I, const double* W, int32_t horizon, double* states,
+                        double* loss, int8_t* active, double* gap, double* bf16_margin, double* resid,
+                        std::vector<double>* lam_prevs) {
   if (check_topo(T) || horizon < 0) return -1;
   auto slots = make_slots(*T);
   std::vector<int> col, ord;
@@ -1068,6 +1079,8 @@ int orc_rollout_log(const orc_topo* T, const orc_inst* I, const double* W, int32
   std::vector<double> x(I->state0, I->state0 + 18 * T->nb), xn;
   double L = loss_initial(*T, P, x);
   if (states) std::memcpy(states, x.data(), sizeof(double) * x.size());
+  std::vector<double> lamp(nsl, 0.0), lamn(nsl, 0.0);
+  if (lam_prevs) lam_prevs->assign((size_t)horizon * nsl, 0.0);
   for (int t = 0; t < horizon; ++t) {
     double lt = 0.0;
     std::vector<int8_t> act_tmp;
@@ -1075,8 +1088,10 @@ int orc_rollout_log(const orc_topo* T, const orc_inst* I, const double* W, int32
     if (resid && !(active && gap)) { act_tmp.resize(nsl); gap_tmp.resize(nsl); }
     StepLog lg{active ? active + (size_t)t * nsl : act_tmp.data(), gap ? gap + (size_t)t * nsl : gap_tmp.data(),
                nullptr, bf16_margin ? bf16_margin + t : nullptr, resid ? resid + t : nullptr, nullptr, nullptr};
+    if (lam_prevs) std::copy(lamp.begin(), lamp.end(), lam_prevs->begin() + (size_t)t * nsl);
     step<double>(*T, slots, ord, P, Wv, t, x, xn, weight_of_state(*T, t + 1, horizon), &lt,
-                 ((active && gap) || resid) ? &lg : nullptr);
+                 ((active && gap) || resid) ? &lg : nullptr, T->warmstart ? lamp.data() : nullptr, lamn.data());
+    lamp.swap(lamn);
     L += lt;
     x.swap(xn);
     if (states) std::memcpy(states + (size_t)(t + 1) * 18 * T->nb, x.data(), sizeof(double) * x.size());
@@ -1084,6 +1099,7 @@ int orc_rollout_log(const orc_topo* T, const orc_inst* I, const double* W, int32
   if (loss) *loss = L;
   return 0;
 }
+extern "C" {
 
 // Loss and its gradient with respect to the initial state, every per-instance parameter and
 // the controller weights: back-propagation through time, one step at a time. Each step is
@@ -1097,8 +1113,9 @@ int orc_rollout_grad(const orc_topo* T, const orc_inst* I, const double* W, int3
   make_schedule(slots, col, ord);
   const int nb = T->nb;
   const int np_ = param_count(T->n_layers, T->widths, T->skip);
-  std::vector<double> states((size_t)(horizon + 1) * 18 * nb);
-  if (orc_rollout(T, I, W, horizon, states.data(), loss, nullptr, nullptr, nullptr)) return -1;
+  std::vector<double> states((size_t)(horizon + 1) * 18 * nb), lamps;
+  if (rollout_impl(T, I, W, horizon, states.data(), loss, nullptr, nullptr, nullptr, nullptr, &lamps)) return -1;
+  const size_t nsl = slots.size();
 
   Tape tape;
   Tape* saved = g_tape;
@@ -1135,7 +1152,8 @@ int orc_rollout_grad(const orc_topo* T, const orc_inst* I, const double* W, int3
     std::vector<AD> Wl = lift_leaf(W, np_);
     std::vector<AD> x = lift_leaf(states.data() + (size_t)t * 18 * nb, 18 * nb), xn;
     AD lt;
-    step<AD>(*T, slots, ord, P, Wl, t, x, xn, weight_of_state(*T, t + 1, horizon), &lt, nullptr);
+    step<AD>(*T, slots, ord, P, Wl, t, x, xn, weight_of_state(*T, t + 1, horizon), &lt, nullptr,
+             T->warmstart ? lamps.data() + (size_t)t * nsl : nullptr);
     AD l0 = (t == 0) ? loss_initial(*T, P, x) : AD(0.0);
     tape.adj.assign(tape.pa.size(), 0.0);
     for (int k = 0; k < 18 * nb; ++k)

@@ -10,9 +10,10 @@ What each test pins:
   with the number of sweeps;
 * the warm-start network, against the textbook dense-layer definition in numpy (exact mode)
   and with torch's bfloat16 conversion at the storage points;
-* the application of the warm start: a zero network is the cold start bit for bit, the
-  projection on the bounds, and a network that outputs the converged impulses makes zero sweeps
-  give the converged step;
+* the application of the warm start: with no weight on the previous impulses a zero network is
+  the cold start bit for bit; with a weight it is the damped previous-impulse start projected on
+  every row kind's bounds; starting from converged impulses (previous ones, or a network's
+  output) leaves nothing for the sweeps;
 * the training gradient, by central differences, the closed form of the output-bias gradient
   and its vanishing at a perfect fit;
 * reverse mode with a state-independent warm start, by central differences.
@@ -67,7 +68,6 @@ def test_group_features_closed_form_first_step():
         vx, vy = x0[0, 12], x0[0, 13]
         mass = m.mass[i]
         M = mass.sum()
-        pc = (mass[:, None] * x0[:, :3]).sum(0) / M
         tau_h = m.motor[i, 0, 1] * h
         for j in range(8):  # joints: closed, no relative motion
             lin, hin = f[2 * j], f[2 * j + 1]
@@ -76,10 +76,10 @@ def test_group_features_closed_form_first_step():
             for g, code, bound in ((lin, O.WS_JOINT, 0.0), (hin, O.WS_HINGE, tau_h)):
                 np.testing.assert_allclose(g[0:3], 0.0, atol=1e-12)
                 np.testing.assert_allclose(g[9], bound, rtol=1e-12)
-                np.testing.assert_allclose(g[10], M * G * h / 4.0, rtol=1e-12)
-                assert g[11] == 4.0 and g[15] == code
-                np.testing.assert_allclose(g[12:14], (q - pc)[:2], atol=1e-12)
+                assert (g[10:13] == 0.0).all()  # first step: no previous impulses
+                np.testing.assert_allclose(g[13], M * G * h / 4.0, rtol=1e-12)
                 np.testing.assert_allclose(g[14], q[2] - m.ground_z, atol=1e-12)
+                assert g[15] == code
             np.testing.assert_allclose(lin[3:6], 0.0, atol=1e-6)  # closed joint (to the inputs' float32 grid)
             np.testing.assert_allclose(hin[3:5], 0.0, atol=1e-6)  # aligned hinge axes
             assert abs(hin[5]) <= m.motor[i, j, 2] + 1e-12  # servo rate within +-vmax
@@ -96,13 +96,18 @@ def test_group_features_closed_form_first_step():
             np.testing.assert_allclose(g[6], mass[body], rtol=1e-12)
             np.testing.assert_allclose(g[7:9], 1.0 / (1.0 / mass[body] + ell * ell / Ix), rtol=1e-12)
             np.testing.assert_allclose(g[9], 0.8)
-            np.testing.assert_allclose(g[10], M * G * h / 4.0, rtol=1e-12)
-            assert g[11] == 4.0 and g[15] == O.WS_GROUND
-            np.testing.assert_allclose(g[12:14], (q - pc)[:2], atol=1e-12)
+            assert (g[10:13] == 0.0).all()
+            np.testing.assert_allclose(g[13], M * G * h / 4.0, rtol=1e-12)
             np.testing.assert_allclose(g[14], q[2] - m.ground_z, atol=1e-12)
+            assert g[15] == O.WS_GROUND
         for c in range(4, 8):  # torso spheres: inactive contacts contribute zero rows
             g = f[16 + c]
             assert (g[0:9] == 0.0).all()
+        # the previous step's impulses enter as features 10-12 of their group
+        lp = np.arange(1, len(d["lam"]) + 1) / 100.0
+        f2 = O.step_log(m, i, m.state0[i], t=0, lam_prev=lp)["feats"]
+        for g, (typ, sl) in enumerate(groups):
+            np.testing.assert_array_equal(f2[g, 10:13], [lp[k] if k >= 0 else 0.0 for k in sl])
         assert (d["active"][-24:].reshape(8, 3)[:4] == 1).all()
         assert (d["active"][-24:].reshape(8, 3)[4:] == 0).all()
 
@@ -185,9 +190,50 @@ def test_ws_network_bfloat16_storage_points():
 def test_zero_network_is_the_cold_start():
     m = WL.quadruped(B=2, horizon=30)
     st, L, _ = O.rollout_resid(m, 1, 30)
-    m.warmstart, m.ws_W = 1, np.zeros(O.WS_PARAMS)
+    m.warmstart, m.ws_W, m.ws_alpha = 1, np.zeros(O.WS_PARAMS), 0.0
     st2, L2, _ = O.rollout_resid(m, 1, 30)
     assert np.array_equal(st, st2) and L == L2
+
+
+def test_zero_network_is_the_damped_previous_impulse_start():
+    """With a zero network the start is alpha lambda_prev projected on the bounds: joint rows
+    unchanged, normals clipped at 0, friction boxed by mu times the normal, motors by tau_max h."""
+    m = WL.quadruped(B=1, horizon=40)
+    st, _, _ = O.rollout_resid(m, 0, 40)
+    sch = O.schedule(m)
+    kind = sch["kind"]
+    m.warmstart, m.ws_W, m.ws_alpha = 1, np.zeros(O.WS_PARAMS), 0.7
+    rng = np.random.default_rng(3)
+    lp = rng.normal(0, 0.2, len(kind))
+    d = O.step_log(m, 0, st[20], t=20, lam_prev=lp)
+    l0, act = d["lam0"], d["active"]
+    tau_h = m.motor[0, 0, 1] * m.dt
+    for s, k in enumerate(kind):
+        z = 0.7 * lp[s]
+        if k in (0, 1):
+            assert l0[s] == z
+        elif k == 3:
+            assert l0[s] == min(max(z, -tau_h), tau_h)
+        elif k == 2:
+            assert l0[s] == 0.0  # limits start cold
+        elif k == 4:
+            assert l0[s] == (max(z, 0.0) if act[s] else 0.0)
+        elif k == 5:
+            n = s - 1 if kind[s - 1] == 4 else s - 2
+            hi = float(m.sph_mu[0, sch["idx"][s]]) * l0[n]
+            assert l0[s] == (min(max(z, -hi), hi) if act[s] else 0.0)
+
+
+def test_converged_previous_impulses_need_no_sweeps():
+    """Starting from the converged impulses of the same step (alpha = 1, zero network) leaves
+    nothing for the sweeps: zero sweeps give the converged residual and state."""
+    m = WL.quadruped(B=1, horizon=40)
+    st, _, _ = O.rollout_resid(m, 0, 40)
+    ref = O.step_log(m, 0, st[25], t=25, iters=3000)
+    m.warmstart, m.ws_W, m.ws_alpha = 1, np.zeros(O.WS_PARAMS), 1.0
+    d = O.step_log(m, 0, st[25], t=25, iters=0, lam_prev=ref["lam"])
+    assert d["resid"] <= ref["resid"] + 1e-12
+    np.testing.assert_allclose(d["xn"], ref["xn"], rtol=0, atol=1e-12)
 
 
 def test_warm_start_projection_on_the_bounds():
@@ -262,7 +308,7 @@ def test_gradient_with_state_independent_warm_start_central_differences():
     stop-gradient reverse mode is the exact derivative: check it by central differences."""
     m = WL.quadruped(B=1, horizon=8)
     m.exact_mlp = 1
-    m.warmstart, m.ws_W = 1, const_ws([0.25, 0.01, -0.02])
+    m.warmstart, m.ws_W, m.ws_alpha = 1, const_ws([0.25, 0.01, -0.02]), 0.0
     L, g = O.rollout_grad(m, 0)
     eps = 1e-6
     for (b, f) in ((0, 12), (0, 2), (3, 16), (2, 0)):
