@@ -733,17 +733,23 @@ static void step(const orc_topo& T, const std::vector<Slot>& slots, const std::v
   // Initial impulses: zero (cold start), or the learned warm start. The warm start works on
   // groups of three rows: the linear rows of a joint, the angular rows of a hinge with its motor
   // row, and the normal and friction rows of a contact. Each group gets 16 features from its
-  // assembled rows, the pre-solve velocities, the impulses its rows ended the previous step with
-  // (lambda_prev) and the robot's mass distribution. The start is alpha lambda_prev plus the
+  // assembled rows, the pre-solve velocities and the robot's mass distribution. The start is
+  // alpha times the impulses the rows ended the previous step with (lambda_prev) plus the
   // network's three outputs, projected on the rows' bounds and applied in slot order before the
-  // sweeps; a zero network is the damped classic warm start. It is a starting guess, not part of
-  // the modelled dynamics: reverse mode treats it as a constant.
+  // sweeps; a zero network is the damped classic warm start. The network does not see
+  // lambda_prev, so it cannot feed the previous impulses back with a gain. The start is a
+  // guess, not part of the modelled dynamics: reverse mode treats it as a constant.
   std::vector<S> lam(ns_, S(0.0));
   const std::vector<WsGroup> groups = ws_groups(T, slots);
   auto lp = [&](int si) { return si >= 0 && lam_prev ? lam_prev[si] : 0.0; };
   if (T.warmstart || (log && log->feats)) {
-    double mtot = 0.0;
-    for (int b = 0; b < nb; ++b) mtot += val(P.mass[b]);
+    double mtot = 0.0, pc[3] = {0.0, 0.0, 0.0};
+    for (int b = 0; b < nb; ++b) {
+      const double m = val(P.mass[b]);
+      mtot += m;
+      for (int k = 0; k < 3; ++k) pc[k] += m * val(p[b][k]);
+    }
+    for (int k = 0; k < 3; ++k) pc[k] /= mtot;
     int nact = 0;
     for (int si = 0; si < ns_; ++si)
       if ((slots[si].kind == ORC_GN || slots[si].kind == ORC_PN) && rows[si].active) ++nact;
@@ -770,10 +776,12 @@ static void step(const orc_topo& T, const std::vector<Slot>& slots, const std::v
         phi[k] = on ? val(Jv_of(rows[si])) : 0.0;
         phi[3 + k] = on ? val(rows[si].bias) : 0.0;
         phi[6 + k] = on ? val(rows[si].meff) : 0.0;
-        phi[10 + k] = lp(si);
       }
       phi[9] = G.type == WS_GROUND || G.type == WS_PAIR ? val(rows[G.slot[1]].mu)
                : (G.type == WS_HINGE && G.slot[2] >= 0 ? val(rows[G.slot[2]].hi) : 0.0);
+      phi[10] = val(q[0]) - pc[0];
+      phi[11] = val(q[1]) - pc[1];
+      phi[12] = (double)nact;
       phi[13] = mtot * gnorm * h / std::max(1, nact);
       phi[14] = val(q[2]) - T.ground_z;
       phi[15] = (double)G.type;
@@ -787,7 +795,7 @@ static void step(const orc_topo& T, const std::vector<Slot>& slots, const std::v
       g_exact_mlp = exact_ctrl;
       auto clampd = [](double x, double lo, double hi) { return x < lo ? lo : (x > hi ? hi : x); };
       double l0[3] = {0.0, 0.0, 0.0}, z[3];
-      for (int k = 0; k < 3; ++k) z[k] = T.ws_alpha * phi[10 + k] + y[k];  // corrected previous impulses
+      for (int k = 0; k < 3; ++k) z[k] = T.ws_alpha * lp(G.slot[k]) + y[k];  // corrected previous impulses
       if (G.type == WS_GROUND || G.type == WS_PAIR) {
         if (rows[G.slot[0]].active) {
           l0[0] = z[0] > 0.0 ? z[0] : 0.0;

@@ -68,6 +68,7 @@ def test_group_features_closed_form_first_step():
         vx, vy = x0[0, 12], x0[0, 13]
         mass = m.mass[i]
         M = mass.sum()
+        pc = (mass[:, None] * x0[:, :3]).sum(0) / M
         tau_h = m.motor[i, 0, 1] * h
         for j in range(8):  # joints: closed, no relative motion
             lin, hin = f[2 * j], f[2 * j + 1]
@@ -76,7 +77,8 @@ def test_group_features_closed_form_first_step():
             for g, code, bound in ((lin, O.WS_JOINT, 0.0), (hin, O.WS_HINGE, tau_h)):
                 np.testing.assert_allclose(g[0:3], 0.0, atol=1e-12)
                 np.testing.assert_allclose(g[9], bound, rtol=1e-12)
-                assert (g[10:13] == 0.0).all()  # first step: no previous impulses
+                np.testing.assert_allclose(g[10:12], (q - pc)[:2], atol=1e-12)
+                assert g[12] == 4.0
                 np.testing.assert_allclose(g[13], M * G * h / 4.0, rtol=1e-12)
                 np.testing.assert_allclose(g[14], q[2] - m.ground_z, atol=1e-12)
                 assert g[15] == code
@@ -96,18 +98,17 @@ def test_group_features_closed_form_first_step():
             np.testing.assert_allclose(g[6], mass[body], rtol=1e-12)
             np.testing.assert_allclose(g[7:9], 1.0 / (1.0 / mass[body] + ell * ell / Ix), rtol=1e-12)
             np.testing.assert_allclose(g[9], 0.8)
-            assert (g[10:13] == 0.0).all()
+            np.testing.assert_allclose(g[10:12], (q - pc)[:2], atol=1e-12)
+            assert g[12] == 4.0
             np.testing.assert_allclose(g[13], M * G * h / 4.0, rtol=1e-12)
             np.testing.assert_allclose(g[14], q[2] - m.ground_z, atol=1e-12)
             assert g[15] == O.WS_GROUND
         for c in range(4, 8):  # torso spheres: inactive contacts contribute zero rows
             g = f[16 + c]
             assert (g[0:9] == 0.0).all()
-        # the previous step's impulses enter as features 10-12 of their group
+        # the previous step's impulses do not enter the features
         lp = np.arange(1, len(d["lam"]) + 1) / 100.0
-        f2 = O.step_log(m, i, m.state0[i], t=0, lam_prev=lp)["feats"]
-        for g, (typ, sl) in enumerate(groups):
-            np.testing.assert_array_equal(f2[g, 10:13], [lp[k] if k >= 0 else 0.0 for k in sl])
+        np.testing.assert_array_equal(O.step_log(m, i, m.state0[i], t=0, lam_prev=lp)["feats"], f)
         assert (d["active"][-24:].reshape(8, 3)[:4] == 1).all()
         assert (d["active"][-24:].reshape(8, 3)[4:] == 0).all()
 
