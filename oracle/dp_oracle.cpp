@@ -734,11 +734,13 @@ static void step(const orc_topo& T, const std::vector<Slot>& slots, const std::v
   // groups of three rows: the linear rows of a joint, the angular rows of a hinge with its motor
   // row, and the normal and friction rows of a contact. Each group gets 16 features from its
   // assembled rows, the pre-solve velocities and the robot's mass distribution. The start is
-  // alpha times the impulses the rows ended the previous step with (lambda_prev) plus the
-  // network's three outputs, projected on the rows' bounds and applied in slot order before the
-  // sweeps; a zero network is the damped classic warm start. The network does not see
-  // lambda_prev, so it cannot feed the previous impulses back with a gain. The start is a
-  // guess, not part of the modelled dynamics: reverse mode treats it as a constant.
+  // alpha times the impulses the rows ended the previous step with (lambda_prev) plus each row's
+  // effective mass times the network's output for it (a velocity-scale correction, so that an
+  // error moves the bodies by about the same speed on stiff and soft rows), projected on the
+  // rows' bounds and applied in slot order before the sweeps; a zero network is the damped
+  // classic warm start. The network does not see lambda_prev, so it cannot feed the previous
+  // impulses back with a gain. The start is a guess, not part of the modelled dynamics: reverse
+  // mode treats it as a constant.
   std::vector<S> lam(ns_, S(0.0));
   const std::vector<WsGroup> groups = ws_groups(T, slots);
   auto lp = [&](int si) { return si >= 0 && lam_prev ? lam_prev[si] : 0.0; };
@@ -795,7 +797,7 @@ static void step(const orc_topo& T, const std::vector<Slot>& slots, const std::v
       g_exact_mlp = exact_ctrl;
       auto clampd = [](double x, double lo, double hi) { return x < lo ? lo : (x > hi ? hi : x); };
       double l0[3] = {0.0, 0.0, 0.0}, z[3];
-      for (int k = 0; k < 3; ++k) z[k] = T.ws_alpha * lp(G.slot[k]) + y[k];  // corrected previous impulses
+      for (int k = 0; k < 3; ++k) z[k] = T.ws_alpha * lp(G.slot[k]) + phi[6 + k] * y[k];  // corrected previous impulses
       if (G.type == WS_GROUND || G.type == WS_PAIR) {
         if (rows[G.slot[0]].active) {
           l0[0] = z[0] > 0.0 ? z[0] : 0.0;

@@ -12,8 +12,9 @@ What each test pins:
   and with torch's bfloat16 conversion at the storage points;
 * the application of the warm start: with no weight on the previous impulses a zero network is
   the cold start bit for bit; with a weight it is the damped previous-impulse start projected on
-  every row kind's bounds; starting from converged impulses (previous ones, or a network's
-  output) leaves nothing for the sweeps;
+  every row kind's bounds; the network's output is scaled by the rows' effective masses;
+  starting from converged impulses (previous ones, or a network's output) leaves nothing for the
+  sweeps;
 * the training gradient, by central differences, the closed form of the output-bias gradient
   and its vanishing at a perfect fit;
 * reverse mode with a state-independent warm start, by central differences.
@@ -238,28 +239,35 @@ def test_converged_previous_impulses_need_no_sweeps():
 
 
 def test_warm_start_projection_on_the_bounds():
+    """The network's output is a velocity-scale correction: the start is m_eff y per row, then
+    projected (normal >= 0, |friction| <= mu normal)."""
     m = sliding_ball()
     mu = float(m.sph_mu[0, 0])
-    for b3, expect in (([-1.0, 5.0, -5.0], [0.0, 0.0, 0.0]), ([2.0, 5.0, -0.5], [2.0, 2.0 * mu, -0.5]),
-                       ([0.5, -5.0, 5.0], [0.5, -0.5 * mu, 0.5 * mu])):
-        m.warmstart, m.ws_W = 1, const_ws(b3)
+    me = O.step_log(m, 0, m.state0[0], t=0)["feats"][0, 6:9]
+    for y, lam in (([-1.0, 5.0, -5.0], [0.0, 0.0, 0.0]), ([2.0, 5.0, -0.5], None), ([0.5, -50.0, 50.0], None)):
+        m.warmstart, m.ws_W, m.ws_alpha = 1, const_ws(y), 0.7
         d = O.step_log(m, 0, m.state0[0], t=0)
-        np.testing.assert_allclose(d["lam0"], expect, rtol=1e-15)
+        z = me * np.array(y)
+        n = max(z[0], 0.0)
+        expect = [n, min(max(z[1], -mu * n), mu * n), min(max(z[2], -mu * n), mu * n)]
+        np.testing.assert_allclose(d["lam0"], expect if lam is None else lam, rtol=1e-15)
 
 
 def test_converged_warm_start_needs_no_sweeps():
     """A network that outputs the converged impulses of the sliding sphere (m g h normal,
-    -mu m g h along the slip) gives, with zero sweeps, the converged step."""
+    -mu m g h along each slip component), divided by the rows' effective masses, gives with zero
+    sweeps the converged step."""
     m = sliding_ball()
     ref = O.step_log(m, 0, m.state0[0], t=0, iters=20)
     mass, mu, h = float(m.mass[0, 0]), float(m.sph_mu[0, 0]), m.dt
     v = m.state0[0, 0, 12:14]
     lam = mass * G * h
-    # friction rows t1 = x, t2 = y; the converged friction is the box-pyramid corner clipped
-    # per row: each row saturates at -mu lam sign(v) (both slip components are nonzero)
+    # friction rows t1 = x, t2 = y; each row saturates at -mu lam sign(v) (both slip components
+    # are nonzero)
     np.testing.assert_allclose(ref["lam"][1:], -mu * lam * np.sign(v), rtol=1e-9)
     np.testing.assert_allclose(ref["lam"][0], lam, rtol=1e-9)
-    m.warmstart, m.ws_W = 1, const_ws(ref["lam"])
+    me = ref["feats"][0, 6:9]
+    m.warmstart, m.ws_W, m.ws_alpha = 1, const_ws(ref["lam"] / me), 0.7
     ws = O.step_log(m, 0, m.state0[0], t=0, iters=0)
     np.testing.assert_allclose(ws["xn"], ref["xn"], rtol=0, atol=1e-12)
     assert ws["resid"] < 1e-12
