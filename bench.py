@@ -2,9 +2,15 @@
 """Throughput of batched differentiable rigid-body rollouts (arXiv 1611.01652) on GB300.
 
 One step = one forward rollout plus its full reverse-mode gradient (dp_rollout + dp_backward)
-of the quadruped batch: B = 4096 instances, T = 1000 steps of 10 ms, 20 solver sweeps, dense
-controller 24->128->128->8 (bfloat16 weights, fp32 accumulation), loss = negative forward
-displacement, gradient w.r.t. every controller weight. Metric: instance-steps/s (B*T per step).
+of the quadruped batch: B = 4096 instances, T = 1000 steps of 10 ms, dense controller
+24->128->128->8 (bfloat16 weights, fp32 accumulation), loss = negative forward displacement,
+gradient w.r.t. every controller weight. Metric: instance-steps/s (B*T per step).
+
+Two arms: the plain cold-start solver at 20 sweeps, and the warm start accepted by the gate
+(trained network or its zero-network special case, the damped previous-impulse start) at the
+fewest sweeps that reach the plain solver's residual. The warm start is prepared (harvest,
+training, gate) before any timing. The headline value is the accepted warm start's, else the
+plain solver's; both are in the line.
 
 Prints one JSON line. `--impl reference` times the FP64 CPU oracle on the host cores instead.
 """
@@ -37,6 +43,10 @@ def parse():
     p.add_argument("--horizon", type=int, default=1000)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-warmstart", action="store_true", help="time the plain solver only")
+    p.add_argument("--iters", type=int, default=20, help="sweeps of the plain solver")
+    p.add_argument("--alpha", type=float, default=0.7, help="weight of the previous impulses in the warm start")
+    p.add_argument("--ws-train-steps", type=int, default=800)
     return p.parse_args()
 
 
@@ -147,47 +157,57 @@ class Clocks:
 
 
 # ------------------------------------------------------------------------------ GPU arm
-def main():
-    args = parse()
-    rank = int(os.environ.get("RANK", "0"))
-    world_size = int(os.environ.get("WORLD_SIZE", "1"))
-    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
-        run_reference(args, rank)
-        return
-    import numpy as np
+def prepare_warmstart(args):
+    """Untimed: harvest training rows (B=512, 200 steps, 60 sweeps, damped previous-impulse
+    start, perturbed gait), train the warm-start network on the GPU, and run the acceptance gate on
+    held-out robots (B=128, 200 steps) with the trained network and the zero network (damped
+    previous-impulse start) as candidates. Returns (gate report, {name: parameters})."""
     import torch
 
+    from paper_1611_01652_gb300 import warmstart as WS
     from paper_1611_01652_gb300 import workloads as WL
-    from paper_1611_01652_gb300.binding import World
+    from paper_1611_01652_gb300.binding import WS_PARAMS, World
 
-    torch.cuda.set_device(local_rank)
-    dist = None
-    if world_size > 1:
-        import torch.distributed as dist
+    zero = torch.zeros(WS_PARAMS, device="cuda")
+    t0 = time.perf_counter()
+    mh = WL.quadruped(B=512, horizon=200, seed=2002)
+    wh = World(mh, horizon=200, iters=60, warmstart=True)
+    wh.set_warmstart(zero, args.alpha)
+    rows = WS.harvest(wh, torch.tensor(mh.W, device="cuda"), 512 * 200 * 24, noise_sigma=0.1, seed=5)
+    del wh
+    n = rows.shape[0]
+    g = torch.Generator(device="cuda")
+    g.manual_seed(7)
+    perm = torch.randperm(n, device="cuda", generator=g)
+    tr, va = rows[perm[: int(0.9 * n)]], rows[perm[int(0.9 * n):]]
+    mse0 = WS.evaluate(zero, va)
+    net, hist = WS.train(tr, steps=args.ws_train_steps, batch=32768, lr=3e-3, seed=0, val_rows=va,
+                         log_every=args.ws_train_steps)
+    nets = {"learned": net, "damped": zero}
+    mg = WL.quadruped(B=128, horizon=200, seed=3003)
+    rep = WS.accept(mg, [("learned", net, args.alpha), ("damped", zero, args.alpha)], plain_iters=args.iters,
+                    sweep_grid=(5, 7, 10, 14), horizon=200)
+    rep["harvest_rows"] = n
+    rep["val_mse_zero_network"] = mse0
+    rep["val_mse_trained"] = hist[-1][2]
+    rep["prepare_s"] = time.perf_counter() - t0
+    return rep, nets
 
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    B, T = args.batch, args.horizon
-    m = WL.quadruped(B=B, horizon=T, seed=1002 + 17 * rank)
-    stream = torch.cuda.current_stream()
-    world = World(m, stream=stream)
-    W = torch.tensor(m.W, device="cuda")
-    loss = torch.empty(B, device="cuda")
-    dloss = torch.ones(B, device="cuda")
-    dW = torch.empty(world.n_params, device="cuda")
 
-    def step():
-        world.rollout(W, loss)
-        world.backward(dloss, dW)
+def time_arm(world, W, loss, dloss, dW, args, stream, dist):
+    """W warm-up then K timed forward+adjoint steps; (total ms, mean forward ms, mean backward ms,
+    clocks) with CUDA events on the launching stream, bracketed by barrier + synchronize."""
+    import torch
 
     for _ in range(args.warmup):
-        step()
+        world.rollout(W, loss)
+        world.backward(dloss, dW)
     world.sync()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks = Clocks(local_rank)
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     t0 = torch.cuda.Event(enable_timing=True)
@@ -213,8 +233,74 @@ def main():
         tt = torch.tensor([total_ms, fwd_ms, bwd_ms], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         total_ms, fwd_ms, bwd_ms = tt.tolist()
-    ms_per_step = total_ms / args.steps
-    value = B * T * world_size / (ms_per_step / 1e3)
+    return total_ms, fwd_ms, bwd_ms, ck
+
+
+def mean_residual(world, W, B):
+    """Mean per-step solve residual of one untimed rollout of the world."""
+    import torch
+
+    world.set_residual(True)
+    loss = torch.zeros(B, device="cuda")
+    world.rollout(W, loss)
+    r = torch.zeros(B, device="cuda")
+    world.get_residual(r)
+    world.sync()
+    world.set_residual(False)
+    return float(r.mean().item())
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world_size = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import torch
+
+    from paper_1611_01652_gb300 import workloads as WL
+    from paper_1611_01652_gb300.binding import World
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world_size > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    B, T = args.batch, args.horizon
+    rep, nets = (None, {}) if args.no_warmstart else prepare_warmstart(args)
+    m = WL.quadruped(B=B, horizon=T, seed=1002 + 17 * rank)
+    stream = torch.cuda.current_stream()
+    W = torch.tensor(m.W, device="cuda")
+    loss = torch.empty(B, device="cuda")
+    dloss = torch.ones(B, device="cuda")
+
+    # plain cold-start solver at full sweeps (the fallback and judge)
+    world = World(m, stream=stream, iters=args.iters)
+    dW = torch.empty(world.n_params, device="cuda")
+    p_ms, p_fwd, p_bwd, p_ck = time_arm(world, W, loss, dloss, dW, args, stream, dist)
+    plain = {"iters": args.iters, "value": B * T * world_size / (p_ms / args.steps / 1e3),
+             "ms_per_step": p_ms / args.steps, "fwd_ms": p_fwd, "bwd_ms": p_bwd,
+             "resid": mean_residual(world, W, B), "ckpt_every": world.ckpt_every}
+    head = dict(plain, name="plain", clocks=p_ck, world=world)
+    acc = rep["accepted"] if rep else None
+    ws = None
+    if acc:
+        name, n_ws, alpha = acc
+        del world, head["world"]
+        torch.cuda.empty_cache()
+        world = World(m, stream=stream, iters=n_ws, warmstart=True)
+        world.set_warmstart(nets[name], alpha)
+        w_ms, w_fwd, w_bwd, w_ck = time_arm(world, W, loss, dloss, dW, args, stream, dist)
+        ws = {"accepted": name, "iters": n_ws, "alpha": alpha, "value": B * T * world_size / (w_ms / args.steps / 1e3),
+              "ms_per_step": w_ms / args.steps, "fwd_ms": w_fwd, "bwd_ms": w_bwd, "resid": mean_residual(world, W, B),
+              "ckpt_every": world.ckpt_every}
+        head = dict(ws, name="warm start (%s, %d sweeps)" % (name, n_ws), clocks=w_ck, world=world)
+    world = head["world"]
+    ms_per_step = head["ms_per_step"]
+    value = head["value"]
 
     # end to end through the C ABI with host buffers (pinned): W and dloss in, loss and dW out
     e2e = None
@@ -246,33 +332,45 @@ def main():
         if dist:
             dist.destroy_process_group()
         return
-    fl = json.load(open(FLOPS))["quadruped_b4096_t1000"]
+    flops = json.load(open(FLOPS))
+    it = head["iters"]
+    fl = flops["quadruped_b4096_t1000" if it == 20 else "quadruped_b4096_t1000_iters%d" % it]
     peak = SM_COUNT * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12  # TFLOP/s, FP32 FMA at max SM clock
-    achieved = fl["reverse"] * B * T / (bwd_ms / 1e3) / 1e12
+    achieved = fl["reverse"] * B * T / (head["bwd_ms"] / 1e3) / 1e12
     roofline = {"bound": "alu", "kernel": "k_backward", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
-                "basis": "reverse-mode algorithmic FP ops per instance-step (oracle counter) x B x T / dp_backward time; "
-                         "peak = 152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived; no measured FP32 peak)",
+                "basis": "reverse-mode algorithmic FP ops per instance-step at %d sweeps (oracle counter) x B x T / "
+                         "dp_backward time; peak = 152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived from unit counts "
+                         "and the maximum SM clock; no measured FP32 peak)" % it,
                 "step_frac": (fl["forward"] + fl["reverse"]) * B * T / (ms_per_step / 1e3) / 1e12 / peak}
     cpu = None
     if not args.no_cpu_baseline and world_size == 1:
         cores = min(host_cores(), 16)
         v, dt, units = oracle_sample(cores, 2, 100)
         cpu = {"value": v, "unit": "inst-steps/s", "cores": cores, "kind": "oracle",
-               "sample": "%d spawned processes x 2 quadruped instances x 100 steps, forward+adjoint, FP64 oracle "
-                         "(%.1f s wall)" % (cores, dt)}
+               "sample": "%d spawned processes x 2 quadruped instances x 100 steps, forward+adjoint, FP64 oracle, "
+                         "cold start at 20 sweeps (%.1f s wall)" % (cores, dt)}
     n_dense = len(m.widths) - 1 + (1 if m.skip else 0)
-    launches_per_step = 2 + 2 + 4 * n_dense  # prep+forward; pad+backward; per dense layer: gemm, sum, rowsum, sum
+    # per step: two weight preparations + forward; pad + backward; per dense layer gemm, sum, rowsum, sum
+    launches_per_step = 3 + 2 + 4 * n_dense
+    gate = None
+    if rep:
+        gate = {k: rep[k] for k in ("plain_iters", "ref_iters", "plain_resid", "plain_state_err", "plain_grad_err",
+                                    "harvest_rows", "val_mse_zero_network", "val_mse_trained", "prepare_s")}
+        gate["candidates"] = rep["candidates"]
+        gate["accepted"] = rep["accepted"]
     out = {
         "metric": METRIC, "value": value, "unit": "inst-steps/s", "n_gpus": world_size, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "quadruped B=%d T=%d iters=20, MLP 24-128-128-8 (bf16 weights, fp32 acc), "
-                               "forward+adjoint, gradient w.r.t. all controller weights" % (B, T),
-                   "batch": B, "horizon": T, "iters": m.iters, "ckpt_every": world.ckpt_every,
-                   "l2": "working set (checkpoints + controller activations) >> 129 MB L2; no flush needed"},
-        "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": ck,
-        "gpu_launches": launches_per_step * args.steps, "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
+        "config": {"workload": "quadruped B=%d T=%d, MLP 24-128-128-8 (bf16 weights, fp32 acc), forward+adjoint, "
+                               "gradient w.r.t. all controller weights; %s" % (B, T, head["name"]),
+                   "batch": B, "horizon": T, "iters": head["iters"], "ckpt_every": head["ckpt_every"],
+                   "l2": "working set (solver tape + controller activations) >> 129 MB L2; no flush needed"},
+        "plain": plain, "warmstart": ws, "gate": gate,
+        "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": head["clocks"],
+        "plain_clocks": p_ck if ws else None,
+        "gpu_launches": launches_per_step * args.steps, "fwd_ms": head["fwd_ms"], "bwd_ms": head["bwd_ms"],
         "loss_mean": float(loss.mean().item()), "finite": bool(torch.isfinite(dW).all().item()),
     }
     print(json.dumps(out))

@@ -115,6 +115,7 @@ typedef struct {
   int32_t loss_kind, loss_mode, loss_body;
   int32_t ctrl_fp32;              /* 0: bfloat16 storage points (default); 1: the controller keeps its
                                      input, weights and hidden activations in fp32 (no rounding) */
+  int32_t warmstart;              /* 1: reserve room for the learned warm start (dp_set_warmstart) */
 } dp_batch_desc;
 
 typedef struct dp_world dp_world; /* opaque; owned by the library */
@@ -212,6 +213,76 @@ const char* dp_last_error(void);
 
 /* Checkpoint interval K chosen at create (states stored every K steps). */
 int32_t dp_ckpt_every(const dp_world* w);
+
+/*
+ * Learned warm start of the solver (not in the paper; its solver starts from zero impulses).
+ *
+ * The rows are taken in groups of three: the linear rows of each joint (x, y, z), the angular
+ * rows of each hinge with its motor row, the normal, t1, t2 rows of each contact (groups in slot
+ * order of their first row). Each group is described by 16 features taken after row assembly,
+ * before the first sweep (rows of inactive slots give zeros):
+ *   0-2   J v of the three rows (pre-solve velocities)   3-5  their biases
+ *   6-8   their effective masses
+ *   9     contact: friction coefficient; hinge: the motor's bound tau_max h; joint: 0
+ *   10-11 horizontal offset of the group's point from the centre of mass
+ *   12    number of active contacts of the instance
+ *   13    weight share M |g| h / max(1, active contacts)
+ *   14    height above the ground of the group's point (contact point, or the joint's anchor on
+ *         its child body)
+ *   15    group type: 0 ground contact, 1 sphere-pair contact, 2 joint, 3 hinge.
+ * A 16-64-64-3 network y (ReLU hidden layers, linear output; bfloat16 inputs, weights and
+ * hidden activations, fp32 accumulation; flat fp32 parameters W1[64][16], b1[64], W2[64][64],
+ * b2[64], W3[3][64], b3[3], DP_WS_PARAMS floats) gives a velocity-scale correction y per row,
+ * and the start is alpha lambda_prev + m_eff y (m_eff: the row's effective mass), where
+ * lambda_prev are the impulses the rows ended the previous step with (zero before the first step
+ * of a rollout and after dp_set_state; the network does not see them), projected
+ * on the rows' bounds (normal >= 0, |friction| <= mu normal, |motor| <= tau_max h; inactive rows
+ * and limit rows start at zero) and applied in slot order before the sweeps. A zero network is
+ * the damped warm start from the previous step. Reverse mode treats the start as a constant.
+ */
+#define DP_WS_PARAMS 5443
+#define DP_WS_ROW 19 /* a harvested row: 16 features, then the network's ideal output y */
+
+/* Enable the warm start with the network W (host or device, DP_WS_PARAMS floats, copied) and
+   the weight alpha in [0, 1] of the previous impulses, or disable it (W = NULL; alpha is kept
+   for dp_harvest). The world must have been created with desc.warmstart = 1 (DP_EINVAL
+   otherwise). Takes effect from the next dp_step / dp_rollout; a recorded rollout is dropped. */
+dp_status dp_set_warmstart(dp_world* w, const float* W, float alpha);
+
+/* The impulses every slot ended the last step with, [B][n_slots] (host or device): read them,
+   or set them as the lambda_prev of the next dp_step. */
+dp_status dp_set_impulses(dp_world* w, const float* lam);
+dp_status dp_get_impulses(dp_world* w, float* lam);
+
+/* Rollout from the initial state with the world's solver (cold, or warm-started) that harvests
+   one training row per active group per step: rows (device, [max_rows][DP_WS_ROW]) receives the
+   16 features and the network's ideal output, (impulses after the solve - alpha previous
+   impulses) / m_eff per row (0 for inactive rows); u_noise (device, [horizon][B][n_motors], or NULL) is added to the controller
+   output at every step. *n_rows (host) = rows written (<= max_rows). Synchronises the stream.
+   Leaves no rollout for dp_backward. */
+dp_status dp_harvest(dp_world* w, const float* W, const float* u_noise, float* rows, int64_t max_rows,
+                     int64_t* n_rows);
+
+/* Residual of the solve: with on = 1 every later dp_rollout (which restarts the count) and
+   dp_step accumulates, per instance, the RMS over the active rows of the complementarity
+   residual after the sweeps (w = J v + bias + gamma lambda: |w| for joint rows, |min(lambda, w)|
+   for limits and normals, |lambda - clamp(lambda - w, lo, hi)| for motors and friction).
+   dp_get_residual writes the mean over the accumulated steps (device or host, [B]). */
+dp_status dp_set_residual(dp_world* w, int32_t on);
+dp_status dp_get_residual(dp_world* w, float* resid);
+
+/* Training of the warm-start network on harvested rows (all pointers device memory, ordered on
+   `stream`, a cudaStream_t or NULL). dp_ws_loss_grad: loss = (1/n) sum_rows sum_k (y_k -
+   lambda_k)^2 and dW = dloss/dW ([DP_WS_PARAMS]; straight-through bfloat16 roundings), using
+   `work` of dp_ws_workspace_floats(n) floats. dp_ws_forward: outputs y [n][3] for features
+   [n][16]. dp_ws_adam: one Adam step (bias-corrected, step >= 1) on count parameters. */
+int64_t dp_ws_workspace_floats(int64_t n);
+int32_t dp_ws_param_count(void);
+dp_status dp_ws_loss_grad(const float* W, const float* rows, int64_t n, float* loss, float* dW, float* work,
+                          void* stream);
+dp_status dp_ws_forward(const float* W, const float* feats, int64_t n, float* y, float* work, void* stream);
+dp_status dp_ws_adam(float* W, const float* dW, float* m, float* v, int64_t count, int32_t step, float lr, float beta1,
+                     float beta2, float eps, void* stream);
 
 #ifdef __cplusplus
 }

@@ -32,6 +32,8 @@ def main():
         "pendulum3_b1024_t1000": (WL.pendulum3(B=8, horizon=200), range(8), 200),
         "ball_b1_t300": (WL.ball(B=8, horizon=300), range(8), 300),
     }
+    for n in (5, 7, 10, 14):  # the solve at fewer sweeps (a warm-started solver's counts)
+        cases["quadruped_b4096_t1000_iters%d" % n] = (WL.quadruped(B=8, horizon=200, iters=n), range(8), 200)
     for name, (m, inst, T) in cases.items():
         f, r, n = average(m, inst, T)
         res[name] = {"forward": round(float(f), 1), "reverse": round(float(r), 1), "tape_nodes": round(float(n), 1),

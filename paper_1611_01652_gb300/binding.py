@@ -33,7 +33,10 @@ class BatchDesc(C.Structure):
                 ("gravity", C.c_float * 3), ("dt", C.c_float), ("ground_z", C.c_float), ("beta", C.c_float),
                 ("gamma", C.c_float), ("slop", C.c_float), ("iters", C.c_int32), ("horizon", C.c_int32),
                 ("ckpt_every", C.c_int32), ("loss_kind", C.c_int32), ("loss_mode", C.c_int32),
-                ("loss_body", C.c_int32), ("ctrl_fp32", C.c_int32)]
+                ("loss_body", C.c_int32), ("ctrl_fp32", C.c_int32), ("warmstart", C.c_int32)]
+
+WS_PARAMS = 5443
+WS_ROW = 19
 
 
 class ParamGrads(C.Structure):
@@ -43,7 +46,9 @@ class ParamGrads(C.Structure):
 _lib = None
 SYMBOLS = ("dp_create_world", "dp_free", "dp_num_params", "dp_num_slots", "dp_schedule", "dp_set_initial_state",
            "dp_set_state", "dp_get_state", "dp_step", "dp_rollout", "dp_backward", "dp_sync", "dp_last_error",
-           "dp_ckpt_every", "dp_backward_noalloc")
+           "dp_ckpt_every", "dp_backward_noalloc", "dp_set_warmstart", "dp_harvest", "dp_set_residual",
+           "dp_get_residual", "dp_ws_workspace_floats", "dp_ws_param_count", "dp_ws_loss_grad", "dp_ws_forward",
+           "dp_ws_adam", "dp_set_impulses", "dp_get_impulses")
 
 
 def load(build=True):
@@ -72,6 +77,19 @@ def load(build=True):
     lib.dp_backward_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
     lib.dp_sync.argtypes = [C.c_void_p]
     lib.dp_last_error.restype = C.c_char_p
+    lib.dp_set_warmstart.argtypes = [C.c_void_p, C.c_void_p, C.c_float]
+    lib.dp_set_impulses.argtypes = [C.c_void_p, C.c_void_p]
+    lib.dp_get_impulses.argtypes = [C.c_void_p, C.c_void_p]
+    lib.dp_harvest.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]
+    lib.dp_set_residual.argtypes = [C.c_void_p, C.c_int32]
+    lib.dp_get_residual.argtypes = [C.c_void_p, C.c_void_p]
+    lib.dp_ws_workspace_floats.argtypes = [C.c_int64]
+    lib.dp_ws_workspace_floats.restype = C.c_int64
+    lib.dp_ws_param_count.restype = C.c_int32
+    lib.dp_ws_loss_grad.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.dp_ws_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.dp_ws_adam.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_float,
+                               C.c_float, C.c_float, C.c_float, C.c_void_p]
     _lib = lib
     return lib
 
@@ -109,7 +127,7 @@ class World:
     ``stream`` (a torch.cuda.Stream, default: the current stream at creation).
     """
 
-    def __init__(self, model, stream=None, ckpt_every=None, horizon=None, iters=None):
+    def __init__(self, model, stream=None, ckpt_every=None, horizon=None, iters=None, warmstart=False):
         import torch
 
         lib = load()
@@ -153,7 +171,9 @@ class World:
         d.ckpt_every = model.ckpt_every if ckpt_every is None else ckpt_every
         d.loss_kind, d.loss_mode, d.loss_body = model.loss_kind, model.loss_mode, model.loss_body
         d.ctrl_fp32 = int(getattr(model, "ctrl_fp32", 0))
+        d.warmstart = int(bool(warmstart))
         self.horizon = d.horizon
+        self.n_motors = int(sum(1 for f in np.asarray(model.joint_flags).reshape(-1) if f & 2))
         h = C.c_void_p()
         _check(lib.dp_create_world(C.byref(d), C.c_void_p(self.stream.cuda_stream), C.byref(h)))
         self._h = h
@@ -214,6 +234,59 @@ class World:
 
     def sync(self):
         _check(_lib.dp_sync(self._h))
+
+    def set_warmstart(self, W, alpha=0.7):
+        """Enable the learned warm start with network parameters W [WS_PARAMS] and weight alpha
+        of the previous step's impulses (W = None: cold start)."""
+        _check(_lib.dp_set_warmstart(self._h, ptr(W), float(alpha)))
+
+    def set_impulses(self, lam):
+        _check(_lib.dp_set_impulses(self._h, ptr(lam)))
+
+    def get_impulses(self, out):
+        _check(_lib.dp_get_impulses(self._h, ptr(out)))
+        return out
+
+    def harvest(self, W, rows, u_noise=None):
+        """Rollout harvesting (features, ideal network output) rows into ``rows`` [max_rows, 19]
+        (device); returns the number of rows written."""
+        n = C.c_int64(0)
+        _check(_lib.dp_harvest(self._h, ptr(W), ptr(u_noise), ptr(rows), int(rows.shape[0]), C.byref(n)))
+        return int(n.value)
+
+    def set_residual(self, on=True):
+        _check(_lib.dp_set_residual(self._h, int(bool(on))))
+
+    def get_residual(self, out):
+        _check(_lib.dp_get_residual(self._h, ptr(out)))
+        return out
+
+
+# -- warm-start network training (free functions of the C ABI)
+def ws_workspace(n, device="cuda"):
+    import torch
+
+    load()
+    return torch.empty(int(_lib.dp_ws_workspace_floats(int(n))), device=device, dtype=torch.float32)
+
+
+def ws_loss_grad(W, rows, loss, dW, work, stream=None):
+    load()
+    s = C.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(_lib.dp_ws_loss_grad(ptr(W), ptr(rows), int(rows.shape[0]), ptr(loss), ptr(dW), ptr(work), s))
+
+
+def ws_forward(W, feats, y, work, stream=None):
+    load()
+    s = C.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(_lib.dp_ws_forward(ptr(W), ptr(feats), int(feats.shape[0]), ptr(y), ptr(work), s))
+
+
+def ws_adam(W, dW, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    load()
+    s = C.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(_lib.dp_ws_adam(ptr(W), ptr(dW), ptr(m), ptr(v), int(W.numel()), int(step), float(lr), float(beta1),
+                           float(beta2), float(eps), s))
 
 
 def make_rollout_function():

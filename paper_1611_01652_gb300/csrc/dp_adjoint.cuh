@@ -120,7 +120,7 @@ __device__ void pgs_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& VW,
       const float bias = R[RF_BIAS];
       const int o = (it * T.nslots + s) * 32;
       const float la = tp.lam[o];
-      const float lb = it > 0 ? tp.lam[o - T.nslots * 32] : 0.f;
+      const float lb = it > 0 ? tp.lam[o - T.nslots * 32] : (T.ws ? tp.lam0[s * 32] : 0.f);
       const int br = tp.br[o];
       const float dl = la - lb;
       float3 va = f3(0.f, 0.f, 0.f), wa = va, vb = va, wb = va, vba = va, wba = va, vbb = va, wbb = va;
@@ -216,6 +216,48 @@ __device__ void pgs_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& VW,
       RC.a3(rc + RC_ANGB, angBb);
       S[T.sm_lam + s] = -dbar + pbar * (1.f - meff * T.gamma);
     }
+  }
+}
+
+// Reverse of the warm-start application v += M^-1 J^T lambda0 over the warm-started rows. The
+// initial impulses are constants of the step (a starting guess), so only the rows and the
+// inverse masses/inertias that carry them receive adjoints; VB (the adjoint of the velocities
+// after the application) is also the adjoint of the pre-solve velocities.
+template <class RV>
+__device__ void ws_apply_reverse(const DevTopo& T, const LaneT<RV>& L, const SL& VB, const SL& RC, const TapeStep& tp) {
+  const SL& S = L.S;
+  for (int s = 0; s < T.nslots; ++s) {
+    const float dl = tp.lam0[s * 32];
+    if (dl == 0.f) continue;
+    const RV R = L.rows.at(s * RF_N);
+    const int a = T.sa[s], b = T.sb[s], rc = s * RC_N;
+    const float3 lin = R.v3(RF_LIN);
+    float3 linb = f3(0.f, 0.f, 0.f), angAb = linb, angBb = linb;
+    if (a >= 0) {
+      const float3 vba = VB.v3(6 * a), g = dl * VB.v3(6 * a + 3), angA = R.v3(RF_ANGA);
+      const float ima = S[T.sm_invm + a];
+      float ia[6];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) ia[q] = S[T.sm_iinv + 6 * a + q];
+      linb += (dl * ima) * vba;
+      angAb += symv(ia, g);
+      add_outer(S, T.sm_iinvb + 9 * a, g, angA);
+      S[T.sm_invmb + a] += dl * dot3(lin, vba);
+    }
+    if (b >= 0) {
+      const float3 vbb = VB.v3(6 * b), g = dl * VB.v3(6 * b + 3), angB = R.v3(RF_ANGB);
+      const float imb = S[T.sm_invm + b];
+      float ib[6];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) ib[q] = S[T.sm_iinv + 6 * b + q];
+      linb -= (dl * imb) * vbb;
+      angBb += symv(ib, g);
+      add_outer(S, T.sm_iinvb + 9 * b, g, angB);
+      S[T.sm_invmb + b] -= dl * dot3(lin, vbb);
+    }
+    RC.a3(rc + RC_LIN, linb);
+    RC.a3(rc + RC_ANGA, angAb);
+    RC.a3(rc + RC_ANGB, angBb);
   }
 }
 

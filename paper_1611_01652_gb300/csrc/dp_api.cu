@@ -169,6 +169,11 @@ void plan_smem(DevTopo& T, bool backward, int smem_floats_max) {
   T.sm_wst = take(T.nj);
   T.sm_wbr = take(T.nj);
   T.sm_lam = take(T.nslots);
+  // warm-start scratch (features, outputs, harvest row ids): the joint arrays above are dead
+  // once the rows are assembled, so they host it when they are large enough
+  const int wsneed = 19 + T.n_wsg;
+  const int jreg = T.sm_wbr + std::max(T.nj, 1) - T.sm_th;
+  T.sm_ws = wsneed <= jreg ? T.sm_th : take(wsneed);
   T.sm_x0 = T.sm_u = 0;
   T.sm_rows = -1;
   if (!backward) {
@@ -312,6 +317,28 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
     w->kind[s] = slots[s].kind;
     w->colour[s] = col[s];
   }
+  // warm-start groups, in slot order of their first row
+  T.n_wsg = 0;
+  for (int s = 0; s < T.nslots; ++s) {
+    const Slot& q = slots[s];
+    int type = -1, g3[3] = {s, s + 1, s + 2};
+    if (q.kind == RK_JLIN && q.sub == 0) {
+      type = WSG_JOINT;
+    } else if (q.kind == RK_JANG && q.sub == 0) {
+      type = WSG_HINGE;
+      g3[2] = -1;
+      for (int k = 0; k < T.nslots; ++k)
+        if (slots[k].kind == RK_MOTOR && slots[k].idx == q.idx) g3[2] = k;
+    } else if (q.kind == RK_GN) {
+      type = WSG_GROUND;
+    } else if (q.kind == RK_PN) {
+      type = WSG_PAIR;
+    }
+    if (type < 0) continue;
+    T.wsg_type[T.n_wsg] = (int8_t)type;
+    for (int k = 0; k < 3; ++k) T.wsg_slot[T.n_wsg][k] = (int16_t)g3[k];
+    ++T.n_wsg;
+  }
   // parameter fields
   int o = 0;
   T.o_mass = o; o += T.nb;
@@ -350,6 +377,8 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
     T.dump_rows = r;
   }
   T.n_params = (int)np_;
+  T.ws = 0;
+  T.ws_alpha = 0.7f;
   T.mlp_tc = T.n_layers == 3 && !T.skip && T.ctrl_round && T.widths[0] == CtrlTC::K0 && T.widths[1] == CtrlTC::H1 &&
              T.widths[2] == CtrlTC::H2 && T.widths[3] == CtrlTC::NO && !getenv("DP_FORCE_SIMT_CONTROLLER");
   T.topo_id = match_compiled_topology(T, T.nb, T.nj, T.ns, T.np, d->joint_type, d->joint_body, d->joint_flags,
@@ -388,12 +417,16 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
     o += (long long)T.nb * 6 * 32 * 4;
     T.rec_br = o;
     o += (long long)T.iters * T.nslots * 32;
+    o = (o + 15) / 16 * 16;
+    T.rec_lam0 = o;
+    if (d->warmstart) o += (long long)T.nslots * 32 * 4;
     T.rec_bytes = (o + 255) / 256 * 256;
     for (DevTopo* t2 : {&w->Tf, &w->Tb}) {
       t2->rec_lam = T.rec_lam;
       t2->rec_viter = T.rec_viter;
       t2->rec_vminus = T.rec_vminus;
       t2->rec_br = T.rec_br;
+      t2->rec_lam0 = T.rec_lam0;
       t2->rec_bytes = T.rec_bytes;
     }
   }
@@ -474,7 +507,30 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
     D.Wt = D.Wn = D.bias = dummy;
     D.dump = dummy;
   }
-  const int widest = std::max({nf, 6 * T.nj, 3 * T.nb, 3 * T.ns, 32});
+  // warm start (enabled later by dp_set_warmstart), residual sums, harvest counter
+  w->ws_capable = d->warmstart != 0;
+  if (w->ws_capable) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, sizeof(__nv_bfloat16) * WsTC::SIZE) != cudaSuccess) return cleanup(DP_ENOMEM);
+    w->allocs.push_back(p);
+    w->ws_tc = (__nv_bfloat16*)p;
+    if (dalloc(w, &w->ws_master, (size_t)WsTC::PARAMS) || dalloc(w, &w->ws_b, (size_t)WsTC::BSIZE))
+      return cleanup(DP_ENOMEM);
+  }
+  if (dalloc(w, &w->resid, Bz) || dalloc(w, &w->harvest_count, 1) || dalloc(w, &D.lam_prev, (size_t)T.nslots * Bz))
+    return cleanup(DP_ENOMEM);
+  CU(cudaMemsetAsync(w->resid, 0, sizeof(float) * Bz, w->stream));
+  CU(cudaMemsetAsync(D.lam_prev, 0, sizeof(float) * (size_t)std::max(T.nslots, 1) * Bz, w->stream));
+  D.ckpt_lam = nullptr;
+  if (w->ws_capable && !full && dalloc(w, &D.ckpt_lam, (size_t)n_ckpt * T.nslots * Bz)) return cleanup(DP_ENOMEM);
+  D.ws_tc = w->ws_tc;
+  D.ws_b = w->ws_b;
+  D.harvest = nullptr;
+  D.harvest_count = w->harvest_count;
+  D.harvest_max = 0;
+  D.u_noise = nullptr;
+  D.resid = nullptr;
+  const int widest = std::max({nf, 6 * T.nj, 3 * T.nb, 3 * T.ns, T.nslots, 32});
   w->stage_floats = std::max<size_t>((size_t)B * widest, (size_t)np_);
   if (dalloc(w, &w->stage, w->stage_floats)) return cleanup(DP_ENOMEM);
   CU(cudaMemsetAsync(D.status, 0, sizeof(int) * Bp, w->stream));
@@ -547,6 +603,8 @@ dp_status dp_set_state(dp_world* w, const float* state, int32_t t) {
   if (!w) return fail(DP_EINVAL, "world is NULL");
   if (t < 0) return fail(DP_EINVAL, "t must be >= 0");
   TRY(stage_state_in(w, state, w->D.state));
+  // the previous impulses belonged to another trajectory: the next step starts without them
+  CU(cudaMemsetAsync(w->D.lam_prev, 0, sizeof(float) * (size_t)std::max(w->Tf.nslots, 1) * w->Bp, w->stream));
   w->t_now = t;
   w->have_rollout = false;
   return DP_OK;
@@ -576,6 +634,10 @@ dp_status dp_step(dp_world* w, int32_t n_steps, const float* W, uint8_t* active)
   DevPtrs D = w->D;
   D.active = active;
   D.traj = nullptr;
+  if (w->resid_on) {
+    D.resid = w->resid;
+    w->resid_steps += n_steps;
+  }
   CU(launch_forward(w->Tf, D, w->x0, w->t_now, n_steps, 0, 0, w->stream));
   w->t_now += n_steps;
   w->have_rollout = false;
@@ -588,11 +650,90 @@ dp_status dp_rollout(dp_world* w, const float* W, float* loss, float* traj, uint
   DevPtrs D = w->D;
   D.active = active;
   D.traj = traj;
+  if (w->resid_on) {
+    D.resid = w->resid;
+    w->resid_steps = w->Tf.horizon;
+    CU(cudaMemsetAsync(w->resid, 0, sizeof(float) * w->Bp, w->stream));
+  }
   CU(cudaMemsetAsync(D.status, 0, sizeof(int) * w->Bp, w->stream));
   CU(launch_forward(w->Tf, D, w->x0, 0, w->Tf.horizon, 1, D.tape_full, w->stream));
   if (loss) CU(cudaMemcpyAsync(loss, D.loss, sizeof(float) * w->B, cudaMemcpyDefault, w->stream));
   w->t_now = w->Tf.horizon;
   w->have_rollout = true;
+  return DP_OK;
+}
+
+dp_status dp_set_warmstart(dp_world* w, const float* W, float alpha) {
+  if (!w) return fail(DP_EINVAL, "world is NULL");
+  if (!w->ws_capable) return fail(DP_EINVAL, "the world was created without warm-start support (desc.warmstart = 0)");
+  if (!(alpha >= 0.f && alpha <= 1.f)) return fail(DP_EINVAL, "alpha must lie in [0, 1]");
+  if (w->have_rollout) w->have_rollout = false;  // the recorded tape belongs to the other solver
+  w->Tf.ws_alpha = w->Tb.ws_alpha = alpha;
+  if (!W) {
+    w->Tf.ws = w->Tb.ws = 0;
+    return DP_OK;
+  }
+  CU(cudaMemcpyAsync(w->ws_master, W, sizeof(float) * WsTC::PARAMS, cudaMemcpyDefault, w->stream));
+  CU(launch_ws_prep(w->ws_master, w->ws_tc, w->ws_b, w->stream));
+  w->Tf.ws = w->Tb.ws = 1;
+  return DP_OK;
+}
+
+dp_status dp_set_impulses(dp_world* w, const float* lam) {
+  if (!w || !lam) return fail(DP_EINVAL, "world or lam is NULL");
+  const int ns = w->Tf.nslots;
+  if (ns == 0) return DP_OK;
+  CU(cudaMemcpyAsync(w->stage, lam, sizeof(float) * (size_t)w->B * ns, cudaMemcpyDefault, w->stream));
+  CU(launch_state_in(w->B, w->Bp, ns, w->stage, w->D.lam_prev, w->stream));
+  return DP_OK;
+}
+
+dp_status dp_get_impulses(dp_world* w, float* lam) {
+  if (!w || !lam) return fail(DP_EINVAL, "world or lam is NULL");
+  const int ns = w->Tf.nslots;
+  if (ns == 0) return DP_OK;
+  CU(launch_state_out(w->B, w->Bp, ns, w->D.lam_prev, w->stage, w->stream));
+  CU(cudaMemcpyAsync(lam, w->stage, sizeof(float) * (size_t)w->B * ns, cudaMemcpyDefault, w->stream));
+  return DP_OK;
+}
+
+dp_status dp_harvest(dp_world* w, const float* W, const float* u_noise, float* rows, int64_t max_rows,
+                     int64_t* n_rows) {
+  if (!w) return fail(DP_EINVAL, "world is NULL");
+  if (!rows || max_rows < 0 || !n_rows) return fail(DP_EINVAL, "rows or n_rows is NULL, or max_rows < 0");
+  TRY(stage_weights(w, W));
+  DevPtrs D = w->D;
+  D.active = nullptr;
+  D.traj = nullptr;
+  D.harvest = rows;
+  D.harvest_max = max_rows;
+  D.u_noise = u_noise;
+  const DevTopo& T = w->Tf;
+  CU(cudaMemsetAsync(w->harvest_count, 0, sizeof(unsigned long long), w->stream));
+  CU(cudaMemsetAsync(D.status, 0, sizeof(int) * w->Bp, w->stream));
+  CU(launch_forward(T, D, w->x0, 0, T.horizon, 1, 0, w->stream));
+  unsigned long long cnt = 0;
+  CU(cudaMemcpyAsync(&cnt, w->harvest_count, sizeof(cnt), cudaMemcpyDeviceToHost, w->stream));
+  CU(cudaStreamSynchronize(w->stream));
+  *n_rows = (int64_t)std::min<unsigned long long>(cnt, (unsigned long long)max_rows);
+  w->t_now = T.horizon;
+  w->have_rollout = false;
+  return DP_OK;
+}
+
+dp_status dp_set_residual(dp_world* w, int32_t on) {
+  if (!w) return fail(DP_EINVAL, "world is NULL");
+  w->resid_on = on != 0;
+  w->resid_steps = 0;
+  CU(cudaMemsetAsync(w->resid, 0, sizeof(float) * w->Bp, w->stream));
+  return DP_OK;
+}
+
+dp_status dp_get_residual(dp_world* w, float* resid) {
+  if (!w || !resid) return fail(DP_EINVAL, "world or resid is NULL");
+  const float sc = w->resid_steps > 0 ? 1.f / (float)w->resid_steps : 0.f;
+  CU(launch_scale_out(w->B, w->resid, sc, w->stage, w->stream));
+  CU(cudaMemcpyAsync(resid, w->stage, sizeof(float) * w->B, cudaMemcpyDefault, w->stream));
   return DP_OK;
 }
 

@@ -16,6 +16,10 @@
 #define DPK_MAXP 32
 #define DPK_MAXSLOT (5 * DPK_MAXJ + 2 * DPK_MAXJ + 3 * DPK_MAXS + 3 * DPK_MAXP)
 #define DPK_MAXL 6
+#define DPK_MAXWSG (2 * DPK_MAXJ + DPK_MAXS + DPK_MAXP)
+
+// Warm-start group types (feature 15 of a group).
+enum { WSG_GROUND = 0, WSG_PAIR = 1, WSG_JOINT = 2, WSG_HINGE = 3 };
 
 // Row kinds (canonical slot order: joints, limits, motors, ground contacts, pair contacts).
 enum { RK_JLIN = 0, RK_JANG = 1, RK_LIMIT = 2, RK_MOTOR = 3, RK_GN = 4, RK_GT = 5, RK_PN = 6, RK_PT = 7 };
@@ -41,6 +45,14 @@ struct DevTopo {
   int n_layers, skip, n_params, n_motors, ctrl_round;  // ctrl_round: 1 = bfloat16 storage points
   int topo_id;  // 0: run-time topology loops; otherwise the compiled topology with this id
   int mlp_tc;   // 1: the controller is the 24-128-128-8 bfloat16 network, run on the tensor cores
+  int ws;       // 1: the solve starts from the learned warm start (DevPtrs.ws_tc, ws_alpha)
+  float ws_alpha;  // weight of the previous step's impulses in the warm start
+  int sm_ws;    // warm-start scratch per lane: features [16], outputs [3], harvest row ids [n_wsg]
+  // warm-start groups of three rows (slot -1: none): joint linear rows, hinge angular rows with
+  // the motor row, contact normal/t1/t2 rows; type WSG_*
+  int n_wsg;
+  int8_t wsg_type[DPK_MAXWSG];
+  int16_t wsg_slot[DPK_MAXWSG][3];
   int widths[DPK_MAXL + 1];
   int w_off[DPK_MAXL + 2];   // offset of layer l's W[out][in] in the flat weights (l = n_layers: skip)
   float gravity[3], dt, ground_z, beta, gamma, slop, clock_hz;
@@ -67,7 +79,8 @@ struct DevTopo {
   //   viter  [iters][nb*6]        float   velocities after each sweep
   //   vminus [nb*6]               float   velocities after the external impulses
   //   br     [iters][nslots]      uint8   clamp branch (0 inside, 1 lower bound, 2 upper bound)
-  long long rec_lam, rec_viter, rec_vminus, rec_br, rec_bytes;
+  //   lam0   [nslots]             float   initial impulses (warm start; only when DevTopo.ws)
+  long long rec_lam, rec_viter, rec_vminus, rec_br, rec_lam0, rec_bytes;
 };
 
 // Global buffers a kernel works on.
@@ -77,6 +90,15 @@ struct DevPtrs {
   const float* Wn;       // same, each layer [out][in]
   const float* bias;     // controller biases, per layer [out] (then skip bias)
   const __nv_bfloat16* Wtc;  // tensor-core weight layouts (CtrlTC), when DevTopo.mlp_tc
+  const __nv_bfloat16* ws_tc;  // warm-start network, tensor-core layouts (WsTC)
+  const float* ws_b;           // warm-start biases (WsTC::B1, B2, B3)
+  float* harvest;              // optional: harvested rows [harvest_max][19] (features, converged impulses)
+  unsigned long long* harvest_count;
+  long long harvest_max;
+  const float* u_noise;        // optional: controller-output perturbation [T][Bp][n_motors]
+  float* resid;                // optional: per-instance sum of per-step solve residuals [Bp]
+  float* lam_prev;             // impulses the last step ended with [nslots][Bp] (kept across launches)
+  float* ckpt_lam;             // optional: the same at every checkpoint [n_ckpt][nslots][Bp]
   float* state;          // current state [nb*18][Bp]
   float* ckpt;           // checkpoints [n_ckpt][nb*18][Bp]
   float* seg;            // segment states for the backward [K+1][nb*18][Bp]
@@ -105,6 +127,7 @@ struct TapeStep {
   float* viter;   // (it, j) at viter[(it * nb * 6 + j) * 32]
   float* vminus;  // j at vminus[j * 32]
   uint8_t* br;    // (it, s) at br[(it * nslots + s) * 32]
+  float* lam0;    // s at lam0[s * 32]
   const uint8_t* rec;
 };
 __device__ __forceinline__ TapeStep tape_step(const DevTopo& T, const DevPtrs& D, int ts) {
@@ -117,6 +140,7 @@ __device__ __forceinline__ TapeStep tape_step(const DevTopo& T, const DevPtrs& D
   p.viter = (float*)(rec + T.rec_viter) + lane;
   p.vminus = (float*)(rec + T.rec_vminus) + lane;
   p.br = (uint8_t*)(rec + T.rec_br) + lane;
+  p.lam0 = (float*)(rec + T.rec_lam0) + lane;
   return p;
 }
 // Bulk prefetch of a tape record into L2 (issued by one lane; fire-and-forget).

@@ -388,7 +388,8 @@ template <bool TAPE, class RV>
 __device__ void pgs_solve(const DevTopo& T, const LaneT<RV>& L, const SL& X, const TapeStep& tp) {
   const SL& S = L.S;
   const int Bp = T.Bp;
-  for (int s = 0; s < T.nslots; ++s) S[T.sm_lam + s] = 0.f;
+  if (!T.ws)
+    for (int s = 0; s < T.nslots; ++s) S[T.sm_lam + s] = 0.f;
   for (int it = 0; it < T.iters; ++it) {
     for (int oi = 0; oi < T.nslots; ++oi) {
       const int s = T.order[oi];
@@ -466,6 +467,202 @@ __device__ void integrate(const DevTopo& T, const SL& X) {
   }
 }
 
+// ------------------------------------------------------------------------------ warm start
+// Learned warm start. The rows are taken in groups of three (DevTopo.wsg_*): the linear rows of
+// a joint, the angular rows of a hinge with its motor row, the normal and friction rows of a
+// contact. Each group gets 16 features from its assembled rows, the pre-solve velocities and the
+// robot's mass distribution; the 16-64-64-3 bfloat16 network (tensor cores, the warp's 32
+// instances as rows) gives a velocity-scale correction y per row, and the start alpha
+// lambda_prev + m_eff y is projected on the rows' bounds (normal >= 0, |friction| <= mu normal,
+// |motor| <= tau_max h) and applied in slot order before the first sweep. The same features
+// feed the harvest of training rows.
+template <class RV>
+__device__ __forceinline__ float row_jv(const DevTopo& T, const RV& R, const SL& X, int a, int b) {
+  float Jv = 0.f;
+  const float3 lin = R.v3(RF_LIN);
+  if (a >= 0) Jv += dot3(lin, X.v3(18 * a + 12)) + dot3(R.v3(RF_ANGA), X.v3(18 * a + 15));
+  if (b >= 0) Jv += dot3(R.v3(RF_ANGB), X.v3(18 * b + 15)) - dot3(lin, X.v3(18 * b + 12));
+  return Jv;
+}
+
+// Applies impulse dl of row R (slot bodies a, b) to the velocities in X.
+template <class RV>
+__device__ __forceinline__ void row_apply(const DevTopo& T, const SL& S, const RV& R, const SL& X, int a, int b, float dl) {
+  const float3 lin = R.v3(RF_LIN);
+  if (a >= 0) {
+    X.s3(18 * a + 12, X.v3(18 * a + 12) + (dl * S[T.sm_invm + a]) * lin);
+    X.s3(18 * a + 15, X.v3(18 * a + 15) + dl * R.v3(RF_IA));
+  }
+  if (b >= 0) {
+    X.s3(18 * b + 12, X.v3(18 * b + 12) - (dl * S[T.sm_invm + b]) * lin);
+    X.s3(18 * b + 15, X.v3(18 * b + 15) + dl * R.v3(RF_IB));
+  }
+}
+
+// Features, inference, projection and application (ws), harvest row reservation (harvest).
+// On entry S[sm_lam] holds the impulses the previous step ended with (lambda_prev); on exit the
+// initial impulses alpha lambda_prev + network output, projected (warm start), or the same
+// lambda_prev (cold start: the solver zeroes them).
+template <bool TAPE, class RV>
+__device__ void warm_start(const DevTopo& T, const DevPtrs& D, const LaneT<RV>& L, const SL& X, const TapeStep& tp) {
+  const SL& S = L.S;
+  float mtot = 0.f;
+  float3 pc = f3(0.f, 0.f, 0.f);
+  for (int b = 0; b < T.nb; ++b) {
+    const float m = L.P[T.o_mass + b];
+    mtot += m;
+    pc += m * X.v3(18 * b);
+  }
+  pc = (1.f / mtot) * pc;
+  int nact = 0;
+  for (int s = 0; s < T.nslots; ++s)
+    if ((T.skind[s] == RK_GN || T.skind[s] == RK_PN) && L.rows[s * RF_N + RF_MEFF] != 0.f) ++nact;
+  const float gn = sqrtf(T.gravity[0] * T.gravity[0] + T.gravity[1] * T.gravity[1] + T.gravity[2] * T.gravity[2]);
+  const float share = mtot * gn * T.dt / (float)max(1, nact);
+  const SL F = S.at(T.sm_ws), Y = S.at(T.sm_ws + 16), H = S.at(T.sm_ws + 19);
+  const bool harvest = D.harvest != nullptr;
+  const int lane = threadIdx.x & 31;
+  for (int g = 0; g < T.n_wsg; ++g) {
+    const int type = T.wsg_type[g];
+    const int s0 = T.wsg_slot[g][0], s1 = T.wsg_slot[g][1], s2 = T.wsg_slot[g][2];
+    const bool contact = type == WSG_GROUND || type == WSG_PAIR;
+    float3 q;  // the group's point: contact point on body a, or the joint's anchor on its child
+    if (type == WSG_GROUND) {
+      const int qi = T.sidx[s0], a = T.sa[s0];
+      q = X.v3(18 * a) + mv(loadR(X, 18 * a), L.P.v3(T.o_sph_off + 3 * qi)) - L.P[T.o_sph_rad + qi] * f3(0.f, 0.f, 1.f);
+    } else if (type == WSG_PAIR) {
+      const int k = T.pk[T.sidx[s0]], a = T.sa[s0];
+      q = X.v3(18 * a) + mv(loadR(X, 18 * a), L.P.v3(T.o_sph_off + 3 * k)) -
+          L.P[T.o_sph_rad + k] * L.rows.at(s0 * RF_N).v3(RF_LIN);
+    } else {
+      const int j = T.sidx[s0], b = T.sb[s0];
+      q = X.v3(18 * b) + mv(loadR(X, 18 * b), L.P.v3(T.o_anchor + 6 * j + 3));
+    }
+    float lp[3];  // impulses the group's rows ended the previous step with
+    for (int k = 0; k < 3; ++k) {
+      const int s = T.wsg_slot[g][k];
+      const RV R = L.rows.at((s >= 0 ? s : 0) * RF_N);
+      const bool on = s >= 0 && R[RF_MEFF] != 0.f;  // rows of inactive slots contribute zeros
+      F[k] = on ? row_jv(T, R, X, T.sa[s], T.sb[s]) : 0.f;
+      F[3 + k] = on ? R[RF_BIAS] : 0.f;
+      F[6 + k] = on ? R[RF_MEFF] : 0.f;
+      lp[k] = s >= 0 ? S[T.sm_lam + s] : 0.f;
+    }
+    F[9] = contact ? L.rows[s1 * RF_N + RF_BND] : (type == WSG_HINGE && s2 >= 0 ? L.rows[s2 * RF_N + RF_BND] : 0.f);
+    F[10] = q.x - pc.x;
+    F[11] = q.y - pc.y;
+    F[12] = (float)nact;
+    F[13] = share;
+    F[14] = q.z - T.ground_z;
+    F[15] = (float)type;
+    const bool active = L.rows[s0 * RF_N + RF_MEFF] != 0.f;
+    if (harvest) {  // padded lanes (copies of the last instance) harvest nothing
+      const unsigned m = __ballot_sync(FULLMASK, active && L.i < T.B);
+      unsigned long long base = 0;
+      if (lane == 0 && m) base = atomicAdd(D.harvest_count, (unsigned long long)__popc(m));
+      base = __shfl_sync(FULLMASK, base, 0);
+      const long long id = (m >> lane) & 1u ? (long long)(base + __popc(m & ((1u << lane) - 1u))) : -1;
+      const bool keep = id >= 0 && id < D.harvest_max;
+      H[g] = __int_as_float(keep ? (int)id : -1);
+      if (keep) {
+        for (int k = 0; k < 16; ++k) D.harvest[id * 19 + k] = F[k];
+        for (int k = 0; k < 3; ++k) D.harvest[id * 19 + 16 + k] = lp[k];  // replaced after the solve
+      }
+    }
+    if (T.ws) {
+      __syncwarp();
+      mlp3_forward<WsTC::K0, WsTC::H1, WsTC::H2, WsTC::NO>(
+          [&](int f, int r) { return F.lane_at(f, r); }, D.ws_tc + WsTC::W1, D.ws_b + WsTC::B1, D.ws_tc + WsTC::W2,
+          D.ws_b + WsTC::B2, D.ws_tc + WsTC::W3, D.ws_b + WsTC::B3,
+          [&](int f, int r, float v) { Y.lane_at(f, r) = v; }, [](int, int, int, float) {});
+      __syncwarp();
+      float z[3];
+      for (int k = 0; k < 3; ++k) z[k] = T.ws_alpha * lp[k] + F[6 + k] * Y[k];
+      if (contact) {
+        float l0[3] = {0.f, 0.f, 0.f};
+        if (active) {
+          l0[0] = fmaxf(z[0], 0.f);
+          const float hi = L.rows[s1 * RF_N + RF_BND] * l0[0];
+          l0[1] = fminf(fmaxf(z[1], -hi), hi);
+          l0[2] = fminf(fmaxf(z[2], -hi), hi);
+        }
+        S[T.sm_lam + s0] = l0[0];
+        S[T.sm_lam + s1] = l0[1];
+        S[T.sm_lam + s2] = l0[2];
+      } else {
+        for (int k = 0; k < 3; ++k) {
+          const int s = T.wsg_slot[g][k];
+          if (s < 0) continue;
+          float y = L.rows[s * RF_N + RF_MEFF] != 0.f ? z[k] : 0.f;
+          if (T.skind[s] == RK_MOTOR) {
+            const float hi = L.rows[s * RF_N + RF_BND];
+            y = fminf(fmaxf(y, -hi), hi);
+          }
+          S[T.sm_lam + s] = y;
+        }
+      }
+      __syncwarp();
+    }
+  }
+  if (T.ws) {
+    for (int s = 0; s < T.nslots; ++s)
+      if (T.skind[s] == RK_LIMIT) S[T.sm_lam + s] = 0.f;  // limits start cold
+    for (int s = 0; s < T.nslots; ++s) {
+      const float l0 = S[T.sm_lam + s];
+      if (l0 != 0.f) row_apply(T, S, L.rows.at(s * RF_N), X, T.sa[s], T.sb[s], l0);
+    }
+    if (TAPE)
+      for (int s = 0; s < T.nslots; ++s) tp.lam0[s * 32] = S[T.sm_lam + s];
+  }
+}
+
+// Harvest: per reserved group, the network's ideal output: the impulses after the solve minus
+// alpha times the previous ones (parked in the row's output slots before the solve), divided by
+// the row's effective mass (zero for inactive rows).
+template <class RV>
+__device__ void harvest_finish(const DevTopo& T, const DevPtrs& D, const LaneT<RV>& L) {
+  const SL& S = L.S;
+  const SL H = S.at(T.sm_ws + 19);
+  for (int g = 0; g < T.n_wsg; ++g) {
+    const int id = __float_as_int(H[g]);
+    if (id < 0) continue;
+    float* row = D.harvest + (long long)id * 19;
+    for (int k = 0; k < 3; ++k) {
+      const int s = T.wsg_slot[g][k];
+      const float me = row[6 + k];
+      row[16 + k] = me != 0.f ? ((s >= 0 ? S[T.sm_lam + s] : 0.f) - T.ws_alpha * row[16 + k]) / me : 0.f;
+    }
+  }
+}
+
+// RMS complementarity residual of the solve over the active rows, with w = J v + bias + gamma
+// lambda: bilateral |w|; one-sided |min(lambda, w)|; boxed |lambda - clamp(lambda - w, lo, hi)|.
+template <class RV>
+__device__ float solve_residual(const DevTopo& T, const LaneT<RV>& L, const SL& X) {
+  const SL& S = L.S;
+  float ss = 0.f;
+  int na = 0;
+  for (int s = 0; s < T.nslots; ++s) {
+    const RV R = L.rows.at(s * RF_N);
+    if (R[RF_MEFF] == 0.f) continue;
+    const int kind = T.skind[s];
+    const float l = S[T.sm_lam + s];
+    const float w = row_jv(T, R, X, T.sa[s], T.sb[s]) + R[RF_BIAS] + T.gamma * l;
+    float e;
+    if (kind == RK_JLIN || kind == RK_JANG) {
+      e = w;
+    } else if (kind == RK_LIMIT || kind == RK_GN || kind == RK_PN) {
+      e = fminf(l, w);
+    } else {
+      const float hi = (kind == RK_MOTOR) ? R[RF_BND] : R[RF_BND] * S[T.sm_lam + T.snormal[s]];
+      e = l - fminf(fmaxf(l - w, -hi), hi);
+    }
+    ss += e * e;
+    ++na;
+  }
+  return na ? sqrtf(ss / (float)na) : 0.f;
+}
+
 // One full step x_t -> x_{t+1} in place on X. Returns the loss term of x_{t+1}.
 template <class Q, bool TAPE, class RV>
 __device__ void pgs_solve_static(const DevTopo& T, const LaneT<RV>& L, const SL& X, const TapeStep& tp);
@@ -483,6 +680,10 @@ __device__ float step_forward(const DevTopo& T, const DevPtrs& D, const LaneT<RV
       controller_forward_tc(T, D, act, dump_col);
     else
       controller_forward(T, D, act);
+    if (D.u_noise) {  // perturbed controller output (harvest of training rows)
+      const float* nz = D.u_noise + ((size_t)t * T.B + min(L.i, T.B - 1)) * T.n_motors;  // [T][B][n_motors]
+      for (int m = 0; m < T.n_motors && m < T.widths[T.n_layers]; ++m) act[T.n_layers][m] += nz[m];
+    }
     if (dump_col) {
       const size_t N = (size_t)T.horizon * T.Bp;
       for (int l = 0; l <= T.n_layers; ++l) {
@@ -506,10 +707,13 @@ __device__ float step_forward(const DevTopo& T, const DevPtrs& D, const LaneT<RV
   if (TAPE && !RV::is_global) {
     for (int f = 0; f < T.nslots * RF_N; ++f) tp.rows[f * 32] = L.rows[f];
   }
+  if (T.ws || D.harvest) warm_start<TAPE>(T, D, L, X, tp);
   if constexpr (Q::id == 0)
     pgs_solve<TAPE>(T, L, X, tp);
   else
     pgs_solve_static<Q, TAPE>(T, L, X, tp);
+  if (D.harvest) harvest_finish(T, D, L);
+  if (D.resid) D.resid[L.i] += solve_residual(T, L, X);
   integrate(T, X);
   float w = loss_weight(T, t + 1);
   return w != 0.f ? w * loss_value(T, L, X) : 0.f;

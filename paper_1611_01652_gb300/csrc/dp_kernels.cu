@@ -87,6 +87,10 @@ __global__ void k_param_out(int B, int Bp, int o, int n, const float* __restrict
   if (i >= B) return;
   for (int f = 0; f < n; ++f) dst[(size_t)i * n + f] = src[(size_t)(o + f) * Bp + i];
 }
+__global__ void k_scale_out(int B, const float* __restrict__ src, float sc, float* dst) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < B) dst[i] = src[i] * sc;
+}
 __global__ void k_pad_scalar(int B, int Bp, const float* __restrict__ src, float* dst) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Bp) return;
@@ -130,13 +134,20 @@ __global__ void __launch_bounds__(32, 1) k_forward(const __grid_constant__ DevTo
   SL act[DPK_MAXL + 1];
   for (int l = 0; l <= DPK_MAXL; ++l) act[l] = SL{sm + T.sm_act[l] * 32};
   copy_state_to_smem(T, rollout ? x0 : D.state, i, X);
+  // impulses of the previous step (the warm start's lambda_prev): none before a rollout
+  for (int s = 0; s < T.nslots; ++s) L.S[T.sm_lam + s] = rollout ? 0.f : D.lam_prev[(size_t)s * T.Bp + i];
   float loss = 0.f;
   if (rollout && T.loss_kind == 3) loss = -dot3(L.P.v3(T.o_loss_target), loss_point(T, L, X));
   const int B = T.B;
   for (int k = 0; k < nsteps; ++k) {
     const int t = t0 + k;
     if (rollout) {
-      if (t % D.ckpt_every == 0) copy_state_from_smem(T, D.ckpt + (size_t)(t / D.ckpt_every) * 18 * T.nb * T.Bp, i, X);
+      if (t % D.ckpt_every == 0) {
+        copy_state_from_smem(T, D.ckpt + (size_t)(t / D.ckpt_every) * 18 * T.nb * T.Bp, i, X);
+        if (D.ckpt_lam)
+          for (int s = 0; s < T.nslots; ++s)
+            D.ckpt_lam[((size_t)(t / D.ckpt_every) * T.nslots + s) * T.Bp + i] = L.S[T.sm_lam + s];
+      }
       if (D.traj && i < B)
         for (int f = 0; f < 18 * T.nb; ++f) D.traj[((size_t)t * B + i) * 18 * T.nb + f] = X[f];
     }
@@ -148,6 +159,7 @@ __global__ void __launch_bounds__(32, 1) k_forward(const __grid_constant__ DevTo
   }
   if (rollout && D.traj && i < B)
     for (int f = 0; f < 18 * T.nb; ++f) D.traj[((size_t)(t0 + nsteps) * B + i) * 18 * T.nb + f] = X[f];
+  for (int s = 0; s < T.nslots; ++s) D.lam_prev[(size_t)s * T.Bp + i] = L.S[T.sm_lam + s];
   copy_state_from_smem(T, D.state, i, X);
   bool bad = !isfinite(loss);
   for (int f = 0; f < 18 * T.nb; ++f) bad |= !isfinite(X[f]);
@@ -208,6 +220,7 @@ __device__ void reverse_step(const DevTopo& T, const DevPtrs& D, const BwdCtx& C
     pgs_reverse_static<Q>(T, L, tp);
   else
     pgs_reverse(T, Bl, VW, C.VB, C.RC, tp);
+  if (T.ws) ws_apply_reverse(T, L, C.VB, C.RC, tp);
   rows_reverse(T, Bl, C.XB, C.VB, C.RC);
   external_reverse(T, Bl, C.XB, C.VB);
   if (T.n_layers > 0) {
@@ -246,6 +259,8 @@ __global__ void __launch_bounds__(32, 1) k_backward(const __grid_constant__ DevT
       const int ta = c * K;
       const int tb = min(T.horizon, ta + K);
       copy_state_to_smem(T, D.ckpt + (size_t)c * sbytes, i, C.X);
+      if (T.ws)  // the previous impulses the segment's first step started from
+        for (int s = 0; s < T.nslots; ++s) C.S[T.sm_lam + s] = D.ckpt_lam[((size_t)c * T.nslots + s) * Bp + i];
       for (int t = ta; t < tb; ++t) {
         copy_state_from_smem(T, D.seg + (size_t)(t - ta) * sbytes, i, C.X);
         const TapeStep tp = tape_step(T, D, t - ta);
@@ -362,6 +377,10 @@ cudaError_t launch_state_out(int B, int Bp, int nf, const float* src, float* dst
 }
 cudaError_t launch_param_out(int B, int Bp, int o, int n, const float* src, float* dst, cudaStream_t s) {
   k_param_out<<<(B + 127) / 128, 128, 0, s>>>(B, Bp, o, n, src, dst);
+  return cudaGetLastError();
+}
+cudaError_t launch_scale_out(int B, const float* src, float scale, float* dst, cudaStream_t s) {
+  k_scale_out<<<(B + 127) / 128, 128, 0, s>>>(B, src, scale, dst);
   return cudaGetLastError();
 }
 cudaError_t launch_pad_scalar(int B, int Bp, const float* src, float* dst, cudaStream_t s) {

@@ -6,6 +6,8 @@
 
 cudaError_t launch_prep_weights(const DevTopo& T, const float* W, float* Wt, float* Wn, float* bias, cudaStream_t s);
 cudaError_t launch_prep_weights_tc(const DevTopo& T, const float* W, __nv_bfloat16* Wc, cudaStream_t s);
+cudaError_t launch_ws_prep(const float* W, __nv_bfloat16* tc, float* bias, cudaStream_t s);
+cudaError_t launch_scale_out(int B, const float* src, float scale, float* dst, cudaStream_t s);
 cudaError_t launch_state_in(int B, int Bp, int nf, const float* src, float* dst, cudaStream_t s);
 cudaError_t launch_state_out(int B, int Bp, int nf, const float* src, float* dst, cudaStream_t s);
 cudaError_t launch_param_out(int B, int Bp, int o, int n, const float* src, float* dst, cudaStream_t s);

@@ -113,6 +113,23 @@ struct CtrlTC {
   static constexpr int SIZE = W1T + 24 * H1;
 };
 
+// The learned warm-start network 16-64-64-3: bfloat16 tensor-core layouts (as CtrlTC) and the
+// fp32 bias array; the flat fp32 parameter vector is W1[64][16], b1, W2[64][64], b2, W3[3][64], b3.
+struct WsTC {
+  static constexpr int K0 = 16, H1 = 64, H2 = 64, NO = 3;
+  static constexpr int W1 = 0;                   // [H1][16]
+  static constexpr int W2 = W1 + H1 * 16;        // [H2][H1]
+  static constexpr int W3 = W2 + H2 * H1;        // [8][H2]
+  static constexpr int W3T = W3 + 8 * H2;        // [H2][16]
+  static constexpr int W2T = W3T + H2 * 16;      // [H1][H2]
+  static constexpr int W1T = W2T + H1 * H2;      // [16][H1]
+  static constexpr int SIZE = W1T + 16 * H1;
+  static constexpr int B1 = 0, B2 = 64, B3 = 128, BSIZE = 136;
+  // flat parameter offsets
+  static constexpr int F_W1 = 0, F_B1 = F_W1 + H1 * K0, F_W2 = F_B1 + H1, F_B2 = F_W2 + H2 * H1, F_W3 = F_B2 + H2,
+                       F_B3 = F_W3 + NO * H2, PARAMS = F_B3 + NO;
+};
+
 // Three dense layers K0 -> H1 -> H2 -> NO (ReLU hidden, linear output) for the 32 rows of a
 // warp. in(f, row): the K0 inputs (bfloat16-exact fp32); weights [Np][Kp] bf16 with fp32 biases;
 // out(f, row, v) receives the NO outputs; hid(layer, f, row, v) the hidden activations.

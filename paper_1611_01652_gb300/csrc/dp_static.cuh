@@ -156,7 +156,7 @@ __device__ void pgs_solve_static(const DevTopo& T, const LaneT<RV>& L, const SL&
     im[b] = S[T.sm_invm + b];
   }
 #pragma unroll
-  for (int s = 0; s < NS; ++s) lam[s] = 0.f;
+  for (int s = 0; s < NS; ++s) lam[s] = T.ws ? S[T.sm_lam + s] : 0.f;
   const float gamma = T.gamma;
   for (int it = 0; it < T.iters; ++it) {
     static_for<NS>([&](auto OI) {
@@ -299,7 +299,7 @@ __device__ __noinline__ void pgs_reverse_static(const DevTopo& T, const LaneT<GS
       const float3 angB = b >= 0 ? R.v3(RF_ANGB) : f3(0.f, 0.f, 0.f);
       const int o = (it * NS + s) * 32;
       const float la = lc[s];
-      const float lb = it > 0 ? __ldg(tlam + o - NS * 32) : 0.f;
+      const float lb = it > 0 ? __ldg(tlam + o - NS * 32) : (T.ws ? __ldg(tp.lam0 + s * 32) : 0.f);
       const int br = __ldg(tbr + o);
       float bnd = 0.f, lnrm = 0.f;
       if constexpr (kind == RK_GT || kind == RK_PT) {

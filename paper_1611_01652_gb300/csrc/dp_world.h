@@ -19,6 +19,15 @@ struct dp_world {
   float* Wmaster = nullptr;
   float *Wt = nullptr, *Wn = nullptr, *Wb = nullptr;
   __nv_bfloat16* Wtc = nullptr;  // tensor-core layouts of the controller (DevTopo.mlp_tc)
+  bool ws_capable = false;       // created with room for the warm start (tape lam0 record)
+  float* ws_master = nullptr;    // warm-start parameters [DP_WS_PARAMS]
+  __nv_bfloat16* ws_tc = nullptr;
+  float* ws_b = nullptr;
+  unsigned long long* harvest_count = nullptr;
+  float* resid = nullptr;        // per-instance residual sums [Bp]
+  float ws_alpha = 0.7f;
+  bool resid_on = false;
+  int resid_steps = 0;
   float* stage = nullptr;      // device staging buffer for user-layout inputs/outputs
   size_t stage_floats = 0;
   float* dW_stage = nullptr;   // [n_params]

@@ -1,0 +1,290 @@
+"""GPU parity of the learned warm start (through the C ABI) against the FP64 oracle: the network's
+inference and training gradient, the harvested rows, warm-started steps, their residual and
+reverse mode; then what a trained network gains over the cold start at equal sweeps."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_1611_01652_gb300 import binding as Bd  # noqa: E402
+from paper_1611_01652_gb300 import warmstart as WS  # noqa: E402
+from paper_1611_01652_gb300 import workloads as WL  # noqa: E402
+from paper_1611_01652_gb300.binding import World  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TIE = 1e-5
+
+
+def exact_network(rng):
+    """Parameters and inputs on coarse dyadic grids: the pre-activations of both hidden layers are
+    exact in fp32 (at most 22 significant bits), so both sides take the same bfloat16 rounding
+    decisions; only the linear output layer rounds. Layer 1: weights k/32 (|k| <= 32), biases
+    k/256; layer 2: weights k/32 (|k| <= 4), biases k/8192; layer 3: weights k/32, biases k/64."""
+    I, H, Oo = O.WS_IN, O.WS_H, O.WS_OUT
+    W1 = rng.integers(-32, 33, (H, I)) / 32.0
+    b1 = rng.integers(-64, 65, H) / 256.0
+    W2 = rng.integers(-4, 5, (H, H)) / 32.0
+    b2 = rng.integers(-64, 65, H) / 8192.0
+    W3 = rng.integers(-32, 33, (Oo, H)) / 32.0
+    b3 = rng.integers(-64, 65, Oo) / 64.0
+    return np.concatenate([W1.ravel(), b1, W2.ravel(), b2, W3.ravel(), b3])
+
+
+def exact_features(rng, n):
+    return rng.integers(-16, 17, (n, O.WS_IN)) / 8.0
+
+
+def test_ws_inference_matches_oracle_on_exact_grid():
+    rng = np.random.default_rng(11)
+    W = exact_network(rng)
+    X = exact_features(rng, 1000)  # 31 full warps and a ragged tail
+    y_o = O.ws_forward(W, X)
+    Wd = torch.tensor(W, dtype=torch.float32, device="cuda")
+    Xd = torch.tensor(X, dtype=torch.float32, device="cuda")
+    y = torch.zeros(X.shape[0], 3, device="cuda")
+    work = Bd.ws_workspace(X.shape[0])
+    Bd.ws_forward(Wd, Xd, y, work)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(y.cpu().double().numpy(), y_o, rtol=1e-6, atol=1e-6)
+
+
+@pytest.mark.parametrize("n", [1, 37, 4096])
+def test_ws_training_gradient_matches_oracle(n):
+    rng = np.random.default_rng(12 + n)
+    W = exact_network(rng)
+    X = exact_features(rng, n)
+    Y = rng.normal(0.0, 0.5, (n, 3)).astype(np.float32).astype(np.float64)
+    rows = np.concatenate([X, Y], axis=1)
+    L_o, g_o = O.ws_loss_grad(W, rows)
+    Wd = torch.tensor(W, dtype=torch.float32, device="cuda")
+    R = torch.tensor(rows, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    dW = torch.zeros(O.WS_PARAMS, device="cuda")
+    Bd.ws_loss_grad(Wd, R, loss, dW, Bd.ws_workspace(n))
+    torch.cuda.synchronize()
+    assert abs(loss.item() - L_o) <= 1e-5 * max(1.0, abs(L_o))
+    g = dW.cpu().double().numpy()
+    assert np.linalg.norm(g - g_o) <= 1e-4 * np.linalg.norm(g_o), np.linalg.norm(g - g_o) / np.linalg.norm(g_o)
+
+
+def test_adam_step_matches_definition():
+    rng = np.random.default_rng(13)
+    W = rng.normal(0, 1, 1000).astype(np.float32)
+    g = rng.normal(0, 1, 1000).astype(np.float32)
+    Wd, gd = torch.tensor(W, device="cuda"), torch.tensor(g, device="cuda")
+    m, v = torch.zeros_like(Wd), torch.zeros_like(Wd)
+    Bd.ws_adam(Wd, gd, m, v, 1, 0.01)
+    Bd.ws_adam(Wd, gd, m, v, 2, 0.01)
+    Wr, mr, vr = W.astype(np.float64), np.zeros(1000), np.zeros(1000)
+    for t in (1, 2):
+        mr = 0.9 * mr + 0.1 * g
+        vr = 0.999 * vr + 0.001 * g.astype(np.float64) ** 2
+        Wr = Wr - 0.01 * (mr / (1 - 0.9 ** t)) / (np.sqrt(vr / (1 - 0.999 ** t)) + 1e-8)
+    np.testing.assert_allclose(Wd.cpu().numpy(), Wr, rtol=1e-5, atol=1e-6)
+
+
+# ----------------------------------------------------------------------------- in the step
+def oracle_states(m, horizon):
+    return [O.rollout(m, i, horizon=horizon)[0] for i in range(m.B)]
+
+
+def nearest_rows(g, o):
+    """For every GPU row, the oracle row closest in feature space (features identify a contact:
+    instance-specific offsets and heights)."""
+    d = ((g[:, None, :16] - o[None, :, :16]) ** 2).sum(-1)
+    return d.argmin(1)
+
+
+def test_harvested_rows_match_oracle():
+    """Harvest from oracle states: one step per instance from x_t (as the initial state of a
+    one-step world); every active row group gives a row whose features and post-solve impulses
+    match the oracle's (fp32 controller)."""
+    m = WL.quadruped(B=40, horizon=60)
+    m.ctrl_fp32 = 1
+    st = oracle_states(m, 60)
+    groups = O.ws_groups(m)
+    for t in (7, 31, 59):
+        x = np.stack([s[t] for s in st])
+        w = World(m, horizon=1, warmstart=True)
+        w.set_initial_state(torch.tensor(x, dtype=torch.float32, device="cuda"))
+        Wt = torch.tensor(m.W, device="cuda")
+        rows = WS.harvest(w, Wt, 40 * len(groups), noise_sigma=0.0).cpu().double().numpy()
+        orows, ogaps = [], []
+        for i in range(m.B):
+            d = O.step_log(m, i, x[i], t=0)
+            for g, (typ, sl) in enumerate(groups):
+                if not d["active"][sl[0]]:
+                    continue
+                lam = [d["lam"][k] if k >= 0 else 0.0 for k in sl]
+                orows.append(np.concatenate([d["feats"][g], lam]))
+                ogaps.append(d["gap"][sl[0]] if typ in (O.WS_GROUND, O.WS_PAIR) else np.inf)
+        orows = np.array(orows)
+        near_tie = (np.array(ogaps) < TIE).sum()
+        assert abs(len(rows) - len(orows)) <= near_tie, (t, len(rows), len(orows))
+        k = nearest_rows(rows, orows)
+        scale = np.maximum(1.0, np.abs(orows[k]))
+        err_f = np.abs(rows[:, :16] - orows[k, :16]) / scale[:, :16]
+        # the harvested output is (impulse after the solve - alpha * previous impulse) / m_eff with
+        # no previous impulse here; compare in impulse units (m_eff = features 6-8)
+        err_l = np.abs(rows[:, 16:] * rows[:, 6:9] - orows[k, 16:]) / scale[:, 16:]
+        assert err_f.max() <= 1e-4, (t, err_f.max())
+        assert err_l.max() <= 1e-3, (t, err_l.max())
+        assert len(np.unique(k)) == len(k)  # one-to-one
+
+
+def small_network(seed=3):
+    W = WS.init_params(seed, out_scale=0.5)
+    W[-3] = 0.3  # normal impulse bias near the weight share
+    return W
+
+
+def constant_network(b3=(0.05, 0.01, -0.02)):
+    """A network whose output is b3 for every input (zero weights): no rounding decision depends
+    on the features, so both sides warm-start every group with the same projected impulses."""
+    W = WS.init_params(0)
+    W[-3 - 3 * 64:-3] = 0.0
+    W[-3:] = b3
+    return W
+
+
+def oracle_ws_trajectory(m, i, horizon):
+    """Oracle rollout of a warm-started instance one step at a time: states, and the impulses each
+    step ended with (the next step's lambda_prev)."""
+    x = m.state0[i].astype(np.float64)
+    lp = np.zeros(len(O.schedule(m)["kind"]))
+    xs, lps = [x], [lp]
+    for t in range(horizon):
+        d = O.step_log(m, i, x, t=t, lam_prev=lp)
+        x, lp = d["xn"], d["lam"]
+        xs.append(x)
+        lps.append(lp)
+    return xs, lps
+
+
+@pytest.mark.parametrize("net", ["trained-like", "constant"])
+def test_warm_started_steps_match_oracle(net):
+    """Teacher-forced warm-started steps from the oracle's state and previous impulses: next
+    state within 1e-4, impulses after the solve within 1e-3 and the residual of the solve within
+    1e-4 absolute. With a feature-dependent network, steps whose bfloat16 roundings came within
+    1e-6 (relative) of a tie are skipped: the two sides accumulate in different precisions, so
+    such roundings may go either way."""
+    m = WL.quadruped(B=16, horizon=80)
+    m.ctrl_fp32 = 1
+    Wws = small_network() if net == "trained-like" else constant_network()
+    m.warmstart, m.ws_W, m.ws_alpha = 1, Wws.astype(np.float64), 0.7
+    gate = 1e-6 if net == "trained-like" else -1.0
+    trajs = [oracle_ws_trajectory(m, i, 80) for i in range(m.B)]
+    w = World(m, horizon=80, warmstart=True)
+    w.set_warmstart(torch.tensor(Wws, device="cuda"), 0.7)
+    W = torch.tensor(m.W, device="cuda")
+    checked = 0
+    for t in range(3, 80, 11):
+        x = np.stack([tr[0][t] for tr in trajs]).astype(np.float32)
+        lp = np.stack([tr[1][t] for tr in trajs]).astype(np.float32)
+        w.set_state(torch.tensor(x, device="cuda"), t)
+        w.set_impulses(torch.tensor(lp, device="cuda"))
+        w.set_residual(True)
+        act = torch.zeros(1, m.B, w.n_slots, dtype=torch.uint8, device="cuda")
+        w.step(1, W, act)
+        out = torch.zeros(m.B, m.nb, 18, device="cuda")
+        res = torch.zeros(m.B, device="cuda")
+        lam = torch.zeros(m.B, w.n_slots, device="cuda")
+        w.get_state(out)
+        w.get_residual(res)
+        w.get_impulses(lam)
+        w.sync()
+        out, res, act, lam = (out.cpu().double().numpy(), res.cpu().double().numpy(), act.cpu().numpy()[0],
+                              lam.cpu().double().numpy())
+        for i in range(m.B):
+            d = O.step_log(m, i, x[i].astype(np.float64), t=t, lam_prev=lp[i].astype(np.float64))
+            ok = d["gap"] >= TIE
+            assert np.array_equal(act[i][ok], d["active"][ok]), (t, i)
+            if ok.all() and d["margin"] > gate:
+                err = np.abs(out[i] - d["xn"]) / np.maximum(1.0, np.abs(d["xn"]))
+                assert err.max() <= 1e-4, (t, i, err.max())
+                assert np.abs(lam[i] - d["lam"]).max() <= 1e-3, (t, i, np.abs(lam[i] - d["lam"]).max())
+                assert abs(res[i] - d["resid"]) <= 1e-4, (t, i, res[i], d["resid"])
+                checked += 1
+    assert checked >= (0.1 if net == "trained-like" else 0.9) * m.B * len(range(3, 80, 11))
+
+
+@pytest.mark.parametrize("ckpt", [None, 8])
+def test_warm_started_gradients_match_oracle(ckpt):
+    """Reverse mode through warm-started rollouts (start alpha lambda_prev + constant network
+    output, treated as constant) against the oracle's gradient of the same function; 30 steps,
+    fp32 controller; the whole tape recorded by the rollout, or 8-step segments recomputed from
+    checkpoints of the state and of the previous impulses."""
+    m = WL.quadruped(B=4, horizon=30)
+    m.ctrl_fp32 = 1
+    Wws = constant_network()
+    m.warmstart, m.ws_W, m.ws_alpha = 1, Wws.astype(np.float64), 0.7
+    w = World(m, horizon=30, warmstart=True, ckpt_every=ckpt)
+    w.set_warmstart(torch.tensor(Wws, device="cuda"), 0.7)
+    loss = torch.zeros(m.B, device="cuda")
+    W = torch.tensor(m.W, device="cuda")
+    w.rollout(W, loss)
+    dW = torch.zeros(w.n_params, device="cuda")
+    ds = torch.zeros(m.B, m.nb, 18, device="cuda")
+    dp = {k: torch.zeros(getattr(m, k).shape, device="cuda") for k in ("mass", "inertia", "sph_off", "sph_rad")}
+    w.backward(torch.ones(m.B, device="cuda"), dW, ds, dp)
+    w.sync()
+    Wsum = None
+    for i in range(m.B):
+        L, go = O.rollout_grad(m, i, horizon=30)
+        assert abs(loss[i].item() - L) <= 1e-4 * max(1.0, abs(L))
+        for k, g in (("state0", ds[i]), ("mass", dp["mass"][i]), ("inertia", dp["inertia"][i]),
+                     ("sph_off", dp["sph_off"][i]), ("sph_rad", dp["sph_rad"][i])):
+            g = g.cpu().double().numpy()
+            e = np.linalg.norm(g - go[k]) / max(np.linalg.norm(go[k]), 1e-12)
+            assert e <= 1e-3, (i, k, e)
+        Wsum = go["W"] if Wsum is None else Wsum + go["W"]
+    g = dW.cpu().double().numpy()
+    assert np.linalg.norm(g - Wsum) <= 1e-3 * np.linalg.norm(Wsum)
+
+
+def test_residual_of_cold_start_matches_oracle():
+    m = WL.quadruped(B=8, horizon=40)
+    m.ctrl_fp32 = 1
+    w = World(m, horizon=40)
+    w.set_residual(True)
+    loss = torch.zeros(m.B, device="cuda")
+    w.rollout(torch.tensor(m.W, device="cuda"), loss)
+    res = torch.zeros(m.B, device="cuda")
+    w.get_residual(res)
+    w.sync()
+    res = res.cpu().double().numpy()
+    for i in range(m.B):
+        _, _, r = O.rollout_resid(m, i, 40)
+        assert abs(res[i] - r.mean()) <= 2e-4 * max(1.0, r.mean()) + 1e-5, (i, res[i], r.mean())
+
+
+# ----------------------------------------------------------------------------- what it gains
+def test_learned_warm_start_training_and_acceptance_gate():
+    """Harvest from perturbed rollouts solved with many sweeps (near-converged impulses) from the
+    damped previous-impulse start, train the network on the GPU (it must predict the harvested
+    corrections better than the zero network), then run the acceptance gate on held-out robots
+    with three candidates: the trained network, the zero network (damped previous-impulse start)
+    and a network whose output is far too large. The gate must reject the last, and accept a warm
+    start that reaches the plain solver's residual with fewer sweeps than its 20."""
+    torch.manual_seed(0)
+    zero = torch.zeros(Bd.WS_PARAMS, device="cuda")
+    mh = WL.quadruped(B=512, horizon=200, seed=2002)
+    wh = World(mh, horizon=200, iters=60, warmstart=True)
+    wh.set_warmstart(zero, 0.7)
+    rows = WS.harvest(wh, torch.tensor(mh.W, device="cuda"), 512 * 200 * 24, noise_sigma=0.1, seed=5)
+    assert rows.shape[0] > 512 * 200 * 16
+    n = rows.shape[0]
+    perm = torch.randperm(n, device="cuda")
+    tr, va = rows[perm[: int(0.9 * n)]], rows[perm[int(0.9 * n):]]
+    e0 = WS.evaluate(zero, va)
+    Wws, hist = WS.train(tr, steps=800, batch=32768, lr=3e-3, seed=0, val_rows=va, log_every=800)
+    assert hist[-1][2] < e0, (e0, hist)
+    bad = torch.tensor(constant_network((50.0, 50.0, 50.0)), device="cuda")
+    m = WL.quadruped(B=128, horizon=200, seed=3003)
+    rep = WS.accept(m, [("learned", Wws, 0.7), ("damped", zero, 0.7), ("bad", bad, 0.7)], plain_iters=20,
+                    sweep_grid=(5, 7, 10, 14), horizon=200)
+    print("acceptance gate", rep)
+    assert not any(c["accepted"] for c in rep["candidates"] if c["name"] == "bad"), rep
+    assert rep["accepted"] is not None and rep["accepted"][1] < 20, rep
