@@ -47,6 +47,9 @@ def parse():
     p.add_argument("--iters", type=int, default=20, help="sweeps of the plain solver")
     p.add_argument("--alpha", type=float, default=0.7, help="weight of the previous impulses in the warm start")
     p.add_argument("--ws-train-steps", type=int, default=800)
+    p.add_argument("--fixed-warmstart", type=int, default=0, metavar="N",
+                   help="skip the preparation and the gate: time the damped previous-impulse start at N sweeps "
+                        "(for profiling the timed kernels alone)")
     return p.parse_args()
 
 
@@ -270,7 +273,15 @@ def main():
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     B, T = args.batch, args.horizon
-    rep, nets = (None, {}) if args.no_warmstart else prepare_warmstart(args)
+    if args.no_warmstart:
+        rep, nets = None, {}
+    elif args.fixed_warmstart:
+        from paper_1611_01652_gb300.binding import WS_PARAMS
+
+        rep = {"accepted": ("damped", args.fixed_warmstart, args.alpha), "fixed": True}
+        nets = {"damped": torch.zeros(WS_PARAMS, device="cuda")}
+    else:
+        rep, nets = prepare_warmstart(args)
     m = WL.quadruped(B=B, horizon=T, seed=1002 + 17 * rank)
     stream = torch.cuda.current_stream()
     W = torch.tensor(m.W, device="cuda")
@@ -354,7 +365,7 @@ def main():
     # per step: two weight preparations + forward; pad + backward; per dense layer gemm, sum, rowsum, sum
     launches_per_step = 3 + 2 + 4 * n_dense
     gate = None
-    if rep:
+    if rep and not rep.get("fixed"):
         gate = {k: rep[k] for k in ("plain_iters", "ref_iters", "plain_resid", "plain_state_err", "plain_grad_err",
                                     "harvest_rows", "val_mse_zero_network", "val_mse_trained", "prepare_s")}
         gate["candidates"] = rep["candidates"]
