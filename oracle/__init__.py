@@ -53,7 +53,8 @@ class Topo(C.Structure):
                 ("gravity", C.c_double * 3), ("dt", C.c_double), ("ground_z", C.c_double),
                 ("beta", C.c_double), ("gamma", C.c_double), ("slop", C.c_double), ("iters", C.c_int32),
                 ("loss_kind", C.c_int32), ("loss_mode", C.c_int32), ("loss_body", C.c_int32),
-                ("exact_mlp", C.c_int32), ("warmstart", C.c_int32), ("ws_W", PD), ("ws_alpha", C.c_double)]
+                ("exact_mlp", C.c_int32), ("warmstart", C.c_int32), ("ws_W", PD), ("ws_alpha", C.c_double),
+                ("grad_decay", C.c_double)]
 
 WS_IN, WS_H, WS_OUT = 16, 64, 3
 WS_PARAMS = WS_IN * WS_H + WS_H + WS_H * WS_H + WS_H + WS_H * WS_OUT + WS_OUT
@@ -124,6 +125,7 @@ def topo(m, keep, iters=None):
     t.warmstart = int(bool(getattr(m, "warmstart", 0)) and ws is not None)
     t.ws_W = keep.f64(ws) if t.warmstart else None
     t.ws_alpha = float(getattr(m, "ws_alpha", 0.7))
+    t.grad_decay = float(getattr(m, "grad_decay", 1.0))
     return t
 
 

@@ -245,6 +245,7 @@ typedef struct {
   int32_t warmstart;           // 1: the solve starts from the learned warm start (ws_W, ws_alpha)
   const double* ws_W;          // warm-start network parameters [ORC_WS_PARAMS]
   double ws_alpha;             // weight of the previous step's impulses in the warm start
+  double grad_decay;           // section 3.2: adjoint passed from step t+1 back to step t times alpha
 } orc_topo;
 
 // Learned warm start: a 16-64-64-3 network per contact (W1, b1, W2, b2, W3, b3; W[out][in]).
@@ -1166,8 +1167,11 @@ int orc_rollout_grad(const orc_topo* T, const orc_inst* I, const double* W, int3
              T->warmstart ? lamps.data() + (size_t)t * nsl : nullptr);
     AD l0 = (t == 0) ? loss_initial(*T, P, x) : AD(0.0);
     tape.adj.assign(tape.pa.size(), 0.0);
+    // the gradient reaching step t from later steps is decreased by alpha (section 3.2); the
+    // loss term of x_{t+1} itself enters undecayed
+    const double decay = T->grad_decay > 0.0 ? T->grad_decay : 1.0;
     for (int k = 0; k < 18 * nb; ++k)
-      if (xn[k].id >= 0) tape.adj[xn[k].id] += xbar[k];
+      if (xn[k].id >= 0) tape.adj[xn[k].id] += decay * xbar[k];
     if (lt.id >= 0) tape.adj[lt.id] += 1.0;
     if (l0.id >= 0) tape.adj[l0.id] += 1.0;
     tape.backward();

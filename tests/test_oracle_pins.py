@@ -434,3 +434,19 @@ def test_gradient_matches_central_differences_quadruped_controller():
         assert abs(fd - g["W"][k]) <= 1e-4 * (abs(fd) + 1e-4), (k, fd, g["W"][k])
         checked += 1
     assert checked >= 10
+
+
+def test_gradient_decay_closed_form_in_flight():
+    """Section 3.2's decay of the gradient by alpha per time step: for a ball in free flight the
+    loss of the final position has dL/dv0 = T h alpha^(T-1) dL/dp_T (each step passes the
+    adjoint of the later steps back scaled by alpha; T = 1 needs no decay)."""
+    m = WL.ball(B=1, horizon=30)
+    m.state0[0, 0, 2] = 5.0  # high enough not to land within 30 steps
+    st, _, act, _ = O.rollout(m, 0, log=True)
+    assert not act.any()
+    g_pT = 2.0 * (st[-1, 0, :3] - m.loss_target[0])
+    for alpha in (1.0, 0.9, 0.5):
+        m.grad_decay = alpha
+        _, g = O.rollout_grad(m, 0)
+        np.testing.assert_allclose(g["state0"][0, 12:15], 30 * m.dt * alpha ** 29 * g_pT, rtol=1e-10)
+        np.testing.assert_allclose(g["state0"][0, 0:3], alpha ** 29 * g_pT, rtol=1e-10)
