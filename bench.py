@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--iters", type=int, default=20, help="sweeps of the plain solver")
     p.add_argument("--alpha", type=float, default=0.7, help="weight of the previous impulses in the warm start")
     p.add_argument("--ws-train-steps", type=int, default=800)
+    p.add_argument("--no-arms", action="store_true", help="skip the uneven arm batch")
     p.add_argument("--fixed-warmstart", type=int, default=0, metavar="N",
                    help="skip the preparation and the gate: time the damped previous-impulse start at N sweeps "
                         "(for profiling the timed kernels alone)")
@@ -239,6 +240,42 @@ def time_arm(world, W, loss, dloss, dW, args, stream, dist):
     return total_ms, fwd_ms, bwd_ms, ck
 
 
+def time_uneven_arms(args):
+    """Uneven batch of 8192 robot arms (3-7 links, horizons 200-2000 steps of 5 ms, controller
+    32-256-256-7): bins per link count, autotuned launch configurations, one CUDA graph replayed
+    per forward + adjoint pass. Metric: instance-steps actually simulated per second."""
+    import torch
+
+    from paper_1611_01652_gb300 import workloads as WL
+    from paper_1611_01652_gb300.batching import UnevenBatch
+
+    t0 = time.perf_counter()
+    bins = WL.arms(B=8192)
+    W = torch.tensor(bins[min(bins)].W, device="cuda")
+    ub = UnevenBatch(bins, W, tune=True, tune_horizon=64)
+    ub.capture()
+    prep = time.perf_counter() - t0
+    for _ in range(max(1, args.warmup - 1)):
+        ub.run()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        ub.run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    out = {"metric": "inst-steps/s fwd+adjoint, uneven arms B=8192", "value": ub.instance_steps / (ms / 1e3),
+           "unit": "inst-steps/s", "ms_per_step": ms, "instance_steps_per_step": ub.instance_steps,
+           "bins": {str(k): {"B": ub.models[k].B, "max_horizon": ub.models[k].horizon, "config": ub.config[k]}
+                    for k in ub.keys},
+           "graph": True, "prepare_s": prep, "finite": bool(torch.isfinite(ub.dW).all().item())}
+    del ub
+    torch.cuda.empty_cache()
+    return out
+
+
 def mean_residual(world, W, B):
     """Mean per-step solve residual of one untimed rollout of the world."""
     import torch
@@ -339,10 +376,15 @@ def main():
         e2e = {"value": B * T * world_size / (ems / 1e3), "unit": "inst-steps/s",
                "h2d_bytes_per_step": 4 * (world.n_params + B), "d2h_bytes_per_step": 4 * (B + world.n_params)}
 
+    del world, head
+    torch.cuda.empty_cache()
+    arms = None if args.no_arms else time_uneven_arms(args)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
+    head = dict(ws if ws else plain, clocks=w_ck if ws else p_ck, name=("warm start (%s, %d sweeps)" % (
+        ws["accepted"], ws["iters"])) if ws else "plain")
     flops = json.load(open(FLOPS))
     it = head["iters"]
     fl = flops["quadruped_b4096_t1000" if it == 20 else "quadruped_b4096_t1000_iters%d" % it]
@@ -378,7 +420,7 @@ def main():
                                "gradient w.r.t. all controller weights; %s" % (B, T, head["name"]),
                    "batch": B, "horizon": T, "iters": head["iters"], "ckpt_every": head["ckpt_every"],
                    "l2": "working set (solver tape + controller activations) >> 129 MB L2; no flush needed"},
-        "plain": plain, "warmstart": ws, "gate": gate,
+        "plain": plain, "warmstart": ws, "gate": gate, "uneven_arms": arms,
         "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": head["clocks"],
         "plain_clocks": p_ck if ws else None,
         "gpu_launches": launches_per_step * args.steps, "fwd_ms": head["fwd_ms"], "bwd_ms": head["bwd_ms"],

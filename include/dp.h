@@ -116,6 +116,17 @@ typedef struct {
   int32_t ctrl_fp32;              /* 0: bfloat16 storage points (default); 1: the controller keeps its
                                      input, weights and hidden activations in fp32 (no rounding) */
   int32_t warmstart;              /* 1: reserve room for the learned warm start (dp_set_warmstart) */
+  const int32_t* horizons;        /* [B] per-instance horizons in [1, horizon], or NULL (all = horizon).
+                                     In dp_rollout an instance's loss of Eq. L ends at its own
+                                     horizon; a warp of 32 instances steps to the largest horizon
+                                     among them (instances past their horizon keep stepping with a
+                                     zero loss weight and get zero adjoints); the trajectory rows
+                                     beyond a warp's largest horizon are not written. */
+  int32_t rows_global;            /* 1: keep the constraint rows in global memory even when they fit
+                                     in shared memory (a launch-configuration choice) */
+  int32_t dw_splits;              /* split count of the controller-gradient reduction (0 = automatic) */
+  float grad_decay;               /* alpha of section 3.2: the state adjoint passed from step t+1 back to
+                                     step t is multiplied by alpha (0 or 1: no decay) */
 } dp_batch_desc;
 
 typedef struct dp_world dp_world; /* opaque; owned by the library */

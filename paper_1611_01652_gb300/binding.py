@@ -33,7 +33,8 @@ class BatchDesc(C.Structure):
                 ("gravity", C.c_float * 3), ("dt", C.c_float), ("ground_z", C.c_float), ("beta", C.c_float),
                 ("gamma", C.c_float), ("slop", C.c_float), ("iters", C.c_int32), ("horizon", C.c_int32),
                 ("ckpt_every", C.c_int32), ("loss_kind", C.c_int32), ("loss_mode", C.c_int32),
-                ("loss_body", C.c_int32), ("ctrl_fp32", C.c_int32), ("warmstart", C.c_int32)]
+                ("loss_body", C.c_int32), ("ctrl_fp32", C.c_int32), ("warmstart", C.c_int32),
+                ("horizons", PI), ("rows_global", C.c_int32), ("dw_splits", C.c_int32), ("grad_decay", C.c_float)]
 
 WS_PARAMS = 5443
 WS_ROW = 19
@@ -127,7 +128,8 @@ class World:
     ``stream`` (a torch.cuda.Stream, default: the current stream at creation).
     """
 
-    def __init__(self, model, stream=None, ckpt_every=None, horizon=None, iters=None, warmstart=False):
+    def __init__(self, model, stream=None, ckpt_every=None, horizon=None, iters=None, warmstart=False,
+                 rows_global=False, dw_splits=0):
         import torch
 
         lib = load()
@@ -172,6 +174,11 @@ class World:
         d.loss_kind, d.loss_mode, d.loss_body = model.loss_kind, model.loss_mode, model.loss_body
         d.ctrl_fp32 = int(getattr(model, "ctrl_fp32", 0))
         d.warmstart = int(bool(warmstart))
+        hz = getattr(model, "horizons", None)
+        d.horizons = i32(np.minimum(hz, d.horizon)) if hz is not None else None
+        d.rows_global = int(bool(rows_global))
+        d.dw_splits = int(dw_splits)
+        d.grad_decay = float(getattr(model, "grad_decay", 1.0))
         self.horizon = d.horizon
         self.n_motors = int(sum(1 for f in np.asarray(model.joint_flags).reshape(-1) if f & 2))
         h = C.c_void_p()

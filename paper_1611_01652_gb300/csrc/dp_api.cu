@@ -98,6 +98,12 @@ dp_status validate(const dp_batch_desc* d) {
   if (d->n_spheres < 0 || d->n_spheres > DP_MAX_SPHERES) return fail(DP_EINVAL, "n_spheres out of range [0, 32]");
   if (d->n_pairs < 0 || d->n_pairs > DP_MAX_PAIRS) return fail(DP_EINVAL, "n_pairs out of range [0, 32]");
   if (d->horizon < 1) return fail(DP_EINVAL, "horizon must be >= 1");
+  if (d->horizons)
+    for (int i = 0; i < d->n_instances; ++i)
+      if (d->horizons[i] < 1 || d->horizons[i] > d->horizon)
+        return fail(DP_EINVAL, "horizons[" + std::to_string(i) + "] out of range [1, horizon]");
+  if (d->dw_splits < 0) return fail(DP_EINVAL, "dw_splits must be >= 0");
+  if (!(d->grad_decay >= 0.f && d->grad_decay <= 1.f)) return fail(DP_EINVAL, "grad_decay must lie in [0, 1]");
   if (d->iters < 1) return fail(DP_EINVAL, "iters must be >= 1");
   if (!(d->dt > 0.f)) return fail(DP_EINVAL, "dt must be > 0");
   if (d->ckpt_every < 0) return fail(DP_EINVAL, "ckpt_every must be >= 0");
@@ -157,7 +163,7 @@ int feature_count(const dp_batch_desc* d, int n_motors) {
 
 // Shared-memory plan (units of 32 floats per warp). Forward kernel: controller activations on
 // chip; backward kernel: row-adjoint accumulators on chip, activations in the global dump.
-void plan_smem(DevTopo& T, bool backward, int smem_floats_max) {
+void plan_smem(DevTopo& T, bool backward, int smem_floats_max, bool rows_on_chip = true) {
   int o = 0;
   auto take = [&](int n) { int r = o; o += std::max(n, 1); return r; };
   T.sm_x = take(18 * T.nb);
@@ -187,7 +193,7 @@ void plan_smem(DevTopo& T, bool backward, int smem_floats_max) {
     else
       acts = 1;
     const int rows = T.nslots * RF_N;
-    if ((region + std::max(acts, rows)) * 32 <= smem_floats_max) {
+    if (rows_on_chip && (region + std::max(acts, rows)) * 32 <= smem_floats_max) {
       T.sm_rows = region;
       o = region + std::max(acts, rows);
     } else {
@@ -379,6 +385,7 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
   T.n_params = (int)np_;
   T.ws = 0;
   T.ws_alpha = 0.7f;
+  T.grad_decay = d->grad_decay > 0.f ? d->grad_decay : 1.f;
   T.mlp_tc = T.n_layers == 3 && !T.skip && T.ctrl_round && T.widths[0] == CtrlTC::K0 && T.widths[1] == CtrlTC::H1 &&
              T.widths[2] == CtrlTC::H2 && T.widths[3] == CtrlTC::NO && !getenv("DP_FORCE_SIMT_CONTROLLER");
   T.topo_id = match_compiled_topology(T, T.nb, T.nj, T.ns, T.np, d->joint_type, d->joint_body, d->joint_flags,
@@ -391,7 +398,7 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
   int dev = 0, smem_max = 0;
   CU(cudaGetDevice(&dev));
   CU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  plan_smem(w->Tf, false, smem_max / (int)sizeof(float));
+  plan_smem(w->Tf, false, smem_max / (int)sizeof(float), d->rows_global == 0);
   plan_smem(w->Tb, true, smem_max / (int)sizeof(float));
   size_t need = (size_t)std::max(w->Tf.sm_total, w->Tb.sm_total) * 32 * sizeof(float);
   if (need > (size_t)smem_max) {
@@ -481,11 +488,13 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
         dalloc(w, &w->Wt, (size_t)wtot) || dalloc(w, &w->Wn, (size_t)wtot) || dalloc(w, &w->Wb, (size_t)wtot) ||
         dalloc(w, &w->dW_stage, (size_t)np_))
       return cleanup(DP_ENOMEM);
+    // columns of steps a warp never reaches (uneven horizons) stay zero for the dW reduction
+    CU(cudaMemsetAsync(D.dump, 0, sizeof(float) * (size_t)T.dump_rows * T.horizon * Bp, w->stream));
     CU(cudaMemsetAsync(w->Wt, 0, sizeof(float) * wtot, w->stream));
     CU(cudaMemsetAsync(w->Wn, 0, sizeof(float) * wtot, w->stream));
     CU(cudaMemsetAsync(w->Wb, 0, sizeof(float) * wtot, w->stream));
     size_t N = (size_t)T.horizon * Bp;
-    w->splits = (int)std::min<size_t>(256, (N + 16383) / 16384);
+    w->splits = d->dw_splits > 0 ? std::min(d->dw_splits, 256) : (int)std::min<size_t>(256, (N + 16383) / 16384);
     size_t maxlayer = 0;
     for (int l = 0; l <= T.n_layers; ++l) maxlayer = std::max(maxlayer, (size_t)T.widths[l]);
     w->partial_floats = (size_t)w->splits * maxlayer * maxlayer;
@@ -517,8 +526,17 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
     if (dalloc(w, &w->ws_master, (size_t)WsTC::PARAMS) || dalloc(w, &w->ws_b, (size_t)WsTC::BSIZE))
       return cleanup(DP_ENOMEM);
   }
-  if (dalloc(w, &w->resid, Bz) || dalloc(w, &w->harvest_count, 1) || dalloc(w, &D.lam_prev, (size_t)T.nslots * Bz))
+  int* hz = nullptr;
+  if (dalloc(w, &w->resid, Bz) || dalloc(w, &w->harvest_count, 1) || dalloc(w, &D.lam_prev, (size_t)T.nslots * Bz) ||
+      dalloc(w, &hz, Bz))
     return cleanup(DP_ENOMEM);
+  {
+    std::vector<int> hh(Bp);
+    for (int i = 0; i < Bp; ++i) hh[i] = d->horizons ? d->horizons[i < B ? i : B - 1] : d->horizon;
+    CU(cudaMemcpyAsync(hz, hh.data(), sizeof(int) * Bp, cudaMemcpyHostToDevice, w->stream));
+    CU(cudaStreamSynchronize(w->stream));
+  }
+  D.hz = hz;
   CU(cudaMemsetAsync(w->resid, 0, sizeof(float) * Bz, w->stream));
   CU(cudaMemsetAsync(D.lam_prev, 0, sizeof(float) * (size_t)std::max(T.nslots, 1) * Bz, w->stream));
   D.ckpt_lam = nullptr;

@@ -47,6 +47,7 @@ struct DevTopo {
   int mlp_tc;   // 1: the controller is the 24-128-128-8 bfloat16 network, run on the tensor cores
   int ws;       // 1: the solve starts from the learned warm start (DevPtrs.ws_tc, ws_alpha)
   float ws_alpha;  // weight of the previous step's impulses in the warm start
+  float grad_decay;  // reverse mode: state adjoint x alpha per step (section 3.2); 1 = none
   int sm_ws;    // warm-start scratch per lane: features [16], outputs [3], harvest row ids [n_wsg]
   // warm-start groups of three rows (slot -1: none): joint linear rows, hinge angular rows with
   // the motor row, contact normal/t1/t2 rows; type WSG_*
@@ -97,6 +98,7 @@ struct DevPtrs {
   long long harvest_max;
   const float* u_noise;        // optional: controller-output perturbation [T][Bp][n_motors]
   float* resid;                // optional: per-instance sum of per-step solve residuals [Bp]
+  const int* hz;               // per-instance horizons [Bp]
   float* lam_prev;             // impulses the last step ended with [nslots][Bp] (kept across launches)
   float* ckpt_lam;             // optional: the same at every checkpoint [n_ckpt][nslots][Bp]
   float* state;          // current state [nb*18][Bp]

@@ -5,6 +5,8 @@
 #pragma once
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "dp_device.cuh"
 #include "dp_mma.cuh"
 
@@ -74,9 +76,18 @@ __device__ __forceinline__ float loss_value(const DevTopo& T, const LaneT<RV>& L
     default: return dot3(y, q);
   }
 }
-__device__ __forceinline__ float loss_weight(const DevTopo& T, int t_next) {
-  if (T.loss_mode == 1) return 1.f / (float)T.horizon;
-  return t_next == T.horizon ? 1.f : 0.f;
+// Weight of l(x_{t_next}) in Eq. L for an instance of horizon h: the final state, or the mean
+// over the states 1..h.
+__device__ __forceinline__ float loss_weight(const DevTopo& T, int t_next, int h) {
+  if (T.loss_mode == 1) return t_next <= h ? 1.f / (float)h : 0.f;
+  return t_next == h ? 1.f : 0.f;
+}
+// Largest horizon among the warp's instances.
+__device__ __forceinline__ int warp_horizon(const DevPtrs& D, int i) {
+  int h = D.hz[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) h = max(h, __shfl_xor_sync(0xffffffffu, h, o));
+  return h;
 }
 
 __device__ __forceinline__ float qz(const DevTopo& T, float x) { return T.ctrl_round ? bf16r(x) : x; }
@@ -704,7 +715,8 @@ __device__ float step_forward(const DevTopo& T, const DevPtrs& D, const LaneT<RV
       for (int k = 0; k < 6; ++k) tp.vminus[(6 * b + k) * 32] = X[18 * b + 12 + k];
   }
   assemble_rows(T, L, X, active_out);
-  if (TAPE && !RV::is_global) {
+  // the rows go to the tape, unless they were assembled in it (segment recompute)
+  if constexpr (TAPE && !std::is_same<RV, GS>::value) {
     for (int f = 0; f < T.nslots * RF_N; ++f) tp.rows[f * 32] = L.rows[f];
   }
   if (T.ws || D.harvest) warm_start<TAPE>(T, D, L, X, tp);
@@ -715,6 +727,6 @@ __device__ float step_forward(const DevTopo& T, const DevPtrs& D, const LaneT<RV
   if (D.harvest) harvest_finish(T, D, L);
   if (D.resid) D.resid[L.i] += solve_residual(T, L, X);
   integrate(T, X);
-  float w = loss_weight(T, t + 1);
+  float w = loss_weight(T, t + 1, D.hz[L.i]);
   return w != 0.f ? w * loss_value(T, L, X) : 0.f;
 }

@@ -139,7 +139,9 @@ __global__ void __launch_bounds__(32, 1) k_forward(const __grid_constant__ DevTo
   float loss = 0.f;
   if (rollout && T.loss_kind == 3) loss = -dot3(L.P.v3(T.o_loss_target), loss_point(T, L, X));
   const int B = T.B;
-  for (int k = 0; k < nsteps; ++k) {
+  // a rollout steps the warp to the largest horizon among its instances
+  const int nrun = rollout ? min(nsteps, warp_horizon(D, i)) : nsteps;
+  for (int k = 0; k < nrun; ++k) {
     const int t = t0 + k;
     if (rollout) {
       if (t % D.ckpt_every == 0) {
@@ -158,7 +160,7 @@ __global__ void __launch_bounds__(32, 1) k_forward(const __grid_constant__ DevTo
       loss += step_forward<false, Q>(T, D, L, X, act, t, ao);
   }
   if (rollout && D.traj && i < B)
-    for (int f = 0; f < 18 * T.nb; ++f) D.traj[((size_t)(t0 + nsteps) * B + i) * 18 * T.nb + f] = X[f];
+    for (int f = 0; f < 18 * T.nb; ++f) D.traj[((size_t)(t0 + nrun) * B + i) * 18 * T.nb + f] = X[f];
   for (int s = 0; s < T.nslots; ++s) D.lam_prev[(size_t)s * T.Bp + i] = L.S[T.sm_lam + s];
   copy_state_from_smem(T, D.state, i, X);
   bool bad = !isfinite(loss);
@@ -199,7 +201,9 @@ __device__ void reverse_step(const DevTopo& T, const DevPtrs& D, const BwdCtx& C
   const SL zb1{C.S.p + (T.sm_zb + maxw) * 32};
   // loss term and integrator with x_{t+1} on chip
   copy_state_to_smem(T, x_t1, i, C.X);
-  loss_reverse(T, Bl, C.X, C.XB, loss_weight(T, t + 1) * C.dl);
+  if (T.grad_decay != 1.f)  // section 3.2: the adjoint from later steps shrinks by alpha per step
+    for (int f = 0; f < 18 * T.nb; ++f) C.XB[f] *= T.grad_decay;
+  loss_reverse(T, Bl, C.X, C.XB, loss_weight(T, t + 1, D.hz[i]) * C.dl);
   integrate_reverse(T, GC{x_t + i, Bp}, C.X, C.XB, C.VB);
   // x_t on chip for every later stage; its per-step forward quantities are recomputed
   // bit-identically (hinge kinematics, servo targets, inverse inertias)
@@ -250,14 +254,15 @@ __global__ void __launch_bounds__(32, 1) k_backward(const __grid_constant__ DevT
            SL{sm + T.sm_sbar * 32}, GC{D.prm + i, Bp}, GL{D.grad_prm + i, Bp}, i, D.dloss[i]};
   for (int f = 0; f < nf; ++f) C.XB[f] = 0.f;
   const size_t sbytes = (size_t)nf * Bp;
+  const int Tw = warp_horizon(D, i);  // the rollout stepped this warp to Tw
   if (D.tape_full) {
-    for (int t = T.horizon - 1; t >= 0; --t)
-      reverse_step<Q, GSR>(T, D, C, t, t, D.ckpt + (size_t)t * sbytes, t + 1 < T.horizon ? D.ckpt + (size_t)(t + 1) * sbytes : D.state);
+    for (int t = Tw - 1; t >= 0; --t)
+      reverse_step<Q, GSR>(T, D, C, t, t, D.ckpt + (size_t)t * sbytes, t + 1 < Tw ? D.ckpt + (size_t)(t + 1) * sbytes : D.state);
   } else {
     const int K = D.ckpt_every;
-    for (int c = D.n_ckpt - 1; c >= 0; --c) {
+    for (int c = (Tw - 1) / K; c >= 0; --c) {
       const int ta = c * K;
-      const int tb = min(T.horizon, ta + K);
+      const int tb = min(Tw, ta + K);
       copy_state_to_smem(T, D.ckpt + (size_t)c * sbytes, i, C.X);
       if (T.ws)  // the previous impulses the segment's first step started from
         for (int s = 0; s < T.nslots; ++s) C.S[T.sm_lam + s] = D.ckpt_lam[((size_t)c * T.nslots + s) * Bp + i];

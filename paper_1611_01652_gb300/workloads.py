@@ -407,3 +407,87 @@ def pendulum1(B=1, L=0.5, m=1.0, amp_deg=1.0, horizon=3000, dt=0.001, iters=20, 
                  joint_flags=np.zeros(1, np.int32), sphere_body=np.zeros(0, np.int32),
                  pair_sphere=np.zeros((0, 2), np.int32), nb=1, dt=dt, iters=iters, horizon=horizon,
                  loss_kind=L_LINEAR, loss_mode=M_FINAL, loss_body=0, **d)
+
+
+ARM_WIDTHS = [32, 256, 256, 7]
+
+
+def arms(B=8192, seed=1003, iters=10, dt=0.005, hmin=200, hmax=2000, links=(3, 7), widths=None, out_scale=0.1,
+         w_seed=None, tau_max=60.0):
+    """Uneven batch of robot arms on a table, returned as one Model per link count (a bin of one
+    topology), each with per-instance ``horizons`` and the instances' original indices ``ids``.
+
+    Per instance: n ~ U{links} hinged links (capsules of radius 0.02 m, length U[0.1, 0.4] m, mass
+    2 kg/m x length) stacked upward from a base 0.1 m above the table (z = 0); joint 0 yaws about
+    the world z axis (motor only), the other joints pitch about their body y axes (limits
+    +-0.75 pi, motors); servos gain 10 1/s, ``tau_max`` N m (60 N m holds the longest arm, six
+    0.4 m links, level against gravity: 56.5 N m; weaker servos let long arms collapse into
+    chaotic swinging whose reverse-mode gradient overflows), 90 deg/s. A sphere of radius 0.03 m
+    at the tip (mu 0.5, e 0) touches the table. Initial yaw U[-pi, pi], relative pitches
+    U[-0.6, 0.6], at rest. Horizon U{hmin..hmax} steps of 5 ms. Controller 32 -> 256 -> 256 -> 7
+    (bfloat16; 76,039 parameters, Xavier-uniform, output layer x ``out_scale``) shared by all
+    instances, fed by the n joint angles, n joint rates and the tip-to-target vector (zero padded
+    to 32); outputs beyond n are unused. Loss: distance of the tip to a seeded target on or above
+    the table at the instance's last step."""
+    rng = np.random.default_rng(seed)
+    widths = list(widths or ARM_WIDTHS)
+    n_of = rng.integers(links[0], links[1] + 1, size=B)
+    h_of = rng.integers(hmin, hmax + 1, size=B)
+    base_z, crad, tip_r = 0.1, 0.02, 0.03
+    per = []
+    for i in range(B):
+        n = int(n_of[i])
+        L = rng.uniform(0.1, 0.4, size=n)
+        psi = rng.uniform(-math.pi, math.pi)
+        th = rng.uniform(-0.6, 0.6, size=n)
+        th[0] = 0.0
+        reach = float(L.sum())
+        rr = rng.uniform(0.2, 0.8) * reach
+        ang = rng.uniform(0.0, 2.0 * math.pi)
+        target = np.array([rr * math.cos(ang), rr * math.sin(ang), rng.uniform(0.03, 0.3)])
+        per.append((n, L, psi, th, target))
+    wr = np.random.default_rng(seed + 7 if w_seed is None else w_seed)
+    W = xavier_weights(widths, 0, wr, out_scale=out_scale)
+    bins = {}
+    for n in range(links[0], links[1] + 1):
+        ids = np.flatnonzero(n_of == n)
+        if len(ids) == 0:
+            continue
+        Bn = len(ids)
+        d = _empty(Bn, n, n, 1)
+        for r, i in enumerate(ids):
+            _, L, psi, th, target = per[i]
+            pivot = np.array([0.0, 0.0, base_z])
+            pitch = 0.0
+            for k in range(n):
+                pitch += th[k]
+                R = _rot_z(psi) @ _rot_y(pitch)
+                c = pivot + R @ np.array([0.0, 0.0, L[k] / 2])
+                d["state0"][r, k] = _state(c, R, np.zeros(3), np.zeros(3))
+                pivot = pivot + R @ np.array([0.0, 0.0, L[k]])
+                d["mass"][r, k] = 2.0 * L[k]
+                d["inertia"][r, k] = _capsule_inertia(2.0 * L[k], crad, L[k])
+                d["anchor"][r, k, 0] = [0.0, 0.0, base_z] if k == 0 else [0.0, 0.0, L[k - 1] / 2]
+                d["anchor"][r, k, 1] = [0.0, 0.0, -L[k] / 2]
+                d["axis"][r, k, :] = [0.0, 0.0, 1.0] if k == 0 else [0.0, 1.0, 0.0]
+                d["ref"][r, k, :] = [1.0, 0.0, 0.0]
+                d["limit"][r, k] = [-0.75 * math.pi, 0.75 * math.pi]
+                d["motor"][r, k] = [10.0, tau_max, math.pi / 2]
+            d["sph_off"][r, 0] = [0.0, 0.0, L[n - 1] / 2]
+            d["sph_rad"][r, 0] = tip_r
+            d["sph_mu"][r, 0] = 0.5
+            d["sph_e"][r, 0] = 0.0
+            d["loss_point"][r] = [0.0, 0.0, L[n - 1] / 2]
+            d["loss_target"][r] = target
+        _finish(d)
+        jb = np.array([[k - 1, k] for k in range(n)], np.int32)
+        jf = np.array([FLAG_MOTOR] + [FLAG_LIMIT | FLAG_MOTOR] * (n - 1), np.int32)
+        hz = h_of[ids].astype(np.int32)
+        mdl = Model(name="arm%d" % n, B=Bn, joint_type=np.full(n, HINGE, np.int32), joint_body=jb, joint_flags=jf,
+                    sphere_body=np.array([n - 1], np.int32), pair_sphere=np.zeros((0, 2), np.int32), nb=n,
+                    widths=widths, features=F_ANGLES | F_RATES | F_TARGET, W=W, dt=dt, iters=iters,
+                    horizon=int(hz.max()), loss_kind=L_DIST, loss_mode=M_FINAL, loss_body=n - 1, **d)
+        mdl.horizons = hz
+        mdl.ids = ids.astype(np.int64)
+        bins[n] = mdl
+    return bins

@@ -164,8 +164,8 @@ def rel_err(a, b):
     return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-12)
 
 
-def gpu_grads(m, horizon, ckpt_every=None):
-    w = World(m, horizon=horizon, ckpt_every=ckpt_every)
+def gpu_grads(m, horizon, ckpt_every=None, rows_global=False):
+    w = World(m, horizon=horizon, ckpt_every=ckpt_every, rows_global=rows_global)
     loss = torch.zeros(m.B, device="cuda")
     W = torch.tensor(m.W, device="cuda") if m.W is not None and len(m.W) else None
     w.rollout(W, loss)
@@ -183,8 +183,8 @@ def gpu_grads(m, horizon, ckpt_every=None):
     return out
 
 
-def check_grads(m, horizon, keys, instances, ckpt_every=None, with_W=False):
-    g = gpu_grads(m, horizon, ckpt_every)
+def check_grads(m, horizon, keys, instances, ckpt_every=None, with_W=False, rows_global=False):
+    g = gpu_grads(m, horizon, ckpt_every, rows_global)
     Wsum = None
     for i in instances:
         L, go = O.rollout_grad(m, i, horizon=horizon)
@@ -258,3 +258,28 @@ def test_tensor_core_controller_matches_simt(monkeypatch):
     assert np.abs(ta[1] - tb[1]).max() <= 1e-5
     assert rel_err(ga["W"], gb["W"]) <= 1e-3
     assert rel_err(ga["state0"], gb["state0"]) <= 1e-3
+
+
+@pytest.mark.parametrize("ckpt", [None, 8])
+def test_gradients_with_rows_in_global_memory(ckpt):
+    """The launch configuration that keeps the constraint rows in global memory (chosen for
+    robots whose rows do not fit on chip, or by the autotuner) records them in the solver tape
+    too: gradients of the whole tape and of recomputed segments match the oracle."""
+    m = WL.quadruped(B=4, horizon=20)
+    m.ctrl_fp32 = 1
+    g, Wsum = check_grads(m, 20, ("state0", "mass", "anchor", "motor", "sph_rad"), range(4), ckpt_every=ckpt,
+                          with_W=True, rows_global=True)
+    assert rel_err(g["W"], Wsum) <= GRAD_RTOL
+    check_grads(WL.pendulum3(B=4, horizon=60), 60, ("state0", "anchor", "mass"), range(4), ckpt_every=ckpt,
+                rows_global=True)
+
+
+def test_gradient_decay_quadruped():
+    """Section 3.2's decay of the gradient per time step, on the quadruped (fp32 controller,
+    whole tape and 8-step segments)."""
+    for ckpt in (None, 8):
+        m = WL.quadruped(B=4, horizon=30)
+        m.ctrl_fp32 = 1
+        m.grad_decay = 0.9
+        g, Wsum = check_grads(m, 30, ("state0", "mass", "motor"), range(4), ckpt_every=ckpt, with_W=True)
+        assert rel_err(g["W"], Wsum) <= GRAD_RTOL

@@ -1,0 +1,114 @@
+"""Uneven batches (robot arms of 3-7 links with per-instance horizons) through the C ABI against
+the FP64 oracle, and the batching runner (bins, autotuned launch configurations, CUDA graph)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_1611_01652_gb300 import workloads as WL  # noqa: E402
+from paper_1611_01652_gb300.batching import UnevenBatch  # noqa: E402
+from paper_1611_01652_gb300.binding import World  # noqa: E402
+
+from test_gpu_parity import divergence_step, rel_err  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def test_uneven_horizons_match_oracle():
+    """Each instance stops contributing to its loss at its own horizon; states up to the first
+    legitimate divergence (horizons up to 100 steps: 1e-4 for at least 90 % of the instances,
+    1e-3 for all) and the loss of clean instances match the oracle's rollout of that instance
+    over its own horizon (fp32 controller). Servo-rate and motor-impulse clamps are branch
+    decisions whose near ties are not logged; an instance that meets one may exceed 1e-4."""
+    bins = WL.arms(B=60, hmin=20, hmax=100)
+    clean = total = tight = 0
+    for n, m in bins.items():
+        m.ctrl_fp32 = 1
+        w = World(m)
+        T = w.horizon
+        traj = torch.zeros(T + 1, m.B, m.nb, 18, device="cuda")
+        act = torch.zeros(T, m.B, w.n_slots, dtype=torch.uint8, device="cuda")
+        loss = torch.zeros(m.B, device="cuda")
+        w.rollout(torch.tensor(m.W, device="cuda"), loss, traj, act)
+        w.sync()
+        traj, act, loss = traj.cpu().double().numpy(), act.cpu().numpy(), loss.cpu().double().numpy()
+        kinds = O.schedule(m)["kind"]
+        for i in range(m.B):
+            h = int(m.horizons[i])
+            st, L, a_o, gap = O.rollout(m, i, horizon=h, log=True)
+            te = divergence_step(act[:h, i], a_o, gap, kinds)
+            err = (np.abs(traj[:te + 1, i] - st[:te + 1]) / np.maximum(1.0, np.abs(st[:te + 1]))).max(axis=(1, 2))
+            tight += err.max() <= 1e-4
+            assert err.max() <= 1e-3, (n, i, h, te, err.max())
+            total += 1
+            if te == h:
+                clean += 1
+                assert abs(loss[i] - L) <= 1e-3 * max(1.0, abs(L)), (n, i, loss[i], L)
+    assert clean >= 0.5 * total, (clean, total)
+    assert tight >= 0.9 * total, (tight, total)
+
+
+def test_uneven_gradients_match_oracle():
+    """Gradients of instances with their own horizons, with and without the gradient decay of
+    section 3.2, against the oracle."""
+    for decay in (1.0, 0.95):
+        bins = WL.arms(B=15, hmin=8, hmax=30, seed=1013)
+        for n, m in bins.items():
+            m.ctrl_fp32 = 1
+            m.grad_decay = decay
+            w = World(m)
+            loss = torch.zeros(m.B, device="cuda")
+            w.rollout(torch.tensor(m.W, device="cuda"), loss)
+            dW = torch.zeros(w.n_params, device="cuda")
+            ds = torch.zeros(m.B, m.nb, 18, device="cuda")
+            dp = {k: torch.zeros(getattr(m, k).shape, device="cuda") for k in ("mass", "anchor", "motor", "loss_target")}
+            w.backward(torch.ones(m.B, device="cuda"), dW, ds, dp)
+            w.sync()
+            Wsum = None
+            for i in range(m.B):
+                L, go = O.rollout_grad(m, i, horizon=int(m.horizons[i]))
+                assert abs(loss[i].item() - L) <= 1e-4 * max(1.0, abs(L))
+                for k, g in (("state0", ds[i]), ("mass", dp["mass"][i]), ("anchor", dp["anchor"][i]),
+                             ("motor", dp["motor"][i]), ("loss_target", dp["loss_target"][i])):
+                    e = rel_err(g.cpu().double().numpy(), go[k])
+                    assert e <= 1e-3, (decay, n, i, k, e)
+                Wsum = go["W"] if Wsum is None else Wsum + go["W"]
+            assert rel_err(dW.cpu().double().numpy(), Wsum) <= 1e-3, (decay, n)
+
+
+def test_batching_runner_graph_and_autotuner():
+    """The runner's results in the bins' original order equal those of one plain world per bin
+    (bit for bit: each instance's arithmetic is independent of the batch); the captured CUDA
+    graph replays them bit for bit; every tuned configuration gives the same losses."""
+    bins = WL.arms(B=256, hmin=50, hmax=300, seed=1023)
+    W = torch.tensor(bins[3].W, device="cuda")
+    ub = UnevenBatch(bins, W, tune=True, tune_horizon=32)
+    dW_eager = ub.run().clone()
+    torch.cuda.synchronize()
+    eager = ub.losses()
+    assert torch.isfinite(dW_eager).all() and dW_eager.abs().max() > 0
+    for k, m in bins.items():
+        w = World(m)
+        loss = torch.zeros(m.B, device="cuda")
+        w.rollout(W, loss)
+        w.sync()
+        assert np.array_equal(loss.cpu().numpy(), eager[k]), k
+        assert len(ub.tuning[k]) == 8 and all(ms > 0 for _, ms in ub.tuning[k])
+    ub.capture()
+    for _ in range(2):
+        dW = ub.run()
+        torch.cuda.synchronize()
+        replay = ub.losses()
+        for k in bins:
+            assert np.array_equal(replay[k], eager[k]), k
+        assert torch.equal(dW, dW_eager)
+    # every launch configuration computes the same rollout (splits only reorder the dW sums)
+    ub2 = UnevenBatch(bins, W, tune=False)
+    dW2 = ub2.run()
+    torch.cuda.synchronize()
+    other = ub2.losses()
+    for k in bins:
+        assert np.array_equal(other[k], eager[k]), k
+    assert rel_err(dW2.cpu().double().numpy(), dW_eager.cpu().double().numpy()) <= 1e-5
+    assert ub.instance_steps == sum(int(np.sum(m.horizons)) for m in bins.values())
