@@ -399,9 +399,9 @@ def main():
     cpu = None
     if not args.no_cpu_baseline and world_size == 1:
         cores = min(host_cores(), 16)
-        v, dt, units = oracle_sample(cores, 2, 100)
+        v, dt, units = oracle_sample(cores, 8, 1000)
         cpu = {"value": v, "unit": "inst-steps/s", "cores": cores, "kind": "oracle",
-               "sample": "%d spawned processes x 2 quadruped instances x 100 steps, forward+adjoint, FP64 oracle, "
+               "sample": "%d spawned processes x 8 quadruped instances x 1000 steps, forward+adjoint, FP64 oracle, "
                          "cold start at 20 sweeps (%.1f s wall)" % (cores, dt)}
     n_dense = len(m.widths) - 1 + (1 if m.skip else 0)
     # per step: two weight preparations + forward; pad + backward; per dense layer gemm, sum, rowsum, sum
