@@ -188,10 +188,15 @@ void plan_smem(DevTopo& T, bool backward, int smem_floats_max, bool rows_on_chip
     for (int l = 0; l <= DPK_MAXL; ++l) T.sm_act[l] = 0;
     const int region = o;
     int acts = 0;
-    if (T.n_layers > 0)
+    if (T.ext_ctrl) {  // wide controller: only its input features and its output are on chip
+      T.sm_act[0] = region;
+      T.sm_act[T.n_layers] = region + T.widths[0];
+      acts = T.widths[0] + T.widths[T.n_layers];
+    } else if (T.n_layers > 0) {
       for (int l = 0; l <= T.n_layers; ++l) { T.sm_act[l] = region + acts; acts += T.widths[l]; }
-    else
+    } else {
       acts = 1;
+    }
     const int rows = T.nslots * RF_N;
     if (rows_on_chip && (region + std::max(acts, rows)) * 32 <= smem_floats_max) {
       T.sm_rows = region;
@@ -216,7 +221,8 @@ void plan_smem(DevTopo& T, bool backward, int smem_floats_max, bool rows_on_chip
     T.sm_vw = take(6 * T.nb);
     // controller-reverse ping-pong buffers: the row-adjoint region is free by then
     int maxw = 1;
-    for (int l = 0; l <= T.n_layers && T.n_layers > 0; ++l) maxw = std::max(maxw, T.widths[l]);
+    for (int l = 0; l <= T.n_layers && T.n_layers > 0; ++l)
+      if (!T.ext_ctrl || l == 0 || l == T.n_layers) maxw = std::max(maxw, T.widths[l]);
     T.sm_zb = 2 * maxw <= 12 * T.nslots ? T.sm_rc : take(2 * maxw);
   }
   T.sm_total = o;
@@ -388,6 +394,31 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
   T.grad_decay = d->grad_decay > 0.f ? d->grad_decay : 1.f;
   T.mlp_tc = T.n_layers == 3 && !T.skip && T.ctrl_round && T.widths[0] == CtrlTC::K0 && T.widths[1] == CtrlTC::H1 &&
              T.widths[2] == CtrlTC::H2 && T.widths[3] == CtrlTC::NO && !getenv("DP_FORCE_SIMT_CONTROLLER");
+  // wide bfloat16 controllers (hidden layers beyond 256) run as batched tensor-core products
+  // between step launches; DP_FORCE_WIDE_CONTROLLER selects that path for any eligible network
+  {
+    const bool shape = T.n_layers == 3 && !T.skip && T.ctrl_round && T.widths[1] % 64 == 0 && T.widths[2] % 64 == 0 &&
+                       T.widths[3] <= 8 && T.widths[0] <= 256;
+    const bool wide = T.n_layers == 3 && (T.widths[1] > 256 || T.widths[2] > 256);
+    T.ext_ctrl = shape && (wide || getenv("DP_FORCE_WIDE_CONTROLLER") != nullptr);
+    if (T.ext_ctrl) {
+      T.mlp_tc = 0;
+      T.ext_k0p = (T.widths[0] + 63) / 64 * 64;
+      T.ext_nop = 8;
+      w->ext.k0p = T.ext_k0p;
+      w->ext.h1 = T.widths[1];
+      w->ext.h2 = T.widths[2];
+      w->ext.no = T.widths[3];
+      size_t o = 0;
+      w->ext.w1 = o; o += (size_t)T.widths[1] * T.ext_k0p;
+      w->ext.w2 = o; o += (size_t)T.widths[2] * T.widths[1];
+      w->ext.w3 = o; o += (size_t)8 * T.widths[2];
+      w->ext.w3t = o; o += (size_t)T.widths[2] * 16;
+      w->ext.w2t = o; o += (size_t)T.widths[1] * T.widths[2];
+      w->ext.w1t = o; o += (size_t)T.ext_k0p * T.widths[1];
+      w->ext.size = o;
+    }
+  }
   T.topo_id = match_compiled_topology(T, T.nb, T.nj, T.ns, T.np, d->joint_type, d->joint_body, d->joint_flags,
                                       d->sphere_body, d->pair_sphere);
   if (getenv("DP_FORCE_RUNTIME_TOPOLOGY")) T.topo_id = 0;
@@ -463,6 +494,8 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
     }
   }
   K = std::min(K, T.horizon);
+  if (T.ext_ctrl && !full)
+    return cleanup(fail(DP_ENOMEM, "a wide controller needs the whole solver tape in device memory"));
   const int n_ckpt = (T.horizon + K - 1) / K;
   const int tape_steps = full ? T.horizon : K;
   DevPtrs& D = w->D;
@@ -509,6 +542,24 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
       w->Wtc = (__nv_bfloat16*)p;
     }
     D.Wtc = w->Wtc;
+    if (T.ext_ctrl) {
+      const size_t k0p = (size_t)T.ext_k0p, h1 = (size_t)T.widths[1], h2 = (size_t)T.widths[2];
+      void* p[4] = {nullptr, nullptr, nullptr, nullptr};
+      const size_t nbf[4] = {w->ext.size, Bz * k0p, Bz * h1, Bz * h2};
+      for (int k = 0; k < 4; ++k) {
+        if (cudaMalloc(&p[k], sizeof(__nv_bfloat16) * nbf[k]) != cudaSuccess) return cleanup(DP_ENOMEM);
+        w->allocs.push_back(p[k]);
+      }
+      w->ext_w = (__nv_bfloat16*)p[0];
+      D.s_ext = (__nv_bfloat16*)p[1];
+      w->ext_h1 = (__nv_bfloat16*)p[2];
+      w->ext_h2 = (__nv_bfloat16*)p[3];
+      float* sb = nullptr;
+      if (dalloc(w, &D.u_ext, (size_t)T.horizon * Bz * 8) || dalloc(w, &D.ub_ext, Bz * 16) || dalloc(w, &sb, Bz * k0p) ||
+          dalloc(w, &w->ext_d1, Bz * h1) || dalloc(w, &w->ext_d2, Bz * h2))
+        return cleanup(DP_ENOMEM);
+      D.sbar_ext = sb;
+    }
   } else {
     float* dummy = nullptr;
     if (dalloc(w, &dummy, 8)) return cleanup(DP_ENOMEM);
@@ -641,6 +692,7 @@ static dp_status stage_weights(dp_world* w, const float* W) {
   CU(cudaMemcpyAsync(w->Wmaster, W, sizeof(float) * w->n_params, cudaMemcpyDefault, w->stream));
   CU(launch_prep_weights(w->Tf, w->Wmaster, w->Wt, w->Wn, w->Wb, w->stream));
   if (w->Tf.mlp_tc) CU(launch_prep_weights_tc(w->Tf, w->Wmaster, w->Wtc, w->stream));
+  if (w->Tf.ext_ctrl) CU(launch_prep_ext(w->ext, w->Tf.widths[0], w->Wmaster, w->ext_w, w->stream));
   return DP_OK;
 }
 
@@ -648,6 +700,8 @@ dp_status dp_step(dp_world* w, int32_t n_steps, const float* W, uint8_t* active)
   if (!w) return fail(DP_EINVAL, "world is NULL");
   if (n_steps < 0) return fail(DP_EINVAL, "n_steps must be >= 0");
   if (n_steps == 0) return DP_OK;
+  if (w->Tf.ext_ctrl && w->t_now + n_steps > w->Tf.horizon)
+    return fail(DP_EINVAL, "with a wide controller dp_step cannot go past the horizon");
   TRY(stage_weights(w, W));
   DevPtrs D = w->D;
   D.active = active;
@@ -656,7 +710,10 @@ dp_status dp_step(dp_world* w, int32_t n_steps, const float* W, uint8_t* active)
     D.resid = w->resid;
     w->resid_steps += n_steps;
   }
-  CU(launch_forward(w->Tf, D, w->x0, w->t_now, n_steps, 0, 0, w->stream));
+  if (w->Tf.ext_ctrl)
+    CU(ext_forward(w, w->Tf, D, w->t_now, n_steps, 0, 0));
+  else
+    CU(launch_forward(w->Tf, D, w->x0, w->t_now, n_steps, 0, 0, w->stream));
   w->t_now += n_steps;
   w->have_rollout = false;
   return DP_OK;
@@ -674,7 +731,10 @@ dp_status dp_rollout(dp_world* w, const float* W, float* loss, float* traj, uint
     CU(cudaMemsetAsync(w->resid, 0, sizeof(float) * w->Bp, w->stream));
   }
   CU(cudaMemsetAsync(D.status, 0, sizeof(int) * w->Bp, w->stream));
-  CU(launch_forward(w->Tf, D, w->x0, 0, w->Tf.horizon, 1, D.tape_full, w->stream));
+  if (w->Tf.ext_ctrl)
+    CU(ext_forward(w, w->Tf, D, 0, w->Tf.horizon, 1, D.tape_full));
+  else
+    CU(launch_forward(w->Tf, D, w->x0, 0, w->Tf.horizon, 1, D.tape_full, w->stream));
   if (loss) CU(cudaMemcpyAsync(loss, D.loss, sizeof(float) * w->B, cudaMemcpyDefault, w->stream));
   w->t_now = w->Tf.horizon;
   w->have_rollout = true;
@@ -729,7 +789,10 @@ dp_status dp_harvest(dp_world* w, const float* W, const float* u_noise, float* r
   const DevTopo& T = w->Tf;
   CU(cudaMemsetAsync(w->harvest_count, 0, sizeof(unsigned long long), w->stream));
   CU(cudaMemsetAsync(D.status, 0, sizeof(int) * w->Bp, w->stream));
-  CU(launch_forward(T, D, w->x0, 0, T.horizon, 1, 0, w->stream));
+  if (T.ext_ctrl)
+    CU(ext_forward(w, T, D, 0, T.horizon, 1, 0));
+  else
+    CU(launch_forward(T, D, w->x0, 0, T.horizon, 1, 0, w->stream));
   unsigned long long cnt = 0;
   CU(cudaMemcpyAsync(&cnt, w->harvest_count, sizeof(cnt), cudaMemcpyDeviceToHost, w->stream));
   CU(cudaStreamSynchronize(w->stream));
@@ -764,7 +827,10 @@ dp_status dp_backward(dp_world* w, const float* dloss, float* dW, float* dstate0
   CU(cudaMemcpyAsync(w->stage, dloss, sizeof(float) * w->B, cudaMemcpyDefault, w->stream));
   CU(launch_pad_scalar(w->B, w->Bp, w->stage, D.dloss, w->stream));
   CU(cudaMemsetAsync(D.grad_prm, 0, sizeof(float) * (size_t)T.n_pfields * w->Bp, w->stream));
-  CU(launch_backward(T, D, w->stream));
+  if (T.ext_ctrl)
+    CU(ext_backward(w, T, D));
+  else
+    CU(launch_backward(T, D, w->stream));
   if (dstate0) {
     CU(launch_state_out(w->B, w->Bp, w->nf, D.grad_state0, w->stage, w->stream));
     CU(cudaMemcpyAsync(dstate0, w->stage, sizeof(float) * (size_t)w->B * w->nf, cudaMemcpyDefault, w->stream));

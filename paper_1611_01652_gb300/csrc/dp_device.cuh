@@ -45,6 +45,10 @@ struct DevTopo {
   int n_layers, skip, n_params, n_motors, ctrl_round;  // ctrl_round: 1 = bfloat16 storage points
   int topo_id;  // 0: run-time topology loops; otherwise the compiled topology with this id
   int mlp_tc;   // 1: the controller is the 24-128-128-8 bfloat16 network, run on the tensor cores
+  // 1: the controller is evaluated between step launches by batched tensor-core products over all
+  // instances (wide bfloat16 networks); the step kernels read its output u_t and write the next
+  // step's input features s_{t+1}
+  int ext_ctrl, ext_k0p, ext_nop;  // padded input width (multiple of 64) and output width (8)
   int ws;       // 1: the solve starts from the learned warm start (DevPtrs.ws_tc, ws_alpha)
   float ws_alpha;  // weight of the previous step's impulses in the warm start
   float grad_decay;  // reverse mode: state adjoint x alpha per step (section 3.2); 1 = none
@@ -99,6 +103,13 @@ struct DevPtrs {
   const float* u_noise;        // optional: controller-output perturbation [T][Bp][n_motors]
   float* resid;                // optional: per-instance sum of per-step solve residuals [Bp]
   const int* hz;               // per-instance horizons [Bp]
+  // wide-controller buffers (DevTopo.ext_ctrl): features of the step about to run [Bp][ext_k0p]
+  // bf16, controller outputs of every step [T][Bp][ext_nop], output adjoint of the step being
+  // reversed [Bp][16], input adjoint of the features [Bp][ext_k0p]
+  __nv_bfloat16* s_ext;
+  float* u_ext;
+  float* ub_ext;
+  const float* sbar_ext;
   float* lam_prev;             // impulses the last step ended with [nslots][Bp] (kept across launches)
   float* ckpt_lam;             // optional: the same at every checkpoint [n_ckpt][nslots][Bp]
   float* state;          // current state [nb*18][Bp]

@@ -685,7 +685,12 @@ template <bool TAPE, class Q = DynTopo, class RV, class AV>
 __device__ float step_forward(const DevTopo& T, const DevPtrs& D, const LaneT<RV>& L, const SL& X, const AV* act, int t,
                               uint8_t* active_out, int ts = 0, float* dump_col = nullptr) {
   hinge_kinematics(T, L, X);
-  if (T.n_layers > 0) {
+  if (T.ext_ctrl) {
+    // wide controller: its output for this step was computed between launches
+    const float* ue = D.u_ext + ((size_t)t * T.Bp + L.i) * T.ext_nop;
+    for (int m = 0; m < T.widths[T.n_layers]; ++m) act[T.n_layers][m] = ue[m];
+    servo_targets(T, L, act[T.n_layers]);
+  } else if (T.n_layers > 0) {
     controller_features(T, L, X, t, act[0]);
     if (T.mlp_tc)
       controller_forward_tc(T, D, act, dump_col);

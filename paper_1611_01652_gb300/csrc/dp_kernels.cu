@@ -133,14 +133,17 @@ __global__ void __launch_bounds__(32, 1) k_forward(const __grid_constant__ DevTo
   SL X{sm + T.sm_x * 32};
   SL act[DPK_MAXL + 1];
   for (int l = 0; l <= DPK_MAXL; ++l) act[l] = SL{sm + T.sm_act[l] * 32};
-  copy_state_to_smem(T, rollout ? x0 : D.state, i, X);
+  // rollout 1: a whole rollout from x0; rollout 2: the part of a rollout from step t0 on, from
+  // the state and loss the previous part left (from x0 when t0 = 0)
+  const bool fresh = rollout == 1 || (rollout == 2 && t0 == 0);
+  copy_state_to_smem(T, fresh ? x0 : D.state, i, X);
   // impulses of the previous step (the warm start's lambda_prev): none before a rollout
-  for (int s = 0; s < T.nslots; ++s) L.S[T.sm_lam + s] = rollout ? 0.f : D.lam_prev[(size_t)s * T.Bp + i];
-  float loss = 0.f;
-  if (rollout && T.loss_kind == 3) loss = -dot3(L.P.v3(T.o_loss_target), loss_point(T, L, X));
+  for (int s = 0; s < T.nslots; ++s) L.S[T.sm_lam + s] = fresh ? 0.f : D.lam_prev[(size_t)s * T.Bp + i];
+  float loss = (rollout == 2 && !fresh) ? D.loss[i] : 0.f;
+  if (fresh && T.loss_kind == 3) loss = -dot3(L.P.v3(T.o_loss_target), loss_point(T, L, X));
   const int B = T.B;
   // a rollout steps the warp to the largest horizon among its instances
-  const int nrun = rollout ? min(nsteps, warp_horizon(D, i)) : nsteps;
+  const int nrun = rollout ? max(0, min(nsteps, warp_horizon(D, i) - t0)) : nsteps;
   for (int k = 0; k < nrun; ++k) {
     const int t = t0 + k;
     if (rollout) {
@@ -153,14 +156,30 @@ __global__ void __launch_bounds__(32, 1) k_forward(const __grid_constant__ DevTo
       if (D.traj && i < B)
         for (int f = 0; f < 18 * T.nb; ++f) D.traj[((size_t)t * B + i) * 18 * T.nb + f] = X[f];
     }
-    uint8_t* ao = (D.active && i < B) ? D.active + ((size_t)k * B + i) * T.nslots : nullptr;
+    // the activity log is per rollout step (rollout parts) or per call step (dp_step)
+    uint8_t* ao = (D.active && i < B) ? D.active + ((size_t)(rollout == 2 ? t : k) * B + i) * T.nslots : nullptr;
     if (REC)
-      loss += step_forward<true, Q>(T, D, L, X, act, t, ao, t, T.n_layers > 0 ? D.dump + (size_t)t * T.Bp + i : nullptr);
+      loss += step_forward<true, Q>(T, D, L, X, act, t, ao, t,
+                                    T.n_layers > 0 && !T.ext_ctrl ? D.dump + (size_t)t * T.Bp + i : nullptr);
     else
       loss += step_forward<false, Q>(T, D, L, X, act, t, ao);
   }
   if (rollout && D.traj && i < B)
     for (int f = 0; f < 18 * T.nb; ++f) D.traj[((size_t)(t0 + nrun) * B + i) * 18 * T.nb + f] = X[f];
+  if (T.ext_ctrl && t0 + nrun < T.horizon) {
+    // wide controller: input features of the next step, bf16 for the products, and the
+    // activation dump column for the weight gradient
+    const int tn = t0 + nrun;
+    hinge_kinematics(T, L, X);
+    controller_features(T, L, X, tn, act[0]);
+    __nv_bfloat16* sx = D.s_ext + (size_t)i * T.ext_k0p;
+    const size_t N = (size_t)T.horizon * T.Bp;
+    for (int k = 0; k < T.ext_k0p; ++k) {
+      const float v = k < T.widths[0] ? act[0][k] : 0.f;
+      sx[k] = __float2bfloat16_rn(v);
+      if (REC && k < T.widths[0]) D.dump[(size_t)(T.dump_act[0] + k) * N + (size_t)tn * T.Bp + i] = v;
+    }
+  }
   for (int s = 0; s < T.nslots; ++s) D.lam_prev[(size_t)s * T.Bp + i] = L.S[T.sm_lam + s];
   copy_state_from_smem(T, D.state, i, X);
   bool bad = !isfinite(loss);
@@ -195,6 +214,7 @@ __device__ void reverse_step(const DevTopo& T, const DevPtrs& D, const BwdCtx& C
     act[l] = GW{D.dump + (size_t)T.dump_act[l] * N + n, N};
     del[l] = GW{D.dump + (size_t)T.dump_del[l] * N + n, N};
   }
+  if (T.ext_ctrl) act[T.n_layers] = GW{D.u_ext + n * T.ext_nop, 1};  // wide controller's output u_t
   const SL VW{C.S.p + T.sm_vw * 32}, zb0{C.S.p + T.sm_zb * 32};
   int maxw = 1;
   for (int l = 0; l <= T.n_layers && T.n_layers > 0; ++l) maxw = max(maxw, T.widths[l]);
@@ -227,7 +247,13 @@ __device__ void reverse_step(const DevTopo& T, const DevPtrs& D, const BwdCtx& C
   if (T.ws) ws_apply_reverse(T, L, C.VB, C.RC, tp);
   rows_reverse(T, Bl, C.XB, C.VB, C.RC);
   external_reverse(T, Bl, C.XB, C.VB);
-  if (T.n_layers > 0) {
+  if (T.ext_ctrl) {
+    // wide controller: the output adjoint goes to the batched products; the features' adjoint
+    // comes back into the next launch
+    servo_reverse(T, Bl, act[T.n_layers], del[T.n_layers - 1], zb0);
+    float* ub = D.ub_ext + (size_t)i * 16;
+    for (int o = 0; o < 16; ++o) ub[o] = o < T.widths[T.n_layers] ? zb0[o] : 0.f;
+  } else if (T.n_layers > 0) {
     servo_reverse(T, Bl, act[T.n_layers], del[T.n_layers - 1], zb0);
     if (T.mlp_tc)
       controller_reverse_tc(T, D, act, del, zb0, C.sbar);
@@ -281,6 +307,54 @@ __global__ void __launch_bounds__(32, 1) k_backward(const __grid_constant__ DevT
     }
   }
   if (T.loss_kind == 3) {  // initial term -a.q(x_0) of the displacement loss
+    copy_state_to_smem(T, D.ckpt, i, C.X);
+    const int b = T.loss_body;
+    M3 R = loadR(C.X, 18 * b);
+    float3 c = C.P.v3(T.o_loss_point), a = C.P.v3(T.o_loss_target);
+    float3 gq = -C.dl * a;
+    C.XB.a3(18 * b, gq);
+    add_outer(C.XB, 18 * b + 3, gq, c);
+    C.G.red3(T.o_loss_point, mtv(R, gq));
+    C.G.red3(T.o_loss_target, -C.dl * (C.X.v3(18 * b) + mv(R, c)));
+  }
+  for (int f = 0; f < nf; ++f) D.grad_state0[(size_t)f * Bp + i] = C.XB[f];
+}
+
+// Wide controller, reverse mode one step per launch. Launch t adds the adjoint of the input
+// features s_{t+1} (from the products of step t+1, DevPtrs.sbar_ext) to the state adjoint of
+// x_{t+1}, then reverses step t down to the controller-output adjoint (DevPtrs.ub_ext). The state
+// adjoint is carried between launches in grad_state0 (zeroed before the first). Launch t = -1
+// adds the adjoint of s_0 and the initial term of the loss.
+template <class Q>
+__global__ void __launch_bounds__(32, 1) k_backward_ext(const __grid_constant__ DevTopo T, const __grid_constant__ DevPtrs D,
+                                                        int t) {
+  const int lane = threadIdx.x;
+  const int i = blockIdx.x * 32 + lane;
+  const int Bp = T.Bp;
+  const int nf = 18 * T.nb;
+  float* sm = g_smem + lane;
+  BwdCtx C{SL{sm}, SL{sm + T.sm_x * 32}, SL{sm + T.sm_xb * 32}, SL{sm + T.sm_vb * 32}, SL{sm + T.sm_rc * 32},
+           SL{sm + T.sm_sbar * 32}, GC{D.prm + i, Bp}, GL{D.grad_prm + i, Bp}, i, D.dloss[i]};
+  const int Tw = warp_horizon(D, i);
+  if (t >= Tw) return;  // this warp's rollout ended before step t
+  const size_t sbytes = (size_t)nf * Bp;
+  for (int f = 0; f < nf; ++f) C.XB[f] = D.grad_state0[(size_t)f * Bp + i];
+  const int tn = t + 1;
+  if (tn < Tw) {  // adjoint of the features of x_{t+1}
+    copy_state_to_smem(T, D.ckpt + (size_t)tn * sbytes, i, C.X);
+    LaneT<GSR> L{C.S, C.P, GSR{D.ckpt}, i};
+    BLaneT<GSR> Bl{L, C.X, C.G, GC{D.ckpt, 32}};
+    hinge_kinematics(T, L, C.X);
+    for (int j = 0; j < T.nj; ++j) {
+      C.S[T.sm_thb + j] = 0.f; C.S[T.sm_thdb + j] = 0.f; C.S[T.sm_wstb + j] = 0.f;
+      C.S.s3(T.sm_uab + 3 * j, f3(0.f, 0.f, 0.f));
+    }
+    features_reverse(T, Bl, C.XB, GC{D.sbar_ext + (size_t)i * T.ext_k0p, 1});
+    hinge_reverse(T, Bl, C.XB);
+  }
+  if (t >= 0) {
+    reverse_step<Q, GSR>(T, D, C, t, t, D.ckpt + (size_t)t * sbytes, tn < Tw ? D.ckpt + (size_t)tn * sbytes : D.state);
+  } else if (T.loss_kind == 3) {  // initial term -a.q(x_0) of the displacement loss
     copy_state_to_smem(T, D.ckpt, i, C.X);
     const int b = T.loss_body;
     M3 R = loadR(C.X, 18 * b);
@@ -420,6 +494,18 @@ static cudaError_t launch_backward_q(const DevTopo& T, const DevPtrs& D, cudaStr
   if (e != cudaSuccess) return e;
   k_backward<Q><<<T.Bp / 32, 32, smem, s>>>(T, D);
   return cudaGetLastError();
+}
+template <class Q>
+static cudaError_t launch_backward_ext_q(const DevTopo& T, const DevPtrs& D, int t, cudaStream_t s) {
+  size_t smem = SM_BYTES(T);
+  cudaError_t e = cudaFuncSetAttribute(k_backward_ext<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_backward_ext<Q><<<T.Bp / 32, 32, smem, s>>>(T, D, t);
+  return cudaGetLastError();
+}
+cudaError_t launch_backward_ext(const DevTopo& T, const DevPtrs& D, int t, cudaStream_t s) {
+  if (T.topo_id == QuadrupedTopo::id) return launch_backward_ext_q<QuadrupedTopo>(T, D, t, s);
+  return launch_backward_ext_q<DynTopo>(T, D, t, s);
 }
 cudaError_t launch_backward(const DevTopo& T, const DevPtrs& D, cudaStream_t s) {
   if (T.topo_id == QuadrupedTopo::id) return launch_backward_q<QuadrupedTopo>(T, D, s);

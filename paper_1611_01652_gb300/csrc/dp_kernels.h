@@ -15,6 +15,7 @@ cudaError_t launch_pad_scalar(int B, int Bp, const float* src, float* dst, cudaS
 cudaError_t launch_forward(const DevTopo& T, const DevPtrs& D, const float* x0, int t0, int nsteps, int rollout,
                            int record, cudaStream_t s);
 cudaError_t launch_backward(const DevTopo& T, const DevPtrs& D, cudaStream_t s);
+cudaError_t launch_backward_ext(const DevTopo& T, const DevPtrs& D, int t, cudaStream_t s);
 cudaError_t launch_dw(const float* del, const float* act, int M, int C, size_t N, float* partial, int splits,
                       size_t chunk, cudaStream_t s);
 cudaError_t launch_rowsum(const float* del, int M, size_t N, float* partial, int splits, size_t chunk, cudaStream_t s);

@@ -51,6 +51,7 @@ dp_status scratch_address(float** out) {
 extern "C" dp_status dp_backward_noalloc(dp_world* w, const float* dloss, float* dW) {
   if (!w) return dp_internal_fail(DP_EINVAL, "world is NULL");
   if (!w->have_rollout) return dp_internal_fail(DP_ESTATE, "dp_backward_noalloc needs a preceding dp_rollout");
+  if (w->Tb.ext_ctrl) return dp_internal_fail(DP_EINVAL, "dp_backward_noalloc does not serve wide controllers; use dp_backward");
   if (!dloss || !dW) return dp_internal_fail(DP_EINVAL, "dloss and dW are required");
   if (w->n_params == 0) return dp_internal_fail(DP_EINVAL, "the world has no controller");
   const DevTopo& T = w->Tb;
