@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--alpha", type=float, default=0.7, help="weight of the previous impulses in the warm start")
     p.add_argument("--ws-train-steps", type=int, default=800)
     p.add_argument("--no-arms", action="store_true", help="skip the uneven arm batch")
+    p.add_argument("--no-wide", action="store_true", help="skip the wide (1.1 M-parameter) controller")
     p.add_argument("--fixed-warmstart", type=int, default=0, metavar="N",
                    help="skip the preparation and the gate: time the damped previous-impulse start at N sweeps "
                         "(for profiling the timed kernels alone)")
@@ -276,6 +277,49 @@ def time_uneven_arms(args):
     return out
 
 
+def time_wide_controller(args, alpha):
+    """The quadruped B=4096, T=1000 with the 64-1024-1024-8 controller (1,124,360 parameters,
+    batched tensor-core products between step launches): forward + adjoint of the plain solver
+    at 20 sweeps and of the damped previous-impulse start at 10 sweeps, 1 warm-up + ``steps``
+    timed steps each, with the mean solve residual of each."""
+    import torch
+
+    from paper_1611_01652_gb300 import workloads as WL
+    from paper_1611_01652_gb300.binding import WS_PARAMS, World
+
+    m = WL.quadruped(B=4096, horizon=1000, widths=[64, 1024, 1024, 8])
+    W = torch.tensor(m.W, device="cuda")
+    loss = torch.zeros(m.B, device="cuda")
+    dl = torch.ones(m.B, device="cuda")
+    out = {"workload": "quadruped B=4096 T=1000, controller 64-1024-1024-8 (1,124,360 parameters, bf16)"}
+    for name, iters, warm in (("plain", 20, False), ("warm_start", 10, True)):
+        w = World(m, iters=iters, warmstart=warm)
+        if warm:
+            w.set_warmstart(torch.zeros(WS_PARAMS, device="cuda"), alpha)
+        dW = torch.zeros(w.n_params, device="cuda")
+        w.rollout(W, loss)
+        w.backward(dl, dW)
+        w.sync()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        fwd = bwd = 0.0
+        for _ in range(args.steps):
+            ev[0].record()
+            w.rollout(W, loss)
+            ev[1].record()
+            w.backward(dl, dW)
+            ev[2].record()
+            torch.cuda.synchronize()
+            fwd += ev[0].elapsed_time(ev[1])
+            bwd += ev[1].elapsed_time(ev[2])
+        ms = (fwd + bwd) / args.steps
+        out[name] = {"iters": iters, "value": m.B * m.horizon / (ms / 1e3), "unit": "inst-steps/s", "ms_per_step": ms,
+                     "fwd_ms": fwd / args.steps, "bwd_ms": bwd / args.steps, "resid": mean_residual(w, W, m.B),
+                     "finite": bool(torch.isfinite(dW).all().item())}
+        del w
+        torch.cuda.empty_cache()
+    return out
+
+
 def mean_residual(world, W, B):
     """Mean per-step solve residual of one untimed rollout of the world."""
     import torch
@@ -379,6 +423,7 @@ def main():
     del world, head
     torch.cuda.empty_cache()
     arms = None if args.no_arms else time_uneven_arms(args)
+    wide = None if args.no_wide else time_wide_controller(args, args.alpha)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -420,7 +465,7 @@ def main():
                                "gradient w.r.t. all controller weights; %s" % (B, T, head["name"]),
                    "batch": B, "horizon": T, "iters": head["iters"], "ckpt_every": head["ckpt_every"],
                    "l2": "working set (solver tape + controller activations) >> 129 MB L2; no flush needed"},
-        "plain": plain, "warmstart": ws, "gate": gate, "uneven_arms": arms,
+        "plain": plain, "warmstart": ws, "gate": gate, "uneven_arms": arms, "wide_controller": wide,
         "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": head["clocks"],
         "plain_clocks": p_ck if ws else None,
         "gpu_launches": launches_per_step * args.steps, "fwd_ms": head["fwd_ms"], "bwd_ms": head["bwd_ms"],
