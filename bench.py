@@ -49,6 +49,10 @@ def parse():
     p.add_argument("--ws-train-steps", type=int, default=800)
     p.add_argument("--no-arms", action="store_true", help="skip the uneven arm batch")
     p.add_argument("--no-wide", action="store_true", help="skip the wide (1.1 M-parameter) controller")
+    p.add_argument("--wide-only", action="store_true",
+                   help="time only the wide controller (for profiling; prints its object as the line)")
+    p.add_argument("--wide-batch", type=int, default=4096)
+    p.add_argument("--wide-horizon", type=int, default=1000)
     p.add_argument("--fixed-warmstart", type=int, default=0, metavar="N",
                    help="skip the preparation and the gate: time the damped previous-impulse start at N sweeps "
                         "(for profiling the timed kernels alone)")
@@ -287,11 +291,12 @@ def time_wide_controller(args, alpha):
     from paper_1611_01652_gb300 import workloads as WL
     from paper_1611_01652_gb300.binding import WS_PARAMS, World
 
-    m = WL.quadruped(B=4096, horizon=1000, widths=[64, 1024, 1024, 8])
+    m = WL.quadruped(B=args.wide_batch, horizon=args.wide_horizon, widths=[64, 1024, 1024, 8])
     W = torch.tensor(m.W, device="cuda")
     loss = torch.zeros(m.B, device="cuda")
     dl = torch.ones(m.B, device="cuda")
-    out = {"workload": "quadruped B=4096 T=1000, controller 64-1024-1024-8 (1,124,360 parameters, bf16)"}
+    out = {"workload": "quadruped B=%d T=%d, controller 64-1024-1024-8 (1,124,360 parameters, bf16)" % (
+        m.B, m.horizon)}
     for name, iters, warm in (("plain", 20, False), ("warm_start", 10, True)):
         w = World(m, iters=iters, warmstart=warm)
         if warm:
@@ -348,6 +353,9 @@ def main():
     from paper_1611_01652_gb300.binding import World
 
     torch.cuda.set_device(local_rank)
+    if args.wide_only:
+        print(json.dumps(time_wide_controller(args, args.alpha)))
+        return
     dist = None
     if world_size > 1:
         import torch.distributed as dist
