@@ -530,7 +530,8 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
     w->splits = d->dw_splits > 0 ? std::min(d->dw_splits, 256) : (int)std::min<size_t>(256, (N + 16383) / 16384);
     size_t maxlayer = 0;
     for (int l = 0; l <= T.n_layers; ++l) maxlayer = std::max(maxlayer, (size_t)T.widths[l]);
-    w->partial_floats = (size_t)w->splits * maxlayer * maxlayer;
+    // the wide controller's tensor-core weight gradient splits its columns up to 20 ways
+    w->partial_floats = (size_t)std::max(w->splits, T.ext_ctrl ? 20 : 1) * maxlayer * maxlayer;
     if (dalloc(w, &w->partial, w->partial_floats)) return cleanup(DP_ENOMEM);
     D.Wt = w->Wt;
     D.Wn = w->Wn;
@@ -848,7 +849,10 @@ dp_status dp_backward(dp_world* w, const float* dloss, float* dW, float* dstate0
       CU(cudaMemcpyAsync(g.dst, w->stage, sizeof(float) * (size_t)w->B * g.n, cudaMemcpyDefault, w->stream));
     }
   }
-  if (dW && w->n_params > 0) {
+  if (dW && w->n_params > 0 && T.ext_ctrl) {
+    CU(ext_weight_grad(w, T, D, w->dW_stage));
+    CU(cudaMemcpyAsync(dW, w->dW_stage, sizeof(float) * w->n_params, cudaMemcpyDefault, w->stream));
+  } else if (dW && w->n_params > 0) {
     const size_t N = (size_t)T.horizon * w->Bp;
     const int splits = w->splits;
     const size_t chunk = ((N + splits - 1) / splits + 15) / 16 * 16;

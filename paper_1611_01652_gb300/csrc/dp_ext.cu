@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "dp_kernels.h"
@@ -27,7 +28,8 @@ struct GemmEpi {
   int kind;
   const float* bias;      // [N] (forward)
   int nvalid;             // real columns (forward output)
-  void* out;              // bf16 (EPI_FWD_HIDDEN) or fp32, row-major with leading dimension ldo
+  void* out;              // bf16 (EPI_FWD_HIDDEN; EPI_BWD_HIDDEN: high plane) or fp32, row-major, leading dim ldo
+  __nv_bfloat16* out_lo;  // EPI_BWD_HIDDEN: low plane (value minus its bfloat16 rounding)
   int ldo;
   float* dump;            // feature-major dump [row][ncol], column col0 + m; or nullptr
   int dump_row;
@@ -109,12 +111,298 @@ __global__ void __launch_bounds__(128) k_ctrl_gemm(const void* __restrict__ Av, 
           static_cast<float*>(e.out)[(size_t)m * e.ldo + n] = v;
         } else if (e.kind == EPI_BWD_HIDDEN) {
           if (!(e.mask[(size_t)(e.mask_row + n) * e.ncol + e.col0 + m] > 0.f)) v = 0.f;
-          static_cast<float*>(e.out)[(size_t)m * e.ldo + n] = v;
+          const float hi = bf16_round(v);
+          static_cast<__nv_bfloat16*>(e.out)[(size_t)m * e.ldo + n] = __float2bfloat16_rn(hi);
+          e.out_lo[(size_t)m * e.ldo + n] = __float2bfloat16_rn(v - hi);
         } else {
           static_cast<float*>(e.out)[(size_t)m * e.ldo + n] = v;
         }
         if (e.dump && n < e.nvalid) e.dump[(size_t)(e.dump_row + n) * e.ncol + e.col0 + m] = v;
       }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Tiled products: a CTA of 8 warps computes a 128 x BN tile of C = A B^T; A (bf16, optionally a
+// second bf16 plane holding the low part of a split fp32 operand) and B are staged through
+// shared memory in 32-column k-chunks by cp.async (double buffered, rows past M zero-filled),
+// fragments are read with ldmatrix from rows padded to 40 halves (80 bytes: the 8 row addresses
+// of an 8x8 matrix fall in 8 different 16-byte bank groups).
+constexpr int TBM = 128, TBK = 32, TLDS = 40;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void ldsm_x4(const void* p, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(smem_u32(p)));
+}
+
+
+template <int BN, bool SPLIT>
+__global__ void __launch_bounds__(256) k_tc_gemm(const __nv_bfloat16* __restrict__ Ahi, const __nv_bfloat16* __restrict__ Alo,
+                                                 const __nv_bfloat16* __restrict__ B, int M, int N, int K, const GemmEpi e) {
+  constexpr int WN = BN / 32, WM = 8 / WN, WTM = TBM / WM, MT = WTM / 16;
+  constexpr int APL = TBM * TLDS, BPL = BN * TLDS;  // halves per plane and stage
+  extern __shared__ __align__(16) unsigned char tc_smem[];
+  __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(tc_smem);       // [2][SPLIT+1][APL]
+  __nv_bfloat16* sB = sA + 2 * (SPLIT ? 2 : 1) * APL;                    // [2][BPL]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, q = lane & 3;
+  const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * BN;
+  const int wr = (warp / WN) * WTM, wc = (warp % WN) * 32;
+  auto load = [&](int kc, int buf) {
+    const int k0 = kc * TBK;
+    for (int c = tid; c < TBM * 4; c += 256) {
+      const int r = c >> 2, col = (c & 3) * 8;
+      const bool ok = m0 + r < M;
+      const size_t off = (size_t)(ok ? m0 + r : 0) * K + k0 + col;
+      cp_async16(sA + (size_t)(buf * (SPLIT ? 2 : 1)) * APL + r * TLDS + col, Ahi + off, ok);
+      if constexpr (SPLIT) cp_async16(sA + (size_t)(buf * 2 + 1) * APL + r * TLDS + col, Alo + off, ok);
+    }
+    for (int c = tid; c < BN * 4; c += 256) {
+      const int r = c >> 2, col = (c & 3) * 8;
+      cp_async16(sB + (size_t)buf * BPL + r * TLDS + col, B + (size_t)(n0 + r) * K + k0 + col, true);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  float acc[MT][4][4];
+#pragma unroll
+  for (int a = 0; a < MT; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+  const int nk = K / TBK;
+  load(0, 0);
+  for (int kc = 0; kc < nk; ++kc) {
+    const int buf = kc & 1;
+    if (kc + 1 < nk) {
+      load(kc + 1, buf ^ 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();
+    const __nv_bfloat16* a_hi = sA + (size_t)(buf * (SPLIT ? 2 : 1)) * APL;
+    const __nv_bfloat16* b_s = sB + (size_t)buf * BPL;
+#pragma unroll
+    for (int kk = 0; kk < TBK; kk += 16) {
+      uint32_t bf[4][2];
+#pragma unroll
+      for (int np = 0; np < 2; ++np) {
+        const __nv_bfloat16* p = b_s + (wc + np * 16 + (lane & 7) + (lane >> 4) * 8) * TLDS + kk + ((lane >> 3) & 1) * 8;
+        ldsm_x4(p, bf[2 * np][0], bf[2 * np][1], bf[2 * np + 1][0], bf[2 * np + 1][1]);
+      }
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt) {
+        uint32_t af[4];
+        const int row = wr + mt * 16 + (lane & 15), col = kk + (lane >> 4) * 8;
+        ldsm_x4(a_hi + row * TLDS + col, af[0], af[1], af[2], af[3]);
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) mma_bf16_16816(acc[mt][nt], af, bf[nt][0], bf[nt][1]);
+        if constexpr (SPLIT) {
+          ldsm_x4(a_hi + APL + row * TLDS + col, af[0], af[1], af[2], af[3]);
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) mma_bf16_16816(acc[mt][nt], af, bf[nt][0], bf[nt][1]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int m = m0 + wr + mt * 16 + g + (k >= 2 ? 8 : 0);
+        const int n = n0 + wc + nt * 8 + 2 * q + (k & 1);
+        if (m >= M) continue;
+        float v = acc[mt][nt][k];
+        if (e.kind == EPI_FWD_HIDDEN) {
+          v = bf16_round(fmaxf(v + e.bias[n], 0.f));
+          static_cast<__nv_bfloat16*>(e.out)[(size_t)m * e.ldo + n] = __float2bfloat16_rn(v);
+        } else if (e.kind == EPI_BWD_HIDDEN) {
+          if (!(e.mask[(size_t)(e.mask_row + n) * e.ncol + e.col0 + m] > 0.f)) v = 0.f;
+          const float hi = bf16_round(v);
+          static_cast<__nv_bfloat16*>(e.out)[(size_t)m * e.ldo + n] = __float2bfloat16_rn(hi);
+          e.out_lo[(size_t)m * e.ldo + n] = __float2bfloat16_rn(v - hi);
+        } else {
+          static_cast<float*>(e.out)[(size_t)m * e.ldo + n] = v;
+        }
+        if (e.dump) e.dump[(size_t)(e.dump_row + n) * e.ncol + e.col0 + m] = v;
+      }
+}
+
+template <int BN, bool SPLIT>
+cudaError_t tc_gemm(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, const __nv_bfloat16* B, int M, int N, int K,
+                    const GemmEpi& e, cudaStream_t s) {
+  const int smem = (2 * (SPLIT ? 2 : 1) * TBM * TLDS + 2 * BN * TLDS) * (int)sizeof(__nv_bfloat16);
+  cudaError_t r = cudaFuncSetAttribute(k_tc_gemm<BN, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (r != cudaSuccess) return r;
+  dim3 grid(N / BN, (M + TBM - 1) / TBM);
+  k_tc_gemm<BN, SPLIT><<<grid, 256, smem, s>>>(Ahi, Alo, B, M, N, K, e);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Weight gradient of a wide layer on the tensor cores: partial[split][o][c] = sum over the split's
+// dump columns n of delta[o][n] act[c][n] (Eq. 4's chain rule summed over steps and instances).
+// Both operands are fp32 dump rows (column index n contiguous); they are converted to bfloat16
+// while they are staged in shared memory: activations are bfloat16 values already (exact), deltas
+// are split into a high and a low bfloat16 part (two products). A CTA computes a 128 x BN tile of
+// rows of A against rows of B; with TRANS, A holds the activations and B the deltas (layers with
+// few outputs) and the tile is stored transposed. Loads for the next 32-column chunk are issued
+// into registers before the current chunk's products.
+template <int BN, bool SPLIT_A, bool SPLIT_B, bool TRANS>
+__global__ void __launch_bounds__(256, 2) k_dw_tc(const float* __restrict__ A, int MA, const float* __restrict__ Bm, int MB,
+                                                  size_t N, size_t chunk, float* __restrict__ partial) {
+  constexpr int WN = BN / 32, WM = 8 / WN, WTM = TBM / WM, MT = WTM / 16;
+  constexpr int PA = SPLIT_A ? 2 : 1, PB = SPLIT_B ? 2 : 1;
+  constexpr int APL = TBM * TLDS, BPL = BN * TLDS;
+  constexpr int LA = TBM * 8 / 256, LB = (BN * 8 + 255) / 256;  // float4 loads per thread and chunk
+  extern __shared__ __align__(16) unsigned char dw_smem[];
+  __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(dw_smem);  // [2][PA][APL]
+  __nv_bfloat16* sB = sA + 2 * PA * APL;                           // [2][PB][BPL]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, q = lane & 3;
+  const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * BN;
+  const int wr = (warp / WN) * WTM, wc = (warp % WN) * 32;
+  const size_t k0 = (size_t)blockIdx.z * chunk, k1 = min(N, k0 + chunk);
+  const int nk = k1 > k0 ? (int)((k1 - k0) / TBK) : 0;
+  float4 ra[LA], rb[LB];
+  auto gload = [&](int kc) {
+    const size_t kb = k0 + (size_t)kc * TBK;
+#pragma unroll
+    for (int j = 0; j < LA; ++j) {
+      const int c = tid + j * 256, r = c >> 3, col = (c & 7) * 4;
+      ra[j] = m0 + r < MA ? __ldg(reinterpret_cast<const float4*>(A + (size_t)(m0 + r) * N + kb + col))
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int j = 0; j < LB; ++j) {
+      const int c = tid + j * 256, r = c >> 3, col = (c & 7) * 4;
+      rb[j] = (c < BN * 8 && n0 + r < MB) ? __ldg(reinterpret_cast<const float4*>(Bm + (size_t)(n0 + r) * N + kb + col))
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  auto put = [](__nv_bfloat16* hi, __nv_bfloat16* lo, float4 v) {
+    const float h[4] = {bf16_round(v.x), bf16_round(v.y), bf16_round(v.z), bf16_round(v.w)};
+    *reinterpret_cast<uint2*>(hi) = make_uint2(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]));
+    if (lo) *reinterpret_cast<uint2*>(lo) = make_uint2(pack_bf16(v.x - h[0], v.y - h[1]), pack_bf16(v.z - h[2], v.w - h[3]));
+  };
+  auto sstore = [&](int buf) {
+#pragma unroll
+    for (int j = 0; j < LA; ++j) {
+      const int c = tid + j * 256, r = c >> 3, col = (c & 7) * 4;
+      __nv_bfloat16* p = sA + (size_t)buf * PA * APL + r * TLDS + col;
+      put(p, SPLIT_A ? p + APL : nullptr, ra[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < LB; ++j) {
+      const int c = tid + j * 256, r = c >> 3, col = (c & 7) * 4;
+      if (c >= BN * 8) continue;
+      __nv_bfloat16* p = sB + (size_t)buf * PB * BPL + r * TLDS + col;
+      put(p, SPLIT_B ? p + BPL : nullptr, rb[j]);
+    }
+  };
+  float acc[MT][4][4];
+#pragma unroll
+  for (int a = 0; a < MT; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+  if (nk > 0) {
+    gload(0);
+    sstore(0);
+  }
+  __syncthreads();
+  for (int kc = 0; kc < nk; ++kc) {
+    const int buf = kc & 1;
+    if (kc + 1 < nk) gload(kc + 1);
+    const __nv_bfloat16* a_s = sA + (size_t)buf * PA * APL;
+    const __nv_bfloat16* b_s = sB + (size_t)buf * PB * BPL;
+#pragma unroll
+    for (int kk = 0; kk < TBK; kk += 16) {
+      uint32_t bf[PB][4][2];
+#pragma unroll
+      for (int pb = 0; pb < PB; ++pb)
+#pragma unroll
+        for (int np = 0; np < 2; ++np) {
+          const __nv_bfloat16* p =
+              b_s + pb * BPL + (wc + np * 16 + (lane & 7) + (lane >> 4) * 8) * TLDS + kk + ((lane >> 3) & 1) * 8;
+          ldsm_x4(p, bf[pb][2 * np][0], bf[pb][2 * np][1], bf[pb][2 * np + 1][0], bf[pb][2 * np + 1][1]);
+        }
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt) {
+        const int row = wr + mt * 16 + (lane & 15), col = kk + (lane >> 4) * 8;
+#pragma unroll
+        for (int pa = 0; pa < PA; ++pa) {
+          uint32_t af[4];
+          ldsm_x4(a_s + pa * APL + row * TLDS + col, af[0], af[1], af[2], af[3]);
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) {
+            mma_bf16_16816(acc[mt][nt], af, bf[0][nt][0], bf[0][nt][1]);
+            if constexpr (SPLIT_B) {
+              if (pa == 0) mma_bf16_16816(acc[mt][nt], af, bf[PB - 1][nt][0], bf[PB - 1][nt][1]);
+            }
+          }
+        }
+      }
+    }
+    if (kc + 1 < nk) sstore(buf ^ 1);
+    __syncthreads();
+  }
+  float* P = partial + (size_t)blockIdx.z * MA * MB;
+#pragma unroll
+  for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int m = m0 + wr + mt * 16 + g + (k >= 2 ? 8 : 0);
+        const int n = n0 + wc + nt * 8 + 2 * q + (k & 1);
+        if (m >= MA || n >= MB) continue;
+        if (TRANS)
+          P[(size_t)n * MA + m] = acc[mt][nt][k];
+        else
+          P[(size_t)m * MB + n] = acc[mt][nt][k];
+      }
+}
+
+// Split count for a grid of `tiles` CTAs: the one whose last wave is fullest (2 CTAs per SM on
+// 152 SMs), at most `cap`.
+int dw_splits_for(int tiles, int cap) {
+  const int slots = 2 * 152;
+  int best = 1;
+  double best_cost = 1e30;
+  for (int s = 1; s <= std::min(cap, 64); ++s) {
+    const double waves = std::ceil((double)tiles * s / slots);
+    const double cost = waves / s + 1e-3 * s;  // time per unit of work, then fewer partials
+    if (cost < best_cost) best_cost = cost, best = s;
+  }
+  return best;
+}
+
+template <int BN, bool SPLIT_A, bool SPLIT_B, bool TRANS>
+cudaError_t dw_tc(const float* A, int MA, const float* Bm, int MB, size_t N, float* partial, size_t partial_floats,
+                  int* splits_out, cudaStream_t s) {
+  constexpr int smem = (2 * (SPLIT_A ? 2 : 1) * TBM * TLDS + 2 * (SPLIT_B ? 2 : 1) * BN * TLDS) * (int)sizeof(__nv_bfloat16);
+  cudaError_t r = cudaFuncSetAttribute(k_dw_tc<BN, SPLIT_A, SPLIT_B, TRANS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (r != cudaSuccess) return r;
+  const int gx = (MB + BN - 1) / BN, gy = (MA + TBM - 1) / TBM;
+  const int cap = (int)std::max<size_t>(1, partial_floats / ((size_t)MA * MB));
+  const int splits = dw_splits_for(gx * gy, cap);
+  const size_t chunk = ((N + splits - 1) / splits + TBK - 1) / TBK * TBK;
+  k_dw_tc<BN, SPLIT_A, SPLIT_B, TRANS><<<dim3(gx, gy, splits), 256, smem, s>>>(A, MA, Bm, MB, N, chunk, partial);
+  *splits_out = splits;
+  return cudaGetLastError();
 }
 
 template <int NT, bool AF32>
@@ -164,6 +452,13 @@ cudaError_t launch_prep_ext(const ExtLayout& Lo, int K0, const float* W, __nv_bf
   return cudaGetLastError();
 }
 
+// Tile width of the tiled products: 128 columns where N allows it.
+template <bool SPLIT>
+cudaError_t tc_gemm_n(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, const __nv_bfloat16* B, int M, int N, int K,
+                      const GemmEpi& e, cudaStream_t s) {
+  return N % 128 == 0 ? tc_gemm<128, SPLIT>(Ahi, Alo, B, M, N, K, e, s) : tc_gemm<64, SPLIT>(Ahi, Alo, B, M, N, K, e, s);
+}
+
 // Controller products of step t (forward): s_t -> h1 -> h2 -> u_t; with `record` the activations
 // also go to the dump columns of step t.
 cudaError_t ext_forward_products(dp_world* w, const DevTopo& T, const DevPtrs& D, int t, bool record) {
@@ -181,14 +476,14 @@ cudaError_t ext_forward_products(dp_world* w, const DevTopo& T, const DevPtrs& D
   e.ldo = Lo.h1;
   e.dump = record ? D.dump : nullptr;
   e.dump_row = T.dump_act[1];
-  cudaError_t r = gemm<8, false>(D.s_ext, Lo.k0p, w->ext_w + Lo.w1, M, Lo.h1, Lo.k0p, e, w->stream);
+  cudaError_t r = tc_gemm_n<false>(D.s_ext, nullptr, w->ext_w + Lo.w1, M, Lo.h1, Lo.k0p, e, w->stream);
   if (r != cudaSuccess) return r;
   e.bias = D.bias + T.w_off[1];
   e.nvalid = Lo.h2;
   e.out = w->ext_h2;
   e.ldo = Lo.h2;
   e.dump_row = T.dump_act[2];
-  r = gemm<8, false>(w->ext_h1, Lo.h1, w->ext_w + Lo.w2, M, Lo.h2, Lo.h1, e, w->stream);
+  r = tc_gemm_n<false>(w->ext_h1, nullptr, w->ext_w + Lo.w2, M, Lo.h2, Lo.h1, e, w->stream);
   if (r != cudaSuccess) return r;
   e.kind = EPI_FWD_OUT;
   e.bias = D.bias + T.w_off[2];
@@ -200,15 +495,21 @@ cudaError_t ext_forward_products(dp_world* w, const DevTopo& T, const DevPtrs& D
 }
 
 // Controller products of step t (reverse): u_bar -> delta_2 -> delta_1 -> s_bar, deltas to the dump.
+// The deltas are kept as two bfloat16 planes (high part, then the low remainder) in the fp32
+// delta buffers, which hold exactly the two planes.
 cudaError_t ext_backward_products(dp_world* w, const DevTopo& T, const DevPtrs& D, int t) {
   const ExtLayout& Lo = w->ext;
   const int M = T.Bp;
+  __nv_bfloat16* d2 = reinterpret_cast<__nv_bfloat16*>(w->ext_d2);
+  __nv_bfloat16* d1 = reinterpret_cast<__nv_bfloat16*>(w->ext_d1);
+  const size_t p2 = (size_t)M * Lo.h2, p1 = (size_t)M * Lo.h1;
   GemmEpi e{};
   e.ncol = (size_t)T.horizon * T.Bp;
   e.col0 = (size_t)t * T.Bp;
   e.kind = EPI_BWD_HIDDEN;
   e.nvalid = Lo.h2;
-  e.out = w->ext_d2;
+  e.out = d2;
+  e.out_lo = d2 + p2;
   e.ldo = Lo.h2;
   e.dump = D.dump;
   e.dump_row = T.dump_del[1];
@@ -217,18 +518,20 @@ cudaError_t ext_backward_products(dp_world* w, const DevTopo& T, const DevPtrs& 
   cudaError_t r = gemm<8, true>(D.ub_ext, 16, w->ext_w + Lo.w3t, M, Lo.h2, 16, e, w->stream);
   if (r != cudaSuccess) return r;
   e.nvalid = Lo.h1;
-  e.out = w->ext_d1;
+  e.out = d1;
+  e.out_lo = d1 + p1;
   e.ldo = Lo.h1;
   e.dump_row = T.dump_del[0];
   e.mask_row = T.dump_act[1];
-  r = gemm<8, true>(w->ext_d2, Lo.h2, w->ext_w + Lo.w2t, M, Lo.h1, Lo.h2, e, w->stream);
+  r = tc_gemm_n<true>(d2, d2 + p2, w->ext_w + Lo.w2t, M, Lo.h1, Lo.h2, e, w->stream);
   if (r != cudaSuccess) return r;
   e.kind = EPI_BWD_IN;
   e.nvalid = Lo.k0p;
   e.out = const_cast<float*>(D.sbar_ext);
+  e.out_lo = nullptr;
   e.ldo = Lo.k0p;
   e.dump = nullptr;
-  return gemm<8, true>(w->ext_d1, Lo.h1, w->ext_w + Lo.w1t, M, Lo.k0p, Lo.h1, e, w->stream);
+  return tc_gemm_n<true>(d1, d1 + p1, w->ext_w + Lo.w1t, M, Lo.k0p, Lo.h1, e, w->stream);
 }
 
 // A rollout part with the wide controller: the features of the start state, then per step the
@@ -254,4 +557,36 @@ cudaError_t ext_backward(dp_world* w, const DevTopo& T, const DevPtrs& D) {
     if (r == cudaSuccess && t >= 0) r = ext_backward_products(w, T, D, t);
   }
   return r;
+}
+
+// Controller gradient of the wide path, summed over all steps and instances, into dst (flat
+// layout of the master weights: per layer W[out][in] then b[out]).
+cudaError_t ext_weight_grad(dp_world* w, const DevTopo& T, const DevPtrs& D, float* dst) {
+  const ExtLayout& Lo = w->ext;
+  const size_t N = (size_t)T.horizon * T.Bp;
+  const int rows[4] = {T.widths[0], Lo.h1, Lo.h2, Lo.no};
+  size_t off = 0;
+  for (int l = 0; l < 3; ++l) {
+    const int ni = rows[l], no_ = rows[l + 1];
+    const float* del = D.dump + (size_t)T.dump_del[l] * N;
+    const float* act = D.dump + (size_t)T.dump_act[l] * N;
+    int splits = 1;
+    cudaError_t r;
+    if (l == 2)
+      r = dw_tc<32, false, true, true>(act, ni, del, no_, N, w->partial, w->partial_floats, &splits, w->stream);
+    else if (ni <= 64)
+      r = dw_tc<64, true, false, false>(del, no_, act, ni, N, w->partial, w->partial_floats, &splits, w->stream);
+    else
+      r = dw_tc<128, true, false, false>(del, no_, act, ni, N, w->partial, w->partial_floats, &splits, w->stream);
+    if (r == cudaSuccess) r = launch_sum_splits(w->partial, splits, (size_t)no_ * ni, dst + off, w->stream);
+    if (r != cudaSuccess) return r;
+    off += (size_t)no_ * ni;
+    const int bs = w->splits;
+    const size_t chunk = ((N + bs - 1) / bs + 15) / 16 * 16;
+    r = launch_rowsum(del, no_, N, w->partial, bs, chunk, w->stream);
+    if (r == cudaSuccess) r = launch_sum_splits(w->partial, bs, (size_t)no_, dst + off, w->stream);
+    if (r != cudaSuccess) return r;
+    off += no_;
+  }
+  return cudaSuccess;
 }
