@@ -235,13 +235,61 @@ __device__ void pgs_solve_static(const DevTopo& T, const LaneT<RV>& L, const SL&
 }
 
 // ---------------------------------------------------------------------------- reverse sweeps
-// Same arithmetic as pgs_reverse with constant slots. Working velocities and the impulse of
-// every row after the sweep being reversed live in registers (one tape load per row per sweep);
+// Same arithmetic as pgs_reverse with constant slots. Working velocities live in registers;
 // velocity adjoints, impulse adjoints and row-adjoint accumulators in shared memory; I^-1 J^T is
 // recomputed from the on-chip world inverse inertias. Which rows are active on some lane is
-// decided once per step (a bit mask), and the clamp branch enters the arithmetic as a selector,
-// so the loads of a row are issued before any of them is used.
+// decided once per step (a bit mask), and the clamp branch enters the arithmetic as a selector.
+// Every tape value a row needs (row fields, its impulse before and after the sweep, the clamp
+// branch, the contact's normal impulse) is loaded one row ahead of its use, so the L2 latency of
+// the tape overlaps the arithmetic of the row before (the last row of a sweep prefetches the
+// first row of the sweep before it).
 // Called with a read-only tape view (the whole tape was recorded by the rollout kernel).
+struct RowIn {
+  float meff, bias, la, lb, bnd, lnrm;
+  float3 lin, angA, angB;
+  int br;
+};
+
+// Position of slot s in the sweep order.
+template <class Q>
+__device__ __forceinline__ constexpr int order_pos(int s) {
+  for (int k = 0; k < Q::NS; ++k)
+    if (Q::S.order[k] == s) return k;
+  return -1;
+}
+
+template <class Q, int s>
+__device__ __forceinline__ RowIn load_row(const DevTopo& T, const LaneT<GSR>& L, const TapeStep& tp, int it) {
+  constexpr int NS = Q::NS;
+  constexpr int kind = Q::S.kind[s], sub = Q::S.sub[s], a = Q::S.a[s], b = Q::S.b[s];
+  const GSR R = L.rows.at(s * RF_N);
+  RowIn r;
+  r.meff = R[RF_MEFF];
+  r.bias = R[RF_BIAS];
+  if constexpr (lin_is_constant<kind, sub>()) r.lin = const_lin<kind, sub>();
+  else if constexpr (lin_is_zero<kind>()) r.lin = f3(0.f, 0.f, 0.f);
+  else r.lin = R.v3(RF_LIN);
+  r.angA = a >= 0 ? R.v3(RF_ANGA) : f3(0.f, 0.f, 0.f);
+  r.angB = b >= 0 ? R.v3(RF_ANGB) : f3(0.f, 0.f, 0.f);
+  const int o = (it * NS + s) * 32;
+  r.la = __ldg(tp.lam + o);
+  r.lb = it > 0 ? __ldg(tp.lam + o - NS * 32) : (T.ws ? __ldg(tp.lam0 + s * 32) : 0.f);
+  r.br = __ldg(tp.br + o);
+  r.bnd = 0.f;
+  r.lnrm = 0.f;
+  if constexpr (kind == RK_GT || kind == RK_PT) {
+    // the contact's normal impulse as the friction row saw it: after this sweep when the normal
+    // row comes first in the sweep order, else before it
+    constexpr int nrm = Q::S.normal[s];
+    r.bnd = R[RF_BND];
+    if constexpr (order_pos<Q>(nrm) < order_pos<Q>(s))
+      r.lnrm = __ldg(tp.lam + (it * NS + nrm) * 32);
+    else
+      r.lnrm = it > 0 ? __ldg(tp.lam + ((it - 1) * NS + nrm) * 32) : (T.ws ? __ldg(tp.lam0 + nrm * 32) : 0.f);
+  }
+  return r;
+}
+
 template <class Q>
 __device__ __noinline__ void pgs_reverse_static(const DevTopo& T, const LaneT<GSR>& L, const TapeStep& tp) {
   constexpr int NB = Q::NB, NS = Q::NS;
@@ -249,11 +297,9 @@ __device__ __noinline__ void pgs_reverse_static(const DevTopo& T, const LaneT<GS
   // shared-memory views re-derived from the __shared__ array so their address space is known
   const SL S{g_smem + (threadIdx.x & 31)};
   const SL VB = S.at(T.sm_vb), RC = S.at(T.sm_rc);
-  const float* tlam = tp.lam;
-  const uint8_t* tbr = tp.br;
   const float gamma = T.gamma;
   const int iters = T.iters;
-  float v[NB][6], im[NB], lc[NS];
+  float v[NB][6], im[NB];
 #pragma unroll
   for (int b = 0; b < NB; ++b) im[b] = S[T.sm_invm + b];
   unsigned live[NW];
@@ -268,12 +314,9 @@ __device__ __noinline__ void pgs_reverse_static(const DevTopo& T, const LaneT<GS
       live[s >> 5] |= 1u << (s & 31);
     }
   });
-  // impulses after the last sweep
 #pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    lc[s] = __ldg(tlam + ((iters - 1) * NS + s) * 32);
-    S[T.sm_lam + s] = 0.f;
-  }
+  for (int s = 0; s < NS; ++s) S[T.sm_lam + s] = 0.f;
+  RowIn cur = load_row<Q, Q::S.order[NS - 1]>(T, L, tp, iters - 1);
   for (int it = iters - 1; it >= 0; --it) {
     {
       const float* vi = tp.viter + it * NB * 6 * 32;
@@ -283,119 +326,112 @@ __device__ __noinline__ void pgs_reverse_static(const DevTopo& T, const LaneT<GS
         for (int k = 0; k < 6; ++k) v[b][k] = __ldg(vi + (6 * b + k) * 32);
     }
     static_for<NS>([&](auto RI) {
-      constexpr int s = Q::S.order[NS - 1 - decltype(RI)::value];
-      constexpr int kind = Q::S.kind[s], sub = Q::S.sub[s], a = Q::S.a[s], b = Q::S.b[s];
-      if constexpr (maybe_inactive<kind>())
-        if (!((live[s >> 5] >> (s & 31)) & 1u)) return;
-      const GSR R = L.rows.at(s * RF_N);
-      // loads first
-      const float meff = R[RF_MEFF];
-      const float bias = R[RF_BIAS];
-      float3 lin;
-      if constexpr (lin_is_constant<kind, sub>()) lin = const_lin<kind, sub>();
-      else if constexpr (lin_is_zero<kind>()) lin = f3(0.f, 0.f, 0.f);
-      else lin = R.v3(RF_LIN);
-      const float3 angA = a >= 0 ? R.v3(RF_ANGA) : f3(0.f, 0.f, 0.f);
-      const float3 angB = b >= 0 ? R.v3(RF_ANGB) : f3(0.f, 0.f, 0.f);
-      const int o = (it * NS + s) * 32;
-      const float la = lc[s];
-      const float lb = it > 0 ? __ldg(tlam + o - NS * 32) : (T.ws ? __ldg(tp.lam0 + s * 32) : 0.f);
-      const int br = __ldg(tbr + o);
-      float bnd = 0.f, lnrm = 0.f;
-      if constexpr (kind == RK_GT || kind == RK_PT) {
-        constexpr int nrm = Q::S.normal[s];
-        bnd = R[RF_BND];
-        lnrm = lc[nrm];
+      constexpr int ri = decltype(RI)::value;
+      constexpr int s = Q::S.order[NS - 1 - ri];
+      constexpr int kind = Q::S.kind[s], a = Q::S.a[s], b = Q::S.b[s];
+      RowIn nxt;
+      if constexpr (ri + 1 < NS) {
+        nxt = load_row<Q, Q::S.order[NS - 2 - ri]>(T, L, tp, it);
+      } else {
+        nxt = it > 0 ? load_row<Q, Q::S.order[NS - 1]>(T, L, tp, it - 1) : cur;
       }
-      float ia[6], ib[6];
-      if (a >= 0) {
+      bool active = true;
+      if constexpr (maybe_inactive<kind>()) active = (live[s >> 5] >> (s & 31)) & 1u;
+      if (active) {
+        const float meff = cur.meff, bias = cur.bias;
+        const float3 lin = cur.lin, angA = cur.angA, angB = cur.angB;
+        const float la = cur.la, lb = cur.lb;
+        const int br = cur.br;
+        float ia[6], ib[6];
+        if (a >= 0) {
 #pragma unroll
-        for (int q = 0; q < 6; ++q) ia[q] = S[T.sm_iinv + 6 * a + q];
-      }
-      if (b >= 0) {
+          for (int q = 0; q < 6; ++q) ia[q] = S[T.sm_iinv + 6 * a + q];
+        }
+        if (b >= 0) {
 #pragma unroll
-        for (int q = 0; q < 6; ++q) ib[q] = S[T.sm_iinv + 6 * b + q];
+          for (int q = 0; q < 6; ++q) ib[q] = S[T.sm_iinv + 6 * b + q];
+        }
+        const float dl = la - lb;
+        float dbar = 0.f;
+        float3 va = f3(0.f, 0.f, 0.f), wa = va, vb3 = va, wb3 = va, vba = va, wba = va, vbb = va, wbb = va;
+        if (a >= 0) {
+          const float3 IA = symv(ia, angA);
+          const float c = dl * im[a];
+          v[a][0] -= c * lin.x; v[a][1] -= c * lin.y; v[a][2] -= c * lin.z;
+          v[a][3] -= dl * IA.x; v[a][4] -= dl * IA.y; v[a][5] -= dl * IA.z;
+          va = f3(v[a][0], v[a][1], v[a][2]);
+          wa = f3(v[a][3], v[a][4], v[a][5]);
+          vba = VB.v3(6 * a);
+          wba = VB.v3(6 * a + 3);
+          dbar += im[a] * dot3(lin, vba) + dot3(IA, wba);
+        }
+        if (b >= 0) {
+          const float3 IB = symv(ib, angB);
+          const float c = dl * im[b];
+          v[b][0] += c * lin.x; v[b][1] += c * lin.y; v[b][2] += c * lin.z;
+          v[b][3] -= dl * IB.x; v[b][4] -= dl * IB.y; v[b][5] -= dl * IB.z;
+          vb3 = f3(v[b][0], v[b][1], v[b][2]);
+          wb3 = f3(v[b][3], v[b][4], v[b][5]);
+          vbb = VB.v3(6 * b);
+          wbb = VB.v3(6 * b + 3);
+          dbar += -im[b] * dot3(lin, vbb) + dot3(IB, wbb);
+        }
+        float3 linb = dl * ((a >= 0 ? im[a] : 0.f) * vba - (b >= 0 ? im[b] : 0.f) * vbb);
+        float3 angAb = f3(0.f, 0.f, 0.f), angBb = angAb;
+        if (a >= 0) {
+          const float3 g = dl * wba;
+          angAb += symv(ia, g);
+          const int ib9 = T.sm_iinvb + 9 * a;
+          S[ib9 + 0] += g.x * angA.x; S[ib9 + 1] += g.x * angA.y; S[ib9 + 2] += g.x * angA.z;
+          S[ib9 + 3] += g.y * angA.x; S[ib9 + 4] += g.y * angA.y; S[ib9 + 5] += g.y * angA.z;
+          S[ib9 + 6] += g.z * angA.x; S[ib9 + 7] += g.z * angA.y; S[ib9 + 8] += g.z * angA.z;
+          if constexpr (!lin_is_zero<kind>()) S[T.sm_invmb + a] += dl * dot3(lin, vba);
+        }
+        if (b >= 0) {
+          const float3 g = dl * wbb;
+          angBb += symv(ib, g);
+          const int ib9 = T.sm_iinvb + 9 * b;
+          S[ib9 + 0] += g.x * angB.x; S[ib9 + 1] += g.x * angB.y; S[ib9 + 2] += g.x * angB.z;
+          S[ib9 + 3] += g.y * angB.x; S[ib9 + 4] += g.y * angB.y; S[ib9 + 5] += g.y * angB.z;
+          S[ib9 + 6] += g.z * angB.x; S[ib9 + 7] += g.z * angB.y; S[ib9 + 8] += g.z * angB.z;
+          if constexpr (!lin_is_zero<kind>()) S[T.sm_invmb + b] -= dl * dot3(lin, vbb);
+        }
+        const float lbar_a = S[T.sm_lam + s] + dbar;
+        const int rc = s * RC_N;
+        const float inside = br == 0 ? 1.f : 0.f;
+        const float sg = br == 2 ? 1.f : (br == 1 ? -1.f : 0.f);
+        const float pbar = inside * lbar_a;
+        if constexpr (kind == RK_GT || kind == RK_PT) {
+          constexpr int ns_ = Q::S.normal[s];
+          RC[rc + RC_BND] += sg * cur.lnrm * lbar_a;
+          S[T.sm_lam + ns_] += sg * cur.bnd * lbar_a;
+        } else if constexpr (kind == RK_MOTOR) {
+          RC[rc + RC_BND] += sg * lbar_a;
+        }
+        float Jv = 0.f;
+        if (a >= 0) Jv += dot3(lin, va) + dot3(angA, wa);
+        if (b >= 0) Jv += dot3(angB, wb3) - dot3(lin, vb3);
+        RC[rc + RC_MEFF] += -pbar * (Jv + bias + gamma * lb);
+        const float jvb = -meff * pbar;
+        RC[rc + RC_BIAS] += jvb;
+        if (a >= 0) {
+          VB.s3(6 * a, vba + jvb * lin);
+          VB.s3(6 * a + 3, wba + jvb * angA);
+          linb += jvb * va;
+          angAb += jvb * wa;
+        }
+        if (b >= 0) {
+          VB.s3(6 * b, vbb - jvb * lin);
+          VB.s3(6 * b + 3, wbb + jvb * angB);
+          linb -= jvb * vb3;
+          angBb += jvb * wb3;
+        }
+        if constexpr (!lin_is_constant<kind, Q::S.sub[s]>() && !lin_is_zero<kind>()) RC.a3(rc + RC_LIN, linb);
+        if (a >= 0) RC.a3(rc + RC_ANGA, angAb);
+        if (b >= 0) RC.a3(rc + RC_ANGB, angBb);
+        S[T.sm_lam + s] = -dbar + pbar * (1.f - meff * gamma);
       }
-      const float dl = la - lb;
-      float dbar = 0.f;
-      float3 va = f3(0.f, 0.f, 0.f), wa = va, vb3 = va, wb3 = va, vba = va, wba = va, vbb = va, wbb = va;
-      if (a >= 0) {
-        const float3 IA = symv(ia, angA);
-        const float c = dl * im[a];
-        v[a][0] -= c * lin.x; v[a][1] -= c * lin.y; v[a][2] -= c * lin.z;
-        v[a][3] -= dl * IA.x; v[a][4] -= dl * IA.y; v[a][5] -= dl * IA.z;
-        va = f3(v[a][0], v[a][1], v[a][2]);
-        wa = f3(v[a][3], v[a][4], v[a][5]);
-        vba = VB.v3(6 * a);
-        wba = VB.v3(6 * a + 3);
-        dbar += im[a] * dot3(lin, vba) + dot3(IA, wba);
-      }
-      if (b >= 0) {
-        const float3 IB = symv(ib, angB);
-        const float c = dl * im[b];
-        v[b][0] += c * lin.x; v[b][1] += c * lin.y; v[b][2] += c * lin.z;
-        v[b][3] -= dl * IB.x; v[b][4] -= dl * IB.y; v[b][5] -= dl * IB.z;
-        vb3 = f3(v[b][0], v[b][1], v[b][2]);
-        wb3 = f3(v[b][3], v[b][4], v[b][5]);
-        vbb = VB.v3(6 * b);
-        wbb = VB.v3(6 * b + 3);
-        dbar += -im[b] * dot3(lin, vbb) + dot3(IB, wbb);
-      }
-      float3 linb = dl * ((a >= 0 ? im[a] : 0.f) * vba - (b >= 0 ? im[b] : 0.f) * vbb);
-      float3 angAb = f3(0.f, 0.f, 0.f), angBb = angAb;
-      if (a >= 0) {
-        const float3 g = dl * wba;
-        angAb += symv(ia, g);
-        const int ib9 = T.sm_iinvb + 9 * a;
-        S[ib9 + 0] += g.x * angA.x; S[ib9 + 1] += g.x * angA.y; S[ib9 + 2] += g.x * angA.z;
-        S[ib9 + 3] += g.y * angA.x; S[ib9 + 4] += g.y * angA.y; S[ib9 + 5] += g.y * angA.z;
-        S[ib9 + 6] += g.z * angA.x; S[ib9 + 7] += g.z * angA.y; S[ib9 + 8] += g.z * angA.z;
-        if constexpr (!lin_is_zero<kind>()) S[T.sm_invmb + a] += dl * dot3(lin, vba);
-      }
-      if (b >= 0) {
-        const float3 g = dl * wbb;
-        angBb += symv(ib, g);
-        const int ib9 = T.sm_iinvb + 9 * b;
-        S[ib9 + 0] += g.x * angB.x; S[ib9 + 1] += g.x * angB.y; S[ib9 + 2] += g.x * angB.z;
-        S[ib9 + 3] += g.y * angB.x; S[ib9 + 4] += g.y * angB.y; S[ib9 + 5] += g.y * angB.z;
-        S[ib9 + 6] += g.z * angB.x; S[ib9 + 7] += g.z * angB.y; S[ib9 + 8] += g.z * angB.z;
-        if constexpr (!lin_is_zero<kind>()) S[T.sm_invmb + b] -= dl * dot3(lin, vbb);
-      }
-      const float lbar_a = S[T.sm_lam + s] + dbar;
-      const int rc = s * RC_N;
-      const float inside = br == 0 ? 1.f : 0.f;
-      const float sg = br == 2 ? 1.f : (br == 1 ? -1.f : 0.f);
-      const float pbar = inside * lbar_a;
-      if constexpr (kind == RK_GT || kind == RK_PT) {
-        constexpr int ns_ = Q::S.normal[s];
-        RC[rc + RC_BND] += sg * lnrm * lbar_a;
-        S[T.sm_lam + ns_] += sg * bnd * lbar_a;
-      } else if constexpr (kind == RK_MOTOR) {
-        RC[rc + RC_BND] += sg * lbar_a;
-      }
-      float Jv = 0.f;
-      if (a >= 0) Jv += dot3(lin, va) + dot3(angA, wa);
-      if (b >= 0) Jv += dot3(angB, wb3) - dot3(lin, vb3);
-      RC[rc + RC_MEFF] += -pbar * (Jv + bias + gamma * lb);
-      const float jvb = -meff * pbar;
-      RC[rc + RC_BIAS] += jvb;
-      if (a >= 0) {
-        VB.s3(6 * a, vba + jvb * lin);
-        VB.s3(6 * a + 3, wba + jvb * angA);
-        linb += jvb * va;
-        angAb += jvb * wa;
-      }
-      if (b >= 0) {
-        VB.s3(6 * b, vbb - jvb * lin);
-        VB.s3(6 * b + 3, wbb + jvb * angB);
-        linb -= jvb * vb3;
-        angBb += jvb * wb3;
-      }
-      if constexpr (!lin_is_constant<kind, sub>() && !lin_is_zero<kind>()) RC.a3(rc + RC_LIN, linb);
-      if (a >= 0) RC.a3(rc + RC_ANGA, angAb);
-      if (b >= 0) RC.a3(rc + RC_ANGB, angBb);
-      S[T.sm_lam + s] = -dbar + pbar * (1.f - meff * gamma);
-      lc[s] = lb;
+      cur = nxt;
     });
   }
 }
