@@ -390,6 +390,7 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
   }
   T.n_params = (int)np_;
   T.ws = 0;
+  T.ws_net = 0;
   T.ws_alpha = 0.7f;
   T.grad_decay = d->grad_decay > 0.f ? d->grad_decay : 1.f;
   T.mlp_tc = T.n_layers == 3 && !T.skip && T.ctrl_round && T.widths[0] == CtrlTC::K0 && T.widths[1] == CtrlTC::H1 &&
@@ -755,6 +756,14 @@ dp_status dp_set_warmstart(dp_world* w, const float* W, float alpha) {
   CU(cudaMemcpyAsync(w->ws_master, W, sizeof(float) * WsTC::PARAMS, cudaMemcpyDefault, w->stream));
   CU(launch_ws_prep(w->ws_master, w->ws_tc, w->ws_b, w->stream));
   w->Tf.ws = w->Tb.ws = 1;
+  {  // an identically zero network is the damped start: the kernels skip its evaluation
+    std::vector<float> hw(WsTC::PARAMS);
+    CU(cudaMemcpyAsync(hw.data(), w->ws_master, sizeof(float) * WsTC::PARAMS, cudaMemcpyDeviceToHost, w->stream));
+    CU(cudaStreamSynchronize(w->stream));
+    int nz = 0;
+    for (float x : hw) nz |= x != 0.f;
+    w->Tf.ws_net = w->Tb.ws_net = nz;
+  }
   return DP_OK;
 }
 

@@ -51,6 +51,7 @@ struct DevTopo {
   int ext_ctrl, ext_k0p, ext_nop;  // padded input width (multiple of 64) and output width (8)
   int ws;       // 1: the solve starts from the learned warm start (DevPtrs.ws_tc, ws_alpha)
   float ws_alpha;  // weight of the previous step's impulses in the warm start
+  int ws_net;      // 0: the network is identically zero (the damped start alpha * previous impulses)
   float grad_decay;  // reverse mode: state adjoint x alpha per step (section 3.2); 1 = none
   int sm_ws;    // warm-start scratch per lane: features [16], outputs [3], harvest row ids [n_wsg]
   // warm-start groups of three rows (slot -1: none): joint linear rows, hinge angular rows with

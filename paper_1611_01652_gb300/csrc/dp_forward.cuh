@@ -517,26 +517,38 @@ __device__ __forceinline__ void row_apply(const DevTopo& T, const SL& S, const R
 template <bool TAPE, class RV>
 __device__ void warm_start(const DevTopo& T, const DevPtrs& D, const LaneT<RV>& L, const SL& X, const TapeStep& tp) {
   const SL& S = L.S;
+  const bool harvest = D.harvest != nullptr;
+  // the features are needed by a nonzero network and by the harvest; with an identically zero
+  // network the start is alpha * (previous impulses) + m_eff * 0, computed without them
+  const bool feat = harvest || (T.ws && T.ws_net);
   float mtot = 0.f;
   float3 pc = f3(0.f, 0.f, 0.f);
-  for (int b = 0; b < T.nb; ++b) {
-    const float m = L.P[T.o_mass + b];
-    mtot += m;
-    pc += m * X.v3(18 * b);
-  }
-  pc = (1.f / mtot) * pc;
   int nact = 0;
-  for (int s = 0; s < T.nslots; ++s)
-    if ((T.skind[s] == RK_GN || T.skind[s] == RK_PN) && L.rows[s * RF_N + RF_MEFF] != 0.f) ++nact;
-  const float gn = sqrtf(T.gravity[0] * T.gravity[0] + T.gravity[1] * T.gravity[1] + T.gravity[2] * T.gravity[2]);
-  const float share = mtot * gn * T.dt / (float)max(1, nact);
+  float share = 0.f;
+  if (feat) {
+    for (int b = 0; b < T.nb; ++b) {
+      const float m = L.P[T.o_mass + b];
+      mtot += m;
+      pc += m * X.v3(18 * b);
+    }
+    pc = (1.f / mtot) * pc;
+    for (int s = 0; s < T.nslots; ++s)
+      if ((T.skind[s] == RK_GN || T.skind[s] == RK_PN) && L.rows[s * RF_N + RF_MEFF] != 0.f) ++nact;
+    const float gn = sqrtf(T.gravity[0] * T.gravity[0] + T.gravity[1] * T.gravity[1] + T.gravity[2] * T.gravity[2]);
+    share = mtot * gn * T.dt / (float)max(1, nact);
+  }
   const SL F = S.at(T.sm_ws), Y = S.at(T.sm_ws + 16), H = S.at(T.sm_ws + 19);
-  const bool harvest = D.harvest != nullptr;
   const int lane = threadIdx.x & 31;
   for (int g = 0; g < T.n_wsg; ++g) {
     const int type = T.wsg_type[g];
     const int s0 = T.wsg_slot[g][0], s1 = T.wsg_slot[g][1], s2 = T.wsg_slot[g][2];
     const bool contact = type == WSG_GROUND || type == WSG_PAIR;
+    float lp[3];  // impulses the group's rows ended the previous step with
+    for (int k = 0; k < 3; ++k) {
+      const int s = T.wsg_slot[g][k];
+      lp[k] = s >= 0 ? S[T.sm_lam + s] : 0.f;
+    }
+    if (feat) {
     float3 q;  // the group's point: contact point on body a, or the joint's anchor on its child
     if (type == WSG_GROUND) {
       const int qi = T.sidx[s0], a = T.sa[s0];
@@ -549,7 +561,6 @@ __device__ void warm_start(const DevTopo& T, const DevPtrs& D, const LaneT<RV>& 
       const int j = T.sidx[s0], b = T.sb[s0];
       q = X.v3(18 * b) + mv(loadR(X, 18 * b), L.P.v3(T.o_anchor + 6 * j + 3));
     }
-    float lp[3];  // impulses the group's rows ended the previous step with
     for (int k = 0; k < 3; ++k) {
       const int s = T.wsg_slot[g][k];
       const RV R = L.rows.at((s >= 0 ? s : 0) * RF_N);
@@ -557,7 +568,6 @@ __device__ void warm_start(const DevTopo& T, const DevPtrs& D, const LaneT<RV>& 
       F[k] = on ? row_jv(T, R, X, T.sa[s], T.sb[s]) : 0.f;
       F[3 + k] = on ? R[RF_BIAS] : 0.f;
       F[6 + k] = on ? R[RF_MEFF] : 0.f;
-      lp[k] = s >= 0 ? S[T.sm_lam + s] : 0.f;
     }
     F[9] = contact ? L.rows[s1 * RF_N + RF_BND] : (type == WSG_HINGE && s2 >= 0 ? L.rows[s2 * RF_N + RF_BND] : 0.f);
     F[10] = q.x - pc.x;
@@ -566,6 +576,7 @@ __device__ void warm_start(const DevTopo& T, const DevPtrs& D, const LaneT<RV>& 
     F[13] = share;
     F[14] = q.z - T.ground_z;
     F[15] = (float)type;
+    }
     const bool active = L.rows[s0 * RF_N + RF_MEFF] != 0.f;
     if (harvest) {  // padded lanes (copies of the last instance) harvest nothing
       const unsigned m = __ballot_sync(FULLMASK, active && L.i < T.B);
@@ -581,14 +592,18 @@ __device__ void warm_start(const DevTopo& T, const DevPtrs& D, const LaneT<RV>& 
       }
     }
     if (T.ws) {
-      __syncwarp();
-      mlp3_forward<WsTC::K0, WsTC::H1, WsTC::H2, WsTC::NO>(
-          [&](int f, int r) { return F.lane_at(f, r); }, D.ws_tc + WsTC::W1, D.ws_b + WsTC::B1, D.ws_tc + WsTC::W2,
-          D.ws_b + WsTC::B2, D.ws_tc + WsTC::W3, D.ws_b + WsTC::B3,
-          [&](int f, int r, float v) { Y.lane_at(f, r) = v; }, [](int, int, int, float) {});
-      __syncwarp();
       float z[3];
-      for (int k = 0; k < 3; ++k) z[k] = T.ws_alpha * lp[k] + F[6 + k] * Y[k];
+      if (T.ws_net) {
+        __syncwarp();
+        mlp3_forward<WsTC::K0, WsTC::H1, WsTC::H2, WsTC::NO>(
+            [&](int f, int r) { return F.lane_at(f, r); }, D.ws_tc + WsTC::W1, D.ws_b + WsTC::B1, D.ws_tc + WsTC::W2,
+            D.ws_b + WsTC::B2, D.ws_tc + WsTC::W3, D.ws_b + WsTC::B3,
+            [&](int f, int r, float v) { Y.lane_at(f, r) = v; }, [](int, int, int, float) {});
+        __syncwarp();
+        for (int k = 0; k < 3; ++k) z[k] = T.ws_alpha * lp[k] + F[6 + k] * Y[k];
+      } else {
+        for (int k = 0; k < 3; ++k) z[k] = T.ws_alpha * lp[k];
+      }
       if (contact) {
         float l0[3] = {0.f, 0.f, 0.f};
         if (active) {

@@ -299,9 +299,17 @@ __device__ __noinline__ void pgs_reverse_static(const DevTopo& T, const LaneT<GS
   const SL VB = S.at(T.sm_vb), RC = S.at(T.sm_rc);
   const float gamma = T.gamma;
   const int iters = T.iters;
-  float v[NB][6], im[NB];
+  // v: working velocities; ib9r, imbr: adjoints of the world inverse inertias and inverse
+  // masses, summed in registers over the sweeps (added to their zeroed shared-memory
+  // accumulators at the end, so the sums are the same)
+  float v[NB][6], im[NB], ib9r[NB][9], imbr[NB];
 #pragma unroll
-  for (int b = 0; b < NB; ++b) im[b] = S[T.sm_invm + b];
+  for (int b = 0; b < NB; ++b) {
+    im[b] = S[T.sm_invm + b];
+    imbr[b] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) ib9r[b][k] = 0.f;
+  }
   unsigned live[NW];
 #pragma unroll
   for (int w = 0; w < NW; ++w) live[w] = 0u;
@@ -381,20 +389,20 @@ __device__ __noinline__ void pgs_reverse_static(const DevTopo& T, const LaneT<GS
         if (a >= 0) {
           const float3 g = dl * wba;
           angAb += symv(ia, g);
-          const int ib9 = T.sm_iinvb + 9 * a;
-          S[ib9 + 0] += g.x * angA.x; S[ib9 + 1] += g.x * angA.y; S[ib9 + 2] += g.x * angA.z;
-          S[ib9 + 3] += g.y * angA.x; S[ib9 + 4] += g.y * angA.y; S[ib9 + 5] += g.y * angA.z;
-          S[ib9 + 6] += g.z * angA.x; S[ib9 + 7] += g.z * angA.y; S[ib9 + 8] += g.z * angA.z;
-          if constexpr (!lin_is_zero<kind>()) S[T.sm_invmb + a] += dl * dot3(lin, vba);
+          float* q = ib9r[a];
+          q[0] += g.x * angA.x; q[1] += g.x * angA.y; q[2] += g.x * angA.z;
+          q[3] += g.y * angA.x; q[4] += g.y * angA.y; q[5] += g.y * angA.z;
+          q[6] += g.z * angA.x; q[7] += g.z * angA.y; q[8] += g.z * angA.z;
+          if constexpr (!lin_is_zero<kind>()) imbr[a] += dl * dot3(lin, vba);
         }
         if (b >= 0) {
           const float3 g = dl * wbb;
           angBb += symv(ib, g);
-          const int ib9 = T.sm_iinvb + 9 * b;
-          S[ib9 + 0] += g.x * angB.x; S[ib9 + 1] += g.x * angB.y; S[ib9 + 2] += g.x * angB.z;
-          S[ib9 + 3] += g.y * angB.x; S[ib9 + 4] += g.y * angB.y; S[ib9 + 5] += g.y * angB.z;
-          S[ib9 + 6] += g.z * angB.x; S[ib9 + 7] += g.z * angB.y; S[ib9 + 8] += g.z * angB.z;
-          if constexpr (!lin_is_zero<kind>()) S[T.sm_invmb + b] -= dl * dot3(lin, vbb);
+          float* q = ib9r[b];
+          q[0] += g.x * angB.x; q[1] += g.x * angB.y; q[2] += g.x * angB.z;
+          q[3] += g.y * angB.x; q[4] += g.y * angB.y; q[5] += g.y * angB.z;
+          q[6] += g.z * angB.x; q[7] += g.z * angB.y; q[8] += g.z * angB.z;
+          if constexpr (!lin_is_zero<kind>()) imbr[b] -= dl * dot3(lin, vbb);
         }
         const float lbar_a = S[T.sm_lam + s] + dbar;
         const int rc = s * RC_N;
@@ -433,5 +441,11 @@ __device__ __noinline__ void pgs_reverse_static(const DevTopo& T, const LaneT<GS
       }
       cur = nxt;
     });
+  }
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    S[T.sm_invmb + b] += imbr[b];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) S[T.sm_iinvb + 9 * b + k] += ib9r[b][k];
   }
 }

@@ -163,7 +163,12 @@ def oracle_ws_trajectory(m, i, horizon):
     return xs, lps
 
 
-@pytest.mark.parametrize("net", ["trained-like", "constant"])
+def zero_network():
+    """The damped previous-impulse start (the kernels skip evaluating an all-zero network)."""
+    return np.zeros(O.WS_PARAMS, np.float32)
+
+
+@pytest.mark.parametrize("net", ["trained-like", "constant", "zero"])
 def test_warm_started_steps_match_oracle(net):
     """Teacher-forced warm-started steps from the oracle's state and previous impulses: next
     state within 1e-4, impulses after the solve within 1e-3 and the residual of the solve within
@@ -172,7 +177,7 @@ def test_warm_started_steps_match_oracle(net):
     such roundings may go either way."""
     m = WL.quadruped(B=16, horizon=80)
     m.ctrl_fp32 = 1
-    Wws = small_network() if net == "trained-like" else constant_network()
+    Wws = {"trained-like": small_network, "constant": constant_network, "zero": zero_network}[net]()
     m.warmstart, m.ws_W, m.ws_alpha = 1, Wws.astype(np.float64), 0.7
     gate = 1e-6 if net == "trained-like" else -1.0
     trajs = [oracle_ws_trajectory(m, i, 80) for i in range(m.B)]
@@ -210,15 +215,15 @@ def test_warm_started_steps_match_oracle(net):
     assert checked >= (0.1 if net == "trained-like" else 0.9) * m.B * len(range(3, 80, 11))
 
 
-@pytest.mark.parametrize("ckpt", [None, 8])
-def test_warm_started_gradients_match_oracle(ckpt):
+@pytest.mark.parametrize("ckpt,net", [(None, "constant"), (8, "constant"), (None, "zero")])
+def test_warm_started_gradients_match_oracle(ckpt, net):
     """Reverse mode through warm-started rollouts (start alpha lambda_prev + constant network
     output, treated as constant) against the oracle's gradient of the same function; 30 steps,
     fp32 controller; the whole tape recorded by the rollout, or 8-step segments recomputed from
     checkpoints of the state and of the previous impulses."""
     m = WL.quadruped(B=4, horizon=30)
     m.ctrl_fp32 = 1
-    Wws = constant_network()
+    Wws = constant_network() if net == "constant" else zero_network()
     m.warmstart, m.ws_W, m.ws_alpha = 1, Wws.astype(np.float64), 0.7
     w = World(m, horizon=30, warmstart=True, ckpt_every=ckpt)
     w.set_warmstart(torch.tensor(Wws, device="cuda"), 0.7)
