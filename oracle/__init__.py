@@ -54,7 +54,7 @@ class Topo(C.Structure):
                 ("beta", C.c_double), ("gamma", C.c_double), ("slop", C.c_double), ("iters", C.c_int32),
                 ("loss_kind", C.c_int32), ("loss_mode", C.c_int32), ("loss_body", C.c_int32),
                 ("exact_mlp", C.c_int32), ("warmstart", C.c_int32), ("ws_W", PD), ("ws_alpha", C.c_double),
-                ("grad_decay", C.c_double)]
+                ("grad_decay", C.c_double), ("n_recurrent", C.c_int32)]
 
 WS_IN, WS_H, WS_OUT = 16, 64, 3
 WS_PARAMS = WS_IN * WS_H + WS_H + WS_H * WS_H + WS_H + WS_H * WS_OUT + WS_OUT
@@ -126,6 +126,7 @@ def topo(m, keep, iters=None):
     t.ws_W = keep.f64(ws) if t.warmstart else None
     t.ws_alpha = float(getattr(m, "ws_alpha", 0.7))
     t.grad_decay = float(getattr(m, "grad_decay", 1.0))
+    t.n_recurrent = int(getattr(m, "n_recurrent", 0))
     return t
 
 
@@ -253,12 +254,13 @@ def flops(m, i=0, horizon=None, W=None):
     return tuple(out)
 
 
-def step_log(m, i, x, t=0, W=None, iters=None, lam_prev=None):
+def step_log(m, i, x, t=0, W=None, iters=None, lam_prev=None, h_prev=None):
     """One step from state ``x`` with the full step record: dict with ``xn`` [nb, 18], ``active``,
     ``gap``, ``lam`` (final impulses), ``lam0`` (initial impulses), ``margin`` (bfloat16 tie
     margin), ``resid`` (RMS residual of the solve) and ``feats`` [groups, 16] (warm-start
-    features of every group, see ``ws_groups``). ``lam_prev`` [n_slots]: the impulses the
-    previous step ended with (default zeros)."""
+    features of every group, see ``ws_groups``) and ``h`` (the controller's next recurrent
+    state). ``lam_prev`` [n_slots]: the impulses the previous step ended with (default zeros);
+    ``h_prev`` [n_recurrent]: the controller's recurrent state (default zeros)."""
     keep = _Keep()
     tp = topo(m, keep, iters)
     s = inst(m, i, keep)
@@ -270,14 +272,34 @@ def step_log(m, i, x, t=0, W=None, iters=None, lam_prev=None):
     gap, lam, lam0 = np.zeros(max(ns, 1)), np.zeros(max(ns, 1)), np.zeros(max(ns, 1))
     marg, resid = np.zeros(1), np.zeros(1)
     feats = np.zeros((max(nc, 1), WS_IN))
+    H = int(getattr(m, "n_recurrent", 0))
+    hn = np.zeros(max(H, 1))
     r = lib().orc_step_log(C.byref(tp), C.byref(s), weights(m, keep, W), t, _dp(x), _dp(xn),
                            active.ctypes.data_as(C.POINTER(C.c_int8)), _dp(gap), _dp(lam), _dp(marg), _dp(resid),
                            _dp(feats), _dp(lam0),
-                           keep.f64(lam_prev) if lam_prev is not None else None)
+                           keep.f64(lam_prev) if lam_prev is not None else None,
+                           keep.f64(h_prev) if h_prev is not None else None, _dp(hn))
     if r != 0:
         raise ValueError("oracle rejected the model")
     return dict(xn=xn.reshape(m.nb, 18), active=active[:ns], gap=gap[:ns], lam=lam[:ns], lam0=lam0[:ns],
-                margin=float(marg[0]), resid=float(resid[0]), feats=feats[:nc])
+                margin=float(marg[0]), resid=float(resid[0]), feats=feats[:nc], h=hn[:H])
+
+
+def rollout_rec(m, i, horizon=None, W=None, iters=None):
+    """Rollout of instance ``i`` with the controller's recurrent state of every step:
+    (states [T+1, nb, 18], loss, h [T+1, n_recurrent]); h[0] = 0."""
+    T = m.horizon if horizon is None else horizon
+    keep = _Keep()
+    t = topo(m, keep, iters)
+    s = inst(m, i, keep)
+    H = int(getattr(m, "n_recurrent", 0))
+    states = np.zeros((T + 1, m.nb, 18))
+    hs = np.zeros((T + 1, max(H, 1)))
+    loss = C.c_double(0.0)
+    r = lib().orc_rollout_rec(C.byref(t), C.byref(s), weights(m, keep, W), T, _dp(states), C.byref(loss), _dp(hs))
+    if r != 0:
+        raise ValueError("oracle rejected the model")
+    return states, loss.value, hs[:, :H]
 
 
 def rollout_resid(m, i, horizon=None, W=None, iters=None):

@@ -16,8 +16,9 @@
 //   * semi-implicit Euler: the new velocities are integrated to give the new positions;
 //   * branchless sphere contact detection (every slot is evaluated, inactive slots are masked);
 //   * servo motors with gain, maximal torque and maximal velocity.
-// The controller is the dense policy of Eq. g (section 2.2) without the recurrent part;
-// the rollout loss is Eq. L. Gradients are reverse mode through the whole rollout
+// The controller is the dense policy of Eq. g (section 2.2), optionally with its recurrent
+// state h^t (h^0 = 0): the network reads [features, h^t] and its last outputs, through tanh,
+// give h^{t+1}; the rollout loss is Eq. L. Gradients are reverse mode through the whole rollout
 // (section 2.1.1, back-propagation through time), obtained here with a plain operator-
 // overloading tape that records every arithmetic operation of one step.
 //
@@ -87,6 +88,10 @@ inline AD atan2(AD y, AD x) {
   double d = x.v * x.v + y.v * y.v;
   return mk(std::atan2(y.v, x.v), y.id, x.v / d, x.id, -y.v / d);
 }
+inline AD tanh(AD a) {
+  double r = std::tanh(a.v);
+  return mk(r, a.id, 1.0 - r * r, -1, 0.0);
+}
 
 // Counting scalar: every arithmetic operation and elementary function adds one to g_flops
 // (the instrumented counter that gives the algorithmic work of one step).
@@ -108,6 +113,7 @@ inline CNT sqrt(CNT a) { g_flops += 1; return CNT(std::sqrt(a.v)); }
 inline CNT sin(CNT a) { g_flops += 1; return CNT(std::sin(a.v)); }
 inline CNT cos(CNT a) { g_flops += 1; return CNT(std::cos(a.v)); }
 inline CNT atan2(CNT y, CNT x) { g_flops += 1; return CNT(std::atan2(y.v, x.v)); }
+inline CNT tanh(CNT a) { g_flops += 1; return CNT(std::tanh(a.v)); }
 
 inline double val(double x) { return x; }
 inline double val(const AD& x) { return x.v; }
@@ -116,6 +122,7 @@ using std::sqrt;
 using std::sin;
 using std::cos;
 using std::atan2;
+using std::tanh;
 
 // Round to bfloat16 (8 significant bits), round-to-nearest-even. Straight-through
 // derivative for the AD type (the rounding is treated as the identity in reverse mode).
@@ -246,6 +253,8 @@ typedef struct {
   const double* ws_W;          // warm-start network parameters [ORC_WS_PARAMS]
   double ws_alpha;             // weight of the previous step's impulses in the warm start
   double grad_decay;           // section 3.2: adjoint passed from step t+1 back to step t times alpha
+  int32_t n_recurrent;         // H: recurrent state of the controller (Eq. g), the last H inputs and
+                               //    outputs of the network; 0 = feed-forward
 } orc_topo;
 
 // Learned warm start: a 16-64-64-3 network per contact (W1, b1, W2, b2, W3, b3; W[out][in]).
@@ -466,7 +475,8 @@ template <class S> static S loss_initial(const orc_topo& T, const Inst<S>& P, co
 template <class S>
 static void step(const orc_topo& T, const std::vector<Slot>& slots, const std::vector<int>& order, const Inst<S>& P,
                  const std::vector<S>& W, int t, const std::vector<S>& x, std::vector<S>& xn, double w_next, S* loss,
-                 StepLog* log, const double* lam_prev = nullptr, double* lam_out = nullptr) {
+                 StepLog* log, const double* lam_prev = nullptr, double* lam_out = nullptr,
+                 const std::vector<S>* h_in = nullptr, std::vector<S>* h_out = nullptr) {
   const double h = T.dt;
   const int nb = T.nb, nj = T.nj;
   g_exact_mlp = T.exact_mlp != 0;
@@ -500,9 +510,13 @@ static void step(const orc_topo& T, const std::vector<Slot>& slots, const std::v
   for (int j = 0; j < nj; ++j)
     if (T.joint_type[j] == ORC_HINGE && (T.joint_flags[j] & ORC_FLAG_MOTOR)) motors.push_back(j);
 
-  // Controller (Eq. g, feed-forward): features -> dense ReLU layers -> linear output.
-  // bfloat16 storage points: the input vector, every weight, every hidden activation.
+  // Controller (Eq. g): [features, h^t] -> dense ReLU layers -> linear output; the first outputs
+  // are the motor signals u^t, the last H give the next recurrent state h^{t+1} = tanh(.).
+  // bfloat16 storage points: the input vector (h^t included), every weight, every hidden
+  // activation; h^{t+1} itself is kept in full precision.
   std::vector<S> u(motors.size(), S(0.0));
+  const int H = T.n_recurrent;
+  if (h_out) h_out->assign(H, S(0.0));
   if (T.n_layers > 0) {
     std::vector<S> s;
     if (T.features & ORC_F_ANGLES) for (int j : motors) s.push_back(theta[j]);
@@ -523,7 +537,8 @@ static void step(const orc_topo& T, const std::vector<Slot>& slots, const std::v
       V3<S> d = vsub(loss_point_of(T, P, x), get3(P.loss_target, 0));
       for (int k = 0; k < 3; ++k) s.push_back(d[k]);
     }
-    s.resize(T.widths[0], S(0.0));
+    s.resize(T.widths[0] - H, S(0.0));
+    for (int k = 0; k < H; ++k) s.push_back(h_in ? (*h_in)[k] : S(0.0));
     for (auto& e : s) e = round_bf16(e);
     std::vector<S> a = s;
     size_t off = 0;
@@ -548,6 +563,8 @@ static void step(const orc_topo& T, const std::vector<Slot>& slots, const std::v
       a = z;
     }
     for (size_t m = 0; m < motors.size() && m < a.size(); ++m) u[m] = a[m];
+    if (h_out)
+      for (int k = 0; k < H; ++k) (*h_out)[k] = tanh(a[a.size() - H + k]);
   }
 
   // Servo: target joint rate w* = clamp(k (u - theta), -vmax, vmax).
@@ -909,6 +926,10 @@ static int check_topo(const orc_topo* T) {
     if (k < 0 || l < 0 || k >= T->ns || l >= T->ns || T->sphere_body[k] == T->sphere_body[l]) return -1;
   }
   if (T->loss_body < 0 || T->loss_body >= T->nb) return -1;
+  if (T->n_recurrent < 0) return -1;
+  if (T->n_recurrent > 0 &&
+      (T->n_layers < 1 || T->skip || T->widths[0] <= T->n_recurrent || T->widths[T->n_layers] <= T->n_recurrent))
+    return -1;
   return 0;
 }
 
@@ -967,10 +988,12 @@ int orc_schedule(const orc_topo* T, int32_t* kind, int32_t* idx, int32_t* sub, i
 
 // One step from a given state (used for teacher-forced comparisons), with the solve's residual,
 // the warm-start features of every group [orc_ws_groups][16] and the initial impulses [n_slots];
-// lam_prev [n_slots] (or NULL: zeros) are the impulses the previous step ended with.
+// lam_prev [n_slots] (or NULL: zeros) are the impulses the previous step ended with; h_prev
+// [n_recurrent] (or NULL: zeros) the controller's recurrent state, h_next (optional) receives
+// the next one.
 int orc_step_log(const orc_topo* T, const orc_inst* I, const double* W, int32_t t, const double* x, double* xn,
                  int8_t* active, double* gap, double* lambda, double* bf16_margin, double* resid, double* feats,
-                 double* lam0, const double* lam_prev) {
+                 double* lam0, const double* lam_prev, const double* h_prev, double* h_next) {
   if (check_topo(T)) return -1;
   auto slots = make_slots(*T);
   std::vector<int> col, ord;
@@ -982,8 +1005,12 @@ int orc_step_log(const orc_topo* T, const orc_inst* I, const double* W, int32_t 
   std::vector<int8_t> act(slots.size());
   std::vector<double> gp(slots.size());
   StepLog lg{active ? active : act.data(), gap ? gap : gp.data(), lambda, bf16_margin, resid, feats, lam0};
-  step<double>(*T, slots, ord, P, Wv, t, xs, xo, 0.0, nullptr, &lg, lam_prev);
+  const int H = T->n_recurrent;
+  std::vector<double> hin(H, 0.0), hout;
+  if (h_prev) std::copy(h_prev, h_prev + H, hin.begin());
+  step<double>(*T, slots, ord, P, Wv, t, xs, xo, 0.0, nullptr, &lg, lam_prev, nullptr, &hin, &hout);
   std::memcpy(xn, xo.data(), sizeof(double) * xo.size());
+  if (h_next && H > 0) std::memcpy(h_next, hout.data(), sizeof(double) * H);
   return 0;
 }
 
@@ -1067,7 +1094,12 @@ int orc_rollout(const orc_topo* T, const orc_inst* I, const double* W, int32_t h
 }
 static int rollout_impl(const orc_topo* T, const orc_inst* I, const double* W, int32_t horizon, double* states,
                         double* loss, int8_t* active, double* gap, double* bf16_margin, double* resid,
-                        std::vector<double>* lam_prevs);
+                        std::vector<double>* lam_prevs, double* hs = nullptr);
+// Rollout with the controller's recurrent state of every step [horizon + 1][n_recurrent] (h^0 = 0).
+int orc_rollout_rec(const orc_topo* T, const orc_inst* I, const double* W, int32_t horizon, double* states,
+                    double* loss, double* hs) {
+  return rollout_impl(T, I, W, horizon, states, loss, nullptr, nullptr, nullptr, nullptr, nullptr, hs);
+}
 // orc_rollout that also gives the residual of every step's solve [horizon].
 int orc_rollout_log(const orc_topo* T, const orc_inst* I, const double* W, int32_t horizon, double* states,
                     double* loss, int8_t* active, double* gap, double* bf16_margin, double* resid) {
@@ -1078,7 +1110,7 @@ int orc_rollout_log(const orc_topo* T, const orc_inst* I, const double* W, int32
 // (zero before the first step), and lam_prevs (optional) receives them per step [horizon][n_slots].
 static int rollout_impl(const orc_topo* T, const orc_inst* I, const double* W, int32_t horizon, double* states,
                         double* loss, int8_t* active, double* gap, double* bf16_margin, double* resid,
-                        std::vector<double>* lam_prevs) {
+                        std::vector<double>* lam_prevs, double* hs) {
   if (check_topo(T) || horizon < 0) return -1;
   auto slots = make_slots(*T);
   std::vector<int> col, ord;
@@ -1092,6 +1124,9 @@ static int rollout_impl(const orc_topo* T, const orc_inst* I, const double* W, i
   if (states) std::memcpy(states, x.data(), sizeof(double) * x.size());
   std::vector<double> lamp(nsl, 0.0), lamn(nsl, 0.0);
   if (lam_prevs) lam_prevs->assign((size_t)horizon * nsl, 0.0);
+  const int H = T->n_recurrent;
+  std::vector<double> hcur(H, 0.0), hnext;
+  if (hs && H > 0) std::memset(hs, 0, sizeof(double) * H);
   for (int t = 0; t < horizon; ++t) {
     double lt = 0.0;
     std::vector<int8_t> act_tmp;
@@ -1101,8 +1136,11 @@ static int rollout_impl(const orc_topo* T, const orc_inst* I, const double* W, i
                nullptr, bf16_margin ? bf16_margin + t : nullptr, resid ? resid + t : nullptr, nullptr, nullptr};
     if (lam_prevs) std::copy(lamp.begin(), lamp.end(), lam_prevs->begin() + (size_t)t * nsl);
     step<double>(*T, slots, ord, P, Wv, t, x, xn, weight_of_state(*T, t + 1, horizon), &lt,
-                 ((active && gap) || resid) ? &lg : nullptr, T->warmstart ? lamp.data() : nullptr, lamn.data());
+                 ((active && gap) || resid) ? &lg : nullptr, T->warmstart ? lamp.data() : nullptr, lamn.data(), &hcur,
+                 &hnext);
     lamp.swap(lamn);
+    hcur.swap(hnext);
+    if (hs && H > 0) std::memcpy(hs + (size_t)(t + 1) * H, hcur.data(), sizeof(double) * H);
     L += lt;
     x.swap(xn);
     if (states) std::memcpy(states + (size_t)(t + 1) * 18 * T->nb, x.data(), sizeof(double) * x.size());
@@ -1125,7 +1163,10 @@ int orc_rollout_grad(const orc_topo* T, const orc_inst* I, const double* W, int3
   const int nb = T->nb;
   const int np_ = param_count(T->n_layers, T->widths, T->skip);
   std::vector<double> states((size_t)(horizon + 1) * 18 * nb), lamps;
-  if (rollout_impl(T, I, W, horizon, states.data(), loss, nullptr, nullptr, nullptr, nullptr, &lamps)) return -1;
+  const int H = T->n_recurrent;
+  std::vector<double> hs((size_t)(horizon + 1) * std::max(H, 1));
+  if (rollout_impl(T, I, W, horizon, states.data(), loss, nullptr, nullptr, nullptr, nullptr, &lamps, hs.data()))
+    return -1;
   const size_t nsl = slots.size();
 
   Tape tape;
@@ -1143,7 +1184,7 @@ int orc_rollout_grad(const orc_topo* T, const orc_inst* I, const double* W, int3
   zero(G->sph_rad, T->ns); zero(G->sph_mu, T->ns); zero(G->sph_e, T->ns); zero(G->loss_point, 3);
   zero(G->loss_target, 3); zero(G->state0, 18 * nb); zero(G->W, np_);
 
-  std::vector<double> xbar(18 * nb, 0.0);
+  std::vector<double> xbar(18 * nb, 0.0), hbar(H, 0.0);
   for (int t = horizon - 1; t >= 0; --t) {
     tape.clear();
     Inst<AD> P;
@@ -1162,9 +1203,10 @@ int orc_rollout_grad(const orc_topo* T, const orc_inst* I, const double* W, int3
     P.loss_target = lift_leaf(I->loss_target, 3);
     std::vector<AD> Wl = lift_leaf(W, np_);
     std::vector<AD> x = lift_leaf(states.data() + (size_t)t * 18 * nb, 18 * nb), xn;
+    std::vector<AD> hin = lift_leaf(hs.data() + (size_t)t * H, H), hout;
     AD lt;
     step<AD>(*T, slots, ord, P, Wl, t, x, xn, weight_of_state(*T, t + 1, horizon), &lt, nullptr,
-             T->warmstart ? lamps.data() + (size_t)t * nsl : nullptr);
+             T->warmstart ? lamps.data() + (size_t)t * nsl : nullptr, nullptr, &hin, &hout);
     AD l0 = (t == 0) ? loss_initial(*T, P, x) : AD(0.0);
     tape.adj.assign(tape.pa.size(), 0.0);
     // the gradient reaching step t from later steps is decreased by alpha (section 3.2); the
@@ -1172,10 +1214,13 @@ int orc_rollout_grad(const orc_topo* T, const orc_inst* I, const double* W, int3
     const double decay = T->grad_decay > 0.0 ? T->grad_decay : 1.0;
     for (int k = 0; k < 18 * nb; ++k)
       if (xn[k].id >= 0) tape.adj[xn[k].id] += decay * xbar[k];
+    for (int k = 0; k < H; ++k)  // the recurrent state's adjoint decays like the state's
+      if (hout[k].id >= 0) tape.adj[hout[k].id] += decay * hbar[k];
     if (lt.id >= 0) tape.adj[lt.id] += 1.0;
     if (l0.id >= 0) tape.adj[l0.id] += 1.0;
     tape.backward();
     for (int k = 0; k < 18 * nb; ++k) xbar[k] = x[k].id >= 0 ? tape.adj[x[k].id] : 0.0;
+    for (int k = 0; k < H; ++k) hbar[k] = hin[k].id >= 0 ? tape.adj[hin[k].id] : 0.0;
     acc(G->mass, P.mass, tape); acc(G->inertia, P.inertia, tape); acc(G->anchor, P.anchor, tape);
     acc(G->axis, P.axis, tape); acc(G->ref, P.ref, tape); acc(G->limit, P.limit, tape);
     acc(G->motor, P.motor, tape); acc(G->sph_off, P.sph_off, tape); acc(G->sph_rad, P.sph_rad, tape);

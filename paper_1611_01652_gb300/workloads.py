@@ -265,7 +265,7 @@ QUADRUPED_WIDTHS = [24, 128, 128, 8]
 
 
 def quadruped(B=4096, seed=1002, horizon=1000, iters=20, dt=0.01, widths=None, skip=0, yaw=0.3, vel=0.1,
-              w_seed=None, out_scale=0.1):
+              w_seed=None, out_scale=0.1, n_recurrent=0):
     """Quadruped: box torso 0.6x0.3x0.1 m, 8 kg; 4 legs x 2 capsule links (0.2 m, radius 0.025,
     0.5 kg) on hinges about the body y axis with limits +-60 deg and servo motors (gain 30 1/s,
     4 N m, 45 deg/s); sphere feet r=0.03 and four r=0.05 spheres inside the torso, all touching
@@ -275,11 +275,17 @@ def quadruped(B=4096, seed=1002, horizon=1000, iters=20, dt=0.01, widths=None, s
     Loss: negative forward (x) displacement of the torso. Per instance a seeded yaw in
     [-yaw, yaw] and a common horizontal velocity in [-vel, vel]^2.
 
+    ``n_recurrent`` = H > 0 gives the controller the recurrent state of Eq. g: the network
+    (default 24+H -> 128 -> 128 -> 8+H) reads the sensors and h^t, and its last H outputs give
+    h^{t+1} = tanh(.), starting from h^0 = 0.
+
     The output layer's Xavier weights are scaled by ``out_scale`` (0.1): the paper starts its
     quadruped controller from a zero output layer (section 3.3); a full-size random output layer
     closes an unstable feedback loop through the servos (gain 30/s) whose reverse-mode gradient
     grows about e^0.24 per step and overflows float32 within a few hundred steps."""
     rng = np.random.default_rng(seed)
+    if widths is None and n_recurrent:
+        widths = [QUADRUPED_WIDTHS[0] + n_recurrent, *QUADRUPED_WIDTHS[1:-1], QUADRUPED_WIDTHS[-1] + n_recurrent]
     widths = list(widths or QUADRUPED_WIDTHS)
     nb, nj, ns = 9, 8, 8
     d = _empty(B, nb, nj, ns)
@@ -334,10 +340,12 @@ def quadruped(B=4096, seed=1002, horizon=1000, iters=20, dt=0.01, widths=None, s
     _finish(d)
     wr = np.random.default_rng(seed + 7 if w_seed is None else w_seed)
     W = xavier_weights(widths, skip, wr, out_scale=out_scale)
-    return Model(name="quadruped", B=B, joint_type=jt, joint_body=jb, joint_flags=jf, sphere_body=sb,
-                 pair_sphere=np.zeros((0, 2), np.int32), nb=nb, widths=widths, skip=skip,
-                 features=F_ANGLES | F_RATES | F_CLOCK | F_IMU, imu_body=0, clock_hz=1.5, W=W, dt=dt,
-                 iters=iters, horizon=horizon, loss_kind=L_DISP, loss_mode=M_FINAL, loss_body=0, **d)
+    m = Model(name="quadruped", B=B, joint_type=jt, joint_body=jb, joint_flags=jf, sphere_body=sb,
+              pair_sphere=np.zeros((0, 2), np.int32), nb=nb, widths=widths, skip=skip,
+              features=F_ANGLES | F_RATES | F_CLOCK | F_IMU, imu_body=0, clock_hz=1.5, W=W, dt=dt,
+              iters=iters, horizon=horizon, loss_kind=L_DISP, loss_mode=M_FINAL, loss_body=0, **d)
+    m.n_recurrent = int(n_recurrent)
+    return m
 
 
 def two_spheres(B=4, seed=1003, horizon=60, iters=20, dt=0.01, e=0.0, mu=0.3, gravity=(0.0, 0.0, 0.0)):
