@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--ws-train-steps", type=int, default=800)
     p.add_argument("--no-arms", action="store_true", help="skip the uneven arm batch")
     p.add_argument("--no-wide", action="store_true", help="skip the wide (1.1 M-parameter) controller")
+    p.add_argument("--no-recurrent", action="store_true", help="skip the recurrent controller")
+    p.add_argument("--recurrent-only", action="store_true", help="time only the recurrent controller")
     p.add_argument("--wide-only", action="store_true",
                    help="time only the wide controller (for profiling; prints its object as the line)")
     p.add_argument("--wide-batch", type=int, default=4096)
@@ -281,6 +283,50 @@ def time_uneven_arms(args):
     return out
 
 
+def time_recurrent_controller(args, alpha, H=8):
+    """The quadruped B=4096, T=1000 with the recurrent controller of Eq. g (24+H -> 128 -> 128 ->
+    8+H, H = 8 units of recurrent state, bf16 storage points): forward + adjoint of the plain solver
+    at 20 sweeps and of the damped previous-impulse start at 10 sweeps, 1 warm-up + ``steps``
+    timed steps each, with the mean solve residual of each."""
+    import torch
+
+    from paper_1611_01652_gb300 import workloads as WL
+    from paper_1611_01652_gb300.binding import WS_PARAMS, World
+
+    m = WL.quadruped(B=args.batch, horizon=args.horizon, n_recurrent=H)
+    W = torch.tensor(m.W, device="cuda")
+    loss = torch.zeros(m.B, device="cuda")
+    dl = torch.ones(m.B, device="cuda")
+    out = {"workload": "quadruped B=%d T=%d, recurrent controller %s (h: %d units, bf16)" % (
+        m.B, m.horizon, "-".join(map(str, m.widths)), H)}
+    for name, iters, warm in (("plain", 20, False), ("warm_start", 10, True)):
+        w = World(m, iters=iters, warmstart=warm)
+        if warm:
+            w.set_warmstart(torch.zeros(WS_PARAMS, device="cuda"), alpha)
+        dW = torch.zeros(w.n_params, device="cuda")
+        w.rollout(W, loss)
+        w.backward(dl, dW)
+        w.sync()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        fwd = bwd = 0.0
+        for _ in range(args.steps):
+            ev[0].record()
+            w.rollout(W, loss)
+            ev[1].record()
+            w.backward(dl, dW)
+            ev[2].record()
+            torch.cuda.synchronize()
+            fwd += ev[0].elapsed_time(ev[1])
+            bwd += ev[1].elapsed_time(ev[2])
+        ms = (fwd + bwd) / args.steps
+        out[name] = {"iters": iters, "value": m.B * m.horizon / (ms / 1e3), "unit": "inst-steps/s", "ms_per_step": ms,
+                     "fwd_ms": fwd / args.steps, "bwd_ms": bwd / args.steps, "resid": mean_residual(w, W, m.B),
+                     "finite": bool(torch.isfinite(dW).all().item())}
+        del w
+        torch.cuda.empty_cache()
+    return out
+
+
 def time_wide_controller(args, alpha):
     """The quadruped B=4096, T=1000 with the 64-1024-1024-8 controller (1,124,360 parameters,
     batched tensor-core products between step launches): forward + adjoint of the plain solver
@@ -355,6 +401,9 @@ def main():
     torch.cuda.set_device(local_rank)
     if args.wide_only:
         print(json.dumps(time_wide_controller(args, args.alpha)))
+        return
+    if args.recurrent_only:
+        print(json.dumps(time_recurrent_controller(args, args.alpha)))
         return
     dist = None
     if world_size > 1:
@@ -432,6 +481,7 @@ def main():
     torch.cuda.empty_cache()
     arms = None if args.no_arms else time_uneven_arms(args)
     wide = None if args.no_wide else time_wide_controller(args, args.alpha)
+    recurrent = None if args.no_recurrent else time_recurrent_controller(args, args.alpha)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -474,6 +524,7 @@ def main():
                    "batch": B, "horizon": T, "iters": head["iters"], "ckpt_every": head["ckpt_every"],
                    "l2": "working set (solver tape + controller activations) >> 129 MB L2; no flush needed"},
         "plain": plain, "warmstart": ws, "gate": gate, "uneven_arms": arms, "wide_controller": wide,
+        "recurrent_controller": recurrent,
         "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": head["clocks"],
         "plain_clocks": p_ck if ws else None,
         "gpu_launches": launches_per_step * args.steps, "fwd_ms": head["fwd_ms"], "bwd_ms": head["bwd_ms"],

@@ -127,6 +127,13 @@ typedef struct {
   int32_t dw_splits;              /* split count of the controller-gradient reduction (0 = automatic) */
   float grad_decay;               /* alpha of section 3.2: the state adjoint passed from step t+1 back to
                                      step t is multiplied by alpha (0 or 1: no decay) */
+  int32_t n_recurrent;            /* H >= 0: the recurrent controller state h^t of Eq. g (section 2.2):
+                                     the last H network inputs are h^t (a bfloat16 storage point
+                                     unless ctrl_fp32), the last H outputs z give
+                                     h^{t+1} = tanh(z), h^0 = 0 at the start of a rollout; the
+                                     first outputs stay the motor signals. Needs n_layers >= 1,
+                                     no skip layer, widths[0] >= features + H and
+                                     widths[n_layers] >= motors + H. 0 = feed-forward. */
 } dp_batch_desc;
 
 typedef struct dp_world dp_world; /* opaque; owned by the library */
@@ -259,6 +266,12 @@ int32_t dp_ckpt_every(const dp_world* w);
    for dp_harvest). The world must have been created with desc.warmstart = 1 (DP_EINVAL
    otherwise). Takes effect from the next dp_step / dp_rollout; a recorded rollout is dropped. */
 dp_status dp_set_warmstart(dp_world* w, const float* W, float alpha);
+
+/* The controller's recurrent state h (n_recurrent > 0): set h [B][n_recurrent] (host or device)
+   as the state the next dp_step starts from, or read the current one into h. dp_set_state and
+   every dp_rollout start from h = 0. DP_EINVAL if the world has no recurrent state. */
+dp_status dp_set_recurrent(dp_world* w, const float* h);
+dp_status dp_get_recurrent(dp_world* w, float* h);
 
 /* The impulses every slot ended the last step with, [B][n_slots] (host or device): read them,
    or set them as the lambda_prev of the next dp_step. */

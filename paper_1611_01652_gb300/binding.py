@@ -34,7 +34,8 @@ class BatchDesc(C.Structure):
                 ("gamma", C.c_float), ("slop", C.c_float), ("iters", C.c_int32), ("horizon", C.c_int32),
                 ("ckpt_every", C.c_int32), ("loss_kind", C.c_int32), ("loss_mode", C.c_int32),
                 ("loss_body", C.c_int32), ("ctrl_fp32", C.c_int32), ("warmstart", C.c_int32),
-                ("horizons", PI), ("rows_global", C.c_int32), ("dw_splits", C.c_int32), ("grad_decay", C.c_float)]
+                ("horizons", PI), ("rows_global", C.c_int32), ("dw_splits", C.c_int32), ("grad_decay", C.c_float),
+                ("n_recurrent", C.c_int32)]
 
 WS_PARAMS = 5443
 WS_ROW = 19
@@ -49,7 +50,7 @@ SYMBOLS = ("dp_create_world", "dp_free", "dp_num_params", "dp_num_slots", "dp_sc
            "dp_set_state", "dp_get_state", "dp_step", "dp_rollout", "dp_backward", "dp_sync", "dp_last_error",
            "dp_ckpt_every", "dp_backward_noalloc", "dp_set_warmstart", "dp_harvest", "dp_set_residual",
            "dp_get_residual", "dp_ws_workspace_floats", "dp_ws_param_count", "dp_ws_loss_grad", "dp_ws_forward",
-           "dp_ws_adam", "dp_set_impulses", "dp_get_impulses")
+           "dp_ws_adam", "dp_set_impulses", "dp_get_impulses", "dp_set_recurrent", "dp_get_recurrent")
 
 
 def load(build=True):
@@ -81,6 +82,8 @@ def load(build=True):
     lib.dp_set_warmstart.argtypes = [C.c_void_p, C.c_void_p, C.c_float]
     lib.dp_set_impulses.argtypes = [C.c_void_p, C.c_void_p]
     lib.dp_get_impulses.argtypes = [C.c_void_p, C.c_void_p]
+    lib.dp_set_recurrent.argtypes = [C.c_void_p, C.c_void_p]
+    lib.dp_get_recurrent.argtypes = [C.c_void_p, C.c_void_p]
     lib.dp_harvest.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]
     lib.dp_set_residual.argtypes = [C.c_void_p, C.c_int32]
     lib.dp_get_residual.argtypes = [C.c_void_p, C.c_void_p]
@@ -179,6 +182,8 @@ class World:
         d.rows_global = int(bool(rows_global))
         d.dw_splits = int(dw_splits)
         d.grad_decay = float(getattr(model, "grad_decay", 1.0))
+        d.n_recurrent = int(getattr(model, "n_recurrent", 0))
+        self.n_recurrent = d.n_recurrent
         self.horizon = d.horizon
         self.n_motors = int(sum(1 for f in np.asarray(model.joint_flags).reshape(-1) if f & 2))
         h = C.c_void_p()
@@ -252,6 +257,14 @@ class World:
 
     def get_impulses(self, out):
         _check(_lib.dp_get_impulses(self._h, ptr(out)))
+
+    def set_recurrent(self, h):
+        """The controller's recurrent state [B, n_recurrent] the next step starts from."""
+        _check(_lib.dp_set_recurrent(self._h, ptr(h)))
+
+    def get_recurrent(self, out):
+        """Reads the controller's current recurrent state into ``out`` [B, n_recurrent]."""
+        _check(_lib.dp_get_recurrent(self._h, ptr(out)))
         return out
 
     def harvest(self, W, rows, u_noise=None):

@@ -104,6 +104,7 @@ dp_status validate(const dp_batch_desc* d) {
         return fail(DP_EINVAL, "horizons[" + std::to_string(i) + "] out of range [1, horizon]");
   if (d->dw_splits < 0) return fail(DP_EINVAL, "dw_splits must be >= 0");
   if (!(d->grad_decay >= 0.f && d->grad_decay <= 1.f)) return fail(DP_EINVAL, "grad_decay must lie in [0, 1]");
+  if (d->n_recurrent < 0 || d->n_recurrent > 64) return fail(DP_EINVAL, "n_recurrent out of range [0, 64]");
   if (d->iters < 1) return fail(DP_EINVAL, "iters must be >= 1");
   if (!(d->dt > 0.f)) return fail(DP_EINVAL, "dt must be > 0");
   if (d->ckpt_every < 0) return fail(DP_EINVAL, "ckpt_every must be >= 0");
@@ -175,6 +176,7 @@ void plan_smem(DevTopo& T, bool backward, int smem_floats_max, bool rows_on_chip
   T.sm_wst = take(T.nj);
   T.sm_wbr = take(T.nj);
   T.sm_lam = take(T.nslots);
+  T.sm_h = take(T.n_rec);
   // warm-start scratch (features, outputs, harvest row ids): the joint arrays above are dead
   // once the rows are assembled, so they host it when they are large enough
   const int wsneed = 19 + T.n_wsg;
@@ -205,7 +207,7 @@ void plan_smem(DevTopo& T, bool backward, int smem_floats_max, bool rows_on_chip
       o = region + acts;
     }
     T.sm_xb = T.sm_vb = T.sm_thb = T.sm_thdb = T.sm_uab = T.sm_wstb = T.sm_iinvb = T.sm_invmb = T.sm_rc = T.sm_sbar = 0;
-    T.sm_vw = T.sm_zb = 0;
+    T.sm_vw = T.sm_zb = T.sm_hb = 0;
   } else {
     for (int l = 0; l <= DPK_MAXL; ++l) T.sm_act[l] = 0;
     T.sm_xb = take(18 * T.nb);
@@ -219,6 +221,7 @@ void plan_smem(DevTopo& T, bool backward, int smem_floats_max, bool rows_on_chip
     T.sm_rc = take(12 * T.nslots);
     T.sm_sbar = take(T.n_layers > 0 ? T.widths[0] : 1);
     T.sm_vw = take(6 * T.nb);
+    T.sm_hb = take(T.n_rec);
     // controller-reverse ping-pong buffers: the row-adjoint region is free by then
     int maxw = 1;
     for (int l = 0; l <= T.n_layers && T.n_layers > 0; ++l)
@@ -372,8 +375,10 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
   int wtot = 0;
   if (T.n_layers > 0) {
     for (int l = 0; l <= T.n_layers; ++l) T.widths[l] = d->widths[l];
-    if (feature_count(d, T.n_motors) > T.widths[0])
-      return cleanup(fail(DP_EINVAL, "controller input width is smaller than the selected features"));
+    if (feature_count(d, T.n_motors) + d->n_recurrent > T.widths[0])
+      return cleanup(fail(DP_EINVAL, "controller input width is smaller than the selected features (+ recurrent state)"));
+    if (d->n_recurrent > 0 && (T.skip || T.n_motors + d->n_recurrent > T.widths[T.n_layers]))
+      return cleanup(fail(DP_EINVAL, "a recurrent controller needs no skip layer and widths[n_layers] >= motors + n_recurrent"));
     const int nl = T.n_layers + (T.skip ? 1 : 0);
     for (int l = 0; l < nl; ++l) {
       int ni = l < T.n_layers ? T.widths[l] : T.widths[0];
@@ -391,14 +396,15 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
   T.n_params = (int)np_;
   T.ws = 0;
   T.ws_net = 0;
+  T.n_rec = T.n_layers > 0 ? d->n_recurrent : 0;
   T.ws_alpha = 0.7f;
   T.grad_decay = d->grad_decay > 0.f ? d->grad_decay : 1.f;
-  T.mlp_tc = T.n_layers == 3 && !T.skip && T.ctrl_round && T.widths[0] == CtrlTC::K0 && T.widths[1] == CtrlTC::H1 &&
+  T.mlp_tc = T.n_rec == 0 && T.n_layers == 3 && !T.skip && T.ctrl_round && T.widths[0] == CtrlTC::K0 && T.widths[1] == CtrlTC::H1 &&
              T.widths[2] == CtrlTC::H2 && T.widths[3] == CtrlTC::NO && !getenv("DP_FORCE_SIMT_CONTROLLER");
   // wide bfloat16 controllers (hidden layers beyond 256) run as batched tensor-core products
   // between step launches; DP_FORCE_WIDE_CONTROLLER selects that path for any eligible network
   {
-    const bool shape = T.n_layers == 3 && !T.skip && T.ctrl_round && T.widths[1] % 64 == 0 && T.widths[2] % 64 == 0 &&
+    const bool shape = T.n_rec == 0 && T.n_layers == 3 && !T.skip && T.ctrl_round && T.widths[1] % 64 == 0 && T.widths[2] % 64 == 0 &&
                        T.widths[3] <= 8 && T.widths[0] <= 256;
     const bool wide = T.n_layers == 3 && (T.widths[1] > 256 || T.widths[2] > 256);
     T.ext_ctrl = shape && (wide || getenv("DP_FORCE_WIDE_CONTROLLER") != nullptr);
@@ -594,6 +600,12 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
   CU(cudaMemsetAsync(D.lam_prev, 0, sizeof(float) * (size_t)std::max(T.nslots, 1) * Bz, w->stream));
   D.ckpt_lam = nullptr;
   if (w->ws_capable && !full && dalloc(w, &D.ckpt_lam, (size_t)n_ckpt * T.nslots * Bz)) return cleanup(DP_ENOMEM);
+  D.hrec = D.ckpt_h = nullptr;
+  if (T.n_rec > 0) {
+    if (dalloc(w, &D.hrec, (size_t)T.n_rec * Bz)) return cleanup(DP_ENOMEM);
+    CU(cudaMemsetAsync(D.hrec, 0, sizeof(float) * (size_t)T.n_rec * Bz, w->stream));
+    if (!full && dalloc(w, &D.ckpt_h, (size_t)n_ckpt * T.n_rec * Bz)) return cleanup(DP_ENOMEM);
+  }
   D.ws_tc = w->ws_tc;
   D.ws_b = w->ws_b;
   D.harvest = nullptr;
@@ -676,6 +688,7 @@ dp_status dp_set_state(dp_world* w, const float* state, int32_t t) {
   TRY(stage_state_in(w, state, w->D.state));
   // the previous impulses belonged to another trajectory: the next step starts without them
   CU(cudaMemsetAsync(w->D.lam_prev, 0, sizeof(float) * (size_t)std::max(w->Tf.nslots, 1) * w->Bp, w->stream));
+  if (w->D.hrec) CU(cudaMemsetAsync(w->D.hrec, 0, sizeof(float) * (size_t)w->Tf.n_rec * w->Bp, w->stream));
   w->t_now = t;
   w->have_rollout = false;
   return DP_OK;
@@ -782,6 +795,26 @@ dp_status dp_get_impulses(dp_world* w, float* lam) {
   if (ns == 0) return DP_OK;
   CU(launch_state_out(w->B, w->Bp, ns, w->D.lam_prev, w->stage, w->stream));
   CU(cudaMemcpyAsync(lam, w->stage, sizeof(float) * (size_t)w->B * ns, cudaMemcpyDefault, w->stream));
+  return DP_OK;
+}
+
+dp_status dp_set_recurrent(dp_world* w, const float* h) {
+  if (!w || !h) return fail(DP_EINVAL, "world or h is NULL");
+  const int H = w->Tf.n_rec;
+  if (H == 0) return fail(DP_EINVAL, "the world has no recurrent controller state");
+  if ((size_t)w->B * H > w->stage_floats) return fail(DP_EINVAL, "staging buffer too small");
+  CU(cudaMemcpyAsync(w->stage, h, sizeof(float) * (size_t)w->B * H, cudaMemcpyDefault, w->stream));
+  CU(launch_state_in(w->B, w->Bp, H, w->stage, w->D.hrec, w->stream));
+  return DP_OK;
+}
+
+dp_status dp_get_recurrent(dp_world* w, float* h) {
+  if (!w || !h) return fail(DP_EINVAL, "world or h is NULL");
+  const int H = w->Tf.n_rec;
+  if (H == 0) return fail(DP_EINVAL, "the world has no recurrent controller state");
+  if ((size_t)w->B * H > w->stage_floats) return fail(DP_EINVAL, "staging buffer too small");
+  CU(launch_state_out(w->B, w->Bp, H, w->D.hrec, w->stage, w->stream));
+  CU(cudaMemcpyAsync(h, w->stage, sizeof(float) * (size_t)w->B * H, cudaMemcpyDefault, w->stream));
   return DP_OK;
 }
 

@@ -52,6 +52,9 @@ struct DevTopo {
   int ws;       // 1: the solve starts from the learned warm start (DevPtrs.ws_tc, ws_alpha)
   float ws_alpha;  // weight of the previous step's impulses in the warm start
   int ws_net;      // 0: the network is identically zero (the damped start alpha * previous impulses)
+  int n_rec;       // H: the controller's recurrent state (Eq. g): its last H inputs are h^t, its last
+                   //    H outputs give h^{t+1} = tanh(.); 0 = feed-forward
+  int sm_h, sm_hb; // on-chip h^t (forward) and the adjoint of h^{t+1} carried between reverse steps
   float grad_decay;  // reverse mode: state adjoint x alpha per step (section 3.2); 1 = none
   int sm_ws;    // warm-start scratch per lane: features [16], outputs [3], harvest row ids [n_wsg]
   // warm-start groups of three rows (slot -1: none): joint linear rows, hinge angular rows with
@@ -116,6 +119,8 @@ struct DevPtrs {
   float* state;          // current state [nb*18][Bp]
   float* ckpt;           // checkpoints [n_ckpt][nb*18][Bp]
   float* seg;            // segment states for the backward [K+1][nb*18][Bp]
+  float* hrec;           // the controller's recurrent state h [n_rec][Bp] between launches
+  float* ckpt_h;         // h at every checkpoint [n_ckpt][n_rec][Bp] (segment recompute), or NULL
   float* rows;           // constraint rows without a tape (rows that do not fit on chip) [nslots][RF_N][Bp]
   // Per-step solver tape, tape_steps slots: the whole horizon when it fits in device memory
   // (recorded by the rollout), else one checkpoint segment (recorded by the backward pass).

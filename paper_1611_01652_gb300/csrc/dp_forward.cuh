@@ -707,10 +707,18 @@ __device__ float step_forward(const DevTopo& T, const DevPtrs& D, const LaneT<RV
     servo_targets(T, L, act[T.n_layers]);
   } else if (T.n_layers > 0) {
     controller_features(T, L, X, t, act[0]);
+    if (T.n_rec) {  // recurrent state h^t: the last inputs (a bfloat16 storage point like the sensors)
+      const int base = T.widths[0] - T.n_rec;
+      for (int k = 0; k < T.n_rec; ++k) act[0][base + k] = qz(T, L.S[T.sm_h + k]);
+    }
     if (T.mlp_tc)
       controller_forward_tc(T, D, act, dump_col);
     else
       controller_forward(T, D, act);
+    if (T.n_rec) {  // h^{t+1} = tanh of the last outputs
+      const int base = T.widths[T.n_layers] - T.n_rec;
+      for (int k = 0; k < T.n_rec; ++k) L.S[T.sm_h + k] = tanhf(act[T.n_layers][base + k]);
+    }
     if (D.u_noise) {  // perturbed controller output (harvest of training rows)
       const float* nz = D.u_noise + ((size_t)t * T.B + min(L.i, T.B - 1)) * T.n_motors;  // [T][B][n_motors]
       for (int m = 0; m < T.n_motors && m < T.widths[T.n_layers]; ++m) act[T.n_layers][m] += nz[m];

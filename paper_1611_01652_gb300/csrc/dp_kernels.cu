@@ -139,6 +139,8 @@ __global__ void __launch_bounds__(32, 1) k_forward(const __grid_constant__ DevTo
   copy_state_to_smem(T, fresh ? x0 : D.state, i, X);
   // impulses of the previous step (the warm start's lambda_prev): none before a rollout
   for (int s = 0; s < T.nslots; ++s) L.S[T.sm_lam + s] = fresh ? 0.f : D.lam_prev[(size_t)s * T.Bp + i];
+  // the controller's recurrent state: h^0 = 0 at the start of a rollout
+  for (int k = 0; k < T.n_rec; ++k) L.S[T.sm_h + k] = fresh ? 0.f : D.hrec[(size_t)k * T.Bp + i];
   float loss = (rollout == 2 && !fresh) ? D.loss[i] : 0.f;
   if (fresh && T.loss_kind == 3) loss = -dot3(L.P.v3(T.o_loss_target), loss_point(T, L, X));
   const int B = T.B;
@@ -152,6 +154,9 @@ __global__ void __launch_bounds__(32, 1) k_forward(const __grid_constant__ DevTo
         if (D.ckpt_lam)
           for (int s = 0; s < T.nslots; ++s)
             D.ckpt_lam[((size_t)(t / D.ckpt_every) * T.nslots + s) * T.Bp + i] = L.S[T.sm_lam + s];
+        if (D.ckpt_h)
+          for (int k = 0; k < T.n_rec; ++k)
+            D.ckpt_h[((size_t)(t / D.ckpt_every) * T.n_rec + k) * T.Bp + i] = L.S[T.sm_h + k];
       }
       if (D.traj && i < B)
         for (int f = 0; f < 18 * T.nb; ++f) D.traj[((size_t)t * B + i) * 18 * T.nb + f] = X[f];
@@ -181,6 +186,7 @@ __global__ void __launch_bounds__(32, 1) k_forward(const __grid_constant__ DevTo
     }
   }
   for (int s = 0; s < T.nslots; ++s) D.lam_prev[(size_t)s * T.Bp + i] = L.S[T.sm_lam + s];
+  for (int k = 0; k < T.n_rec; ++k) D.hrec[(size_t)k * T.Bp + i] = L.S[T.sm_h + k];
   copy_state_from_smem(T, D.state, i, X);
   bool bad = !isfinite(loss);
   for (int f = 0; f < 18 * T.nb; ++f) bad |= !isfinite(X[f]);
@@ -221,8 +227,10 @@ __device__ void reverse_step(const DevTopo& T, const DevPtrs& D, const BwdCtx& C
   const SL zb1{C.S.p + (T.sm_zb + maxw) * 32};
   // loss term and integrator with x_{t+1} on chip
   copy_state_to_smem(T, x_t1, i, C.X);
-  if (T.grad_decay != 1.f)  // section 3.2: the adjoint from later steps shrinks by alpha per step
+  if (T.grad_decay != 1.f) {  // section 3.2: the adjoint from later steps shrinks by alpha per step
     for (int f = 0; f < 18 * T.nb; ++f) C.XB[f] *= T.grad_decay;
+    for (int k = 0; k < T.n_rec; ++k) C.S[T.sm_hb + k] *= T.grad_decay;  // and so does h's
+  }
   loss_reverse(T, Bl, C.X, C.XB, loss_weight(T, t + 1, D.hz[i]) * C.dl);
   integrate_reverse(T, GC{x_t + i, Bp}, C.X, C.XB, C.VB);
   // x_t on chip for every later stage; its per-step forward quantities are recomputed
@@ -255,11 +263,24 @@ __device__ void reverse_step(const DevTopo& T, const DevPtrs& D, const BwdCtx& C
     for (int o = 0; o < 16; ++o) ub[o] = o < T.widths[T.n_layers] ? zb0[o] : 0.f;
   } else if (T.n_layers > 0) {
     servo_reverse(T, Bl, act[T.n_layers], del[T.n_layers - 1], zb0);
+    if (T.n_rec) {  // adjoint of the recurrent outputs: h^{t+1} = tanh(z)
+      const int base = T.widths[T.n_layers] - T.n_rec;
+      for (int k = 0; k < T.n_rec; ++k) {
+        const float th = tanhf(act[T.n_layers][base + k]);
+        const float zb = C.S[T.sm_hb + k] * (1.f - th * th);
+        zb0[base + k] = zb;
+        del[T.n_layers - 1][base + k] = zb;
+      }
+    }
     if (T.mlp_tc)
       controller_reverse_tc(T, D, act, del, zb0, C.sbar);
     else
       controller_reverse(T, D, act, del, zb0, zb1, C.sbar);
     features_reverse(T, Bl, C.XB, C.sbar);
+    if (T.n_rec) {  // adjoint of h^t (straight through its bfloat16 rounding), carried to step t - 1
+      const int base = T.widths[0] - T.n_rec;
+      for (int k = 0; k < T.n_rec; ++k) C.S[T.sm_hb + k] = C.sbar[base + k];
+    }
   } else {
     servo_reverse(T, Bl, act[0], act[0], zb0);
   }
@@ -279,6 +300,7 @@ __global__ void __launch_bounds__(32, 1) k_backward(const __grid_constant__ DevT
   BwdCtx C{SL{sm}, SL{sm + T.sm_x * 32}, SL{sm + T.sm_xb * 32}, SL{sm + T.sm_vb * 32}, SL{sm + T.sm_rc * 32},
            SL{sm + T.sm_sbar * 32}, GC{D.prm + i, Bp}, GL{D.grad_prm + i, Bp}, i, D.dloss[i]};
   for (int f = 0; f < nf; ++f) C.XB[f] = 0.f;
+  for (int k = 0; k < T.n_rec; ++k) C.S[T.sm_hb + k] = 0.f;  // no adjoint reaches h^T
   const size_t sbytes = (size_t)nf * Bp;
   const int Tw = warp_horizon(D, i);  // the rollout stepped this warp to Tw
   if (D.tape_full) {
@@ -292,6 +314,8 @@ __global__ void __launch_bounds__(32, 1) k_backward(const __grid_constant__ DevT
       copy_state_to_smem(T, D.ckpt + (size_t)c * sbytes, i, C.X);
       if (T.ws)  // the previous impulses the segment's first step started from
         for (int s = 0; s < T.nslots; ++s) C.S[T.sm_lam + s] = D.ckpt_lam[((size_t)c * T.nslots + s) * Bp + i];
+      for (int k = 0; k < T.n_rec; ++k)  // the controller's recurrent state at the segment's start
+        C.S[T.sm_h + k] = D.ckpt_h[((size_t)c * T.n_rec + k) * Bp + i];
       for (int t = ta; t < tb; ++t) {
         copy_state_from_smem(T, D.seg + (size_t)(t - ta) * sbytes, i, C.X);
         const TapeStep tp = tape_step(T, D, t - ta);

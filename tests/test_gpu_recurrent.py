@@ -1,0 +1,125 @@
+"""Recurrent controller (Eq. g with its state h^t: the last network inputs are h^t, the last
+outputs give h^{t+1} = tanh(.), h^0 = 0) through the C ABI against the FP64 oracle: free
+rollouts, teacher-forced single steps (state and recurrent state in, both out) and gradients
+back-propagated through both the physical and the recurrent state (whole tape and checkpoint
+segments, with and without the gradient decay of section 3.2)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_1611_01652_gb300 import workloads as WL  # noqa: E402
+from paper_1611_01652_gb300.binding import World  # noqa: E402
+
+from test_gpu_parity import GRAD_RTOL, TIE, compare_rollout, gpu_grads, gpu_rollout, rel_err  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+H = 4
+
+
+def rec_model(B, T, fp32=1):
+    m = WL.quadruped(B=B, horizon=T, n_recurrent=H)
+    m.ctrl_fp32 = fp32
+    return m
+
+
+def test_recurrent_rollout_matches_oracle():
+    """100-step rollouts (fp32 controller): states, losses and active sets as for the
+    feed-forward quadruped; the recurrent state after the rollout within 1e-4 wherever the
+    trajectory stayed on the oracle's."""
+    m = rec_model(40, 100)
+    compare_rollout(m, 100, range(0, 40, 4), min_clean=0.5)
+    w, traj, _, _ = gpu_rollout(m, 100)
+    h = torch.zeros(m.B, H, device="cuda")
+    w.get_recurrent(h)
+    w.sync()
+    h = h.cpu().double().numpy()
+    close = 0
+    for i in range(0, 40, 4):
+        st, _, hs = O.rollout_rec(m, i, horizon=100)
+        if (np.abs(traj[:, i] - st) / np.maximum(1.0, np.abs(st))).max() <= 1e-4:
+            assert np.abs(h[i] - hs[-1]).max() <= 1e-4, (i, h[i], hs[-1])
+            close += 1
+        assert np.abs(hs[1:]).max() > 1e-3  # the state does evolve
+    assert close >= 5
+
+
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_recurrent_teacher_forced_steps(fp32):
+    """One GPU step from oracle states and recurrent states at many times: next state, next
+    recurrent state and active set (bfloat16 controller: steps whose rounding decisions came
+    within 1e-5 of a tie are skipped)."""
+    m = rec_model(8, 120, fp32)
+    w = World(m, horizon=120)
+    W = torch.tensor(m.W, device="cuda")
+    ref = [O.rollout_rec(m, i, horizon=120) for i in range(m.B)]
+    checked = total = 0
+    for t in range(0, 120, 9):
+        x = np.stack([r[0][t] for r in ref]).astype(np.float32)
+        hp = np.stack([r[2][t] for r in ref]).astype(np.float32)
+        w.set_state(torch.tensor(x, device="cuda"), t)
+        w.set_recurrent(torch.tensor(hp, device="cuda"))
+        act = torch.zeros(1, m.B, w.n_slots, dtype=torch.uint8, device="cuda")
+        w.step(1, W, act)
+        out = torch.zeros(m.B, m.nb, 18, device="cuda")
+        hn = torch.zeros(m.B, H, device="cuda")
+        w.get_state(out)
+        w.get_recurrent(hn)
+        w.sync()
+        out, hn, act = out.cpu().double().numpy(), hn.cpu().double().numpy(), act.cpu().numpy()[0]
+        for i in range(m.B):
+            d = O.step_log(m, i, x[i].astype(np.float64), t=t, h_prev=hp[i].astype(np.float64))
+            ok = d["gap"] >= TIE
+            assert np.array_equal(act[i][ok], d["active"][ok]), (t, i)
+            total += 1
+            if ok.all() and (fp32 or d["margin"] > TIE):
+                err = np.abs(out[i] - d["xn"]) / np.maximum(1.0, np.abs(d["xn"]))
+                assert err.max() <= 1e-4, (t, i, err.max())
+                assert np.abs(hn[i] - d["h"]).max() <= 1e-4, (t, i, hn[i], d["h"])
+                checked += 1
+    assert checked >= (0.9 if fp32 else 0.3) * total, (checked, total)
+
+
+@pytest.mark.parametrize("fp32,T,ckpt,decay", [(1, 30, None, 1.0), (1, 30, 8, 1.0), (1, 30, None, 0.9),
+                                               (0, 10, None, 1.0)])
+def test_recurrent_gradients_match_oracle(fp32, T, ckpt, decay):
+    """Gradients w.r.t. every controller weight (the recurrent columns and rows included), the
+    initial state and the model parameters within 1e-3 of the oracle's back-propagation through
+    time; the whole solver tape, or 8-step checkpoint segments recomputed from the checkpointed
+    state and recurrent state; gradient decay 0.9 applied to both adjoints. With bfloat16 storage
+    points the recurrent input adds one rounding per step and unit; where the fp32 and FP64 sums
+    straddle a rounding boundary the two sides store values one bfloat16 step apart and the
+    trajectories part by 1e-4 or more within a step or two (fp32 drift alone stays below 5e-6
+    over these 10 steps), so that case checks the instances whose whole trajectory stayed within
+    1e-5 of the oracle's (no rounding went the other way), and the weight gradient summed over
+    instances when all of them did."""
+    B = 4 if fp32 else 8
+    m = rec_model(B, T, fp32)
+    m.grad_decay = decay
+    inst = list(range(B))
+    if not fp32:
+        _, traj, _, _ = gpu_rollout(m, T)
+        inst = []
+        for i in range(B):
+            st = O.rollout(m, i, horizon=T)[0]
+            if (np.abs(traj[:, i] - st) / np.maximum(1.0, np.abs(st))).max() <= 1e-5:
+                inst.append(i)
+        assert len(inst) >= 2, inst
+    g = gpu_grads(m, T, ckpt)
+    Wsum = None
+    for i in inst:
+        L, go = O.rollout_grad(m, i, horizon=T)
+        assert abs(g["loss"][i] - L) <= 1e-4 * max(1.0, abs(L))
+        for k in ("state0", "mass", "inertia", "motor"):
+            e = rel_err(g[k][i], go[k])
+            assert e <= GRAD_RTOL, (i, k, e)
+        Wsum = go["W"] if Wsum is None else Wsum + go["W"]
+    if len(inst) < B:
+        return
+    assert rel_err(g["W"], Wsum) <= GRAD_RTOL
+    ni = m.widths[0]
+    rec_cols = [o * ni + k for o in range(m.widths[1]) for k in range(ni - H, ni)]
+    assert np.linalg.norm(Wsum[rec_cols]) > 0.0
+    assert rel_err(g["W"][rec_cols], Wsum[rec_cols]) <= GRAD_RTOL
