@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--no-arms", action="store_true", help="skip the uneven arm batch")
     p.add_argument("--no-wide", action="store_true", help="skip the wide (1.1 M-parameter) controller")
     p.add_argument("--no-recurrent", action="store_true", help="skip the recurrent controller")
+    p.add_argument("--no-sysid", action="store_true", help="skip the system-identification fit")
+    p.add_argument("--sysid-only", action="store_true", help="time only the system-identification fit")
     p.add_argument("--recurrent-only", action="store_true", help="time only the recurrent controller")
     p.add_argument("--wide-only", action="store_true",
                    help="time only the wide controller (for profiling; prints its object as the line)")
@@ -327,6 +329,39 @@ def time_recurrent_controller(args, alpha, H=8):
     return out
 
 
+def time_sysid(args, iters=300):
+    """System identification: 1024 three-link pendulums x 4 swings (B = 4096, T = 300 steps of
+    1 ms) fitted to their own observed far-end positions by Adam on the library's link-mass
+    gradients (rollout + reverse pass + Adam per iteration). Timed: ``iters`` iterations after 3
+    warm-up iterations; reported with the fraction of pendulums whose masses are within 1 %."""
+    import numpy as np
+    import torch
+
+    from paper_1611_01652_gb300 import workloads as WL
+    from paper_1611_01652_gb300.sysid import Fit, observe
+
+    m = WL.pendulum_sysid(B=args.batch, K=4, horizon=300)
+    obs = observe(m, {"mass": m.mass_true})
+    f = Fit(m, obs, names=("mass",), lr=0.03, shared=4)
+    for _ in range(3):
+        f.step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(iters - 3):
+        f.step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / (iters - 3)
+    loss = f.run(0).cpu().numpy()
+    err = np.abs(f.p["mass"].cpu().numpy() - m.mass_true[::4]).max(axis=1) / m.mass_true[::4].min(axis=1)
+    return {"workload": "pendulum mass identification: %d 3-link pendulums x 4 swings, T = 300, %d Adam iterations"
+                        % (m.B // 4, iters),
+            "ms_per_iteration": ms, "value": m.B * m.horizon / (ms / 1e3), "unit": "inst-steps/s (fwd+adjoint+Adam)",
+            "fitted_within_1pct": float((err < 1e-2).mean()), "loss_median_m2": float(np.median(loss))}
+
+
 def time_wide_controller(args, alpha):
     """The quadruped B=4096, T=1000 with the 64-1024-1024-8 controller (1,124,360 parameters,
     batched tensor-core products between step launches): forward + adjoint of the plain solver
@@ -401,6 +436,9 @@ def main():
     torch.cuda.set_device(local_rank)
     if args.wide_only:
         print(json.dumps(time_wide_controller(args, args.alpha)))
+        return
+    if args.sysid_only:
+        print(json.dumps(time_sysid(args)))
         return
     if args.recurrent_only:
         print(json.dumps(time_recurrent_controller(args, args.alpha)))
@@ -482,6 +520,7 @@ def main():
     arms = None if args.no_arms else time_uneven_arms(args)
     wide = None if args.no_wide else time_wide_controller(args, args.alpha)
     recurrent = None if args.no_recurrent else time_recurrent_controller(args, args.alpha)
+    sysid = None if args.no_sysid else time_sysid(args)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -524,7 +563,7 @@ def main():
                    "batch": B, "horizon": T, "iters": head["iters"], "ckpt_every": head["ckpt_every"],
                    "l2": "working set (solver tape + controller activations) >> 129 MB L2; no flush needed"},
         "plain": plain, "warmstart": ws, "gate": gate, "uneven_arms": arms, "wide_controller": wide,
-        "recurrent_controller": recurrent,
+        "recurrent_controller": recurrent, "sysid": sysid,
         "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": head["clocks"],
         "plain_clocks": p_ck if ws else None,
         "gpu_launches": launches_per_step * args.steps, "fwd_ms": head["fwd_ms"], "bwd_ms": head["bwd_ms"],

@@ -50,7 +50,8 @@ SYMBOLS = ("dp_create_world", "dp_free", "dp_num_params", "dp_num_slots", "dp_sc
            "dp_set_state", "dp_get_state", "dp_step", "dp_rollout", "dp_backward", "dp_sync", "dp_last_error",
            "dp_ckpt_every", "dp_backward_noalloc", "dp_set_warmstart", "dp_harvest", "dp_set_residual",
            "dp_get_residual", "dp_ws_workspace_floats", "dp_ws_param_count", "dp_ws_loss_grad", "dp_ws_forward",
-           "dp_ws_adam", "dp_set_impulses", "dp_get_impulses", "dp_set_recurrent", "dp_get_recurrent")
+           "dp_ws_adam", "dp_set_impulses", "dp_get_impulses", "dp_set_recurrent", "dp_get_recurrent",
+           "dp_set_params")
 
 
 def load(build=True):
@@ -83,6 +84,7 @@ def load(build=True):
     lib.dp_set_impulses.argtypes = [C.c_void_p, C.c_void_p]
     lib.dp_get_impulses.argtypes = [C.c_void_p, C.c_void_p]
     lib.dp_set_recurrent.argtypes = [C.c_void_p, C.c_void_p]
+    lib.dp_set_params.argtypes = [C.c_void_p, C.c_void_p]
     lib.dp_get_recurrent.argtypes = [C.c_void_p, C.c_void_p]
     lib.dp_harvest.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]
     lib.dp_set_residual.argtypes = [C.c_void_p, C.c_int32]
@@ -107,6 +109,12 @@ class DPError(RuntimeError):
 def _check(status):
     if status != DP_OK:
         raise DPError(status, _lib.dp_last_error().decode())
+
+
+def torch_float32():
+    import torch
+
+    return torch.float32
 
 
 def ptr(x):
@@ -239,6 +247,23 @@ class World:
                 v = dparams.get(k)
                 setattr(pg, k, C.cast(ptr(v), PF) if v is not None else None)
         _check(_lib.dp_backward(self._h, ptr(dloss), ptr(dW), ptr(dstate0), C.byref(pg) if pg is not None else None))
+
+    def set_params(self, **groups):
+        """Replace per-instance parameter groups in place (``mass=``, ``sph_e=``, ... arrays of the
+        model's shapes, host or device); the next backward needs a new rollout."""
+        pg = ParamGrads()
+        keep = []
+        for k in PARAM_GRADS:
+            v = groups.pop(k, None)
+            if isinstance(v, np.ndarray):
+                v = np.ascontiguousarray(v, np.float32)
+                keep.append(v)
+            elif v is not None and v.dtype != torch_float32():
+                raise TypeError("%s must be float32" % k)
+            setattr(pg, k, C.cast(ptr(v), PF) if v is not None else None)
+        if groups:
+            raise ValueError("unknown parameter groups: %s" % sorted(groups))
+        _check(_lib.dp_set_params(self._h, C.byref(pg)))
 
     def backward_noalloc(self, dloss, dW):
         """dL/dW through the last rollout without any device allocation (static scratch)."""

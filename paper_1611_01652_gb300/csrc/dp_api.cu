@@ -798,6 +798,24 @@ dp_status dp_get_impulses(dp_world* w, float* lam) {
   return DP_OK;
 }
 
+dp_status dp_set_params(dp_world* w, const dp_param_grads* p) {
+  if (!w || !p) return fail(DP_EINVAL, "world or p is NULL");
+  const DevTopo& T = w->Tf;
+  struct G { const float* src; int off, n; } groups[] = {
+      {p->mass, T.o_mass, T.nb},           {p->inertia, T.o_inertia, 3 * T.nb},  {p->anchor, T.o_anchor, 6 * T.nj},
+      {p->limit, T.o_limit, 2 * T.nj},     {p->motor, T.o_motor, 3 * T.nj},      {p->sph_off, T.o_sph_off, 3 * T.ns},
+      {p->sph_rad, T.o_sph_rad, T.ns},     {p->sph_mu, T.o_sph_mu, T.ns},        {p->sph_e, T.o_sph_e, T.ns},
+      {p->loss_point, T.o_loss_point, 3},  {p->loss_target, T.o_loss_target, 3}};
+  for (const G& g : groups) {
+    if (!g.src || g.n == 0) continue;
+    if ((size_t)w->B * g.n > w->stage_floats) return fail(DP_EINVAL, "staging buffer too small");
+    CU(cudaMemcpyAsync(w->stage, g.src, sizeof(float) * (size_t)w->B * g.n, cudaMemcpyDefault, w->stream));
+    CU(launch_param_in(w->B, w->Bp, g.off, g.n, w->stage, const_cast<float*>(w->D.prm), w->stream));
+  }
+  w->have_rollout = false;  // a recorded rollout belongs to the old parameters
+  return DP_OK;
+}
+
 dp_status dp_set_recurrent(dp_world* w, const float* h) {
   if (!w || !h) return fail(DP_EINVAL, "world or h is NULL");
   const int H = w->Tf.n_rec;

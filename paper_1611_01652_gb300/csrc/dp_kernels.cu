@@ -87,6 +87,14 @@ __global__ void k_param_out(int B, int Bp, int o, int n, const float* __restrict
   if (i >= B) return;
   for (int f = 0; f < n; ++f) dst[(size_t)i * n + f] = src[(size_t)(o + f) * Bp + i];
 }
+// Per-instance parameter group [B][n] -> the [field][Bp] parameter array (padded lanes copy the
+// last instance).
+__global__ void k_param_in(int B, int Bp, int o, int n, const float* __restrict__ src, float* dst) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Bp) return;
+  const int si = min(i, B - 1);
+  for (int f = 0; f < n; ++f) dst[(size_t)(o + f) * Bp + i] = src[(size_t)si * n + f];
+}
 __global__ void k_scale_out(int B, const float* __restrict__ src, float sc, float* dst) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < B) dst[i] = src[i] * sc;
@@ -480,6 +488,10 @@ cudaError_t launch_state_out(int B, int Bp, int nf, const float* src, float* dst
 }
 cudaError_t launch_param_out(int B, int Bp, int o, int n, const float* src, float* dst, cudaStream_t s) {
   k_param_out<<<(B + 127) / 128, 128, 0, s>>>(B, Bp, o, n, src, dst);
+  return cudaGetLastError();
+}
+cudaError_t launch_param_in(int B, int Bp, int o, int n, const float* src, float* dst, cudaStream_t s) {
+  k_param_in<<<(Bp + 127) / 128, 128, 0, s>>>(B, Bp, o, n, src, dst);
   return cudaGetLastError();
 }
 cudaError_t launch_scale_out(int B, const float* src, float scale, float* dst, cudaStream_t s) {

@@ -11,6 +11,7 @@ cudaError_t launch_scale_out(int B, const float* src, float scale, float* dst, c
 cudaError_t launch_state_in(int B, int Bp, int nf, const float* src, float* dst, cudaStream_t s);
 cudaError_t launch_state_out(int B, int Bp, int nf, const float* src, float* dst, cudaStream_t s);
 cudaError_t launch_param_out(int B, int Bp, int o, int n, const float* src, float* dst, cudaStream_t s);
+cudaError_t launch_param_in(int B, int Bp, int o, int n, const float* src, float* dst, cudaStream_t s);
 cudaError_t launch_pad_scalar(int B, int Bp, const float* src, float* dst, cudaStream_t s);
 cudaError_t launch_forward(const DevTopo& T, const DevPtrs& D, const float* x0, int t0, int nsteps, int rollout,
                            int record, cudaStream_t s);

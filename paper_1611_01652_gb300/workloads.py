@@ -209,6 +209,52 @@ def ball(B=1, seed=1000, horizon=300, iters=20, dt=0.01):
                  loss_kind=L_SQDIST, loss_mode=M_FINAL, loss_body=0, **d)
 
 
+def pendulum_sysid(B=4096, K=4, seed=1004, horizon=300, iters=10, dt=0.001, m0=1.0, rod_radius=0.02):
+    """3-link pendulum chains for system identification of their link masses: B / K pendulums,
+    each released K times from different seeded angles (instances g*K .. g*K+K-1 are the swings
+    of pendulum g). Chains as ``pendulum3`` (lengths U[0.3,1.0] m, hinges about y, uniform-rod
+    inertias of the nominal mass ``m0``), relative initial angles U[-pi/2, pi/2]. Each pendulum has
+    hidden link masses ``mass_true`` U[0.5,2.0] kg (per instance, equal within a pendulum; the
+    rotational inertias are the known nominal ones); the model starts from ``m0``. Loss: squared
+    distance of the last link's far end at the final step to ``loss_target`` (its observed
+    position, set by the caller)."""
+    assert B % K == 0
+    rng = np.random.default_rng(seed)
+    nb = nj = 3
+    d = _empty(B, nb, nj, 0)
+    mass_true = np.zeros((B, nb))
+    for g in range(B // K):
+        L = rng.uniform(0.3, 1.0, size=nb)
+        mt = rng.uniform(0.5, 2.0, size=nb)
+        for i in range(g * K, (g + 1) * K):
+            th = rng.uniform(-math.pi / 2, math.pi / 2, size=nb)
+            phi = 0.0
+            pivot = np.zeros(3)
+            for k in range(nb):
+                phi += th[k]
+                R = _rot_y(phi)
+                c = pivot + R @ np.array([0.0, 0.0, -L[k] / 2])
+                d["state0"][i, k] = _state(c, R, np.zeros(3), np.zeros(3))
+                pivot = pivot + R @ np.array([0.0, 0.0, -L[k]])
+                d["mass"][i, k] = m0
+                It = m0 * (3 * rod_radius ** 2 + L[k] ** 2) / 12.0
+                d["inertia"][i, k] = [It, It, 0.5 * m0 * rod_radius ** 2]
+                d["anchor"][i, k, 0] = [0.0, 0.0, 0.0] if k == 0 else [0.0, 0.0, -L[k - 1] / 2]
+                d["anchor"][i, k, 1] = [0.0, 0.0, L[k] / 2]
+                d["axis"][i, k, :] = [0.0, 1.0, 0.0]
+                d["ref"][i, k, :] = [1.0, 0.0, 0.0]
+            d["loss_point"][i] = [0.0, 0.0, -L[2] / 2]
+            mass_true[i] = mt
+    _finish(d)
+    mdl = Model(name="pendulum_sysid", B=B, joint_type=np.full(nj, HINGE, np.int32),
+                joint_body=np.array([[-1, 0], [0, 1], [1, 2]], np.int32), joint_flags=np.zeros(nj, np.int32),
+                sphere_body=np.zeros(0, np.int32), pair_sphere=np.zeros((0, 2), np.int32), nb=nb, dt=dt,
+                iters=iters, horizon=horizon, loss_kind=L_SQDIST, loss_mode=M_FINAL, loss_body=2, **d)
+    mdl.mass_true = f32(mass_true)
+    mdl.throws = K
+    return mdl
+
+
 def pendulum3(B=1024, seed=1001, horizon=1000, iters=10, dt=0.001, ckpt_every=32, rod_radius=0.02):
     """3-link pendulum chains, first hinge pinned to the world at the origin, horizontal (y)
     hinge axes. Links are uniform rods (thin cylinders of radius ``rod_radius``) of length
