@@ -361,3 +361,59 @@ def ws_groups(m):
         elif kind[i] == 6:
             out.append((WS_PAIR, (i, i + 1, i + 2)))
     return out
+
+
+# ----------------------------------------------------------------------------- camera
+class Camera(C.Structure):
+    _fields_ = [("W", C.c_int32), ("H", C.c_int32), ("f", C.c_double), ("plane", C.c_double), ("pos", C.c_double * 3),
+                ("rot", C.c_double * 9)]
+
+
+class Scene(C.Structure):
+    _fields_ = [("n_obj", C.c_int32), ("body", PI), ("center", PD), ("half", PD), ("tex", PI), ("n_tex", C.c_int32),
+                ("tex_h", C.c_int32), ("tex_w", C.c_int32), ("tex_data", PD)]
+
+
+def _camera_scene(cs, keep, tex=None):
+    cam = Camera()
+    cam.W, cam.H, cam.f, cam.plane = int(cs.W), int(cs.H), float(cs.f), float(cs.plane)
+    for k in range(3):
+        cam.pos[k] = float(cs.cam_pos[k])
+    for k in range(9):
+        cam.rot[k] = float(np.asarray(cs.cam_rot).reshape(-1)[k])
+    sc = Scene()
+    sc.n_obj = len(cs.obj_body)
+    sc.body, sc.center, sc.half, sc.tex = keep.i32(cs.obj_body), keep.f64(cs.obj_center), keep.f64(cs.obj_half), keep.i32(cs.obj_tex)
+    t = np.asarray(cs.textures if tex is None else tex, np.float64)
+    sc.n_tex, sc.tex_h, sc.tex_w = t.shape[0], t.shape[1], t.shape[2]
+    sc.tex_data = keep.f64(t)
+    return cam, sc
+
+
+def render(cs, state, tex=None):
+    """Frame [H, W, 3] of camera scene ``cs`` (see ``workloads.camera_scene``) for one state
+    [nb, 18], and the box each pixel sees [H, W] (-1: none)."""
+    keep = _Keep()
+    cam, sc = _camera_scene(cs, keep, tex)
+    state = np.ascontiguousarray(np.asarray(state, np.float64).reshape(-1))
+    img = np.zeros((cs.H, cs.W, 3))
+    hit = np.zeros((cs.H, cs.W), np.int32)
+    r = lib().orc_render(C.byref(cam), C.byref(sc), state.size // 18, _dp(state), _dp(img), _ip(hit))
+    if r != 0:
+        raise ValueError("oracle rejected the camera or scene")
+    return img, hit
+
+
+def render_grad(cs, state, dimage, tex=None):
+    """Gradient of sum(dimage * frame) w.r.t. the state [nb, 18] and the textures."""
+    keep = _Keep()
+    cam, sc = _camera_scene(cs, keep, tex)
+    state = np.ascontiguousarray(np.asarray(state, np.float64).reshape(-1))
+    dimage = np.ascontiguousarray(np.asarray(dimage, np.float64).reshape(-1))
+    ds = np.zeros_like(state)
+    t = np.asarray(cs.textures if tex is None else tex)
+    dt = np.zeros(t.shape)
+    r = lib().orc_render_grad(C.byref(cam), C.byref(sc), state.size // 18, _dp(state), _dp(dimage), _dp(ds), _dp(dt))
+    if r != 0:
+        raise ValueError("oracle rejected the camera or scene")
+    return ds.reshape(-1, 18), dt

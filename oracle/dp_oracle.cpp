@@ -1287,3 +1287,145 @@ int orc_flops(const orc_topo* T, const orc_inst* I, const double* W, int32_t hor
 }
 
 }  // extern "C"
+
+// ========================================================================================
+// Differentiable camera (section 4, the inverted pendulum seen by a camera): a pinhole ray
+// tracer over textured oriented boxes carried by the bodies. Per pixel (row i, column j) the ray
+// from the camera centre C runs along d = R_c^T (P ((j + 1/2) - W/2) / f, P ((i + 1/2) - H/2) / f, P)
+// (f: focal length in pixels, P: distance of the projection plane), so that t = 1 is the
+// projection plane; every box is intersected (slab test in the box's frame), and of
+// the hits at t >= 1 (in front of the projection plane) the nearest is kept. The hit face (the
+// box axis k of the entry slab) gives texture coordinates from the two other local coordinates,
+// u = (x_a / h_a + 1) / 2, v = (x_b / h_b + 1) / 2 with a = (k + 1) mod 3, b = (k + 2) mod 3,
+// and the colour is the bilinear interpolation of the box's texture (texel centres at
+// ((c + 1/2) / Wt, (r + 1/2) / Ht), clamped at the edges), which gives the frame non-zero
+// derivatives with respect to the state and the texture. Rays that hit nothing are black.
+// Reverse mode keeps the discrete choices (which box, which face, which texels) of the forward
+// pass and differentiates the rest (the oracle's tape).
+extern "C" {
+typedef struct {
+  int32_t W, H;     // image width and height in pixels
+  double f;         // focal length in pixels
+  double plane;     // distance of the projection plane from C (world units); hits before it are not seen
+  double pos[3];    // camera centre C (world)
+  double rot[9];    // R_c, row-major: rows are the camera's x (image right), y (image down) and z (optical) axes
+} orc_camera;
+typedef struct {
+  int32_t n_obj;
+  const int32_t* body;    // [n_obj] body carrying the box (-1: the world)
+  const double* center;   // [n_obj][3] box centre in the body frame
+  const double* half;     // [n_obj][3] half extents along the body axes
+  const int32_t* tex;     // [n_obj] texture index
+  int32_t n_tex, tex_h, tex_w;
+  const double* tex_data; // [n_tex][tex_h][tex_w][3]
+} orc_scene;
+}  // extern "C"
+
+namespace orc {
+
+template <class S>
+static void render_impl(const orc_camera& cam, const orc_scene& sc, const std::vector<S>& x, const std::vector<S>& tex,
+                        std::vector<S>& img, int32_t* hit_obj) {
+  const int W = cam.W, H = cam.H, th = sc.tex_h, tw = sc.tex_w;
+  img.assign((size_t)W * H * 3, S(0.0));
+  for (int i = 0; i < H; ++i)
+    for (int j = 0; j < W; ++j) {
+      const double dc[3] = {cam.plane * ((j + 0.5) - 0.5 * W) / cam.f, cam.plane * ((i + 0.5) - 0.5 * H) / cam.f, cam.plane};
+      double d[3];
+      for (int r = 0; r < 3; ++r) d[r] = cam.rot[0 * 3 + r] * dc[0] + cam.rot[1 * 3 + r] * dc[1] + cam.rot[2 * 3 + r] * dc[2];
+      int best = -1, bk = 0;
+      double bt = INFINITY;
+      S bl[3], dl[3];  // ray in the best box's frame
+      for (int o = 0; o < sc.n_obj; ++o) {
+        const int b = sc.body[o];
+        // box frame: centre c_w = p + R c, axes = columns of R (R maps body to world)
+        S R[9], p[3];
+        for (int k = 0; k < 9; ++k) R[k] = b >= 0 ? x[18 * b + 3 + k] : S(k % 4 == 0 ? 1.0 : 0.0);
+        for (int k = 0; k < 3; ++k) p[k] = b >= 0 ? x[18 * b + k] : S(0.0);
+        S cw[3], ol[3], dlo[3];
+        for (int r = 0; r < 3; ++r)
+          cw[r] = p[r] + R[3 * r] * sc.center[3 * o] + R[3 * r + 1] * sc.center[3 * o + 1] + R[3 * r + 2] * sc.center[3 * o + 2];
+        for (int k = 0; k < 3; ++k) {  // R^T (C - c_w), R^T d
+          ol[k] = R[k] * (S(cam.pos[0]) - cw[0]) + R[3 + k] * (S(cam.pos[1]) - cw[1]) + R[6 + k] * (S(cam.pos[2]) - cw[2]);
+          dlo[k] = R[k] * d[0] + R[3 + k] * d[1] + R[6 + k] * d[2];
+        }
+        double tn = -INFINITY, tf = INFINITY;
+        int kn = 0;
+        bool miss = false;
+        for (int k = 0; k < 3; ++k) {
+          const double h = sc.half[3 * o + k];
+          if (val(dlo[k]) == 0.0) {
+            if (std::fabs(val(ol[k])) > h) miss = true;
+            continue;
+          }
+          double t1 = (-h - val(ol[k])) / val(dlo[k]), t2 = (h - val(ol[k])) / val(dlo[k]);
+          if (t1 > t2) std::swap(t1, t2);
+          if (t1 > tn) { tn = t1; kn = k; }
+          tf = std::min(tf, t2);
+        }
+        if (miss || !(tn <= tf) || !(tn >= 1.0) || !(tn < bt)) continue;
+        best = o; bk = kn; bt = tn;
+        for (int k = 0; k < 3; ++k) { bl[k] = ol[k]; dl[k] = dlo[k]; }
+      }
+      if (hit_obj) hit_obj[(size_t)i * W + j] = best;
+      if (best < 0) continue;
+      // the entry plane: x_k = s h_k with s = -sign(d_k)
+      const double hk = sc.half[3 * best + bk];
+      const double s = val(dl[bk]) > 0.0 ? -1.0 : 1.0;
+      S t = (S(s * hk) - bl[bk]) / dl[bk];
+      const int a = (bk + 1) % 3, c = (bk + 2) % 3;
+      S u = ((bl[a] + t * dl[a]) / S(sc.half[3 * best + a]) + S(1.0)) * S(0.5);
+      S v = ((bl[c] + t * dl[c]) / S(sc.half[3 * best + c]) + S(1.0)) * S(0.5);
+      // bilinear texture sample, texel centres at (c + 1/2) / tw, clamped at the edges
+      S xs = u * S((double)tw) - S(0.5), ys = v * S((double)th) - S(0.5);
+      const double x0f = std::floor(val(xs)), y0f = std::floor(val(ys));
+      S fx = xs - S(x0f), fy = ys - S(y0f);
+      auto cl = [](int q, int n) { return q < 0 ? 0 : (q >= n ? n - 1 : q); };
+      const int x0 = cl((int)x0f, tw), x1 = cl((int)x0f + 1, tw), y0 = cl((int)y0f, th), y1 = cl((int)y0f + 1, th);
+      const size_t tb = (size_t)sc.tex[best] * th * tw * 3;
+      for (int ch = 0; ch < 3; ++ch) {
+        const S t00 = tex[tb + ((size_t)y0 * tw + x0) * 3 + ch], t01 = tex[tb + ((size_t)y0 * tw + x1) * 3 + ch];
+        const S t10 = tex[tb + ((size_t)y1 * tw + x0) * 3 + ch], t11 = tex[tb + ((size_t)y1 * tw + x1) * 3 + ch];
+        img[((size_t)i * W + j) * 3 + ch] = (S(1.0) - fy) * ((S(1.0) - fx) * t00 + fx * t01) + fy * ((S(1.0) - fx) * t10 + fx * t11);
+      }
+    }
+}
+
+}  // namespace orc
+
+extern "C" {
+
+// Frame [H][W][3] of the scene for one instance's state [nb][18]; hit_obj [H][W] (optional)
+// receives the index of the box each pixel sees (-1: none).
+int orc_render(const orc_camera* cam, const orc_scene* sc, int32_t nb, const double* state, double* image,
+               int32_t* hit_obj) {
+  if (!cam || !sc || cam->W < 1 || cam->H < 1 || sc->tex_h < 1 || sc->tex_w < 1) return -1;
+  std::vector<double> x(state, state + 18 * nb), tex(sc->tex_data, sc->tex_data + (size_t)sc->n_tex * sc->tex_h * sc->tex_w * 3), img;
+  render_impl<double>(*cam, *sc, x, tex, img, hit_obj);
+  std::memcpy(image, img.data(), sizeof(double) * img.size());
+  return 0;
+}
+
+// Reverse mode of orc_render for the scalar sum(dimage * image): its gradient with respect to
+// the state [nb][18] (dstate; velocities get zero) and to every texel (dtex, optional).
+int orc_render_grad(const orc_camera* cam, const orc_scene* sc, int32_t nb, const double* state, const double* dimage,
+                    double* dstate, double* dtex) {
+  if (!cam || !sc || cam->W < 1 || cam->H < 1 || sc->tex_h < 1 || sc->tex_w < 1) return -1;
+  Tape tape;
+  Tape* saved = g_tape;
+  g_tape = &tape;
+  const size_t ntex = (size_t)sc->n_tex * sc->tex_h * sc->tex_w * 3;
+  std::vector<AD> x = lift_leaf(state, 18 * nb), tex = lift_leaf(sc->tex_data, ntex), img;
+  render_impl<AD>(*cam, *sc, x, tex, img, nullptr);
+  tape.adj.assign(tape.pa.size(), 0.0);
+  for (size_t k = 0; k < img.size(); ++k)
+    if (img[k].id >= 0) tape.adj[img[k].id] += dimage[k];
+  tape.backward();
+  for (int k = 0; k < 18 * nb; ++k) dstate[k] = tape.adj[x[k].id];
+  if (dtex)
+    for (size_t k = 0; k < ntex; ++k) dtex[k] = tape.adj[tex[k].id];
+  g_tape = saved;
+  return 0;
+}
+
+}  // extern "C"

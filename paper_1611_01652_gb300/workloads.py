@@ -255,6 +255,60 @@ def pendulum_sysid(B=4096, K=4, seed=1004, horizon=300, iters=10, dt=0.001, m0=1
     return mdl
 
 
+class CameraScene:
+    """A camera looking at textured boxes carried by a model's bodies (attributes: W, H, f (focal
+    length in pixels), plane (distance of the projection plane, m), cam_pos [3], cam_rot [3, 3] (rows: image right, image down, optical axis), obj_body,
+    obj_center [n, 3], obj_half [n, 3], obj_tex, textures [n_tex, th, tw, 3], states [B, nb, 18])."""
+
+
+def procedural_textures(n, th=64, tw=64, seed=7):
+    """Seeded smooth colour patterns (sums of a few random plane waves plus a checker), values in
+    [0, 1]: stand-ins for the photographs the paper's textures were made from."""
+    rng = np.random.default_rng(seed)
+    yy, xx = np.meshgrid((np.arange(th) + 0.5) / th, (np.arange(tw) + 0.5) / tw, indexing="ij")
+    out = np.zeros((n, th, tw, 3), np.float32)
+    for t in range(n):
+        for ch in range(3):
+            v = np.full((th, tw), 0.5)
+            for _ in range(3):
+                kx, ky, ph = rng.uniform(-8, 8), rng.uniform(-8, 8), rng.uniform(0, 2 * math.pi)
+                v += 0.15 * np.sin(2 * math.pi * (kx * xx + ky * yy) + ph)
+            v += 0.1 * np.sign(np.sin(2 * math.pi * 4 * xx) * np.sin(2 * math.pi * 4 * yy))
+            out[t, :, :, ch] = np.clip(v, 0.0, 1.0)
+    return out
+
+
+def camera_scene(B=4096, W=288, H=96, seed=1005, tex_size=64):
+    """The 3-link pendulum seen by a camera (the paper's camera sensor, section 4, at its 288 x 96
+    resolution): the three links as textured boxes (0.12 x 0.12 x L m) on bodies 0-2, a textured
+    backdrop box 1 m behind the hinge plane, and a camera 3 m in front of it looking along +y
+    (image right = +x, image down = -z), focal length W / 2 pixels, projection plane 0.05 m in
+    front of it. States: ``pendulum3``
+    chains (seeded lengths and angles), positions only."""
+    pm = pendulum3(B=B, seed=seed, horizon=1)
+    cs = CameraScene()
+    cs.W, cs.H, cs.f, cs.plane = W, H, 0.5 * W, 0.05
+    cs.cam_pos = np.array([0.0, -3.0, -0.9])
+    cs.cam_rot = np.array([[1.0, 0.0, 0.0], [0.0, 0.0, -1.0], [0.0, 1.0, 0.0]])
+    L = pm.link_length[0]
+    cs.obj_body = np.array([-1, 0, 1, 2], np.int32)
+    cs.obj_center = np.array([[0.0, 1.0, -0.9], [0.0, 0.0, 0.0], [0.0, 0.0, 0.0], [0.0, 0.0, 0.0]])
+    cs.obj_half = np.array([[8.0, 0.05, 3.0], [0.06, 0.06, L[0] / 2], [0.06, 0.06, L[1] / 2], [0.06, 0.06, L[2] / 2]])
+    cs.obj_tex = np.array([0, 1, 2, 3], np.int32)
+    cs.textures = procedural_textures(4, tex_size, tex_size, seed)
+    st = np.asarray(pm.state0, np.float32).copy()
+    # every instance carries the first chain's link lengths (the boxes are shared); its own angles
+    for i in range(B):
+        R = [st[i, k, 3:12].reshape(3, 3) for k in range(3)]
+        pivot = np.zeros(3)
+        for k in range(3):
+            st[i, k, 0:3] = pivot + R[k] @ np.array([0.0, 0.0, -L[k] / 2])
+            pivot = pivot + R[k] @ np.array([0.0, 0.0, -L[k]])
+    cs.states = st
+    cs.nb = 3
+    return cs
+
+
 def pendulum3(B=1024, seed=1001, horizon=1000, iters=10, dt=0.001, ckpt_every=32, rod_radius=0.02):
     """3-link pendulum chains, first hinge pinned to the world at the origin, horizontal (y)
     hinge axes. Links are uniform rods (thin cylinders of radius ``rod_radius``) of length

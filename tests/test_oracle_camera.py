@@ -1,0 +1,119 @@
+"""Pins of the oracle's differentiable camera (section 4: pinhole rays through the pixel centres,
+nearest hit in front of the projection plane, bilinear texture interpolation) against facts that
+do not come from its own formulas: the pinhole geometry of a fronto-parallel face worked out
+here, a linear texture (which bilinear interpolation reproduces exactly), the visibility rules,
+and central differences of its forward pass (no GPU)."""
+import numpy as np
+
+import oracle as O
+from paper_1611_01652_gb300.workloads import CameraScene
+
+ROT_Y = np.array([[1.0, 0.0, 0.0], [0.0, 0.0, -1.0], [0.0, 1.0, 0.0]])  # look along +y, image down = -z
+
+
+def scene(boxes, W=40, H=16, f=20.0, plane=0.05, tex=None, th=8, tw=8):
+    """boxes: list of (body, centre, half, tex index); camera at the origin looking along +y."""
+    cs = CameraScene()
+    cs.W, cs.H, cs.f, cs.plane = W, H, f, plane
+    cs.cam_pos = np.zeros(3)
+    cs.cam_rot = ROT_Y
+    cs.obj_body = np.array([b[0] for b in boxes], np.int32)
+    cs.obj_center = np.array([b[1] for b in boxes], np.float64)
+    cs.obj_half = np.array([b[2] for b in boxes], np.float64)
+    cs.obj_tex = np.array([b[3] for b in boxes], np.int32)
+    if tex is None:
+        tex = np.random.default_rng(0).uniform(0, 1, size=(max(b[3] for b in boxes) + 1, th, tw, 3))
+    cs.textures = tex
+    return cs
+
+
+def linear_texture(th, tw, coef):
+    """Texel (r, c, ch) = a u_c + b v_r + c0 at the texel centres u_c = (c + 1/2)/tw, v_r = (r + 1/2)/th."""
+    u = (np.arange(tw) + 0.5) / tw
+    v = (np.arange(th) + 0.5) / th
+    out = np.zeros((1, th, tw, 3))
+    for ch, (a, b, c0) in enumerate(coef):
+        out[0, :, :, ch] = a * u[None, :] + b * v[:, None] + c0
+    return out
+
+
+def test_fronto_parallel_face_with_linear_texture():
+    """A world box whose -y face (x in [-hx, hx], z in [-hz, hz]) sits at distance D fills part of
+    the view. The pixel (i, j) ray meets y = D at x = D ((j + 1/2) - W/2)/f, z = -D ((i + 1/2) -
+    H/2)/f; the face's coordinates are u = (z / hz + 1)/2, v = (x / hx + 1)/2 (axis k = y, then z,
+    then x); a texture linear in (u, v) comes back exactly wherever the sample is inside the
+    texel-centre grid."""
+    W, H, f, D = 40, 16, 20.0, 2.0
+    hx, hy, hz = 1.5, 0.1, 0.6
+    th, tw = 8, 8
+    coef = [(0.3, 0.5, 0.1), (-0.2, 0.4, 0.5), (0.7, -0.1, 0.2)]
+    cs = scene([(-1, [0.0, D + hy, 0.0], [hx, hy, hz], 0)], W, H, f, tex=linear_texture(th, tw, coef), th=th, tw=tw)
+    img, hit = O.render(cs, np.zeros((0, 18)))
+    checked = 0
+    for i in range(H):
+        for j in range(W):
+            x = D * ((j + 0.5) - W / 2) / f
+            z = -D * ((i + 0.5) - H / 2) / f
+            inside = abs(x) <= hx and abs(z) <= hz
+            assert hit[i, j] == (0 if inside else -1), (i, j)
+            if not inside:
+                assert np.all(img[i, j] == 0.0)
+                continue
+            u, v = (z / hz + 1) / 2, (x / hx + 1) / 2
+            if not (0.5 / tw <= u <= 1 - 0.5 / tw and 0.5 / th <= v <= 1 - 0.5 / th):
+                continue
+            for ch, (a, b, c0) in enumerate(coef):
+                assert abs(img[i, j, ch] - (a * u + b * v + c0)) <= 1e-12, (i, j, ch)
+            checked += 1
+    assert checked >= 100
+
+
+def test_nearest_hit_in_front_of_the_projection_plane():
+    """Along the optical axis: of two boxes the nearer is seen; a box between the camera and the
+    projection plane, or behind the camera, is not seen."""
+    near = (-1, [0.0, 1.0, 0.0], [0.3, 0.05, 0.3], 0)
+    far = (-1, [0.0, 2.0, 0.0], [2.0, 0.05, 2.0], 1)
+    inside_plane = (-1, [0.0, 0.02, 0.0], [0.5, 0.01, 0.5], 2)  # y in [0.01, 0.03] < plane 0.05
+    behind = (-1, [0.0, -1.0, 0.0], [5.0, 0.05, 5.0], 3)
+    cs = scene([far, behind, inside_plane, near])
+    _, hit = O.render(cs, np.zeros((0, 18)))
+    assert hit[8, 20] == 3  # the near box, index 3 in the list
+    assert hit[0, 0] == 0  # beyond the near box's silhouette: the far backdrop
+    assert not np.any(hit == 1) and not np.any(hit == 2)
+
+
+def test_gradients_match_central_differences():
+    """A body-carried box fills the view (no silhouette in the frame): the gradient of a random
+    weighting of the frame with respect to the body's position and rotation entries and to the
+    texels equals central differences of the forward pass."""
+    rng = np.random.default_rng(1)
+    th = tw = 6
+    cs = scene([(0, [0.0, 0.0, 0.0], [4.0, 0.2, 3.0], 0)], W=24, H=10, f=10.0, th=th, tw=tw)
+    ang = 0.2
+    Rz = np.array([[np.cos(ang), -np.sin(ang), 0.0], [np.sin(ang), np.cos(ang), 0.0], [0.0, 0.0, 1.0]])
+    x = np.zeros((1, 18))
+    x[0, 0:3] = [0.1, 2.0, -0.05]
+    x[0, 3:12] = Rz.reshape(-1)
+    img, hit = O.render(cs, x)
+    assert np.all(hit == 0)
+    wgt = rng.normal(size=img.shape)
+    ds, dt = O.render_grad(cs, x, wgt)
+
+    def f(xx=None, tt=None):
+        return float(np.sum(wgt * O.render(cs, x if xx is None else xx, tex=tt)[0]))
+
+    for k in list(range(12)):
+        eps = 1e-6
+        xp, xm = x.copy(), x.copy()
+        xp[0, k] += eps
+        xm[0, k] -= eps
+        fd = (f(xp) - f(xm)) / (2 * eps)
+        assert abs(fd - ds[0, k]) <= 1e-6 * max(1.0, abs(fd)), (k, fd, ds[0, k])
+    assert np.all(ds[0, 12:] == 0.0)
+    for idx in [(0, 2, 3, 0), (0, 0, 0, 1), (0, 5, 1, 2), (0, 3, 3, 1)]:
+        eps = 1e-6
+        tp, tm = cs.textures.copy(), cs.textures.copy()
+        tp[idx] += eps
+        tm[idx] -= eps
+        fd = (f(tt=tp) - f(tt=tm)) / (2 * eps)
+        assert abs(fd - dt[idx]) <= 1e-7 * max(1.0, abs(fd)), (idx, fd, dt[idx])
