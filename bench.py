@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--no-wide", action="store_true", help="skip the wide (1.1 M-parameter) controller")
     p.add_argument("--no-recurrent", action="store_true", help="skip the recurrent controller")
     p.add_argument("--no-sysid", action="store_true", help="skip the system-identification fit")
+    p.add_argument("--no-camera", action="store_true", help="skip the differentiable camera")
+    p.add_argument("--camera-only", action="store_true", help="time only the differentiable camera")
     p.add_argument("--sysid-only", action="store_true", help="time only the system-identification fit")
     p.add_argument("--recurrent-only", action="store_true", help="time only the recurrent controller")
     p.add_argument("--wide-only", action="store_true",
@@ -362,6 +364,54 @@ def time_sysid(args, iters=300):
             "fitted_within_1pct": float((err < 1e-2).mean()), "loss_median_m2": float(np.median(loss))}
 
 
+def time_camera(args, reps=20):
+    """The differentiable camera: 4096 frames of 288 x 96 pixels (the paper's resolution) of the
+    3-link pendulum scene per call; forward (frames) and forward + reverse (gradient of a frame
+    weighting w.r.t. the body poses), ``reps`` timed calls each after 3 warm-up calls. Roofline of
+    the forward kernel: HBM, 12 bytes written per pixel (the frame; poses and textures stay in
+    cache)."""
+    import torch
+
+    from paper_1611_01652_gb300 import workloads as WL
+    from paper_1611_01652_gb300.binding import CameraRig
+
+    cs = WL.camera_scene(B=args.batch, W=288, H=96)
+    rig = CameraRig(cs)
+    st = torch.tensor(cs.states, device="cuda")
+    tex = torch.tensor(cs.textures, device="cuda")
+    img = torch.zeros(st.shape[0], cs.H, cs.W, 3, device="cuda")
+    dimg = torch.ones_like(img)
+    ds = torch.zeros_like(st)
+    s = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(reps):
+            fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    f_ms = timed(lambda: rig.render(st, tex, img))
+    fb_ms = timed(lambda: (rig.render(st, tex, img), rig.render_backward(st, tex, dimg, ds)))
+    npix = st.shape[0] * cs.H * cs.W
+    peak, source = 6800.0, "fallback"
+    pf = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    if os.path.exists(pf):
+        with open(pf) as fh:
+            peak, source = float(json.load(fh)["hbm_gbs"]), "measured"
+    achieved = npix * 12 / (f_ms / 1e3) / 1e9
+    return {"workload": "camera: %d frames of 288 x 96, pendulum scene (4 textured boxes)" % st.shape[0],
+            "fwd_ms": f_ms, "fwd_bwd_ms": fb_ms, "frames_per_s_fwd": st.shape[0] / (f_ms / 1e3),
+            "frames_per_s_fwd_bwd": st.shape[0] / (fb_ms / 1e3), "unit": "frames/s",
+            "roofline_fwd": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "peak_source": source}}
+
+
 def time_wide_controller(args, alpha):
     """The quadruped B=4096, T=1000 with the 64-1024-1024-8 controller (1,124,360 parameters,
     batched tensor-core products between step launches): forward + adjoint of the plain solver
@@ -436,6 +486,9 @@ def main():
     torch.cuda.set_device(local_rank)
     if args.wide_only:
         print(json.dumps(time_wide_controller(args, args.alpha)))
+        return
+    if args.camera_only:
+        print(json.dumps(time_camera(args)))
         return
     if args.sysid_only:
         print(json.dumps(time_sysid(args)))
@@ -521,6 +574,7 @@ def main():
     wide = None if args.no_wide else time_wide_controller(args, args.alpha)
     recurrent = None if args.no_recurrent else time_recurrent_controller(args, args.alpha)
     sysid = None if args.no_sysid else time_sysid(args)
+    camera = None if args.no_camera else time_camera(args)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -563,7 +617,7 @@ def main():
                    "batch": B, "horizon": T, "iters": head["iters"], "ckpt_every": head["ckpt_every"],
                    "l2": "working set (solver tape + controller activations) >> 129 MB L2; no flush needed"},
         "plain": plain, "warmstart": ws, "gate": gate, "uneven_arms": arms, "wide_controller": wide,
-        "recurrent_controller": recurrent, "sysid": sysid,
+        "recurrent_controller": recurrent, "sysid": sysid, "camera": camera,
         "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": head["clocks"],
         "plain_clocks": p_ck if ws else None,
         "gpu_launches": launches_per_step * args.steps, "fwd_ms": head["fwd_ms"], "bwd_ms": head["bwd_ms"],

@@ -315,6 +315,56 @@ dp_status dp_ws_forward(const float* W, const float* feats, int64_t n, float* y,
 dp_status dp_ws_adam(float* W, const float* dW, float* m, float* v, int64_t count, int32_t step, float lr, float beta1,
                      float beta2, float eps, void* stream);
 
+/* ------------------------------------------------------------------------------------------
+   Differentiable camera (section 4: the inverted pendulum observed by a camera). A pinhole ray
+   tracer over textured oriented boxes carried by the bodies, batched over instances. The pixel
+   (row i, column j) ray leaves the camera centre C along
+       d = R_c^T (P ((j + 1/2) - W/2) / f, P ((i + 1/2) - H/2) / f, P),
+   so t = 1 is the projection plane at distance P; of the box hits at t >= 1 (in front of the
+   projection plane) the nearest is seen. The entry face (box axis k) gives texture coordinates
+   u = (x_a / h_a + 1) / 2, v = (x_b / h_b + 1) / 2 (a = k+1, b = k+2 mod 3, x: the hit point in the
+   box frame, h: half extents) and the colour is the bilinear interpolation of the box's texture
+   (texel centres at ((c + 1/2) / Wt, (r + 1/2) / Ht), clamped at the edges). Rays that hit
+   nothing are black. Reverse mode keeps the forward pass's discrete choices (box, face, texels)
+   and differentiates the rest, so the frame's derivatives with respect to the body poses and the
+   texels are those of the bilinear interpolation. */
+#define DP_CAMERA_MAX_OBJECTS 16
+
+typedef struct {
+  int32_t width, height; /* pixels */
+  float focal;           /* focal length f in pixels */
+  float plane;           /* distance P of the projection plane from the camera centre (world units) */
+  float position[3];     /* camera centre C (world) */
+  float rotation[9];     /* R_c, row-major: rows are the image-right, image-down and optical axes (world) */
+} dp_camera;
+
+typedef struct {
+  int32_t n_obj;           /* boxes, <= DP_CAMERA_MAX_OBJECTS */
+  const int32_t* body;     /* [n_obj] body carrying the box, -1 = the world frame (host) */
+  const float* center;     /* [n_obj][3] box centre in the body frame (host) */
+  const float* half;       /* [n_obj][3] half extents along the body axes, > 0 (host) */
+  const int32_t* tex;      /* [n_obj] texture index (host) */
+  int32_t n_tex, tex_h, tex_w; /* textures [n_tex][tex_h][tex_w][3] */
+} dp_scene;
+
+/* Frames image [B][H][W][3] (device) of B instances with body states state [B][nb][18]
+   (device; p, R row-major, v, w as dp_get_state) and textures [n_tex][tex_h][tex_w][3]
+   (device); hit [B][H][W] (device, optional) receives the box each pixel sees (-1: none). All
+   buffers are caller-owned; ordered on `stream` (a cudaStream_t or NULL). DP_EINVAL for a
+   malformed camera or scene (dp_camera_last_error says why). */
+dp_status dp_render(const dp_camera* cam, const dp_scene* scene, int32_t n_instances, int32_t n_bodies,
+                    const float* state, const float* textures, float* image, int32_t* hit, void* stream);
+
+/* Reverse mode of dp_render for the scalar sum(dimage * image): dstate [B][nb][18] (device,
+   overwritten; the velocity entries stay zero) and, when not NULL, dtextures [n_tex][tex_h]
+   [tex_w][3] (device, overwritten). */
+dp_status dp_render_backward(const dp_camera* cam, const dp_scene* scene, int32_t n_instances, int32_t n_bodies,
+                             const float* state, const float* textures, const float* dimage, float* dstate,
+                             float* dtextures, void* stream);
+
+/* Message of the last camera call that failed on this thread. */
+const char* dp_camera_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -51,7 +51,7 @@ SYMBOLS = ("dp_create_world", "dp_free", "dp_num_params", "dp_num_slots", "dp_sc
            "dp_ckpt_every", "dp_backward_noalloc", "dp_set_warmstart", "dp_harvest", "dp_set_residual",
            "dp_get_residual", "dp_ws_workspace_floats", "dp_ws_param_count", "dp_ws_loss_grad", "dp_ws_forward",
            "dp_ws_adam", "dp_set_impulses", "dp_get_impulses", "dp_set_recurrent", "dp_get_recurrent",
-           "dp_set_params")
+           "dp_set_params", "dp_render", "dp_render_backward", "dp_camera_last_error")
 
 
 def load(build=True):
@@ -85,6 +85,11 @@ def load(build=True):
     lib.dp_get_impulses.argtypes = [C.c_void_p, C.c_void_p]
     lib.dp_set_recurrent.argtypes = [C.c_void_p, C.c_void_p]
     lib.dp_set_params.argtypes = [C.c_void_p, C.c_void_p]
+    lib.dp_render.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                              C.c_void_p, C.c_void_p]
+    lib.dp_render_backward.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.dp_camera_last_error.restype = C.c_char_p
     lib.dp_get_recurrent.argtypes = [C.c_void_p, C.c_void_p]
     lib.dp_harvest.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]
     lib.dp_set_residual.argtypes = [C.c_void_p, C.c_int32]
@@ -357,3 +362,57 @@ def make_rollout_function():
             return dW, ds, None
 
     return Rollout
+
+
+# ----------------------------------------------------------------------------- camera
+class Camera(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("focal", C.c_float), ("plane", C.c_float),
+                ("position", C.c_float * 3), ("rotation", C.c_float * 9)]
+
+
+class Scene(C.Structure):
+    _fields_ = [("n_obj", C.c_int32), ("body", PI), ("center", PF), ("half", PF), ("tex", PI),
+                ("n_tex", C.c_int32), ("tex_h", C.c_int32), ("tex_w", C.c_int32)]
+
+
+class CameraRig:
+    """The camera and scene of a ``workloads.CameraScene`` as the library's structures (host
+    arrays kept alive here); ``textures`` is a device tensor the caller provides to each call."""
+
+    def __init__(self, cs):
+        load()
+        self.cam = Camera()
+        self.cam.width, self.cam.height, self.cam.focal, self.cam.plane = int(cs.W), int(cs.H), float(cs.f), float(cs.plane)
+        for k in range(3):
+            self.cam.position[k] = float(cs.cam_pos[k])
+        for k in range(9):
+            self.cam.rotation[k] = float(np.asarray(cs.cam_rot).reshape(-1)[k])
+        self._keep = [np.ascontiguousarray(np.asarray(cs.obj_body, np.int32)),
+                      np.ascontiguousarray(np.asarray(cs.obj_center, np.float32)),
+                      np.ascontiguousarray(np.asarray(cs.obj_half, np.float32)),
+                      np.ascontiguousarray(np.asarray(cs.obj_tex, np.int32))]
+        self.scene = Scene()
+        self.scene.n_obj = len(self._keep[0])
+        self.scene.body = self._keep[0].ctypes.data_as(PI)
+        self.scene.center = self._keep[1].ctypes.data_as(PF)
+        self.scene.half = self._keep[2].ctypes.data_as(PF)
+        self.scene.tex = self._keep[3].ctypes.data_as(PI)
+        t = np.asarray(cs.textures)
+        self.scene.n_tex, self.scene.tex_h, self.scene.tex_w = t.shape[0], t.shape[1], t.shape[2]
+        self.nb = int(cs.nb)
+
+    def _check(self, r):
+        if r != 0:
+            raise RuntimeError("camera call failed (status %d): %s" % (r, _lib.dp_camera_last_error().decode()))
+
+    def render(self, state, textures, image, hit=None, stream=None):
+        """Frames image [B, H, W, 3] of states [B, nb, 18] (device tensors)."""
+        s = C.c_void_p(stream.cuda_stream) if stream is not None else None
+        self._check(_lib.dp_render(C.byref(self.cam), C.byref(self.scene), int(state.shape[0]), self.nb, ptr(state),
+                                   ptr(textures), ptr(image), ptr(hit), s))
+
+    def render_backward(self, state, textures, dimage, dstate, dtextures=None, stream=None):
+        """dstate [B, nb, 18] (and dtextures) of sum(dimage * image)."""
+        s = C.c_void_p(stream.cuda_stream) if stream is not None else None
+        self._check(_lib.dp_render_backward(C.byref(self.cam), C.byref(self.scene), int(state.shape[0]), self.nb,
+                                            ptr(state), ptr(textures), ptr(dimage), ptr(dstate), ptr(dtextures), s))

@@ -1,0 +1,386 @@
+// Differentiable camera (arXiv 1611.01652, section 4: the inverted pendulum observed by a camera).
+// A pinhole ray tracer over textured oriented boxes carried by the bodies, batched over
+// instances: one thread per pixel. The pixel (i, j) ray leaves the camera centre C along
+// d = R_c^T (P ((j + 1/2) - W/2) / f, P ((i + 1/2) - H/2) / f, P), so t = 1 is the projection plane
+// at distance P; every box is intersected with the slab test in its own frame, and of the hits at
+// t >= 1 (in front of the projection plane) the nearest is kept. The entry face (box axis k)
+// gives texture coordinates u = (x_a / h_a + 1) / 2, v = (x_b / h_b + 1) / 2 (a = k+1, b = k+2
+// mod 3) and the colour is the bilinear interpolation of the box's texture (texel centres at
+// ((c + 1/2) / Wt, (r + 1/2) / Ht), clamped at the edges), so the frame has non-zero derivatives
+// with respect to the state and the texels. Reverse mode keeps the forward pass's discrete
+// choices (box, face, texels) and differentiates the rest.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <string>
+
+#include "../../include/dp.h"
+
+namespace {
+
+constexpr int kMaxObj = DP_CAMERA_MAX_OBJECTS;
+
+struct CamArgs {
+  int W, H, B, nb, n_obj, th, tw;
+  float f, plane;
+  float C[3], Rc[9];
+  int body[kMaxObj], tex[kMaxObj];
+  float cen[kMaxObj][3], half[kMaxObj][3];
+};
+
+struct Hit {
+  int obj, k;
+  float t;
+  float ol[3], dl[3];  // ray origin and direction in the hit box's frame
+};
+
+// Frame of one box for one instance: R (box to world), centre c_w, and the camera centre in the
+// box frame o = R^T (C - c_w) (the same for every pixel).
+struct BoxFrame {
+  float R[9], cw[3], o[3];
+};
+
+__device__ __forceinline__ float pick3(const float (&v)[3], int k) { return k == 0 ? v[0] : (k == 1 ? v[1] : v[2]); }
+
+__device__ __forceinline__ void box_frame(const CamArgs& A, const float* __restrict__ state, int inst, int o, BoxFrame& F) {
+  const int b = A.body[o];
+  float p[3];
+  if (b >= 0) {
+    const float* x = state + ((size_t)inst * A.nb + b) * 18;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) p[k] = __ldg(x + k);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) F.R[k] = __ldg(x + 3 + k);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) F.R[k] = (k % 4 == 0) ? 1.f : 0.f;
+    p[0] = p[1] = p[2] = 0.f;
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) F.cw[r] = p[r] + F.R[3 * r] * A.cen[o][0] + F.R[3 * r + 1] * A.cen[o][1] + F.R[3 * r + 2] * A.cen[o][2];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) F.o[k] = F.R[k] * (A.C[0] - F.cw[0]) + F.R[3 + k] * (A.C[1] - F.cw[1]) + F.R[6 + k] * (A.C[2] - F.cw[2]);
+}
+
+// The box frames of the block's instance, computed once per block into shared memory (every
+// block of 256 pixels lies in one instance when W * H is a multiple of 256; otherwise each
+// thread computes its own, see `trace`).
+__device__ __forceinline__ bool stage_frames(const CamArgs& A, const float* __restrict__ state, BoxFrame* sf, int& inst0) {
+  const size_t npix = (size_t)A.W * A.H;
+  const size_t first = (size_t)blockIdx.x * blockDim.x;
+  inst0 = (int)(first / npix);
+  const bool uniform = npix % blockDim.x == 0 && inst0 < A.B;
+  if (uniform)
+    for (int o = threadIdx.x; o < A.n_obj; o += blockDim.x) box_frame(A, state, inst0, o, sf[o]);
+  __syncthreads();
+  return uniform;
+}
+
+__device__ __forceinline__ void ray_dir(const CamArgs& A, int i, int j, float d[3]) {
+  const float dc0 = A.plane * (((float)j + 0.5f) - 0.5f * (float)A.W) / A.f;
+  const float dc1 = A.plane * (((float)i + 0.5f) - 0.5f * (float)A.H) / A.f;
+  const float dc2 = A.plane;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) d[r] = A.Rc[r] * dc0 + A.Rc[3 + r] * dc1 + A.Rc[6 + r] * dc2;
+}
+
+// Nearest box hit at t >= 1 along the ray of pixel (i, j) of instance `inst` (obj = -1: none);
+// box frames from shared memory (sf) when staged, else computed here.
+__device__ Hit trace(const CamArgs& A, const float* __restrict__ state, const BoxFrame* sf, bool staged, int inst, int i,
+                     int j) {
+  float d[3];
+  ray_dir(A, i, j, d);
+  Hit h;
+  h.obj = -1;
+  h.k = 0;
+  h.t = INFINITY;
+  for (int o = 0; o < A.n_obj; ++o) {
+    BoxFrame F;
+    if (staged)
+      F = sf[o];
+    else
+      box_frame(A, state, inst, o, F);
+    float dl[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) dl[k] = F.R[k] * d[0] + F.R[3 + k] * d[1] + F.R[6 + k] * d[2];
+    float tn = -INFINITY, tf = INFINITY;
+    int kn = 0;
+    bool miss = false;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float hk = A.half[o][k];
+      if (dl[k] == 0.f) {
+        if (fabsf(F.o[k]) > hk) miss = true;
+        continue;
+      }
+      const float inv = __frcp_rn(dl[k]);  // one correctly rounded reciprocal per slab
+      float t1 = (-hk - F.o[k]) * inv, t2 = (hk - F.o[k]) * inv;
+      if (t1 > t2) {
+        const float s = t1;
+        t1 = t2;
+        t2 = s;
+      }
+      if (t1 > tn) {
+        tn = t1;
+        kn = k;
+      }
+      tf = fminf(tf, t2);
+    }
+    if (miss || !(tn <= tf) || !(tn >= 1.f) || !(tn < h.t)) continue;
+    h.obj = o;
+    h.k = kn;
+    h.t = tn;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      h.ol[k] = F.o[k];
+      h.dl[k] = dl[k];
+    }
+  }
+  return h;
+}
+
+// Texture coordinates of a hit: the entry-plane parameter t, the hit point's two in-face
+// coordinates qa, qc, and the bilinear sample position.
+struct Sample {
+  int a, c;
+  float s, t, qa, qc, fx, fy;
+  int x0, x1, y0, y1;
+};
+
+__device__ __forceinline__ Sample sample_of(const CamArgs& A, const Hit& h) {
+  Sample S;
+  const int k = h.k;
+  S.a = (k + 1) % 3;
+  S.c = (k + 2) % 3;
+  const float hk = A.half[h.obj][k];
+  const float dk = pick3(h.dl, k), ok = pick3(h.ol, k);
+  S.s = dk > 0.f ? -1.f : 1.f;
+  S.t = (S.s * hk - ok) / dk;
+  S.qa = pick3(h.ol, S.a) + S.t * pick3(h.dl, S.a);
+  S.qc = pick3(h.ol, S.c) + S.t * pick3(h.dl, S.c);
+  const float u = (S.qa / A.half[h.obj][S.a] + 1.f) * 0.5f;
+  const float v = (S.qc / A.half[h.obj][S.c] + 1.f) * 0.5f;
+  const float xs = u * (float)A.tw - 0.5f, ys = v * (float)A.th - 0.5f;
+  const float x0f = floorf(xs), y0f = floorf(ys);
+  S.fx = xs - x0f;
+  S.fy = ys - y0f;
+  auto cl = [](int q, int n) { return q < 0 ? 0 : (q >= n ? n - 1 : q); };
+  S.x0 = cl((int)x0f, A.tw);
+  S.x1 = cl((int)x0f + 1, A.tw);
+  S.y0 = cl((int)y0f, A.th);
+  S.y1 = cl((int)y0f + 1, A.th);
+  return S;
+}
+
+__global__ void __launch_bounds__(256) k_render(const __grid_constant__ CamArgs A, const float* __restrict__ state,
+                                                const float* __restrict__ tex, float* __restrict__ image,
+                                                int* __restrict__ hit_out) {
+  __shared__ BoxFrame sf[kMaxObj];
+  int inst0;
+  const bool staged = stage_frames(A, state, sf, inst0);
+  const size_t npix = (size_t)A.W * A.H;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= npix * A.B) return;
+  const int inst = (int)(idx / npix);
+  const int pix = (int)(idx % npix), i = pix / A.W, j = pix % A.W;
+  const Hit h = trace(A, state, sf, staged, inst, i, j);
+  float col[3] = {0.f, 0.f, 0.f};
+  if (h.obj >= 0) {
+    const Sample S = sample_of(A, h);
+    const float* T = tex + (size_t)A.tex[h.obj] * A.th * A.tw * 3;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      const float t00 = __ldg(T + ((size_t)S.y0 * A.tw + S.x0) * 3 + ch), t01 = __ldg(T + ((size_t)S.y0 * A.tw + S.x1) * 3 + ch);
+      const float t10 = __ldg(T + ((size_t)S.y1 * A.tw + S.x0) * 3 + ch), t11 = __ldg(T + ((size_t)S.y1 * A.tw + S.x1) * 3 + ch);
+      col[ch] = (1.f - S.fy) * ((1.f - S.fx) * t00 + S.fx * t01) + S.fy * ((1.f - S.fx) * t10 + S.fx * t11);
+    }
+  }
+  float* o = image + idx * 3;
+  o[0] = col[0];
+  o[1] = col[1];
+  o[2] = col[2];
+  if (hit_out) hit_out[idx] = h.obj;
+}
+
+// Reverse mode: dstate[inst][body][0..11] (position, rotation entries) += the pixel's share of
+// d(sum dimage * image); dtex (optional) += the texel shares. A warp whose 32 pixels belong to one
+// instance sums its state shares per body with shuffles before one atomic per value.
+__global__ void __launch_bounds__(256) k_render_bwd(const __grid_constant__ CamArgs A, const float* __restrict__ state,
+                                                    const float* __restrict__ tex, const float* __restrict__ dimage,
+                                                    float* __restrict__ dstate, float* __restrict__ dtex) {
+  __shared__ BoxFrame sf[kMaxObj];
+  int inst0s;
+  const bool staged = stage_frames(A, state, sf, inst0s);
+  const size_t npix = (size_t)A.W * A.H;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = idx < npix * A.B;
+  const int inst = live ? (int)(idx / npix) : -1;
+  float g[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) g[k] = 0.f;
+  int gb = -1;  // body receiving g (-1: none)
+  if (live) {
+    const int pix = (int)(idx % npix), i = pix / A.W, j = pix % A.W;
+    const Hit h = trace(A, state, sf, staged, inst, i, j);
+    if (h.obj >= 0) {
+      const Sample S = sample_of(A, h);
+      const float* T = tex + (size_t)A.tex[h.obj] * A.th * A.tw * 3;
+      const float* dI = dimage + idx * 3;
+      float dfx = 0.f, dfy = 0.f;
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        const float gi = dI[ch];
+        const size_t i00 = ((size_t)S.y0 * A.tw + S.x0) * 3 + ch, i01 = ((size_t)S.y0 * A.tw + S.x1) * 3 + ch;
+        const size_t i10 = ((size_t)S.y1 * A.tw + S.x0) * 3 + ch, i11 = ((size_t)S.y1 * A.tw + S.x1) * 3 + ch;
+        const float t00 = __ldg(T + i00), t01 = __ldg(T + i01), t10 = __ldg(T + i10), t11 = __ldg(T + i11);
+        dfx += gi * ((1.f - S.fy) * (t01 - t00) + S.fy * (t11 - t10));
+        dfy += gi * (((1.f - S.fx) * t10 + S.fx * t11) - ((1.f - S.fx) * t00 + S.fx * t01));
+        if (dtex && gi != 0.f) {
+          float* D = dtex + (size_t)A.tex[h.obj] * A.th * A.tw * 3;
+          atomicAdd(D + i00, gi * (1.f - S.fx) * (1.f - S.fy));
+          atomicAdd(D + i01, gi * S.fx * (1.f - S.fy));
+          atomicAdd(D + i10, gi * (1.f - S.fx) * S.fy);
+          atomicAdd(D + i11, gi * S.fx * S.fy);
+        }
+      }
+      const int b = A.body[h.obj];
+      if (b >= 0) {
+        BoxFrame F;
+        if (staged)
+          F = sf[h.obj];
+        else
+          box_frame(A, state, inst, h.obj, F);
+        // fx = u tw - 1/2 - floor, u = (qa / h_a + 1)/2: dqa = dfx tw / (2 h_a); likewise qc
+        const float dqa = dfx * (float)A.tw * 0.5f / A.half[h.obj][S.a];
+        const float dqc = dfy * (float)A.th * 0.5f / A.half[h.obj][S.c];
+        const float dt = dqa * pick3(h.dl, S.a) + dqc * pick3(h.dl, S.c);
+        const float dk = pick3(h.dl, h.k);
+        float dol[3], ddl[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          // qa = ol_a + t dl_a, qc = ol_c + t dl_c, t = (s h_k - ol_k) / dl_k
+          dol[k] = (k == S.a ? dqa : 0.f) + (k == S.c ? dqc : 0.f) + (k == h.k ? -dt / dk : 0.f);
+          ddl[k] = (k == S.a ? dqa * S.t : 0.f) + (k == S.c ? dqc * S.t : 0.f) + (k == h.k ? -dt * S.t / dk : 0.f);
+        }
+        float d[3];
+        ray_dir(A, i, j, d);
+        // ol_k = sum_r R[r][k] (C_r - cw_r), dl_k = sum_r R[r][k] d_r, cw = p + R c
+        float dcw[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          dcw[r] = -(F.R[3 * r] * dol[0] + F.R[3 * r + 1] * dol[1] + F.R[3 * r + 2] * dol[2]);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) g[3 + 3 * r + k] += dol[k] * (A.C[r] - F.cw[r]) + ddl[k] * d[r];
+        }
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          g[r] += dcw[r];
+#pragma unroll
+          for (int m = 0; m < 3; ++m) g[3 + 3 * r + m] += dcw[r] * A.cen[h.obj][m];
+        }
+        gb = b;
+      }
+    }
+  }
+  const unsigned full = 0xffffffffu;
+  const int inst0 = __shfl_sync(full, inst, 0);
+  if (__all_sync(full, inst == inst0) && inst0 >= 0) {
+    for (int b = 0; b < A.nb; ++b) {
+      if (!__any_sync(full, gb == b)) continue;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        float v = gb == b ? g[k] : 0.f;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(full, v, off);
+        if ((threadIdx.x & 31) == 0) atomicAdd(dstate + ((size_t)inst0 * A.nb + b) * 18 + k, v);
+      }
+    }
+  } else if (gb >= 0) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) atomicAdd(dstate + ((size_t)inst * A.nb + gb) * 18 + k, g[k]);
+  }
+}
+
+thread_local std::string g_cam_err;
+
+dp_status cam_args(const dp_camera* cam, const dp_scene* sc, int32_t B, int32_t nb, CamArgs& A) {
+  if (!cam || !sc) { g_cam_err = "camera or scene is NULL"; return DP_EINVAL; }
+  if (cam->width < 1 || cam->height < 1 || !(cam->focal > 0.f) || !(cam->plane > 0.f)) {
+    g_cam_err = "camera: width, height, focal and plane must be positive";
+    return DP_EINVAL;
+  }
+  if (B < 0 || nb < 0 || sc->n_obj < 0 || sc->n_obj > kMaxObj) {
+    g_cam_err = "scene: n_obj out of range [0, DP_CAMERA_MAX_OBJECTS], or a negative size";
+    return DP_EINVAL;
+  }
+  if (sc->n_obj > 0 && (!sc->body || !sc->center || !sc->half || !sc->tex)) {
+    g_cam_err = "scene arrays are required when n_obj > 0";
+    return DP_EINVAL;
+  }
+  if (sc->tex_h < 1 || sc->tex_w < 1 || sc->n_tex < 1) { g_cam_err = "scene: texture sizes must be >= 1"; return DP_EINVAL; }
+  A.W = cam->width;
+  A.H = cam->height;
+  A.B = B;
+  A.nb = nb;
+  A.n_obj = sc->n_obj;
+  A.th = sc->tex_h;
+  A.tw = sc->tex_w;
+  A.f = cam->focal;
+  A.plane = cam->plane;
+  for (int k = 0; k < 3; ++k) A.C[k] = cam->position[k];
+  for (int k = 0; k < 9; ++k) A.Rc[k] = cam->rotation[k];
+  for (int o = 0; o < sc->n_obj; ++o) {
+    if (sc->body[o] < -1 || sc->body[o] >= nb) { g_cam_err = "scene: object body out of range"; return DP_EINVAL; }
+    if (sc->tex[o] < 0 || sc->tex[o] >= sc->n_tex) { g_cam_err = "scene: object texture out of range"; return DP_EINVAL; }
+    A.body[o] = sc->body[o];
+    A.tex[o] = sc->tex[o];
+    for (int k = 0; k < 3; ++k) {
+      A.cen[o][k] = sc->center[3 * o + k];
+      A.half[o][k] = sc->half[3 * o + k];
+      if (!(A.half[o][k] > 0.f)) { g_cam_err = "scene: half extents must be positive"; return DP_EINVAL; }
+    }
+  }
+  return DP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dp_status dp_render(const dp_camera* cam, const dp_scene* scene, int32_t n_instances, int32_t n_bodies,
+                    const float* state, const float* textures, float* image, int32_t* hit, void* stream) {
+  CamArgs A;
+  dp_status st = cam_args(cam, scene, n_instances, n_bodies, A);
+  if (st != DP_OK) return st;
+  if (!state || !textures || !image) { g_cam_err = "state, textures and image are required"; return DP_EINVAL; }
+  const size_t n = (size_t)A.W * A.H * A.B;
+  if (n == 0) return DP_OK;
+  k_render<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(A, state, textures, image, hit);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { g_cam_err = cudaGetErrorString(e); return DP_ECUDA; }
+  return DP_OK;
+}
+
+dp_status dp_render_backward(const dp_camera* cam, const dp_scene* scene, int32_t n_instances, int32_t n_bodies,
+                             const float* state, const float* textures, const float* dimage, float* dstate,
+                             float* dtextures, void* stream) {
+  CamArgs A;
+  dp_status st = cam_args(cam, scene, n_instances, n_bodies, A);
+  if (st != DP_OK) return st;
+  if (!state || !textures || !dimage || !dstate) { g_cam_err = "state, textures, dimage and dstate are required"; return DP_EINVAL; }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(dstate, 0, sizeof(float) * (size_t)A.B * A.nb * 18, s);
+  if (e == cudaSuccess && dtextures)
+    e = cudaMemsetAsync(dtextures, 0, sizeof(float) * (size_t)scene->n_tex * A.th * A.tw * 3, s);
+  const size_t n = (size_t)A.W * A.H * A.B;
+  if (e == cudaSuccess && n > 0) {
+    k_render_bwd<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(A, state, textures, dimage, dstate, dtextures);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) { g_cam_err = cudaGetErrorString(e); return DP_ECUDA; }
+  return DP_OK;
+}
+
+const char* dp_camera_last_error(void) { return g_cam_err.c_str(); }
+
+}  // extern "C"
