@@ -19,6 +19,7 @@
 namespace {
 
 constexpr int kMaxObj = DP_CAMERA_MAX_OBJECTS;
+constexpr int kThreads = 256, kPixPerThread = 4, kChunk = kThreads * kPixPerThread;
 
 struct CamArgs {
   int W, H, B, nb, n_obj, th, tw;
@@ -62,18 +63,35 @@ __device__ __forceinline__ void box_frame(const CamArgs& A, const float* __restr
   for (int k = 0; k < 3; ++k) F.o[k] = F.R[k] * (A.C[0] - F.cw[0]) + F.R[3 + k] * (A.C[1] - F.cw[1]) + F.R[6 + k] * (A.C[2] - F.cw[2]);
 }
 
-// The box frames of the block's instance, computed once per block into shared memory (every
-// block of 256 pixels lies in one instance when W * H is a multiple of 256; otherwise each
-// thread computes its own, see `trace`).
-__device__ __forceinline__ bool stage_frames(const CamArgs& A, const float* __restrict__ state, BoxFrame* sf, int& inst0) {
-  const size_t npix = (size_t)A.W * A.H;
-  const size_t first = (size_t)blockIdx.x * blockDim.x;
-  inst0 = (int)(first / npix);
-  const bool uniform = npix % blockDim.x == 0 && inst0 < A.B;
+// Work split: a block takes kChunk consecutive pixels of the batch, kPixPerThread per thread
+// (pixel first + threadIdx.x + r kThreads). When W * H is a multiple of kChunk every block lies in
+// one instance and its box frames are computed once into shared memory; otherwise each thread
+// computes its own (see `trace`).
+__device__ __forceinline__ bool stage_frames(const CamArgs& A, const float* __restrict__ state, BoxFrame* sf, int& inst0,
+                                             int& pix0) {
+  const int npix = A.W * A.H;
+  const int chunks = npix / kChunk;
+  const bool uniform = npix % kChunk == 0;
+  inst0 = uniform ? (int)(blockIdx.x / chunks) : 0;
+  pix0 = uniform ? (int)(blockIdx.x % chunks) * kChunk : 0;
   if (uniform)
     for (int o = threadIdx.x; o < A.n_obj; o += blockDim.x) box_frame(A, state, inst0, o, sf[o]);
   __syncthreads();
   return uniform;
+}
+// Instance and pixel of the r-th pixel of this thread.
+__device__ __forceinline__ bool pixel_of(const CamArgs& A, bool uniform, int inst0, int pix0, int r, int& inst, int& pix) {
+  const int npix = A.W * A.H;
+  if (uniform) {
+    inst = inst0;
+    pix = pix0 + (int)threadIdx.x + r * kThreads;
+    return true;
+  }
+  const long long idx = (long long)blockIdx.x * kChunk + threadIdx.x + (long long)r * kThreads;
+  if (idx >= (long long)npix * A.B) return false;
+  inst = (int)(idx / npix);
+  pix = (int)(idx - (long long)inst * npix);
+  return true;
 }
 
 __device__ __forceinline__ void ray_dir(const CamArgs& A, int i, int j, float d[3]) {
@@ -172,55 +190,61 @@ __device__ __forceinline__ Sample sample_of(const CamArgs& A, const Hit& h) {
   return S;
 }
 
-__global__ void __launch_bounds__(256) k_render(const __grid_constant__ CamArgs A, const float* __restrict__ state,
-                                                const float* __restrict__ tex, float* __restrict__ image,
-                                                int* __restrict__ hit_out) {
+__global__ void __launch_bounds__(kThreads) k_render(const __grid_constant__ CamArgs A, const float* __restrict__ state,
+                                                     const float* __restrict__ tex, float* __restrict__ image,
+                                                     int* __restrict__ hit_out) {
   __shared__ BoxFrame sf[kMaxObj];
-  int inst0;
-  const bool staged = stage_frames(A, state, sf, inst0);
-  const size_t npix = (size_t)A.W * A.H;
-  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= npix * A.B) return;
-  const int inst = (int)(idx / npix);
-  const int pix = (int)(idx % npix), i = pix / A.W, j = pix % A.W;
-  const Hit h = trace(A, state, sf, staged, inst, i, j);
-  float col[3] = {0.f, 0.f, 0.f};
-  if (h.obj >= 0) {
-    const Sample S = sample_of(A, h);
-    const float* T = tex + (size_t)A.tex[h.obj] * A.th * A.tw * 3;
+  int inst0, pix0;
+  const bool staged = stage_frames(A, state, sf, inst0, pix0);
+  const int npix = A.W * A.H;
+#pragma unroll 1
+  for (int r = 0; r < kPixPerThread; ++r) {
+    int inst, pix;
+    if (!pixel_of(A, staged, inst0, pix0, r, inst, pix)) break;
+    const int i = pix / A.W, j = pix - i * A.W;
+    const Hit h = trace(A, state, sf, staged, inst, i, j);
+    float col[3] = {0.f, 0.f, 0.f};
+    if (h.obj >= 0) {
+      const Sample S = sample_of(A, h);
+      const float* T = tex + (size_t)A.tex[h.obj] * A.th * A.tw * 3;
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-      const float t00 = __ldg(T + ((size_t)S.y0 * A.tw + S.x0) * 3 + ch), t01 = __ldg(T + ((size_t)S.y0 * A.tw + S.x1) * 3 + ch);
-      const float t10 = __ldg(T + ((size_t)S.y1 * A.tw + S.x0) * 3 + ch), t11 = __ldg(T + ((size_t)S.y1 * A.tw + S.x1) * 3 + ch);
-      col[ch] = (1.f - S.fy) * ((1.f - S.fx) * t00 + S.fx * t01) + S.fy * ((1.f - S.fx) * t10 + S.fx * t11);
+      for (int ch = 0; ch < 3; ++ch) {
+        const float t00 = __ldg(T + (S.y0 * A.tw + S.x0) * 3 + ch), t01 = __ldg(T + (S.y0 * A.tw + S.x1) * 3 + ch);
+        const float t10 = __ldg(T + (S.y1 * A.tw + S.x0) * 3 + ch), t11 = __ldg(T + (S.y1 * A.tw + S.x1) * 3 + ch);
+        col[ch] = (1.f - S.fy) * ((1.f - S.fx) * t00 + S.fx * t01) + S.fy * ((1.f - S.fx) * t10 + S.fx * t11);
+      }
     }
+    const size_t idx = (size_t)inst * npix + pix;
+    float* o = image + idx * 3;
+    o[0] = col[0];
+    o[1] = col[1];
+    o[2] = col[2];
+    if (hit_out) hit_out[idx] = h.obj;
   }
-  float* o = image + idx * 3;
-  o[0] = col[0];
-  o[1] = col[1];
-  o[2] = col[2];
-  if (hit_out) hit_out[idx] = h.obj;
 }
 
 // Reverse mode: dstate[inst][body][0..11] (position, rotation entries) += the pixel's share of
 // d(sum dimage * image); dtex (optional) += the texel shares. A warp whose 32 pixels belong to one
 // instance sums its state shares per body with shuffles before one atomic per value.
-__global__ void __launch_bounds__(256) k_render_bwd(const __grid_constant__ CamArgs A, const float* __restrict__ state,
-                                                    const float* __restrict__ tex, const float* __restrict__ dimage,
-                                                    float* __restrict__ dstate, float* __restrict__ dtex) {
+__global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__ CamArgs A, const float* __restrict__ state,
+                                                         const float* __restrict__ tex, const float* __restrict__ dimage,
+                                                         float* __restrict__ dstate, float* __restrict__ dtex) {
   __shared__ BoxFrame sf[kMaxObj];
-  int inst0s;
-  const bool staged = stage_frames(A, state, sf, inst0s);
-  const size_t npix = (size_t)A.W * A.H;
-  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool live = idx < npix * A.B;
-  const int inst = live ? (int)(idx / npix) : -1;
+  int inst0s, pix0;
+  const bool staged = stage_frames(A, state, sf, inst0s, pix0);
+  const int npixi = A.W * A.H;
+#pragma unroll 1
+  for (int rr = 0; rr < kPixPerThread; ++rr) {
+  int inst = -1, pixr = 0;
+  const bool live = pixel_of(A, staged, inst0s, pix0, rr, inst, pixr);
+  if (!live) inst = -1;
+  const size_t idx = (size_t)(live ? inst : 0) * npixi + pixr;
   float g[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) g[k] = 0.f;
   int gb = -1;  // body receiving g (-1: none)
   if (live) {
-    const int pix = (int)(idx % npix), i = pix / A.W, j = pix % A.W;
+    const int pix = pixr, i = pix / A.W, j = pix - (pix / A.W) * A.W;
     const Hit h = trace(A, state, sf, staged, inst, i, j);
     if (h.obj >= 0) {
       const Sample S = sample_of(A, h);
@@ -299,6 +323,7 @@ __global__ void __launch_bounds__(256) k_render_bwd(const __grid_constant__ CamA
 #pragma unroll
     for (int k = 0; k < 12; ++k) atomicAdd(dstate + ((size_t)inst * A.nb + gb) * 18 + k, g[k]);
   }
+  }
 }
 
 thread_local std::string g_cam_err;
@@ -355,7 +380,7 @@ dp_status dp_render(const dp_camera* cam, const dp_scene* scene, int32_t n_insta
   if (!state || !textures || !image) { g_cam_err = "state, textures and image are required"; return DP_EINVAL; }
   const size_t n = (size_t)A.W * A.H * A.B;
   if (n == 0) return DP_OK;
-  k_render<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(A, state, textures, image, hit);
+  k_render<<<(unsigned)((n + kChunk - 1) / kChunk), kThreads, 0, (cudaStream_t)stream>>>(A, state, textures, image, hit);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { g_cam_err = cudaGetErrorString(e); return DP_ECUDA; }
   return DP_OK;
@@ -374,7 +399,7 @@ dp_status dp_render_backward(const dp_camera* cam, const dp_scene* scene, int32_
     e = cudaMemsetAsync(dtextures, 0, sizeof(float) * (size_t)scene->n_tex * A.th * A.tw * 3, s);
   const size_t n = (size_t)A.W * A.H * A.B;
   if (e == cudaSuccess && n > 0) {
-    k_render_bwd<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(A, state, textures, dimage, dstate, dtextures);
+    k_render_bwd<<<(unsigned)((n + kChunk - 1) / kChunk), kThreads, 0, s>>>(A, state, textures, dimage, dstate, dtextures);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) { g_cam_err = cudaGetErrorString(e); return DP_ECUDA; }

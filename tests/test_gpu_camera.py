@@ -46,11 +46,13 @@ def test_frames_match_oracle():
     assert (hit >= 1).mean() > 0.005  # the pendulum is in view
 
 
-def test_gradients_match_oracle():
+@pytest.mark.parametrize("W,H,B", [(144, 48, 8), (288, 96, 4)])
+def test_gradients_match_oracle(W, H, B):
     """Reverse mode of a random weighting of the frames: gradients w.r.t. the three link bodies'
     positions and rotation entries, and w.r.t. every texel, within 1e-3 (relative) of the
-    oracle's, on instances whose hit sets agree everywhere."""
-    cs = WL.camera_scene(B=8, W=144, H=48)
+    oracle's, on instances whose hit sets agree everywhere; at 144 x 48 (the per-thread frame
+    path) and at the full 288 x 96 (box frames staged per block)."""
+    cs = WL.camera_scene(B=B, W=W, H=H)
     rig, st, tex, img, hit = gpu_frames(cs, cs.states)
     rng = np.random.default_rng(2)
     dimg = rng.normal(size=img.shape).astype(np.float32)
@@ -73,7 +75,7 @@ def test_gradients_match_oracle():
             assert e <= 1e-3, (i, b, e)
         assert np.all(ds[i, :, 12:] == 0.0)
         checked += 1
-    assert checked >= 4, checked
+    assert checked >= B // 2, checked
     # texel gradients summed over all instances (every instance's hits must agree for this sum)
     if all(np.array_equal(hit[i], O.render(cs, cs.states[i])[1]) for i in range(cs.states.shape[0])):
         for i in range(cs.states.shape[0]):
