@@ -524,6 +524,72 @@ def pendulum1(B=1, L=0.5, m=1.0, amp_deg=1.0, horizon=3000, dt=0.001, iters=20, 
 ARM_WIDTHS = [32, 256, 256, 7]
 
 
+ARM4_WIDTHS = [11, 64, 64, 4]
+
+
+def arm4dof(B=256, seed=1006, horizon=300, iters=20, dt=0.005, widths=None, grad_decay=0.9, w_seed=None):
+    """The paper's 4-degree-of-freedom arm (section 3.2): 1 m long, 32 kg, a 2-DoF actuated
+    universal joint at the base and another at the elbow, servos of gain 30 1/s, 30 N m and
+    45 deg/s. A universal (Cardan) joint is two revolute joints whose perpendicular axes meet in
+    one point; here each is a hinge pair with a cross body (2 kg, moments of inertia 0.1 kg m^2,
+    a motor housing; lighter crosses let the 20 sweeps leave the hinges drifting by centiradians)
+    between them: the base cross yaws about the world z axis and the upper arm pitches about the
+    cross's y axis; at the elbow the cross pitches about the upper arm's y axis and the forearm
+    rolls about the cross's x axis. Upper arm and forearm: 0.5 m, 14 kg each (uniform rods, radius
+    0.04 m); steps of 5 ms. The arm starts
+    upright at rest with its base at the origin. No gravity (with 30 N m the servos cannot hold
+    32 kg of arm off the vertical). Per instance a seeded target at 0.3-0.9 m from the base in the
+    upper half-space. Controller 11 -> 64 -> 64 -> 4 fed by the 4 joint angles and rates and the
+    tip-to-target vector, its output layer zero (the paper starts from the zero policy). Loss: the
+    tip's distance to the target averaged over the steps (the paper's per-step averaged
+    objective), reverse mode with the gradient decay ``grad_decay`` (section 3.2)."""
+    rng = np.random.default_rng(seed)
+    widths = list(widths or ARM4_WIDTHS)
+    nb = nj = 4
+    d = _empty(B, nb, nj, 0)
+    Lk, mk, rk = 0.5, 14.0, 0.04
+    It = mk * (3 * rk ** 2 + Lk ** 2) / 12.0
+    mc, Ic = 2.0, 0.1
+    for i in range(B):
+        # bodies: 0 base cross at the origin, 1 upper arm (centre z = 0.25), 2 elbow cross (z = 0.5),
+        # 3 forearm (centre z = 0.75)
+        for k, z in enumerate((0.0, 0.25, 0.5, 0.75)):
+            d["state0"][i, k] = _state(np.array([0.0, 0.0, z]), np.eye(3), np.zeros(3), np.zeros(3))
+        d["mass"][i] = [mc, mk, mc, mk]
+        d["inertia"][i] = [[Ic, Ic, Ic], [It, It, 0.5 * mk * rk ** 2], [Ic, Ic, Ic], [It, It, 0.5 * mk * rk ** 2]]
+        d["anchor"][i, 0] = [[0.0, 0.0, 0.0], [0.0, 0.0, 0.0]]
+        d["anchor"][i, 1] = [[0.0, 0.0, 0.0], [0.0, 0.0, -0.25]]
+        d["anchor"][i, 2] = [[0.0, 0.0, 0.25], [0.0, 0.0, 0.0]]
+        d["anchor"][i, 3] = [[0.0, 0.0, 0.0], [0.0, 0.0, -0.25]]
+        d["axis"][i, 0] = [[0.0, 0.0, 1.0], [0.0, 0.0, 1.0]]
+        d["ref"][i, 0] = [[1.0, 0.0, 0.0], [1.0, 0.0, 0.0]]
+        d["axis"][i, 1] = [[0.0, 1.0, 0.0], [0.0, 1.0, 0.0]]
+        d["ref"][i, 1] = [[1.0, 0.0, 0.0], [1.0, 0.0, 0.0]]
+        d["axis"][i, 2] = [[0.0, 1.0, 0.0], [0.0, 1.0, 0.0]]
+        d["ref"][i, 2] = [[1.0, 0.0, 0.0], [1.0, 0.0, 0.0]]
+        d["axis"][i, 3] = [[1.0, 0.0, 0.0], [1.0, 0.0, 0.0]]
+        d["ref"][i, 3] = [[0.0, 1.0, 0.0], [0.0, 1.0, 0.0]]
+        d["motor"][i, :] = [30.0, 30.0, math.pi / 4]
+        d["limit"][i, :] = [-math.pi, math.pi]
+        rr = rng.uniform(0.3, 0.9)
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        u[2] = abs(u[2])
+        d["loss_point"][i] = [0.0, 0.0, 0.25]
+        d["loss_target"][i] = rr * u
+    _finish(d)
+    wr = np.random.default_rng(seed + 7 if w_seed is None else w_seed)
+    W = xavier_weights(widths, 0, wr, zero_output=True)
+    mdl = Model(name="arm4dof", B=B, joint_type=np.full(nj, HINGE, np.int32),
+                joint_body=np.array([[-1, 0], [0, 1], [1, 2], [2, 3]], np.int32),
+                joint_flags=np.full(nj, FLAG_MOTOR, np.int32), sphere_body=np.zeros(0, np.int32),
+                pair_sphere=np.zeros((0, 2), np.int32), nb=nb, widths=widths, features=F_ANGLES | F_RATES | F_TARGET,
+                W=W, dt=dt, iters=iters, horizon=horizon, loss_kind=L_DIST, loss_mode=M_MEAN, loss_body=3,
+                gravity=(0.0, 0.0, 0.0), **d)
+    mdl.grad_decay = grad_decay
+    return mdl
+
+
 def arms(B=8192, seed=1003, iters=10, dt=0.005, hmin=200, hmax=2000, links=(3, 7), widths=None, out_scale=0.1,
          w_seed=None, tau_max=60.0, grad_decay=0.9):
     """Uneven batch of robot arms on a table, returned as one Model per link count (a bin of one
