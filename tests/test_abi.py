@@ -111,3 +111,60 @@ def test_null_world_calls_fail_cleanly():
 
 def test_build_flags_target_sm103a():
     assert "arch=compute_103a,code=sm_103a" in build.FLAGS
+
+
+def test_recurrent_descriptor_validation():
+    """n_recurrent out of range, or a network too narrow for the sensors plus the recurrent state,
+    is rejected at world creation."""
+    lib = binding.load()
+    d, keep = _desc(workloads.quadruped(B=2, horizon=5))
+    d.n_recurrent = -1
+    h = C.c_void_p()
+    assert lib.dp_create_world(C.byref(d), None, C.byref(h)) == binding.DP_EINVAL
+    assert b"n_recurrent" in lib.dp_last_error()
+    d.n_recurrent = 4  # 24 sensor inputs + 4 recurrent > widths[0] = 24
+    st = lib.dp_create_world(C.byref(d), None, C.byref(h))
+    assert st == binding.DP_EINVAL and not h.value
+    assert b"recurrent" in lib.dp_last_error()
+
+
+def test_new_world_calls_reject_null():
+    lib = binding.load()
+    assert lib.dp_set_params(None, None) == binding.DP_EINVAL
+    assert lib.dp_set_recurrent(None, None) == binding.DP_EINVAL
+    assert lib.dp_get_recurrent(None, None) == binding.DP_EINVAL
+
+
+def _camera(n_obj=2, half=0.5):
+    cam = binding.Camera()
+    cam.width, cam.height, cam.focal, cam.plane = 8, 4, 4.0, 0.05
+    for k, v in enumerate((1.0, 0.0, 0.0, 0.0, 0.0, -1.0, 0.0, 1.0, 0.0)):
+        cam.rotation[k] = v
+    keep = [np.full(n_obj, -1, np.int32), np.zeros((n_obj, 3), np.float32), np.full((n_obj, 3), half, np.float32),
+            np.zeros(n_obj, np.int32)]
+    sc = binding.Scene()
+    sc.n_obj = n_obj
+    sc.body = keep[0].ctypes.data_as(binding.PI)
+    sc.center = keep[1].ctypes.data_as(binding.PF)
+    sc.half = keep[2].ctypes.data_as(binding.PF)
+    sc.tex = keep[3].ctypes.data_as(binding.PI)
+    sc.n_tex, sc.tex_h, sc.tex_w = 1, 2, 2
+    return cam, sc, keep
+
+
+@pytest.mark.parametrize("case,needle", [
+    ("too_many", b"n_obj"), ("flat_box", b"half extents"), ("bad_texture", b"texture"), ("bad_camera", b"positive"),
+])
+def test_camera_validation_rejects_bad_scene(case, needle):
+    """Malformed cameras and scenes are rejected on the host with a message, before any launch."""
+    lib = binding.load()
+    cam, sc, keep = _camera(n_obj=17 if case == "too_many" else 2, half=0.0 if case == "flat_box" else 0.5)
+    if case == "bad_texture":
+        keep[3][1] = 5
+    if case == "bad_camera":
+        cam.focal = 0.0
+    st = lib.dp_render(C.byref(cam), C.byref(sc), 1, 1, None, None, None, None, None)
+    assert st == binding.DP_EINVAL
+    assert needle in lib.dp_camera_last_error()
+    st = lib.dp_render_backward(C.byref(cam), C.byref(sc), 1, 1, None, None, None, None, None, None)
+    assert st == binding.DP_EINVAL
