@@ -517,7 +517,7 @@ def main():
     loss = torch.empty(B, device="cuda")
     dloss = torch.ones(B, device="cuda")
 
-    # plain cold-start solver at full sweeps (the fallback and judge)
+    # plain cold-start solver at full sweeps (the fallback, and the reference for equal residual)
     world = World(m, stream=stream, iters=args.iters)
     dW = torch.empty(world.n_params, device="cuda")
     p_ms, p_fwd, p_bwd, p_ck = time_arm(world, W, loss, dloss, dW, args, stream, dist)

@@ -195,8 +195,8 @@ def _controller_gradient(model, iters, net, alpha, W, horizon):
 def accept(model, candidates, plain_iters=20, sweep_grid=(5, 7, 10, 14), horizon=200, ref_iters=80, state_tol=1e-3,
            grad_tol=2e-2):
     """Acceptance gate of warm starts against the plain cold-start solver at ``plain_iters``
-    sweeps on held-out robots (``model``; its controller weights drive them). The judge of
-    state and gradient errors is the plain solver at ``ref_iters`` sweeps.
+    sweeps on held-out robots (``model``; its controller weights drive them). State and gradient
+    errors are measured against the plain solver at ``ref_iters`` sweeps.
 
     For each candidate (name, network parameters, alpha), at the smallest sweep count N of the
     grid where it gets there, the warm-started solver must (1) stay finite over a
