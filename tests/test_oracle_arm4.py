@@ -49,3 +49,31 @@ def test_composed_universal_joints_follow_forward_kinematics():
             assert np.abs(tip - tip_fk).max() <= 5e-3, (i, t, tip, tip_fk)
             moved = max(moved, abs(th0), abs(th1), abs(th2), abs(th3))
     assert moved > 0.2
+
+
+def test_reach_gradient_matches_central_differences():
+    """The reaching objective (distance to the target averaged over the steps) of the arm under a
+    non-zero controller: its reverse-mode gradient w.r.t. controller weights equals central
+    differences of the oracle's forward pass (no decay, controller unrounded)."""
+    from test_oracle_pins import _same_activity
+
+    m = WL.arm4dof(B=2, horizon=40, grad_decay=1.0)
+    m.exact_mlp = 1
+    rng = np.random.default_rng(8)
+    W = np.asarray(m.W, np.float64).copy()
+    n3 = m.widths[2] * m.widths[3] + m.widths[3]
+    W[-n3:] = rng.uniform(-0.2, 0.2, size=n3)
+    L, g = O.rollout_grad(m, 0, W=W)
+    n1 = m.widths[0] * m.widths[1]
+    checked = 0
+    for k in [3, 40, n1 - 5, n1 + 64 + 100, len(W) - n3 + 5, len(W) - 3, len(W) - 1]:
+        eps = 1e-6
+        Wp, Wm = W.copy(), W.copy()
+        Wp[k] += eps
+        Wm[k] -= eps
+        if not _same_activity(m, 0, m.horizon, None, None, Wp, Wm):
+            continue
+        fd = (O.rollout(m, 0, W=Wp)[1] - O.rollout(m, 0, W=Wm)[1]) / (2 * eps)
+        assert abs(fd - g["W"][k]) <= 1e-4 * (abs(fd) + 1e-4), (k, fd, g["W"][k])
+        checked += 1
+    assert checked >= 5
