@@ -28,6 +28,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_1611_01652_gb300.replicas import max_over_ranks, replica_seed, whole_job_rate  # noqa: E402
+
 METRIC = "inst-steps/s fwd+adjoint, quadruped B=4096; warm-start vs plain @equal resid"
 FLOPS = os.path.join(ROOT, "tests", "golden", "flops_per_instance_step.json")
 SM_COUNT, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
@@ -244,10 +246,7 @@ def time_arm(world, W, loss, dloss, dW, args, stream, dist):
     total_ms = t0.elapsed_time(t1)
     fwd_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
     bwd_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
-    if dist:
-        tt = torch.tensor([total_ms, fwd_ms, bwd_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms, fwd_ms, bwd_ms = tt.tolist()
+    total_ms, fwd_ms, bwd_ms = max_over_ranks([total_ms, fwd_ms, bwd_ms], dist, "cuda")
     return total_ms, fwd_ms, bwd_ms, ck
 
 
@@ -511,7 +510,7 @@ def main():
         nets = {"damped": torch.zeros(WS_PARAMS, device="cuda")}
     else:
         rep, nets = prepare_warmstart(args)
-    m = WL.quadruped(B=B, horizon=T, seed=1002 + 17 * rank)
+    m = WL.quadruped(B=B, horizon=T, seed=replica_seed(1002, rank))
     stream = torch.cuda.current_stream()
     W = torch.tensor(m.W, device="cuda")
     loss = torch.empty(B, device="cuda")
@@ -521,7 +520,7 @@ def main():
     world = World(m, stream=stream, iters=args.iters)
     dW = torch.empty(world.n_params, device="cuda")
     p_ms, p_fwd, p_bwd, p_ck = time_arm(world, W, loss, dloss, dW, args, stream, dist)
-    plain = {"iters": args.iters, "value": B * T * world_size / (p_ms / args.steps / 1e3),
+    plain = {"iters": args.iters, "value": whole_job_rate(B * T, world_size, p_ms / args.steps),
              "ms_per_step": p_ms / args.steps, "fwd_ms": p_fwd, "bwd_ms": p_bwd,
              "resid": mean_residual(world, W, B), "ckpt_every": world.ckpt_every}
     head = dict(plain, name="plain", clocks=p_ck, world=world)
@@ -534,7 +533,7 @@ def main():
         world = World(m, stream=stream, iters=n_ws, warmstart=True)
         world.set_warmstart(nets[name], alpha)
         w_ms, w_fwd, w_bwd, w_ck = time_arm(world, W, loss, dloss, dW, args, stream, dist)
-        ws = {"accepted": name, "iters": n_ws, "alpha": alpha, "value": B * T * world_size / (w_ms / args.steps / 1e3),
+        ws = {"accepted": name, "iters": n_ws, "alpha": alpha, "value": whole_job_rate(B * T, world_size, w_ms / args.steps),
               "ms_per_step": w_ms / args.steps, "fwd_ms": w_fwd, "bwd_ms": w_bwd, "resid": mean_residual(world, W, B),
               "ckpt_every": world.ckpt_every}
         head = dict(ws, name="warm start (%s, %d sweeps)" % (name, n_ws), clocks=w_ck, world=world)
@@ -561,11 +560,8 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         ems = e0.elapsed_time(e1) / args.steps
-        if dist:
-            tt = torch.tensor([ems], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ems = tt.item()
-        e2e = {"value": B * T * world_size / (ems / 1e3), "unit": "inst-steps/s",
+        ems = max_over_ranks([ems], dist, "cuda")[0]
+        e2e = {"value": whole_job_rate(B * T, world_size, ems), "unit": "inst-steps/s",
                "h2d_bytes_per_step": 4 * (world.n_params + B), "d2h_bytes_per_step": 4 * (B + world.n_params)}
 
     del world, head
