@@ -371,7 +371,7 @@ class Camera(C.Structure):
 
 class Scene(C.Structure):
     _fields_ = [("n_obj", C.c_int32), ("body", PI), ("center", PD), ("half", PD), ("tex", PI), ("n_tex", C.c_int32),
-                ("tex_h", C.c_int32), ("tex_w", C.c_int32), ("tex_data", PD)]
+                ("tex_h", C.c_int32), ("tex_w", C.c_int32), ("tex_data", PD), ("kind", PI)]
 
 
 def _camera_scene(cs, keep, tex=None):
@@ -387,6 +387,8 @@ def _camera_scene(cs, keep, tex=None):
     t = np.asarray(cs.textures if tex is None else tex, np.float64)
     sc.n_tex, sc.tex_h, sc.tex_w = t.shape[0], t.shape[1], t.shape[2]
     sc.tex_data = keep.f64(t)
+    kind = getattr(cs, "obj_kind", None)
+    sc.kind = keep.i32(kind) if kind is not None else None
     return cam, sc
 
 

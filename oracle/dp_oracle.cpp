@@ -1300,7 +1300,10 @@ int orc_flops(const orc_topo* T, const orc_inst* I, const double* W, int32_t hor
 // and the colour is the bilinear interpolation of the box's texture (texel centres at
 // ((c + 1/2) / Wt, (r + 1/2) / Ht), clamped at the edges), which gives the frame non-zero
 // derivatives with respect to the state and the texture. Rays that hit nothing are black.
-// Reverse mode keeps the discrete choices (which box, which face, which texels) of the forward
+// Spheres (kind 1, radius = half[0]) are intersected as |C + t d - c_w| = r; their texture
+// coordinates come from the hit point's direction in the sphere's body frame,
+// u = atan2(y, x) / (2 pi) + 1/2, v = acos(z / r) / pi.
+// Reverse mode keeps the discrete choices (which object, which face, which texels) of the forward
 // pass and differentiates the rest (the oracle's tape).
 extern "C" {
 typedef struct {
@@ -1318,6 +1321,7 @@ typedef struct {
   const int32_t* tex;     // [n_obj] texture index
   int32_t n_tex, tex_h, tex_w;
   const double* tex_data; // [n_tex][tex_h][tex_w][3]
+  const int32_t* kind;    // [n_obj] 0 = box, 1 = sphere of radius half[0] (NULL: all boxes)
 } orc_scene;
 }  // extern "C"
 
@@ -1349,6 +1353,19 @@ static void render_impl(const orc_camera& cam, const orc_scene& sc, const std::v
           ol[k] = R[k] * (S(cam.pos[0]) - cw[0]) + R[3 + k] * (S(cam.pos[1]) - cw[1]) + R[6 + k] * (S(cam.pos[2]) - cw[2]);
           dlo[k] = R[k] * d[0] + R[3 + k] * d[1] + R[6 + k] * d[2];
         }
+        if (sc.kind && sc.kind[o] == 1) {  // sphere: a t^2 + 2 b t + c = 0 in the body frame
+          const double r = sc.half[3 * o];
+          const double a = val(dlo[0]) * val(dlo[0]) + val(dlo[1]) * val(dlo[1]) + val(dlo[2]) * val(dlo[2]);
+          const double b = val(dlo[0]) * val(ol[0]) + val(dlo[1]) * val(ol[1]) + val(dlo[2]) * val(ol[2]);
+          const double c = val(ol[0]) * val(ol[0]) + val(ol[1]) * val(ol[1]) + val(ol[2]) * val(ol[2]) - r * r;
+          const double disc = b * b - a * c;
+          if (!(disc >= 0.0)) continue;
+          const double tn = (-b - std::sqrt(disc)) / a;
+          if (!(tn >= 1.0) || !(tn < bt)) continue;
+          best = o; bk = -1; bt = tn;
+          for (int k = 0; k < 3; ++k) { bl[k] = ol[k]; dl[k] = dlo[k]; }
+          continue;
+        }
         double tn = -INFINITY, tf = INFINITY;
         int kn = 0;
         bool miss = false;
@@ -1369,13 +1386,30 @@ static void render_impl(const orc_camera& cam, const orc_scene& sc, const std::v
       }
       if (hit_obj) hit_obj[(size_t)i * W + j] = best;
       if (best < 0) continue;
-      // the entry plane: x_k = s h_k with s = -sign(d_k)
-      const double hk = sc.half[3 * best + bk];
-      const double s = val(dl[bk]) > 0.0 ? -1.0 : 1.0;
-      S t = (S(s * hk) - bl[bk]) / dl[bk];
-      const int a = (bk + 1) % 3, c = (bk + 2) % 3;
-      S u = ((bl[a] + t * dl[a]) / S(sc.half[3 * best + a]) + S(1.0)) * S(0.5);
-      S v = ((bl[c] + t * dl[c]) / S(sc.half[3 * best + c]) + S(1.0)) * S(0.5);
+      S u, v;
+      if (bk < 0) {  // sphere: the near root, then the hit direction's spherical angles
+        const double r = sc.half[3 * best];
+        S a = dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2];
+        S b = dl[0] * bl[0] + dl[1] * bl[1] + dl[2] * bl[2];
+        S c = bl[0] * bl[0] + bl[1] * bl[1] + bl[2] * bl[2] - S(r * r);
+        S t = (-b - sqrt(b * b - a * c)) / a;
+        S px = bl[0] + t * dl[0], py = bl[1] + t * dl[1], pz = bl[2] + t * dl[2];
+        u = atan2(py, px) / S(2.0 * M_PI) + S(0.5);
+        double zr = val(pz) / r;
+        zr = zr > 1.0 ? 1.0 : (zr < -1.0 ? -1.0 : zr);
+        // v = acos(pz / r) / pi, d v / d pz = -1 / (pi r sqrt(1 - (pz/r)^2))
+        const double vv = std::acos(zr) / M_PI;
+        const double dv = -1.0 / (M_PI * r * std::sqrt(std::max(1e-300, 1.0 - zr * zr)));
+        v = S(vv) + (pz - S(val(pz))) * S(dv);
+      } else {
+        // the entry plane: x_k = s h_k with s = -sign(d_k)
+        const double hk = sc.half[3 * best + bk];
+        const double s = val(dl[bk]) > 0.0 ? -1.0 : 1.0;
+        S t = (S(s * hk) - bl[bk]) / dl[bk];
+        const int a = (bk + 1) % 3, c = (bk + 2) % 3;
+        u = ((bl[a] + t * dl[a]) / S(sc.half[3 * best + a]) + S(1.0)) * S(0.5);
+        v = ((bl[c] + t * dl[c]) / S(sc.half[3 * best + c]) + S(1.0)) * S(0.5);
+      }
       // bilinear texture sample, texel centres at (c + 1/2) / tw, clamped at the edges
       S xs = u * S((double)tw) - S(0.5), ys = v * S((double)th) - S(0.5);
       const double x0f = std::floor(val(xs)), y0f = std::floor(val(ys));

@@ -11,8 +11,9 @@ from paper_1611_01652_gb300.workloads import CameraScene
 ROT_Y = np.array([[1.0, 0.0, 0.0], [0.0, 0.0, -1.0], [0.0, 1.0, 0.0]])  # look along +y, image down = -z
 
 
-def scene(boxes, W=40, H=16, f=20.0, plane=0.05, tex=None, th=8, tw=8):
-    """boxes: list of (body, centre, half, tex index); camera at the origin looking along +y."""
+def scene(boxes, W=40, H=16, f=20.0, plane=0.05, tex=None, th=8, tw=8, kinds=None):
+    """boxes: list of (body, centre, half, tex index); camera at the origin looking along +y;
+    kinds: per object 0 (box) or 1 (sphere of radius half[0])."""
     cs = CameraScene()
     cs.W, cs.H, cs.f, cs.plane = W, H, f, plane
     cs.cam_pos = np.zeros(3)
@@ -24,6 +25,8 @@ def scene(boxes, W=40, H=16, f=20.0, plane=0.05, tex=None, th=8, tw=8):
     if tex is None:
         tex = np.random.default_rng(0).uniform(0, 1, size=(max(b[3] for b in boxes) + 1, th, tw, 3))
     cs.textures = tex
+    if kinds is not None:
+        cs.obj_kind = np.array(kinds, np.int32)
     return cs
 
 
@@ -111,6 +114,80 @@ def test_gradients_match_central_differences():
         assert abs(fd - ds[0, k]) <= 1e-6 * max(1.0, abs(fd)), (k, fd, ds[0, k])
     assert np.all(ds[0, 12:] == 0.0)
     for idx in [(0, 2, 3, 0), (0, 0, 0, 1), (0, 5, 1, 2), (0, 3, 3, 1)]:
+        eps = 1e-6
+        tp, tm = cs.textures.copy(), cs.textures.copy()
+        tp[idx] += eps
+        tm[idx] -= eps
+        fd = (f(tt=tp) - f(tt=tm)) / (2 * eps)
+        assert abs(fd - dt[idx]) <= 1e-7 * max(1.0, abs(fd)), (idx, fd, dt[idx])
+
+
+def test_sphere_with_linear_texture():
+    """A world sphere of radius r centred at (0, D, 0): the pixel (i, j) ray meets it where
+    |t d - c| = r (near root), seen from outside; the hit direction p (from the centre) gives
+    u = atan2(p_y, p_x) / (2 pi) + 1/2, v = acos(p_z / r) / pi, and a texture linear in (u, v)
+    comes back exactly inside the texel-centre grid; rays that miss are black."""
+    W, H, f, D, r = 40, 16, 20.0, 3.0, 1.0
+    th, tw = 8, 8
+    coef = [(0.3, 0.5, 0.1), (-0.2, 0.4, 0.5), (0.7, -0.1, 0.2)]
+    cs = scene([(-1, [0.0, D, 0.0], [r, r, r], 0)], W, H, f, tex=linear_texture(th, tw, coef), th=th, tw=tw, kinds=[1])
+    img, hit = O.render(cs, np.zeros((0, 18)))
+    checked = 0
+    for i in range(H):
+        for j in range(W):
+            d = np.array([((j + 0.5) - W / 2) / f, 1.0, -((i + 0.5) - H / 2) / f]) * cs.plane
+            c = np.array([0.0, D, 0.0])
+            a, b, cc = d @ d, d @ (-c), c @ c - r * r
+            disc = b * b - a * cc
+            if disc < 0:
+                assert hit[i, j] == -1 and np.all(img[i, j] == 0.0), (i, j)
+                continue
+            assert hit[i, j] == 0, (i, j)
+            p = ((-b - np.sqrt(disc)) / a) * d - c
+            u = np.arctan2(p[1], p[0]) / (2 * np.pi) + 0.5
+            v = np.arccos(np.clip(p[2] / r, -1, 1)) / np.pi
+            if not (0.5 / tw <= u <= 1 - 0.5 / tw and 0.5 / th <= v <= 1 - 0.5 / th):
+                continue
+            for ch, (ca, cb, c0) in enumerate(coef):
+                assert abs(img[i, j, ch] - (ca * u + cb * v + c0)) <= 1e-12, (i, j, ch)
+            checked += 1
+    assert checked >= 50
+
+
+def test_sphere_occludes_box_and_gradients_match_central_differences():
+    """A body-carried sphere in front of a backdrop box is seen where it covers the backdrop; a
+    large sphere filling the frame (no silhouette) has the gradients of a random frame weighting
+    w.r.t. its body's position and rotation entries and its texels equal central differences."""
+    back = (-1, [0.0, 6.0, 0.0], [20.0, 0.1, 20.0], 0)
+    ball = (0, [0.0, 0.0, 0.0], [0.5, 0.5, 0.5], 1)
+    cs = scene([back, ball], kinds=[0, 1])
+    x = np.zeros((1, 18))
+    x[0, 0:3] = [0.0, 3.0, 0.0]
+    x[0, 3:12] = np.eye(3).reshape(-1)
+    _, hit = O.render(cs, x)
+    assert hit[8, 20] == 1 and hit[0, 0] == 0
+    rng = np.random.default_rng(3)
+    cs = scene([(0, [0.0, 0.0, 0.0], [2.5, 2.5, 2.5], 0)], W=24, H=10, f=10.0, th=6, tw=6, kinds=[1])
+    ang = 0.3
+    R = np.array([[np.cos(ang), -np.sin(ang), 0.0], [np.sin(ang), np.cos(ang), 0.0], [0.0, 0.0, 1.0]])
+    x[0, 0:3] = [0.05, 3.0, -0.1]
+    x[0, 3:12] = R.reshape(-1)
+    img, hit = O.render(cs, x)
+    assert np.all(hit == 0)
+    wgt = rng.normal(size=img.shape)
+    ds, dt = O.render_grad(cs, x, wgt)
+
+    def f(xx=None, tt=None):
+        return float(np.sum(wgt * O.render(cs, x if xx is None else xx, tex=tt)[0]))
+
+    for k in range(12):
+        eps = 1e-6
+        xp, xm = x.copy(), x.copy()
+        xp[0, k] += eps
+        xm[0, k] -= eps
+        fd = (f(xp) - f(xm)) / (2 * eps)
+        assert abs(fd - ds[0, k]) <= 1e-5 * max(1.0, abs(fd)), (k, fd, ds[0, k])
+    for idx in [(0, 2, 3, 0), (0, 4, 1, 2)]:
         eps = 1e-6
         tp, tm = cs.textures.copy(), cs.textures.copy()
         tp[idx] += eps
