@@ -267,16 +267,19 @@ int32_t dp_ckpt_every(const dp_world* w);
    otherwise). Takes effect from the next dp_step / dp_rollout; a recorded rollout is dropped. */
 dp_status dp_set_warmstart(dp_world* w, const float* W, float alpha);
 
-/* Replace per-instance parameters in place (system identification, hardware-parameter search):
-   each non-NULL pointer of p (host or device, shapes of the matching dp_batch_desc arrays,
-   [B][n]) overwrites that group for every instance; NULL groups are kept. The values are not
-   validated (a non-positive mass or inertia gives non-finite states, reported by dp_sync). A
-   recorded rollout is dropped: dp_backward needs a new dp_rollout. Stream-ordered. */
+/* Replace per-instance parameters in place, for system identification and hardware-parameter
+   search by gradient descent through the engine (section 5's outlook; the gradients are
+   dp_backward's dp_param_grads): each non-NULL pointer of p (host or device, caller-owned,
+   shapes of the matching dp_batch_desc arrays, [B][n], float) overwrites that group for every
+   instance; NULL groups are kept. The values are not validated (a non-positive mass or inertia
+   gives non-finite states, reported by dp_sync). A recorded rollout is dropped: dp_backward needs
+   a new dp_rollout. DP_EINVAL for a NULL world or p. Stream-ordered. */
 dp_status dp_set_params(dp_world* w, const dp_param_grads* p);
 
-/* The controller's recurrent state h (n_recurrent > 0): set h [B][n_recurrent] (host or device)
-   as the state the next dp_step starts from, or read the current one into h. dp_set_state and
-   every dp_rollout start from h = 0. DP_EINVAL if the world has no recurrent state. */
+/* The controller's recurrent state h^t of Eq. g (section 2.2; n_recurrent > 0): set h
+   [B][n_recurrent] (float, host or device, caller-owned, copied) as the state the next dp_step
+   starts from, or read the current one into h. dp_set_state and every dp_rollout start from
+   h = 0. Stream-ordered. DP_EINVAL for a NULL world or h, or a world without recurrent state. */
 dp_status dp_set_recurrent(dp_world* w, const float* h);
 dp_status dp_get_recurrent(dp_world* w, float* h);
 
