@@ -499,6 +499,9 @@ def main():
     if world_size > 1:
         import torch.distributed as dist
 
+        # the secondary workloads are reported at N = 1; a scaling run times the headline only
+        args.no_arms = args.no_wide = args.no_recurrent = args.no_sysid = args.no_camera = True
+
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     B, T = args.batch, args.horizon
     if args.no_warmstart:
