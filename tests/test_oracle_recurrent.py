@@ -112,3 +112,39 @@ def test_recurrent_gradient_matches_central_differences():
     assert checked >= 10
     # the recurrent weights do carry gradient
     assert np.abs(g["W"][[w1 + o * ni1 + 24 for o in range(no1)]]).max() > 0.0
+
+
+def test_gradient_decay_also_cuts_the_recurrent_adjoint():
+    """With the decay alpha -> 0 nothing reaches step T-1 from later steps, through the state or
+    through h: with the final-state loss, dL/dW is then the derivative of the last step alone,
+    taken from the stored x_{T-1} and h_{T-1} (central differences of one oracle step); an
+    undecayed recurrent adjoint would add the earlier steps' share through h."""
+    m = WL.quadruped(B=1, horizon=6, n_recurrent=2)
+    m.exact_mlp = 1
+    rng = np.random.default_rng(11)
+    W = m.W.astype(np.float64).copy()
+    (w1, b1, ni1, no1), _, (w3, b3, ni3, no3) = _layers(m.widths)
+    for o in range(no1):
+        W[w1 + o * ni1 + 24:w1 + o * ni1 + 26] = rng.uniform(-0.4, 0.4, size=2)
+    W[w3 + 8 * ni3:w3 + 10 * ni3] = rng.uniform(-0.3, 0.3, size=2 * ni3)
+    st, _, hs = O.rollout_rec(m, 0, W=W)
+    m.grad_decay = 1e-12
+    _, g = O.rollout_grad(m, 0, W=W)
+    T = m.horizon
+    a = np.asarray(m.loss_target[0], np.float64)
+    c = np.asarray(m.loss_point[0], np.float64)
+
+    def last_step_loss(Wv):
+        xn = O.step_log(m, 0, st[T - 1], t=T - 1, W=Wv, h_prev=hs[T - 1])["xn"]
+        return a @ (xn[0, 0:3] + xn[0, 3:12].reshape(3, 3) @ c)  # x_T's term a.q of the displacement loss
+
+    idx = [w1 + 7 * ni1 + 24, w1 + 90 * ni1 + 25, w1 + 3 * ni1 + 5, w3 + 2 * ni3 + 9]
+    for k in idx:
+        eps = 1e-6
+        Wp, Wm = W.copy(), W.copy()
+        Wp[k] += eps
+        Wm[k] -= eps
+        fd = (last_step_loss(Wp) - last_step_loss(Wm)) / (2 * eps)
+        assert abs(fd - g["W"][k]) <= 1e-5 * (abs(fd) + 1e-5), (k, fd, g["W"][k])
+    # the recurrent-input columns still get the last step's share (h_{T-1} != 0)
+    assert any(abs(g["W"][k]) > 0 for k in idx[:2])
