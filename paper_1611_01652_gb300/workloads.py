@@ -527,7 +527,8 @@ ARM_WIDTHS = [32, 256, 256, 7]
 ARM4_WIDTHS = [11, 64, 64, 4]
 
 
-def arm4dof(B=256, seed=1006, horizon=300, iters=20, dt=0.005, widths=None, grad_decay=0.5, w_seed=None):
+def arm4dof(B=256, seed=1006, horizon=300, iters=20, dt=0.005, widths=None, grad_decay=0.5, w_seed=None,
+            bend=(0.5, 1.0)):
     """The paper's 4-degree-of-freedom arm (section 3.2): 1 m long, 32 kg, a 2-DoF actuated
     universal joint at the base and another at the elbow, servos of gain 30 1/s, 30 N m and
     45 deg/s. A universal (Cardan) joint is two revolute joints whose perpendicular axes meet in
@@ -536,8 +537,10 @@ def arm4dof(B=256, seed=1006, horizon=300, iters=20, dt=0.005, widths=None, grad
     between them: the base cross yaws about the world z axis and the upper arm pitches about the
     cross's y axis; at the elbow the cross pitches about the upper arm's y axis and the forearm
     rolls about the cross's x axis. Upper arm and forearm: 0.5 m, 14 kg each (uniform rods, radius
-    0.04 m); steps of 5 ms. The arm starts
-    upright at rest with its base at the origin. No gravity (with 30 N m the servos cannot hold
+    0.04 m); steps of 5 ms. The arm starts at rest with its base at the origin, the upper arm
+    pitched by ``bend[0]`` and the elbow by ``bend[1]`` rad (upright, (0, 0), is a kinematic
+    singularity: the tip lies on the base yaw axis); the hinges' reference vectors make that
+    pose the zero of every joint angle, so the zero policy holds it. No gravity (with 30 N m the servos cannot hold
     32 kg of arm off the vertical). Per instance a seeded target at 0.3-0.9 m from the base in the
     upper half-space. Controller 11 -> 64 -> 64 -> 4 fed by the 4 joint angles and rates and the
     tip-to-target vector, its output layer zero (the paper starts from the zero policy). Loss: the
@@ -552,11 +555,17 @@ def arm4dof(B=256, seed=1006, horizon=300, iters=20, dt=0.005, widths=None, grad
     Lk, mk, rk = 0.5, 14.0, 0.04
     It = mk * (3 * rk ** 2 + Lk ** 2) / 12.0
     mc, Ic = 2.0, 0.1
+    R1 = _rot_y(bend[0])
+    R2 = R1 @ _rot_y(bend[1])
+    elbow = R1 @ np.array([0.0, 0.0, 0.5])
+    poses = [(np.zeros(3), np.eye(3)), (R1 @ np.array([0.0, 0.0, 0.25]), R1), (elbow, R2),
+             (elbow + R2 @ np.array([0.0, 0.0, 0.25]), R2)]
+    ref_up = _rot_y(-bend[0]) @ np.array([1.0, 0.0, 0.0])  # x of the cross, seen from the upper arm
+    ref_el = _rot_y(-bend[1]) @ np.array([1.0, 0.0, 0.0])  # x of the upper arm, seen from the elbow cross
     for i in range(B):
-        # bodies: 0 base cross at the origin, 1 upper arm (centre z = 0.25), 2 elbow cross (z = 0.5),
-        # 3 forearm (centre z = 0.75)
-        for k, z in enumerate((0.0, 0.25, 0.5, 0.75)):
-            d["state0"][i, k] = _state(np.array([0.0, 0.0, z]), np.eye(3), np.zeros(3), np.zeros(3))
+        # bodies: 0 base cross at the origin, 1 upper arm, 2 elbow cross, 3 forearm
+        for k, (c, R) in enumerate(poses):
+            d["state0"][i, k] = _state(c, R, np.zeros(3), np.zeros(3))
         d["mass"][i] = [mc, mk, mc, mk]
         d["inertia"][i] = [[Ic, Ic, Ic], [It, It, 0.5 * mk * rk ** 2], [Ic, Ic, Ic], [It, It, 0.5 * mk * rk ** 2]]
         d["anchor"][i, 0] = [[0.0, 0.0, 0.0], [0.0, 0.0, 0.0]]
@@ -566,9 +575,9 @@ def arm4dof(B=256, seed=1006, horizon=300, iters=20, dt=0.005, widths=None, grad
         d["axis"][i, 0] = [[0.0, 0.0, 1.0], [0.0, 0.0, 1.0]]
         d["ref"][i, 0] = [[1.0, 0.0, 0.0], [1.0, 0.0, 0.0]]
         d["axis"][i, 1] = [[0.0, 1.0, 0.0], [0.0, 1.0, 0.0]]
-        d["ref"][i, 1] = [[1.0, 0.0, 0.0], [1.0, 0.0, 0.0]]
+        d["ref"][i, 1] = [[1.0, 0.0, 0.0], ref_up]
         d["axis"][i, 2] = [[0.0, 1.0, 0.0], [0.0, 1.0, 0.0]]
-        d["ref"][i, 2] = [[1.0, 0.0, 0.0], [1.0, 0.0, 0.0]]
+        d["ref"][i, 2] = [[1.0, 0.0, 0.0], ref_el]
         d["axis"][i, 3] = [[1.0, 0.0, 0.0], [1.0, 0.0, 0.0]]
         d["ref"][i, 3] = [[0.0, 1.0, 0.0], [0.0, 1.0, 0.0]]
         d["motor"][i, :] = [30.0, 30.0, math.pi / 4]
