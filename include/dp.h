@@ -268,7 +268,7 @@ int32_t dp_ckpt_every(const dp_world* w);
 dp_status dp_set_warmstart(dp_world* w, const float* W, float alpha);
 
 /* Replace per-instance parameters in place, for system identification and hardware-parameter
-   search by gradient descent through the engine (section 5's outlook; the gradients are
+   search by gradient descent through the engine (the section 4 Discussion's outlook; the gradients are
    dp_backward's dp_param_grads): each non-NULL pointer of p (host or device, caller-owned,
    shapes of the matching dp_batch_desc arrays, [B][n], float) overwrites that group for every
    instance; NULL groups are kept. The values are not validated (a non-positive mass or inertia
@@ -319,7 +319,7 @@ dp_status dp_ws_adam(float* W, const float* dW, float* m, float* v, int64_t coun
                      float beta2, float eps, void* stream);
 
 /* ------------------------------------------------------------------------------------------
-   Differentiable camera (section 4: the inverted pendulum observed by a camera). A pinhole ray
+   Differentiable camera (section 3.4: the inverted pendulum observed by a camera). A pinhole ray
    tracer over textured oriented boxes carried by the bodies, batched over instances. The pixel
    (row i, column j) ray leaves the camera centre C along
        d = R_c^T (P ((j + 1/2) - W/2) / f, P ((i + 1/2) - H/2) / f, P),

@@ -1289,7 +1289,7 @@ int orc_flops(const orc_topo* T, const orc_inst* I, const double* W, int32_t hor
 }  // extern "C"
 
 // ========================================================================================
-// Differentiable camera (section 4, the inverted pendulum seen by a camera): a pinhole ray
+// Differentiable camera (section 3.4, the inverted pendulum seen by a camera): a pinhole ray
 // tracer over textured oriented boxes carried by the bodies. Per pixel (row i, column j) the ray
 // from the camera centre C runs along d = R_c^T (P ((j + 1/2) - W/2) / f, P ((i + 1/2) - H/2) / f, P)
 // (f: focal length in pixels, P: distance of the projection plane), so that t = 1 is the

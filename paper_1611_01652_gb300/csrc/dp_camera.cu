@@ -1,4 +1,4 @@
-// Differentiable camera (arXiv 1611.01652, section 4: the inverted pendulum observed by a camera).
+// Differentiable camera (arXiv 1611.01652, section 3.4: the inverted pendulum observed by a camera).
 // A pinhole ray tracer over textured oriented boxes carried by the bodies, batched over
 // instances: one thread per pixel. The pixel (i, j) ray leaves the camera centre C along
 // d = R_c^T (P ((j + 1/2) - W/2) / f, P ((i + 1/2) - H/2) / f, P), so t = 1 is the projection plane

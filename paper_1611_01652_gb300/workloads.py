@@ -279,7 +279,7 @@ def procedural_textures(n, th=64, tw=64, seed=7):
 
 
 def camera_scene(B=4096, W=288, H=96, seed=1005, tex_size=64):
-    """The 3-link pendulum seen by a camera (the paper's camera sensor, section 4, at its 288 x 96
+    """The 3-link pendulum seen by a camera (the paper's camera sensor, section 3.4, at its 288 x 96
     resolution): the three links as textured boxes (0.12 x 0.12 x L m) on bodies 0-2, a textured
     backdrop box 1 m behind the hinge plane, and a camera 3 m in front of it looking along +y
     (image right = +x, image down = -z), focal length W / 2 pixels, projection plane 0.05 m in

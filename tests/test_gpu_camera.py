@@ -1,4 +1,4 @@
-"""Differentiable camera (section 4) through the C ABI against the FP64 oracle: frames of the
+"""Differentiable camera (section 3.4) through the C ABI against the FP64 oracle: frames of the
 camera scene (the 3-link pendulum in front of a textured backdrop), the box each pixel sees, and
 the reverse mode to the body poses and the texels; also at the full 288 x 96 size in the
 4096-frame launch configuration the bench times, on sampled instances."""

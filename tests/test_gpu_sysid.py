@@ -1,5 +1,5 @@
 """System identification (model parameters fitted by gradient descent through the engine,
-paper section 5) through the C ABI: in-place parameter replacement (dp_set_params) against a
+paper section 4, Discussion) through the C ABI: in-place parameter replacement (dp_set_params) against a
 world created with the same parameters, and a batched fit of 3-link pendulums' link masses to
 observations computed by the FP64 oracle, confirmed by the oracle at the fitted masses."""
 import numpy as np

@@ -1,4 +1,4 @@
-"""Pins of the oracle's differentiable camera (section 4: pinhole rays through the pixel centres,
+"""Pins of the oracle's differentiable camera (section 3.4: pinhole rays through the pixel centres,
 nearest hit in front of the projection plane, bilinear texture interpolation) against facts that
 do not come from its own formulas: the pinhole geometry of a fronto-parallel face worked out
 here, a linear texture (which bilinear interpolation reproduces exactly), the visibility rules,
