@@ -55,9 +55,12 @@ __device__ void loss_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& X,
 // ---------------------------------------------------------------- integrate + Eq. 1 reverse
 // XB holds the adjoint of x_{t+1}; on return its p/R fields hold the adjoint of x_t's p/R,
 // its v/w fields are zero, and VB holds the adjoint of the solver's output velocities.
-__device__ void integrate_reverse(const DevTopo& T, const GC& Xt, const SL& X, const SL& XB, const SL& VB) {
+// (bmask: the bodies to process, bit b)
+__device__ void integrate_reverse(const DevTopo& T, const GC& Xt, const SL& X, const SL& XB, const SL& VB,
+                                  uint32_t bmask = 0xffffffffu) {
   const float h = T.dt;
   for (int b = 0; b < T.nb; ++b) {
+    if (!((bmask >> b) & 1u)) continue;
     M3 R = loadRg(Xt, 18 * b);
     float3 w = X.v3(18 * b + 15);  // solver output angular velocity
     M3 A;
@@ -493,10 +496,12 @@ __device__ void rows_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& XB
 // (x_t's v, w, R) and the mass/inertia gradients. IINVB/INVMB hold the world inverse-inertia
 // and inverse-mass adjoints gathered from the solver and the rows.
 template <class RV>
-__device__ void external_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& XB, const SL& VB) {
+__device__ void external_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& XB, const SL& VB,
+                                 uint32_t bmask = 0xffffffffu) {
   const SL& S = B.L.S;
   const float h = T.dt;
   for (int b = 0; b < T.nb; ++b) {
+    if (!((bmask >> b) & 1u)) continue;
     M3 R = loadRg(B.X0, 18 * b);
     float3 I = B.L.P.v3(T.o_inertia + 3 * b);
     float3 Ii = f3(1.f / I.x, 1.f / I.y, 1.f / I.z);

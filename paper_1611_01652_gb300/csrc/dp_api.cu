@@ -220,7 +220,8 @@ void plan_smem(DevTopo& T, bool backward, int smem_floats_max, bool rows_on_chip
     T.sm_invmb = take(T.nb);
     T.sm_rc = take(12 * T.nslots);
     T.sm_sbar = take(T.n_layers > 0 ? T.widths[0] : 1);
-    T.sm_vw = take(6 * T.nb);
+    // the run-time reverse sweep's working velocities, or the multi-warp sweep's hand-off ring
+    T.sm_vw = T.sm_ring = take(std::max(6 * T.nb, 4 * DPK_MW_CH));
     T.sm_hb = take(T.n_rec);
     // controller-reverse ping-pong buffers: the row-adjoint region is free by then
     int maxw = 1;
@@ -331,6 +332,30 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
     T.order[s] = (int16_t)ord[s];
     w->kind[s] = slots[s].kind;
     w->colour[s] = col[s];
+  }
+  // body ownership of the multi-warp reverse pass (stages outside the sweeps): longest processing
+  // time over four warps by the number of row sides touching each body (ties: lower index)
+  {
+    int cnt[DPK_MAXB] = {0}, load[4] = {0};
+    bool done[DPK_MAXB] = {false};
+    for (const Slot& q : slots) {
+      if (q.a >= 0) ++cnt[q.a];
+      if (q.b >= 0) ++cnt[q.b];
+    }
+    for (int k = 0; k < T.nb; ++k) {
+      int best = -1;
+      for (int b = 0; b < T.nb; ++b)
+        if (!done[b] && (best < 0 || cnt[b] > cnt[best])) best = b;
+      done[best] = true;
+      int h = 0;
+      for (int g = 1; g < 4; ++g)
+        if (load[g] < load[h]) h = g;
+      T.mw_own[best] = (int8_t)h;
+      load[h] += cnt[best];
+    }
+    for (int g = 0; g < 4; ++g) T.mw_bmask[g] = T.mw_jmask[g] = 0u;
+    for (int b = 0; b < T.nb; ++b) T.mw_bmask[T.mw_own[b]] |= 1u << b;
+    for (int j = 0; j < T.nj; ++j) T.mw_jmask[T.mw_own[T.jb[j]]] |= 1u << j;
   }
   // warm-start groups, in slot order of their first row
   T.n_wsg = 0;

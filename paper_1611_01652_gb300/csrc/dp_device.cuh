@@ -17,6 +17,8 @@
 #define DPK_MAXSLOT (5 * DPK_MAXJ + 2 * DPK_MAXJ + 3 * DPK_MAXS + 3 * DPK_MAXP)
 #define DPK_MAXL 6
 #define DPK_MAXWSG (2 * DPK_MAXJ + DPK_MAXS + DPK_MAXP)
+// rows per chunk of the multi-warp reverse sweep's hand-off ring (dp_mw.cuh)
+#define DPK_MW_CH 20
 
 // Warm-start group types (feature 15 of a group).
 enum { WSG_GROUND = 0, WSG_PAIR = 1, WSG_JOINT = 2, WSG_HINGE = 3 };
@@ -80,6 +82,11 @@ struct DevTopo {
   int sm_x0, sm_x, sm_xb, sm_vb, sm_iinv, sm_invm, sm_th, sm_thd, sm_ua, sm_wst, sm_wbr, sm_lam, sm_u;
   int sm_thb, sm_thdb, sm_uab, sm_wstb, sm_iinvb, sm_invmb, sm_rc, sm_sbar, sm_vw, sm_zb, sm_act[DPK_MAXL + 1], sm_rows,
       sm_total;
+  int sm_ring;  // multi-warp reverse sweep: two buffers of DPK_MW_CH (j, p_bar) pairs (shares sm_vw's region)
+  // multi-warp reverse pass: the warp (0..3) that owns each body's adjoint accumulators in the
+  // stages outside the sweeps, and the matching body / joint (by child body) masks per warp
+  int8_t mw_own[DPK_MAXB];
+  uint32_t mw_bmask[4], mw_jmask[4];
   // activation/delta dump offsets (rows of [feature][T*Bp]); act l = input of layer l
   int dump_act[DPK_MAXL + 1], dump_del[DPK_MAXL + 1], dump_rows;
   // tape record of one (step, warp), lanes interleaved ([field][32]): byte offsets
@@ -150,7 +157,8 @@ struct TapeStep {
   const uint8_t* rec;
 };
 __device__ __forceinline__ TapeStep tape_step(const DevTopo& T, const DevPtrs& D, int ts) {
-  const int lane = threadIdx.x & 31, warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  // one CTA per group of 32 instances (its warps share the group's lanes)
+  const int lane = threadIdx.x & 31, warp = blockIdx.x;
   const uint8_t* rec = D.tape + ((size_t)ts * (T.Bp / 32) + warp) * (size_t)T.rec_bytes;
   TapeStep p;
   p.rec = rec;

@@ -37,10 +37,12 @@ template <class XV>
 __device__ __forceinline__ M3 body_R(const XV& X, int b) { return b >= 0 ? loadRv(X, 18 * b) : eye3(); }
 
 // Hinge axis (world), angle about it between the two reference vectors, and its rate.
+// (jmask: the joints to process, bit j; the multi-warp kernels split them between warps)
 template <class RV, class XV>
-__device__ void hinge_kinematics(const DevTopo& T, const LaneT<RV>& L, const XV& X) {
+__device__ void hinge_kinematics(const DevTopo& T, const LaneT<RV>& L, const XV& X, uint32_t jmask = 0xffffffffu) {
   const SL& S = L.S;
   for (int j = 0; j < T.nj; ++j) {
+    if (!((jmask >> j) & 1u)) continue;
     int a = T.ja[j], b = T.jb[j];
     M3 Ra = body_R(X, a);
     float3 ua = mv(Ra, L.P.v3(T.o_axis + 6 * j));
@@ -194,10 +196,11 @@ __device__ void controller_forward_tc(const DevTopo& T, const DevPtrs& D, const 
 
 // Servo targets w* = clamp(k (u - theta), -vmax, vmax).
 template <class RV, class AV>
-__device__ void servo_targets(const DevTopo& T, const LaneT<RV>& L, const AV& u) {
+__device__ void servo_targets(const DevTopo& T, const LaneT<RV>& L, const AV& u, uint32_t jmask = 0xffffffffu) {
   const SL& S = L.S;
   for (int m = 0; m < T.n_motors; ++m) {
     int j = T.motor_joint[m];
+    if (!((jmask >> j) & 1u)) continue;
     float k = L.P[T.o_motor + 3 * j], vmax = L.P[T.o_motor + 3 * j + 2];
     float um = (T.n_layers > 0 && m < T.widths[T.n_layers]) ? u[m] : 0.f;
     float x = k * (um - S[T.sm_th + j]);
@@ -232,11 +235,13 @@ __device__ void external_impulses(const DevTopo& T, const LaneT<RV>& L, const SL
   }
 }
 
-// World inverse inertia and inverse mass of every body at state X (no state change).
+// World inverse inertia and inverse mass of every body at state X (no state change; bmask:
+// the bodies to process, bit b).
 template <class RV, class XV>
-__device__ void inverse_inertia(const DevTopo& T, const LaneT<RV>& L, const XV& X) {
+__device__ void inverse_inertia(const DevTopo& T, const LaneT<RV>& L, const XV& X, uint32_t bmask = 0xffffffffu) {
   const SL& S = L.S;
   for (int b = 0; b < T.nb; ++b) {
+    if (!((bmask >> b) & 1u)) continue;
     M3 R = loadRv(X, 18 * b);
     float3 I = L.P.v3(T.o_inertia + 3 * b);
     float ii[6];

@@ -3,9 +3,10 @@
 // and layout transposes.
 #include <cuda_runtime.h>
 
+#include <cstdlib>
 #include <type_traits>
 
-#include "dp_static.cuh"
+#include "dp_mw.cuh"
 #include "dp_kernels.h"
 
 extern __shared__ float g_smem[];
@@ -211,42 +212,55 @@ struct BwdCtx {
   float dl;
 };
 
-// Reverse of step t from its tape slot ts, with x_t and x_{t+1} in global memory. RV is the
-// tape-row view: read-only (GSR) when the rollout recorded the whole tape, else GS.
-template <class Q, class RV>
-__device__ void reverse_step(const DevTopo& T, const DevPtrs& D, const BwdCtx& C, int t, int ts, const float* x_t,
-                             const float* x_t1) {
+// Per-step views of the reverse pass: the step's tape record, its controller dump columns and the
+// lane views built on them.
+template <class RV>
+struct RevStep {
+  TapeStep tp;
+  LaneT<RV> L;
+  BLaneT<RV> Bl;
+  GW act[DPK_MAXL + 1], del[DPK_MAXL + 1];
+  SL zb0, zb1;
+};
+template <class RV>
+__device__ __forceinline__ RevStep<RV> rev_views(const DevTopo& T, const DevPtrs& D, const BwdCtx& C, int t, int ts) {
   const int Bp = T.Bp, i = C.i;
   const size_t N = (size_t)T.horizon * Bp;
   const size_t n = (size_t)t * Bp + i;
   const TapeStep tp = tape_step(T, D, ts);
-  if (ts > 0) prefetch_record_l2(T, tape_step(T, D, ts - 1).rec);  // the next step to reverse
   LaneT<RV> L{C.S, C.P, RV{tp.rows}, i};
-  BLaneT<RV> Bl{L, C.X, C.G, GC{tp.vminus, 32}};
-  GW act[DPK_MAXL + 1], del[DPK_MAXL + 1];
+  RevStep<RV> V{tp, L, BLaneT<RV>{L, C.X, C.G, GC{tp.vminus, 32}}, {}, {}, SL{C.S.p + T.sm_zb * 32}, SL{nullptr}};
   for (int l = 0; l <= DPK_MAXL; ++l) {
-    act[l] = GW{D.dump + (size_t)T.dump_act[l] * N + n, N};
-    del[l] = GW{D.dump + (size_t)T.dump_del[l] * N + n, N};
+    V.act[l] = GW{D.dump + (size_t)T.dump_act[l] * N + n, N};
+    V.del[l] = GW{D.dump + (size_t)T.dump_del[l] * N + n, N};
   }
-  if (T.ext_ctrl) act[T.n_layers] = GW{D.u_ext + n * T.ext_nop, 1};  // wide controller's output u_t
-  const SL VW{C.S.p + T.sm_vw * 32}, zb0{C.S.p + T.sm_zb * 32};
+  if (T.ext_ctrl) V.act[T.n_layers] = GW{D.u_ext + n * T.ext_nop, 1};  // wide controller's output u_t
   int maxw = 1;
   for (int l = 0; l <= T.n_layers && T.n_layers > 0; ++l) maxw = max(maxw, T.widths[l]);
-  const SL zb1{C.S.p + (T.sm_zb + maxw) * 32};
-  // loss term and integrator with x_{t+1} on chip
+  V.zb1 = SL{C.S.p + (T.sm_zb + maxw) * 32};
+  return V;
+}
+
+// First part of the reverse of step t (through the zeroing of the solver's adjoint
+// accumulators): loss term and integrator with x_{t+1} on chip, then x_t and its per-step
+// forward quantities recomputed bit-identically (hinge kinematics, servo targets, inverse
+// inertias).
+template <class Q, class RV>
+__device__ void reverse_step_head(const DevTopo& T, const DevPtrs& D, const BwdCtx& C, const RevStep<RV>& V, int t,
+                                  int ts, const float* x_t, const float* x_t1) {
+  const int Bp = T.Bp, i = C.i;
+  if (ts > 0) prefetch_record_l2(T, tape_step(T, D, ts - 1).rec);  // the next step to reverse
   copy_state_to_smem(T, x_t1, i, C.X);
   if (T.grad_decay != 1.f) {  // section 3.2: the adjoint from later steps shrinks by alpha per step
     for (int f = 0; f < 18 * T.nb; ++f) C.XB[f] *= T.grad_decay;
     for (int k = 0; k < T.n_rec; ++k) C.S[T.sm_hb + k] *= T.grad_decay;  // and so does h's
   }
-  loss_reverse(T, Bl, C.X, C.XB, loss_weight(T, t + 1, D.hz[i]) * C.dl);
+  loss_reverse(T, V.Bl, C.X, C.XB, loss_weight(T, t + 1, D.hz[i]) * C.dl);
   integrate_reverse(T, GC{x_t + i, Bp}, C.X, C.XB, C.VB);
-  // x_t on chip for every later stage; its per-step forward quantities are recomputed
-  // bit-identically (hinge kinematics, servo targets, inverse inertias)
   copy_state_to_smem(T, x_t, i, C.X);
-  hinge_kinematics(T, L, C.X);
-  servo_targets(T, L, act[T.n_layers > 0 ? T.n_layers : 0]);
-  inverse_inertia(T, L, C.X);
+  hinge_kinematics(T, V.L, C.X);
+  servo_targets(T, V.L, V.act[T.n_layers > 0 ? T.n_layers : 0]);
+  inverse_inertia(T, V.L, C.X);
   for (int j = 0; j < T.nj; ++j) {
     C.S[T.sm_thb + j] = 0.f; C.S[T.sm_thdb + j] = 0.f; C.S[T.sm_wstb + j] = 0.f;
     C.S.s3(T.sm_uab + 3 * j, f3(0.f, 0.f, 0.f));
@@ -256,43 +270,71 @@ __device__ void reverse_step(const DevTopo& T, const DevPtrs& D, const BwdCtx& C
     for (int q = 0; q < 9; ++q) C.S[T.sm_iinvb + 9 * b + q] = 0.f;
   }
   for (int q = 0; q < T.nslots * RC_N; ++q) C.RC[q] = 0.f;
-  if constexpr (Q::id != 0 && std::is_same<RV, GSR>::value)
-    pgs_reverse_static<Q>(T, L, tp);
-  else
-    pgs_reverse(T, Bl, VW, C.VB, C.RC, tp);
-  if (T.ws) ws_apply_reverse(T, L, C.VB, C.RC, tp);
-  rows_reverse(T, Bl, C.XB, C.VB, C.RC);
-  external_reverse(T, Bl, C.XB, C.VB);
+}
+
+// Servo-target, controller, feature and hinge-kinematics reverse of step t (after the
+// external impulses' reverse), down to the adjoint of x_t.
+template <class RV>
+__device__ void reverse_step_ctrl(const DevTopo& T, const DevPtrs& D, const BwdCtx& C, const RevStep<RV>& V) {
+  const int i = C.i;
+  const GW* act = V.act;
+  const GW* del = V.del;
   if (T.ext_ctrl) {
     // wide controller: the output adjoint goes to the batched products; the features' adjoint
     // comes back into the next launch
-    servo_reverse(T, Bl, act[T.n_layers], del[T.n_layers - 1], zb0);
+    servo_reverse(T, V.Bl, act[T.n_layers], del[T.n_layers - 1], V.zb0);
     float* ub = D.ub_ext + (size_t)i * 16;
-    for (int o = 0; o < 16; ++o) ub[o] = o < T.widths[T.n_layers] ? zb0[o] : 0.f;
+    for (int o = 0; o < 16; ++o) ub[o] = o < T.widths[T.n_layers] ? V.zb0[o] : 0.f;
   } else if (T.n_layers > 0) {
-    servo_reverse(T, Bl, act[T.n_layers], del[T.n_layers - 1], zb0);
+    servo_reverse(T, V.Bl, act[T.n_layers], del[T.n_layers - 1], V.zb0);
     if (T.n_rec) {  // adjoint of the recurrent outputs: h^{t+1} = tanh(z)
       const int base = T.widths[T.n_layers] - T.n_rec;
       for (int k = 0; k < T.n_rec; ++k) {
         const float th = tanhf(act[T.n_layers][base + k]);
         const float zb = C.S[T.sm_hb + k] * (1.f - th * th);
-        zb0[base + k] = zb;
+        V.zb0[base + k] = zb;
         del[T.n_layers - 1][base + k] = zb;
       }
     }
     if (T.mlp_tc)
-      controller_reverse_tc(T, D, act, del, zb0, C.sbar);
+      controller_reverse_tc(T, D, act, del, V.zb0, C.sbar);
     else
-      controller_reverse(T, D, act, del, zb0, zb1, C.sbar);
-    features_reverse(T, Bl, C.XB, C.sbar);
+      controller_reverse(T, D, act, del, V.zb0, V.zb1, C.sbar);
+    features_reverse(T, V.Bl, C.XB, C.sbar);
     if (T.n_rec) {  // adjoint of h^t (straight through its bfloat16 rounding), carried to step t - 1
       const int base = T.widths[0] - T.n_rec;
       for (int k = 0; k < T.n_rec; ++k) C.S[T.sm_hb + k] = C.sbar[base + k];
     }
   } else {
-    servo_reverse(T, Bl, act[0], act[0], zb0);
+    servo_reverse(T, V.Bl, act[0], act[0], V.zb0);
   }
-  hinge_reverse(T, Bl, C.XB);
+  hinge_reverse(T, V.Bl, C.XB);
+}
+
+// Last part of the reverse of step t (after the solver's reverse sweeps): warm-start
+// application, row assembly, external impulses, then the stages above, down to the adjoint of x_t.
+template <class Q, class RV>
+__device__ void reverse_step_tail(const DevTopo& T, const DevPtrs& D, const BwdCtx& C, const RevStep<RV>& V) {
+  if (T.ws) ws_apply_reverse(T, V.L, C.VB, C.RC, V.tp);
+  rows_reverse(T, V.Bl, C.XB, C.VB, C.RC);
+  external_reverse(T, V.Bl, C.XB, C.VB);
+  reverse_step_ctrl(T, D, C, V);
+}
+
+// Reverse of step t from its tape slot ts, with x_t and x_{t+1} in global memory. RV is the
+// tape-row view: read-only (GSR) when the rollout recorded the whole tape, else GS.
+template <class Q, class RV>
+__device__ void reverse_step(const DevTopo& T, const DevPtrs& D, const BwdCtx& C, int t, int ts, const float* x_t,
+                             const float* x_t1) {
+  const RevStep<RV> V = rev_views<RV>(T, D, C, t, ts);
+  reverse_step_head<Q, RV>(T, D, C, V, t, ts, x_t, x_t1);
+  if constexpr (Q::id != 0 && std::is_same<RV, GSR>::value) {
+    pgs_reverse_static<Q>(T, V.L, V.tp);
+  } else {
+    const SL VW{C.S.p + T.sm_vw * 32};
+    pgs_reverse(T, V.Bl, VW, C.VB, C.RC, V.tp);
+  }
+  reverse_step_tail<Q, RV>(T, D, C, V);
 }
 
 // Reverse mode through the last rollout, last step first. With a full tape every step is read
@@ -338,6 +380,94 @@ __global__ void __launch_bounds__(32, 1) k_backward(const __grid_constant__ DevT
         reverse_step<Q, GS>(T, D, C, t, t - ta, D.seg + (size_t)(t - ta) * sbytes, D.seg + (size_t)(t - ta + 1) * sbytes);
     }
   }
+  if (T.loss_kind == 3) {  // initial term -a.q(x_0) of the displacement loss
+    copy_state_to_smem(T, D.ckpt, i, C.X);
+    const int b = T.loss_body;
+    M3 R = loadR(C.X, 18 * b);
+    float3 c = C.P.v3(T.o_loss_point), a = C.P.v3(T.o_loss_target);
+    float3 gq = -C.dl * a;
+    C.XB.a3(18 * b, gq);
+    add_outer(C.XB, 18 * b + 3, gq, c);
+    C.G.red3(T.o_loss_point, mtv(R, gq));
+    C.G.red3(T.o_loss_target, -C.dl * (C.X.v3(18 * b) + mv(R, c)));
+  }
+  for (int f = 0; f < nf; ++f) D.grad_state0[(size_t)f * Bp + i] = C.XB[f];
+}
+
+// Reverse mode through the last rollout on four warps per group of 32 instances (compiled
+// topology, whole tape recorded by the rollout). Every warp runs every phase of a step on its
+// share: bodies and joints split by DevTopo.mw_own (state copies, integrator, hinge kinematics,
+// servo targets, inverse inertias, warm-start and row-assembly reverse, external impulses),
+// the solver's reverse sweeps split into the chain and three helpers (dp_mw.cuh); warp 0 alone
+// runs the servo, controller, feature and hinge reverse. The warps meet at CTA barrier 1
+// between phases; every warp executes the same barrier sequence. Same arithmetic as
+// k_backward up to the order of the row-adjoint sums, which is fixed.
+template <class Q>
+__global__ void __launch_bounds__(128, 1) k_backward_mw(const __grid_constant__ DevTopo T, const __grid_constant__ DevPtrs D) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
+  const int Bp = T.Bp;
+  const int nf = 18 * T.nb;
+  float* sm = g_smem + lane;
+  BwdCtx C{SL{sm}, SL{sm + T.sm_x * 32}, SL{sm + T.sm_xb * 32}, SL{sm + T.sm_vb * 32}, SL{sm + T.sm_rc * 32},
+           SL{sm + T.sm_sbar * 32}, GC{D.prm + i, Bp}, GL{D.grad_prm + i, Bp}, i, D.dloss[i]};
+  const uint32_t bm = T.mw_bmask[warp], jm = T.mw_jmask[warp];
+  for (int f = warp; f < nf; f += 4) C.XB[f] = 0.f;
+  if (warp == 0)
+    for (int k = 0; k < T.n_rec; ++k) C.S[T.sm_hb + k] = 0.f;
+  const size_t sbytes = (size_t)nf * Bp;
+  const int Tw = warp_horizon(D, i);  // the same for the CTA's four warps (same instances)
+  for (int t = Tw - 1; t >= 0; --t) {
+    const RevStep<GSR> V = rev_views<GSR>(T, D, C, t, t);
+    const float* x_t = D.ckpt + (size_t)t * sbytes;
+    // x_{t+1} is on chip from the previous (later) step, except for the first one reversed
+    if (t == Tw - 1) {
+      const float* x_t1 = t + 1 < Tw ? D.ckpt + (size_t)(t + 1) * sbytes : D.state;
+      for (int f = warp; f < nf; f += 4) C.X[f] = x_t1[(size_t)f * Bp + i];
+    }
+    if (warp == 0 && t > 0) prefetch_record_l2(T, tape_step(T, D, t - 1).rec);  // the next step to reverse
+    if (T.grad_decay != 1.f) {  // section 3.2: the adjoint from later steps shrinks by alpha per step
+      for (int f = warp; f < nf; f += 4) C.XB[f] *= T.grad_decay;
+      if (warp == 0)
+        for (int k = 0; k < T.n_rec; ++k) C.S[T.sm_hb + k] *= T.grad_decay;  // and so does h's
+    }
+    mw_barrier();
+    // loss term (by the loss body's owner) and integrator, x_{t+1} on chip
+    if (T.mw_own[T.loss_body] == warp) loss_reverse(T, V.Bl, C.X, C.XB, loss_weight(T, t + 1, D.hz[i]) * C.dl);
+    integrate_reverse(T, GC{x_t + i, Bp}, C.X, C.XB, C.VB, bm);
+    mw_barrier();
+    // x_t on chip; accumulators zeroed
+    for (int f = warp; f < nf; f += 4) C.X[f] = x_t[(size_t)f * Bp + i];
+    for (int j = 0; j < T.nj; ++j) {
+      if (!((jm >> j) & 1u)) continue;
+      C.S[T.sm_thb + j] = 0.f; C.S[T.sm_thdb + j] = 0.f; C.S[T.sm_wstb + j] = 0.f;
+      C.S.s3(T.sm_uab + 3 * j, f3(0.f, 0.f, 0.f));
+    }
+    for (int b = 0; b < T.nb; ++b) {
+      if (!((bm >> b) & 1u)) continue;
+      C.S[T.sm_invmb + b] = 0.f;
+      for (int q = 0; q < 9; ++q) C.S[T.sm_iinvb + 9 * b + q] = 0.f;
+    }
+    for (int q = warp; q < T.nslots * RC_N; q += 4) C.RC[q] = 0.f;
+    mw_barrier();
+    // per-step forward quantities of x_t, recomputed bit-identically
+    hinge_kinematics(T, V.L, C.X, jm);
+    servo_targets(T, V.L, V.act[T.n_layers > 0 ? T.n_layers : 0], jm);
+    inverse_inertia(T, V.L, C.X, bm);
+    mw_barrier();
+    pgs_reverse_mw<Q>(T, V.L, V.tp, warp);
+    if (T.ws) {
+      ws_apply_reverse_own(T, V.L, C.VB, C.RC, V.tp, warp);
+      mw_barrier();
+    }
+    rows_reverse_own(T, V.Bl, C.XB, C.VB, C.RC, warp);
+    mw_barrier();
+    external_reverse(T, V.Bl, C.XB, C.VB, bm);
+    mw_barrier();
+    if (warp == 0) reverse_step_ctrl(T, D, C, V);
+    mw_barrier();
+  }
+  if (warp != 0) return;
   if (T.loss_kind == 3) {  // initial term -a.q(x_0) of the displacement loss
     copy_state_to_smem(T, D.ckpt, i, C.X);
     const int b = T.loss_body;
@@ -543,7 +673,18 @@ cudaError_t launch_backward_ext(const DevTopo& T, const DevPtrs& D, int t, cudaS
   if (T.topo_id == QuadrupedTopo::id) return launch_backward_ext_q<QuadrupedTopo>(T, D, t, s);
   return launch_backward_ext_q<DynTopo>(T, D, t, s);
 }
+template <class Q>
+static cudaError_t launch_backward_mw_q(const DevTopo& T, const DevPtrs& D, cudaStream_t s) {
+  size_t smem = SM_BYTES(T);
+  cudaError_t e = cudaFuncSetAttribute(k_backward_mw<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_backward_mw<Q><<<T.Bp / 32, 128, smem, s>>>(T, D);
+  return cudaGetLastError();
+}
 cudaError_t launch_backward(const DevTopo& T, const DevPtrs& D, cudaStream_t s) {
+  // compiled topology with the whole tape: the solver's reverse sweeps on four warps per group
+  if (T.topo_id == QuadrupedTopo::id && D.tape_full && !getenv("DP_SINGLE_WARP_BACKWARD"))
+    return launch_backward_mw_q<QuadrupedTopo>(T, D, s);
   if (T.topo_id == QuadrupedTopo::id) return launch_backward_q<QuadrupedTopo>(T, D, s);
   return launch_backward_q<DynTopo>(T, D, s);
 }

@@ -160,8 +160,26 @@ def test_single_step_horizon():
 
 
 # ------------------------------------------------------------------------------ gradients
+# Gradients are compared element by element: |g_k - o_k| <= GRAD_RTOL * max(|o_k|, floor) with
+# floor = ELEM_FLOOR * max_k |o_k| over the parameter group: an entry of at least a twentieth of
+# the group's largest is held to 1e-3 of itself, smaller entries to 5e-5 of the largest. Small
+# entries are sums of larger per-step terms that cancel (a servo gain's gradient sums
+# (u - theta) w*_bar over the steps, with u and theta close), so their fp32 rounding is set by
+# the terms, not by the sum; at 1e-2 the worst such entry (quadruped, 40 steps) misses by 10 %.
+ELEM_FLOOR = 5e-2
+
+
 def rel_err(a, b):
     return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-12)
+
+
+def elem_err(a, b, floor=ELEM_FLOOR):
+    """Largest per-element error, each relative to max(|b_k|, floor * max |b|)."""
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    top = float(np.abs(b).max()) if b.size else 0.0
+    scale = np.maximum(np.abs(b), max(floor * top, 1e-30))
+    return float((np.abs(a - b) / scale).max()) if b.size else 0.0
 
 
 def gpu_grads(m, horizon, ckpt_every=None, rows_global=False):
@@ -190,7 +208,7 @@ def check_grads(m, horizon, keys, instances, ckpt_every=None, with_W=False, rows
         L, go = O.rollout_grad(m, i, horizon=horizon)
         assert abs(g["loss"][i] - L) <= 1e-4 * max(1.0, abs(L))
         for k in keys:
-            e = rel_err(g[k][i], go[k])
+            e = elem_err(g[k][i], go[k])
             assert e <= GRAD_RTOL, (m.name, i, k, e, g[k][i].ravel()[:6], go[k].ravel()[:6])
         if with_W:
             Wsum = go["W"] if Wsum is None else Wsum + go["W"]
@@ -229,7 +247,7 @@ def test_quadruped_gradients_controller(fp32, T, ckpt):
     m.ctrl_fp32 = fp32
     g, Wsum = check_grads(m, T, ("state0", "mass", "inertia", "anchor", "motor", "sph_off", "sph_rad"), range(4),
                           ckpt_every=ckpt, with_W=True)
-    assert rel_err(g["W"], Wsum) <= GRAD_RTOL
+    assert elem_err(g["W"], Wsum) <= GRAD_RTOL
 
 
 def test_quadruped_runtime_topology_path(monkeypatch):
@@ -239,7 +257,9 @@ def test_quadruped_runtime_topology_path(monkeypatch):
     m = WL.quadruped(B=8, horizon=60)
     m.ctrl_fp32 = 1
     compare_rollout(m, 60, range(8), min_clean=0.5)
-    check_grads(WL.quadruped(B=2, horizon=20), 20, ("state0", "anchor", "motor"), range(2))
+    m = WL.quadruped(B=2, horizon=20)
+    m.ctrl_fp32 = 1  # 20 steps: beyond the horizon where bfloat16 rounding decisions are shared
+    check_grads(m, 20, ("state0", "anchor", "motor"), range(2))
 
 
 def test_tensor_core_controller_matches_simt(monkeypatch):
@@ -269,7 +289,7 @@ def test_gradients_with_rows_in_global_memory(ckpt):
     m.ctrl_fp32 = 1
     g, Wsum = check_grads(m, 20, ("state0", "mass", "anchor", "motor", "sph_rad"), range(4), ckpt_every=ckpt,
                           with_W=True, rows_global=True)
-    assert rel_err(g["W"], Wsum) <= GRAD_RTOL
+    assert elem_err(g["W"], Wsum) <= GRAD_RTOL
     check_grads(WL.pendulum3(B=4, horizon=60), 60, ("state0", "anchor", "mass"), range(4), ckpt_every=ckpt,
                 rows_global=True)
 
@@ -282,4 +302,4 @@ def test_gradient_decay_quadruped():
         m.ctrl_fp32 = 1
         m.grad_decay = 0.9
         g, Wsum = check_grads(m, 30, ("state0", "mass", "motor"), range(4), ckpt_every=ckpt, with_W=True)
-        assert rel_err(g["W"], Wsum) <= GRAD_RTOL
+        assert elem_err(g["W"], Wsum) <= GRAD_RTOL

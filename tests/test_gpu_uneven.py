@@ -10,7 +10,7 @@ from paper_1611_01652_gb300 import workloads as WL  # noqa: E402
 from paper_1611_01652_gb300.batching import UnevenBatch  # noqa: E402
 from paper_1611_01652_gb300.binding import World  # noqa: E402
 
-from test_gpu_parity import divergence_step, rel_err  # noqa: E402
+from test_gpu_parity import divergence_step, elem_err, rel_err  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -71,10 +71,10 @@ def test_uneven_gradients_match_oracle():
                 assert abs(loss[i].item() - L) <= 1e-4 * max(1.0, abs(L))
                 for k, g in (("state0", ds[i]), ("mass", dp["mass"][i]), ("anchor", dp["anchor"][i]),
                              ("motor", dp["motor"][i]), ("loss_target", dp["loss_target"][i])):
-                    e = rel_err(g.cpu().double().numpy(), go[k])
+                    e = elem_err(g.cpu().double().numpy(), go[k])
                     assert e <= 1e-3, (decay, n, i, k, e)
                 Wsum = go["W"] if Wsum is None else Wsum + go["W"]
-            assert rel_err(dW.cpu().double().numpy(), Wsum) <= 1e-3, (decay, n)
+            assert elem_err(dW.cpu().double().numpy(), Wsum) <= 1e-3, (decay, n)
 
 
 def test_batching_runner_graph_and_autotuner():
