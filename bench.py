@@ -33,6 +33,11 @@ from paper_1611_01652_gb300.replicas import max_over_ranks, replica_seed, whole_
 METRIC = "inst-steps/s fwd+adjoint, quadruped B=4096; warm-start vs plain @equal resid"
 FLOPS = os.path.join(ROOT, "tests", "golden", "flops_per_instance_step.json")
 SM_COUNT, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
+# DRAM bytes (read + written) per instance-step of k_backward_mw, damped start at 10 sweeps:
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch at B = 1024, T = 20 (293.4 MB +
+# 18.8 MB; profiles/k_backward_mw_quadruped_b1024_t20_ws10.md) / (B T). The tape is read once
+# per launch, so the traffic of the full launch scales with B T.
+BWD_TRAFFIC_PER_INST_STEP = {10: (293375744 + 18790656) / (1024 * 20)}
 
 
 def parse():
@@ -54,6 +59,7 @@ def parse():
     p.add_argument("--no-recurrent", action="store_true", help="skip the recurrent controller")
     p.add_argument("--no-sysid", action="store_true", help="skip the system-identification fit")
     p.add_argument("--no-camera", action="store_true", help="skip the differentiable camera")
+    p.add_argument("--no-small", action="store_true", help="skip the ball and pendulum workloads")
     p.add_argument("--camera-only", action="store_true", help="time only the differentiable camera")
     p.add_argument("--sysid-only", action="store_true", help="time only the system-identification fit")
     p.add_argument("--recurrent-only", action="store_true", help="time only the recurrent controller")
@@ -330,6 +336,49 @@ def time_recurrent_controller(args, alpha, H=8):
     return out
 
 
+def time_small_workloads(args, reps=3):
+    """The parity workloads shaped like the paper's ball and pendulum experiments, timed forward
+    and forward + adjoint (1 warm-up + ``reps`` timed passes each, CUDA events): the ball
+    (r = 0.1 m, T = 300 steps of 10 ms, 20 sweeps) at B = 1 and B = 4096, and 3-link pendulums
+    (B = 1024, T = 1000 steps of 1 ms, 10 sweeps, state checkpoints every 32 steps, gradient
+    w.r.t. link parameters and initial angles through the state). Metric: instance-steps/s."""
+    import torch
+
+    from paper_1611_01652_gb300 import workloads as WL
+    from paper_1611_01652_gb300.binding import World
+
+    out = {}
+    for name, m in (("ball_b1", WL.ball(B=1, horizon=300)), ("ball_b4096", WL.ball(B=4096, horizon=300)),
+                    ("pendulum3_b1024", WL.pendulum3(B=1024, horizon=1000))):
+        w = World(m)
+        loss = torch.zeros(m.B, device="cuda")
+        dl = torch.ones(m.B, device="cuda")
+        ds = torch.zeros(m.B, m.nb, 18, device="cuda")
+        dp = {"mass": torch.zeros(m.mass.shape, device="cuda"), "anchor": torch.zeros(m.anchor.shape, device="cuda")}
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        fwd = bwd = 0.0
+        for r in range(reps + 1):
+            ev[0].record()
+            w.rollout(None, loss)
+            ev[1].record()
+            w.backward(dl, None, ds, dp)
+            ev[2].record()
+            torch.cuda.synchronize()
+            if r > 0:
+                fwd += ev[0].elapsed_time(ev[1])
+                bwd += ev[1].elapsed_time(ev[2])
+        w.sync()
+        fwd, bwd = fwd / reps, bwd / reps
+        units = m.B * m.horizon
+        out[name] = {"batch": m.B, "horizon": m.horizon, "iters": m.iters, "ckpt_every": w.ckpt_every,
+                     "fwd_ms": fwd, "fwd_bwd_ms": fwd + bwd, "fwd_inst_steps_per_s": units / (fwd / 1e3),
+                     "fwd_adjoint_inst_steps_per_s": units / ((fwd + bwd) / 1e3),
+                     "finite": bool(torch.isfinite(ds).all().item())}
+        del w
+        torch.cuda.empty_cache()
+    return out
+
+
 def time_sysid(args, iters=300):
     """System identification: 1024 three-link pendulums x 4 swings (B = 4096, T = 300 steps of
     1 ms) fitted to their own observed far-end positions by Adam on the library's link-mass
@@ -500,9 +549,12 @@ def main():
         import torch.distributed as dist
 
         # the secondary workloads are reported at N = 1; a scaling run times the headline only
-        args.no_arms = args.no_wide = args.no_recurrent = args.no_sysid = args.no_camera = True
+        args.no_arms = args.no_wide = args.no_recurrent = args.no_sysid = args.no_camera = args.no_small = True
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    from paper_1611_01652_gb300.binding import fma_peak
+
+    fp32_peak = fma_peak() / 1e12  # TFLOP/s, measured on this GPU
     B, T = args.batch, args.horizon
     if args.no_warmstart:
         rep, nets = None, {}
@@ -574,6 +626,7 @@ def main():
     recurrent = None if args.no_recurrent else time_recurrent_controller(args, args.alpha)
     sysid = None if args.no_sysid else time_sysid(args)
     camera = None if args.no_camera else time_camera(args)
+    small = None if args.no_small else time_small_workloads(args)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -583,13 +636,17 @@ def main():
     flops = json.load(open(FLOPS))
     it = head["iters"]
     fl = flops["quadruped_b4096_t1000" if it == 20 else "quadruped_b4096_t1000_iters%d" % it]
-    peak = SM_COUNT * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12  # TFLOP/s, FP32 FMA at max SM clock
+    derived = SM_COUNT * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12  # TFLOP/s, FP32 FMA at max SM clock
+    peak = fp32_peak if fp32_peak > 0 else derived
     achieved = fl["reverse"] * B * T / (head["bwd_ms"] / 1e3) / 1e12
     roofline = {"bound": "alu", "kernel": "k_backward", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": (BWD_TRAFFIC_PER_INST_STEP[it] * B * T
+                                                      if it in BWD_TRAFFIC_PER_INST_STEP else None),
+                "peak_derived": derived,
                 "basis": "reverse-mode algorithmic FP ops per instance-step at %d sweeps (oracle counter) x B x T / "
-                         "dp_backward time; peak = 152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived from unit counts "
-                         "and the maximum SM clock; no measured FP32 peak)" % it,
+                         "dp_backward time; peak = %s" % (it, (
+                             "measured FP32 FMA throughput of this GPU (dp_fma_peak, best of 5 launches)"
+                             if fp32_peak > 0 else "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)")),
                 "step_frac": (fl["forward"] + fl["reverse"]) * B * T / (ms_per_step / 1e3) / 1e12 / peak}
     cpu = None
     if not args.no_cpu_baseline and world_size == 1:
@@ -616,7 +673,7 @@ def main():
                    "batch": B, "horizon": T, "iters": head["iters"], "ckpt_every": head["ckpt_every"],
                    "l2": "working set (solver tape + controller activations) >> 129 MB L2; no flush needed"},
         "plain": plain, "warmstart": ws, "gate": gate, "uneven_arms": arms, "wide_controller": wide,
-        "recurrent_controller": recurrent, "sysid": sysid, "camera": camera,
+        "recurrent_controller": recurrent, "sysid": sysid, "camera": camera, "small_workloads": small,
         "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": head["clocks"],
         "plain_clocks": p_ck if ws else None,
         "gpu_launches": launches_per_step * args.steps, "fwd_ms": head["fwd_ms"], "bwd_ms": head["bwd_ms"],

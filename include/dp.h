@@ -37,7 +37,8 @@ typedef enum {
   DP_EINVAL = 1,   /* invalid descriptor or argument (nothing was enqueued) */
   DP_ENOMEM = 2,   /* device allocation failed */
   DP_ECUDA = 3,    /* a CUDA call failed; see dp_last_error */
-  DP_ETIMEOUT = 4, /* a bounded wait ran out */
+  DP_ETIMEOUT = 4, /* a bounded wait ran out (reserved: no kernel of this library waits on another
+                      thread or device, so no call returns it) */
   DP_ENAN = 5,     /* a rollout produced a non-finite state or loss */
   DP_ESTATE = 6    /* call out of order (e.g. dp_backward without a matching dp_rollout) */
 } dp_status;
@@ -212,7 +213,8 @@ dp_status dp_backward(dp_world* w, const float* dloss, float* dW, float* dstate0
  * which every GPU that loads the library holds until the process exits, for the split partial
  * sums of the gradient reduction.
  *   - The first call on a device looks up that device's address of the array; make that first
- *     call before any stream capture.
+ *     call before any stream capture. The world's device must be current (DP_EINVAL otherwise),
+ *     and a cudaDeviceReset after the first call is not supported (the array may move).
  *   - A controller layer with more than DP_NOALLOC_SCRATCH_FLOATS weights is rejected with
  *     DP_EINVAL before anything is enqueued.
  *   - All calls on a device share the array. Every value a call reads from it is written
@@ -223,8 +225,32 @@ dp_status dp_backward(dp_world* w, const float* dloss, float* dW, float* dstate0
 #define DP_NOALLOC_SCRATCH_FLOATS (1 << 20)
 dp_status dp_backward_noalloc(dp_world* w, const float* dloss, float* dW);
 
-/* Synchronise the world's stream; DP_ENAN if the last rollout produced a non-finite value. */
+/* Synchronise the world's stream; DP_ENAN if the last rollout (or dp_step) produced a non-finite
+   state or loss, or the last dp_backward a non-finite gradient, naming the first such instance in
+   dp_last_error(). */
 dp_status dp_sync(dp_world* w);
+
+/* Per-instance status flags (the failure report of the problem statement's batch, section 2.2:
+   one robot's non-finite values do not stop the others): bit DP_INST_NAN_STATE is set when the
+   instance met a non-finite state or loss in the rollout or steps since the last dp_rollout, bit
+   DP_INST_NAN_GRAD when its state or parameter adjoint in the last dp_backward was non-finite.
+   dp_instance_status copies the B words to status ([B] int32, host or device, caller-owned),
+   stream-ordered. dp_last_error_detail synchronises the stream and writes a one-line report to
+   buf (at most n bytes including the terminating NUL): how many instances carry each flag, the
+   first eight of them, and the thread's last error message; it returns DP_ENAN when any flag is
+   set, DP_OK otherwise, DP_EINVAL for a NULL world (or a NULL buf with n > 0). */
+#define DP_INST_NAN_STATE 1
+#define DP_INST_NAN_GRAD 2
+dp_status dp_instance_status(dp_world* w, int32_t* status);
+dp_status dp_last_error_detail(dp_world* w, char* buf, size_t n);
+
+/* Measurement utility (not part of the method): enqueues on `stream` a kernel that keeps every
+   SM's FP32 FMA pipes busy (8 blocks of 256 threads per SM, 8 independent FMA chains per thread,
+   iters x 16 FMAs per chain) and writes the FLOPs it performs (2 per FMA) to *flops (host).
+   sink: a device buffer of at least 8 x SMs x 256 floats that the kernel may write. The caller
+   times the kernel on the stream; FLOPs / time is the device's measured FP32 peak, the
+   denominator of the roofline of the FP32-bound kernels. DP_EINVAL for iters < 1 or NULLs. */
+dp_status dp_fma_peak(int64_t iters, float* sink, int64_t* flops, void* stream);
 
 /* Message of the last failed call on this thread (never NULL). */
 const char* dp_last_error(void);

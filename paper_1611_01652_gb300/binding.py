@@ -51,7 +51,9 @@ SYMBOLS = ("dp_create_world", "dp_free", "dp_num_params", "dp_num_slots", "dp_sc
            "dp_ckpt_every", "dp_backward_noalloc", "dp_set_warmstart", "dp_harvest", "dp_set_residual",
            "dp_get_residual", "dp_ws_workspace_floats", "dp_ws_param_count", "dp_ws_loss_grad", "dp_ws_forward",
            "dp_ws_adam", "dp_set_impulses", "dp_get_impulses", "dp_set_recurrent", "dp_get_recurrent",
-           "dp_set_params", "dp_render", "dp_render_backward", "dp_camera_last_error")
+           "dp_set_params", "dp_render", "dp_render_backward", "dp_camera_last_error", "dp_instance_status",
+           "dp_last_error_detail", "dp_fma_peak")
+INST_NAN_STATE, INST_NAN_GRAD = 1, 2
 
 
 def load(build=True):
@@ -79,6 +81,9 @@ def load(build=True):
     lib.dp_backward.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(ParamGrads)]
     lib.dp_backward_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
     lib.dp_sync.argtypes = [C.c_void_p]
+    lib.dp_instance_status.argtypes = [C.c_void_p, C.c_void_p]
+    lib.dp_fma_peak.argtypes = [C.c_int64, C.c_void_p, C.POINTER(C.c_int64), C.c_void_p]
+    lib.dp_last_error_detail.argtypes = [C.c_void_p, C.c_char_p, C.c_size_t]
     lib.dp_last_error.restype = C.c_char_p
     lib.dp_set_warmstart.argtypes = [C.c_void_p, C.c_void_p, C.c_float]
     lib.dp_set_impulses.argtypes = [C.c_void_p, C.c_void_p]
@@ -277,6 +282,18 @@ class World:
     def sync(self):
         _check(_lib.dp_sync(self._h))
 
+    def instance_status(self, out):
+        """Per-instance status flags into ``out`` ([B] int32, host or device): bit INST_NAN_STATE
+        (non-finite state or loss), bit INST_NAN_GRAD (non-finite gradient in the last backward)."""
+        _check(_lib.dp_instance_status(self._h, ptr(out)))
+        return out
+
+    def error_detail(self):
+        """(status, one-line report of the flagged instances and the last error)."""
+        buf = C.create_string_buffer(1024)
+        st = _lib.dp_last_error_detail(self._h, buf, len(buf))
+        return st, buf.value.decode()
+
     def set_warmstart(self, W, alpha=0.7):
         """Enable the learned warm start with network parameters W [WS_PARAMS] and weight alpha
         of the previous step's impulses (W = None: cold start)."""
@@ -339,6 +356,28 @@ def ws_adam(W, dW, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None
                            float(beta2), float(eps), s))
 
 
+def fma_peak(iters=4096, repeats=5):
+    """Measured FP32 FMA throughput of the current device (FLOP/s): the best of ``repeats`` timed
+    launches of the library's FMA kernel (CUDA events on the current stream, after one warm-up)."""
+    import torch
+
+    load()
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sink = torch.empty(8 * props.multi_processor_count * 256, device="cuda")
+    st = torch.cuda.current_stream()
+    fl = C.c_int64(0)
+    best = 0.0
+    for r in range(repeats + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        _check(_lib.dp_fma_peak(int(iters), ptr(sink), C.byref(fl), C.c_void_p(st.cuda_stream)))
+        e1.record(st)
+        e1.synchronize()
+        if r > 0:
+            best = max(best, fl.value / (e0.elapsed_time(e1) * 1e-3))
+    return best
+
+
 def make_rollout_function():
     """torch.autograd.Function: loss[B] = rollout(W, state0) through a World; backward returns
     dL/dW and dL/dstate0 from the library's reverse-mode kernels."""
@@ -347,10 +386,13 @@ def make_rollout_function():
     class Rollout(torch.autograd.Function):
         @staticmethod
         def forward(ctx, W, state0, world):
-            world.set_initial_state(state0.detach().contiguous())
+            # the library reads float32: inputs of another dtype are converted (gradients are
+            # returned in the inputs' dtypes)
+            world.set_initial_state(state0.detach().to(torch.float32).contiguous())
             loss = torch.empty(world.B, device=state0.device, dtype=torch.float32)
-            world.rollout(W.detach().contiguous(), loss)
+            world.rollout(W.detach().to(torch.float32).contiguous() if W is not None else None, loss)
             ctx.world = world
+            ctx.dtypes = (W.dtype if W is not None else None, state0.dtype)
             return loss
 
         @staticmethod
@@ -359,7 +401,8 @@ def make_rollout_function():
             dW = torch.empty(w.n_params, device=gl.device, dtype=torch.float32) if w.n_params else None
             ds = torch.empty(w.B, w.nb, 18, device=gl.device, dtype=torch.float32)
             w.backward(gl.contiguous().float(), dW, ds)
-            return dW, ds, None
+            tw, ts = ctx.dtypes
+            return (dW.to(tw) if dW is not None else None), ds.to(ts), None
 
     return Rollout
 

@@ -221,7 +221,9 @@ void plan_smem(DevTopo& T, bool backward, int smem_floats_max, bool rows_on_chip
     T.sm_rc = take(12 * T.nslots);
     T.sm_sbar = take(T.n_layers > 0 ? T.widths[0] : 1);
     // the run-time reverse sweep's working velocities, or the multi-warp sweep's hand-off ring
-    T.sm_vw = T.sm_ring = take(std::max(6 * T.nb, 4 * DPK_MW_CH));
+    // (compiled topologies without the wide controller: the worlds that run the multi-warp kernel)
+    const bool mw = T.topo_id != 0 && !T.ext_ctrl;
+    T.sm_vw = T.sm_ring = take(mw ? std::max(6 * T.nb, 4 * DPK_MW_CH) : 6 * T.nb);
     T.sm_hb = take(T.n_rec);
     // controller-reverse ping-pong buffers: the row-adjoint region is free by then
     int maxw = 1;
@@ -460,6 +462,7 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
   w->Tb = T;
   int dev = 0, smem_max = 0;
   CU(cudaGetDevice(&dev));
+  w->device = dev;
   CU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   plan_smem(w->Tf, false, smem_max / (int)sizeof(float), d->rows_global == 0);
   plan_smem(w->Tb, true, smem_max / (int)sizeof(float));
@@ -917,6 +920,7 @@ dp_status dp_backward(dp_world* w, const float* dloss, float* dW, float* dstate0
     CU(ext_backward(w, T, D));
   else
     CU(launch_backward(T, D, w->stream));
+  CU(launch_check_grads(w->B, w->Bp, w->nf, T.n_pfields, D.grad_state0, D.grad_prm, D.status, w->stream));
   if (dstate0) {
     CU(launch_state_out(w->B, w->Bp, w->nf, D.grad_state0, w->stage, w->stream));
     CU(cudaMemcpyAsync(dstate0, w->stage, sizeof(float) * (size_t)w->B * w->nf, cudaMemcpyDefault, w->stream));
@@ -961,14 +965,58 @@ dp_status dp_backward(dp_world* w, const float* dloss, float* dW, float* dstate0
   return DP_OK;
 }
 
+// Per-instance status words after a synchronisation of the world's stream.
+static dp_status read_status(dp_world* w, std::vector<int>& st) {
+  CU(cudaStreamSynchronize(w->stream));
+  st.assign(w->Bp, 0);
+  CU(cudaMemcpy(st.data(), w->D.status, sizeof(int) * w->Bp, cudaMemcpyDeviceToHost));
+  return DP_OK;
+}
+
 dp_status dp_sync(dp_world* w) {
   if (!w) return fail(DP_EINVAL, "world is NULL");
-  CU(cudaStreamSynchronize(w->stream));
-  std::vector<int> st(w->Bp);
-  CU(cudaMemcpy(st.data(), w->D.status, sizeof(int) * w->Bp, cudaMemcpyDeviceToHost));
-  for (int i = 0; i < w->B; ++i)
-    if (st[i]) return fail(DP_ENAN, "instance " + std::to_string(i) + " produced a non-finite state or loss");
+  std::vector<int> st;
+  TRY(read_status(w, st));
+  for (int i = 0; i < w->B; ++i) {
+    if (st[i] & DPK_ST_NAN_STATE)
+      return fail(DP_ENAN, "instance " + std::to_string(i) + " produced a non-finite state or loss");
+    if (st[i] & DPK_ST_NAN_GRAD)
+      return fail(DP_ENAN, "instance " + std::to_string(i) + " produced a non-finite gradient");
+  }
   return DP_OK;
+}
+
+dp_status dp_instance_status(dp_world* w, int32_t* status) {
+  if (!w || !status) return fail(DP_EINVAL, "world or status is NULL");
+  CU(cudaMemcpyAsync(status, w->D.status, sizeof(int32_t) * w->B, cudaMemcpyDefault, w->stream));
+  return DP_OK;
+}
+
+dp_status dp_last_error_detail(dp_world* w, char* buf, size_t n) {
+  if (!w || (!buf && n > 0)) return fail(DP_EINVAL, "world or buf is NULL");
+  std::vector<int> st;
+  TRY(read_status(w, st));
+  std::string msg;
+  int bad = 0;
+  for (int bit : {DPK_ST_NAN_STATE, DPK_ST_NAN_GRAD}) {
+    std::string list;
+    int cnt = 0;
+    for (int i = 0; i < w->B; ++i)
+      if (st[i] & bit) {
+        if (cnt < 8) list += (cnt ? ", " : "") + std::to_string(i);
+        ++cnt;
+      }
+    bad += cnt;
+    msg += (bit == DPK_ST_NAN_STATE ? "non-finite state or loss: " : "; non-finite gradient: ") + std::to_string(cnt) +
+           " of " + std::to_string(w->B) + " instances" + (cnt ? " (" + list + (cnt > 8 ? ", ..." : "") + ")" : "");
+  }
+  msg += "; last error: " + g_err;
+  if (n > 0) {
+    const size_t k = std::min(n - 1, msg.size());
+    std::memcpy(buf, msg.data(), k);
+    buf[k] = '\0';
+  }
+  return bad ? DP_ENAN : DP_OK;
 }
 
 }  // extern "C"

@@ -17,6 +17,10 @@
 #define DPK_MAXSLOT (5 * DPK_MAXJ + 2 * DPK_MAXJ + 3 * DPK_MAXS + 3 * DPK_MAXP)
 #define DPK_MAXL 6
 #define DPK_MAXWSG (2 * DPK_MAXJ + DPK_MAXS + DPK_MAXP)
+// per-instance status bits (DevPtrs.status): non-finite state or loss in a forward launch,
+// non-finite state or parameter adjoint in the last reverse pass
+#define DPK_ST_NAN_STATE 1
+#define DPK_ST_NAN_GRAD 2
 // rows per chunk of the multi-warp reverse sweep's hand-off ring (dp_mw.cuh)
 #define DPK_MW_CH 20
 

@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(32, 1) k_forward(const __grid_constant__ DevTo
   bool bad = !isfinite(loss);
   for (int f = 0; f < 18 * T.nb; ++f) bad |= !isfinite(X[f]);
   if (rollout) D.loss[i] = loss;
-  if (bad && i < B) D.status[i] = 1;
+  if (bad && i < B) D.status[i] |= DPK_ST_NAN_STATE;
 }
 
 // ------------------------------------------------------------------------------ backward
@@ -528,6 +528,23 @@ __global__ void __launch_bounds__(32, 1) k_backward_ext(const __grid_constant__ 
     C.G.red3(T.o_loss_target, -C.dl * (C.X.v3(18 * b) + mv(R, c)));
   }
   for (int f = 0; f < nf; ++f) D.grad_state0[(size_t)f * Bp + i] = C.XB[f];
+}
+
+// Per-instance gradient check after a reverse pass: status bit DPK_ST_NAN_GRAD set where the
+// state or parameter adjoint holds a non-finite value, cleared elsewhere.
+__global__ void k_check_grads(int B, int Bp, int nf, int np, const float* __restrict__ gs, const float* __restrict__ gp,
+                              int* status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B) return;
+  bool bad = false;
+  for (int f = 0; f < nf; ++f) bad |= !isfinite(gs[(size_t)f * Bp + i]);
+  for (int f = 0; f < np; ++f) bad |= !isfinite(gp[(size_t)f * Bp + i]);
+  status[i] = (status[i] & ~DPK_ST_NAN_GRAD) | (bad ? DPK_ST_NAN_GRAD : 0);
+}
+cudaError_t launch_check_grads(int B, int Bp, int nf, int np, const float* gs, const float* gp, int* status,
+                               cudaStream_t s) {
+  k_check_grads<<<(B + 127) / 128, 128, 0, s>>>(B, Bp, nf, np, gs, gp, status);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------------------ dW reduction

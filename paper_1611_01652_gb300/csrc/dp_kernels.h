@@ -20,6 +20,8 @@ cudaError_t launch_backward_ext(const DevTopo& T, const DevPtrs& D, int t, cudaS
 cudaError_t launch_dw(const float* del, const float* act, int M, int C, size_t N, float* partial, int splits,
                       size_t chunk, cudaStream_t s);
 cudaError_t launch_rowsum(const float* del, int M, size_t N, float* partial, int splits, size_t chunk, cudaStream_t s);
+cudaError_t launch_check_grads(int B, int Bp, int nf, int np, const float* gs, const float* gp, int* status,
+                               cudaStream_t s);
 cudaError_t launch_sum_splits(const float* partial, int splits, size_t count, float* out, cudaStream_t s);
 int match_compiled_topology(const DevTopo& T, int nb, int nj, int ns, int np, const int* jtype, const int* jbody,
                             const int* jflags, const int* sbody, const int* pair);

@@ -20,13 +20,17 @@ constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
 float* g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the static array on the current device. In host code the array's name is
-// only a host-side stand-in, so the address is looked up once per device with that device
-// current, and reused afterwards.
-dp_status scratch_address(float** out) {
+// Device address of the static array on the world's device, which must be current. In host
+// code the array's name is only a host-side stand-in, so the address is looked up once per
+// device with that device current, and reused afterwards (a cudaDeviceReset after that first
+// call would reload the module and may move the array: not supported).
+dp_status scratch_address(int world_dev, float** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return dp_internal_fail(DP_ECUDA, (std::string("cudaGetDevice: ") + cudaGetErrorString(e)).c_str());
+  if (dev != world_dev)
+    return dp_internal_fail(DP_EINVAL, ("the world's device " + std::to_string(world_dev) + " is not current (device " +
+                                        std::to_string(dev) + " is)").c_str());
   if (dev < 0 || dev >= kMaxDevices) return dp_internal_fail(DP_EINVAL, "device ordinal out of range");
   std::lock_guard<std::mutex> lock(g_scratch_mu);
   if (!g_scratch_addr[dev]) {
@@ -66,7 +70,7 @@ extern "C" dp_status dp_backward_noalloc(dp_world* w, const float* dloss, float*
                                           std::to_string(DP_NOALLOC_SCRATCH_FLOATS) + " floats").c_str());
   }
   float* scratch = nullptr;
-  dp_status st = scratch_address(&scratch);
+  dp_status st = scratch_address(w->device, &scratch);
   if (st != DP_OK) return st;
   DevPtrs& D = w->D;
   CUN(cudaMemcpyAsync(w->stage, dloss, sizeof(float) * w->B, cudaMemcpyDefault, w->stream));

@@ -19,6 +19,7 @@ struct dp_world {
   DevTopo Tf, Tb;  // same topology; forward / backward shared-memory layouts
   DevPtrs D;
   cudaStream_t stream = nullptr;
+  int device = 0;  // the CUDA device current at creation (the world's buffers live there)
   int B = 0, Bp = 0, nf = 0;
   int64_t n_params = 0;
   int w_total = 0;
