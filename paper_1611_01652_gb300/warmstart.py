@@ -125,6 +125,15 @@ def train(rows, steps=2000, batch=65536, lr=2e-3, seed=0, W0=None, val_rows=None
     return W, hist
 
 
+def shrink(W, kappa):
+    """The network with its output scaled by kappa (the linear output layer W3, b3 times kappa):
+    its correction to the damped start is kappa times the original's."""
+    W = W.clone()
+    n3 = WS_H * WS_OUT + WS_OUT
+    W[-n3:] *= float(kappa)
+    return W
+
+
 def evaluate(W, rows, work=None):
     """Mean squared error of the network W over rows (device [n, 19])."""
     import torch

@@ -268,11 +268,15 @@ def test_residual_of_cold_start_matches_oracle():
 # ----------------------------------------------------------------------------- what it gains
 def test_learned_warm_start_training_and_acceptance_gate():
     """Harvest from perturbed rollouts solved with many sweeps (near-converged impulses) from the
-    damped previous-impulse start, train the network on the GPU (it must predict the harvested
-    corrections better than the zero network), then run the acceptance gate on held-out robots
-    with three candidates: the trained network, the zero network (damped previous-impulse start)
-    and a network whose output is far too large. The gate must reject the last, and accept a warm
-    start that reaches the plain solver's residual with fewer sweeps than its 20."""
+    damped previous-impulse start, train the network on the GPU: what it gains over the method
+    without it (the zero network) is checked on held-out rows, a lower error in predicting the
+    converged impulses. Then the acceptance gate on held-out robots with the trained network, the
+    same network with its correction shrunk to a half and a quarter, the zero network (damped
+    previous-impulse start) and a network whose output is far too large: the gate must reject the
+    last and accept a warm start that reaches the plain solver's residual with fewer sweeps than
+    its 20. Whether a trained candidate is the one accepted is reported, not required: on the
+    quadruped's four-footed stance the per-group features do not determine the converged
+    impulses well enough for the corrections to lower the solve residual (see the bench's gate)."""
     torch.manual_seed(0)
     zero = torch.zeros(Bd.WS_PARAMS, device="cuda")
     mh = WL.quadruped(B=512, horizon=200, seed=2002)
@@ -288,8 +292,9 @@ def test_learned_warm_start_training_and_acceptance_gate():
     assert hist[-1][2] < e0, (e0, hist)
     bad = torch.tensor(constant_network((50.0, 50.0, 50.0)), device="cuda")
     m = WL.quadruped(B=128, horizon=200, seed=3003)
-    rep = WS.accept(m, [("learned", Wws, 0.7), ("damped", zero, 0.7), ("bad", bad, 0.7)], plain_iters=20,
-                    sweep_grid=(5, 7, 10, 14), horizon=200)
+    rep = WS.accept(m, [("learned", Wws, 0.7), ("learned x0.5", WS.shrink(Wws, 0.5), 0.7),
+                        ("learned x0.25", WS.shrink(Wws, 0.25), 0.7), ("damped", zero, 0.7), ("bad", bad, 0.7)],
+                    plain_iters=20, sweep_grid=(5, 7, 10, 14), horizon=200)
     print("acceptance gate", rep)
     assert not any(c["accepted"] for c in rep["candidates"] if c["name"] == "bad"), rep
     assert rep["accepted"] is not None and rep["accepted"][1] < 20, rep
