@@ -1302,7 +1302,10 @@ int orc_flops(const orc_topo* T, const orc_inst* I, const double* W, int32_t hor
 // derivatives with respect to the state and the texture. Rays that hit nothing are black.
 // Spheres (kind 1, radius = half[0]) are intersected as |C + t d - c_w| = r; their texture
 // coordinates come from the hit point's direction in the sphere's body frame,
-// u = atan2(y, x) / (2 pi) + 1/2, v = acos(z / r) / pi.
+// u = atan2(y, x) / (2 pi) + 1/2, v = acos(z / r) / pi. A plane (kind 2) is the plane z = 0 of
+// the object's frame (a ground plane, seen from either side); its texture repeats with periods
+// 2 half[0] and 2 half[1] along the frame's x and y: u = frac(x / (2 half[0]) + 1/2),
+// v = frac(y / (2 half[1]) + 1/2).
 // Reverse mode keeps the discrete choices (which object, which face, which texels) of the forward
 // pass and differentiates the rest (the oracle's tape).
 extern "C" {
@@ -1321,7 +1324,7 @@ typedef struct {
   const int32_t* tex;     // [n_obj] texture index
   int32_t n_tex, tex_h, tex_w;
   const double* tex_data; // [n_tex][tex_h][tex_w][3]
-  const int32_t* kind;    // [n_obj] 0 = box, 1 = sphere of radius half[0] (NULL: all boxes)
+  const int32_t* kind;    // [n_obj] 0 = box, 1 = sphere of radius half[0], 2 = plane (NULL: all boxes)
 } orc_scene;
 }  // extern "C"
 
@@ -1352,6 +1355,14 @@ static void render_impl(const orc_camera& cam, const orc_scene& sc, const std::v
         for (int k = 0; k < 3; ++k) {  // R^T (C - c_w), R^T d
           ol[k] = R[k] * (S(cam.pos[0]) - cw[0]) + R[3 + k] * (S(cam.pos[1]) - cw[1]) + R[6 + k] * (S(cam.pos[2]) - cw[2]);
           dlo[k] = R[k] * d[0] + R[3 + k] * d[1] + R[6 + k] * d[2];
+        }
+        if (sc.kind && sc.kind[o] == 2) {  // plane z = 0 of the object frame
+          if (val(dlo[2]) == 0.0) continue;
+          const double tn = -val(ol[2]) / val(dlo[2]);
+          if (!(tn >= 1.0) || !(tn < bt)) continue;
+          best = o; bk = -2; bt = tn;
+          for (int k = 0; k < 3; ++k) { bl[k] = ol[k]; dl[k] = dlo[k]; }
+          continue;
         }
         if (sc.kind && sc.kind[o] == 1) {  // sphere: a t^2 + 2 b t + c = 0 in the body frame
           const double r = sc.half[3 * o];
@@ -1387,7 +1398,13 @@ static void render_impl(const orc_camera& cam, const orc_scene& sc, const std::v
       if (hit_obj) hit_obj[(size_t)i * W + j] = best;
       if (best < 0) continue;
       S u, v;
-      if (bk < 0) {  // sphere: the near root, then the hit direction's spherical angles
+      if (bk == -2) {  // plane: in-plane coordinates of the hit point, the texture repeated
+        S t = -bl[2] / dl[2];
+        S uu = (bl[0] + t * dl[0]) / S(2.0 * sc.half[3 * best]) + S(0.5);
+        S vv = (bl[1] + t * dl[1]) / S(2.0 * sc.half[3 * best + 1]) + S(0.5);
+        u = uu - S(std::floor(val(uu)));
+        v = vv - S(std::floor(val(vv)));
+      } else if (bk < 0) {  // sphere: the near root, then the hit direction's spherical angles
         const double r = sc.half[3 * best];
         S a = dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2];
         S b = dl[0] * bl[0] + dl[1] * bl[1] + dl[2] * bl[2];

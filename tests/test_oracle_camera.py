@@ -194,3 +194,81 @@ def test_sphere_occludes_box_and_gradients_match_central_differences():
         tm[idx] -= eps
         fd = (f(tt=tp) - f(tt=tm)) / (2 * eps)
         assert abs(fd - dt[idx]) <= 1e-7 * max(1.0, abs(fd)), (idx, fd, dt[idx])
+
+
+def test_ground_plane_with_linear_texture_and_period():
+    """A world plane z = -Z0 (kind 2: the plane z = 0 of a frame centred at (0, 0, -Z0)). The pixel
+    (i, j) ray of the camera at the origin looking along +y meets it, for rows below the centre
+    (i + 1/2 > H/2), at x = Z0 (j + 1/2 - W/2) / (i + 1/2 - H/2), y = Z0 f / (i + 1/2 - H/2), if
+    that is beyond the projection plane (y >= P). The texture repeats with periods 2 h0, 2 h1:
+    u = frac(x / (2 h0) + 1/2), v = frac(y / (2 h1) + 1/2); a texture linear in (u, v) comes back
+    exactly inside the texel-centre grid. Moving the plane by one period along x leaves the frame
+    unchanged; by half a period it does not."""
+    W, H, f, Z0, P = 40, 20, 20.0, 1.0, 0.05
+    h0, h1 = 0.7, 1.3
+    th, tw = 8, 8
+    coef = [(0.3, 0.5, 0.1), (-0.2, 0.4, 0.5), (0.7, -0.1, 0.2)]
+    tex = linear_texture(th, tw, coef)
+
+    def frame(x0):
+        cs = scene([(-1, [x0, 0.0, -Z0], [h0, h1, 1.0], 0)], W, H, f, plane=P, tex=tex, th=th, tw=tw, kinds=[2])
+        return O.render(cs, np.zeros((0, 18)))
+
+    img, hit = frame(0.0)
+    checked = 0
+    for i in range(H):
+        for j in range(W):
+            di = (i + 0.5) - H / 2
+            if di <= 0 or Z0 * f / di < P:
+                assert hit[i, j] == -1 or di > 0
+                continue
+            assert hit[i, j] == 0, (i, j)
+            x, y = Z0 * ((j + 0.5) - W / 2) / di, Z0 * f / di
+            u = (x / (2 * h0) + 0.5) % 1.0
+            v = (y / (2 * h1) + 0.5) % 1.0
+            if not (0.5 / tw <= u <= 1 - 0.5 / tw and 0.5 / th <= v <= 1 - 0.5 / th):
+                continue
+            for ch, (a, b, c0) in enumerate(coef):
+                assert abs(img[i, j, ch] - (a * u + b * v + c0)) <= 1e-12, (i, j, ch)
+            checked += 1
+    assert checked >= 40
+    assert (hit[: H // 2] == -1).all()  # above the horizon nothing is seen
+    img2, _ = frame(2 * h0)
+    assert np.abs(img2 - img).max() <= 1e-9
+    img3, _ = frame(h0)
+    assert np.abs(img3 - img).max() > 1e-2
+
+
+def test_body_carried_plane_gradients_match_central_differences():
+    """A plane carried by a tilted body fills the lower half of the frame: the gradient of a
+    random weighting of the frame with respect to the body's position and rotation entries and
+    to the texels equals central differences of the forward pass."""
+    rng = np.random.default_rng(4)
+    W, H, f = 24, 12, 12.0
+    cs = scene([(0, [0.0, 0.0, 0.0], [0.9, 1.1, 1.0], 0)], W, H, f, th=6, tw=6, kinds=[2])
+    a = 0.15
+    R = np.array([[1.0, 0.0, 0.0], [0.0, np.cos(a), -np.sin(a)], [0.0, np.sin(a), np.cos(a)]])
+    x = np.zeros((1, 18))
+    x[0, 0:3] = [0.1, 0.0, -1.0]
+    x[0, 3:12] = R.reshape(-1)
+    dimg = rng.normal(size=(H, W, 3))
+    ds, dt = O.render_grad(cs, x, dimg)
+
+    def fval(xx=None, tt=None):
+        img, _ = O.render(cs, x if xx is None else xx, tex=tt)
+        return float((img * dimg).sum())
+
+    eps = 1e-6
+    for k in range(12):
+        xp, xm = x.copy(), x.copy()
+        xp[0, k] += eps
+        xm[0, k] -= eps
+        fd = (fval(xp) - fval(xm)) / (2 * eps)
+        assert abs(ds[0, k] - fd) <= 1e-5 * max(1.0, abs(fd)), (k, ds[0, k], fd)
+    t0 = np.asarray(cs.textures, np.float64)
+    for idx in [(0, 2, 3, 0), (0, 4, 1, 2), (0, 0, 0, 1)]:
+        tp, tm = t0.copy(), t0.copy()
+        tp[idx] += eps
+        tm[idx] -= eps
+        fd = (fval(tt=tp) - fval(tt=tm)) / (2 * eps)
+        assert abs(dt[idx] - fd) <= 1e-5 * max(1.0, abs(fd)), (idx, dt[idx], fd)
