@@ -457,11 +457,21 @@ def time_camera(args, reps=20):
         with open(pf) as fh:
             peak, source = float(json.load(fh)["hbm_gbs"]), "measured"
     achieved = npix * 12 / (f_ms / 1e3) / 1e9
-    return {"workload": "camera: %d frames of 288 x 96, pendulum scene (4 textured boxes)" % st.shape[0],
-            "fwd_ms": f_ms, "fwd_bwd_ms": fb_ms, "frames_per_s_fwd": st.shape[0] / (f_ms / 1e3),
-            "frames_per_s_fwd_bwd": st.shape[0] / (fb_ms / 1e3), "unit": "frames/s",
-            "roofline_fwd": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "peak_source": source}}
+    out = {"workload": "camera: %d frames of 288 x 96, pendulum scene (4 textured boxes)" % st.shape[0],
+           "fwd_ms": f_ms, "fwd_bwd_ms": fb_ms, "frames_per_s_fwd": st.shape[0] / (f_ms / 1e3),
+           "frames_per_s_fwd_bwd": st.shape[0] / (fb_ms / 1e3), "unit": "frames/s",
+           "roofline_fwd": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak, "peak_source": source}}
+    # the same frames with a sphere on the last link and a textured ground plane
+    cm = WL.camera_scene(B=args.batch, W=288, H=96, mixed=True)
+    rig = CameraRig(cm)
+    tex = torch.tensor(cm.textures, device="cuda")
+    f_ms = timed(lambda: rig.render(st, tex, img))
+    fb_ms = timed(lambda: (rig.render(st, tex, img), rig.render_backward(st, tex, dimg, ds)))
+    out["mixed"] = {"workload": "the same with a sphere and a ground plane (6 objects)", "fwd_ms": f_ms,
+                    "fwd_bwd_ms": fb_ms, "frames_per_s_fwd": st.shape[0] / (f_ms / 1e3),
+                    "frames_per_s_fwd_bwd": st.shape[0] / (fb_ms / 1e3)}
+    return out
 
 
 def time_wide_controller(args, alpha):

@@ -346,17 +346,22 @@ dp_status dp_ws_adam(float* W, const float* dW, float* m, float* v, int64_t coun
 
 /* ------------------------------------------------------------------------------------------
    Differentiable camera (section 3.4: the inverted pendulum observed by a camera). A pinhole ray
-   tracer over textured oriented boxes carried by the bodies, batched over instances. The pixel
+   tracer over textured objects carried by the bodies (oriented boxes, spheres, planes), batched
+   over instances. The pixel
    (row i, column j) ray leaves the camera centre C along
        d = R_c^T (P ((j + 1/2) - W/2) / f, P ((i + 1/2) - H/2) / f, P),
-   so t = 1 is the projection plane at distance P; of the box hits at t >= 1 (in front of the
-   projection plane) the nearest is seen. The entry face (box axis k) gives texture coordinates
-   u = (x_a / h_a + 1) / 2, v = (x_b / h_b + 1) / 2 (a = k+1, b = k+2 mod 3, x: the hit point in the
-   box frame, h: half extents) and the colour is the bilinear interpolation of the box's texture
+   so t = 1 is the projection plane at distance P; of the object hits at t >= 1 (in front of the
+   projection plane) the nearest is seen. Texture coordinates from the hit point x in the
+   object's frame (centre c in the body frame, axes of the body): a box's entry face (box axis k)
+   gives u = (x_a / h_a + 1) / 2, v = (x_b / h_b + 1) / 2 (a = k+1, b = k+2 mod 3, h: half extents);
+   a sphere of radius h_0 gives u = atan2(x_1, x_0) / (2 pi) + 1/2, v = acos(x_2 / h_0) / pi; a plane
+   (the plane x_2 = 0, seen from either side) gives u = frac(x_0 / (2 h_0) + 1/2),
+   v = frac(x_1 / (2 h_1) + 1/2) (the texture repeats). The colour is the bilinear interpolation of the object's texture
    (texel centres at ((c + 1/2) / Wt, (r + 1/2) / Ht), clamped at the edges). Rays that hit
-   nothing are black. Reverse mode keeps the forward pass's discrete choices (box, face, texels)
-   and differentiates the rest, so the frame's derivatives with respect to the body poses and the
-   texels are those of the bilinear interpolation. */
+   nothing are black. Reverse mode keeps the forward pass's discrete choices (object, face,
+   texels, the period of a plane's texture) and differentiates the rest, so the frame's
+   derivatives with respect to the body poses and the texels are those of the bilinear
+   interpolation. */
 #define DP_CAMERA_MAX_OBJECTS 16
 
 typedef struct {
@@ -367,18 +372,21 @@ typedef struct {
   float rotation[9];     /* R_c, row-major: rows are the image-right, image-down and optical axes (world) */
 } dp_camera;
 
+enum { DP_OBJ_BOX = 0, DP_OBJ_SPHERE = 1, DP_OBJ_PLANE = 2 };
 typedef struct {
-  int32_t n_obj;           /* boxes, <= DP_CAMERA_MAX_OBJECTS */
-  const int32_t* body;     /* [n_obj] body carrying the box, -1 = the world frame (host) */
-  const float* center;     /* [n_obj][3] box centre in the body frame (host) */
-  const float* half;       /* [n_obj][3] half extents along the body axes, > 0 (host) */
+  int32_t n_obj;           /* objects, <= DP_CAMERA_MAX_OBJECTS */
+  const int32_t* body;     /* [n_obj] body carrying the object, -1 = the world frame (host) */
+  const float* center;     /* [n_obj][3] object centre in the body frame (host) */
+  const float* half;       /* [n_obj][3] box half extents along the body axes; sphere: radius in
+                              [0]; plane: texture half periods in [0], [1]; all > 0 (host) */
   const int32_t* tex;      /* [n_obj] texture index (host) */
   int32_t n_tex, tex_h, tex_w; /* textures [n_tex][tex_h][tex_w][3] */
+  const int32_t* kind;     /* [n_obj] DP_OBJ_* (host), or NULL: every object is a box */
 } dp_scene;
 
 /* Frames image [B][H][W][3] (device) of B instances with body states state [B][nb][18]
    (device; p, R row-major, v, w as dp_get_state) and textures [n_tex][tex_h][tex_w][3]
-   (device); hit [B][H][W] (device, optional) receives the box each pixel sees (-1: none). All
+   (device); hit [B][H][W] (device, optional) receives the object each pixel sees (-1: none). All
    buffers are caller-owned; ordered on `stream` (a cudaStream_t or NULL). DP_EINVAL for a
    malformed camera or scene (dp_camera_last_error says why). */
 dp_status dp_render(const dp_camera* cam, const dp_scene* scene, int32_t n_instances, int32_t n_bodies,

@@ -415,7 +415,7 @@ class Camera(C.Structure):
 
 class Scene(C.Structure):
     _fields_ = [("n_obj", C.c_int32), ("body", PI), ("center", PF), ("half", PF), ("tex", PI),
-                ("n_tex", C.c_int32), ("tex_h", C.c_int32), ("tex_w", C.c_int32)]
+                ("n_tex", C.c_int32), ("tex_h", C.c_int32), ("tex_w", C.c_int32), ("kind", PI)]
 
 
 class CameraRig:
@@ -433,13 +433,15 @@ class CameraRig:
         self._keep = [np.ascontiguousarray(np.asarray(cs.obj_body, np.int32)),
                       np.ascontiguousarray(np.asarray(cs.obj_center, np.float32)),
                       np.ascontiguousarray(np.asarray(cs.obj_half, np.float32)),
-                      np.ascontiguousarray(np.asarray(cs.obj_tex, np.int32))]
+                      np.ascontiguousarray(np.asarray(cs.obj_tex, np.int32)),
+                      np.ascontiguousarray(np.asarray(getattr(cs, "obj_kind", np.zeros(len(cs.obj_body))), np.int32))]
         self.scene = Scene()
         self.scene.n_obj = len(self._keep[0])
         self.scene.body = self._keep[0].ctypes.data_as(PI)
         self.scene.center = self._keep[1].ctypes.data_as(PF)
         self.scene.half = self._keep[2].ctypes.data_as(PF)
         self.scene.tex = self._keep[3].ctypes.data_as(PI)
+        self.scene.kind = self._keep[4].ctypes.data_as(PI)
         t = np.asarray(cs.textures)
         self.scene.n_tex, self.scene.tex_h, self.scene.tex_w = t.shape[0], t.shape[1], t.shape[2]
         self.nb = int(cs.nb)

@@ -1,14 +1,17 @@
 // Differentiable camera (arXiv 1611.01652, section 3.4: the inverted pendulum observed by a camera).
-// A pinhole ray tracer over textured oriented boxes carried by the bodies, batched over
-// instances: one thread per pixel. The pixel (i, j) ray leaves the camera centre C along
-// d = R_c^T (P ((j + 1/2) - W/2) / f, P ((i + 1/2) - H/2) / f, P), so t = 1 is the projection plane
-// at distance P; every box is intersected with the slab test in its own frame, and of the hits at
-// t >= 1 (in front of the projection plane) the nearest is kept. The entry face (box axis k)
-// gives texture coordinates u = (x_a / h_a + 1) / 2, v = (x_b / h_b + 1) / 2 (a = k+1, b = k+2
-// mod 3) and the colour is the bilinear interpolation of the box's texture (texel centres at
+// A pinhole ray tracer over textured objects carried by the bodies (oriented boxes, spheres,
+// planes), batched over instances: four pixels per thread. The pixel (i, j) ray leaves the camera
+// centre C along d = R_c^T (P ((j + 1/2) - W/2) / f, P ((i + 1/2) - H/2) / f, P), so t = 1 is the
+// projection plane at distance P; every object is intersected in its own frame (boxes: slab
+// test; spheres: |o + t d| = r; planes: the frame's z = 0), and of the hits at t >= 1 (in front
+// of the projection plane) the nearest is kept. Texture coordinates come from the hit point in
+// the object's frame (box: the entry face, u = (x_a / h_a + 1) / 2, v = (x_b / h_b + 1) / 2 with
+// a = k+1, b = k+2 mod 3 for face axis k; sphere: u = atan2(y, x) / (2 pi) + 1/2,
+// v = acos(z / r) / pi; plane: u = frac(x / (2 h_0) + 1/2), v = frac(y / (2 h_1) + 1/2)) and the
+// colour is the bilinear interpolation of the object's texture (texel centres at
 // ((c + 1/2) / Wt, (r + 1/2) / Ht), clamped at the edges), so the frame has non-zero derivatives
 // with respect to the state and the texels. Reverse mode keeps the forward pass's discrete
-// choices (box, face, texels) and differentiates the rest.
+// choices (object, face, texels, texture period) and differentiates the rest.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -25,14 +28,14 @@ struct CamArgs {
   int W, H, B, nb, n_obj, th, tw;
   float f, plane;
   float C[3], Rc[9];
-  int body[kMaxObj], tex[kMaxObj];
+  int body[kMaxObj], tex[kMaxObj], kind[kMaxObj];
   float cen[kMaxObj][3], half[kMaxObj][3];
 };
 
 struct Hit {
-  int obj, k;
+  int obj, k;          // k: the entry face's axis (boxes); -1 sphere, -2 plane
   float t;
-  float ol[3], dl[3];  // ray origin and direction in the hit box's frame
+  float ol[3], dl[3];  // ray origin and direction in the hit object's frame
 };
 
 // Frame of one box for one instance: R (box to world), centre c_w, and the camera centre in the
@@ -121,6 +124,37 @@ __device__ Hit trace(const CamArgs& A, const float* __restrict__ state, const Bo
     float dl[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) dl[k] = F.R[k] * d[0] + F.R[3 + k] * d[1] + F.R[6 + k] * d[2];
+    if (A.kind[o] != DP_OBJ_BOX) {
+      float tn;
+      int kn;
+      if (A.kind[o] == DP_OBJ_SPHERE) {
+        // near root of a t^2 + 2 b t + c = 0 with the discriminant as a r^2 - |d x o|^2 (no
+        // cancellation when the sphere is far)
+        const float r = A.half[o][0];
+        const float a = dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2];
+        const float b = dl[0] * F.o[0] + dl[1] * F.o[1] + dl[2] * F.o[2];
+        const float cx = dl[1] * F.o[2] - dl[2] * F.o[1], cy = dl[2] * F.o[0] - dl[0] * F.o[2],
+                    cz = dl[0] * F.o[1] - dl[1] * F.o[0];
+        const float disc = a * r * r - (cx * cx + cy * cy + cz * cz);
+        if (!(disc >= 0.f)) continue;
+        tn = (-b - sqrtf(disc)) / a;
+        kn = -1;
+      } else {
+        if (dl[2] == 0.f) continue;
+        tn = -F.o[2] / dl[2];
+        kn = -2;
+      }
+      if (!(tn >= 1.f) || !(tn < h.t)) continue;
+      h.obj = o;
+      h.k = kn;
+      h.t = tn;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        h.ol[k] = F.o[k];
+        h.dl[k] = dl[k];
+      }
+      continue;
+    }
     float tn = -INFINITY, tf = INFINITY;
     int kn = 0;
     bool miss = false;
@@ -157,27 +191,48 @@ __device__ Hit trace(const CamArgs& A, const float* __restrict__ state, const Bo
   return h;
 }
 
-// Texture coordinates of a hit: the entry-plane parameter t, the hit point's two in-face
-// coordinates qa, qc, and the bilinear sample position.
+// Texture coordinates of a hit: the hit parameter t, the hit point p in the object's frame (for a
+// box face: its two in-face coordinates qa = p_a, qc = p_c), and the bilinear sample position.
 struct Sample {
   int a, c;
   float s, t, qa, qc, fx, fy;
+  float p[3];
   int x0, x1, y0, y1;
 };
 
 __device__ __forceinline__ Sample sample_of(const CamArgs& A, const Hit& h) {
   Sample S;
-  const int k = h.k;
-  S.a = (k + 1) % 3;
-  S.c = (k + 2) % 3;
-  const float hk = A.half[h.obj][k];
-  const float dk = pick3(h.dl, k), ok = pick3(h.ol, k);
-  S.s = dk > 0.f ? -1.f : 1.f;
-  S.t = (S.s * hk - ok) / dk;
-  S.qa = pick3(h.ol, S.a) + S.t * pick3(h.dl, S.a);
-  S.qc = pick3(h.ol, S.c) + S.t * pick3(h.dl, S.c);
-  const float u = (S.qa / A.half[h.obj][S.a] + 1.f) * 0.5f;
-  const float v = (S.qc / A.half[h.obj][S.c] + 1.f) * 0.5f;
+  float u, v;
+  if (h.k >= 0) {
+    const int k = h.k;
+    S.a = (k + 1) % 3;
+    S.c = (k + 2) % 3;
+    const float hk = A.half[h.obj][k];
+    const float dk = pick3(h.dl, k), ok = pick3(h.ol, k);
+    S.s = dk > 0.f ? -1.f : 1.f;
+    S.t = (S.s * hk - ok) / dk;
+    S.qa = pick3(h.ol, S.a) + S.t * pick3(h.dl, S.a);
+    S.qc = pick3(h.ol, S.c) + S.t * pick3(h.dl, S.c);
+    u = (S.qa / A.half[h.obj][S.a] + 1.f) * 0.5f;
+    v = (S.qc / A.half[h.obj][S.c] + 1.f) * 0.5f;
+  } else {
+    S.a = 0;
+    S.c = 1;
+    S.s = 0.f;
+    S.t = h.t;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) S.p[k] = h.ol[k] + S.t * h.dl[k];
+    if (h.k == -1) {  // sphere: the hit direction's spherical angles in the body frame
+      const float r = A.half[h.obj][0];
+      u = atan2f(S.p[1], S.p[0]) * (0.5f / 3.14159265358979f) + 0.5f;
+      v = acosf(fminf(fmaxf(S.p[2] / r, -1.f), 1.f)) * (1.f / 3.14159265358979f);
+    } else {  // plane: in-plane coordinates, the texture repeated
+      const float uu = S.p[0] / (2.f * A.half[h.obj][0]) + 0.5f, vv = S.p[1] / (2.f * A.half[h.obj][1]) + 0.5f;
+      u = uu - floorf(uu);
+      v = vv - floorf(vv);
+    }
+    S.qa = S.qc = 0.f;
+  }
   const float xs = u * (float)A.tw - 0.5f, ys = v * (float)A.th - 0.5f;
   const float x0f = floorf(xs), y0f = floorf(ys);
   S.fx = xs - x0f;
@@ -274,17 +329,53 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__
           F = sf[h.obj];
         else
           box_frame(A, state, inst, h.obj, F);
-        // fx = u tw - 1/2 - floor, u = (qa / h_a + 1)/2: dqa = dfx tw / (2 h_a); likewise qc
-        const float dqa = dfx * (float)A.tw * 0.5f / A.half[h.obj][S.a];
-        const float dqc = dfy * (float)A.th * 0.5f / A.half[h.obj][S.c];
-        const float dt = dqa * pick3(h.dl, S.a) + dqc * pick3(h.dl, S.c);
-        const float dk = pick3(h.dl, h.k);
+        // fx = u tw - 1/2 - floor: du = dfx tw; likewise dv = dfy th
+        const float gu = dfx * (float)A.tw, gv = dfy * (float)A.th;
         float dol[3], ddl[3];
+        if (h.k >= 0) {
+          // u = (qa / h_a + 1)/2: dqa = du / (2 h_a); likewise qc
+          const float dqa = gu * 0.5f / A.half[h.obj][S.a];
+          const float dqc = gv * 0.5f / A.half[h.obj][S.c];
+          const float dt = dqa * pick3(h.dl, S.a) + dqc * pick3(h.dl, S.c);
+          const float dk = pick3(h.dl, h.k);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          // qa = ol_a + t dl_a, qc = ol_c + t dl_c, t = (s h_k - ol_k) / dl_k
-          dol[k] = (k == S.a ? dqa : 0.f) + (k == S.c ? dqc : 0.f) + (k == h.k ? -dt / dk : 0.f);
-          ddl[k] = (k == S.a ? dqa * S.t : 0.f) + (k == S.c ? dqc * S.t : 0.f) + (k == h.k ? -dt * S.t / dk : 0.f);
+          for (int k = 0; k < 3; ++k) {
+            // qa = ol_a + t dl_a, qc = ol_c + t dl_c, t = (s h_k - ol_k) / dl_k
+            dol[k] = (k == S.a ? dqa : 0.f) + (k == S.c ? dqc : 0.f) + (k == h.k ? -dt / dk : 0.f);
+            ddl[k] = (k == S.a ? dqa * S.t : 0.f) + (k == S.c ? dqc * S.t : 0.f) + (k == h.k ? -dt * S.t / dk : 0.f);
+          }
+        } else {
+          // adjoint of the hit point p = o + t d, then of o and d through t
+          float gp[3];
+          if (h.k == -1) {
+            const float r = A.half[h.obj][0];
+            const float rho2 = S.p[0] * S.p[0] + S.p[1] * S.p[1];
+            const float cu = gu * (0.5f / 3.14159265358979f) / fmaxf(rho2, 1e-30f);
+            const float zr = fminf(fmaxf(S.p[2] / r, -1.f), 1.f);
+            gp[0] = -cu * S.p[1];
+            gp[1] = cu * S.p[0];
+            gp[2] = -gv / (3.14159265358979f * r * sqrtf(fmaxf(1e-30f, 1.f - zr * zr)));
+            // a t^2 + 2 b t + c = 0: dt/do = -p / (a t + b), dt/dd = -t p / (a t + b)
+            const float a = h.dl[0] * h.dl[0] + h.dl[1] * h.dl[1] + h.dl[2] * h.dl[2];
+            const float b = h.dl[0] * h.ol[0] + h.dl[1] * h.ol[1] + h.dl[2] * h.ol[2];
+            const float q = (gp[0] * h.dl[0] + gp[1] * h.dl[1] + gp[2] * h.dl[2]) / (a * S.t + b);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              dol[k] = gp[k] - q * S.p[k];
+              ddl[k] = S.t * (gp[k] - q * S.p[k]);
+            }
+          } else {
+            gp[0] = gu * 0.5f / A.half[h.obj][0];
+            gp[1] = gv * 0.5f / A.half[h.obj][1];
+            // t = -o_z / d_z: dt/do_z = -1 / d_z, dt/dd_z = -t / d_z
+            const float q = (gp[0] * h.dl[0] + gp[1] * h.dl[1]) / h.dl[2];
+            dol[0] = gp[0];
+            dol[1] = gp[1];
+            dol[2] = -q;
+            ddl[0] = S.t * gp[0];
+            ddl[1] = S.t * gp[1];
+            ddl[2] = -q * S.t;
+          }
         }
         float d[3];
         ray_dir(A, i, j, d);
@@ -359,6 +450,8 @@ dp_status cam_args(const dp_camera* cam, const dp_scene* sc, int32_t B, int32_t 
     if (sc->tex[o] < 0 || sc->tex[o] >= sc->n_tex) { g_cam_err = "scene: object texture out of range"; return DP_EINVAL; }
     A.body[o] = sc->body[o];
     A.tex[o] = sc->tex[o];
+    A.kind[o] = sc->kind ? sc->kind[o] : DP_OBJ_BOX;
+    if (A.kind[o] < DP_OBJ_BOX || A.kind[o] > DP_OBJ_PLANE) { g_cam_err = "scene: unknown object kind"; return DP_EINVAL; }
     for (int k = 0; k < 3; ++k) {
       A.cen[o][k] = sc->center[3 * o + k];
       A.half[o][k] = sc->half[3 * o + k];

@@ -256,9 +256,10 @@ def pendulum_sysid(B=4096, K=4, seed=1004, horizon=300, iters=10, dt=0.001, m0=1
 
 
 class CameraScene:
-    """A camera looking at textured boxes carried by a model's bodies (attributes: W, H, f (focal
+    """A camera looking at textured objects carried by a model's bodies (attributes: W, H, f (focal
     length in pixels), plane (distance of the projection plane, m), cam_pos [3], cam_rot [3, 3] (rows: image right, image down, optical axis), obj_body,
-    obj_center [n, 3], obj_half [n, 3], obj_tex, textures [n_tex, th, tw, 3], states [B, nb, 18])."""
+    obj_center [n, 3], obj_half [n, 3], obj_tex, textures [n_tex, th, tw, 3], states [B, nb, 18],
+    and optionally obj_kind [n]: 0 box, 1 sphere of radius half[0], 2 plane; absent: all boxes)."""
 
 
 def procedural_textures(n, th=64, tw=64, seed=7):
@@ -278,12 +279,13 @@ def procedural_textures(n, th=64, tw=64, seed=7):
     return out
 
 
-def camera_scene(B=4096, W=288, H=96, seed=1005, tex_size=64):
+def camera_scene(B=4096, W=288, H=96, seed=1005, tex_size=64, mixed=False):
     """The 3-link pendulum seen by a camera (the paper's camera sensor, section 3.4, at its 288 x 96
     resolution): the three links as textured boxes (0.12 x 0.12 x L m) on bodies 0-2, a textured
     backdrop box 1 m behind the hinge plane, and a camera 3 m in front of it looking along +y
     (image right = +x, image down = -z), focal length W / 2 pixels, projection plane 0.05 m in
-    front of it. States: ``pendulum3``
+    front of it. With ``mixed`` also a sphere of radius 0.09 m at the far end of the last link and
+    a textured ground plane 1.5 m below the hinge (texture period 1 m). States: ``pendulum3``
     chains (seeded lengths and angles), positions only."""
     pm = pendulum3(B=B, seed=seed, horizon=1)
     cs = CameraScene()
@@ -296,6 +298,13 @@ def camera_scene(B=4096, W=288, H=96, seed=1005, tex_size=64):
     cs.obj_half = np.array([[8.0, 0.05, 3.0], [0.06, 0.06, L[0] / 2], [0.06, 0.06, L[1] / 2], [0.06, 0.06, L[2] / 2]])
     cs.obj_tex = np.array([0, 1, 2, 3], np.int32)
     cs.textures = procedural_textures(4, tex_size, tex_size, seed)
+    if mixed:
+        cs.obj_body = np.concatenate([cs.obj_body, [2, -1]]).astype(np.int32)
+        cs.obj_center = np.concatenate([cs.obj_center, [[0.0, 0.0, -L[2] / 2], [0.0, 0.0, -1.5]]])
+        cs.obj_half = np.concatenate([cs.obj_half, [[0.09, 0.09, 0.09], [0.5, 0.5, 1.0]]])
+        cs.obj_tex = np.array([0, 1, 2, 3, 4, 5], np.int32)
+        cs.obj_kind = np.array([0, 0, 0, 0, 1, 2], np.int32)
+        cs.textures = procedural_textures(6, tex_size, tex_size, seed)
     st = np.asarray(pm.state0, np.float32).copy()
     # every instance carries the first chain's link lengths (the boxes are shared); its own angles
     for i in range(B):

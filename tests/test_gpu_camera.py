@@ -1,6 +1,7 @@
 """Differentiable camera (section 3.4) through the C ABI against the FP64 oracle: frames of the
-camera scene (the 3-link pendulum in front of a textured backdrop), the box each pixel sees, and
-the reverse mode to the body poses and the texels; also at the full 288 x 96 size in the
+camera scene (the 3-link pendulum in front of a textured backdrop; boxes only, and mixed with a
+sphere on the last link and a textured ground plane), the object each pixel sees, and the
+reverse mode to the body poses and the texels; also at the full 288 x 96 size in the
 4096-frame launch configuration the bench times, on sampled instances."""
 import numpy as np
 import pytest
@@ -39,20 +40,24 @@ def compare(cs, states, inst, img, hit):
     return True
 
 
-def test_frames_match_oracle():
-    cs = WL.camera_scene(B=16, W=144, H=48)
+@pytest.mark.parametrize("mixed", [False, True])
+def test_frames_match_oracle(mixed):
+    cs = WL.camera_scene(B=16, W=144, H=48, mixed=mixed)
     _, _, _, img, hit = gpu_frames(cs, cs.states)
     compare(cs, cs.states, range(16), img, hit)
     assert (hit >= 1).mean() > 0.005  # the pendulum is in view
+    if mixed:
+        assert (hit == 4).mean() > 1e-4 and (hit == 5).mean() > 0.05  # the sphere and the ground
 
 
-@pytest.mark.parametrize("W,H,B", [(144, 48, 8), (288, 96, 4)])
-def test_gradients_match_oracle(W, H, B):
+@pytest.mark.parametrize("W,H,B,mixed", [(144, 48, 8, False), (288, 96, 4, False), (144, 48, 8, True),
+                                         (288, 96, 4, True)])
+def test_gradients_match_oracle(W, H, B, mixed):
     """Reverse mode of a random weighting of the frames: gradients w.r.t. the three link bodies'
     positions and rotation entries, and w.r.t. every texel, within 1e-3 (relative) of the
     oracle's, on instances whose hit sets agree everywhere; at 144 x 48 (the per-thread frame
     path) and at the full 288 x 96 (box frames staged per block)."""
-    cs = WL.camera_scene(B=B, W=W, H=H)
+    cs = WL.camera_scene(B=B, W=W, H=H, mixed=mixed)
     rig, st, tex, img, hit = gpu_frames(cs, cs.states)
     rng = np.random.default_rng(2)
     dimg = rng.normal(size=img.shape).astype(np.float32)
