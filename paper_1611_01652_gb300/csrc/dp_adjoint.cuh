@@ -56,7 +56,7 @@ __device__ void loss_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL& X,
 // XB holds the adjoint of x_{t+1}; on return its p/R fields hold the adjoint of x_t's p/R,
 // its v/w fields are zero, and VB holds the adjoint of the solver's output velocities.
 // (bmask: the bodies to process, bit b)
-__device__ void integrate_reverse(const DevTopo& T, const GC& Xt, const SL& X, const SL& XB, const SL& VB,
+__device__ inline void integrate_reverse(const DevTopo& T, const GC& Xt, const SL& X, const SL& XB, const SL& VB,
                                   uint32_t bmask = 0xffffffffu) {
   const float h = T.dt;
   for (int b = 0; b < T.nb; ++b) {

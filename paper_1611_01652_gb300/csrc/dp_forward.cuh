@@ -465,7 +465,7 @@ __device__ void pgs_solve(const DevTopo& T, const LaneT<RV>& L, const SL& X, con
 }
 
 // Semi-implicit Euler on positions with the new velocities, then the Eq. 1 renormalisation.
-__device__ void integrate(const DevTopo& T, const SL& X) {
+__device__ inline void integrate(const DevTopo& T, const SL& X) {
   const float h = T.dt;
   for (int b = 0; b < T.nb; ++b) {
     float3 p = X.v3(18 * b), v = X.v3(18 * b + 12), w = X.v3(18 * b + 15);
