@@ -6,11 +6,13 @@ of the quadruped batch: B = 4096 instances, T = 1000 steps of 10 ms, dense contr
 24->128->128->8 (bfloat16 weights, fp32 accumulation), loss = negative forward displacement,
 gradient w.r.t. every controller weight. Metric: instance-steps/s (B*T per step).
 
-Two arms: the plain cold-start solver at 20 sweeps, and the warm start accepted by the gate
-(trained network or its zero-network special case, the damped previous-impulse start) at the
-fewest sweeps that reach the plain solver's residual. The warm start is prepared (harvest,
-training, gate) before any timing. The headline value is the accepted warm start's, else the
-plain solver's; both are in the line.
+Two arms: the plain cold-start solver at 20 sweeps, and a warm start accepted by the gate
+(trained network, shrunk copies of it, or the zero network: the damped previous-impulse start)
+at the fewest sweeps that reach the plain solver's residual on held-out robots over the same
+horizon. The warm start is prepared (harvest, training, gate) before any timing. The gate's
+accepted warm starts are timed in its order; the headline value is the first whose mean residual
+on the timed workload is within RESID_TOL of the plain solver's (equal residual), else the plain
+solver's; both arms are in the line.
 
 Prints one JSON line. `--impl reference` times the FP64 CPU oracle on the host cores instead.
 """
@@ -33,6 +35,9 @@ from paper_1611_01652_gb300.replicas import max_over_ranks, replica_seed, whole_
 METRIC = "inst-steps/s fwd+adjoint, quadruped B=4096; warm-start vs plain @equal resid"
 FLOPS = os.path.join(ROOT, "tests", "golden", "flops_per_instance_step.json")
 SM_COUNT, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
+# a warm start is at equal residual when its mean residual on the timed workload is at most this
+# fraction above the plain solver's
+RESID_TOL = 0.02
 # DRAM bytes (read + written) per instance-step of k_backward_mw, damped start at 10 sweeps:
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch at B = 1024, T = 20 (293.4 MB +
 # 18.8 MB; profiles/k_backward_mw_quadruped_b1024_t20_ws10.md) / (B T). The tape is read once
@@ -210,9 +215,11 @@ def prepare_warmstart(args):
     # prediction with a large error costs the solver less); the zero network is the damped start
     nets = {"learned": net, "learned x0.5": WS.shrink(net, 0.5), "learned x0.25": WS.shrink(net, 0.25),
             "damped": zero}
-    mg = WL.quadruped(B=128, horizon=200, seed=3003)
+    # held-out robots over the timed workload's horizon (a correction's effect on the residual
+    # can grow over a long rollout)
+    mg = WL.quadruped(B=128, horizon=args.horizon, seed=3003)
     rep = WS.accept(mg, [(k, v, args.alpha) for k, v in nets.items()], plain_iters=args.iters,
-                    sweep_grid=(5, 7, 10, 14), horizon=200)
+                    sweep_grid=(5, 7, 10, 14), horizon=args.horizon)
     rep["harvest_rows"] = n
     rep["val_mse_zero_network"] = mse0
     rep["val_mse_trained"] = hist[-1][2]
@@ -598,19 +605,27 @@ def main():
              "ms_per_step": p_ms / args.steps, "fwd_ms": p_fwd, "bwd_ms": p_bwd,
              "resid": mean_residual(world, W, B), "ckpt_every": world.ckpt_every}
     head = dict(plain, name="plain", clocks=p_ck, world=world)
-    acc = rep["accepted"] if rep else None
-    ws = None
-    if acc:
-        name, n_ws, alpha = acc
-        del world, head["world"]
+    # the gate's accepted warm starts in its order (fewest sweeps, then lowest residual); the
+    # headline takes the first whose mean residual on this workload stays within RESID_TOL of
+    # the plain solver's (equal residual), else the plain solver
+    ws, tried = None, []
+    for name, n_ws, alpha in ((rep.get("accepted_all") or [rep["accepted"]]) if rep and rep["accepted"] else [])[:3]:
+        world2 = World(m, stream=stream, iters=n_ws, warmstart=True)
+        world2.set_warmstart(nets[name], alpha)
+        w_ms, w_fwd, w_bwd, w_ck = time_arm(world2, W, loss, dloss, dW, args, stream, dist)
+        arm = {"accepted": name, "iters": n_ws, "alpha": alpha,
+               "value": whole_job_rate(B * T, world_size, w_ms / args.steps), "ms_per_step": w_ms / args.steps,
+               "fwd_ms": w_fwd, "bwd_ms": w_bwd, "resid": mean_residual(world2, W, B), "ckpt_every": world2.ckpt_every}
+        arm["equal_residual"] = bool(arm["resid"] <= plain["resid"] * (1.0 + RESID_TOL))
+        tried.append({k: arm[k] for k in ("accepted", "iters", "value", "resid", "equal_residual")})
+        if arm["equal_residual"]:
+            ws, ws_ck = arm, w_ck
+            del world, head["world"]
+            world = world2
+            head = dict(ws, name="warm start (%s, %d sweeps)" % (name, n_ws), clocks=w_ck, world=world)
+            break
+        del world2
         torch.cuda.empty_cache()
-        world = World(m, stream=stream, iters=n_ws, warmstart=True)
-        world.set_warmstart(nets[name], alpha)
-        w_ms, w_fwd, w_bwd, w_ck = time_arm(world, W, loss, dloss, dW, args, stream, dist)
-        ws = {"accepted": name, "iters": n_ws, "alpha": alpha, "value": whole_job_rate(B * T, world_size, w_ms / args.steps),
-              "ms_per_step": w_ms / args.steps, "fwd_ms": w_fwd, "bwd_ms": w_bwd, "resid": mean_residual(world, W, B),
-              "ckpt_every": world.ckpt_every}
-        head = dict(ws, name="warm start (%s, %d sweeps)" % (name, n_ws), clocks=w_ck, world=world)
     world = head["world"]
     ms_per_step = head["ms_per_step"]
     value = head["value"]
@@ -650,7 +665,7 @@ def main():
         if dist:
             dist.destroy_process_group()
         return
-    head = dict(ws if ws else plain, clocks=w_ck if ws else p_ck, name=("warm start (%s, %d sweeps)" % (
+    head = dict(ws if ws else plain, clocks=ws_ck if ws else p_ck, name=("warm start (%s, %d sweeps)" % (
         ws["accepted"], ws["iters"])) if ws else "plain")
     flops = json.load(open(FLOPS))
     it = head["iters"]
@@ -683,16 +698,17 @@ def main():
                                     "harvest_rows", "val_mse_zero_network", "val_mse_trained", "prepare_s")}
         gate["candidates"] = rep["candidates"]
         gate["accepted"] = rep["accepted"]
+        gate["accepted_all"] = rep.get("accepted_all")
+        gate["timed"] = tried  # the accepted warm starts timed on the workload, with their residuals
         # does the learned network itself (not its zero special case) earn the headline?
-        acc = rep["accepted"]
         learned = [c for c in rep["candidates"] if c["name"].startswith("learned")]
-        gate["learned_accepted"] = bool(acc and acc[0].startswith("learned"))
+        gate["learned_accepted"] = bool(ws and ws["accepted"].startswith("learned"))
         gate["learned_summary"] = (
-            "a trained network (%s) is the accepted warm start" % acc[0] if gate["learned_accepted"] else
-            "no trained network reaches the plain solver's residual at fewer sweeps than the damped start "
-            "(best learned: %s); the headline arm is the damped previous-impulse start (the zero network)" % (
+            "a trained network (%s) is the headline warm start" % ws["accepted"] if gate["learned_accepted"] else
+            "no trained network is the headline warm start (best learned on the gate, residual/sweeps/name: %s; "
+            "timed candidates: %s); the headline arm is %s" % (
                 min(((c["resid"] if c["resid"] is not None else float("inf"), c["iters"], c["name"]) for c in learned),
-                    default=None),))
+                    default=None), [(t["accepted"], t["iters"], t["equal_residual"]) for t in tried], head["name"]))
     out = {
         "metric": METRIC, "value": value, "unit": "inst-steps/s", "n_gpus": world_size, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",

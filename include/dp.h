@@ -259,6 +259,17 @@ const char* dp_last_error(void);
 int32_t dp_ckpt_every(const dp_world* w);
 
 /*
+ * How the world evaluates its controller u = g(s(x) | W) (section 2.2, Eq. g), chosen at create:
+ * DP_CTRL_NONE (no controller), DP_CTRL_SIMT (in the step, one lane per instance, fp32 FMA),
+ * DP_CTRL_TENSOR (in the step on the tensor cores: bfloat16 networks K0-H-H-NO with K0 <= 32,
+ * NO <= 16, H in {64, 128, 256}; the warp's 32 instances are the rows of each product),
+ * DP_CTRL_WIDE (bfloat16 networks with a hidden layer wider than 256: batched tensor-core
+ * products between per-step launches). -1 for a NULL world.
+ */
+enum { DP_CTRL_NONE = 0, DP_CTRL_SIMT = 1, DP_CTRL_TENSOR = 2, DP_CTRL_WIDE = 3 };
+int32_t dp_controller_kind(const dp_world* w);
+
+/*
  * Learned warm start of the solver (not in the paper; its solver starts from zero impulses).
  *
  * The rows are taken in groups of three: the linear rows of each joint (x, y, z), the angular

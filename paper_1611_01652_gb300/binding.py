@@ -52,8 +52,9 @@ SYMBOLS = ("dp_create_world", "dp_free", "dp_num_params", "dp_num_slots", "dp_sc
            "dp_get_residual", "dp_ws_workspace_floats", "dp_ws_param_count", "dp_ws_loss_grad", "dp_ws_forward",
            "dp_ws_adam", "dp_set_impulses", "dp_get_impulses", "dp_set_recurrent", "dp_get_recurrent",
            "dp_set_params", "dp_render", "dp_render_backward", "dp_camera_last_error", "dp_instance_status",
-           "dp_last_error_detail", "dp_fma_peak")
+           "dp_last_error_detail", "dp_fma_peak", "dp_controller_kind")
 INST_NAN_STATE, INST_NAN_GRAD = 1, 2
+CTRL_NONE, CTRL_SIMT, CTRL_TENSOR, CTRL_WIDE = 0, 1, 2, 3
 
 
 def load(build=True):
@@ -72,6 +73,7 @@ def load(build=True):
     lib.dp_num_params.restype = C.c_int64
     lib.dp_num_slots.argtypes = [C.c_void_p]
     lib.dp_ckpt_every.argtypes = [C.c_void_p]
+    lib.dp_controller_kind.argtypes = [C.c_void_p]
     lib.dp_schedule.argtypes = [C.c_void_p] + [PI] * 7
     lib.dp_set_initial_state.argtypes = [C.c_void_p, C.c_void_p]
     lib.dp_set_state.argtypes = [C.c_void_p, C.c_void_p, C.c_int32]
@@ -211,6 +213,8 @@ class World:
         self.n_params = int(lib.dp_num_params(h))
         self.n_slots = int(lib.dp_num_slots(h))
         self.ckpt_every = int(lib.dp_ckpt_every(h))
+        # DP_CTRL_*: none, SIMT in the step, tensor cores in the step, wide batched products
+        self.controller_kind = int(lib.dp_controller_kind(h))
 
     # -- lifetime
     def free(self):

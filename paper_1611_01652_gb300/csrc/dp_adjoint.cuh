@@ -642,19 +642,24 @@ __device__ void controller_reverse(const DevTopo& T, const DevPtrs& D, const AV*
   if (T.skip) dense_bwd(D.Wn + T.w_off[L], T.widths[0], T.widths[L], del[L - 1], act[0], sbar, false, true);
 }
 
-// Controller reverse on the tensor cores (bfloat16 24-128-128-8 network). zb0 holds u_bar; the
-// output delta is already in del[2]. Hidden deltas go to del[1], del[0]; the input adjoint to sbar.
-template <class AV>
+// Controller reverse on the tensor cores (the networks of controller_forward_tc). zb0 holds u_bar;
+// the output delta is already in del[2]. Hidden deltas go to del[1], del[0]; the input adjoint to
+// sbar.
+template <class Q, class AV>
 __device__ void controller_reverse_tc(const DevTopo& T, const DevPtrs& D, const AV* act, const AV* del, const SL& zb0,
                                       const SL& sbar) {
   const __nv_bfloat16* Wc = D.Wtc;
   const AV a1 = act[1], a2 = act[2], e0 = del[0], e1 = del[1];
   __syncwarp();
-  mlp3_backward<CtrlTC::K0, CtrlTC::H1, CtrlTC::H2, CtrlTC::NO>(
-      [&](int f, int r) { return zb0.lane_at(f, r); }, Wc + CtrlTC::W3T, Wc + CtrlTC::W2T, Wc + CtrlTC::W1T,
-      [&](int l, int f, int r) { return (l == 1 ? a1 : a2).lane_at(f, r) > 0.f; },
-      [&](int l, int f, int r, float v) { (l == 1 ? e0 : e1).lane_at(f, r) = v; },
-      [&](int f, int r, float v) { sbar.lane_at(f, r) = v; });
+  ctrl_tc_dispatch<Q>(T, [&](auto HC) {
+    constexpr int H = decltype(HC)::value;
+    constexpr CtrlTCLayout Lw = ctrl_tc_layout(H, H);
+    mlp3_backward<CTRL_TC_KP0, H, H, CTRL_TC_NOP>(
+        T.widths[0], T.widths[3], [&](int f, int r) { return zb0.lane_at(f, r); }, Wc + Lw.w3t, Wc + Lw.w2t,
+        Wc + Lw.w1t, [&](int l, int f, int r) { return (l == 1 ? a1 : a2).lane_at(f, r) > 0.f; },
+        [&](int l, int f, int r, float v) { (l == 1 ? e0 : e1).lane_at(f, r) = v; },
+        [&](int f, int r, float v) { sbar.lane_at(f, r) = v; });
+  });
   __syncwarp();
 }
 

@@ -426,8 +426,10 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
   T.n_rec = T.n_layers > 0 ? d->n_recurrent : 0;
   T.ws_alpha = 0.7f;
   T.grad_decay = d->grad_decay > 0.f ? d->grad_decay : 1.f;
-  T.mlp_tc = T.n_rec == 0 && T.n_layers == 3 && !T.skip && T.ctrl_round && T.widths[0] == CtrlTC::K0 && T.widths[1] == CtrlTC::H1 &&
-             T.widths[2] == CtrlTC::H2 && T.widths[3] == CtrlTC::NO && !getenv("DP_FORCE_SIMT_CONTROLLER");
+  // bfloat16 controllers K0-H-H-NO with K0 <= 32, NO <= 16 and H in {64, 128, 256} run on the
+  // tensor cores inside the step (recurrent ones too: h is among the inputs and outputs)
+  T.mlp_tc = T.n_layers == 3 && !T.skip && T.ctrl_round && T.widths[0] <= CTRL_TC_KP0 && T.widths[3] <= CTRL_TC_NOP &&
+             T.widths[1] == T.widths[2] && ctrl_tc_width(T.widths[1]) && !getenv("DP_FORCE_SIMT_CONTROLLER");
   // wide bfloat16 controllers (hidden layers beyond 256) run as batched tensor-core products
   // between step launches; DP_FORCE_WIDE_CONTROLLER selects that path for any eligible network
   {
@@ -456,6 +458,8 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
   T.topo_id = match_compiled_topology(T, T.nb, T.nj, T.ns, T.np, d->joint_type, d->joint_body, d->joint_flags,
                                       d->sphere_body, d->pair_sphere);
   if (getenv("DP_FORCE_RUNTIME_TOPOLOGY")) T.topo_id = 0;
+  // the compiled topology's kernels carry the 128-wide tensor-core controller only
+  if (T.topo_id != 0 && T.widths[1] != 128) T.mlp_tc = 0;
   w->n_params = np_;
   w->w_total = wtot;
   w->Tf = T;
@@ -573,7 +577,8 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
     D.bias = w->Wb;
     if (T.mlp_tc) {
       void* p = nullptr;
-      if (cudaMalloc(&p, sizeof(__nv_bfloat16) * CtrlTC::SIZE) != cudaSuccess) return cleanup(DP_ENOMEM);
+      const size_t n = (size_t)ctrl_tc_layout(T.widths[1], T.widths[2]).size;
+      if (cudaMalloc(&p, sizeof(__nv_bfloat16) * n) != cudaSuccess) return cleanup(DP_ENOMEM);
       w->allocs.push_back(p);
       w->Wtc = (__nv_bfloat16*)p;
     }
@@ -681,6 +686,13 @@ void dp_free(dp_world* w) {
 int64_t dp_num_params(const dp_world* w) { return w ? w->n_params : -1; }
 int32_t dp_num_slots(const dp_world* w) { return w ? w->Tf.nslots : -1; }
 int32_t dp_ckpt_every(const dp_world* w) { return w ? w->D.ckpt_every : -1; }
+int32_t dp_controller_kind(const dp_world* w) {
+  if (!w) return -1;
+  const DevTopo& T = w->Tf;
+  if (T.n_layers == 0) return DP_CTRL_NONE;
+  if (T.ext_ctrl) return DP_CTRL_WIDE;
+  return T.mlp_tc ? DP_CTRL_TENSOR : DP_CTRL_SIMT;
+}
 
 dp_status dp_schedule(const dp_world* w, int32_t* kind, int32_t* idx, int32_t* sub, int32_t* body_a, int32_t* body_b,
                       int32_t* colour, int32_t* order) {

@@ -169,28 +169,59 @@ __device__ void controller_forward(const DevTopo& T, const DevPtrs& D, const AV*
   }
 }
 
-// Controller forward on the tensor cores (the bfloat16 24-128-128-8 network): the warp's 32
-// instances are the rows of each product. act[0] holds the features, act[3] receives u. Hidden
-// activations go to the dump column when one is given, to act[1], act[2] when those are dump
-// views (segment recompute), and nowhere otherwise.
-template <class AV>
-__device__ void controller_forward_tc(const DevTopo& T, const DevPtrs& D, const AV* act, float* dump_col) {
+// Hidden widths of the tensor-core controller a kernel is built for: the compiled quadruped
+// topology carries the 128-wide networks only; the run-time topology every supported width.
+template <class Q, class F>
+__device__ __forceinline__ void ctrl_tc_dispatch(const DevTopo& T, F&& f) {
+  if constexpr (Q::id != 0) {
+    f(std::integral_constant<int, 128>{});
+  } else {
+    if (T.widths[1] == 64) f(std::integral_constant<int, 64>{});
+    else if (T.widths[1] == 128) f(std::integral_constant<int, 128>{});
+    else f(std::integral_constant<int, 256>{});
+  }
+}
+
+// Controller forward on the tensor cores (a bfloat16 K0-H-H-NO network, K0 <= 32, NO <= 16, H in
+// {64, 128, 256}): the warp's 32 instances are the rows of each product. act[0] holds the
+// features, act[3] receives the outputs. Hidden activations go to the dump column when one is
+// given, to act[1], act[2] when those are dump views (segment recompute), and nowhere otherwise.
+template <int H, class AV>
+__device__ __forceinline__ void ctrl_tc_forward(const DevTopo& T, const DevPtrs& D, const AV* act, float* dump_col) {
   const __nv_bfloat16* Wc = D.Wtc;
   const size_t N = (size_t)T.horizon * T.Bp;
   const int lane = threadIdx.x & 31;
   float* dbase = dump_col ? dump_col - lane : nullptr;
   const int d1 = T.dump_act[1], d2 = T.dump_act[2];
   const AV a0 = act[0], a1 = act[1], a2 = act[2], a3 = act[3];
-  __syncwarp();
-  mlp3_forward<CtrlTC::K0, CtrlTC::H1, CtrlTC::H2, CtrlTC::NO>(
-      [&](int f, int r) { return a0.lane_at(f, r); }, Wc + CtrlTC::W1, D.bias + T.w_off[0], Wc + CtrlTC::W2,
-      D.bias + T.w_off[1], Wc + CtrlTC::W3, D.bias + T.w_off[2], [&](int f, int r, float v) { a3.lane_at(f, r) = v; },
+  constexpr CtrlTCLayout Lw = ctrl_tc_layout(H, H);
+  mlp3_forward<CTRL_TC_KP0, H, H, CTRL_TC_NOP>(
+      T.widths[0], T.widths[3], [&](int f, int r) { return a0.lane_at(f, r); }, Wc + Lw.w1, D.bias + T.w_off[0],
+      Wc + Lw.w2, D.bias + T.w_off[1], Wc + Lw.w3, D.bias + T.w_off[2],
+      [&](int f, int r, float v) { a3.lane_at(f, r) = v; },
       [&](int l, int f, int r, float v) {
         if (dbase)
           dbase[(size_t)((l == 1 ? d1 : d2) + f) * N + r] = v;
         else if constexpr (!std::is_same<AV, SL>::value)
           (l == 1 ? a1 : a2).lane_at(f, r) = v;
       });
+}
+// The run-time topology's kernels call each width out of line, so that the register needs of
+// the widest network do not fall on the whole persistent kernel.
+template <int H, class AV>
+__device__ __noinline__ void ctrl_tc_forward_call(const DevTopo& T, const DevPtrs& D, const AV* act, float* dump_col) {
+  ctrl_tc_forward<H, AV>(T, D, act, dump_col);
+}
+template <class Q, class AV>
+__device__ void controller_forward_tc(const DevTopo& T, const DevPtrs& D, const AV* act, float* dump_col) {
+  __syncwarp();
+  if constexpr (Q::id != 0) {
+    ctrl_tc_forward<128, AV>(T, D, act, dump_col);
+  } else {
+    if (T.widths[1] == 64) ctrl_tc_forward_call<64, AV>(T, D, act, dump_col);
+    else if (T.widths[1] == 128) ctrl_tc_forward_call<128, AV>(T, D, act, dump_col);
+    else ctrl_tc_forward_call<256, AV>(T, D, act, dump_col);
+  }
   __syncwarp();
 }
 
@@ -601,6 +632,7 @@ __device__ void warm_start(const DevTopo& T, const DevPtrs& D, const LaneT<RV>& 
       if (T.ws_net) {
         __syncwarp();
         mlp3_forward<WsTC::K0, WsTC::H1, WsTC::H2, WsTC::NO>(
+            WsTC::K0, WsTC::NO,
             [&](int f, int r) { return F.lane_at(f, r); }, D.ws_tc + WsTC::W1, D.ws_b + WsTC::B1, D.ws_tc + WsTC::W2,
             D.ws_b + WsTC::B2, D.ws_tc + WsTC::W3, D.ws_b + WsTC::B3,
             [&](int f, int r, float v) { Y.lane_at(f, r) = v; }, [](int, int, int, float) {});
@@ -717,7 +749,7 @@ __device__ float step_forward(const DevTopo& T, const DevPtrs& D, const LaneT<RV
       for (int k = 0; k < T.n_rec; ++k) act[0][base + k] = qz(T, L.S[T.sm_h + k]);
     }
     if (T.mlp_tc)
-      controller_forward_tc(T, D, act, dump_col);
+      controller_forward_tc<Q>(T, D, act, dump_col);
     else
       controller_forward(T, D, act);
     if (T.n_rec) {  // h^{t+1} = tanh of the last outputs

@@ -35,32 +35,34 @@ __global__ void k_prep_weights(const __grid_constant__ DevTopo T, const float* _
   }
 }
 
-// Tensor-core layouts of the 24-128-128-8 controller (CtrlTC), bfloat16, zero padded.
+// Tensor-core layouts of a K0-H1-H2-NO controller (ctrl_tc_layout), bfloat16, zero padded.
 __global__ void k_prep_weights_tc(const __grid_constant__ DevTopo T, const float* __restrict__ W, __nv_bfloat16* Wc) {
-  int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= CtrlTC::SIZE) return;
+  const int K0 = T.widths[0], H1 = T.widths[1], H2 = T.widths[2], NO = T.widths[3];
+  const CtrlTCLayout Lw = ctrl_tc_layout(H1, H2);
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= Lw.size) return;
   // flat master layout: per layer W[out][in] then b[out]
-  const int m1 = CtrlTC::K0 * CtrlTC::H1 + CtrlTC::H1, m2 = m1 + CtrlTC::H1 * CtrlTC::H2 + CtrlTC::H2;
+  const int m1 = K0 * H1 + H1, m2 = m1 + H1 * H2 + H2;
   auto w = [&](int l, int o, int i) { return W[(l == 0 ? 0 : l == 1 ? m1 : m2) + o * T.widths[l] + i]; };
   float v = 0.f;
-  if (p < CtrlTC::W2) {  // W1 [H1][32]
-    int o = p / 32, i = p % 32;
-    v = i < CtrlTC::K0 ? w(0, o, i) : 0.f;
-  } else if (p < CtrlTC::W3) {  // W2 [H2][H1]
-    int q = p - CtrlTC::W2, o = q / CtrlTC::H1, i = q % CtrlTC::H1;
+  if (p < Lw.w2) {  // W1 [H1][32]
+    const int o = p / CTRL_TC_KP0, i = p % CTRL_TC_KP0;
+    v = i < K0 ? w(0, o, i) : 0.f;
+  } else if (p < Lw.w3) {  // W2 [H2][H1]
+    const int q = p - Lw.w2, o = q / H1, i = q % H1;
     v = w(1, o, i);
-  } else if (p < CtrlTC::W3T) {  // W3 [8][H2]
-    int q = p - CtrlTC::W3, o = q / CtrlTC::H2, i = q % CtrlTC::H2;
-    v = o < CtrlTC::NO ? w(2, o, i) : 0.f;
-  } else if (p < CtrlTC::W2T) {  // W3^T [H2][16]
-    int q = p - CtrlTC::W3T, i = q / 16, o = q % 16;
-    v = o < CtrlTC::NO ? w(2, o, i) : 0.f;
-  } else if (p < CtrlTC::W1T) {  // W2^T [H1][H2]
-    int q = p - CtrlTC::W2T, i = q / CtrlTC::H2, o = q % CtrlTC::H2;
+  } else if (p < Lw.w3t) {  // W3 [16][H2]
+    const int q = p - Lw.w3, o = q / H2, i = q % H2;
+    v = o < NO ? w(2, o, i) : 0.f;
+  } else if (p < Lw.w2t) {  // W3^T [H2][16]
+    const int q = p - Lw.w3t, i = q / CTRL_TC_NOP, o = q % CTRL_TC_NOP;
+    v = o < NO ? w(2, o, i) : 0.f;
+  } else if (p < Lw.w1t) {  // W2^T [H1][H2]
+    const int q = p - Lw.w2t, i = q / H2, o = q % H2;
     v = w(1, o, i);
-  } else {  // W1^T [24][H1]
-    int q = p - CtrlTC::W1T, i = q / CtrlTC::H1, o = q % CtrlTC::H1;
-    v = w(0, o, i);
+  } else {  // W1^T [32][H1]
+    const int q = p - Lw.w1t, i = q / H1, o = q % H1;
+    v = i < K0 ? w(0, o, i) : 0.f;
   }
   Wc[p] = __float2bfloat16_rn(v);
 }
@@ -191,7 +193,8 @@ cudaError_t launch_prep_weights(const DevTopo& T, const float* W, float* Wt, flo
   return cudaGetLastError();
 }
 cudaError_t launch_prep_weights_tc(const DevTopo& T, const float* W, __nv_bfloat16* Wc, cudaStream_t s) {
-  k_prep_weights_tc<<<(CtrlTC::SIZE + 255) / 256, 256, 0, s>>>(T, W, Wc);
+  const int n = ctrl_tc_layout(T.widths[1], T.widths[2]).size;
+  k_prep_weights_tc<<<(n + 255) / 256, 256, 0, s>>>(T, W, Wc);
   return cudaGetLastError();
 }
 cudaError_t launch_state_in(int B, int Bp, int nf, const float* src, float* dst, cudaStream_t s) {

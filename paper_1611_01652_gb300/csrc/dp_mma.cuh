@@ -37,38 +37,44 @@ __device__ __forceinline__ void load_b(const __nv_bfloat16* __restrict__ W, int 
   b1 = __ldg(reinterpret_cast<const unsigned int*>(p + 8));
 }
 
-// A fragments of one k-tile of the input x(f, row) (rows of m-tile mt; features >= K are zero).
-template <int K, class IN>
-__device__ __forceinline__ void load_a_lanes(IN& x, int mt, int kt, uint32_t (&a)[4]) {
+// A fragments of one k-tile of the input x(f, row) (rows of m-tile mt; features >= k0 are zero).
+template <class IN>
+__device__ __forceinline__ void load_a_lanes(IN& x, int k0, int mt, int kt, uint32_t (&a)[4]) {
   const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
   const int r0 = mt * 16 + g, r1 = r0 + 8, c = kt * 16 + 2 * q;
-  auto v = [&](int f, int r) { return f < K ? x(f, r) : 0.f; };
+  auto v = [&](int f, int r) { return f < k0 ? x(f, r) : 0.f; };
   a[0] = pack_bf16(v(c, r0), v(c + 1, r0));
   a[1] = pack_bf16(v(c, r1), v(c + 1, r1));
   a[2] = pack_bf16(v(c + 8, r0), v(c + 9, r0));
   a[3] = pack_bf16(v(c + 8, r1), v(c + 9, r1));
 }
 
-// One dense layer on an m-tile: acc[NT][4] = bias + A (KT k-tiles) * W^T. W is [Np][Kp] bf16.
+// acc[NT][4] += A (KT k-tiles, the matrix's k-tiles k1 / 16 ..) * W^T for the output columns
+// n1 .. n1 + 8 NT. W is [N][Kp] bf16 (k contiguous).
 template <int KT, int NT>
-__device__ __forceinline__ void dense_mma(const uint32_t (&a)[KT][4], const __nv_bfloat16* __restrict__ W,
-                                          const float* __restrict__ bias, int nvalid, float (&acc)[NT][4]) {
-  const int q = threadIdx.x & 3;
-#pragma unroll
-  for (int nt = 0; nt < NT; ++nt) {
-    const int c = nt * 8 + 2 * q;
-    const float b0 = bias && c < nvalid ? __ldg(bias + c) : 0.f;
-    const float b1 = bias && c + 1 < nvalid ? __ldg(bias + c + 1) : 0.f;
-    acc[nt][0] = b0; acc[nt][1] = b1; acc[nt][2] = b0; acc[nt][3] = b1;
-  }
+__device__ __forceinline__ void mma_acc(const uint32_t (&a)[KT][4], const __nv_bfloat16* __restrict__ W, int Kp, int n1,
+                                        int k1, float (&acc)[NT][4]) {
 #pragma unroll
   for (int kt = 0; kt < KT; ++kt)
 #pragma unroll
     for (int nt = 0; nt < NT; ++nt) {
       uint32_t b0, b1;
-      load_b(W, KT * 16, nt * 8, kt * 16, b0, b1);
+      load_b(W, Kp, n1 + nt * 8, k1 + kt * 16, b0, b1);
       mma_bf16_16816(acc[nt], a[kt], b0, b1);
     }
+}
+
+// acc[NT][4] = bias + A * W^T for the output columns n1 .. n1 + 8 NT (columns >= nvalid get no bias).
+template <int NT>
+__device__ __forceinline__ void bias_init(const float* __restrict__ bias, int n1, int nvalid, float (&acc)[NT][4]) {
+  const int q = threadIdx.x & 3;
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt) {
+    const int c = n1 + nt * 8 + 2 * q;
+    const float b0 = bias && c < nvalid ? __ldg(bias + c) : 0.f;
+    const float b1 = bias && c + 1 < nvalid ? __ldg(bias + c + 1) : 0.f;
+    acc[nt][0] = b0; acc[nt][1] = b1; acc[nt][2] = b0; acc[nt][3] = b1;
+  }
 }
 
 // ReLU, bfloat16 rounding, and the C -> A fragment conversion for the next layer.
@@ -87,33 +93,41 @@ __device__ __forceinline__ void relu_to_a(float (&acc)[NT][4], uint32_t (&a)[NT 
   }
 }
 
-// Store C fragments (features along n) of an m-tile: dst(f, row) = acc.
+// Store C fragments (features along n, the first at column n1) of an m-tile: dst(f, row) = acc.
 template <int NT, class F>
-__device__ __forceinline__ void store_c(const float (&acc)[NT][4], int mt, int nvalid, F&& dst) {
+__device__ __forceinline__ void store_c(const float (&acc)[NT][4], int mt, int n1, int nvalid, F&& dst) {
   const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
   const int r0 = mt * 16 + g, r1 = r0 + 8;
 #pragma unroll
   for (int nt = 0; nt < NT; ++nt) {
-    const int c = nt * 8 + 2 * q;
+    const int c = n1 + nt * 8 + 2 * q;
     if (c < nvalid) { dst(c, r0, acc[nt][0]); dst(c, r1, acc[nt][2]); }
     if (c + 1 < nvalid) { dst(c + 1, r0, acc[nt][1]); dst(c + 1, r1, acc[nt][3]); }
   }
 }
 
-// bfloat16 weight layouts of the 24-128-128-8 controller for the tensor-core path: forward
-// matrices [out][in_pad16] and transposed matrices [in][out_pad16] (padding is zero).
-struct CtrlTC {
-  static constexpr int K0 = 24, H1 = 128, H2 = 128, NO = 8;
-  static constexpr int W1 = 0;                   // [H1][32]
-  static constexpr int W2 = W1 + H1 * 32;        // [H2][H1]
-  static constexpr int W3 = W2 + H2 * H1;        // [8][H2]
-  static constexpr int W3T = W3 + 8 * H2;        // [H2][16]
-  static constexpr int W2T = W3T + H2 * 16;      // [H1][H2]
-  static constexpr int W1T = W2T + H1 * H2;      // [24][H1]
-  static constexpr int SIZE = W1T + 24 * H1;
+// bfloat16 weight layouts of an in-step controller K0-H1-H2-NO on the tensor cores (K0 <= 32
+// inputs, NO <= 16 outputs, hidden widths multiples of 64): forward matrices [out][in_pad] and
+// transposed matrices [in][out_pad], padding zero. Offsets in bfloat16 elements.
+struct CtrlTCLayout {
+  int w1, w2, w3, w3t, w2t, w1t, size;
 };
+__host__ __device__ constexpr CtrlTCLayout ctrl_tc_layout(int h1, int h2) {
+  CtrlTCLayout l{};
+  l.w1 = 0;                   // [H1][32]
+  l.w2 = l.w1 + h1 * 32;      // [H2][H1]
+  l.w3 = l.w2 + h2 * h1;      // [16][H2]
+  l.w3t = l.w3 + 16 * h2;     // [H2][16]
+  l.w2t = l.w3t + h2 * 16;    // [H1][H2]
+  l.w1t = l.w2t + h1 * h2;    // [32][H1]
+  l.size = l.w1t + 32 * h1;
+  return l;
+}
+constexpr int CTRL_TC_KP0 = 32, CTRL_TC_NOP = 16;
+// Hidden widths with a compiled tensor-core controller (both layers the same width).
+__host__ __device__ constexpr bool ctrl_tc_width(int h) { return h == 64 || h == 128 || h == 256; }
 
-// The learned warm-start network 16-64-64-3: bfloat16 tensor-core layouts (as CtrlTC) and the
+// The learned warm-start network 16-64-64-3: bfloat16 tensor-core layouts (as the controller's) and the
 // fp32 bias array; the flat fp32 parameter vector is W1[64][16], b1, W2[64][64], b2, W3[3][64], b3.
 struct WsTC {
   static constexpr int K0 = 16, H1 = 64, H2 = 64, NO = 3;
@@ -130,36 +144,52 @@ struct WsTC {
                        F_B3 = F_W3 + NO * H2, PARAMS = F_B3 + NO;
 };
 
-// Three dense layers K0 -> H1 -> H2 -> NO (ReLU hidden, linear output) for the 32 rows of a
-// warp. in(f, row): the K0 inputs (bfloat16-exact fp32); weights [Np][Kp] bf16 with fp32 biases;
-// out(f, row, v) receives the NO outputs; hid(layer, f, row, v) the hidden activations.
-template <int K0, int H1, int H2, int NO, class IN, class OUT, class HID>
-__device__ void mlp3_forward(IN&& in, const __nv_bfloat16* W1, const float* b1, const __nv_bfloat16* W2,
+// Hidden layers are computed in chunks of MMA_CHUNK output columns, so that a layer's
+// accumulators never hold more than one chunk (a 256-wide layer fits the register file).
+#define MMA_CHUNK 64
+
+// Three dense layers k0 -> H1 -> H2 -> no (ReLU hidden, linear output) for the 32 rows of a
+// warp, k0 <= KP0 inputs and no <= NOP outputs. in(f, row): the inputs (bfloat16-exact fp32);
+// weights [N][Kp] bf16 with fp32 biases; out(f, row, v) receives the outputs; hid(layer, f,
+// row, v) the hidden activations. Layer 2's chunks feed layer 3's accumulators directly. Every
+// output's sum runs over k in increasing order, whatever the chunking.
+template <int KP0, int H1, int H2, int NOP, class IN, class OUT, class HID>
+__device__ void mlp3_forward(int k0, int no, IN&& in, const __nv_bfloat16* W1, const float* b1, const __nv_bfloat16* W2,
                              const float* b2, const __nv_bfloat16* W3, const float* b3, OUT&& out, HID&& hid) {
-  constexpr int KT0 = pad16<K0>() / 16, NT1 = H1 / 8, NT2 = H2 / 8, NT3 = pad8<NO>() / 8;
-  static_assert(H1 % 16 == 0 && H2 % 16 == 0, "hidden widths must be multiples of 16");
+  constexpr int KT0 = pad16<KP0>() / 16, NT3 = pad8<NOP>() / 8, C = MMA_CHUNK, NTC = C / 8;
+  static_assert(H1 % C == 0 && H2 % C == 0, "hidden widths must be multiples of the chunk");
 #pragma unroll 1
   for (int mt = 0; mt < 2; ++mt) {
     uint32_t a0[KT0][4];
 #pragma unroll
-    for (int kt = 0; kt < KT0; ++kt) load_a_lanes<K0>(in, mt, kt, a0[kt]);
-    uint32_t a1[NT1 / 2][4];
-    {
-      float acc[NT1][4];
-      dense_mma<KT0, NT1>(a0, W1, b1, H1, acc);
-      relu_to_a<NT1>(acc, a1);
-      store_c<NT1>(acc, mt, H1, [&](int f, int r, float v) { hid(1, f, r, v); });
+    for (int kt = 0; kt < KT0; ++kt) load_a_lanes(in, k0, mt, kt, a0[kt]);
+    uint32_t a1[H1 / 16][4];
+#pragma unroll
+    for (int c = 0; c < H1 / C; ++c) {
+      float acc[NTC][4];
+      bias_init<NTC>(b1, c * C, H1, acc);
+      mma_acc<KT0, NTC>(a0, W1, KT0 * 16, c * C, 0, acc);
+      uint32_t t[NTC / 2][4];
+      relu_to_a<NTC>(acc, t);
+      store_c<NTC>(acc, mt, c * C, H1, [&](int f, int r, float v) { hid(1, f, r, v); });
+#pragma unroll
+      for (int kt = 0; kt < NTC / 2; ++kt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) a1[c * (NTC / 2) + kt][e] = t[kt][e];
     }
-    uint32_t a2[NT2 / 2][4];
-    {
-      float acc[NT2][4];
-      dense_mma<NT1 / 2, NT2>(a1, W2, b2, H2, acc);
-      relu_to_a<NT2>(acc, a2);
-      store_c<NT2>(acc, mt, H2, [&](int f, int r, float v) { hid(2, f, r, v); });
+    float acc3[NT3][4];
+    bias_init<NT3>(b3, 0, no, acc3);
+#pragma unroll
+    for (int c = 0; c < H2 / C; ++c) {
+      float acc[NTC][4];
+      bias_init<NTC>(b2, c * C, H2, acc);
+      mma_acc<H1 / 16, NTC>(a1, W2, H1, c * C, 0, acc);
+      uint32_t a2[NTC / 2][4];
+      relu_to_a<NTC>(acc, a2);
+      store_c<NTC>(acc, mt, c * C, H2, [&](int f, int r, float v) { hid(2, f, r, v); });
+      mma_acc<NTC / 2, NT3>(a2, W3, H2, 0, c * C, acc3);
     }
-    float acc[NT3][4];
-    dense_mma<NT2 / 2, NT3>(a2, W3, b3, NO, acc);
-    store_c<NT3>(acc, mt, NO, out);
+    store_c<NT3>(acc3, mt, 0, no, out);
   }
 }
 
@@ -184,33 +214,56 @@ __device__ __forceinline__ void split_to_a(const float (&d)[NT][4], uint32_t (&h
   }
 }
 
-// acc[NT][4] += (hi + lo) * W'^T with W' stored [Np][Kp] bf16 (here the transposed weights).
+// acc[NT][4] += (hi + lo) * W'^T for the output columns n1 .. n1 + 8 NT, the k-tiles from k1;
+// W' stored [N][Kp] bf16 (here the transposed weights).
 template <int KT, int NT>
-__device__ __forceinline__ void dense_mma_split(const uint32_t (&hi)[KT][4], const uint32_t (&lo)[KT][4],
-                                                const __nv_bfloat16* __restrict__ W, float (&acc)[NT][4]) {
-#pragma unroll
-  for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-    for (int k = 0; k < 4; ++k) acc[nt][k] = 0.f;
+__device__ __forceinline__ void mma_acc_split(const uint32_t (&hi)[KT][4], const uint32_t (&lo)[KT][4],
+                                              const __nv_bfloat16* __restrict__ W, int Kp, int n1, int k1,
+                                              float (&acc)[NT][4]) {
 #pragma unroll
   for (int kt = 0; kt < KT; ++kt)
 #pragma unroll
     for (int nt = 0; nt < NT; ++nt) {
       uint32_t b0, b1;
-      load_b(W, KT * 16, nt * 8, kt * 16, b0, b1);
+      load_b(W, Kp, n1 + nt * 8, k1 + kt * 16, b0, b1);
       mma_bf16_16816(acc[nt], hi[kt], b0, b1);
       mma_bf16_16816(acc[nt], lo[kt], b0, b1);
     }
 }
+template <int NT>
+__device__ __forceinline__ void zero_acc(float (&acc)[NT][4]) {
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[nt][k] = 0.f;
+}
+// Zeroes the fragment entries of hidden layer l whose unit was not positive (ReLU adjoint).
+template <int NT, class MASK>
+__device__ __forceinline__ void relu_mask(float (&d)[NT][4], MASK& mask, int l, int mt, int n1) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+  const int r0 = mt * 16 + g, r1 = r0 + 8;
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt) {
+    const int c = n1 + nt * 8 + 2 * q;
+    if (!mask(l, c, r0)) d[nt][0] = 0.f;
+    if (!mask(l, c + 1, r0)) d[nt][1] = 0.f;
+    if (!mask(l, c, r1)) d[nt][2] = 0.f;
+    if (!mask(l, c + 1, r1)) d[nt][3] = 0.f;
+  }
+}
 
-// Reverse mode of mlp3_forward for the 32 rows of a warp. ubar(f, row): the output adjoint. mask(layer, f, row) tells whether hidden unit f of that layer was positive.
-// del(layer, f, row, v) receives the adjoint of each layer's pre-activation output (layer 3 =
-// output, 2, 1 hidden); sbar(f, row, v) the input adjoint. Transposed weights W't are [Kin_p][Kout_p].
-template <int K0, int H1, int H2, int NO, class UBAR, class MASK, class DEL, class SBAR>
-__device__ void mlp3_backward(UBAR&& ubar, const __nv_bfloat16* W3t, const __nv_bfloat16* W2t,
+// Reverse mode of mlp3_forward for the 32 rows of a warp. ubar(f, row): the output adjoint
+// (no <= NOP outputs); mask(layer, f, row): whether hidden unit f of that layer was positive;
+// del(layer, f, row, v) receives the adjoint of each hidden layer's pre-activation (2, 1);
+// sbar(f, row, v) the adjoint of the k0 inputs. Transposed weights W't are [Kin_p][Kout_p]. The
+// first layer's deltas are formed one chunk at a time, each from every chunk of the second
+// layer's deltas (recomputed per chunk: their product has only NOP terms), so that no layer's
+// deltas are held whole; every sum still runs over k in increasing order.
+template <int KP0, int H1, int H2, int NOP, class UBAR, class MASK, class DEL, class SBAR>
+__device__ void mlp3_backward(int k0, int no, UBAR&& ubar, const __nv_bfloat16* W3t, const __nv_bfloat16* W2t,
                               const __nv_bfloat16* W1t, MASK&& mask, DEL&& del, SBAR&& sbar) {
-  constexpr int NT2 = H2 / 8, NT1 = H1 / 8, NT0 = pad8<K0>() / 8;
-  constexpr int KT3 = pad16<NO>() / 16;
+  constexpr int NT0 = pad8<KP0>() / 8, KT3 = pad16<NOP>() / 16, C = MMA_CHUNK, NTC = C / 8;
+  static_assert(H1 % C == 0 && H2 % C == 0, "hidden widths must be multiples of the chunk");
   const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
 #pragma unroll 1
   for (int mt = 0; mt < 2; ++mt) {
@@ -221,45 +274,36 @@ __device__ void mlp3_backward(UBAR&& ubar, const __nv_bfloat16* W3t, const __nv_
 #pragma unroll
       for (int nt = 0; nt < 2 * KT3; ++nt) {
         const int c = nt * 8 + 2 * q, r0 = mt * 16 + g, r1 = r0 + 8;
-        d3[nt][0] = c < NO ? ubar(c, r0) : 0.f;
-        d3[nt][1] = c + 1 < NO ? ubar(c + 1, r0) : 0.f;
-        d3[nt][2] = c < NO ? ubar(c, r1) : 0.f;
-        d3[nt][3] = c + 1 < NO ? ubar(c + 1, r1) : 0.f;
+        d3[nt][0] = c < no ? ubar(c, r0) : 0.f;
+        d3[nt][1] = c + 1 < no ? ubar(c + 1, r0) : 0.f;
+        d3[nt][2] = c < no ? ubar(c, r1) : 0.f;
+        d3[nt][3] = c + 1 < no ? ubar(c + 1, r1) : 0.f;
       }
       split_to_a<2 * KT3>(d3, h3, l3);
     }
-    uint32_t h2[NT2 / 2][4], l2[NT2 / 2][4];
-    {
-      float d2[NT2][4];
-      dense_mma_split<KT3, NT2>(h3, l3, W3t, d2);
-#pragma unroll
-      for (int nt = 0; nt < NT2; ++nt) {
-        const int c = nt * 8 + 2 * q, r0 = mt * 16 + g, r1 = r0 + 8;
-        if (!mask(2, c, r0)) d2[nt][0] = 0.f;
-        if (!mask(2, c + 1, r0)) d2[nt][1] = 0.f;
-        if (!mask(2, c, r1)) d2[nt][2] = 0.f;
-        if (!mask(2, c + 1, r1)) d2[nt][3] = 0.f;
-      }
-      store_c<NT2>(d2, mt, H2, [&](int f, int r, float v) { del(2, f, r, v); });
-      split_to_a<NT2>(d2, h2, l2);
-    }
-    uint32_t h1[NT1 / 2][4], l1[NT1 / 2][4];
-    {
-      float d1[NT1][4];
-      dense_mma_split<NT2 / 2, NT1>(h2, l2, W2t, d1);
-#pragma unroll
-      for (int nt = 0; nt < NT1; ++nt) {
-        const int c = nt * 8 + 2 * q, r0 = mt * 16 + g, r1 = r0 + 8;
-        if (!mask(1, c, r0)) d1[nt][0] = 0.f;
-        if (!mask(1, c + 1, r0)) d1[nt][1] = 0.f;
-        if (!mask(1, c, r1)) d1[nt][2] = 0.f;
-        if (!mask(1, c + 1, r1)) d1[nt][3] = 0.f;
-      }
-      store_c<NT1>(d1, mt, H1, [&](int f, int r, float v) { del(1, f, r, v); });
-      split_to_a<NT1>(d1, h1, l1);
-    }
     float s[NT0][4];
-    dense_mma_split<NT1 / 2, NT0>(h1, l1, W1t, s);
-    store_c<NT0>(s, mt, K0, sbar);
+    zero_acc<NT0>(s);
+#pragma unroll 1
+    for (int c1 = 0; c1 < H1 / C; ++c1) {
+      float d1[NTC][4];
+      zero_acc<NTC>(d1);
+#pragma unroll 1
+      for (int c2 = 0; c2 < H2 / C; ++c2) {
+        float d2[NTC][4];
+        zero_acc<NTC>(d2);
+        mma_acc_split<KT3, NTC>(h3, l3, W3t, KT3 * 16, c2 * C, 0, d2);
+        relu_mask<NTC>(d2, mask, 2, mt, c2 * C);
+        if (c1 == 0) store_c<NTC>(d2, mt, c2 * C, H2, [&](int f, int r, float v) { del(2, f, r, v); });
+        uint32_t h2[NTC / 2][4], l2[NTC / 2][4];
+        split_to_a<NTC>(d2, h2, l2);
+        mma_acc_split<NTC / 2, NTC>(h2, l2, W2t, H2, c1 * C, c2 * C, d1);
+      }
+      relu_mask<NTC>(d1, mask, 1, mt, c1 * C);
+      store_c<NTC>(d1, mt, c1 * C, H1, [&](int f, int r, float v) { del(1, f, r, v); });
+      uint32_t h1[NTC / 2][4], l1[NTC / 2][4];
+      split_to_a<NTC>(d1, h1, l1);
+      mma_acc_split<NTC / 2, NT0>(h1, l1, W1t, H1, 0, c1 * C, s);
+    }
+    store_c<NT0>(s, mt, 0, k0, sbar);
   }
 }

@@ -181,7 +181,7 @@ __device__ void reverse_step_head(const DevTopo& T, const DevPtrs& D, const BwdC
 
 // Servo-target, controller, feature and hinge-kinematics reverse of step t (after the
 // external impulses' reverse), down to the adjoint of x_t.
-template <class RV>
+template <class Q, class RV>
 __device__ void reverse_step_ctrl(const DevTopo& T, const DevPtrs& D, const BwdCtx& C, const RevStep<RV>& V) {
   const int i = C.i;
   const GW* act = V.act;
@@ -204,7 +204,7 @@ __device__ void reverse_step_ctrl(const DevTopo& T, const DevPtrs& D, const BwdC
       }
     }
     if (T.mlp_tc)
-      controller_reverse_tc(T, D, act, del, V.zb0, C.sbar);
+      controller_reverse_tc<Q>(T, D, act, del, V.zb0, C.sbar);
     else
       controller_reverse(T, D, act, del, V.zb0, V.zb1, C.sbar);
     features_reverse(T, V.Bl, C.XB, C.sbar);
@@ -225,7 +225,7 @@ __device__ void reverse_step_tail(const DevTopo& T, const DevPtrs& D, const BwdC
   if (T.ws) ws_apply_reverse(T, V.L, C.VB, C.RC, V.tp);
   rows_reverse(T, V.Bl, C.XB, C.VB, C.RC);
   external_reverse(T, V.Bl, C.XB, C.VB);
-  reverse_step_ctrl(T, D, C, V);
+  reverse_step_ctrl<Q>(T, D, C, V);
 }
 
 // Reverse of step t from its tape slot ts, with x_t and x_{t+1} in global memory. RV is the
@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(128, 1) k_backward_mw(const __grid_constant__ 
     mw_barrier();
     external_reverse(T, V.Bl, C.XB, C.VB, bm);
     mw_barrier();
-    if (warp == 0) reverse_step_ctrl(T, D, C, V);
+    if (warp == 0) reverse_step_ctrl<Q>(T, D, C, V);
     mw_barrier();
   }
   if (warp != 0) return;

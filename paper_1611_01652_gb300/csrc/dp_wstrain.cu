@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(32 * WS_WARPS) k_ws_infer(const __nv_bfloat16*
   const long long base = ((long long)blockIdx.x * WS_WARPS + (threadIdx.x >> 5)) * 32;
   if (base >= n) return;  // whole warp leaves together
   mlp3_forward<WsTC::K0, WsTC::H1, WsTC::H2, WsTC::NO>(
+      WsTC::K0, WsTC::NO,
       [&](int f, int r) { return base + r < n ? x[(base + r) * stride + f] : 0.f; }, tc + WsTC::W1, bias + WsTC::B1,
       tc + WsTC::W2, bias + WsTC::B2, tc + WsTC::W3, bias + WsTC::B3,
       [&](int f, int r, float v) {
@@ -94,6 +95,7 @@ __global__ void __launch_bounds__(32 * WS_WARPS) k_ws_fwdbwd(const __nv_bfloat16
   for (int f = 0; f < WsTC::K0; ++f) act[(size_t)f * np + me] = valid ? bf16r(rows[me * WS_ROW + f]) : 0.f;
   auto col = [&](int r) { return base + r; };
   mlp3_forward<WsTC::K0, WsTC::H1, WsTC::H2, WsTC::NO>(
+      WsTC::K0, WsTC::NO,
       [&](int f, int r) { return col(r) < n ? rows[col(r) * WS_ROW + f] : 0.f; }, tc + WsTC::W1, bias + WsTC::B1,
       tc + WsTC::W2, bias + WsTC::B2, tc + WsTC::W3, bias + WsTC::B3,
       [&](int f, int r, float v) { ys[warp][f][r] = v; },
@@ -114,6 +116,7 @@ __global__ void __launch_bounds__(32 * WS_WARPS) k_ws_fwdbwd(const __nv_bfloat16
   if (lane == 0) loss_part[wid] = e;
   __syncwarp();
   mlp3_backward<WsTC::K0, WsTC::H1, WsTC::H2, WsTC::NO>(
+      WsTC::K0, WsTC::NO,
       [&](int f, int r) { return ubs[warp][f][r]; }, tc + WsTC::W3T, tc + WsTC::W2T, tc + WsTC::W1T,
       [&](int l, int f, int r) {
         return act[(size_t)((l == 1 ? WsTC::K0 : WsTC::K0 + WsTC::H1) + f) * np + col(r)] > 0.f;

@@ -214,7 +214,8 @@ def accept(model, candidates, plain_iters=20, sweep_grid=(5, 7, 10, 14), horizon
     times; relative, scale floor 1) at most ``state_tol`` above the plain solver's, and (3) make
     a 10-step controller-gradient error (relative norm) at most ``grad_tol`` above the plain
     solver's. Returns a report dict; ``report["accepted"]`` is the accepted (name, N, alpha) with
-    the fewest sweeps, or None (the plain solver is then used)."""
+    the fewest sweeps (ties: the lower residual), or None (the plain solver is then used);
+    ``report["accepted_all"]`` lists every accepted (name, N, alpha) in that order."""
     import torch
 
     from .binding import World
@@ -253,7 +254,6 @@ def accept(model, candidates, plain_iters=20, sweep_grid=(5, 7, 10, 14), horizon
 
     rep["plain_state_err"] = state_err(plain_iters, None, 0.0)
     rep["plain_grad_err"] = grad_err(plain_iters, None, 0.0)
-    best = None
     for name, net, alpha in candidates:
         for N in sorted(sweep_grid):
             if N >= plain_iters:
@@ -269,8 +269,8 @@ def accept(model, candidates, plain_iters=20, sweep_grid=(5, 7, 10, 14), horizon
             entry["accepted"] = bool(entry["state_err"] <= rep["plain_state_err"] + state_tol and
                                      entry["grad_err"] <= rep["plain_grad_err"] + grad_tol)
             rep["candidates"].append(entry)
-            if entry["accepted"] and (best is None or N < best[1]):
-                best = (name, N, alpha)
             break  # the smallest sweep count at which this candidate reaches the plain residual
-    rep["accepted"] = best
+    ok = sorted((c for c in rep["candidates"] if c["accepted"]), key=lambda c: (c["iters"], c["resid"]))
+    rep["accepted_all"] = [(c["name"], c["iters"], c["alpha"]) for c in ok]
+    rep["accepted"] = rep["accepted_all"][0] if ok else None
     return rep
