@@ -256,14 +256,16 @@ __device__ __forceinline__ void relu_mask(float (&d)[NT][4], MASK& mask, int l, 
 // (no <= NOP outputs); mask(layer, f, row): whether hidden unit f of that layer was positive;
 // del(layer, f, row, v) receives the adjoint of each hidden layer's pre-activation (2, 1);
 // sbar(f, row, v) the adjoint of the k0 inputs. Transposed weights W't are [Kin_p][Kout_p]. The
-// first layer's deltas are formed one chunk at a time, each from every chunk of the second
-// layer's deltas (recomputed per chunk: their product has only NOP terms), so that no layer's
-// deltas are held whole; every sum still runs over k in increasing order.
+// first layer's deltas are formed C1 = min(H1, 128) columns at a time, each from every
+// MMA_CHUNK-column chunk of the second layer's deltas (recomputed when H1 > 128: their product
+// has only NOP terms), so that a 256-wide network's deltas are never held whole; every sum still
+// runs over k in increasing order.
 template <int KP0, int H1, int H2, int NOP, class UBAR, class MASK, class DEL, class SBAR>
 __device__ void mlp3_backward(int k0, int no, UBAR&& ubar, const __nv_bfloat16* W3t, const __nv_bfloat16* W2t,
                               const __nv_bfloat16* W1t, MASK&& mask, DEL&& del, SBAR&& sbar) {
   constexpr int NT0 = pad8<KP0>() / 8, KT3 = pad16<NOP>() / 16, C = MMA_CHUNK, NTC = C / 8;
-  static_assert(H1 % C == 0 && H2 % C == 0, "hidden widths must be multiples of the chunk");
+  constexpr int C1 = H1 < 128 ? H1 : 128, NT1 = C1 / 8;
+  static_assert(H1 % C1 == 0 && H2 % C == 0 && C1 % 16 == 0, "hidden widths must be multiples of the chunks");
   const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
 #pragma unroll 1
   for (int mt = 0; mt < 2; ++mt) {
@@ -284,9 +286,9 @@ __device__ void mlp3_backward(int k0, int no, UBAR&& ubar, const __nv_bfloat16* 
     float s[NT0][4];
     zero_acc<NT0>(s);
 #pragma unroll 1
-    for (int c1 = 0; c1 < H1 / C; ++c1) {
-      float d1[NTC][4];
-      zero_acc<NTC>(d1);
+    for (int c1 = 0; c1 < H1 / C1; ++c1) {
+      float d1[NT1][4];
+      zero_acc<NT1>(d1);
 #pragma unroll 1
       for (int c2 = 0; c2 < H2 / C; ++c2) {
         float d2[NTC][4];
@@ -296,13 +298,13 @@ __device__ void mlp3_backward(int k0, int no, UBAR&& ubar, const __nv_bfloat16* 
         if (c1 == 0) store_c<NTC>(d2, mt, c2 * C, H2, [&](int f, int r, float v) { del(2, f, r, v); });
         uint32_t h2[NTC / 2][4], l2[NTC / 2][4];
         split_to_a<NTC>(d2, h2, l2);
-        mma_acc_split<NTC / 2, NTC>(h2, l2, W2t, H2, c1 * C, c2 * C, d1);
+        mma_acc_split<NTC / 2, NT1>(h2, l2, W2t, H2, c1 * C1, c2 * C, d1);
       }
-      relu_mask<NTC>(d1, mask, 1, mt, c1 * C);
-      store_c<NTC>(d1, mt, c1 * C, H1, [&](int f, int r, float v) { del(1, f, r, v); });
-      uint32_t h1[NTC / 2][4], l1[NTC / 2][4];
-      split_to_a<NTC>(d1, h1, l1);
-      mma_acc_split<NTC / 2, NT0>(h1, l1, W1t, H1, 0, c1 * C, s);
+      relu_mask<NT1>(d1, mask, 1, mt, c1 * C1);
+      store_c<NT1>(d1, mt, c1 * C1, H1, [&](int f, int r, float v) { del(1, f, r, v); });
+      uint32_t h1[NT1 / 2][4], l1[NT1 / 2][4];
+      split_to_a<NT1>(d1, h1, l1);
+      mma_acc_split<NT1 / 2, NT0>(h1, l1, W1t, H1, 0, c1 * C1, s);
     }
     store_c<NT0>(s, mt, 0, k0, sbar);
   }
