@@ -187,7 +187,8 @@ __device__ __forceinline__ void ctrl_tc_dispatch(const DevTopo& T, F&& f) {
 // features, act[3] receives the outputs. Hidden activations go to the dump column when one is
 // given, to act[1], act[2] when those are dump views (segment recompute), and nowhere otherwise.
 template <int H, class AV>
-__device__ __forceinline__ void ctrl_tc_forward(const DevTopo& T, const DevPtrs& D, const AV* act, float* dump_col) {
+__device__ __forceinline__ void ctrl_tc_forward(const DevTopo& T, const DevPtrs& D, const AV* act, float* dump_col,
+                                                int mt0 = 0, int mt1 = 2) {
   const __nv_bfloat16* Wc = D.Wtc;
   const size_t N = (size_t)T.horizon * T.Bp;
   const int lane = threadIdx.x & 31;
@@ -204,7 +205,8 @@ __device__ __forceinline__ void ctrl_tc_forward(const DevTopo& T, const DevPtrs&
           dbase[(size_t)((l == 1 ? d1 : d2) + f) * N + r] = v;
         else if constexpr (!std::is_same<AV, SL>::value)
           (l == 1 ? a1 : a2).lane_at(f, r) = v;
-      });
+      },
+      mt0, mt1);
 }
 // The run-time topology's kernels call each width out of line, so that the register needs of
 // the widest network do not fall on the whole persistent kernel.
@@ -241,13 +243,15 @@ __device__ void servo_targets(const DevTopo& T, const LaneT<RV>& L, const AV& u,
   }
 }
 
-// Gravity and the explicit gyroscopic term; world inverse inertia and inverse mass.
+// Gravity and the explicit gyroscopic term; world inverse inertia and inverse mass (bmask: the
+// bodies to process, bit b).
 template <class RV>
-__device__ void external_impulses(const DevTopo& T, const LaneT<RV>& L, const SL& X) {
+__device__ void external_impulses(const DevTopo& T, const LaneT<RV>& L, const SL& X, uint32_t bmask = 0xffffffffu) {
   const SL& S = L.S;
   const float h = T.dt;
   const float3 g = f3(T.gravity[0], T.gravity[1], T.gravity[2]);
   for (int b = 0; b < T.nb; ++b) {
+    if (!((bmask >> b) & 1u)) continue;
     M3 R = loadR(X, 18 * b);
     float3 I = L.P.v3(T.o_inertia + 3 * b);
     float m = L.P[T.o_mass + b];
@@ -292,15 +296,17 @@ struct RowGeo {
   bool active;
 };
 
-// Assemble every constraint slot of this instance into rows (slot order).
+// Assemble constraint slots s0, s0 + sstep, ... of this instance into rows (every slot by
+// default; each slot's row depends on the state alone, so the slots may be split over warps).
 template <class RV>
-__device__ void assemble_rows(const DevTopo& T, const LaneT<RV>& L, const SL& X, uint8_t* active_out) {
+__device__ void assemble_rows(const DevTopo& T, const LaneT<RV>& L, const SL& X, uint8_t* active_out, int s0 = 0,
+                              int sstep = 1) {
   const SL& S = L.S;
   const float h = T.dt;
   const float bh = T.beta / h;
   const float INF = __int_as_float(0x7f800000);
   const float3 ez = f3(0.f, 0.f, 1.f);
-  for (int s = 0; s < T.nslots; ++s) {
+  for (int s = s0; s < T.nslots; s += sstep) {
     const int kind = T.skind[s], idx = T.sidx[s], sub = T.ssub[s], a = T.sa[s], b = T.sb[s];
     float3 lin = f3(0.f, 0.f, 0.f), angA = lin, angB = lin;
     float bias = 0.f, bnd = 0.f;
@@ -496,9 +502,10 @@ __device__ void pgs_solve(const DevTopo& T, const LaneT<RV>& L, const SL& X, con
 }
 
 // Semi-implicit Euler on positions with the new velocities, then the Eq. 1 renormalisation.
-__device__ inline void integrate(const DevTopo& T, const SL& X) {
+__device__ inline void integrate(const DevTopo& T, const SL& X, uint32_t bmask = 0xffffffffu) {
   const float h = T.dt;
   for (int b = 0; b < T.nb; ++b) {
+    if (!((bmask >> b) & 1u)) continue;
     float3 p = X.v3(18 * b), v = X.v3(18 * b + 12), w = X.v3(18 * b + 15);
     M3 R = loadR(X, 18 * b), A;
 #pragma unroll
@@ -534,15 +541,49 @@ __device__ __forceinline__ float row_jv(const DevTopo& T, const RV& R, const SL&
 
 // Applies impulse dl of row R (slot bodies a, b) to the velocities in X.
 template <class RV>
-__device__ __forceinline__ void row_apply(const DevTopo& T, const SL& S, const RV& R, const SL& X, int a, int b, float dl) {
+__device__ __forceinline__ void row_apply(const DevTopo& T, const SL& S, const RV& R, const SL& X, int a, int b, float dl,
+                                          uint32_t bmask = 0xffffffffu) {
   const float3 lin = R.v3(RF_LIN);
-  if (a >= 0) {
+  if (a >= 0 && ((bmask >> a) & 1u)) {
     X.s3(18 * a + 12, X.v3(18 * a + 12) + (dl * S[T.sm_invm + a]) * lin);
     X.s3(18 * a + 15, X.v3(18 * a + 15) + dl * R.v3(RF_IA));
   }
-  if (b >= 0) {
+  if (b >= 0 && ((bmask >> b) & 1u)) {
     X.s3(18 * b + 12, X.v3(18 * b + 12) - (dl * S[T.sm_invm + b]) * lin);
     X.s3(18 * b + 15, X.v3(18 * b + 15) + dl * R.v3(RF_IB));
+  }
+}
+
+// Projection of row group g's start z onto its rows' bounds, into S[sm_lam]: normal >= 0,
+// |friction| <= mu lambda0_n, |motor| <= tau_max h, inactive rows 0.
+template <class RV>
+__device__ __forceinline__ void ws_project(const DevTopo& T, const LaneT<RV>& L, int g, const float (&z)[3]) {
+  const SL& S = L.S;
+  const int type = T.wsg_type[g];
+  const int s0 = T.wsg_slot[g][0], s1 = T.wsg_slot[g][1], s2 = T.wsg_slot[g][2];
+  const bool active = L.rows[s0 * RF_N + RF_MEFF] != 0.f;
+  if (type == WSG_GROUND || type == WSG_PAIR) {
+    float l0[3] = {0.f, 0.f, 0.f};
+    if (active) {
+      l0[0] = fmaxf(z[0], 0.f);
+      const float hi = L.rows[s1 * RF_N + RF_BND] * l0[0];
+      l0[1] = fminf(fmaxf(z[1], -hi), hi);
+      l0[2] = fminf(fmaxf(z[2], -hi), hi);
+    }
+    S[T.sm_lam + s0] = l0[0];
+    S[T.sm_lam + s1] = l0[1];
+    S[T.sm_lam + s2] = l0[2];
+  } else {
+    for (int k = 0; k < 3; ++k) {
+      const int s = T.wsg_slot[g][k];
+      if (s < 0) continue;
+      float y = L.rows[s * RF_N + RF_MEFF] != 0.f ? z[k] : 0.f;
+      if (T.skind[s] == RK_MOTOR) {
+        const float hi = L.rows[s * RF_N + RF_BND];
+        y = fminf(fmaxf(y, -hi), hi);
+      }
+      S[T.sm_lam + s] = y;
+    }
   }
 }
 
@@ -641,29 +682,7 @@ __device__ void warm_start(const DevTopo& T, const DevPtrs& D, const LaneT<RV>& 
       } else {
         for (int k = 0; k < 3; ++k) z[k] = T.ws_alpha * lp[k];
       }
-      if (contact) {
-        float l0[3] = {0.f, 0.f, 0.f};
-        if (active) {
-          l0[0] = fmaxf(z[0], 0.f);
-          const float hi = L.rows[s1 * RF_N + RF_BND] * l0[0];
-          l0[1] = fminf(fmaxf(z[1], -hi), hi);
-          l0[2] = fminf(fmaxf(z[2], -hi), hi);
-        }
-        S[T.sm_lam + s0] = l0[0];
-        S[T.sm_lam + s1] = l0[1];
-        S[T.sm_lam + s2] = l0[2];
-      } else {
-        for (int k = 0; k < 3; ++k) {
-          const int s = T.wsg_slot[g][k];
-          if (s < 0) continue;
-          float y = L.rows[s * RF_N + RF_MEFF] != 0.f ? z[k] : 0.f;
-          if (T.skind[s] == RK_MOTOR) {
-            const float hi = L.rows[s * RF_N + RF_BND];
-            y = fminf(fmaxf(y, -hi), hi);
-          }
-          S[T.sm_lam + s] = y;
-        }
-      }
+      ws_project(T, L, g, z);
       __syncwarp();
     }
   }

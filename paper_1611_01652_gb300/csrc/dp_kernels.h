@@ -1,5 +1,5 @@
-// Host-side launchers of the kernels in dp_kernels.cu, dp_fwd.cu, dp_bwd.cu, dp_bwd_mw.cu and
-// dp_bwd_ext.cu (internal to libdphys).
+// Host-side launchers of the kernels in dp_kernels.cu, dp_fwd.cu, dp_fwd_mw.cu, dp_bwd.cu,
+// dp_bwd_mw.cu and dp_bwd_ext.cu (internal to libdphys).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -16,6 +16,8 @@ cudaError_t launch_param_in(int B, int Bp, int o, int n, const float* src, float
 cudaError_t launch_pad_scalar(int B, int Bp, const float* src, float* dst, cudaStream_t s);
 cudaError_t launch_forward(const DevTopo& T, const DevPtrs& D, const float* x0, int t0, int nsteps, int rollout,
                            int record, cudaStream_t s);
+cudaError_t launch_forward_mw_quadruped(const DevTopo& T, const DevPtrs& D, const float* x0, int t0, int nsteps,
+                                        int rollout, cudaStream_t s);
 cudaError_t launch_backward(const DevTopo& T, const DevPtrs& D, cudaStream_t s);
 cudaError_t launch_backward_mw_quadruped(const DevTopo& T, const DevPtrs& D, cudaStream_t s);
 cudaError_t launch_backward_ext(const DevTopo& T, const DevPtrs& D, int t, cudaStream_t s);

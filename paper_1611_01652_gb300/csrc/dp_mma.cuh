@@ -152,14 +152,16 @@ struct WsTC {
 // warp, k0 <= KP0 inputs and no <= NOP outputs. in(f, row): the inputs (bfloat16-exact fp32);
 // weights [N][Kp] bf16 with fp32 biases; out(f, row, v) receives the outputs; hid(layer, f,
 // row, v) the hidden activations. Layer 2's chunks feed layer 3's accumulators directly. Every
-// output's sum runs over k in increasing order, whatever the chunking.
+// output's sum runs over k in increasing order, whatever the chunking. Only the 16-row m-tiles
+// mt0 .. mt1 - 1 are computed (two warps may take one each).
 template <int KP0, int H1, int H2, int NOP, class IN, class OUT, class HID>
 __device__ void mlp3_forward(int k0, int no, IN&& in, const __nv_bfloat16* W1, const float* b1, const __nv_bfloat16* W2,
-                             const float* b2, const __nv_bfloat16* W3, const float* b3, OUT&& out, HID&& hid) {
+                             const float* b2, const __nv_bfloat16* W3, const float* b3, OUT&& out, HID&& hid,
+                             int mt0 = 0, int mt1 = 2) {
   constexpr int KT0 = pad16<KP0>() / 16, NT3 = pad8<NOP>() / 8, C = MMA_CHUNK, NTC = C / 8;
   static_assert(H1 % C == 0 && H2 % C == 0, "hidden widths must be multiples of the chunk");
 #pragma unroll 1
-  for (int mt = 0; mt < 2; ++mt) {
+  for (int mt = mt0; mt < mt1; ++mt) {
     uint32_t a0[KT0][4];
 #pragma unroll
     for (int kt = 0; kt < KT0; ++kt) load_a_lanes(in, k0, mt, kt, a0[kt]);

@@ -678,3 +678,34 @@ __device__ void rows_reverse_own(const DevTopo& T, const BLaneT<RV>& B, const SL
     }
   }
 }
+
+// ------------------------------------------------------------------------------------------
+// Forward stages split over the four warps (the four-warp rollout kernel).
+
+// The damped previous-impulse start (zero network, no harvest): warp w takes the row groups
+// g = w, w + 4, ... (their starting impulses, projected) and the limit slots s = w, w + 4, ...
+// (which start cold); after a CTA barrier it adds v += M^-1 J^T lambda0 to the bodies it owns
+// (bmask), slot by slot in slot order, and records slots s = w, w + 4, ... of lambda0 on the
+// tape. The same values as warm_start, in the same order per body.
+template <bool TAPE, class RV>
+__device__ void warm_start_mw(const DevTopo& T, const LaneT<RV>& L, const SL& X, const TapeStep& tp, int w,
+                              uint32_t bmask) {
+  const SL& S = L.S;
+  for (int g = w; g < T.n_wsg; g += 4) {
+    float z[3];
+    for (int k = 0; k < 3; ++k) {
+      const int s = T.wsg_slot[g][k];
+      z[k] = T.ws_alpha * (s >= 0 ? S[T.sm_lam + s] : 0.f);
+    }
+    ws_project(T, L, g, z);
+  }
+  for (int s = w; s < T.nslots; s += 4)
+    if (T.skind[s] == RK_LIMIT) S[T.sm_lam + s] = 0.f;
+  mw_barrier();
+  for (int s = 0; s < T.nslots; ++s) {
+    const float l0 = S[T.sm_lam + s];
+    if (l0 != 0.f) row_apply(T, S, L.rows.at(s * RF_N), X, T.sa[s], T.sb[s], l0, bmask);
+  }
+  if (TAPE)
+    for (int s = w; s < T.nslots; s += 4) tp.lam0[s * 32] = S[T.sm_lam + s];
+}

@@ -110,6 +110,127 @@ __global__ void __launch_bounds__(32, 1) k_forward(const __grid_constant__ DevTo
   if (bad && i < B) D.status[i] |= DPK_ST_NAN_STATE;
 }
 
+// Persistent rollout of the compiled topology with the solver tape, on four warps per group of
+// 32 instances (one CTA per group; a lane is an instance in every warp, as in k_forward). The
+// stages outside the sweeps are split: warp w takes the joints and bodies it owns
+// (DevTopo.mw_jmask, mw_bmask: kinematics, servo targets, external impulses, the warm start's
+// application, integration), every fourth constraint slot of the row assembly and every fourth
+// field of the tape and checkpoint copies; warps 0 and 1 take one 16-row tile each of the
+// tensor-core controller's products. The sweeps, the controller's features and the loss run on
+// warp 0. Each quantity is computed by the same arithmetic in the same order as in k_forward,
+// so the two kernels give identical results. For rollouts (rollout != 0) without the harvest,
+// gait noise or the wide controller.
+template <class Q>
+__global__ void __launch_bounds__(128, 1) k_forward_mw(const __grid_constant__ DevTopo T, const __grid_constant__ DevPtrs D,
+                                                       const float* __restrict__ x0, int t0, int nsteps, int rollout) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
+  const int Bp = T.Bp, B = T.B, nf = 18 * T.nb;
+  float* sm = g_smem + lane;
+  LaneT<SL> L{SL{sm}, GC{D.prm + i, Bp}, SL{sm + T.sm_rows * 32}, i};
+  const SL X{sm + T.sm_x * 32};
+  SL act[DPK_MAXL + 1];
+  for (int l = 0; l <= DPK_MAXL; ++l) act[l] = SL{sm + T.sm_act[l] * 32};
+  const uint32_t bm = T.mw_bmask[warp], jm = T.mw_jmask[warp];
+  const bool fresh = rollout == 1 || (rollout == 2 && t0 == 0);
+  const float* xs = fresh ? x0 : D.state;
+  for (int f = warp; f < nf; f += 4) X[f] = xs[(size_t)f * Bp + i];
+  for (int s = warp; s < T.nslots; s += 4) L.S[T.sm_lam + s] = fresh ? 0.f : D.lam_prev[(size_t)s * Bp + i];
+  if (warp == 0)
+    for (int k = 0; k < T.n_rec; ++k) L.S[T.sm_h + k] = fresh ? 0.f : D.hrec[(size_t)k * Bp + i];
+  mw_barrier();
+  float loss = (rollout == 2 && !fresh) ? D.loss[i] : 0.f;  // warp 0's copy is the one kept
+  if (fresh && T.loss_kind == 3) loss = -dot3(L.P.v3(T.o_loss_target), loss_point(T, L, X));
+  const int nrun = max(0, min(nsteps, warp_horizon(D, i) - t0));
+  const size_t N = (size_t)T.horizon * Bp;
+  for (int k = 0; k < nrun; ++k) {
+    const int t = t0 + k;
+    if (t % D.ckpt_every == 0) {
+      const size_t c = (size_t)(t / D.ckpt_every);
+      for (int f = warp; f < nf; f += 4) D.ckpt[(c * nf + f) * Bp + i] = X[f];
+      if (D.ckpt_lam)
+        for (int s = warp; s < T.nslots; s += 4) D.ckpt_lam[(c * T.nslots + s) * Bp + i] = L.S[T.sm_lam + s];
+      if (D.ckpt_h && warp == 0)
+        for (int q = 0; q < T.n_rec; ++q) D.ckpt_h[(c * T.n_rec + q) * Bp + i] = L.S[T.sm_h + q];
+    }
+    if (D.traj && i < B)
+      for (int f = warp; f < nf; f += 4) D.traj[((size_t)t * B + i) * nf + f] = X[f];
+    uint8_t* ao = (D.active && i < B) ? D.active + ((size_t)t * B + i) * T.nslots : nullptr;
+    // joint kinematics, controller, servo targets
+    hinge_kinematics(T, L, X, jm);
+    mw_barrier();
+    if (T.n_layers > 0) {
+      float* dump_col = D.dump + (size_t)t * Bp + i;
+      if (warp == 0) {
+        controller_features(T, L, X, t, act[0]);
+        if (T.n_rec) {  // recurrent state h^t: the last inputs
+          const int base = T.widths[0] - T.n_rec;
+          for (int q = 0; q < T.n_rec; ++q) act[0][base + q] = qz(T, L.S[T.sm_h + q]);
+        }
+      }
+      mw_barrier();
+      if (T.mlp_tc) {
+        if (warp < 2) ctrl_tc_forward<128, SL>(T, D, act, dump_col, warp, warp + 1);
+      } else if (warp == 0) {
+        controller_forward(T, D, act);
+      }
+      mw_barrier();
+      if (warp == 0) {
+        if (T.n_rec) {  // h^{t+1} = tanh of the last outputs
+          const int base = T.widths[T.n_layers] - T.n_rec;
+          for (int q = 0; q < T.n_rec; ++q) L.S[T.sm_h + q] = tanhf(act[T.n_layers][base + q]);
+        }
+        for (int l = 0; l <= T.n_layers; ++l) {
+          if (T.mlp_tc && l > 0 && l < T.n_layers) continue;  // hidden layers went straight to the dump
+          for (int q = 0; q < T.widths[l]; ++q) dump_col[(size_t)(T.dump_act[l] + q) * N] = act[l][q];
+        }
+      }
+      servo_targets(T, L, act[T.n_layers], jm);
+    } else {
+      servo_targets(T, L, act[0], jm);
+    }
+    // external impulses and world inverse inertias; the tape's pre-solve velocities
+    external_impulses(T, L, X, bm);
+    const TapeStep tp = tape_step(T, D, t);
+    for (int b = 0; b < T.nb; ++b)
+      if ((bm >> b) & 1u)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) tp.vminus[(6 * b + q) * 32] = X[18 * b + 12 + q];
+    mw_barrier();
+    assemble_rows(T, L, X, ao, warp, 4);
+    mw_barrier();
+    for (int f = warp; f < T.nslots * RF_N; f += 4) tp.rows[f * 32] = L.rows[f];
+    if (T.ws) warm_start_mw<true>(T, L, X, tp, warp, bm);
+    mw_barrier();
+    if (warp == 0) {
+      pgs_solve_static<Q, true>(T, L, X, tp);
+      if (D.resid) D.resid[i] += solve_residual(T, L, X);
+    }
+    mw_barrier();
+    integrate(T, X, bm);
+    mw_barrier();
+    if (warp == 0) {
+      const float w = loss_weight(T, t + 1, D.hz[i]);
+      if (w != 0.f) loss += w * loss_value(T, L, X);
+    }
+  }
+  if (D.traj && i < B)
+    for (int f = warp; f < nf; f += 4) D.traj[((size_t)(t0 + nrun) * B + i) * nf + f] = X[f];
+  for (int s = warp; s < T.nslots; s += 4) D.lam_prev[(size_t)s * Bp + i] = L.S[T.sm_lam + s];
+  if (warp == 0)
+    for (int q = 0; q < T.n_rec; ++q) D.hrec[(size_t)q * Bp + i] = L.S[T.sm_h + q];
+  bool bad = false;
+  for (int f = warp; f < nf; f += 4) {
+    D.state[(size_t)f * Bp + i] = X[f];
+    bad |= !isfinite(X[f]);
+  }
+  if (warp == 0) {
+    bad |= !isfinite(loss);
+    D.loss[i] = loss;
+  }
+  if (bad && i < B) atomicOr(D.status + i, DPK_ST_NAN_STATE);
+}
+
 // ------------------------------------------------------------------------------ backward
 struct BwdCtx {
   SL S, X, XB, VB, RC, sbar;

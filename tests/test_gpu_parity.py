@@ -16,7 +16,7 @@ torch = pytest.importorskip("torch")
 
 import oracle as O  # noqa: E402
 from paper_1611_01652_gb300 import workloads as WL  # noqa: E402
-from paper_1611_01652_gb300.binding import CTRL_SIMT, CTRL_TENSOR, World  # noqa: E402
+from paper_1611_01652_gb300.binding import CTRL_SIMT, CTRL_TENSOR, WS_PARAMS, World  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -158,6 +158,36 @@ def test_tensor_core_widths_teacher_forced_steps(monkeypatch, widths):
     m = WL.quadruped(B=8, horizon=100, widths=widths)
     w = teacher_forced(m, 100, stride=3 if widths[1] == 256 else 7, min_frac=0.15 if widths[1] == 256 else 0.3)
     assert w.controller_kind == CTRL_TENSOR
+
+
+@pytest.mark.parametrize("case", ["bf16 damped start", "bf16 cold", "fp32 controller", "recurrent"])
+def test_four_warp_rollout_matches_single_warp(monkeypatch, case):
+    """The compiled topology's recorded rollouts run on four warps per group of 32 instances; the
+    one-warp kernel (forced here) must give the same trajectory, activity log, losses, solver tape
+    (through the gradients of the reverse pass that reads it) and final state, bit for bit."""
+    m = WL.quadruped(B=40, horizon=30, n_recurrent=4 if case == "recurrent" else 0)
+    if case == "fp32 controller":
+        m.ctrl_fp32 = 1
+    warm = case == "bf16 damped start"
+    outs = []
+    for single in (False, True):
+        if single:
+            monkeypatch.setenv("DP_SINGLE_WARP_FORWARD", "1")
+        w = World(m, horizon=30, iters=10 if warm else 20, warmstart=warm)
+        if warm:
+            w.set_warmstart(torch.zeros(WS_PARAMS, device="cuda"), 0.7)
+        W = torch.tensor(m.W, device="cuda")
+        traj = torch.zeros(31, m.B, m.nb, 18, device="cuda")
+        act = torch.zeros(30, m.B, w.n_slots, dtype=torch.uint8, device="cuda")
+        loss = torch.zeros(m.B, device="cuda")
+        w.rollout(W, loss, traj, act)
+        dW = torch.zeros(w.n_params, device="cuda")
+        ds = torch.zeros(m.B, m.nb, 18, device="cuda")
+        w.backward(torch.ones(m.B, device="cuda"), dW, ds)
+        w.sync()
+        outs.append([x.cpu().numpy() for x in (traj, act, loss, dW, ds)])
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
 
 
 def test_determinism_bitwise():
