@@ -39,10 +39,10 @@ SM_COUNT, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
 # fraction above the plain solver's
 RESID_TOL = 0.02
 # DRAM bytes (read + written) per instance-step of k_backward_mw, damped start at 10 sweeps:
-# dram__bytes_read.sum + dram__bytes_write.sum of one launch at B = 1024, T = 20 (293.4 MB +
-# 18.8 MB; profiles/k_backward_mw_quadruped_b1024_t20_ws10.md) / (B T). The tape is read once
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch at B = 1024, T = 20 (293.0 MB +
+# 18.6 MB; profiles/k_backward_mw_quadruped_b1024_t20_ws10.md) / (B T). The tape is read once
 # per launch, so the traffic of the full launch scales with B T.
-BWD_TRAFFIC_PER_INST_STEP = {10: (293375744 + 18790656) / (1024 * 20)}
+BWD_TRAFFIC_PER_INST_STEP = {10: (293044736 + 18602752) / (1024 * 20)}
 
 
 def parse():
@@ -673,7 +673,8 @@ def main():
     derived = SM_COUNT * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12  # TFLOP/s, FP32 FMA at max SM clock
     peak = fp32_peak if fp32_peak > 0 else derived
     achieved = fl["reverse"] * B * T / (head["bwd_ms"] / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": "k_backward", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+    roofline = {"bound": "alu", "kernel": "k_backward_mw<QuadrupedTopo> (dp_backward)", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": (BWD_TRAFFIC_PER_INST_STEP[it] * B * T
                                                       if it in BWD_TRAFFIC_PER_INST_STEP else None),
                 "peak_derived": derived,
