@@ -950,8 +950,9 @@ dp_status dp_backward(dp_world* w, const float* dloss, float* dW, float* dstate0
       CU(cudaMemcpyAsync(g.dst, w->stage, sizeof(float) * (size_t)w->B * g.n, cudaMemcpyDefault, w->stream));
     }
   }
-  if (dW && w->n_params > 0 && T.ext_ctrl) {
-    CU(ext_weight_grad(w, T, D, w->dW_stage));
+  if (dW && w->n_params > 0 && (T.ext_ctrl || T.mlp_tc)) {
+    // bfloat16 networks on the tensor cores: the weight gradient on the tensor cores too
+    CU(tc_weight_grad(w, T, D, w->dW_stage));
     CU(cudaMemcpyAsync(dW, w->dW_stage, sizeof(float) * w->n_params, cudaMemcpyDefault, w->stream));
   } else if (dW && w->n_params > 0) {
     const size_t N = (size_t)T.horizon * w->Bp;

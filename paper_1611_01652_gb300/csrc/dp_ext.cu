@@ -559,12 +559,14 @@ cudaError_t ext_backward(dp_world* w, const DevTopo& T, const DevPtrs& D) {
   return r;
 }
 
-// Controller gradient of the wide path, summed over all steps and instances, into dst (flat
-// layout of the master weights: per layer W[out][in] then b[out]).
-cudaError_t ext_weight_grad(dp_world* w, const DevTopo& T, const DevPtrs& D, float* dst) {
-  const ExtLayout& Lo = w->ext;
+// Controller gradient of a 3-layer bfloat16 network on the tensor cores (the wide path, and the
+// in-step tensor-core controller), summed over all steps and instances, into dst (flat layout
+// of the master weights: per layer W[out][in] then b[out]). dW_l = sum over the T Bp dump columns
+// of delta_l act_l^T: the activations are bfloat16 values already (exact), the fp32 deltas enter
+// as two bfloat16 parts (hi + lo, 16 significant bits).
+cudaError_t tc_weight_grad(dp_world* w, const DevTopo& T, const DevPtrs& D, float* dst) {
   const size_t N = (size_t)T.horizon * T.Bp;
-  const int rows[4] = {T.widths[0], Lo.h1, Lo.h2, Lo.no};
+  const int rows[4] = {T.widths[0], T.widths[1], T.widths[2], T.widths[3]};
   size_t off = 0;
   for (int l = 0; l < 3; ++l) {
     const int ni = rows[l], no_ = rows[l + 1];

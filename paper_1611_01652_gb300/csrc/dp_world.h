@@ -59,4 +59,4 @@ dp_status dp_internal_fail(dp_status s, const char* msg);
 cudaError_t launch_prep_ext(const ExtLayout& Lo, int K0, const float* W, __nv_bfloat16* out, cudaStream_t s);
 cudaError_t ext_forward(dp_world* w, const DevTopo& T, const DevPtrs& D, int t0, int nsteps, int rollout, int record);
 cudaError_t ext_backward(dp_world* w, const DevTopo& T, const DevPtrs& D);
-cudaError_t ext_weight_grad(dp_world* w, const DevTopo& T, const DevPtrs& D, float* dst);
+cudaError_t tc_weight_grad(dp_world* w, const DevTopo& T, const DevPtrs& D, float* dst);
