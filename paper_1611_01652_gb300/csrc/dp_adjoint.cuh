@@ -644,10 +644,10 @@ __device__ void controller_reverse(const DevTopo& T, const DevPtrs& D, const AV*
 
 // Controller reverse on the tensor cores (the networks of controller_forward_tc). zb0 holds u_bar;
 // the output delta is already in del[2]. Hidden deltas go to del[1], del[0]; the input adjoint to
-// sbar.
+// sbar. Rows of the 16-row tiles mt0 .. mt1 - 1 only (two warps may take one each).
 template <class Q, class AV>
 __device__ void controller_reverse_tc(const DevTopo& T, const DevPtrs& D, const AV* act, const AV* del, const SL& zb0,
-                                      const SL& sbar) {
+                                      const SL& sbar, int mt0 = 0, int mt1 = 2) {
   const __nv_bfloat16* Wc = D.Wtc;
   const AV a1 = act[1], a2 = act[2], e0 = del[0], e1 = del[1];
   __syncwarp();
@@ -658,7 +658,7 @@ __device__ void controller_reverse_tc(const DevTopo& T, const DevPtrs& D, const 
         T.widths[0], T.widths[3], [&](int f, int r) { return zb0.lane_at(f, r); }, Wc + Lw.w3t, Wc + Lw.w2t,
         Wc + Lw.w1t, [&](int l, int f, int r) { return (l == 1 ? a1 : a2).lane_at(f, r) > 0.f; },
         [&](int l, int f, int r, float v) { (l == 1 ? e0 : e1).lane_at(f, r) = v; },
-        [&](int f, int r, float v) { sbar.lane_at(f, r) = v; });
+        [&](int f, int r, float v) { sbar.lane_at(f, r) = v; }, mt0, mt1);
   });
   __syncwarp();
 }

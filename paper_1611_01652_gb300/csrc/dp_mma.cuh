@@ -261,16 +261,16 @@ __device__ __forceinline__ void relu_mask(float (&d)[NT][4], MASK& mask, int l, 
 // first layer's deltas are formed C1 = min(H1, 128) columns at a time, each from every
 // MMA_CHUNK-column chunk of the second layer's deltas (recomputed when H1 > 128: their product
 // has only NOP terms), so that a 256-wide network's deltas are never held whole; every sum still
-// runs over k in increasing order.
+// runs over k in increasing order. Only the 16-row m-tiles mt0 .. mt1 - 1 are computed.
 template <int KP0, int H1, int H2, int NOP, class UBAR, class MASK, class DEL, class SBAR>
 __device__ void mlp3_backward(int k0, int no, UBAR&& ubar, const __nv_bfloat16* W3t, const __nv_bfloat16* W2t,
-                              const __nv_bfloat16* W1t, MASK&& mask, DEL&& del, SBAR&& sbar) {
+                              const __nv_bfloat16* W1t, MASK&& mask, DEL&& del, SBAR&& sbar, int mt0 = 0, int mt1 = 2) {
   constexpr int NT0 = pad8<KP0>() / 8, KT3 = pad16<NOP>() / 16, C = MMA_CHUNK, NTC = C / 8;
   constexpr int C1 = H1 < 128 ? H1 : 128, NT1 = C1 / 8;
   static_assert(H1 % C1 == 0 && H2 % C == 0 && C1 % 16 == 0, "hidden widths must be multiples of the chunks");
   const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
 #pragma unroll 1
-  for (int mt = 0; mt < 2; ++mt) {
+  for (int mt = mt0; mt < mt1; ++mt) {
     // output adjoint (fp32) -> hi/lo A fragments
     uint32_t h3[KT3][4], l3[KT3][4];
     {

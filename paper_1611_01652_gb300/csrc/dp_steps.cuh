@@ -300,6 +300,33 @@ __device__ void reverse_step_head(const DevTopo& T, const DevPtrs& D, const BwdC
   for (int q = 0; q < T.nslots * RC_N; ++q) C.RC[q] = 0.f;
 }
 
+// The in-step controller's reverse around its products: servo targets and the recurrent
+// outputs' tanh (head: u_bar into zb0 and the output delta), then, after the products, the
+// features and the recurrent input (tail).
+template <class RV>
+__device__ void ctrl_reverse_head(const DevTopo& T, const BwdCtx& C, const RevStep<RV>& V) {
+  const GW* act = V.act;
+  const GW* del = V.del;
+  servo_reverse(T, V.Bl, act[T.n_layers], del[T.n_layers - 1], V.zb0);
+  if (T.n_rec) {  // adjoint of the recurrent outputs: h^{t+1} = tanh(z)
+    const int base = T.widths[T.n_layers] - T.n_rec;
+    for (int k = 0; k < T.n_rec; ++k) {
+      const float th = tanhf(act[T.n_layers][base + k]);
+      const float zb = C.S[T.sm_hb + k] * (1.f - th * th);
+      V.zb0[base + k] = zb;
+      del[T.n_layers - 1][base + k] = zb;
+    }
+  }
+}
+template <class RV>
+__device__ void ctrl_reverse_tail(const DevTopo& T, const BwdCtx& C, const RevStep<RV>& V) {
+  features_reverse(T, V.Bl, C.XB, C.sbar);
+  if (T.n_rec) {  // adjoint of h^t (straight through its bfloat16 rounding), carried to step t - 1
+    const int base = T.widths[0] - T.n_rec;
+    for (int k = 0; k < T.n_rec; ++k) C.S[T.sm_hb + k] = C.sbar[base + k];
+  }
+}
+
 // Servo-target, controller, feature and hinge-kinematics reverse of step t (after the
 // external impulses' reverse), down to the adjoint of x_t.
 template <class Q, class RV>
@@ -314,29 +341,38 @@ __device__ void reverse_step_ctrl(const DevTopo& T, const DevPtrs& D, const BwdC
     float* ub = D.ub_ext + (size_t)i * 16;
     for (int o = 0; o < 16; ++o) ub[o] = o < T.widths[T.n_layers] ? V.zb0[o] : 0.f;
   } else if (T.n_layers > 0) {
-    servo_reverse(T, V.Bl, act[T.n_layers], del[T.n_layers - 1], V.zb0);
-    if (T.n_rec) {  // adjoint of the recurrent outputs: h^{t+1} = tanh(z)
-      const int base = T.widths[T.n_layers] - T.n_rec;
-      for (int k = 0; k < T.n_rec; ++k) {
-        const float th = tanhf(act[T.n_layers][base + k]);
-        const float zb = C.S[T.sm_hb + k] * (1.f - th * th);
-        V.zb0[base + k] = zb;
-        del[T.n_layers - 1][base + k] = zb;
-      }
-    }
+    ctrl_reverse_head(T, C, V);
     if (T.mlp_tc)
       controller_reverse_tc<Q>(T, D, act, del, V.zb0, C.sbar);
     else
       controller_reverse(T, D, act, del, V.zb0, V.zb1, C.sbar);
-    features_reverse(T, V.Bl, C.XB, C.sbar);
-    if (T.n_rec) {  // adjoint of h^t (straight through its bfloat16 rounding), carried to step t - 1
-      const int base = T.widths[0] - T.n_rec;
-      for (int k = 0; k < T.n_rec; ++k) C.S[T.sm_hb + k] = C.sbar[base + k];
-    }
+    ctrl_reverse_tail(T, C, V);
   } else {
     servo_reverse(T, V.Bl, act[0], act[0], V.zb0);
   }
   hinge_reverse(T, V.Bl, C.XB);
+}
+
+// reverse_step_ctrl on the four warps of k_backward_mw (called by every warp; ends after a CTA
+// barrier): warp 0 takes the servo, feature and hinge-kinematics reverse, warps 0 and 1 one
+// 16-row tile each of the tensor-core controller's reverse products.
+template <class Q, class RV>
+__device__ void reverse_step_ctrl_mw(const DevTopo& T, const DevPtrs& D, const BwdCtx& C, const RevStep<RV>& V,
+                                     int warp) {
+  if (T.ext_ctrl || T.n_layers == 0 || !T.mlp_tc) {
+    if (warp == 0) reverse_step_ctrl<Q>(T, D, C, V);
+    mw_barrier();
+    return;
+  }
+  if (warp == 0) ctrl_reverse_head(T, C, V);
+  mw_barrier();
+  if (warp < 2) controller_reverse_tc<Q>(T, D, V.act, V.del, V.zb0, C.sbar, warp, warp + 1);
+  mw_barrier();
+  if (warp == 0) {
+    ctrl_reverse_tail(T, C, V);
+    hinge_reverse(T, V.Bl, C.XB);
+  }
+  mw_barrier();
 }
 
 // Last part of the reverse of step t (after the solver's reverse sweeps): warm-start
@@ -492,8 +528,7 @@ __global__ void __launch_bounds__(128, 1) k_backward_mw(const __grid_constant__ 
     mw_barrier();
     external_reverse(T, V.Bl, C.XB, C.VB, bm);
     mw_barrier();
-    if (warp == 0) reverse_step_ctrl<Q>(T, D, C, V);
-    mw_barrier();
+    reverse_step_ctrl_mw<Q>(T, D, C, V, warp);
   }
   if (warp != 0) return;
   if (T.loss_kind == 3) {  // initial term -a.q(x_0) of the displacement loss
