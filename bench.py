@@ -691,8 +691,9 @@ def main():
                "sample": "%d spawned processes x 8 quadruped instances x 1000 steps, forward+adjoint, FP64 oracle, "
                          "cold start at 20 sweeps (%.1f s wall)" % (cores, dt)}
     n_dense = len(m.widths) - 1 + (1 if m.skip else 0)
-    # per step: two weight preparations + forward; pad + backward; per dense layer gemm, sum, rowsum, sum
-    launches_per_step = 3 + 2 + 4 * n_dense
+    # per step: two weight preparations + forward; pad + backward + gradient check; per dense layer
+    # dW product, sum, rowsum, sum
+    launches_per_step = 3 + 3 + 4 * n_dense
     gate = None
     if rep and not rep.get("fixed"):
         gate = {k: rep[k] for k in ("plain_iters", "ref_iters", "plain_resid", "plain_state_err", "plain_grad_err",
