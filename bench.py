@@ -68,6 +68,10 @@ def parse():
     p.add_argument("--camera-only", action="store_true", help="time only the differentiable camera")
     p.add_argument("--sysid-only", action="store_true", help="time only the system-identification fit")
     p.add_argument("--recurrent-only", action="store_true", help="time only the recurrent controller")
+    p.add_argument("--reach-only", action="store_true",
+                   help="train the 4-DoF arm's reaching controller (not in the default run: minutes of training)")
+    p.add_argument("--reach-iters", type=int, default=1000)
+    p.add_argument("--reach-batch", type=int, default=256)
     p.add_argument("--wide-only", action="store_true",
                    help="time only the wide controller (for profiling; prints its object as the line)")
     p.add_argument("--wide-batch", type=int, default=4096)
@@ -390,6 +394,38 @@ def time_small_workloads(args, reps=3):
     return out
 
 
+def time_reach(args):
+    """Reaching with the 4-DoF arm (section 3.2): the controller 11-64-64-4 (bfloat16, tensor cores)
+    trained from the zero policy through the library's gradients on ``--reach-batch`` seeded
+    targets, 300 steps of 5 ms, gradient decay 0.5, gradient norm limited to 1, Adam with the
+    learning rate decaying from 3e-3 to 3e-4, ``--reach-iters`` iterations. Two objectives from the
+    same start: the paper's (the tip's distance to the target averaged over the steps) and its
+    square (smooth at the target: its gradient vanishes there instead of keeping unit length).
+    Reports per objective the time per iteration, the objective's log and the distribution of the
+    tips' final distances before and after training."""
+    import numpy as np
+
+    from paper_1611_01652_gb300 import reach
+    from paper_1611_01652_gb300 import workloads as WL
+
+    def dist(d):
+        q = np.quantile(d, [0.1, 0.5, 0.9])
+        return {"p10": float(q[0]), "median": float(q[1]), "p90": float(q[2]), "mean": float(d.mean()),
+                "within_5cm": float((d < 0.05).mean()), "within_10cm": float((d < 0.10).mean())}
+
+    out = {"workload": "4-DoF arm reaching, %d targets, 300 steps of 5 ms, %d iterations" % (
+        args.reach_batch, args.reach_iters)}
+    for name, kind in (("distance", WL.L_DIST), ("squared distance", WL.L_SQDIST)):
+        m = WL.arm4dof(B=args.reach_batch, horizon=300)
+        m.loss_kind = kind
+        t0 = time.perf_counter()
+        hist, before, after = reach.train(m, args.reach_iters)
+        dt = time.perf_counter() - t0
+        out[name] = {"ms_per_iteration": 1e3 * dt / args.reach_iters, "objective": hist,
+                     "final_distance_m": {"before": dist(before), "after": dist(after)}}
+    return out
+
+
 def time_sysid(args, iters=300):
     """System identification: 1024 three-link pendulums x 4 swings (B = 4096, T = 300 steps of
     1 ms) fitted to their own observed far-end positions by Adam on the library's link-mass
@@ -566,6 +602,9 @@ def main():
         return
     if args.sysid_only:
         print(json.dumps(time_sysid(args)))
+        return
+    if args.reach_only:
+        print(json.dumps(time_reach(args)))
         return
     if args.recurrent_only:
         print(json.dumps(time_recurrent_controller(args, args.alpha)))

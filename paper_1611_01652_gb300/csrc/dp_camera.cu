@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <string>
 
 #include "../../include/dp.h"
@@ -26,6 +27,7 @@ constexpr int kThreads = 256, kPixPerThread = 4, kChunk = kThreads * kPixPerThre
 
 struct CamArgs {
   int W, H, B, nb, n_obj, th, tw;
+  int cull;  // screen rectangles per object (DP_CAMERA_NO_CULL turns them off, for comparison)
   float f, plane;
   float C[3], Rc[9];
   int body[kMaxObj], tex[kMaxObj], kind[kMaxObj];
@@ -39,9 +41,12 @@ struct Hit {
 };
 
 // Frame of one box for one instance: R (box to world), centre c_w, and the camera centre in the
-// box frame o = R^T (C - c_w) (the same for every pixel).
+// box frame o = R^T (C - c_w) (the same for every pixel); when the frames are staged per block,
+// also the object's screen rectangle (rect: j_lo, j_hi, i_lo, i_hi): pixels outside it cannot hit
+// the object.
 struct BoxFrame {
   float R[9], cw[3], o[3];
+  float rect[4];
 };
 
 __device__ __forceinline__ float pick3(const float (&v)[3], int k) { return k == 0 ? v[0] : (k == 1 ? v[1] : v[2]); }
@@ -66,6 +71,47 @@ __device__ __forceinline__ void box_frame(const CamArgs& A, const float* __restr
   for (int k = 0; k < 3; ++k) F.o[k] = F.R[k] * (A.C[0] - F.cw[0]) + F.R[3 + k] * (A.C[1] - F.cw[1]) + F.R[6 + k] * (A.C[2] - F.cw[2]);
 }
 
+// Screen rectangle of object o (frame F): a point q in camera coordinates (q = R_c (x - C)) lies on
+// the ray of pixel (i, j) when j + 1/2 = f q_0 / q_2 + W / 2 and i + 1/2 = f q_1 / q_2 + H / 2, at
+// the ray parameter t = q_2 / P. When every corner of the object's box (a sphere's: the cube
+// around it) is in front of the camera (q_2 > 0), the object's image is the convex hull of the
+// projected corners, so a pixel outside their bounding rectangle (widened by one pixel for
+// rounding) cannot hit it; when every corner lies before the projection plane (q_2 < P), no ray
+// hits it at t >= 1. Otherwise (a corner behind the camera, or a plane) every pixel tests it.
+__device__ __forceinline__ void screen_rect(const CamArgs& A, int o, BoxFrame& F) {
+  F.rect[0] = F.rect[2] = -INFINITY;
+  F.rect[1] = F.rect[3] = INFINITY;
+  if (!A.cull || A.kind[o] == DP_OBJ_PLANE) return;
+  const float h0 = A.half[o][0];
+  const float h1 = A.kind[o] == DP_OBJ_SPHERE ? h0 : A.half[o][1];
+  const float h2 = A.kind[o] == DP_OBJ_SPHERE ? h0 : A.half[o][2];
+  float jlo = INFINITY, jhi = -INFINITY, ilo = INFINITY, ihi = -INFINITY, zmax = -INFINITY;
+  for (int c = 0; c < 8; ++c) {
+    const float l[3] = {c & 1 ? h0 : -h0, c & 2 ? h1 : -h1, c & 4 ? h2 : -h2};
+    float w[3], q[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) w[r] = F.cw[r] + F.R[3 * r] * l[0] + F.R[3 * r + 1] * l[1] + F.R[3 * r + 2] * l[2] - A.C[r];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) q[k] = A.Rc[3 * k] * w[0] + A.Rc[3 * k + 1] * w[1] + A.Rc[3 * k + 2] * w[2];
+    if (!(q[2] > 0.f)) return;  // a corner behind the camera: no bound
+    zmax = fmaxf(zmax, q[2]);
+    const float jc = A.f * q[0] / q[2] + 0.5f * (float)A.W - 0.5f, ic = A.f * q[1] / q[2] + 0.5f * (float)A.H - 0.5f;
+    jlo = fminf(jlo, jc);
+    jhi = fmaxf(jhi, jc);
+    ilo = fminf(ilo, ic);
+    ihi = fmaxf(ihi, ic);
+  }
+  if (zmax < A.plane) {  // wholly before the projection plane
+    F.rect[0] = F.rect[2] = INFINITY;
+    F.rect[1] = F.rect[3] = -INFINITY;
+    return;
+  }
+  F.rect[0] = jlo - 1.f;
+  F.rect[1] = jhi + 1.f;
+  F.rect[2] = ilo - 1.f;
+  F.rect[3] = ihi + 1.f;
+}
+
 // Work split: a block takes kChunk consecutive pixels of the batch, kPixPerThread per thread
 // (pixel first + threadIdx.x + r kThreads). When W * H is a multiple of kChunk every block lies in
 // one instance and its box frames are computed once into shared memory; otherwise each thread
@@ -78,7 +124,10 @@ __device__ __forceinline__ bool stage_frames(const CamArgs& A, const float* __re
   inst0 = uniform ? (int)(blockIdx.x / chunks) : 0;
   pix0 = uniform ? (int)(blockIdx.x % chunks) * kChunk : 0;
   if (uniform)
-    for (int o = threadIdx.x; o < A.n_obj; o += blockDim.x) box_frame(A, state, inst0, o, sf[o]);
+    for (int o = threadIdx.x; o < A.n_obj; o += blockDim.x) {
+      box_frame(A, state, inst0, o, sf[o]);
+      screen_rect(A, o, sf[o]);
+    }
   __syncthreads();
   return uniform;
 }
@@ -116,6 +165,9 @@ __device__ Hit trace(const CamArgs& A, const float* __restrict__ state, const Bo
   h.k = 0;
   h.t = INFINITY;
   for (int o = 0; o < A.n_obj; ++o) {
+    if (staged && ((float)j < sf[o].rect[0] || (float)j > sf[o].rect[1] || (float)i < sf[o].rect[2] ||
+                   (float)i > sf[o].rect[3]))
+      continue;  // outside the object's screen rectangle: no hit
     BoxFrame F;
     if (staged)
       F = sf[o];
@@ -245,7 +297,7 @@ __device__ __forceinline__ Sample sample_of(const CamArgs& A, const Hit& h) {
   return S;
 }
 
-__global__ void __launch_bounds__(kThreads) k_render(const __grid_constant__ CamArgs A, const float* __restrict__ state,
+__global__ void __launch_bounds__(kThreads, 6) k_render(const __grid_constant__ CamArgs A, const float* __restrict__ state,
                                                      const float* __restrict__ tex, float* __restrict__ image,
                                                      int* __restrict__ hit_out) {
   __shared__ BoxFrame sf[kMaxObj];
@@ -443,6 +495,7 @@ dp_status cam_args(const dp_camera* cam, const dp_scene* sc, int32_t B, int32_t 
   A.tw = sc->tex_w;
   A.f = cam->focal;
   A.plane = cam->plane;
+  A.cull = getenv("DP_CAMERA_NO_CULL") ? 0 : 1;
   for (int k = 0; k < 3; ++k) A.C[k] = cam->position[k];
   for (int k = 0; k < 9; ++k) A.Rc[k] = cam->rotation[k];
   for (int o = 0; o < sc->n_obj; ++o) {

@@ -50,3 +50,20 @@ class ReachTrainer:
         R = x[:, 3:12].reshape(-1, 3, 3)
         tip = x[:, 0:3] + np.einsum("bij,bj->bi", R, np.asarray(m.loss_point, np.float64))
         return np.linalg.norm(tip - np.asarray(m.loss_target, np.float64), axis=1)
+
+
+def train(model, iters, lr0=3e-3, lr1=3e-4, clip=1.0, log_every=100):
+    """Trains the model's controller for ``iters`` iterations of ReachTrainer, the learning rate
+    decaying from ``lr0`` to ``lr1`` along a half cosine. Returns the logged (iteration, batch-mean
+    objective) pairs and the tips' final distances to their targets before and after training."""
+    import math
+
+    tr = ReachTrainer(model, lr=lr0, clip=clip)
+    before = tr.final_distance()
+    hist = []
+    for k in range(iters):
+        tr.lr = lr1 + 0.5 * (lr0 - lr1) * (1.0 + math.cos(math.pi * k / iters))
+        loss = tr.step()
+        if k % log_every == 0 or k == iters - 1:
+            hist.append((k, float(loss)))
+    return hist, before, tr.final_distance()

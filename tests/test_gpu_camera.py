@@ -95,3 +95,27 @@ def test_full_size_batch_sampled():
     cs = WL.camera_scene(B=4096, W=288, H=96)
     _, _, _, img, hit = gpu_frames(cs, cs.states)
     compare(cs, cs.states, [0, 1, 777, 2048, 4095], img, hit)
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_screen_rectangles_change_nothing(monkeypatch, mixed):
+    """At 288 x 96 every block of pixels lies in one instance, and each object's screen rectangle
+    lets the block's pixels skip the objects they cannot see. Without the rectangles
+    (DP_CAMERA_NO_CULL) the frames and hit maps are the same bit for bit, and the gradients the
+    same up to the order of the reverse pass's atomic sums."""
+    cs = WL.camera_scene(B=32, W=288, H=96, mixed=mixed)
+    outs = []
+    for off in (False, True):
+        if off:
+            monkeypatch.setenv("DP_CAMERA_NO_CULL", "1")
+        rig, st, tex, img, hit = gpu_frames(cs, cs.states)
+        dimg = np.random.default_rng(3).normal(size=img.shape).astype(np.float32)
+        ds = torch.zeros(st.shape, device="cuda")
+        dt = torch.zeros(tex.shape, device="cuda")
+        rig.render_backward(st, tex, torch.tensor(dimg, device="cuda"), ds, dt)
+        torch.cuda.synchronize()
+        outs.append((img, hit, ds.cpu().numpy(), dt.cpu().numpy()))
+    (ia, ha, sa, ta), (ib, hb, sb, tb) = outs
+    assert np.array_equal(ia, ib) and np.array_equal(ha, hb)
+    assert np.abs(sa - sb).max() <= 1e-5 * max(1.0, np.abs(sb).max())
+    assert np.abs(ta - tb).max() <= 1e-5 * max(1.0, np.abs(tb).max())
