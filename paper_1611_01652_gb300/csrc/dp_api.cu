@@ -219,10 +219,11 @@ void plan_smem(DevTopo& T, bool backward, int smem_floats_max, bool rows_on_chip
     T.sm_iinvb = take(9 * T.nb);
     T.sm_invmb = take(T.nb);
     T.sm_rc = take(12 * T.nslots);
-    T.sm_sbar = take(T.n_layers > 0 ? T.widths[0] : 1);
+    // the in-step controller's input adjoint (the wide controller's goes to the batched products)
+    T.sm_sbar = take(T.n_layers > 0 && !T.ext_ctrl ? T.widths[0] : 1);
     // the run-time reverse sweep's working velocities, or the multi-warp sweep's hand-off ring
-    // (compiled topologies without the wide controller: the worlds that run the multi-warp kernel)
-    const bool mw = T.topo_id != 0 && !T.ext_ctrl;
+    // (compiled topologies: the worlds that run the four-warp kernels)
+    const bool mw = T.topo_id != 0;
     T.sm_vw = T.sm_ring = take(mw ? std::max(6 * T.nb, 4 * DPK_MW_CH) : 6 * T.nb);
     T.sm_hb = take(T.n_rec);
     // controller-reverse ping-pong buffers: the row-adjoint region is free by then

@@ -15,9 +15,9 @@ static cudaError_t launch_forward_t(const DevTopo& T, const DevPtrs& D, const fl
 cudaError_t launch_forward(const DevTopo& T, const DevPtrs& D, const float* x0, int t0, int nsteps, int rollout,
                            int record, cudaStream_t s) {
   // the compiled-topology path keeps its rows on chip; otherwise the run-time path. Its recorded
-  // rollouts run on four warps per group (not the harvest, gait noise or wide controller).
+  // rollouts run on four warps per group (not the harvest or gait noise).
   if (T.topo_id == QuadrupedTopo::id && T.sm_rows >= 0 && record && rollout && !D.harvest && !D.u_noise &&
-      !T.ext_ctrl && !T.ws_net && !getenv("DP_SINGLE_WARP_FORWARD"))
+      !T.ws_net && !getenv("DP_SINGLE_WARP_FORWARD"))
     return launch_forward_mw_quadruped(T, D, x0, t0, nsteps, rollout, s);
   if (T.topo_id == QuadrupedTopo::id && T.sm_rows >= 0)
     return record ? launch_forward_t<SL, true, QuadrupedTopo>(T, D, x0, t0, nsteps, rollout, s)

@@ -118,8 +118,10 @@ __global__ void __launch_bounds__(32, 1) k_forward(const __grid_constant__ DevTo
 // field of the tape and checkpoint copies; warps 0 and 1 take one 16-row tile each of the
 // tensor-core controller's products. The sweeps, the controller's features and the loss run on
 // warp 0. Each quantity is computed by the same arithmetic in the same order as in k_forward,
-// so the two kernels give identical results. For rollouts (rollout != 0) without the harvest,
-// gait noise or the wide controller.
+// so the two kernels give identical results. For rollouts (rollout != 0) without the harvest or
+// gait noise; with the wide controller (one step per launch) the step's controller output comes
+// from the batched products and the next step's input features go back to them, as in
+// k_forward.
 template <class Q>
 __global__ void __launch_bounds__(128, 1) k_forward_mw(const __grid_constant__ DevTopo T, const __grid_constant__ DevPtrs D,
                                                        const float* __restrict__ x0, int t0, int nsteps, int rollout) {
@@ -159,7 +161,15 @@ __global__ void __launch_bounds__(128, 1) k_forward_mw(const __grid_constant__ D
     // joint kinematics, controller, servo targets
     hinge_kinematics(T, L, X, jm);
     mw_barrier();
-    if (T.n_layers > 0) {
+    if (T.ext_ctrl) {
+      // wide controller: its output for this step was computed between launches
+      if (warp == 0) {
+        const float* ue = D.u_ext + ((size_t)t * Bp + i) * T.ext_nop;
+        for (int m = 0; m < T.widths[T.n_layers]; ++m) act[T.n_layers][m] = ue[m];
+      }
+      mw_barrier();
+      servo_targets(T, L, act[T.n_layers], jm);
+    } else if (T.n_layers > 0) {
       float* dump_col = D.dump + (size_t)t * Bp + i;
       if (warp == 0) {
         controller_features(T, L, X, t, act[0]);
@@ -216,6 +226,19 @@ __global__ void __launch_bounds__(128, 1) k_forward_mw(const __grid_constant__ D
   }
   if (D.traj && i < B)
     for (int f = warp; f < nf; f += 4) D.traj[((size_t)(t0 + nrun) * B + i) * nf + f] = X[f];
+  if (T.ext_ctrl && t0 + nrun < T.horizon && warp == 0) {
+    // wide controller: input features of the next step, bf16 for the products, and the
+    // activation dump column for the weight gradient
+    const int tn = t0 + nrun;
+    hinge_kinematics(T, L, X);
+    controller_features(T, L, X, tn, act[0]);
+    __nv_bfloat16* sx = D.s_ext + (size_t)i * T.ext_k0p;
+    for (int q = 0; q < T.ext_k0p; ++q) {
+      const float v = q < T.widths[0] ? act[0][q] : 0.f;
+      sx[q] = __float2bfloat16_rn(v);
+      if (q < T.widths[0]) D.dump[(size_t)(T.dump_act[0] + q) * N + (size_t)tn * Bp + i] = v;
+    }
+  }
   for (int s = warp; s < T.nslots; s += 4) D.lam_prev[(size_t)s * Bp + i] = L.S[T.sm_lam + s];
   if (warp == 0)
     for (int q = 0; q < T.n_rec; ++q) D.hrec[(size_t)q * Bp + i] = L.S[T.sm_h + q];
@@ -466,6 +489,76 @@ __global__ void __launch_bounds__(32, 1) k_backward(const __grid_constant__ DevT
 // runs the servo, controller, feature and hinge reverse. The warps meet at CTA barrier 1
 // between phases; every warp executes the same barrier sequence. Same arithmetic as
 // k_backward up to the order of the row-adjoint sums, which is fixed.
+// One step of the four-warp reverse pass (called by every warp of the CTA; ends after a CTA
+// barrier): step t from its tape record and x_t from the checkpoints, with x_{t+1} on chip in
+// C.X (copied there first from x_t1 when load_x1 is set); the state adjoint in C.XB is that of
+// x_{t+1} on entry and that of x_t on exit.
+template <class Q>
+__device__ void mw_reverse_step(const DevTopo& T, const DevPtrs& D, const BwdCtx& C, int t, const float* x_t1,
+                                bool load_x1, int warp, uint32_t bm, uint32_t jm) {
+  const int i = C.i, Bp = T.Bp, nf = 18 * T.nb;
+  const size_t sbytes = (size_t)nf * Bp;
+  const RevStep<GSR> V = rev_views<GSR>(T, D, C, t, t);
+  const float* x_t = D.ckpt + (size_t)t * sbytes;
+  if (load_x1)
+    for (int f = warp; f < nf; f += 4) C.X[f] = x_t1[(size_t)f * Bp + i];
+  if (warp == 0 && t > 0) prefetch_record_l2(T, tape_step(T, D, t - 1).rec);  // the next step to reverse
+  if (T.grad_decay != 1.f) {  // section 3.2: the adjoint from later steps shrinks by alpha per step
+    for (int f = warp; f < nf; f += 4) C.XB[f] *= T.grad_decay;
+    if (warp == 0)
+      for (int k = 0; k < T.n_rec; ++k) C.S[T.sm_hb + k] *= T.grad_decay;  // and so does h's
+  }
+  mw_barrier();
+  // loss term (by the loss body's owner) and integrator, x_{t+1} on chip
+  if (T.mw_own[T.loss_body] == warp) loss_reverse(T, V.Bl, C.X, C.XB, loss_weight(T, t + 1, D.hz[i]) * C.dl);
+  integrate_reverse(T, GC{x_t + i, Bp}, C.X, C.XB, C.VB, bm);
+  mw_barrier();
+  // x_t on chip; accumulators zeroed
+  for (int f = warp; f < nf; f += 4) C.X[f] = x_t[(size_t)f * Bp + i];
+  for (int j = 0; j < T.nj; ++j) {
+    if (!((jm >> j) & 1u)) continue;
+    C.S[T.sm_thb + j] = 0.f; C.S[T.sm_thdb + j] = 0.f; C.S[T.sm_wstb + j] = 0.f;
+    C.S.s3(T.sm_uab + 3 * j, f3(0.f, 0.f, 0.f));
+  }
+  for (int b = 0; b < T.nb; ++b) {
+    if (!((bm >> b) & 1u)) continue;
+    C.S[T.sm_invmb + b] = 0.f;
+    for (int q = 0; q < 9; ++q) C.S[T.sm_iinvb + 9 * b + q] = 0.f;
+  }
+  for (int q = warp; q < T.nslots * RC_N; q += 4) C.RC[q] = 0.f;
+  mw_barrier();
+  // per-step forward quantities of x_t, recomputed bit-identically
+  hinge_kinematics(T, V.L, C.X, jm);
+  servo_targets(T, V.L, V.act[T.n_layers > 0 ? T.n_layers : 0], jm);
+  inverse_inertia(T, V.L, C.X, bm);
+  mw_barrier();
+  pgs_reverse_mw<Q>(T, V.L, V.tp, warp);
+  if (T.ws) {
+    ws_apply_reverse_own(T, V.L, C.VB, C.RC, V.tp, warp);
+    mw_barrier();
+  }
+  rows_reverse_own(T, V.Bl, C.XB, C.VB, C.RC, warp);
+  mw_barrier();
+  external_reverse(T, V.Bl, C.XB, C.VB, bm);
+  mw_barrier();
+  reverse_step_ctrl_mw<Q>(T, D, C, V, warp);
+}
+
+// Initial term -a.q(x_0) of the displacement loss (warp 0).
+__device__ __forceinline__ void loss_initial_reverse(const DevTopo& T, const DevPtrs& D, const BwdCtx& C) {
+  copy_state_to_smem(T, D.ckpt, C.i, C.X);
+  const int b = T.loss_body;
+  M3 R = loadR(C.X, 18 * b);
+  float3 c = C.P.v3(T.o_loss_point), a = C.P.v3(T.o_loss_target);
+  float3 gq = -C.dl * a;
+  C.XB.a3(18 * b, gq);
+  add_outer(C.XB, 18 * b + 3, gq, c);
+  C.G.red3(T.o_loss_point, mtv(R, gq));
+  C.G.red3(T.o_loss_target, -C.dl * (C.X.v3(18 * b) + mv(R, c)));
+}
+
+// Reverse mode through the last rollout on four warps per group of 32 instances (compiled
+// topology, whole tape): every step by mw_reverse_step, last first.
 template <class Q>
 __global__ void __launch_bounds__(128, 1) k_backward_mw(const __grid_constant__ DevTopo T, const __grid_constant__ DevPtrs D) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -482,67 +575,60 @@ __global__ void __launch_bounds__(128, 1) k_backward_mw(const __grid_constant__ 
   const size_t sbytes = (size_t)nf * Bp;
   const int Tw = warp_horizon(D, i);  // the same for the CTA's four warps (same instances)
   for (int t = Tw - 1; t >= 0; --t) {
-    const RevStep<GSR> V = rev_views<GSR>(T, D, C, t, t);
-    const float* x_t = D.ckpt + (size_t)t * sbytes;
     // x_{t+1} is on chip from the previous (later) step, except for the first one reversed
-    if (t == Tw - 1) {
-      const float* x_t1 = t + 1 < Tw ? D.ckpt + (size_t)(t + 1) * sbytes : D.state;
-      for (int f = warp; f < nf; f += 4) C.X[f] = x_t1[(size_t)f * Bp + i];
-    }
-    if (warp == 0 && t > 0) prefetch_record_l2(T, tape_step(T, D, t - 1).rec);  // the next step to reverse
-    if (T.grad_decay != 1.f) {  // section 3.2: the adjoint from later steps shrinks by alpha per step
-      for (int f = warp; f < nf; f += 4) C.XB[f] *= T.grad_decay;
-      if (warp == 0)
-        for (int k = 0; k < T.n_rec; ++k) C.S[T.sm_hb + k] *= T.grad_decay;  // and so does h's
-    }
+    const float* x_t1 = t + 1 < Tw ? D.ckpt + (size_t)(t + 1) * sbytes : D.state;
+    mw_reverse_step<Q>(T, D, C, t, x_t1, t == Tw - 1, warp, bm, jm);
+  }
+  if (warp != 0) return;
+  if (T.loss_kind == 3) loss_initial_reverse(T, D, C);
+  for (int f = 0; f < nf; ++f) D.grad_state0[(size_t)f * Bp + i] = C.XB[f];
+}
+
+// The wide controller's per-step reverse launches (k_backward_ext) on four warps per group of 32
+// instances (compiled topology, whole tape): the feature adjoint of x_{t+1} (joint kinematics split
+// by joint owner, the features' and hinges' reverse on warp 0), then mw_reverse_step of step t.
+template <class Q>
+__global__ void __launch_bounds__(128, 1) k_backward_ext_mw(const __grid_constant__ DevTopo T,
+                                                           const __grid_constant__ DevPtrs D, int t) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
+  const int Bp = T.Bp;
+  const int nf = 18 * T.nb;
+  float* sm = g_smem + lane;
+  BwdCtx C{SL{sm}, SL{sm + T.sm_x * 32}, SL{sm + T.sm_xb * 32}, SL{sm + T.sm_vb * 32}, SL{sm + T.sm_rc * 32},
+           SL{sm + T.sm_sbar * 32}, GC{D.prm + i, Bp}, GL{D.grad_prm + i, Bp}, i, D.dloss[i]};
+  const uint32_t bm = T.mw_bmask[warp], jm = T.mw_jmask[warp];
+  const int Tw = warp_horizon(D, i);  // the same for the CTA's four warps
+  if (t >= Tw) return;                // this group's rollout ended before step t
+  const size_t sbytes = (size_t)nf * Bp;
+  for (int f = warp; f < nf; f += 4) C.XB[f] = D.grad_state0[(size_t)f * Bp + i];
+  const int tn = t + 1;
+  if (tn < Tw) {  // adjoint of the features of x_{t+1}
+    const float* xs = D.ckpt + (size_t)tn * sbytes;
+    for (int f = warp; f < nf; f += 4) C.X[f] = xs[(size_t)f * Bp + i];
     mw_barrier();
-    // loss term (by the loss body's owner) and integrator, x_{t+1} on chip
-    if (T.mw_own[T.loss_body] == warp) loss_reverse(T, V.Bl, C.X, C.XB, loss_weight(T, t + 1, D.hz[i]) * C.dl);
-    integrate_reverse(T, GC{x_t + i, Bp}, C.X, C.XB, C.VB, bm);
-    mw_barrier();
-    // x_t on chip; accumulators zeroed
-    for (int f = warp; f < nf; f += 4) C.X[f] = x_t[(size_t)f * Bp + i];
+    LaneT<GSR> L{C.S, C.P, GSR{D.ckpt}, i};
+    BLaneT<GSR> Bl{L, C.X, C.G, GC{D.ckpt, 32}};
+    hinge_kinematics(T, L, C.X, jm);
     for (int j = 0; j < T.nj; ++j) {
       if (!((jm >> j) & 1u)) continue;
       C.S[T.sm_thb + j] = 0.f; C.S[T.sm_thdb + j] = 0.f; C.S[T.sm_wstb + j] = 0.f;
       C.S.s3(T.sm_uab + 3 * j, f3(0.f, 0.f, 0.f));
     }
-    for (int b = 0; b < T.nb; ++b) {
-      if (!((bm >> b) & 1u)) continue;
-      C.S[T.sm_invmb + b] = 0.f;
-      for (int q = 0; q < 9; ++q) C.S[T.sm_iinvb + 9 * b + q] = 0.f;
+    mw_barrier();
+    if (warp == 0) {
+      features_reverse(T, Bl, C.XB, GC{D.sbar_ext + (size_t)i * T.ext_k0p, 1});
+      hinge_reverse(T, Bl, C.XB);
     }
-    for (int q = warp; q < T.nslots * RC_N; q += 4) C.RC[q] = 0.f;
     mw_barrier();
-    // per-step forward quantities of x_t, recomputed bit-identically
-    hinge_kinematics(T, V.L, C.X, jm);
-    servo_targets(T, V.L, V.act[T.n_layers > 0 ? T.n_layers : 0], jm);
-    inverse_inertia(T, V.L, C.X, bm);
-    mw_barrier();
-    pgs_reverse_mw<Q>(T, V.L, V.tp, warp);
-    if (T.ws) {
-      ws_apply_reverse_own(T, V.L, C.VB, C.RC, V.tp, warp);
-      mw_barrier();
-    }
-    rows_reverse_own(T, V.Bl, C.XB, C.VB, C.RC, warp);
-    mw_barrier();
-    external_reverse(T, V.Bl, C.XB, C.VB, bm);
-    mw_barrier();
-    reverse_step_ctrl_mw<Q>(T, D, C, V, warp);
   }
-  if (warp != 0) return;
-  if (T.loss_kind == 3) {  // initial term -a.q(x_0) of the displacement loss
-    copy_state_to_smem(T, D.ckpt, i, C.X);
-    const int b = T.loss_body;
-    M3 R = loadR(C.X, 18 * b);
-    float3 c = C.P.v3(T.o_loss_point), a = C.P.v3(T.o_loss_target);
-    float3 gq = -C.dl * a;
-    C.XB.a3(18 * b, gq);
-    add_outer(C.XB, 18 * b + 3, gq, c);
-    C.G.red3(T.o_loss_point, mtv(R, gq));
-    C.G.red3(T.o_loss_target, -C.dl * (C.X.v3(18 * b) + mv(R, c)));
+  if (t >= 0) {
+    mw_reverse_step<Q>(T, D, C, t, D.state, tn >= Tw, warp, bm, jm);
+  } else {
+    if (warp == 0 && T.loss_kind == 3) loss_initial_reverse(T, D, C);
+    mw_barrier();
   }
-  for (int f = 0; f < nf; ++f) D.grad_state0[(size_t)f * Bp + i] = C.XB[f];
+  for (int f = warp; f < nf; f += 4) D.grad_state0[(size_t)f * Bp + i] = C.XB[f];
 }
 
 // Wide controller, reverse mode one step per launch. Launch t adds the adjoint of the input
@@ -579,16 +665,8 @@ __global__ void __launch_bounds__(32, 1) k_backward_ext(const __grid_constant__ 
   }
   if (t >= 0) {
     reverse_step<Q, GSR>(T, D, C, t, t, D.ckpt + (size_t)t * sbytes, tn < Tw ? D.ckpt + (size_t)tn * sbytes : D.state);
-  } else if (T.loss_kind == 3) {  // initial term -a.q(x_0) of the displacement loss
-    copy_state_to_smem(T, D.ckpt, i, C.X);
-    const int b = T.loss_body;
-    M3 R = loadR(C.X, 18 * b);
-    float3 c = C.P.v3(T.o_loss_point), a = C.P.v3(T.o_loss_target);
-    float3 gq = -C.dl * a;
-    C.XB.a3(18 * b, gq);
-    add_outer(C.XB, 18 * b + 3, gq, c);
-    C.G.red3(T.o_loss_point, mtv(R, gq));
-    C.G.red3(T.o_loss_target, -C.dl * (C.X.v3(18 * b) + mv(R, c)));
+  } else if (T.loss_kind == 3) {
+    loss_initial_reverse(T, D, C);
   }
   for (int f = 0; f < nf; ++f) D.grad_state0[(size_t)f * Bp + i] = C.XB[f];
 }

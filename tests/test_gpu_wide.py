@@ -95,3 +95,37 @@ def test_wide_controller_gradients_match_oracle():
             e = elem_err(g[k][i], go[k])
             assert e <= 1e-3, (i, k, e)
     assert elem_err(g["W"], Wsum) <= 1e-3, elem_err(g["W"], Wsum)
+
+
+@pytest.mark.parametrize("warm", [False, True])
+def test_wide_path_four_warp_kernels_match_single_warp(monkeypatch, warm):
+    """The wide path's per-step launches of the compiled topology run on four warps per group of
+    32 instances; the one-warp kernels (forced here) must give the same trajectory, activity log
+    and losses bit for bit (the forward kernels share every sum's order), and the same gradients
+    up to the order of the reverse pass's sums (64-1024-1024-8 controller; cold and damped
+    start)."""
+    from paper_1611_01652_gb300.binding import CTRL_WIDE, WS_PARAMS
+
+    m = WL.quadruped(B=40, horizon=12, widths=WIDE)
+    outs = []
+    for single in (False, True):
+        if single:
+            monkeypatch.setenv("DP_SINGLE_WARP_FORWARD", "1")
+            monkeypatch.setenv("DP_SINGLE_WARP_BACKWARD", "1")
+        w = World(m, horizon=12, iters=10 if warm else 20, warmstart=warm)
+        assert w.controller_kind == CTRL_WIDE
+        if warm:
+            w.set_warmstart(torch.zeros(WS_PARAMS, device="cuda"), 0.7)
+        tr = torch.zeros(13, m.B, m.nb, 18, device="cuda")
+        act = torch.zeros(12, m.B, w.n_slots, dtype=torch.uint8, device="cuda")
+        loss = torch.zeros(m.B, device="cuda")
+        w.rollout(torch.tensor(m.W, device="cuda"), loss, tr, act)
+        dW = torch.zeros(w.n_params, device="cuda")
+        ds = torch.zeros(m.B, m.nb, 18, device="cuda")
+        w.backward(torch.ones(m.B, device="cuda"), dW, ds)
+        w.sync()
+        outs.append([x.cpu().numpy() for x in (tr, act, loss, dW, ds)])
+    for a, b in zip(outs[0][:3], outs[1][:3]):
+        assert np.array_equal(a, b)
+    for a, b in zip(outs[0][3:], outs[1][3:]):
+        assert rel_err(a, b) <= 1e-4, rel_err(a, b)
