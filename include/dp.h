@@ -203,9 +203,10 @@ dp_status dp_backward(dp_world* w, const float* dloss, float* dW, float* dstate0
 
 /*
  * dp_backward_noalloc: dL/dW through the last dp_rollout, for callers that must not allocate
- * device memory once they are running, such as a training loop replayed from a captured CUDA
- * graph or an application that fixes its device memory up front. The paper has no counterpart
- * to this call.
+ * device memory once they are running: an application that reserves all of its device memory up
+ * front (a fixed budget shared with other processes, or a pool that owns the GPU), or one that
+ * runs on a thread or in a phase where an allocation could block or fail. The paper has no
+ * counterpart to this call.
  *
  * It computes the same controller gradient as dp_backward (the other gradients are not
  * produced) and calls no cudaMalloc, cudaFree or other allocating routine: besides the world's

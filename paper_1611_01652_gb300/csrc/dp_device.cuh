@@ -22,7 +22,9 @@
 #define DPK_ST_NAN_STATE 1
 #define DPK_ST_NAN_GRAD 2
 // rows per chunk of the multi-warp reverse sweep's hand-off ring (dp_mw.cuh)
+#ifndef DPK_MW_CH
 #define DPK_MW_CH 20
+#endif
 
 // Warm-start group types (feature 15 of a group).
 enum { WSG_GROUND = 0, WSG_PAIR = 1, WSG_JOINT = 2, WSG_HINGE = 3 };
@@ -174,6 +176,8 @@ __device__ __forceinline__ TapeStep tape_step(const DevTopo& T, const DevPtrs& D
   p.lam0 = (float*)(rec + T.rec_lam0) + lane;
   return p;
 }
+// Pulls the 128-byte line holding p into L2 (fire-and-forget).
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 // Bulk prefetch of a tape record into L2 (issued by one lane; fire-and-forget).
 __device__ __forceinline__ void prefetch_record_l2(const DevTopo& T, const uint8_t* rec) {
   if ((threadIdx.x & 31) != 0) return;

@@ -183,16 +183,18 @@ __device__ __noinline__ void pgs_reverse_chain(const DevTopo& T, const LaneT<GSR
           bool active = true;
           if constexpr (maybe_inactive<kind>()) active = (live[s >> 5] >> (s & 31)) & 1u;
           if (active) {
-            float3 lin;
-            if constexpr (lin_is_constant<kind, sub>()) lin = const_lin<kind, sub>();
-            else lin = f3(0.f, 0.f, 0.f);
+            constexpr int ax = lin_axis<kind, sub>();  // a unit axis or none (no sphere pairs here)
             float dbar = 0.f;
-            if constexpr (a >= 0)
-              dbar += im[a] * (lin.x * vb[a][0] + lin.y * vb[a][1] + lin.z * vb[a][2]) +
-                      (cur.IA.x * vb[a][3] + cur.IA.y * vb[a][4] + cur.IA.z * vb[a][5]);
-            if constexpr (b >= 0)
-              dbar += -im[b] * (lin.x * vb[b][0] + lin.y * vb[b][1] + lin.z * vb[b][2]) +
-                      (cur.IB.x * vb[b][3] + cur.IB.y * vb[b][4] + cur.IB.z * vb[b][5]);
+            if constexpr (a >= 0) {
+              const float wa = cur.IA.x * vb[a][3] + cur.IA.y * vb[a][4] + cur.IA.z * vb[a][5];
+              if constexpr (ax >= 0) dbar += im[a] * vb[a][ax] + wa;
+              else dbar += wa;
+            }
+            if constexpr (b >= 0) {
+              const float wb = cur.IB.x * vb[b][3] + cur.IB.y * vb[b][4] + cur.IB.z * vb[b][5];
+              if constexpr (ax >= 0) dbar += -im[b] * vb[b][ax] + wb;
+              else dbar += wb;
+            }
             const float lbar_a = LB[s] + dbar;  // adjoint of the row's new impulse
             const int br = cur.br;
             const float pbar = br == 0 ? lbar_a : 0.f;
@@ -207,14 +209,12 @@ __device__ __noinline__ void pgs_reverse_chain(const DevTopo& T, const LaneT<GSR
             const float meff = cur.meff;
             const float jvb = -meff * pbar;
             if constexpr (a >= 0) {
-              vb[a][0] = fmaf(jvb, lin.x, vb[a][0]); vb[a][1] = fmaf(jvb, lin.y, vb[a][1]);
-              vb[a][2] = fmaf(jvb, lin.z, vb[a][2]);
+              if constexpr (ax >= 0) vb[a][ax] += jvb;
               vb[a][3] = fmaf(jvb, cur.angA.x, vb[a][3]); vb[a][4] = fmaf(jvb, cur.angA.y, vb[a][4]);
               vb[a][5] = fmaf(jvb, cur.angA.z, vb[a][5]);
             }
             if constexpr (b >= 0) {
-              vb[b][0] = fmaf(-jvb, lin.x, vb[b][0]); vb[b][1] = fmaf(-jvb, lin.y, vb[b][1]);
-              vb[b][2] = fmaf(-jvb, lin.z, vb[b][2]);
+              if constexpr (ax >= 0) vb[b][ax] -= jvb;
               vb[b][3] = fmaf(jvb, cur.angB.x, vb[b][3]); vb[b][4] = fmaf(jvb, cur.angB.y, vb[b][4]);
               vb[b][5] = fmaf(jvb, cur.angB.z, vb[b][5]);
             }
@@ -320,13 +320,11 @@ __device__ __forceinline__ void mw_side(const DevTopo& T, const SL& RC, const Mw
                                         float (&v)[6], float (&vb)[6], const float (&ii)[6], float im,
                                         float (&ib9)[9], float& imb) {
   constexpr int kind = Q::S.kind[s], sub = Q::S.sub[s];
-  float3 lin;
-  if constexpr (lin_is_constant<kind, sub>()) lin = const_lin<kind, sub>();
-  else lin = f3(0.f, 0.f, 0.f);
+  constexpr int ax = lin_axis<kind, sub>();  // the linear part: a unit axis or none
   const float sgn = SIDE_A ? 1.f : -1.f;  // J_v = +lin on side a, -lin on side b
   const float dl = in.la - in.lb;
   const float c = dl * im;
-  v[0] -= sgn * c * lin.x; v[1] -= sgn * c * lin.y; v[2] -= sgn * c * lin.z;
+  if constexpr (ax >= 0) v[ax] -= sgn * c;
   v[3] -= dl * in.I.x; v[4] -= dl * in.I.y; v[5] -= dl * in.I.z;
   // adjoint of M^-1 J^T: dl * v_bar (before the chain's update of this row)
   const float3 g = f3(dl * vb[3], dl * vb[4], dl * vb[5]);
@@ -334,10 +332,12 @@ __device__ __forceinline__ void mw_side(const DevTopo& T, const SL& RC, const Mw
   ib9[0] += g.x * in.ang.x; ib9[1] += g.x * in.ang.y; ib9[2] += g.x * in.ang.z;
   ib9[3] += g.y * in.ang.x; ib9[4] += g.y * in.ang.y; ib9[5] += g.y * in.ang.z;
   ib9[6] += g.z * in.ang.x; ib9[7] += g.z * in.ang.y; ib9[8] += g.z * in.ang.z;
-  if constexpr (!lin_is_zero<kind>()) imb += sgn * dl * (lin.x * vb[0] + lin.y * vb[1] + lin.z * vb[2]);
+  if constexpr (ax >= 0) imb += sgn * dl * vb[ax];
   // Jacobian adjoint from the row's J v term, and this side's share of J v
   angb += jvb * f3(v[3], v[4], v[5]);
-  const float jv = sgn * (lin.x * v[0] + lin.y * v[1] + lin.z * v[2]) + (in.ang.x * v[3] + in.ang.y * v[4] + in.ang.z * v[5]);
+  const float wj = in.ang.x * v[3] + in.ang.y * v[4] + in.ang.z * v[5];
+  float jv = wj;
+  if constexpr (ax >= 0) jv = sgn * v[ax] + wj;
   const int rc = s * RC_N;
   if constexpr (SIDE_A) {
     RC.a3(rc + RC_ANGA, angb);
@@ -347,7 +347,7 @@ __device__ __forceinline__ void mw_side(const DevTopo& T, const SL& RC, const Mw
     RC.a3(rc + RC_ANGB, angb);
     RC[rc + RC_LIN] += -pbar * jv;  // side b's share of the effective-mass adjoint (folded later)
   }
-  vb[0] = fmaf(sgn * jvb, lin.x, vb[0]); vb[1] = fmaf(sgn * jvb, lin.y, vb[1]); vb[2] = fmaf(sgn * jvb, lin.z, vb[2]);
+  if constexpr (ax >= 0) vb[ax] += sgn * jvb;
   vb[3] = fmaf(jvb, in.ang.x, vb[3]); vb[4] = fmaf(jvb, in.ang.y, vb[4]); vb[5] = fmaf(jvb, in.ang.z, vb[5]);
 }
 
@@ -486,15 +486,63 @@ __device__ void pgs_reverse_mw(const DevTopo& T, const LaneT<GSR>& L, const Tape
 // ws_apply_reverse and rows_reverse; rows with a non-constant linear Jacobian part (sphere
 // pairs) are not handled here (the multi-warp kernel is built only for topologies without them).
 
+// Does warp w own a side of slot s?
+__device__ __forceinline__ bool mw_owns_side(const DevTopo& T, int s, int w) {
+  const int a = T.sa[s], b = T.sb[s];
+  return (a >= 0 && T.mw_own[a] == w) || (b >= 0 && T.mw_own[b] == w);
+}
+// The next slot after s with a side owned by warp w (T.nslots if none).
+__device__ __forceinline__ int mw_next_owned(const DevTopo& T, int s, int w) {
+  for (++s; s < T.nslots; ++s)
+    if (mw_owns_side(T, s, w)) break;
+  return s;
+}
+// The row record of slot s (18 lines) into L1.
+__device__ __forceinline__ void mw_row_prefetch(const float* rows, int s) {
+#pragma unroll
+  for (int f = 0; f < RF_N; ++f) prefetch_l1(rows + (s * RF_N + f) * 32);
+}
+// The Jacobian lines of slot s (linear and both angular parts) into L1.
+__device__ __forceinline__ void mw_jac_prefetch(const float* rows, int s) {
+#pragma unroll
+  for (int f = RF_LIN; f < RF_IA; ++f) prefetch_l1(rows + (s * RF_N + f) * 32);
+}
+// The per-instance parameter lines the row-assembly reverse of slot s reads, into L1 (the
+// parameter array stays in L2 across steps; each field of a group is one 128-byte line).
+__device__ __forceinline__ void mw_param_prefetch(const DevTopo& T, const float* prm, int s) {
+  const int idx = T.sidx[s], Bp = T.Bp;
+  int f0 = -1, nf = 0;
+  switch (T.skind[s]) {
+    case RK_JLIN: f0 = T.o_anchor + 6 * idx; nf = 6; break;
+    case RK_JANG: f0 = T.o_axis + 6 * idx; nf = 6; break;
+    case RK_LIMIT: f0 = T.o_limit + 2 * idx; nf = 1; break;
+    case RK_GN:
+    case RK_GT:
+      f0 = T.o_sph_off + 3 * idx; nf = 3;
+      prefetch_l1(prm + (size_t)(T.o_sph_rad + idx) * Bp);
+      if (T.skind[s] == RK_GN) prefetch_l1(prm + (size_t)(T.o_sph_e + idx) * Bp);
+      break;
+    default: break;
+  }
+  for (int f = 0; f < nf; ++f) prefetch_l1(prm + (size_t)(f0 + f) * Bp);
+}
+
 // Reverse of the warm-start application v += M^-1 J^T lambda0, the sides this warp owns.
 template <class RV>
 __device__ void ws_apply_reverse_own(const DevTopo& T, const LaneT<RV>& L, const SL& VB, const SL& RC,
                                      const TapeStep& tp, int w) {
   const SL& S = L.S;
-  for (int s = 0; s < T.nslots; ++s) {
+  // the starting impulses of every slot this warp owns a side of, then the Jacobian lines of
+  // the next owned slot, into L1 ahead of their loads
+  for (int s = 0; s < T.nslots; ++s)
+    if (mw_owns_side(T, s, w)) prefetch_l1(tp.lam0 + s * 32);
+  int nx = mw_next_owned(T, -1, w);
+  if (nx < T.nslots) mw_jac_prefetch(L.rows.p, nx);
+  for (int s = nx; s < T.nslots; s = nx) {
+    nx = mw_next_owned(T, s, w);
+    if (nx < T.nslots) mw_jac_prefetch(L.rows.p, nx);
     const int a = T.sa[s], b = T.sb[s];
     const bool oa = a >= 0 && T.mw_own[a] == w, ob = b >= 0 && T.mw_own[b] == w;
-    if (!oa && !ob) continue;
     const float dl = tp.lam0[s * 32];
     if (dl == 0.f) continue;
     const RV R = L.rows.at(s * RF_N);
@@ -523,20 +571,6 @@ __device__ void ws_apply_reverse_own(const DevTopo& T, const LaneT<RV>& L, const
 
 // Row adjoints pushed back to positions, rotations, the solver's input velocities
 // (restitution), hinge axes/angles, servo targets and parameters: the parts this warp owns.
-// The next slot after s with a side owned by warp w (T.nslots if none).
-__device__ __forceinline__ int mw_next_owned(const DevTopo& T, int s, int w) {
-  for (++s; s < T.nslots; ++s) {
-    const int a = T.sa[s], b = T.sb[s];
-    if ((a >= 0 && T.mw_own[a] == w) || (b >= 0 && T.mw_own[b] == w)) break;
-  }
-  return s;
-}
-// The row record of slot s (18 lines) into L1.
-__device__ __forceinline__ void mw_row_prefetch(const float* rows, int s) {
-  if (s < 0) return;
-#pragma unroll
-  for (int f = 0; f < RF_N; ++f) prefetch_l1(rows + (s * RF_N + f) * 32);
-}
 
 template <class RV>
 __device__ void rows_reverse_own(const DevTopo& T, const BLaneT<RV>& B, const SL& XB, const SL& VB, const SL& RC, int w) {
@@ -546,10 +580,16 @@ __device__ void rows_reverse_own(const DevTopo& T, const BLaneT<RV>& B, const SL
   const float bh = T.beta / h;
   const float3 ez = f3(0.f, 0.f, 1.f);
   int nx = mw_next_owned(T, -1, w);
-  if (nx < T.nslots) mw_row_prefetch(L.rows.p, nx);
+  if (nx < T.nslots) {
+    mw_row_prefetch(L.rows.p, nx);
+    mw_param_prefetch(T, L.P.p, nx);
+  }
   for (int s = nx; s < T.nslots; s = nx) {
     nx = mw_next_owned(T, s, w);
-    if (nx < T.nslots) mw_row_prefetch(L.rows.p, nx);
+    if (nx < T.nslots) {
+      mw_row_prefetch(L.rows.p, nx);
+      mw_param_prefetch(T, L.P.p, nx);
+    }
     const int kind = T.skind[s], idx = T.sidx[s], sub = T.ssub[s], a = T.sa[s], b = T.sb[s];
     const bool oa = a >= 0 && T.mw_own[a] == w, ob = b >= 0 && T.mw_own[b] == w;
     const RV R = L.rows.at(s * RF_N);

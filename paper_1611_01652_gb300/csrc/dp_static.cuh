@@ -134,6 +134,18 @@ __device__ __forceinline__ float3 const_lin() {
   if (KIND == RK_GT) return f3(SUB == 0 ? 1.f : 0.f, SUB == 1 ? 1.f : 0.f, 0.f);
   return f3(0.f, 0.f, 0.f);
 }
+// The axis (0, 1, 2) of a constant linear Jacobian part that is a unit vector, -1 for rows
+// without a linear part, -2 when it is not a compile-time constant (sphere pairs). Products with
+// the part's zero components add exact zeros, which IEEE arithmetic does not let the compiler
+// drop (0 * x is not 0 for infinite or NaN x): the sweeps skip them. The sums are the same up to
+// where the compiler fuses a product into an add.
+template <int KIND, int SUB>
+__device__ __forceinline__ constexpr int lin_axis() {
+  if (KIND == RK_JLIN || KIND == RK_GT) return SUB;
+  if (KIND == RK_GN) return 2;
+  if (KIND == RK_JANG || KIND == RK_LIMIT || KIND == RK_MOTOR) return -1;
+  return -2;
+}
 template <int KIND>
 __device__ __forceinline__ constexpr bool lin_is_zero() {
   return KIND == RK_JANG || KIND == RK_LIMIT || KIND == RK_MOTOR;
@@ -165,19 +177,28 @@ __device__ void pgs_solve_static(const DevTopo& T, const LaneT<RV>& L, const SL&
       const RV R = L.rows.at(s * RF_N);
       const float meff = R[RF_MEFF];
       if (maybe_inactive<kind>() && !__any_sync(FULLMASK, meff != 0.f)) return;
-      float3 lin;
-      if (lin_is_constant<kind, sub>()) lin = const_lin<kind, sub>();
-      else if (lin_is_zero<kind>()) lin = f3(0.f, 0.f, 0.f);
-      else lin = R.v3(RF_LIN);
+      constexpr int ax = lin_axis<kind, sub>();
+      float3 lin = f3(0.f, 0.f, 0.f);
+      if constexpr (ax == -2) lin = R.v3(RF_LIN);
       float Jv = 0.f;
       float3 angA = f3(0.f, 0.f, 0.f), angB = angA;
       if (a >= 0) {
         angA = R.v3(RF_ANGA);
-        Jv += lin.x * v[a][0] + lin.y * v[a][1] + lin.z * v[a][2] + angA.x * v[a][3] + angA.y * v[a][4] + angA.z * v[a][5];
+        if constexpr (ax >= 0)
+          Jv += v[a][ax] + angA.x * v[a][3] + angA.y * v[a][4] + angA.z * v[a][5];
+        else if constexpr (ax == -1)
+          Jv += angA.x * v[a][3] + angA.y * v[a][4] + angA.z * v[a][5];
+        else
+          Jv += lin.x * v[a][0] + lin.y * v[a][1] + lin.z * v[a][2] + angA.x * v[a][3] + angA.y * v[a][4] + angA.z * v[a][5];
       }
       if (b >= 0) {
         angB = R.v3(RF_ANGB);
-        Jv += angB.x * v[b][3] + angB.y * v[b][4] + angB.z * v[b][5] - (lin.x * v[b][0] + lin.y * v[b][1] + lin.z * v[b][2]);
+        if constexpr (ax >= 0)
+          Jv += angB.x * v[b][3] + angB.y * v[b][4] + angB.z * v[b][5] - v[b][ax];
+        else if constexpr (ax == -1)
+          Jv += angB.x * v[b][3] + angB.y * v[b][4] + angB.z * v[b][5];
+        else
+          Jv += angB.x * v[b][3] + angB.y * v[b][4] + angB.z * v[b][5] - (lin.x * v[b][0] + lin.y * v[b][1] + lin.z * v[b][2]);
       }
       const float l0 = lam[s];
       const float pre = l0 - meff * (Jv + R[RF_BIAS] + gamma * l0);
@@ -203,13 +224,21 @@ __device__ void pgs_solve_static(const DevTopo& T, const LaneT<RV>& L, const SL&
       if (a >= 0) {
         const float c = dl * im[a];
         const float3 IA = R.v3(RF_IA);
-        v[a][0] += c * lin.x; v[a][1] += c * lin.y; v[a][2] += c * lin.z;
+        if constexpr (ax >= 0) {
+          v[a][ax] += c;
+        } else if constexpr (ax == -2) {
+          v[a][0] += c * lin.x; v[a][1] += c * lin.y; v[a][2] += c * lin.z;
+        }
         v[a][3] += dl * IA.x; v[a][4] += dl * IA.y; v[a][5] += dl * IA.z;
       }
       if (b >= 0) {
         const float c = dl * im[b];
         const float3 IB = R.v3(RF_IB);
-        v[b][0] -= c * lin.x; v[b][1] -= c * lin.y; v[b][2] -= c * lin.z;
+        if constexpr (ax >= 0) {
+          v[b][ax] -= c;
+        } else if constexpr (ax == -2) {
+          v[b][0] -= c * lin.x; v[b][1] -= c * lin.y; v[b][2] -= c * lin.z;
+        }
         v[b][3] += dl * IB.x; v[b][4] += dl * IB.y; v[b][5] += dl * IB.z;
       }
       if (TAPE) {

@@ -493,6 +493,18 @@ __global__ void __launch_bounds__(32, 1) k_backward(const __grid_constant__ DevT
 // barrier): step t from its tape record and x_t from the checkpoints, with x_{t+1} on chip in
 // C.X (copied there first from x_t1 when load_x1 is set); the state adjoint in C.XB is that of
 // x_{t+1} on entry and that of x_t on exit.
+// Step t's state checkpoint and controller columns of this CTA's 32 instances into L2, one
+// 128-byte line per field, spread over the CTA's threads (the reverse of step t + 1 runs
+// meanwhile).
+__device__ __forceinline__ void mw_prefetch_step_l2(const DevTopo& T, const DevPtrs& D, int t) {
+  const int Bp = T.Bp, nf = 18 * T.nb, base = blockIdx.x * 32;
+  const float* x = D.ckpt + (size_t)t * nf * Bp + base;
+  for (int f = threadIdx.x; f < nf; f += blockDim.x) prefetch_l2(x + (size_t)f * Bp);
+  const size_t N = (size_t)T.horizon * Bp;
+  const float* d = D.dump + (size_t)t * Bp + base;
+  for (int r = threadIdx.x; r < T.dump_rows; r += blockDim.x) prefetch_l2(d + (size_t)r * N);
+}
+
 template <class Q>
 __device__ void mw_reverse_step(const DevTopo& T, const DevPtrs& D, const BwdCtx& C, int t, const float* x_t1,
                                 bool load_x1, int warp, uint32_t bm, uint32_t jm) {
@@ -502,7 +514,10 @@ __device__ void mw_reverse_step(const DevTopo& T, const DevPtrs& D, const BwdCtx
   const float* x_t = D.ckpt + (size_t)t * sbytes;
   if (load_x1)
     for (int f = warp; f < nf; f += 4) C.X[f] = x_t1[(size_t)f * Bp + i];
-  if (warp == 0 && t > 0) prefetch_record_l2(T, tape_step(T, D, t - 1).rec);  // the next step to reverse
+  if (t > 0) {  // the next step to reverse: its tape record, state checkpoint and controller columns
+    if (warp == 0) prefetch_record_l2(T, tape_step(T, D, t - 1).rec);
+    mw_prefetch_step_l2(T, D, t - 1);
+  }
   if (T.grad_decay != 1.f) {  // section 3.2: the adjoint from later steps shrinks by alpha per step
     for (int f = warp; f < nf; f += 4) C.XB[f] *= T.grad_decay;
     if (warp == 0)

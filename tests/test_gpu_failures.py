@@ -8,6 +8,8 @@
   returned, and the next world created and rolled out normally;
 * a reverse pass without a rollout: DP_ESTATE, nothing enqueued.
 """
+import gc
+
 import numpy as np
 import pytest
 
@@ -75,6 +77,9 @@ def test_nan_loss_adjoint_flags_that_gradient_only():
 
 
 def test_allocation_failure_is_enomem_and_releases_everything():
+    # worlds of earlier tests that are still unreferenced would otherwise be collected (and
+    # their device memory freed) while the failing creation runs
+    gc.collect()
     torch.cuda.synchronize()
     free0 = torch.cuda.mem_get_info()[0]
     # a state checkpoint every step of a 2,000,000-step horizon: 330 GB of checkpoints alone
@@ -84,7 +89,7 @@ def test_allocation_failure_is_enomem_and_releases_everything():
     assert e.value.status == DP_ENOMEM, e.value
     torch.cuda.synchronize()
     free1 = torch.cuda.mem_get_info()[0]
-    assert abs(free1 - free0) <= 8 << 20, (free0, free1)
+    assert free1 >= free0 - (8 << 20), (free0, free1)  # nothing the failed creation took is kept
     w, loss = rollout(WL.quadruped(B=B, horizon=T))
     w.sync()
     assert torch.isfinite(loss).all()

@@ -1,6 +1,6 @@
 """dp_backward_noalloc: the controller gradient for callers that cannot allocate device memory
-while they run (a training loop replayed from a captured CUDA graph, an application whose
-device memory is fixed up front). Its scratch is a static device array instead of a buffer
+while they run (an application that reserves its device memory up front, or runs where an
+allocation could block or fail). Its scratch is a static device array instead of a buffer
 allocated for the world; its result must equal dp_backward's, call after call.
 
 Kept in a file of its own that pytest collects last."""
