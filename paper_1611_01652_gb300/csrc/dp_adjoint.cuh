@@ -500,6 +500,11 @@ __device__ void external_reverse(const DevTopo& T, const BLaneT<RV>& B, const SL
                                  uint32_t bmask = 0xffffffffu) {
   const SL& S = B.L.S;
   const float h = T.dt;
+  for (int b = 0; b < T.nb; ++b)  // the bodies' inertia and mass parameter lines into L1
+    if ((bmask >> b) & 1u) {
+      for (int k = 0; k < 3; ++k) prefetch_l1(B.L.P.p + (size_t)(T.o_inertia + 3 * b + k) * B.L.P.s);
+      prefetch_l1(B.L.P.p + (size_t)(T.o_mass + b) * B.L.P.s);
+    }
   for (int b = 0; b < T.nb; ++b) {
     if (!((bmask >> b) & 1u)) continue;
     M3 R = loadRg(B.X0, 18 * b);

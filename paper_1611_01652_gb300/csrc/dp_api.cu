@@ -359,6 +359,15 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
     for (int g = 0; g < 4; ++g) T.mw_bmask[g] = T.mw_jmask[g] = 0u;
     for (int b = 0; b < T.nb; ++b) T.mw_bmask[T.mw_own[b]] |= 1u << b;
     for (int j = 0; j < T.nj; ++j) T.mw_jmask[T.mw_own[T.jb[j]]] |= 1u << j;
+    // each warp's slots with an owned side, in slot order, and which sides it owns
+    for (int g = 0; g < 4; ++g) {
+      int n = 0;
+      for (int q = 0; q < T.nslots; ++q) {
+        const bool oa = T.sa[q] >= 0 && T.mw_own[T.sa[q]] == g, ob = T.sb[q] >= 0 && T.mw_own[T.sb[q]] == g;
+        if (oa || ob) T.mw_slot[g][n++] = (int16_t)(q | (oa ? MW_SLOT_A : 0) | (ob ? MW_SLOT_B : 0));
+      }
+      T.mw_nslot[g] = (int16_t)n;
+    }
   }
   // warm-start groups, in slot order of their first row
   T.n_wsg = 0;

@@ -26,6 +26,10 @@
 #define DPK_MW_CH 20
 #endif
 
+// Flags of DevTopo.mw_slot entries (the slot index takes the low 12 bits).
+#define MW_SLOT_A 0x1000
+#define MW_SLOT_B 0x2000
+
 // Warm-start group types (feature 15 of a group).
 enum { WSG_GROUND = 0, WSG_PAIR = 1, WSG_JOINT = 2, WSG_HINGE = 3 };
 
@@ -93,6 +97,10 @@ struct DevTopo {
   // stages outside the sweeps, and the matching body / joint (by child body) masks per warp
   int8_t mw_own[DPK_MAXB];
   uint32_t mw_bmask[4], mw_jmask[4];
+  // per warp, the slots with a side it owns in slot order: slot | MW_SLOT_A (owns side a) |
+  // MW_SLOT_B (owns side b)
+  int16_t mw_slot[4][DPK_MAXSLOT];
+  int16_t mw_nslot[4];
   // activation/delta dump offsets (rows of [feature][T*Bp]); act l = input of layer l
   int dump_act[DPK_MAXL + 1], dump_del[DPK_MAXL + 1], dump_rows;
   // tape record of one (step, warp), lanes interleaved ([field][32]): byte offsets
@@ -176,6 +184,8 @@ __device__ __forceinline__ TapeStep tape_step(const DevTopo& T, const DevPtrs& D
   p.lam0 = (float*)(rec + T.rec_lam0) + lane;
   return p;
 }
+// Pulls one 128-byte line (a warp's 32 contiguous lanes of one field) into L1 (fire-and-forget).
+__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
 // Pulls the 128-byte line holding p into L2 (fire-and-forget).
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 // Bulk prefetch of a tape record into L2 (issued by one lane; fire-and-forget).

@@ -253,8 +253,6 @@ __device__ __forceinline__ constexpr int mw_local(int body) {
   return n;
 }
 
-// Pulls one 128-byte line (a warp's 32 contiguous lanes of one tape field) into L1.
-__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
 
 // The row sides of helper H's bodies in reverse sweep order: reverse position and side. The
 // helper's loop is unrolled over this sequence, so slots, sides and its bodies' registers are
@@ -486,17 +484,6 @@ __device__ void pgs_reverse_mw(const DevTopo& T, const LaneT<GSR>& L, const Tape
 // ws_apply_reverse and rows_reverse; rows with a non-constant linear Jacobian part (sphere
 // pairs) are not handled here (the multi-warp kernel is built only for topologies without them).
 
-// Does warp w own a side of slot s?
-__device__ __forceinline__ bool mw_owns_side(const DevTopo& T, int s, int w) {
-  const int a = T.sa[s], b = T.sb[s];
-  return (a >= 0 && T.mw_own[a] == w) || (b >= 0 && T.mw_own[b] == w);
-}
-// The next slot after s with a side owned by warp w (T.nslots if none).
-__device__ __forceinline__ int mw_next_owned(const DevTopo& T, int s, int w) {
-  for (++s; s < T.nslots; ++s)
-    if (mw_owns_side(T, s, w)) break;
-  return s;
-}
 // The row record of slot s (18 lines) into L1.
 __device__ __forceinline__ void mw_row_prefetch(const float* rows, int s) {
 #pragma unroll
@@ -533,16 +520,16 @@ __device__ void ws_apply_reverse_own(const DevTopo& T, const LaneT<RV>& L, const
                                      const TapeStep& tp, int w) {
   const SL& S = L.S;
   // the starting impulses of every slot this warp owns a side of, then the Jacobian lines of
-  // the next owned slot, into L1 ahead of their loads
-  for (int s = 0; s < T.nslots; ++s)
-    if (mw_owns_side(T, s, w)) prefetch_l1(tp.lam0 + s * 32);
-  int nx = mw_next_owned(T, -1, w);
-  if (nx < T.nslots) mw_jac_prefetch(L.rows.p, nx);
-  for (int s = nx; s < T.nslots; s = nx) {
-    nx = mw_next_owned(T, s, w);
-    if (nx < T.nslots) mw_jac_prefetch(L.rows.p, nx);
+  // the slots two places ahead in the warp's list, into L1 ahead of their loads
+  const int n = T.mw_nslot[w];
+  const int16_t* lst = T.mw_slot[w];
+  for (int k = 0; k < n; ++k) prefetch_l1(tp.lam0 + (lst[k] & 0xfff) * 32);
+  for (int k = 0; k < 2 && k < n; ++k) mw_jac_prefetch(L.rows.p, lst[k] & 0xfff);
+  for (int k = 0; k < n; ++k) {
+    if (k + 2 < n) mw_jac_prefetch(L.rows.p, lst[k + 2] & 0xfff);
+    const int e = lst[k], s = e & 0xfff;
     const int a = T.sa[s], b = T.sb[s];
-    const bool oa = a >= 0 && T.mw_own[a] == w, ob = b >= 0 && T.mw_own[b] == w;
+    const bool oa = e & MW_SLOT_A, ob = e & MW_SLOT_B;
     const float dl = tp.lam0[s * 32];
     if (dl == 0.f) continue;
     const RV R = L.rows.at(s * RF_N);
@@ -579,19 +566,21 @@ __device__ void rows_reverse_own(const DevTopo& T, const BLaneT<RV>& B, const SL
   const float h = T.dt;
   const float bh = T.beta / h;
   const float3 ez = f3(0.f, 0.f, 1.f);
-  int nx = mw_next_owned(T, -1, w);
-  if (nx < T.nslots) {
-    mw_row_prefetch(L.rows.p, nx);
-    mw_param_prefetch(T, L.P.p, nx);
+  // the row and parameter lines of the slots two places ahead in the warp's list into L1
+  const int n = T.mw_nslot[w];
+  const int16_t* lst = T.mw_slot[w];
+  for (int k = 0; k < 2 && k < n; ++k) {
+    mw_row_prefetch(L.rows.p, lst[k] & 0xfff);
+    mw_param_prefetch(T, L.P.p, lst[k] & 0xfff);
   }
-  for (int s = nx; s < T.nslots; s = nx) {
-    nx = mw_next_owned(T, s, w);
-    if (nx < T.nslots) {
-      mw_row_prefetch(L.rows.p, nx);
-      mw_param_prefetch(T, L.P.p, nx);
+  for (int k = 0; k < n; ++k) {
+    if (k + 2 < n) {
+      mw_row_prefetch(L.rows.p, lst[k + 2] & 0xfff);
+      mw_param_prefetch(T, L.P.p, lst[k + 2] & 0xfff);
     }
+    const int e = lst[k], s = e & 0xfff;
     const int kind = T.skind[s], idx = T.sidx[s], sub = T.ssub[s], a = T.sa[s], b = T.sb[s];
-    const bool oa = a >= 0 && T.mw_own[a] == w, ob = b >= 0 && T.mw_own[b] == w;
+    const bool oa = e & MW_SLOT_A, ob = e & MW_SLOT_B;
     const RV R = L.rows.at(s * RF_N);
     const float meff = R[RF_MEFF];
     if (meff == 0.f) continue;  // inactive on this lane: constant row

@@ -493,16 +493,19 @@ __global__ void __launch_bounds__(32, 1) k_backward(const __grid_constant__ DevT
 // barrier): step t from its tape record and x_t from the checkpoints, with x_{t+1} on chip in
 // C.X (copied there first from x_t1 when load_x1 is set); the state adjoint in C.XB is that of
 // x_{t+1} on entry and that of x_t on exit.
-// Step t's state checkpoint and controller columns of this CTA's 32 instances into L2, one
+// Step t's state checkpoint and controller activations of this CTA's 32 instances into L2, one
 // 128-byte line per field, spread over the CTA's threads (the reverse of step t + 1 runs
 // meanwhile).
 __device__ __forceinline__ void mw_prefetch_step_l2(const DevTopo& T, const DevPtrs& D, int t) {
   const int Bp = T.Bp, nf = 18 * T.nb, base = blockIdx.x * 32;
   const float* x = D.ckpt + (size_t)t * nf * Bp + base;
   for (int f = threadIdx.x; f < nf; f += blockDim.x) prefetch_l2(x + (size_t)f * Bp);
+  // the controller's activation rows (its delta rows are written, not read, by the reverse)
+  if (T.n_layers == 0 || T.ext_ctrl) return;
   const size_t N = (size_t)T.horizon * Bp;
   const float* d = D.dump + (size_t)t * Bp + base;
-  for (int r = threadIdx.x; r < T.dump_rows; r += blockDim.x) prefetch_l2(d + (size_t)r * N);
+  for (int l = 0; l <= T.n_layers; ++l)
+    for (int r = threadIdx.x; r < T.widths[l]; r += blockDim.x) prefetch_l2(d + (size_t)(T.dump_act[l] + r) * N);
 }
 
 template <class Q>
