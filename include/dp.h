@@ -135,6 +135,12 @@ typedef struct {
                                      first outputs stay the motor signals. Needs n_layers >= 1,
                                      no skip layer, widths[0] >= features + H and
                                      widths[n_layers] >= motors + H. 0 = feed-forward. */
+  int32_t one_warp;               /* launch mapping (a configuration choice, not a change of the
+                                     method): 0 = four warps per group of 32 instances for the
+                                     recorded rollout and the reverse pass of the topologies the
+                                     library compiles (the quadruped, arms of 3-7 links) when the
+                                     whole solver tape is kept; 1 = one warp per group for every
+                                     launch. Other topologies always run one warp per group. */
 } dp_batch_desc;
 
 typedef struct dp_world dp_world; /* opaque; owned by the library */

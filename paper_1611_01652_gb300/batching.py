@@ -3,9 +3,10 @@
 Instances are binned by topology (one World per bin, since a world's kernels are specialised
 to one topology); inside a bin they are ordered by horizon, longest first, so that the 32
 instances of a warp have similar horizons and each warp steps only to its own longest one. Each
-bin gets the launch configuration an autotuner picked by timing short rollouts (constraint
-rows on chip or in global memory, whole solver tape or checkpoint segments, split count of the
-controller-gradient reduction). All bins run concurrently, each on its own stream, and the
+bin gets the launch configuration an autotuner picked by timing short rollouts: the mapping of
+a group of 32 instances (four warps, with the compiled topology's kernels, or one warp),
+constraint rows on chip or in global memory, whole solver tape or checkpoint segments, split
+count of the controller-gradient reduction. All bins run concurrently, each on its own stream, and the
 whole pass (every bin's rollout and reverse pass, and the sum of the controller gradients) can
 be captured once as a CUDA graph and replayed as a single launch.
 
@@ -27,8 +28,11 @@ def _order_by_horizon(m):
     return m.subset(perm), perm
 
 
-CANDIDATES = [dict(rows_global=rg, ckpt_every=ck, dw_splits=sp)
-              for rg, ck, sp in itertools.product((False, True), (0, 16), (64, 256))]
+# one warp per group of 32 instances with every row/tape/split choice; four warps per group (the
+# compiled topologies' kernels, which keep the rows on chip and the whole tape) with each split
+CANDIDATES = ([dict(rows_global=rg, ckpt_every=ck, dw_splits=sp, one_warp=True)
+               for rg, ck, sp in itertools.product((False, True), (0, 16), (64, 256))] +
+              [dict(rows_global=False, ckpt_every=0, dw_splits=sp, one_warp=False) for sp in (64, 256)])
 
 
 def autotune(m, W, horizon=64, reps=2, candidates=None, stream=None):
@@ -42,7 +46,7 @@ def autotune(m, W, horizon=64, reps=2, candidates=None, stream=None):
     s = stream or torch.cuda.current_stream()
     for cfg in candidates or CANDIDATES:
         w = World(short, stream=stream, horizon=horizon, ckpt_every=cfg["ckpt_every"], rows_global=cfg["rows_global"],
-                  dw_splits=cfg["dw_splits"])
+                  dw_splits=cfg["dw_splits"], one_warp=cfg["one_warp"])
         loss = torch.zeros(short.B, device="cuda")
         dl = torch.ones(short.B, device="cuda")
         dW = torch.zeros(w.n_params, device="cuda")
@@ -83,10 +87,11 @@ class UnevenBatch:
                 best, res = autotune(m, W, horizon=tune_horizon, stream=self.streams[k])
                 self.tuning[k] = res
             else:
-                best = dict(rows_global=False, ckpt_every=0, dw_splits=0)
+                best = dict(rows_global=False, ckpt_every=0, dw_splits=0, one_warp=False)
             self.config[k] = best
             self.worlds[k] = World(m, stream=self.streams[k], ckpt_every=best["ckpt_every"],
-                                   rows_global=best["rows_global"], dw_splits=best["dw_splits"])
+                                   rows_global=best["rows_global"], dw_splits=best["dw_splits"],
+                                   one_warp=best["one_warp"])
         n_params = self.worlds[self.keys[0]].n_params
         self.loss = {k: torch.zeros(self.models[k].B, device="cuda") for k in self.keys}
         self.dloss = {k: torch.ones(self.models[k].B, device="cuda") for k in self.keys}

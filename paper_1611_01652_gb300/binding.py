@@ -35,7 +35,7 @@ class BatchDesc(C.Structure):
                 ("ckpt_every", C.c_int32), ("loss_kind", C.c_int32), ("loss_mode", C.c_int32),
                 ("loss_body", C.c_int32), ("ctrl_fp32", C.c_int32), ("warmstart", C.c_int32),
                 ("horizons", PI), ("rows_global", C.c_int32), ("dw_splits", C.c_int32), ("grad_decay", C.c_float),
-                ("n_recurrent", C.c_int32)]
+                ("n_recurrent", C.c_int32), ("one_warp", C.c_int32)]
 
 WS_PARAMS = 5443
 WS_ROW = 19
@@ -148,11 +148,13 @@ class World:
     """A batch of robots with one topology living on the current CUDA device.
 
     ``model`` is any object with the attributes of ``workloads.Model``. All calls are ordered on
-    ``stream`` (a torch.cuda.Stream, default: the current stream at creation).
+    ``stream`` (a torch.cuda.Stream, default: the current stream at creation). ``rows_global``,
+    ``dw_splits`` and ``one_warp`` are launch-configuration choices (the descriptor fields of the
+    same names), which the results do not depend on beyond summation order.
     """
 
     def __init__(self, model, stream=None, ckpt_every=None, horizon=None, iters=None, warmstart=False,
-                 rows_global=False, dw_splits=0):
+                 rows_global=False, dw_splits=0, one_warp=False):
         import torch
 
         lib = load()
@@ -201,6 +203,7 @@ class World:
         d.horizons = i32(np.minimum(hz, d.horizon)) if hz is not None else None
         d.rows_global = int(bool(rows_global))
         d.dw_splits = int(dw_splits)
+        d.one_warp = int(bool(one_warp))
         d.grad_decay = float(getattr(model, "grad_decay", 1.0))
         d.n_recurrent = int(getattr(model, "n_recurrent", 0))
         self.n_recurrent = d.n_recurrent

@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libdphys.so")
-SOURCES = ["dp_bwd_mw.cu", "dp_fwd_mw.cu", "dp_fwd.cu", "dp_bwd.cu", "dp_bwd_ext.cu", "dp_kernels.cu", "dp_api.cu", "dp_noalloc.cu", "dp_wstrain.cu", "dp_ext.cu", "dp_camera.cu", "dp_peak.cu"]
+SOURCES = ["dp_bwd_mw_arm.cu", "dp_bwd_mw_arm2.cu", "dp_bwd_mw.cu", "dp_fwd_mw_arm.cu", "dp_fwd_mw.cu", "dp_fwd.cu", "dp_bwd.cu", "dp_bwd_ext.cu", "dp_kernels.cu", "dp_api.cu", "dp_noalloc.cu", "dp_wstrain.cu", "dp_ext.cu", "dp_camera.cu", "dp_peak.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-diag-suppress", "550"]

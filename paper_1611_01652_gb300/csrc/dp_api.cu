@@ -468,8 +468,10 @@ dp_status dp_create_world(const dp_batch_desc* d, void* stream, dp_world** out) 
   T.topo_id = match_compiled_topology(T, T.nb, T.nj, T.ns, T.np, d->joint_type, d->joint_body, d->joint_flags,
                                       d->sphere_body, d->pair_sphere);
   if (getenv("DP_FORCE_RUNTIME_TOPOLOGY")) T.topo_id = 0;
-  // the compiled topology's kernels carry the 128-wide tensor-core controller only
-  if (T.topo_id != 0 && T.widths[1] != 128) T.mlp_tc = 0;
+  T.one_warp = d->one_warp ? 1 : 0;
+  // a compiled topology's kernels carry one width of the tensor-core controller: another width
+  // runs on the SIMT path
+  if (T.topo_id != 0 && T.widths[1] != compiled_ctrl_width(T.topo_id)) T.mlp_tc = 0;
   w->n_params = np_;
   w->w_total = wtot;
   w->Tf = T;

@@ -13,8 +13,8 @@ static cudaError_t launch_backward_q(const DevTopo& T, const DevPtrs& D, cudaStr
 }
 cudaError_t launch_backward(const DevTopo& T, const DevPtrs& D, cudaStream_t s) {
   // compiled topology with the whole tape: the solver's reverse sweeps on four warps per group
-  if (T.topo_id == QuadrupedTopo::id && D.tape_full && !getenv("DP_SINGLE_WARP_BACKWARD"))
-    return launch_backward_mw_quadruped(T, D, s);
+  if (T.topo_id != 0 && D.tape_full && !T.one_warp && !getenv("DP_SINGLE_WARP_BACKWARD"))
+    return T.topo_id == QuadrupedTopo::id ? launch_backward_mw_quadruped(T, D, s) : launch_backward_mw_arm(T, D, s);
   if (T.topo_id == QuadrupedTopo::id) return launch_backward_q<QuadrupedTopo>(T, D, s);
   return launch_backward_q<DynTopo>(T, D, s);
 }

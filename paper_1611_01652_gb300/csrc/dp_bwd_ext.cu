@@ -21,7 +21,7 @@ static cudaError_t launch_backward_ext_mw_q(const DevTopo& T, const DevPtrs& D, 
   return cudaGetLastError();
 }
 cudaError_t launch_backward_ext(const DevTopo& T, const DevPtrs& D, int t, cudaStream_t s) {
-  if (T.topo_id == QuadrupedTopo::id && D.tape_full && !getenv("DP_SINGLE_WARP_BACKWARD"))
+  if (T.topo_id == QuadrupedTopo::id && D.tape_full && !T.one_warp && !getenv("DP_SINGLE_WARP_BACKWARD"))
     return launch_backward_ext_mw_q<QuadrupedTopo>(T, D, t, s);
   if (T.topo_id == QuadrupedTopo::id) return launch_backward_ext_q<QuadrupedTopo>(T, D, t, s);
   return launch_backward_ext_q<DynTopo>(T, D, t, s);

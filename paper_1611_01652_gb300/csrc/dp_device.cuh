@@ -56,6 +56,7 @@ struct DevTopo {
   int iters, horizon, features, imu_body, loss_kind, loss_mode, loss_body;
   int n_layers, skip, n_params, n_motors, ctrl_round;  // ctrl_round: 1 = bfloat16 storage points
   int topo_id;  // 0: run-time topology loops; otherwise the compiled topology with this id
+  int one_warp;  // 1: every launch on one warp per group (no four-warp kernels)
   int mlp_tc;   // 1: the controller is the 24-128-128-8 bfloat16 network, run on the tensor cores
   // 1: the controller is evaluated between step launches by batched tensor-core products over all
   // instances (wide bfloat16 networks); the step kernels read its output u_t and write the next

@@ -169,12 +169,12 @@ __device__ void controller_forward(const DevTopo& T, const DevPtrs& D, const AV*
   }
 }
 
-// Hidden widths of the tensor-core controller a kernel is built for: the compiled quadruped
-// topology carries the 128-wide networks only; the run-time topology every supported width.
+// Hidden widths of the tensor-core controller a kernel is built for: a compiled topology carries
+// one width (Q::CTRL_H); the run-time topology every supported width.
 template <class Q, class F>
 __device__ __forceinline__ void ctrl_tc_dispatch(const DevTopo& T, F&& f) {
   if constexpr (Q::id != 0) {
-    f(std::integral_constant<int, 128>{});
+    f(std::integral_constant<int, Q::CTRL_H>{});
   } else {
     if (T.widths[1] == 64) f(std::integral_constant<int, 64>{});
     else if (T.widths[1] == 128) f(std::integral_constant<int, 128>{});
@@ -208,17 +208,28 @@ __device__ __forceinline__ void ctrl_tc_forward(const DevTopo& T, const DevPtrs&
       },
       mt0, mt1);
 }
-// The run-time topology's kernels call each width out of line, so that the register needs of
-// the widest network do not fall on the whole persistent kernel.
+// The run-time topology's kernels (and the compiled ones with the 256-wide network) call the
+// controller out of line, so that the register needs of the widest network do not fall on the
+// whole persistent kernel.
 template <int H, class AV>
-__device__ __noinline__ void ctrl_tc_forward_call(const DevTopo& T, const DevPtrs& D, const AV* act, float* dump_col) {
-  ctrl_tc_forward<H, AV>(T, D, act, dump_col);
+__device__ __noinline__ void ctrl_tc_forward_call(const DevTopo& T, const DevPtrs& D, const AV* act, float* dump_col,
+                                                  int mt0 = 0, int mt1 = 2) {
+  ctrl_tc_forward<H, AV>(T, D, act, dump_col, mt0, mt1);
+}
+// Controller forward of a compiled topology's kernel (its one width), 16-row tiles mt0 .. mt1 - 1.
+template <class Q, class AV>
+__device__ __forceinline__ void ctrl_tc_forward_q(const DevTopo& T, const DevPtrs& D, const AV* act, float* dump_col,
+                                                  int mt0 = 0, int mt1 = 2) {
+  if constexpr (Q::CTRL_H <= 128)
+    ctrl_tc_forward<Q::CTRL_H, AV>(T, D, act, dump_col, mt0, mt1);
+  else
+    ctrl_tc_forward_call<Q::CTRL_H, AV>(T, D, act, dump_col, mt0, mt1);
 }
 template <class Q, class AV>
 __device__ void controller_forward_tc(const DevTopo& T, const DevPtrs& D, const AV* act, float* dump_col) {
   __syncwarp();
   if constexpr (Q::id != 0) {
-    ctrl_tc_forward<128, AV>(T, D, act, dump_col);
+    ctrl_tc_forward_q<Q, AV>(T, D, act, dump_col);
   } else {
     if (T.widths[1] == 64) ctrl_tc_forward_call<64, AV>(T, D, act, dump_col);
     else if (T.widths[1] == 128) ctrl_tc_forward_call<128, AV>(T, D, act, dump_col);

@@ -15,10 +15,13 @@ static cudaError_t launch_forward_t(const DevTopo& T, const DevPtrs& D, const fl
 cudaError_t launch_forward(const DevTopo& T, const DevPtrs& D, const float* x0, int t0, int nsteps, int rollout,
                            int record, cudaStream_t s) {
   // the compiled-topology path keeps its rows on chip; otherwise the run-time path. Its recorded
-  // rollouts run on four warps per group (not the harvest or gait noise).
-  if (T.topo_id == QuadrupedTopo::id && T.sm_rows >= 0 && record && rollout && !D.harvest && !D.u_noise &&
-      !T.ws_net && !getenv("DP_SINGLE_WARP_FORWARD"))
-    return launch_forward_mw_quadruped(T, D, x0, t0, nsteps, rollout, s);
+  // rollouts run on four warps per group (not the harvest or gait noise, and not when the world
+  // asks for one warp per group). The compiled arms have no one-warp kernels of their own: their
+  // other launches take the run-time path.
+  if (T.topo_id != 0 && T.sm_rows >= 0 && record && rollout && !D.harvest && !D.u_noise && !T.ws_net &&
+      !T.one_warp && !getenv("DP_SINGLE_WARP_FORWARD"))
+    return T.topo_id == QuadrupedTopo::id ? launch_forward_mw_quadruped(T, D, x0, t0, nsteps, rollout, s)
+                                          : launch_forward_mw_arm(T, D, x0, t0, nsteps, rollout, s);
   if (T.topo_id == QuadrupedTopo::id && T.sm_rows >= 0)
     return record ? launch_forward_t<SL, true, QuadrupedTopo>(T, D, x0, t0, nsteps, rollout, s)
                   : launch_forward_t<SL, false, QuadrupedTopo>(T, D, x0, t0, nsteps, rollout, s);

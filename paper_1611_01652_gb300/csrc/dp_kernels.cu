@@ -221,19 +221,33 @@ cudaError_t launch_pad_scalar(int B, int Bp, const float* src, float* dst, cudaS
   k_pad_scalar<<<(Bp + 127) / 128, 128, 0, s>>>(B, Bp, src, dst);
   return cudaGetLastError();
 }
-// Compiled topology matching a run-time one (0: none). The compiled schedule must also equal
-// the run-time schedule slot for slot.
+// Compiled topology Q matching a run-time one: its id, or 0. The compiled schedule must also
+// equal the run-time schedule slot for slot.
+template <class Q>
+static int match_one(const DevTopo& T, int nb, int nj, int ns, int np, const int* jtype, const int* jbody,
+                     const int* jflags, const int* sbody, const int* pair) {
+  if (!topo_matches<Q>(nb, nj, ns, np, jtype, jbody, jflags, sbody, pair)) return 0;
+  const SlotTab& S = Q::S;
+  if (S.n != T.nslots) return 0;
+  for (int q = 0; q < S.n; ++q)
+    if (S.kind[q] != T.skind[q] || S.a[q] != T.sa[q] || S.b[q] != T.sb[q] || S.order[q] != T.order[q] ||
+        S.normal[q] != T.snormal[q] || S.sub[q] != T.ssub[q] || S.idx[q] != T.sidx[q])
+      return 0;
+  return Q::id;
+}
 int match_compiled_topology(const DevTopo& T, int nb, int nj, int ns, int np, const int* jtype, const int* jbody,
                             const int* jflags, const int* sbody, const int* pair) {
-  if (topo_matches<QuadrupedTopo>(nb, nj, ns, np, jtype, jbody, jflags, sbody, pair)) {
-    const SlotTab& S = QuadrupedTopo::S;
-    if (S.n != T.nslots) return 0;
-    for (int q = 0; q < S.n; ++q)
-      if (S.kind[q] != T.skind[q] || S.a[q] != T.sa[q] || S.b[q] != T.sb[q] || S.order[q] != T.order[q] ||
-          S.normal[q] != T.snormal[q] || S.sub[q] != T.ssub[q] || S.idx[q] != T.sidx[q])
-        return 0;
-    return QuadrupedTopo::id;
-  }
+  int id = match_one<QuadrupedTopo>(T, nb, nj, ns, np, jtype, jbody, jflags, sbody, pair);
+  if (!id) id = match_one<ArmTopo<3>>(T, nb, nj, ns, np, jtype, jbody, jflags, sbody, pair);
+  if (!id) id = match_one<ArmTopo<4>>(T, nb, nj, ns, np, jtype, jbody, jflags, sbody, pair);
+  if (!id) id = match_one<ArmTopo<5>>(T, nb, nj, ns, np, jtype, jbody, jflags, sbody, pair);
+  if (!id) id = match_one<ArmTopo<6>>(T, nb, nj, ns, np, jtype, jbody, jflags, sbody, pair);
+  if (!id) id = match_one<ArmTopo<7>>(T, nb, nj, ns, np, jtype, jbody, jflags, sbody, pair);
+  return id;
+}
+int compiled_ctrl_width(int topo_id) {
+  if (topo_id == QuadrupedTopo::id) return QuadrupedTopo::CTRL_H;
+  if (topo_id >= ArmTopo<3>::id && topo_id <= ArmTopo<7>::id) return ArmTopo<3>::CTRL_H;
   return 0;
 }
 cudaError_t launch_dw(const float* del, const float* act, int M, int C, size_t N, float* partial, int splits,

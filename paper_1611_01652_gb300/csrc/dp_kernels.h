@@ -18,8 +18,11 @@ cudaError_t launch_forward(const DevTopo& T, const DevPtrs& D, const float* x0, 
                            int record, cudaStream_t s);
 cudaError_t launch_forward_mw_quadruped(const DevTopo& T, const DevPtrs& D, const float* x0, int t0, int nsteps,
                                         int rollout, cudaStream_t s);
+cudaError_t launch_forward_mw_arm(const DevTopo& T, const DevPtrs& D, const float* x0, int t0, int nsteps,
+                                  int rollout, cudaStream_t s);
 cudaError_t launch_backward(const DevTopo& T, const DevPtrs& D, cudaStream_t s);
 cudaError_t launch_backward_mw_quadruped(const DevTopo& T, const DevPtrs& D, cudaStream_t s);
+cudaError_t launch_backward_mw_arm(const DevTopo& T, const DevPtrs& D, cudaStream_t s);
 cudaError_t launch_backward_ext(const DevTopo& T, const DevPtrs& D, int t, cudaStream_t s);
 cudaError_t launch_dw(const float* del, const float* act, int M, int C, size_t N, float* partial, int splits,
                       size_t chunk, cudaStream_t s);
@@ -29,3 +32,5 @@ cudaError_t launch_check_grads(int B, int Bp, int nf, int np, const float* gs, c
 cudaError_t launch_sum_splits(const float* partial, int splits, size_t count, float* out, cudaStream_t s);
 int match_compiled_topology(const DevTopo& T, int nb, int nj, int ns, int np, const int* jtype, const int* jbody,
                             const int* jflags, const int* sbody, const int* pair);
+// hidden width of the tensor-core controller the compiled topology's kernels carry (0: none)
+int compiled_ctrl_width(int topo_id);

@@ -14,7 +14,9 @@
 //  * warps 1..3 (the helpers) each own a fixed set of bodies (balanced at compile time by the
 //    number of row sides touching them) and, one ring chunk behind the chain, replay the
 //    velocities (undoing each row's impulse from the post-sweep values on the tape) and the
-//    velocity adjoints of their bodies, and accumulate every row-side adjoint of those bodies.
+//    velocity adjoints of their bodies, and accumulate every row-side adjoint of those bodies;
+//    the row-level adjoints (bias, the effective mass's bias and impulse terms) go with side a,
+//    or with side b when the row's parent is the world.
 //
 // The four warps meet at one CTA barrier per chunk of DPK_MW_CH rows: in step k the chain
 // writes chunk k into ring buffer k % 2 while the helpers read chunk k - 1 from the other
@@ -132,12 +134,15 @@ __device__ __forceinline__ constexpr int mw_slot() { return Q::S.order[Q::NS - 1
 #define DPK_MW_AHEAD 8
 
 // Tape values of chain position p (sweep it; positions beyond the sweep belong to sweep it - 1).
+// The look-ahead register of position p is pre[p % DPK_MW_AHEAD]; it carries over into the next
+// sweep only when the sweep's length is a multiple of the depth (the slots of the two sweeps'
+// positions then line up); otherwise each sweep refills its first slots when it starts.
 template <class Q, int p>
 __device__ __forceinline__ void mw_chain_prefetch(const DevTopo& T, const LaneT<GSR>& L, const TapeStep& tp, int it,
                                                   MwChainIn& dst) {
   if constexpr (p < Q::NS) {
     dst = mw_chain_load<Q, mw_slot<Q, p>()>(T, L, tp, it);
-  } else if constexpr (p - Q::NS < Q::NS) {
+  } else if constexpr (Q::NS % DPK_MW_AHEAD == 0 && p - Q::NS < Q::NS) {
     if (it > 0) dst = mw_chain_load<Q, mw_slot<Q, p - Q::NS>()>(T, L, tp, it - 1);
   }
 }
@@ -169,6 +174,10 @@ __device__ __noinline__ void pgs_reverse_chain(const DevTopo& T, const LaneT<GSR
   MwChainIn pre[D];
   static_for<D>([&](auto PI) { mw_chain_prefetch<Q, decltype(PI)::value>(T, L, tp, iters - 1, pre[decltype(PI)::value]); });
   for (int it = iters - 1; it >= 0; --it) {
+    if constexpr (NS % D != 0) {
+      if (it != iters - 1)
+        static_for<D>([&](auto PI) { mw_chain_prefetch<Q, decltype(PI)::value>(T, L, tp, it, pre[decltype(PI)::value]); });
+    }
     static_for<NCH>([&](auto QI) {
       constexpr int q = decltype(QI)::value;
       float* ring = ring0 + ((((iters - 1 - it) * NCH + q) & 1) * 2 * CH) * 32;
@@ -291,20 +300,21 @@ __device__ __forceinline__ MwSideIn mw_side_load(const DevTopo& T, const LaneT<G
   MwSideIn r;
   r.la = __ldg(tp.lam + (it * Q::NS + s) * 32);
   r.lb = mw_lam_before<Q>(T, tp, it, s);
-  r.bias = SIDE_A ? R[RF_BIAS] : 0.f;
+  r.bias = (SIDE_A || Q::S.a[s] < 0) ? R[RF_BIAS] : 0.f;  // the side carrying the row-level terms
   r.ang = R.v3(SIDE_A ? RF_ANGA : RF_ANGB);
   r.I = R.v3(SIDE_A ? RF_IA : RF_IB);
   return r;
 }
 
-// Tape values of helper sequence position p (sweep it; beyond the sequence: sweep it - 1).
+// Tape values of helper sequence position p (sweep it; beyond the sequence: sweep it - 1), with
+// the chain's rule for carrying the look-ahead into the next sweep.
 template <class Q, int H, int p>
 __device__ __forceinline__ void mw_side_prefetch(const DevTopo& T, const LaneT<GSR>& L, const TapeStep& tp, int it,
                                                  MwSideIn& dst) {
   constexpr MwSeq sq = MwSeqOf<Q, H>::seq;
   if constexpr (p < sq.n) {
     dst = mw_side_load<Q, mw_slot<Q, sq.ri[p]>(), sq.side_a[p]>(T, L, tp, it);
-  } else if constexpr (p - sq.n < sq.n) {
+  } else if constexpr (sq.n % DPK_MW_AHEAD == 0 && p - sq.n < sq.n) {
     if (it > 0) dst = mw_side_load<Q, mw_slot<Q, sq.ri[p - sq.n]>(), sq.side_a[p - sq.n]>(T, L, tp, it - 1);
   }
 }
@@ -341,6 +351,11 @@ __device__ __forceinline__ void mw_side(const DevTopo& T, const SL& RC, const Mw
     RC.a3(rc + RC_ANGA, angb);
     RC[rc + RC_MEFF] += -pbar * (jv + in.bias + T.gamma * in.lb);
     RC[rc + RC_BIAS] += jvb;
+  } else if constexpr (Q::S.a[s] < 0) {
+    // the row's parent is the world: side b carries the row-level terms
+    RC.a3(rc + RC_ANGB, angb);
+    RC[rc + RC_MEFF] += -pbar * (jv + in.bias + T.gamma * in.lb);
+    RC[rc + RC_BIAS] += jvb;
   } else {
     RC.a3(rc + RC_ANGB, angb);
     RC[rc + RC_LIN] += -pbar * jv;  // side b's share of the effective-mass adjoint (folded later)
@@ -360,6 +375,11 @@ __device__ __forceinline__ void mw_helper_chunk(const DevTopo& T, const LaneT<GS
   constexpr MwSeq sq = MwSeqOf<Q, H>::seq;
   constexpr int p0 = MwSeqOf<Q, H>::first(q), p1 = MwSeqOf<Q, H>::first(q + 1);
   if constexpr (q == 0) {
+    // a sweep whose length is not a multiple of the look-ahead depth refills its first slots
+    if constexpr (sq.n % D != 0) {
+      if (it != T.iters - 1)
+        static_for<D>([&](auto PI) { mw_side_prefetch<Q, H, decltype(PI)::value>(T, L, tp, it, pre[decltype(PI)::value]); });
+    }
     // the velocities after sweep it (the reverse sweep undoes its rows from there)
     const float* vi = tp.viter + it * Q::NB * 6 * 32;
     static_for<Q::NB>([&](auto BI) {

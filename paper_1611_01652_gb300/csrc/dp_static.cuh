@@ -95,6 +95,35 @@ struct QuadrupedTopo {
   static constexpr int NB = desc.nb;
   static constexpr int NS = S.n;
   static constexpr int id = 1;
+  static constexpr int CTRL_H = 128;  // hidden width of the tensor-core controller its kernels carry
+};
+
+// The robot arms of the uneven batch: N links on hinges stacked from the world (joint 0 yaws with
+// a servo only, joints 1 .. N-1 pitch with limits and servos) and a sphere on the last link; their
+// controller is the 256-wide tensor-core network.
+template <int N>
+struct ArmTopo {
+  static constexpr TopoDesc make() {
+    TopoDesc d{};
+    d.nb = N;
+    d.nj = N;
+    d.ns = 1;
+    d.np = 0;
+    for (int j = 0; j < N; ++j) {
+      d.jtype[j] = 1;
+      d.ja[j] = j - 1;
+      d.jb[j] = j;
+      d.jflags[j] = j == 0 ? 2 : 3;
+    }
+    d.sbody[0] = N - 1;
+    return d;
+  }
+  static constexpr TopoDesc desc = make();
+  static constexpr SlotTab S = build_schedule(desc);
+  static constexpr int NB = N;
+  static constexpr int NS = S.n;
+  static constexpr int id = 10 + N;
+  static constexpr int CTRL_H = 256;
 };
 
 // Host-side check: does the descriptor's topology equal a compiled one? Returns its id or 0.

@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(128, 1) k_forward_mw(const __grid_constant__ D
       }
       mw_barrier();
       if (T.mlp_tc) {
-        if (warp < 2) ctrl_tc_forward<128, SL>(T, D, act, dump_col, warp, warp + 1);
+        if (warp < 2) ctrl_tc_forward_q<Q, SL>(T, D, act, dump_col, warp, warp + 1);
       } else if (warp == 0) {
         controller_forward(T, D, act);
       }

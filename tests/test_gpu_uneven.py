@@ -89,12 +89,13 @@ def test_batching_runner_graph_and_autotuner():
     eager = ub.losses()
     assert torch.isfinite(dW_eager).all() and dW_eager.abs().max() > 0
     for k, m in bins.items():
-        w = World(m)
+        w = World(m, one_warp=ub.config[k]["one_warp"])  # the tuned mapping's kernels
         loss = torch.zeros(m.B, device="cuda")
         w.rollout(W, loss)
         w.sync()
         assert np.array_equal(loss.cpu().numpy(), eager[k]), k
-        assert len(ub.tuning[k]) == 8 and all(ms > 0 for _, ms in ub.tuning[k])
+        assert len(ub.tuning[k]) == 10 and all(ms > 0 for _, ms in ub.tuning[k])
+        assert {c["one_warp"] for c, _ in ub.tuning[k]} == {False, True}
     ub.capture()
     for _ in range(2):
         dW = ub.run()
@@ -103,12 +104,66 @@ def test_batching_runner_graph_and_autotuner():
         for k in bins:
             assert np.array_equal(replay[k], eager[k]), k
         assert torch.equal(dW, dW_eager)
-    # every launch configuration computes the same rollout (splits only reorder the dW sums)
+    # every launch configuration of one mapping computes the same rollout (splits only reorder the
+    # dW sums); the four-warp and one-warp mappings are compared in the next test
     ub2 = UnevenBatch(bins, W, tune=False)
     dW2 = ub2.run()
     torch.cuda.synchronize()
     other = ub2.losses()
-    for k in bins:
+    same = [k for k in bins if ub.config[k]["one_warp"] == ub2.config[k]["one_warp"]]
+    for k in same:
         assert np.array_equal(other[k], eager[k]), k
-    assert rel_err(dW2.cpu().double().numpy(), dW_eager.cpu().double().numpy()) <= 1e-5
+    if len(same) == len(bins):
+        assert rel_err(dW2.cpu().double().numpy(), dW_eager.cpu().double().numpy()) <= 1e-5
+    assert torch.isfinite(dW2).all()
     assert ub.instance_steps == sum(int(np.sum(m.horizons)) for m in bins.values())
+
+
+@pytest.mark.parametrize("tc", [True, False])
+def test_arm_mappings_agree(tc):
+    """The arms (3-7 links) match compiled topologies: by default their recorded rollout and
+    reverse pass run on four warps per group of 32 instances (the compiled kernels); with
+    one_warp the run-time topology's one-warp kernels run instead. Both compute the same rollout
+    and gradients, on instances whose contact and clamp activity agree (a near tie may go either
+    way in float32). With the float32 controller: states and losses within 1e-4, gradients
+    element by element within 1e-3. With the bfloat16 tensor-core controller the two mappings'
+    float32 sums differ in their last bits, and a bfloat16 storage point of the controller can
+    turn such a difference into one bfloat16 step (2^-8 relative) of its input: states and losses
+    within 2e-3 for 90 % of the instances, gradients within 1e-2 (relative norm per instance)."""
+    bins = WL.arms(B=96, hmin=10, hmax=30, seed=1031)
+    compared = total = close = 0
+    for n, m in bins.items():
+        if not tc:
+            m.ctrl_fp32 = 1
+        out = []
+        for one in (False, True):
+            w = World(m, one_warp=one)
+            T = w.horizon
+            traj = torch.zeros(T + 1, m.B, m.nb, 18, device="cuda")
+            act = torch.zeros(T, m.B, w.n_slots, dtype=torch.uint8, device="cuda")
+            loss = torch.zeros(m.B, device="cuda")
+            w.rollout(torch.tensor(m.W, device="cuda"), loss, traj, act)
+            dW = torch.zeros(w.n_params, device="cuda")
+            ds = torch.zeros(m.B, m.nb, 18, device="cuda")
+            w.backward(torch.ones(m.B, device="cuda"), dW, ds)
+            w.sync()
+            out.append([x.cpu().double().numpy() for x in (traj, act, loss, dW, ds)])
+            w.free()
+        (t4, a4, l4, w4, s4), (t1, a1, l1, w1, s1) = out
+        agree = [i for i in range(m.B) if np.array_equal(a4[:, i], a1[:, i])]
+        total += m.B
+        compared += len(agree)
+        for i in agree:
+            err = (np.abs(t4[:, i] - t1[:, i]) / np.maximum(1.0, np.abs(t1[:, i]))).max()
+            lerr = abs(l4[i] - l1[i]) / max(1.0, abs(l1[i]))
+            if not tc:
+                assert err <= 1e-4 and lerr <= 1e-4, (n, i, err, lerr)
+                assert elem_err(s4[i], s1[i]) <= 1e-3, (n, i)
+            elif err <= 2e-3 and lerr <= 2e-3:
+                close += 1
+                assert rel_err(s4[i], s1[i]) <= 1e-2, (n, i, rel_err(s4[i], s1[i]))
+        if not tc and len(agree) == m.B:
+            assert elem_err(w4, w1) <= 1e-3, n
+    assert compared >= 0.9 * total, (compared, total)
+    if tc:
+        assert close >= 0.9 * compared, (close, compared)
