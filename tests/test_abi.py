@@ -168,3 +168,38 @@ def test_camera_validation_rejects_bad_scene(case, needle):
     assert needle in lib.dp_camera_last_error()
     st = lib.dp_render_backward(C.byref(cam), C.byref(sc), 1, 1, None, None, None, None, None, None)
     assert st == binding.DP_EINVAL
+
+
+def _struct_members(src, name):
+    """Member names of the C struct typedef `name` in declaration order."""
+    body = re.search(r"typedef struct\s*\{(.*?)\}\s*" + name + r"\s*;", src, flags=re.S).group(1)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        m = re.match(r"(?:const\s+)?[A-Za-z_][A-Za-z_0-9]*\s*\**\s*(.*)$", decl, flags=re.S)
+        for part in m.group(1).split(","):
+            names.append(re.sub(r"\[.*?\]", "", part).replace("*", "").strip())
+    return names
+
+
+def test_batch_descriptor_layout_agrees_with_header():
+    """The binding's ctypes descriptor lists the header's dp_batch_desc members in the same order
+    (the launch-configuration fields rows_global, dw_splits and one_warp included)."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    assert _struct_members(src, "dp_batch_desc") == [f[0] for f in binding.BatchDesc._fields_]
+
+
+def test_autotuner_space_covers_both_mappings():
+    """The uneven batch's autotuner times one warp per group with every row, tape and split choice,
+    and four warps per group (the compiled topologies' kernels keep the rows on chip and the whole
+    tape) with each split count."""
+    from paper_1611_01652_gb300 import batching
+
+    cands = batching.CANDIDATES
+    four = [c for c in cands if not c["one_warp"]]
+    one = [c for c in cands if c["one_warp"]]
+    assert len(one) == 8 and len(four) == 2
+    assert all(not c["rows_global"] and c["ckpt_every"] == 0 for c in four)
+    assert {c["dw_splits"] for c in four} == {64, 256}
