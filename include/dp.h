@@ -383,7 +383,7 @@ dp_status dp_ws_adam(float* W, const float* dW, float* m, float* v, int64_t coun
 #define DP_CAMERA_MAX_OBJECTS 16
 
 typedef struct {
-  int32_t width, height; /* pixels */
+  int32_t width, height; /* pixels; width * height < 2^24 (DP_EINVAL otherwise) */
   float focal;           /* focal length f in pixels */
   float plane;           /* distance P of the projection plane from the camera centre (world units) */
   float position[3];     /* camera centre C (world) */

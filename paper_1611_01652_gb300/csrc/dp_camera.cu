@@ -29,6 +29,7 @@ struct CamArgs {
   int W, H, B, nb, n_obj, th, tw;
   int cull;  // screen rectangles per object (DP_CAMERA_NO_CULL turns them off, for comparison)
   float f, plane;
+  float pf, invW;  // plane / f and 1 / W (per-pixel arithmetic without divisions)
   float C[3], Rc[9];
   int body[kMaxObj], tex[kMaxObj], kind[kMaxObj];
   float cen[kMaxObj][3], half[kMaxObj][3];
@@ -47,6 +48,10 @@ struct Hit {
 struct BoxFrame {
   float R[9], cw[3], o[3];
   float rect[4];
+  // staged frames: the ray direction in the object's frame is affine in the pixel's camera
+  // coordinates (x, y) = (P/f (j + 1/2 - W/2), P/f (i + 1/2 - H/2)): dl = x e[0..2] + y e[3..5] +
+  // e[6..8], with e the object's R^T times the camera's first two rows and P times its third
+  float e[9];
 };
 
 __device__ __forceinline__ float pick3(const float (&v)[3], int k) { return k == 0 ? v[0] : (k == 1 ? v[1] : v[2]); }
@@ -127,6 +132,13 @@ __device__ __forceinline__ bool stage_frames(const CamArgs& A, const float* __re
     for (int o = threadIdx.x; o < A.n_obj; o += blockDim.x) {
       box_frame(A, state, inst0, o, sf[o]);
       screen_rect(A, o, sf[o]);
+      BoxFrame& F = sf[o];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        F.e[k] = F.R[k] * A.Rc[0] + F.R[3 + k] * A.Rc[1] + F.R[6 + k] * A.Rc[2];
+        F.e[3 + k] = F.R[k] * A.Rc[3] + F.R[3 + k] * A.Rc[4] + F.R[6 + k] * A.Rc[5];
+        F.e[6 + k] = A.plane * (F.R[k] * A.Rc[6] + F.R[3 + k] * A.Rc[7] + F.R[6 + k] * A.Rc[8]);
+      }
     }
   __syncthreads();
   return uniform;
@@ -146,6 +158,23 @@ __device__ __forceinline__ bool pixel_of(const CamArgs& A, bool uniform, int ins
   return true;
 }
 
+// Row i and column j of pixel pix: the float quotient (pix < W H < 2^24, exact in float; the
+// product with the rounded 1/W is within one row), moved by one row when rounding put it across a
+// row boundary, so the result is exact.
+__device__ __forceinline__ void pixel_ij(const CamArgs& A, int pix, int& i, int& j) {
+  int q = (int)(((float)pix + 0.5f) * A.invW);
+  int r = pix - q * A.W;
+  if (r < 0) {
+    --q;
+    r += A.W;
+  } else if (r >= A.W) {
+    ++q;
+    r -= A.W;
+  }
+  i = q;
+  j = r;
+}
+
 __device__ __forceinline__ void ray_dir(const CamArgs& A, int i, int j, float d[3]) {
   const float dc0 = A.plane * (((float)j + 0.5f) - 0.5f * (float)A.W) / A.f;
   const float dc1 = A.plane * (((float)i + 0.5f) - 0.5f * (float)A.H) / A.f;
@@ -158,8 +187,13 @@ __device__ __forceinline__ void ray_dir(const CamArgs& A, int i, int j, float d[
 // box frames from shared memory (sf) when staged, else computed here.
 __device__ Hit trace(const CamArgs& A, const float* __restrict__ state, const BoxFrame* sf, bool staged, int inst, int i,
                      int j) {
-  float d[3];
-  ray_dir(A, i, j, d);
+  float d[3], x = 0.f, y = 0.f;
+  if (staged) {  // the pixel's camera coordinates (per-object directions from the staged e)
+    x = A.pf * (((float)j + 0.5f) - 0.5f * (float)A.W);
+    y = A.pf * (((float)i + 0.5f) - 0.5f * (float)A.H);
+  } else {
+    ray_dir(A, i, j, d);
+  }
   Hit h;
   h.obj = -1;
   h.k = 0;
@@ -169,13 +203,16 @@ __device__ Hit trace(const CamArgs& A, const float* __restrict__ state, const Bo
                    (float)i > sf[o].rect[3]))
       continue;  // outside the object's screen rectangle: no hit
     BoxFrame F;
-    if (staged)
-      F = sf[o];
-    else
-      box_frame(A, state, inst, o, F);
     float dl[3];
+    if (staged) {
+      F = sf[o];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) dl[k] = F.R[k] * d[0] + F.R[3 + k] * d[1] + F.R[6 + k] * d[2];
+      for (int k = 0; k < 3; ++k) dl[k] = fmaf(x, F.e[k], fmaf(y, F.e[3 + k], F.e[6 + k]));
+    } else {
+      box_frame(A, state, inst, o, F);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) dl[k] = F.R[k] * d[0] + F.R[3 + k] * d[1] + F.R[6 + k] * d[2];
+    }
     if (A.kind[o] != DP_OBJ_BOX) {
       float tn;
       int kn;
@@ -297,7 +334,10 @@ __device__ __forceinline__ Sample sample_of(const CamArgs& A, const Hit& h) {
   return S;
 }
 
-__global__ void __launch_bounds__(kThreads, 6) k_render(const __grid_constant__ CamArgs A, const float* __restrict__ state,
+#ifndef DPK_RENDER_BLOCKS
+#define DPK_RENDER_BLOCKS 6
+#endif
+__global__ void __launch_bounds__(kThreads, DPK_RENDER_BLOCKS) k_render(const __grid_constant__ CamArgs A, const float* __restrict__ state,
                                                      const float* __restrict__ tex, float* __restrict__ image,
                                                      int* __restrict__ hit_out) {
   __shared__ BoxFrame sf[kMaxObj];
@@ -308,7 +348,8 @@ __global__ void __launch_bounds__(kThreads, 6) k_render(const __grid_constant__ 
   for (int r = 0; r < kPixPerThread; ++r) {
     int inst, pix;
     if (!pixel_of(A, staged, inst0, pix0, r, inst, pix)) break;
-    const int i = pix / A.W, j = pix - i * A.W;
+    int i, j;
+    pixel_ij(A, pix, i, j);
     const Hit h = trace(A, state, sf, staged, inst, i, j);
     float col[3] = {0.f, 0.f, 0.f};
     if (h.obj >= 0) {
@@ -351,7 +392,8 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__
   for (int k = 0; k < 12; ++k) g[k] = 0.f;
   int gb = -1;  // body receiving g (-1: none)
   if (live) {
-    const int pix = pixr, i = pix / A.W, j = pix - (pix / A.W) * A.W;
+    int i, j;
+    pixel_ij(A, pixr, i, j);
     const Hit h = trace(A, state, sf, staged, inst, i, j);
     if (h.obj >= 0) {
       const Sample S = sample_of(A, h);
@@ -477,6 +519,10 @@ dp_status cam_args(const dp_camera* cam, const dp_scene* sc, int32_t B, int32_t 
     g_cam_err = "camera: width, height, focal and plane must be positive";
     return DP_EINVAL;
   }
+  if ((long long)cam->width * cam->height >= (1LL << 24)) {
+    g_cam_err = "camera: width * height must be below 2^24 pixels";
+    return DP_EINVAL;
+  }
   if (B < 0 || nb < 0 || sc->n_obj < 0 || sc->n_obj > kMaxObj) {
     g_cam_err = "scene: n_obj out of range [0, DP_CAMERA_MAX_OBJECTS], or a negative size";
     return DP_EINVAL;
@@ -495,6 +541,8 @@ dp_status cam_args(const dp_camera* cam, const dp_scene* sc, int32_t B, int32_t 
   A.tw = sc->tex_w;
   A.f = cam->focal;
   A.plane = cam->plane;
+  A.pf = cam->plane / cam->focal;
+  A.invW = 1.f / (float)cam->width;
   A.cull = getenv("DP_CAMERA_NO_CULL") ? 0 : 1;
   for (int k = 0; k < 3; ++k) A.C[k] = cam->position[k];
   for (int k = 0; k < 9; ++k) A.Rc[k] = cam->rotation[k];
