@@ -18,8 +18,8 @@ cudaError_t launch_forward(const DevTopo& T, const DevPtrs& D, const float* x0, 
   // rollouts run on four warps per group (not the harvest or gait noise, and not when the world
   // asks for one warp per group). The compiled arms have no one-warp kernels of their own: their
   // other launches take the run-time path.
-  if (T.topo_id != 0 && T.sm_rows >= 0 && record && rollout && !D.harvest && !D.u_noise && !T.ws_net &&
-      !T.one_warp && !getenv("DP_SINGLE_WARP_FORWARD"))
+  if (T.topo_id != 0 && T.sm_rows >= 0 && record && rollout && !D.harvest && !D.u_noise && !T.one_warp &&
+      !getenv("DP_SINGLE_WARP_FORWARD"))
     return T.topo_id == QuadrupedTopo::id ? launch_forward_mw_quadruped(T, D, x0, t0, nsteps, rollout, s)
                                           : launch_forward_mw_arm(T, D, x0, t0, nsteps, rollout, s);
   if (T.topo_id == QuadrupedTopo::id && T.sm_rows >= 0)

@@ -110,6 +110,13 @@ __global__ void __launch_bounds__(32, 1) k_forward(const __grid_constant__ DevTo
   if (bad && i < B) D.status[i] |= DPK_ST_NAN_STATE;
 }
 
+// The one-warp warm start with the solver tape, out of line (it runs on one warp of k_forward_mw
+// and keeps the network's registers out of that kernel's budget).
+static __device__ __noinline__ void warm_start_call(const DevTopo& T, const DevPtrs& D, const LaneT<SL>& L, const SL& X,
+                                             const TapeStep& tp) {
+  warm_start<true>(T, D, L, X, tp);
+}
+
 // Persistent rollout of the compiled topology with the solver tape, on four warps per group of
 // 32 instances (one CTA per group; a lane is an instance in every warp, as in k_forward). The
 // stages outside the sweeps are split: warp w takes the joints and bodies it owns
@@ -210,7 +217,15 @@ __global__ void __launch_bounds__(128, 1) k_forward_mw(const __grid_constant__ D
     assemble_rows(T, L, X, ao, warp, 4);
     mw_barrier();
     for (int f = warp; f < T.nslots * RF_N; f += 4) tp.rows[f * 32] = L.rows[f];
-    if (T.ws) warm_start_mw<true>(T, L, X, tp, warp, bm);
+    if (T.ws) {
+      if (T.ws_net) {
+        // a learned network's start: the one-warp stage (features, the network on the tensor
+        // cores, projection, application to every body) on warp 0, as in k_forward
+        if (warp == 0) warm_start_call(T, D, L, X, tp);
+      } else {
+        warm_start_mw<true>(T, L, X, tp, warp, bm);
+      }
+    }
     mw_barrier();
     if (warp == 0) {
       pgs_solve_static<Q, true>(T, L, X, tp);

@@ -160,22 +160,27 @@ def test_tensor_core_widths_teacher_forced_steps(monkeypatch, widths):
     assert w.controller_kind == CTRL_TENSOR
 
 
-@pytest.mark.parametrize("case", ["bf16 damped start", "bf16 cold", "fp32 controller", "recurrent"])
+@pytest.mark.parametrize("case", ["bf16 damped start", "learned start", "bf16 cold", "fp32 controller", "recurrent"])
 def test_four_warp_rollout_matches_single_warp(monkeypatch, case):
     """The compiled topology's recorded rollouts run on four warps per group of 32 instances; the
     one-warp kernel (forced here) must give the same trajectory, activity log, losses, solver tape
-    (through the gradients of the reverse pass that reads it) and final state, bit for bit."""
+    (through the gradients of the reverse pass that reads it) and final state, bit for bit. With a
+    learned warm-start network (a seeded random one) the four-warp kernel runs the one-warp warm
+    start on its first warp."""
     m = WL.quadruped(B=40, horizon=30, n_recurrent=4 if case == "recurrent" else 0)
     if case == "fp32 controller":
         m.ctrl_fp32 = 1
-    warm = case == "bf16 damped start"
+    warm = case in ("bf16 damped start", "learned start")
+    net = torch.zeros(WS_PARAMS, device="cuda")
+    if case == "learned start":
+        net = 0.05 * torch.randn(WS_PARAMS, generator=torch.Generator().manual_seed(5)).cuda()
     outs = []
     for single in (False, True):
         if single:
             monkeypatch.setenv("DP_SINGLE_WARP_FORWARD", "1")
         w = World(m, horizon=30, iters=10 if warm else 20, warmstart=warm)
         if warm:
-            w.set_warmstart(torch.zeros(WS_PARAMS, device="cuda"), 0.7)
+            w.set_warmstart(net, 0.7)
         W = torch.tensor(m.W, device="cuda")
         traj = torch.zeros(31, m.B, m.nb, 18, device="cuda")
         act = torch.zeros(30, m.B, w.n_slots, dtype=torch.uint8, device="cuda")
