@@ -262,7 +262,6 @@ __device__ __forceinline__ constexpr int mw_local(int body) {
   return n;
 }
 
-
 // The row sides of helper H's bodies in reverse sweep order: reverse position and side. The
 // helper's loop is unrolled over this sequence, so slots, sides and its bodies' registers are
 // compile-time constants, and the tape values of the next DPK_MW_AHEAD row sides are in flight
